@@ -1,0 +1,231 @@
+"""Pins of the FP64 CPU oracle against closed forms, brute force and invariants.
+
+Nothing here calls the CUDA library.  Each test is chosen so that a plausible slip in
+the oracle (a dropped h^3, a wrong sign, a transposed operand, a wrong transition
+index) fails at least one of them.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import integrate
+from scipy.special import erf
+
+import oracle
+from paper_2405_01522_gb300 import inputs
+
+GOLDEN = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "constants.json")))
+
+
+def rng_fields(shape, k, seed):
+    r = np.random.default_rng(seed)
+    return r.standard_normal((k,) + tuple(shape))
+
+
+# ---------------------------------------------------------------- kernel and Poisson
+
+
+def test_c0_equals_cube_integral():
+    v, _ = integrate.tplquad(lambda z, y, x: 1.0 / math.sqrt(x * x + y * y + z * z),
+                             0, 0.5, 0, 0.5, 0, 0.5, epsabs=1e-12, epsrel=1e-12)
+    assert abs(8 * v - oracle.C0) < 1e-9
+    assert abs(oracle.C0 - GOLDEN["C0_cube_integral"]["value"]) < 1e-15
+
+
+@pytest.mark.parametrize("shape", [(16, 16, 16), (6, 10, 8), (5, 7, 3)])
+def test_poisson_fft_equals_direct_sum(shape):
+    """2x padding makes the periodic FFT convolution the exact aperiodic sum (Sec. 3.1)."""
+    rho = rng_fields(shape, 1, 1)[0]
+    h = 0.37
+    vf = oracle.poisson_fft(rho, h)
+    vd = oracle.poisson_direct(rho, h)
+    assert np.max(np.abs(vf - vd)) <= 1e-12 * np.max(np.abs(vd))
+
+
+def test_kernel_spectrum_real_even_positive():
+    g = oracle.kernel_samples((24, 20, 16), 0.3)
+    full = np.fft.fftn(g)
+    assert np.max(np.abs(full.imag)) < 1e-10 * np.max(np.abs(full.real))
+    assert full.real.min() > 0.0
+    half = oracle.kernel_spectrum((24, 20, 16), 0.3)
+    assert np.allclose(half, full.real[:, :, :9])
+
+
+def gaussian_case(h, L=12.0):
+    n = int(round(L / h))
+    n += n % 2
+    z, y, x = inputs.grid_axes((n, n, n), h)
+    r2 = z[:, None, None] ** 2 + y[None, :, None] ** 2 + x[None, None, :] ** 2
+    rho = np.exp(-r2) / math.pi ** 1.5
+    return n, rho, np.sqrt(r2)
+
+
+def test_gaussian_density_erf_potential_converges():
+    """Normalised Gaussian: V -> erf(r)/r, E_H -> 1/sqrt(2 pi), error O(h^2)."""
+    errs = []
+    hs = (0.4, 0.3, 0.2)
+    for h in hs:
+        n, rho, r = gaussian_case(h)
+        v = oracle.poisson_fft(rho, h)
+        exact = np.where(r > 0, erf(r) / np.where(r > 0, r, 1.0), 2 / math.sqrt(math.pi))
+        assert np.max(np.abs(v - exact)) < 0.1 * h ** 2
+        eh = 0.5 * h ** 3 * np.sum(rho * v)
+        err = abs(eh - GOLDEN["gaussian_hartree_alpha1"]["value"])
+        assert err < 0.015 * h ** 2
+        errs.append(err)
+    for (h1, e1), (h2, e2) in zip(zip(hs, errs), zip(hs[1:], errs[1:])):
+        order = math.log(e1 / e2) / math.log(h1 / h2)
+        assert 1.7 < order < 2.4, order
+    # the centre value approaches 2/sqrt(pi)
+    n, rho, r = gaussian_case(0.2)
+    v = oracle.poisson_fft(rho, 0.2)
+    assert abs(v[n // 2, n // 2, n // 2] - GOLDEN["gaussian_potential_origin_alpha1"]["value"]) < 5e-3
+
+
+# ---------------------------------------------------------------- exchange (Eq. 2)
+
+
+def test_exchange_matches_bruteforce_loops():
+    phi = rng_fields((3, 4, 3), 2, 2)
+    psi = rng_fields((3, 4, 3), 3, 3)
+    h = 0.5
+    a = oracle.exchange_apply(phi, psi, h)
+    b = oracle.exchange_apply_bruteforce(phi, psi, h)
+    assert np.max(np.abs(a - b)) <= 1e-12 * np.max(np.abs(b))
+
+
+def test_one_orbital_exchange_is_minus_hartree():
+    s = inputs.exchange_system(n=16, h=0.4, nocc=1)
+    ex = oracle.exchange_energy(s.phi, s.h)
+    eh = oracle.hartree_energy(s.phi[0] ** 2, s.h)
+    assert ex < 0 and eh > 0
+    assert abs(ex + eh) <= 1e-12 * eh
+
+
+def test_exchange_symmetric_and_negative_definite():
+    s = inputs.exchange_system(n=16, h=0.4, nocc=3, npsi=4)
+    f = np.concatenate([s.phi, s.psi])
+    vf = oracle.exchange_apply(s.phi, f, s.h)
+    X = s.h ** 3 * f.reshape(len(f), -1) @ vf.reshape(len(f), -1).T
+    assert np.max(np.abs(X - X.T)) <= 1e-12 * np.max(np.abs(X))
+    assert np.linalg.eigvalsh(0.5 * (X + X.T)).max() < 0
+
+
+def test_exchange_linear_in_psi_and_quadratic_in_phi():
+    s = inputs.exchange_system(n=12, h=0.5, nocc=2, npsi=2)
+    a = oracle.exchange_apply(s.phi, s.psi, s.h)
+    comb = oracle.exchange_apply(s.phi, (2.0 * s.psi[0] - 3.0 * s.psi[1])[None], s.h)[0]
+    assert np.allclose(comb, 2.0 * a[0] - 3.0 * a[1], rtol=0, atol=1e-12 * np.abs(a).max())
+    scaled = oracle.exchange_apply(2.0 * s.phi, s.psi, s.h)
+    assert np.allclose(scaled, 4.0 * a, rtol=0, atol=1e-12 * np.abs(a).max())
+
+
+# ---------------------------------------------------------------- ACE (Eqs. 11-13)
+
+
+def test_ace_reproduces_exchange_on_its_orbitals():
+    s = inputs.exchange_system(n=16, h=0.4, nocc=4, npsi=3)
+    zeta, W, M, L = oracle.ace_build(s.phi, s.h, return_all=True)
+    assert np.allclose(L @ L.T, -M, atol=1e-13 * np.abs(M).max())
+    vace = oracle.ace_apply(zeta, s.phi, s.h)
+    assert np.max(np.abs(vace - W)) <= 1e-11 * np.max(np.abs(W))
+    # rank k: zeta spans span(W)
+    k = s.phi.shape[0]
+    assert np.linalg.matrix_rank(zeta.reshape(k, -1), tol=1e-8 * np.abs(zeta).max()) == k
+
+
+def test_ace_bounds_exchange_from_above():
+    """With Vx negative definite, V^ACE - Vx is positive semi-definite."""
+    s = inputs.exchange_system(n=16, h=0.4, nocc=3, npsi=5)
+    zeta = oracle.ace_build(s.phi, s.h)
+    vx = oracle.exchange_apply(s.phi, s.psi, s.h)
+    va = oracle.ace_apply(zeta, s.psi, s.h)
+    for p in range(s.psi.shape[0]):
+        ex = oracle.inner(s.psi[p], vx[p], s.h)
+        ea = oracle.inner(s.psi[p], va[p], s.h)
+        assert ea >= ex - 1e-12 * abs(ex)
+        assert ea < 0
+
+
+# ---------------------------------------------------------------- Casida (Eq. 7)
+
+
+def test_casida_K_matches_bruteforce_double_sum():
+    rng = np.random.default_rng(5)
+    po = rng.standard_normal((2, 3, 4, 3))
+    pv = rng.standard_normal((3, 3, 4, 3))
+    h = 0.45
+    a = oracle.casida_K(po, pv, h)
+    b = oracle.casida_K_bruteforce(po, pv, h)
+    assert np.max(np.abs(a - b)) <= 1e-12 * np.max(np.abs(b))
+
+
+def test_casida_K_symmetric_psd_and_Kd_symmetric():
+    s = inputs.casida_system(n=12, h=0.5, nocc=2, nvirt=3)
+    K = oracle.casida_K(s.phi, s.phi_virt, s.h)
+    Kd = oracle.casida_Kd(s.phi, s.phi_virt, s.h)
+    assert np.max(np.abs(K - K.T)) <= 1e-13 * np.abs(K).max()
+    assert np.linalg.eigvalsh(K).min() > -1e-12 * np.abs(K).max()
+    assert np.max(np.abs(Kd - Kd.T)) <= 1e-13 * np.abs(Kd).max()
+    # transition index t = i * nv + a: (ia|ia) is the self energy of rho_ia
+    nv = s.phi_virt.shape[0]
+    for i in range(2):
+        for a in range(nv):
+            e = 2 * oracle.hartree_energy(s.phi[i] * s.phi_virt[a], s.h)
+            assert abs(K[i * nv + a, i * nv + a] - e) <= 1e-12 * abs(e)
+    # K_d[ia, jb] = (ab|ji): the diagonal is <phi_a^2, V[phi_i^2]>
+    for i in range(2):
+        for a in range(nv):
+            v = oracle.poisson_fft(s.phi[i] ** 2, s.h)
+            e = oracle.inner(s.phi_virt[a] ** 2, v, s.h)
+            assert abs(Kd[i * nv + a, i * nv + a] - e) <= 1e-12 * abs(e)
+
+
+def test_casida_independent_particle_limit():
+    s = inputs.casida_system(n=8, h=0.6, nocc=3, nvirt=4)
+    nt = 12
+    A = oracle.tda_matrix(s.eps_occ, s.eps_virt, np.zeros((nt, nt)), None, delta_M=2.0)
+    w, _ = oracle.tda_solve(A, nt)
+    ipa = np.sort((s.eps_virt[None, :] - s.eps_occ[:, None]).ravel())
+    assert np.allclose(w, ipa, atol=1e-14)
+
+
+def test_casida_one_transition_closed_form():
+    s = inputs.casida_system(n=10, h=0.5, nocc=1, nvirt=1)
+    K = oracle.casida_K(s.phi, s.phi_virt, s.h)
+    Kd = oracle.casida_Kd(s.phi, s.phi_virt, s.h)
+    for dm in (2.0, 0.0, 1.0):
+        A = oracle.tda_matrix(s.eps_occ, s.eps_virt, K, Kd, delta_M=dm)
+        w, x = oracle.tda_solve(A, 1)
+        exact = s.eps_virt[0] - s.eps_occ[0] + dm * K[0, 0] - Kd[0, 0]
+        assert abs(w[0] - exact) < 1e-14
+        assert abs(abs(x[0, 0]) - 1) < 1e-14
+
+
+def test_tda_solve_eigenpairs():
+    s = inputs.casida_system(n=10, h=0.5, nocc=2, nvirt=3)
+    K = oracle.casida_K(s.phi, s.phi_virt, s.h)
+    A = oracle.tda_matrix(s.eps_occ, s.eps_virt, K, None, delta_M=1.0)
+    w, X = oracle.tda_solve(A, 4)
+    assert np.all(np.diff(w) >= 0)
+    for k in range(4):
+        assert np.linalg.norm(A @ X[k] - w[k] * X[k]) < 1e-12
+    assert np.allclose(X @ X.T, np.eye(4), atol=1e-12)
+
+
+# ---------------------------------------------------------------- shared input generator
+
+
+def test_splitmix64_published_outputs():
+    r = inputs.SplitMix64(0)
+    got = [hex(r.next_u64()), hex(r.next_u64())]
+    assert got == GOLDEN["splitmix64_seed0_first_outputs"]["value"]
+
+
+def test_orbitals_orthonormal():
+    s = inputs.exchange_system(n=16, h=0.4, nocc=4)
+    f = s.phi.reshape(4, -1)
+    S = s.h ** 3 * f @ f.T
+    assert np.allclose(S, np.eye(4), atol=1e-6)

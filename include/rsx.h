@@ -1,0 +1,132 @@
+/* rsx.h — C ABI of librsx: real-space exact exchange on one GB300 (sm_103a).
+ *
+ * Method: Panta & Strubbe, "Implementation of time-dependent Hartree-Fock in real
+ * space", arXiv 2405.01522.
+ *   Eq. 2 (Sec. 2)       exchange action  (Vx psi_p)(r) = -sum_j phi_j(r) int phi_j(r') psi_p(r') / |r - r'| dr'
+ *   Sec. 3.1             the integral solved as a Poisson problem for rho = phi_j psi_p
+ *   Eqs. 11-13 (Sec 3.1) ACE: W = Vx Phi, M = <Phi, W>, -M = L L^T, zeta = W L^-T, V^ACE = -zeta zeta^T
+ *   Eqs. 6-7 (Sec. 2)    Tamm-Dancoff coupling (ia|jb) and A = diag(de) + delta_M K - K_d
+ *
+ * Discretisation (the paper does not fix one; this is the library's reading):
+ *   grid point (z, y, x) at r = ((x - nx/2) h, (y - ny/2) h, (z - nz/2) h); orbitals are
+ *   zero outside the box.  The potential of a density is V(r) = h^3 sum_r' rho(r') g(r - r')
+ *   with g(d) = 1/(h |d|) and g(0) = C0/h, C0 = 3 ln(2 + sqrt 3) - pi/2 (cell average of
+ *   1/r).  It is evaluated exactly (up to rounding) by FFT on the box padded to 2n per
+ *   axis.  Inner products are <f, g> = h^3 sum_r f(r) g(r).
+ *
+ * Conventions for every call:
+ *   - Array arguments are DEVICE pointers owned by the caller, contiguous, layout
+ *     [orbital][z][y][x] (x fastest), element type double (RSX_FP64 context) or float
+ *     (RSX_FP32 context).  Matrices (M, K, omega, X) are always double.
+ *   - Work is enqueued on `stream` (a cudaStream_t; NULL = legacy default stream) and
+ *     the call returns without synchronising.  Device-side failures found later
+ *     (a non positive definite ACE matrix, a wait that timed out) are reported by
+ *     rsx_sync_status.
+ *   - Return value: RSX_OK or an error code; rsx_last_error gives a message.  No call
+ *     exits, aborts or falls back to a CPU path.
+ *   - The library owns only its workspace (kernel table, twiddles, FFT intermediates,
+ *     panels), allocated in rsx_create or grown by the calls; it never frees or keeps
+ *     caller memory.  One context per stream; contexts share no state.
+ *   - Supported box edges: 16, 24, 32, 40, 48, 56, 64, 80, 96, 112 (padded 2n = 16 A
+ *     with A in {2,3,4,5,6,7,8,10,12,14}); nz must equal ny, nx may differ.
+ */
+#ifndef RSX_H
+#define RSX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rsx_ctx rsx_ctx;
+
+enum {
+  RSX_OK = 0,
+  RSX_EINVAL = 1,         /* bad size, null pointer, unsupported aliasing */
+  RSX_ENOMEM = 2,         /* device allocation failed or workspace limit exceeded */
+  RSX_ECUDA = 3,          /* a CUDA runtime call failed (message in rsx_last_error) */
+  RSX_ENOTPD = 4,         /* -M not positive definite in the ACE Cholesky (deferred) */
+  RSX_ETIMEOUT = 5,       /* a bounded device wait gave up (deferred) */
+  RSX_EUNSUPPORTED = 6    /* box edge or mode not supported */
+};
+
+enum { RSX_FP64 = 0, RSX_FP32 = 1 };
+
+/* Create a context for box (nz, ny, nx) with spacing h (bohr) on `device`.
+ * Builds the kernel spectrum table (h^3 / N_pad times the DFT of g on the padded grid)
+ * and the FFT twiddles on the device; synchronises the device once.
+ * precision: RSX_FP64 or RSX_FP32 (element type of every orbital array).
+ * Errors: RSX_EINVAL (null ctx, h <= 0), RSX_EUNSUPPORTED (edge), RSX_ENOMEM, RSX_ECUDA. */
+int rsx_create(rsx_ctx** ctx, int nz, int ny, int nx, double h, int precision, int device);
+
+/* Free the context and its workspace (synchronises the device).  NULL is a no-op. */
+int rsx_destroy(rsx_ctx* ctx);
+
+/* Message of the last failing call on this context ("" if none).  Valid until the next call. */
+const char* rsx_last_error(const rsx_ctx* ctx);
+
+/* Limit (bytes) on the FFT-intermediate workspace; calls split their pair batch to stay
+ * within it.  Default: 40% of the device memory free at rsx_create, at most 64 GiB. */
+int rsx_set_workspace_limit(rsx_ctx* ctx, size_t bytes);
+
+/* Pair densities rho_q = a_i * b_k (Sec. 3.1: the density whose potential Eq. 2 needs),
+ * q = i * nb + k.  a: [na][N], b: [nb][N], rho: [na * nb][N] (must not alias a or b).
+ * Errors: RSX_EINVAL. */
+int rsx_build_pair_densities(rsx_ctx* ctx, const void* a, int na, const void* b, int nb, void* rho,
+                             void* stream);
+
+/* Exact-exchange action of Eq. 2: out_p = Vx[phi] psi_p = -sum_j phi_j V[phi_j psi_p],
+ * for p < npsi, j < nocc; nocc * npsi pair Poisson solves.
+ * phi: [nocc][N], psi: [npsi][N], out: [npsi][N] (must not alias phi or psi).
+ * Errors: RSX_EINVAL (nocc < 1, npsi < 1, null, aliasing), RSX_ENOMEM. */
+int rsx_exchange_apply(rsx_ctx* ctx, const void* phi, int nocc, const void* psi, int npsi, void* out,
+                       void* stream);
+
+/* ACE projectors of Eqs. 11-12 from the orbitals phi (nocc <= 64):
+ * W = Vx[phi] phi (nocc (nocc + 1) / 2 solves, rho_ij = rho_ji), M_kl = <phi_k, W_l>
+ * symmetrised (FP64), -M = L L^T by FP64 Cholesky on the device, xi = L^-1 W.
+ * phi: [nocc][N]; xi: [nocc][N] (must not alias phi); M_out: device double [nocc][nocc]
+ * receiving the symmetrised M, or NULL.
+ * Errors: RSX_EINVAL, RSX_ENOMEM; RSX_ENOTPD deferred to rsx_sync_status. */
+int rsx_ace_build(rsx_ctx* ctx, const void* phi, int nocc, void* xi, double* M_out, void* stream);
+
+/* ACE action of Eq. 13: out_p = -sum_k xi_k <xi_k, psi_p>.  nxi * npsi <= 4096.
+ * xi: [nxi][N], psi: [npsi][N], out: [npsi][N]; out may equal psi (in place), must not alias xi.
+ * Errors: RSX_EINVAL. */
+int rsx_ace_apply(rsx_ctx* ctx, const void* xi, int nxi, const void* psi, int npsi, void* out, void* stream);
+
+/* Tamm-Dancoff coupling K_{ia,jb} = (ia|jb) (Eqs. 6-7) for transitions t = i * nvirt + a:
+ * K = (h^6 / N_pad) sum_G w_G ghat(G) Re[conj R_t(G) R_s(G)], R_t the DFT of the padded
+ * rho_t = phi_i phi_a, w_G = 1 at kx = 0, Mx/2 and 2 otherwise.  FP32 context: spectra in
+ * FP32, split into bf16 hi + lo and contracted on the tensor cores (hi.hi + hi.lo + lo.hi,
+ * FP32 accumulation, FP64 reduction); FP64 context: FP64 throughout.
+ * phi_occ: [nocc][N], phi_virt: [nvirt][N], K: device double [nt][nt], nt = nocc * nvirt <= 4096.
+ * Errors: RSX_EINVAL, RSX_ENOMEM. */
+int rsx_casida_K(rsx_ctx* ctx, const void* phi_occ, int nocc, const void* phi_virt, int nvirt, double* K,
+                 void* stream);
+
+/* Coulomb term K_d[ia,jb] = (ab|ji) = <phi_a phi_b, V[phi_j phi_i]> of Eq. 7.
+ * Same arguments and layout as rsx_casida_K. */
+int rsx_casida_Kd(rsx_ctx* ctx, const void* phi_occ, int nocc, const void* phi_virt, int nvirt, double* Kd,
+                  void* stream);
+
+/* Lowest nroots eigenpairs of A = diag(eps_a - eps_i) + delta_M K - K_d (Eq. 7, TDA),
+ * FP64 on the device (Householder tridiagonalisation, bisection, inverse iteration).
+ * eps_occ: [nocc], eps_virt: [nvirt], K and Kd: [nt][nt] device doubles (Kd may be NULL);
+ * omega: [nroots] ascending (Hartree); X: [nroots][nt] eigenvectors or NULL.
+ * Errors: RSX_EINVAL (nroots < 1 or > nt, nt > 4096). */
+int rsx_casida_solve(rsx_ctx* ctx, const double* eps_occ, int nocc, const double* eps_virt, int nvirt,
+                     const double* K, const double* Kd, double delta_M, int nroots, double* omega, double* X,
+                     void* stream);
+
+/* Synchronise `stream` and return the first deferred device error since the last call
+ * (RSX_ENOTPD, RSX_ETIMEOUT) or a CUDA error; clears the device status word. */
+int rsx_sync_status(rsx_ctx* ctx, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RSX_H */

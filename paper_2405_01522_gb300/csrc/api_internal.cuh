@@ -1,0 +1,45 @@
+// Context object behind the C ABI and helpers shared by the host-side TUs.
+#pragma once
+#include <algorithm>
+#include <cstddef>
+
+#include "rsx_internal.cuh"
+
+struct rsx_ctx {
+  int device = 0;
+  int precision = 1;
+  double h = 0.0;
+  rsx::Geom g{};
+  int nsm = 0;
+  size_t work_limit = 0;
+  // device buffers owned by the context
+  void* vhat = nullptr;                 // kernel table T[kx][ky][kz] (R)
+  void* tw[3] = {nullptr, nullptr, nullptr};
+  void* work = nullptr;   size_t work_bytes = 0;     // FFT intermediates
+  void* gscr = nullptr;   size_t gscr_bytes = 0;     // pass-2 planes when shared memory is too small
+  double* dsm = nullptr;  size_t dsm_bytes = 0;      // FP64 partials and small matrices
+  void* smallr = nullptr; size_t smallr_bytes = 0;   // small R-typed coefficient matrices
+  int* status = nullptr;                             // deferred device status word
+  void* panel_hi = nullptr; size_t panel_hi_bytes = 0;  // Casida spectrum panel, bf16 hi
+  void* panel_lo = nullptr; size_t panel_lo_bytes = 0;  // bf16 lo
+  void* gemm_part = nullptr; size_t gemm_part_bytes = 0;
+  void* eig_work = nullptr; size_t eig_work_bytes = 0;
+  int p2_occ[2] = {0, 0};
+  char err[512] = {0};
+
+  size_t elem_size() const { return precision == 1 ? 4 : 8; }
+  template <typename R>
+  int pass2_ctas_per_sm() {
+    int& o = p2_occ[sizeof(R) == 8 ? 1 : 0];
+    if (o == 0) o = std::max(1, rsx::pass2_occupancy<R>(g));
+    return o;
+  }
+};
+
+namespace rsx {
+int check_cuda(rsx_ctx* c, cudaError_t e, const char* what);
+int grow(rsx_ctx* c, void** p, size_t* have, size_t need, const char* what);
+int set_error(rsx_ctx* c, int code, const char* msg);
+template <typename R>
+int solve_pairs(rsx_ctx* c, const PairMap<R>& pm, int q0, int nq, int p0, int np, R* out, cudaStream_t s);
+}  // namespace rsx

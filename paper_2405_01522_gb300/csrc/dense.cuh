@@ -1,0 +1,26 @@
+// Declarations of the small dense kernels (dense.cu).
+#pragma once
+#include "rsx_internal.cuh"
+
+namespace rsx {
+
+// Kernel spectrum table T[kx][ky][kz] = scale * ghat(k), k_i in [0, M_i/2]; cos_* hold
+// cos(2 pi j / M_i), j < M_i; buf0/buf1 are FP64 scratch of (M_z/2+1)(M_y/2+1)(M_x/2+1).
+cudaError_t launch_ghat(const Geom& g, double h, double scale, const double* cos_z, const double* cos_y,
+                        const double* cos_x, double* buf0, double* buf1, void* table, bool fp64,
+                        cudaStream_t s);
+template <typename R>
+cudaError_t launch_gram(const R* X, int na, const R* Y, int nb, size_t N, double* part, int nblk,
+                        cudaStream_t s);
+template <typename R>
+cudaError_t launch_gram_reduce(const double* part, int nblk, int na, int nb, double scale, bool transpose,
+                               double* out, R* out_r, cudaStream_t s);
+cudaError_t launch_chol_linv(double* M, int k, double* Linv, float* linv_f, double* linv_d, int* status,
+                             cudaStream_t s);
+template <typename R>
+cudaError_t launch_combine(const R* C, int no, int ni, const R* X, size_t N, R* out, int nblk,
+                           cudaStream_t s);
+template <typename R>
+cudaError_t launch_pair_products(const R* A, int na, const R* B, int nb, size_t N, R* rho, cudaStream_t s);
+
+}  // namespace rsx

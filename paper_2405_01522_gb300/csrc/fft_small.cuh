@@ -1,0 +1,233 @@
+// Register-resident small DFTs used by the line transforms of the pair Poisson solve.
+//
+// dft<N, S>(v) replaces v[0..N) by X[k] = sum_j v[j] exp(S * 2 pi i j k / N)
+// (S = -1 forward, S = +1 inverse, no normalisation).  Supported N: 2, 3, 4, 5, 6, 7,
+// 8, 10, 12, 14, 16.  Odd primes use the symmetric real/imaginary split, 8 and 16 are
+// radix-2 / radix-4 Cooley-Tukey, and the coprime products 6, 10, 12, 14 use the
+// Good-Thomas prime-factor index map, which needs no twiddle factors.  All trig
+// constants are exact decimal expansions of cos/sin of rational multiples of pi.
+#pragma once
+#include <cuda_runtime.h>
+
+#ifndef RSX_HD
+#define RSX_HD __host__ __device__ __forceinline__
+#endif
+
+namespace rsx {
+
+template <typename R>
+struct Cx {
+  R x, y;
+};
+
+template <typename R>
+RSX_HD Cx<R> cx(R a, R b) { Cx<R> c; c.x = a; c.y = b; return c; }
+template <typename R>
+RSX_HD Cx<R> operator+(Cx<R> a, Cx<R> b) { return cx<R>(a.x + b.x, a.y + b.y); }
+template <typename R>
+RSX_HD Cx<R> operator-(Cx<R> a, Cx<R> b) { return cx<R>(a.x - b.x, a.y - b.y); }
+template <typename R>
+RSX_HD Cx<R> cmul(Cx<R> a, Cx<R> b) {
+  return cx<R>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename R>
+RSX_HD Cx<R> cscale(Cx<R> a, R s) { return cx<R>(a.x * s, a.y * s); }
+template <typename R>
+RSX_HD Cx<R> conj(Cx<R> a) { return cx<R>(a.x, -a.y); }
+// S * i * a  for S = +-1
+template <int S, typename R>
+RSX_HD Cx<R> mul_si(Cx<R> a) {
+  return S > 0 ? cx<R>(-a.y, a.x) : cx<R>(a.y, -a.x);
+}
+// (c + S i s) * a
+template <int S, typename R>
+RSX_HD Cx<R> rot(Cx<R> a, R c, R s) {
+  const R ss = S > 0 ? s : -s;
+  return cx<R>(a.x * c - a.y * ss, a.x * ss + a.y * c);
+}
+
+// cos(2 pi j / p) and sin(2 pi j / p) for p in {3, 5, 7, 16}, 0 <= j < p (decimal
+// expansions of the exact values); constexpr so that unrolled uses fold to immediates.
+RSX_HD constexpr double trig_c(int p, int j) {
+  return p == 3 ? (j == 0 ? 1.0 : -0.5)
+       : p == 5 ? (j == 0 ? 1.0 : (j == 1 || j == 4) ? 0.30901699437494742410 : -0.80901699437494742410)
+       : p == 7 ? (j == 0 ? 1.0 : (j == 1 || j == 6) ? 0.62348980185873353053
+                           : (j == 2 || j == 5) ? -0.22252093395631440429 : -0.90096886790241912624)
+       : /* p == 16 */
+         (j == 0 ? 1.0 : j == 1 ? 0.92387953251128675613 : j == 2 ? 0.70710678118654752440
+          : j == 3 ? 0.38268343236508977173 : j == 4 ? 0.0 : j == 5 ? -0.38268343236508977173
+          : j == 6 ? -0.70710678118654752440 : j == 7 ? -0.92387953251128675613 : j == 8 ? -1.0
+          : j == 9 ? -0.92387953251128675613 : j == 10 ? -0.70710678118654752440
+          : j == 11 ? -0.38268343236508977173 : j == 12 ? 0.0 : j == 13 ? 0.38268343236508977173
+          : j == 14 ? 0.70710678118654752440 : 0.92387953251128675613);
+}
+RSX_HD constexpr double trig_s(int p, int j) {
+  // sin(2 pi j / p) = cos(2 pi j / p - pi / 2); written out per p
+  return p == 3 ? (j == 0 ? 0.0 : j == 1 ? 0.86602540378443864676 : -0.86602540378443864676)
+       : p == 5 ? (j == 0 ? 0.0 : j == 1 ? 0.95105651629515357212 : j == 2 ? 0.58778525229247312917
+                           : j == 3 ? -0.58778525229247312917 : -0.95105651629515357212)
+       : p == 7 ? (j == 0 ? 0.0 : j == 1 ? 0.78183148246802980871 : j == 2 ? 0.97492791218182360702
+                           : j == 3 ? 0.43388373911755812048 : j == 4 ? -0.43388373911755812048
+                           : j == 5 ? -0.97492791218182360702 : -0.78183148246802980871)
+       : /* p == 16 */ trig_c(16, (j + 12) % 16);
+}
+
+template <int N, int S>
+struct Dft;
+
+template <int S>
+struct Dft<1, S> {
+  template <typename R> RSX_HD static void run(Cx<R>* v) {}
+};
+
+template <int S>
+struct Dft<2, S> {
+  template <typename R>
+  RSX_HD static void run(Cx<R>* v) {
+    Cx<R> a = v[0], b = v[1];
+    v[0] = a + b;
+    v[1] = a - b;
+  }
+};
+
+template <int S>
+struct Dft<4, S> {
+  template <typename R>
+  RSX_HD static void run(Cx<R>* v) {
+    Cx<R> a = v[0] + v[2], b = v[0] - v[2], c = v[1] + v[3], d = mul_si<S>(v[1] - v[3]);
+    v[0] = a + c;
+    v[2] = a - c;
+    v[1] = b + d;
+    v[3] = b - d;
+  }
+};
+
+// odd prime p: pairs (k, p-k) split into even (cos) and odd (sin) parts
+template <int P, int S>
+struct DftOddPrime {
+  template <typename R>
+  RSX_HD static void run(Cx<R>* v) {
+    constexpr int H = (P - 1) / 2;
+    Cx<R> a[H], b[H];
+    Cx<R> x0 = v[0];
+    Cx<R> sum = x0;
+#pragma unroll
+    for (int k = 1; k <= H; ++k) {
+      a[k - 1] = v[k] + v[P - k];
+      b[k - 1] = v[k] - v[P - k];
+      sum = sum + a[k - 1];
+    }
+    v[0] = sum;
+#pragma unroll
+    for (int m = 1; m <= H; ++m) {
+      Cx<R> re = x0, im = cx<R>(R(0), R(0));
+#pragma unroll
+      for (int k = 1; k <= H; ++k) {
+        const R c = R(trig_c(P, (m * k) % P));
+        const R s = R(trig_s(P, (m * k) % P));
+        re = cx<R>(re.x + c * a[k - 1].x, re.y + c * a[k - 1].y);
+        im = cx<R>(im.x + s * b[k - 1].x, im.y + s * b[k - 1].y);
+      }
+      const Cx<R> u = mul_si<S>(im);
+      v[m] = re + u;
+      v[P - m] = re - u;
+    }
+  }
+};
+template <int S> struct Dft<3, S> : DftOddPrime<3, S> {};
+template <int S> struct Dft<5, S> : DftOddPrime<5, S> {};
+template <int S> struct Dft<7, S> : DftOddPrime<7, S> {};
+
+template <int S>
+struct Dft<8, S> {
+  template <typename R>
+  RSX_HD static void run(Cx<R>* v) {
+    Cx<R> e[4] = {v[0], v[2], v[4], v[6]};
+    Cx<R> o[4] = {v[1], v[3], v[5], v[7]};
+    Dft<4, S>::run(e);
+    Dft<4, S>::run(o);
+    const R r = R(0.70710678118654752440);
+    Cx<R> t1 = rot<S>(o[1], r, r);
+    Cx<R> t2 = mul_si<S>(o[2]);
+    Cx<R> t3 = rot<S>(o[3], -r, r);
+    v[0] = e[0] + o[0];
+    v[4] = e[0] - o[0];
+    v[1] = e[1] + t1;
+    v[5] = e[1] - t1;
+    v[2] = e[2] + t2;
+    v[6] = e[2] - t2;
+    v[3] = e[3] + t3;
+    v[7] = e[3] - t3;
+  }
+};
+
+template <int S>
+struct Dft<16, S> {
+  template <typename R>
+  RSX_HD static void run(Cx<R>* v) {
+    Cx<R> y[4][4];
+#pragma unroll
+    for (int j2 = 0; j2 < 4; ++j2) {
+      Cx<R> c[4] = {v[j2], v[j2 + 4], v[j2 + 8], v[j2 + 12]};
+      Dft<4, S>::run(c);
+#pragma unroll
+      for (int k1 = 0; k1 < 4; ++k1) {
+        const int e = j2 * k1;
+        y[j2][k1] = (e == 0) ? c[k1] : rot<S>(c[k1], R(trig_c(16, e)), R(trig_s(16, e)));
+      }
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+      Cx<R> c[4] = {y[0][k1], y[1][k1], y[2][k1], y[3][k1]};
+      Dft<4, S>::run(c);
+#pragma unroll
+      for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = c[k2];
+    }
+  }
+};
+
+RSX_HD constexpr int modinv(int a, int m) {
+  int r = 1;
+  for (int i = 1; i < m; ++i)
+    if ((a * i) % m == 1) r = i;
+  return r;
+}
+
+// Good-Thomas prime-factor DFT of length P*Q, gcd(P, Q) = 1
+template <int P, int Q, int S>
+struct DftPfa {
+  template <typename R>
+  RSX_HD static void run(Cx<R>* v) {
+    constexpr int N = P * Q;
+    constexpr int qinv = modinv(Q % P, P);
+    constexpr int pinv = modinv(P % Q, Q);
+    Cx<R> y[P][Q];
+#pragma unroll
+    for (int n1 = 0; n1 < P; ++n1)
+#pragma unroll
+      for (int n2 = 0; n2 < Q; ++n2) y[n1][n2] = v[(n1 * Q + n2 * P) % N];
+#pragma unroll
+    for (int n2 = 0; n2 < Q; ++n2) {
+      Cx<R> c[P];
+#pragma unroll
+      for (int n1 = 0; n1 < P; ++n1) c[n1] = y[n1][n2];
+      Dft<P, S>::run(c);
+#pragma unroll
+      for (int n1 = 0; n1 < P; ++n1) y[n1][n2] = c[n1];
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < P; ++k1) {
+      Dft<Q, S>::run(y[k1]);
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < P; ++k1)
+#pragma unroll
+      for (int k2 = 0; k2 < Q; ++k2) v[(k1 * Q * qinv + k2 * P * pinv) % N] = y[k1][k2];
+  }
+};
+template <int S> struct Dft<6, S> : DftPfa<2, 3, S> {};
+template <int S> struct Dft<10, S> : DftPfa<2, 5, S> {};
+template <int S> struct Dft<12, S> : DftPfa<3, 4, S> {};
+template <int S> struct Dft<14, S> : DftPfa<2, 7, S> {};
+
+}  // namespace rsx

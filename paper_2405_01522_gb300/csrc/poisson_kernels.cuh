@@ -1,0 +1,476 @@
+// Pair Poisson solve by pruned, zero-padded FFT convolution: the three passes.
+//
+// The potential of a pair density rho = f1 f2 on the box (nz, ny, nx) is
+//     V = h^3/N_pad * IDFT( ghat * DFT(rho zero-padded to (2nz, 2ny, 2nx)) )
+// restricted to the box (Sec. 3.1: Eq. 2's integral as a Poisson problem at
+// O(N log N); padding twice the box makes the periodic convolution the isolated one).
+// The solve is split so that only one 1-D transform per pass touches HBM:
+//
+//   pass 1  x forward, real-to-complex (two rows y, y+1 packed as one complex line),
+//           output I[q][kx][z][y], kx in [0, Mx/2]       (Mx/2+1) * nz * ny complex
+//   pass 2  per (q, kx): y forward on nz rows, z forward + multiply by vhat + z inverse
+//           on My columns, y inverse keeping y < ny; in place on I
+//   pass 3  per (output p, z, 32 rows): x inverse complex-to-real of every pair of p's
+//           list, keeping x < nx, and  out_p -= partner * V  (Eq. 2's sum over j)
+//
+// Only nz of the 2nz z-planes and ny of the 2ny rows are non-zero, so the x transforms
+// run on nz*ny rows and the y transforms on nz rows per kx; I is 4x smaller than a
+// padded half spectrum.  A line of length M = 16 A is transformed by 16 lanes:
+// lane t holds x[t + 16 a] (a < A), does an A-point DFT, multiplies by the twiddle
+// w_M^{t k1}, and after a shared-memory transpose lane k1 does the 16-point DFT over t,
+// giving X[k1 + A k2].  The inverse of that split is the same steps in reverse, so in
+// pass 2 the z spectrum never leaves registers between forward, multiply and inverse.
+#pragma once
+#include "rsx_internal.cuh"
+
+namespace rsx {
+
+// round-to-nearest-even f32 -> bf16 bit pattern (finite inputs), and back
+__device__ __forceinline__ uint32_t f32_to_bf16_bits(float f) {
+  const uint32_t u = __float_as_uint(f);
+  return (u + 0x7FFFu + ((u >> 16) & 1u)) >> 16;
+}
+__device__ __forceinline__ float bf16_bits_to_f32(uint32_t b) { return __uint_as_float(b << 16); }
+
+// ---------------------------------------------------------------------------------
+// stage helpers (executed by the 16 lanes t of one half-warp on one line)
+// stage 1: v holds x[t + 16 a]; DFT over a, twiddle, store scratch[k1][t]
+template <int A, int S, typename R>
+__device__ __forceinline__ void stage1_store(Cx<R> (&v)[A], int t, const Cx<R>* __restrict__ tw,
+                                             Cx<R>* sc) {
+  Dft<A, S>::run(v);
+#pragma unroll
+  for (int k1 = 1; k1 < A; ++k1) {
+    Cx<R> w = tw[t * A + k1];
+    if (S > 0) w.y = -w.y;
+    v[k1] = cmul(v[k1], w);
+  }
+#pragma unroll
+  for (int k1 = 0; k1 < A; ++k1) sc[k1 * kScrPitch + t] = v[k1];
+}
+
+// stage 2 load: lane s (< A) gathers its 16 values scratch[s][t]
+template <typename R>
+__device__ __forceinline__ void stage2_load(Cx<R> (&u)[16], int s, const Cx<R>* sc) {
+#pragma unroll
+  for (int j = 0; j < 16; ++j) u[j] = sc[s * kScrPitch + j];
+}
+
+// ---------------------------------------------------------------------------------
+// pass 1: x forward (r2c via row pairs).  CTA = (pair q, plane z, 32 rows).
+template <typename R, int AX>
+__global__ void __launch_bounds__(kThreads) k_pass1(Geom g, PairMap<R> pm, int q0, Cx<R>* __restrict__ inter,
+                                                    const Cx<R>* __restrict__ twx) {
+  constexpr int L = 16 * AX;
+  constexpr int SP = AX * kScrPitch;
+  constexpr int H = L / 2 + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Cx<R>* scr = reinterpret_cast<Cx<R>*>(smem_raw);
+  Cx<R>* xs = scr + kLinesPerCta * SP;  // [H][kXsPitch]
+
+  const int nyb = (g.ny + kRowsPerCta - 1) / kRowsPerCta;
+  int b = blockIdx.x;
+  const int yblk = b % nyb;
+  b /= nyb;
+  const int z = b % g.nz;
+  const int ql = b / g.nz;  // local pair slot
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int t = lane & 15, line = warp * 2 + (lane >> 4);
+  const int y0 = yblk * kRowsPerCta;
+  const int ya = y0 + 2 * line, yb = ya + 1;
+  Cx<R>* sc = scr + line * SP;
+
+  const R* f1;
+  const R* f2;
+  pm.pair(q0 + ql, f1, f2);
+  const size_t plane = (size_t)z * g.ny * g.nx;
+  f1 += plane;
+  f2 += plane;
+
+  Cx<R> v[AX];
+#pragma unroll
+  for (int a = 0; a < AX; ++a) {
+    const int x = t + 16 * a;
+    R re = R(0), im = R(0);
+    if (x < g.nx) {
+      if (ya < g.ny) re = __ldg(f1 + (size_t)ya * g.nx + x) * __ldg(f2 + (size_t)ya * g.nx + x);
+      if (yb < g.ny) im = __ldg(f1 + (size_t)yb * g.nx + x) * __ldg(f2 + (size_t)yb * g.nx + x);
+    }
+    v[a] = cx<R>(re, im);
+  }
+  stage1_store<AX, -1>(v, t, twx, sc);
+  __syncwarp();
+  Cx<R> u[16];
+  if (t < AX) {
+    stage2_load(u, t, sc);
+    Dft<16, -1>::run(u);
+  }
+  __syncwarp();
+  if (t < AX) {
+#pragma unroll
+    for (int k2 = 0; k2 < 16; ++k2) sc[t + AX * k2] = u[k2];  // natural order U[k]
+  }
+  __syncwarp();
+  // split the packed line: X_a(k) = (U(k) + conj U(L-k)) / 2,  X_b(k) = (U(k) - conj U(L-k)) / 2i
+  for (int k = t; k < H; k += 16) {
+    const Cx<R> U = sc[k];
+    const Cx<R> Um = sc[(L - k) % L];
+    xs[k * kXsPitch + 2 * line] = cx<R>(R(0.5) * (U.x + Um.x), R(0.5) * (U.y - Um.y));
+    xs[k * kXsPitch + 2 * line + 1] = cx<R>(R(0.5) * (U.y + Um.y), R(-0.5) * (U.x - Um.x));
+  }
+  __syncthreads();
+  const int nrow = min(kRowsPerCta, g.ny - y0);
+  Cx<R>* dst = inter + (size_t)ql * g.inter_elems() + (size_t)z * g.ny + y0;
+  const size_t kstride = (size_t)g.nz * g.ny;
+  for (int e = threadIdx.x; e < H * kRowsPerCta; e += kThreads) {
+    const int kx = e / kRowsPerCta, r = e - kx * kRowsPerCta;
+    if (r < nrow) dst[(size_t)kx * kstride + r] = xs[kx * kXsPitch + r];
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// pass 2 pieces.  D is the (nz x My) plane of one (pair, kx), row pitch DP = My + 1.
+// Row loops step over pairs of rows per warp so that both half-warps of a warp run
+// the same number of iterations (their __syncwarp calls must match).
+
+template <typename R>
+__device__ __forceinline__ void load_plane(Cx<R>* D, int DP, const Cx<R>* P, int nz, int ny) {
+  const int nplane = nz * ny;
+  for (int e = threadIdx.x; e < nplane; e += kThreads) {
+    const int z = e / ny, y = e - z * ny;
+    D[z * DP + y] = P[e];
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ void store_plane(const Cx<R>* D, int DP, Cx<R>* P, int nz, int ny) {
+  const int nplane = nz * ny;
+  for (int e = threadIdx.x; e < nplane; e += kThreads) {
+    const int z = e / ny, y = e - z * ny;
+    P[e] = D[z * DP + y];
+  }
+}
+
+// forward y transform of rows z < nz (input y < ny, output all My)
+template <typename R, int AY>
+__device__ __forceinline__ void y_forward(Cx<R>* D, int DP, int nz, int ny, const Cx<R>* __restrict__ twy,
+                                          Cx<R>* sc) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, t = lane & 15;
+  for (int z0 = 2 * warp; z0 < nz; z0 += kLinesPerCta) {
+    const int z = z0 + (lane >> 4);
+    const bool ok = z < nz;
+    Cx<R> v[AY];
+#pragma unroll
+    for (int a = 0; a < AY; ++a) {
+      const int y = t + 16 * a;
+      v[a] = (ok && y < ny) ? D[z * DP + y] : cx<R>(R(0), R(0));
+    }
+    stage1_store<AY, -1>(v, t, twy, sc);
+    __syncwarp();
+    Cx<R> u[16];
+    if (t < AY) {
+      stage2_load(u, t, sc);
+      Dft<16, -1>::run(u);
+    }
+    __syncwarp();
+    if (ok && t < AY) {
+#pragma unroll
+      for (int k2 = 0; k2 < 16; ++k2) D[z * DP + t + AY * k2] = u[k2];
+    }
+    __syncwarp();
+  }
+}
+
+// inverse y transform of rows z < nz (input all My, output y < ny)
+template <typename R, int AY>
+__device__ __forceinline__ void y_inverse(Cx<R>* D, int DP, int nz, int ny, const Cx<R>* __restrict__ twy,
+                                          Cx<R>* sc) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, t = lane & 15;
+  for (int z0 = 2 * warp; z0 < nz; z0 += kLinesPerCta) {
+    const int z = z0 + (lane >> 4);
+    const bool ok = z < nz;
+    Cx<R> v[AY];
+#pragma unroll
+    for (int a = 0; a < AY; ++a) v[a] = ok ? D[z * DP + t + 16 * a] : cx<R>(R(0), R(0));
+    stage1_store<AY, 1>(v, t, twy, sc);
+    __syncwarp();
+    Cx<R> u[16];
+    if (t < AY) {
+      stage2_load(u, t, sc);
+      Dft<16, 1>::run(u);
+    }
+    __syncwarp();
+    if (ok && t < AY) {
+#pragma unroll
+      for (int k2 = 0; k2 < 16; ++k2) {
+        const int y = t + AY * k2;
+        if (y < ny) D[z * DP + y] = u[k2];
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// pass 2: per (pair, kx) plane: y forward, z forward * vhat * z inverse, y inverse.
+// D lives in shared memory (DSMEM) or, when it does not fit, in a per-CTA slice of
+// global scratch.  Persistent grid over the work items (pair, kx).
+template <typename R, int AY, int AZ, bool DSMEM>
+__global__ void __launch_bounds__(kThreads) k_pass2(Geom g, int nq, Cx<R>* __restrict__ inter,
+                                                    const Cx<R>* __restrict__ twy,
+                                                    const Cx<R>* __restrict__ twz,
+                                                    const R* __restrict__ vhat, R* gscratch) {
+  constexpr int LY = 16 * AY;
+  constexpr int LZ = 16 * AZ;
+  constexpr int AMAX = AY > AZ ? AY : AZ;
+  constexpr int SP = AMAX * kScrPitch;
+  constexpr int DP = LY + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Cx<R>* scr = reinterpret_cast<Cx<R>*>(smem_raw);
+  Cx<R>* D = DSMEM ? scr + kLinesPerCta * SP
+                   : reinterpret_cast<Cx<R>*>(gscratch) + (size_t)blockIdx.x * g.nz * DP;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int t = lane & 15, line = warp * 2 + (lane >> 4);
+  Cx<R>* sc = scr + line * SP;
+  constexpr int Hy = LY / 2 + 1, Hz = LZ / 2 + 1;
+  const int nplane = g.nz * g.ny;
+  const int nwork = nq * g.Hx;
+
+  for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
+    const int ql = w / g.Hx, kx = w - ql * g.Hx;
+    Cx<R>* P = inter + (size_t)ql * g.inter_elems() + (size_t)kx * nplane;
+    load_plane(D, DP, P, g.nz, g.ny);
+    __syncthreads();
+    y_forward<R, AY>(D, DP, g.nz, g.ny, twy, sc);
+    __syncthreads();
+    // z forward, multiply, z inverse on columns ky (LY is a multiple of 16: uniform trips)
+    const R* vrow = vhat + (size_t)kx * Hy * Hz;
+    for (int ky = line; ky < LY; ky += kLinesPerCta) {
+      const int iy = ky <= LY / 2 ? ky : LY - ky;
+      const R* vcol = vrow + (size_t)iy * Hz;
+      Cx<R> v[AZ];
+#pragma unroll
+      for (int a = 0; a < AZ; ++a) {
+        const int z = t + 16 * a;
+        v[a] = (z < g.nz) ? D[z * DP + ky] : cx<R>(R(0), R(0));
+      }
+      stage1_store<AZ, -1>(v, t, twz, sc);
+      __syncwarp();
+      Cx<R> u[16];
+      if (t < AZ) stage2_load(u, t, sc);
+      __syncwarp();
+      if (t < AZ) {
+        Dft<16, -1>::run(u);
+#pragma unroll
+        for (int k2 = 0; k2 < 16; ++k2) {
+          const int kz = t + AZ * k2;
+          const R m = __ldg(vcol + (kz <= LZ / 2 ? kz : LZ - kz));
+          u[k2] = cx<R>(u[k2].x * m, u[k2].y * m);
+        }
+        Dft<16, 1>::run(u);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          Cx<R> w = twz[j * AZ + t];
+          w.y = -w.y;
+          sc[t * kScrPitch + j] = cmul(u[j], w);
+        }
+      }
+      __syncwarp();
+      Cx<R> r[AZ];
+#pragma unroll
+      for (int k1 = 0; k1 < AZ; ++k1) r[k1] = sc[k1 * kScrPitch + t];
+      Dft<AZ, 1>::run(r);
+#pragma unroll
+      for (int a = 0; a < AZ; ++a) {
+        const int z = t + 16 * a;
+        if (z < g.nz) D[z * DP + ky] = r[a];
+      }
+      __syncwarp();
+    }
+    __syncthreads();
+    y_inverse<R, AY>(D, DP, g.nz, g.ny, twy, sc);
+    __syncthreads();
+    store_plane(D, DP, P, g.nz, g.ny);
+    __syncthreads();
+  }
+}
+
+// Casida pair spectra: per (transition q, kx) plane, y forward and z forward, then
+// S_q(G) = sqrt(w_kx * ghat(G) * h^6 / N_pad) * (Re, Im) R_q(G) with w = 1 at kx = 0, Mx/2
+// and 2 otherwise, split into bf16 hi + lo and written to panel row q at column
+// 2 * ((kx * My + ky) * Mz + kz) + {0, 1}.  vhat holds ghat * h^3 / N_pad, so the
+// weight is sqrt(w * vhat * h^3).
+template <int AY, int AZ>
+__global__ void __launch_bounds__(kThreads) k_spectrum(Geom g, int nq, const Cx<float>* __restrict__ inter,
+                                                       const Cx<float>* __restrict__ twy,
+                                                       const Cx<float>* __restrict__ twz,
+                                                       const float* __restrict__ vhat, float h3,
+                                                       uint16_t* __restrict__ hi, uint16_t* __restrict__ lo,
+                                                       size_t ld) {
+  constexpr int LY = 16 * AY;
+  constexpr int LZ = 16 * AZ;
+  constexpr int AMAX = AY > AZ ? AY : AZ;
+  constexpr int SP = AMAX * kScrPitch;
+  constexpr int DP = LY + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Cx<float>* scr = reinterpret_cast<Cx<float>*>(smem_raw);
+  Cx<float>* D = scr + kLinesPerCta * SP;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int t = lane & 15, line = warp * 2 + (lane >> 4);
+  Cx<float>* sc = scr + line * SP;
+  constexpr int Hy = LY / 2 + 1, Hz = LZ / 2 + 1;
+  const int nplane = g.nz * g.ny;
+  const int nwork = nq * g.Hx;
+  for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
+    const int ql = w / g.Hx, kx = w - ql * g.Hx;
+    const Cx<float>* P = inter + (size_t)ql * g.inter_elems() + (size_t)kx * nplane;
+    load_plane(D, DP, P, g.nz, g.ny);
+    __syncthreads();
+    y_forward<float, AY>(D, DP, g.nz, g.ny, twy, sc);
+    __syncthreads();
+    const float wk = (kx == 0 || 2 * kx == g.Mx) ? 1.0f : 2.0f;
+    const float* vrow = vhat + (size_t)kx * Hy * Hz;
+    uint16_t* hrow = hi + (size_t)ql * ld + (size_t)kx * LY * LZ * 2;
+    uint16_t* lrow = lo + (size_t)ql * ld + (size_t)kx * LY * LZ * 2;
+    for (int ky = line; ky < LY; ky += kLinesPerCta) {
+      const int iy = ky <= LY / 2 ? ky : LY - ky;
+      const float* vcol = vrow + (size_t)iy * Hz;
+      Cx<float> v[AZ];
+#pragma unroll
+      for (int a = 0; a < AZ; ++a) {
+        const int z = t + 16 * a;
+        v[a] = (z < g.nz) ? D[z * DP + ky] : cx<float>(0.f, 0.f);
+      }
+      stage1_store<AZ, -1>(v, t, twz, sc);
+      __syncwarp();
+      Cx<float> u[16];
+      if (t < AZ) {
+        stage2_load(u, t, sc);
+        Dft<16, -1>::run(u);
+      }
+      __syncwarp();
+      if (t < AZ) {
+#pragma unroll
+        for (int k2 = 0; k2 < 16; ++k2) {
+          const int kz = t + AZ * k2;
+          const float m = sqrtf(wk * __ldg(vcol + (kz <= LZ / 2 ? kz : LZ - kz)) * h3);
+          sc[kz] = cx<float>(u[k2].x * m, u[k2].y * m);
+        }
+      }
+      __syncwarp();
+      uint32_t* hw = reinterpret_cast<uint32_t*>(hrow + (size_t)ky * LZ * 2);
+      uint32_t* lw = reinterpret_cast<uint32_t*>(lrow + (size_t)ky * LZ * 2);
+      for (int kz = t; kz < LZ; kz += 16) {
+        const Cx<float> c = sc[kz];
+        const uint32_t hx = f32_to_bf16_bits(c.x), hy = f32_to_bf16_bits(c.y);
+        const uint32_t lx = f32_to_bf16_bits(c.x - bf16_bits_to_f32(hx));
+        const uint32_t ly = f32_to_bf16_bits(c.y - bf16_bits_to_f32(hy));
+        hw[kz] = hx | (hy << 16);
+        lw[kz] = lx | (ly << 16);
+      }
+      __syncwarp();
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// pass 3: x inverse (c2r via row pairs) of every pair in output p's list, and
+// out_p(z, y, x) = - sum_e partner_e(z, y, x) V_e(z, y, x).  CTA = (p, z, 32 rows).
+template <typename R, int AX>
+__global__ void __launch_bounds__(kThreads) k_pass3(Geom g, PairMap<R> pm, int q0, int p0,
+                                                    const Cx<R>* __restrict__ inter,
+                                                    const Cx<R>* __restrict__ twx, R* __restrict__ out) {
+  constexpr int L = 16 * AX;
+  constexpr int SP = AX * kScrPitch;
+  constexpr int H = L / 2 + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Cx<R>* scr = reinterpret_cast<Cx<R>*>(smem_raw);
+  Cx<R>* xs = scr + kLinesPerCta * SP;               // [H][kXsPitch]
+  R* tile = reinterpret_cast<R*>(xs + H * kXsPitch);  // [32][nx]: partner, then result
+
+  const int nyb = (g.ny + kRowsPerCta - 1) / kRowsPerCta;
+  int b = blockIdx.x;
+  const int yblk = b % nyb;
+  b /= nyb;
+  const int z = b % g.nz;
+  const int pl = b / g.nz;
+  const int p = p0 + pl;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int t = lane & 15, line = warp * 2 + (lane >> 4);
+  const int y0 = yblk * kRowsPerCta;
+  const int nrow = min(kRowsPerCta, g.ny - y0);
+  Cx<R>* sc = scr + line * SP;
+  const size_t kstride = (size_t)g.nz * g.ny;
+  const size_t plane = (size_t)z * g.ny * g.nx;
+
+  R acc0[16], acc1[16];
+#pragma unroll
+  for (int k2 = 0; k2 < 16; ++k2) acc0[k2] = acc1[k2] = R(0);
+
+  const int ne = pm.nentries(p);
+  for (int e = 0; e < ne; ++e) {
+    int q;
+    const R* partner;
+    pm.entry(p, e, q, partner);
+    const Cx<R>* src = inter + (size_t)(q - q0) * g.inter_elems() + (size_t)z * g.ny + y0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < H * kRowsPerCta; i += kThreads) {
+      const int kx = i / kRowsPerCta, r = i - kx * kRowsPerCta;
+      xs[kx * kXsPitch + r] = (r < nrow) ? src[(size_t)kx * kstride + r] : cx<R>(R(0), R(0));
+    }
+    const R* prow = partner + plane + (size_t)y0 * g.nx;
+    for (int i = threadIdx.x; i < nrow * g.nx; i += kThreads) tile[i] = __ldg(prow + i);
+    __syncthreads();
+
+    // Z(k) = X_a(k) + i X_b(k), Hermitian extension for k > L/2
+    Cx<R> v[AX];
+#pragma unroll
+    for (int a = 0; a < AX; ++a) {
+      const int k = t + 16 * a;
+      Cx<R> xa, xb;
+      if (k < H) {
+        xa = xs[k * kXsPitch + 2 * line];
+        xb = xs[k * kXsPitch + 2 * line + 1];
+      } else {
+        xa = conj(xs[(L - k) * kXsPitch + 2 * line]);
+        xb = conj(xs[(L - k) * kXsPitch + 2 * line + 1]);
+      }
+      v[a] = cx<R>(xa.x - xb.y, xa.y + xb.x);
+    }
+    stage1_store<AX, 1>(v, t, twx, sc);
+    __syncwarp();
+    if (t < AX) {
+      Cx<R> u[16];
+      stage2_load(u, t, sc);
+      Dft<16, 1>::run(u);
+      const int ra = 2 * line, rb = ra + 1;
+#pragma unroll
+      for (int k2 = 0; k2 < 16; ++k2) {
+        const int x = t + AX * k2;
+        if (x < g.nx) {
+          if (ra < nrow) acc0[k2] -= tile[ra * g.nx + x] * u[k2].x;
+          if (rb < nrow) acc1[k2] -= tile[rb * g.nx + x] * u[k2].y;
+        }
+      }
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+  if (t < AX) {
+    const int ra = 2 * line, rb = ra + 1;
+#pragma unroll
+    for (int k2 = 0; k2 < 16; ++k2) {
+      const int x = t + AX * k2;
+      if (x < g.nx) {
+        if (ra < nrow) tile[ra * g.nx + x] = acc0[k2];
+        if (rb < nrow) tile[rb * g.nx + x] = acc1[k2];
+      }
+    }
+  }
+  __syncthreads();
+  R* orow = out + (size_t)pl * g.N() + plane + (size_t)y0 * g.nx;
+  for (int i = threadIdx.x; i < nrow * g.nx; i += kThreads) orow[i] = tile[i];
+}
+
+}  // namespace rsx

@@ -1,0 +1,106 @@
+// Launchers of the pair Poisson passes for one precision R (included once per TU).
+#pragma once
+#include "poisson_kernels.cuh"
+
+namespace rsx {
+
+#define RSX_FOR_EACH_A(X) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(10) X(12) X(14)
+
+inline bool axis_supported_impl(int A) {
+  switch (A) {
+#define RSX_CASE(a) case a: return true;
+    RSX_FOR_EACH_A(RSX_CASE)
+#undef RSX_CASE
+    default: return false;
+  }
+}
+
+template <typename R>
+inline size_t pass1_smem(int AX) {
+  const int L = 16 * AX, H = L / 2 + 1;
+  return sizeof(Cx<R>) * ((size_t)kLinesPerCta * AX * kScrPitch + (size_t)H * kXsPitch);
+}
+template <typename R>
+inline size_t pass3_smem(int AX, int nx) {
+  return pass1_smem<R>(AX) + sizeof(R) * (size_t)kRowsPerCta * nx;
+}
+template <typename R>
+inline size_t pass2_scratch_smem(int AY, int AZ) {
+  const int A = AY > AZ ? AY : AZ;
+  return sizeof(Cx<R>) * (size_t)kLinesPerCta * A * kScrPitch;
+}
+template <typename R>
+inline size_t pass2_plane_bytes(const Geom& g) {
+  return sizeof(Cx<R>) * (size_t)g.nz * (g.My + 1);
+}
+
+inline int max_dyn_smem() {
+  int dev = 0, v = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  return v;
+}
+
+template <typename R>
+size_t pass2_smem_bytes(const Geom& g, bool* fits) {
+  const size_t sc = pass2_scratch_smem<R>(g.Ay, g.Az);
+  const size_t pl = pass2_plane_bytes<R>(g);
+  const bool f = sc + pl <= (size_t)max_dyn_smem();
+  if (fits) *fits = f;
+  return f ? sc + pl : sc;
+}
+
+template <typename R>
+int pass2_occupancy(const Geom& g) {
+  bool fits = false;
+  const size_t smem = pass2_smem_bytes<R>(g, &fits);
+  int nb = 1;
+  switch (g.Ay) {
+#define RSX_CASE(a)                                                                                  \
+  case a: {                                                                                          \
+    auto k = k_pass2<R, a, a, true>;                                                                 \
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess || \
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kThreads, smem) != cudaSuccess) {     \
+      cudaGetLastError();                                                                            \
+      nb = 1;                                                                                        \
+    }                                                                                                \
+    break;                                                                                           \
+  }
+    RSX_FOR_EACH_A(RSX_CASE)
+#undef RSX_CASE
+    default: break;
+  }
+  return nb;
+}
+
+template <typename R>
+cudaError_t launch_pass2(const Geom& g, int nq, Cx<R>* inter, const Cx<R>* twy, const Cx<R>* twz,
+                         const R* vhat, R* gscratch, int grid, cudaStream_t s) {
+  if (nq <= 0) return cudaSuccess;
+  if (g.Ay != g.Az) return cudaErrorInvalidValue;
+  bool fits = false;
+  const size_t smem = pass2_smem_bytes<R>(g, &fits);
+  if (!fits && gscratch == nullptr) return cudaErrorInvalidValue;
+  switch (g.Ay) {
+#define RSX_CASE(a)                                                                                  \
+  case a: {                                                                                          \
+    if (fits) {                                                                                      \
+      auto k = k_pass2<R, a, a, true>;                                                               \
+      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+      if (e != cudaSuccess) return e;                                                                \
+      k<<<grid, kThreads, smem, s>>>(g, nq, inter, twy, twz, vhat, gscratch);                        \
+    } else {                                                                                         \
+      auto k = k_pass2<R, a, a, false>;                                                              \
+      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+      if (e != cudaSuccess) return e;                                                                \
+      k<<<grid, kThreads, smem, s>>>(g, nq, inter, twy, twz, vhat, gscratch);                        \
+    }                                                                                                \
+    return cudaGetLastError();                                                                       \
+  }
+    RSX_FOR_EACH_A(RSX_CASE)
+#undef RSX_CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace rsx

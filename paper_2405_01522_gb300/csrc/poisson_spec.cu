@@ -1,0 +1,33 @@
+// Casida pair-spectrum launcher (fp32 spectra, bf16 hi/lo panel)
+#include "poisson_launch.cuh"
+
+namespace rsx {
+
+cudaError_t launch_spectrum_f32(const Geom& g, int nq, const Cx<float>* inter, const Cx<float>* twy,
+                                const Cx<float>* twz, const float* vhat, float h3, uint16_t* hi,
+                                uint16_t* lo, size_t ld, cudaStream_t s) {
+  if (nq <= 0) return cudaSuccess;
+  if (g.Ay != g.Az) return cudaErrorInvalidValue;
+  const size_t smem = pass2_scratch_smem<float>(g.Ay, g.Az) + pass2_plane_bytes<float>(g);
+  if (smem > (size_t)max_dyn_smem()) return cudaErrorInvalidValue;
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const long long nwork = (long long)nq * g.Hx;
+  const int grid = (int)(nwork < 4LL * nsm ? nwork : 4LL * nsm);
+  switch (g.Ay) {
+#define RSX_CASE(a)                                                                              \
+  case a: {                                                                                      \
+    auto k = k_spectrum<a, a>;                                                                   \
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+    if (e != cudaSuccess) return e;                                                              \
+    k<<<grid, kThreads, smem, s>>>(g, nq, inter, twy, twz, vhat, h3, hi, lo, ld);                \
+    return cudaGetLastError();                                                                   \
+  }
+    RSX_FOR_EACH_A(RSX_CASE)
+#undef RSX_CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace rsx

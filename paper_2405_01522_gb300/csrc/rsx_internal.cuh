@@ -1,0 +1,93 @@
+// Internal declarations shared by the CUDA translation units of librsx.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+
+#include "fft_small.cuh"
+
+namespace rsx {
+
+// Line transforms: an FFT of length M = 16 * A along one axis is done by a half-warp
+// (16 lanes) in two register stages: A-point DFTs over stride-16 inputs, a twiddle,
+// a transpose through shared memory, then 16-point DFTs (see poisson_kernels.cuh).
+constexpr int kLinesPerCta = 16;      // 8 warps x 2 half-warps
+constexpr int kThreads = 256;
+constexpr int kScrPitch = 17;         // scratch row pitch (complex), avoids bank conflicts
+constexpr int kRowsPerCta = 32;       // rows (y) per CTA in the x passes
+constexpr int kXsPitch = kRowsPerCta + 1;
+
+// Which pair densities a batch holds and which pairs each output accumulates.
+//   PROD: pair q = b * na + a  has density A[a] * B[b]  (exchange: A = phi, B = psi;
+//         Casida: A = virtual, B = occupied, so q = i * n_virt + a);
+//         output p (an element of B) accumulates pairs q = p * na + a, partner A[a].
+//   SYM:  unique pairs a <= b of one set A (upper triangle, row-major);
+//         output p accumulates every pair containing p, partner the other orbital.
+enum PairMode { kProd = 0, kSym = 1 };
+
+template <typename R>
+struct PairMap {
+  int mode;
+  const R* A;
+  const R* B;
+  int na, nb;
+  size_t N;  // points per orbital
+
+  __device__ __forceinline__ int npairs() const { return mode == kProd ? na * nb : na * (na + 1) / 2; }
+  __device__ __forceinline__ void pair(int q, const R*& f1, const R*& f2) const {
+    if (mode == kProd) {
+      const int b = q / na, a = q - b * na;
+      f1 = A + (size_t)a * N;
+      f2 = B + (size_t)b * N;
+    } else {
+      int i = 0, rem = q;
+      while (rem >= na - i) { rem -= na - i; ++i; }
+      f1 = A + (size_t)i * N;
+      f2 = A + (size_t)(i + rem) * N;
+    }
+  }
+  __device__ __forceinline__ int nentries(int /*p*/) const { return na; }
+  // entry e of output p: pair index and the orbital multiplied into the accumulator
+  __device__ __forceinline__ void entry(int p, int e, int& q, const R*& partner) const {
+    if (mode == kProd) {
+      q = p * na + e;
+    } else {
+      const int i = p < e ? p : e, j = p < e ? e : p;
+      q = i * na - i * (i - 1) / 2 + (j - i);
+    }
+    partner = A + (size_t)e * N;
+  }
+};
+
+struct Geom {
+  int nz, ny, nx;     // box
+  int Mz, My, Mx;     // padded (2n)
+  int Az, Ay, Ax;     // M / 16
+  int Hx;             // Mx / 2 + 1 (half spectrum along x)
+  __host__ __device__ size_t N() const { return (size_t)nz * ny * nx; }
+  __host__ __device__ size_t inter_elems() const { return (size_t)Hx * nz * ny; }  // complex per pair
+};
+
+// ---- launchers (defined per precision in poisson_f32.cu / poisson_f64.cu)
+template <typename R>
+cudaError_t launch_pass1(const Geom& g, const PairMap<R>& pm, int q0, int nq, Cx<R>* inter,
+                         const Cx<R>* twx, cudaStream_t s);
+template <typename R>
+cudaError_t launch_pass2(const Geom& g, int nq, Cx<R>* inter, const Cx<R>* twy, const Cx<R>* twz,
+                         const R* vhat, R* gscratch, int grid, cudaStream_t s);
+template <typename R>
+cudaError_t launch_pass3(const Geom& g, const PairMap<R>& pm, int q0, int p0, int np, const Cx<R>* inter,
+                         const Cx<R>* twx, R* out, cudaStream_t s);
+// forward y/z transform of each pair plane, weighted by sqrt(w_G vhat(G) h^3) and split
+// into bf16 hi/lo rows of the K panel (t-major, G contiguous)
+cudaError_t launch_spectrum_f32(const Geom& g, int nq, const Cx<float>* inter, const Cx<float>* twy,
+                                const Cx<float>* twz, const float* vhat, float h3, uint16_t* hi,
+                                uint16_t* lo, size_t ld, cudaStream_t s);
+template <typename R>
+size_t pass2_smem_bytes(const Geom& g, bool* fits);
+template <typename R>
+int pass2_occupancy(const Geom& g);  // resident pass-2 CTAs per SM (shared-memory variant)
+
+bool axis_supported(int A);
+
+}  // namespace rsx

@@ -1,0 +1,172 @@
+"""Thin ctypes binding of librsx (include/rsx.h): argument marshalling only.
+
+Every computation runs in the CUDA library.  Tensors are PyTorch CUDA tensors used as
+device memory; the stream is torch's current stream unless one is given.  If the
+library has not been built the first call raises: there is no CPU fallback.
+"""
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librsx.so")
+
+RSX_OK, RSX_EINVAL, RSX_ENOMEM, RSX_ECUDA, RSX_ENOTPD, RSX_ETIMEOUT, RSX_EUNSUPPORTED = range(7)
+RSX_FP64, RSX_FP32 = 0, 1
+ERROR_NAMES = {1: "RSX_EINVAL", 2: "RSX_ENOMEM", 3: "RSX_ECUDA", 4: "RSX_ENOTPD", 5: "RSX_ETIMEOUT",
+               6: "RSX_EUNSUPPORTED"}
+
+# exported symbol -> ctypes argument types (mirrors include/rsx.h)
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+SIGNATURES = {
+    "rsx_create": [ctypes.POINTER(_P), _I, _I, _I, _D, _I, _I],
+    "rsx_destroy": [_P],
+    "rsx_last_error": [_P],
+    "rsx_set_workspace_limit": [_P, ctypes.c_size_t],
+    "rsx_build_pair_densities": [_P, _P, _I, _P, _I, _P, _P],
+    "rsx_exchange_apply": [_P, _P, _I, _P, _I, _P, _P],
+    "rsx_ace_build": [_P, _P, _I, _P, _P, _P],
+    "rsx_ace_apply": [_P, _P, _I, _P, _I, _P, _P],
+    "rsx_casida_K": [_P, _P, _I, _P, _I, _P, _P],
+    "rsx_casida_Kd": [_P, _P, _I, _P, _I, _P, _P],
+    "rsx_casida_solve": [_P, _P, _I, _P, _I, _P, _P, _D, _I, _P, _P, _P],
+    "rsx_sync_status": [_P, _P],
+}
+
+_lib = None
+
+
+class RsxError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERROR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def load(path=LIB_PATH):
+    """Open librsx.so once and declare its signatures."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError(f"librsx.so not found at {path}: build it with __graft_entry__.build()")
+        lib = ctypes.CDLL(path)
+        for name, args in SIGNATURES.items():
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = ctypes.c_char_p if name == "rsx_last_error" else ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Context:
+    """One rsx context: box (nz, ny, nx), spacing h, precision 'fp32' or 'fp64'."""
+
+    def __init__(self, shape, h, precision="fp32", device=0):
+        self.lib = load()
+        self.shape = tuple(int(s) for s in shape)
+        self.h = float(h)
+        self.precision = precision
+        self.dtype = torch.float32 if precision == "fp32" else torch.float64
+        self.device = torch.device("cuda", device)
+        self.N = self.shape[0] * self.shape[1] * self.shape[2]
+        h_ = ctypes.c_void_p()
+        code = self.lib.rsx_create(ctypes.byref(h_), self.shape[0], self.shape[1], self.shape[2], self.h,
+                                   RSX_FP32 if precision == "fp32" else RSX_FP64, device)
+        if code != RSX_OK:
+            raise RsxError(code, "rsx_create failed")
+        self.handle = h_
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.rsx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, code):
+        if code != RSX_OK:
+            raise RsxError(code, self.lib.rsx_last_error(self.handle).decode())
+
+    def _orb(self, t, name):
+        if not (t.is_cuda and t.dtype == self.dtype and t.is_contiguous()):
+            raise ValueError(f"{name}: need a contiguous {self.dtype} CUDA tensor")
+        if t.numel() % self.N:
+            raise ValueError(f"{name}: size is not a multiple of the grid")
+        return t.numel() // self.N
+
+    def _new(self, n):
+        return torch.empty((n,) + self.shape, dtype=self.dtype, device=self.device)
+
+    def set_workspace_limit(self, nbytes):
+        self._check(self.lib.rsx_set_workspace_limit(self.handle, int(nbytes)))
+
+    def pair_densities(self, a, b, out=None, stream=None):
+        na, nb = self._orb(a, "a"), self._orb(b, "b")
+        out = self._new(na * nb) if out is None else out
+        self._check(self.lib.rsx_build_pair_densities(self.handle, _ptr(a), na, _ptr(b), nb, _ptr(out),
+                                                      _stream(stream)))
+        return out
+
+    def exchange_apply(self, phi, psi, out=None, stream=None):
+        nocc, npsi = self._orb(phi, "phi"), self._orb(psi, "psi")
+        out = self._new(npsi) if out is None else out
+        self._check(self.lib.rsx_exchange_apply(self.handle, _ptr(phi), nocc, _ptr(psi), npsi, _ptr(out),
+                                                _stream(stream)))
+        return out
+
+    def ace_build(self, phi, xi=None, M=None, stream=None):
+        nocc = self._orb(phi, "phi")
+        xi = self._new(nocc) if xi is None else xi
+        self._check(self.lib.rsx_ace_build(self.handle, _ptr(phi), nocc, _ptr(xi), _ptr(M), _stream(stream)))
+        return xi
+
+    def ace_apply(self, xi, psi, out=None, stream=None):
+        nxi, npsi = self._orb(xi, "xi"), self._orb(psi, "psi")
+        out = self._new(npsi) if out is None else out
+        self._check(self.lib.rsx_ace_apply(self.handle, _ptr(xi), nxi, _ptr(psi), npsi, _ptr(out),
+                                           _stream(stream)))
+        return out
+
+    def casida_K(self, phi_occ, phi_virt, K=None, stream=None):
+        no, nv = self._orb(phi_occ, "phi_occ"), self._orb(phi_virt, "phi_virt")
+        nt = no * nv
+        K = torch.empty((nt, nt), dtype=torch.float64, device=self.device) if K is None else K
+        self._check(self.lib.rsx_casida_K(self.handle, _ptr(phi_occ), no, _ptr(phi_virt), nv, _ptr(K),
+                                          _stream(stream)))
+        return K
+
+    def casida_Kd(self, phi_occ, phi_virt, Kd=None, stream=None):
+        no, nv = self._orb(phi_occ, "phi_occ"), self._orb(phi_virt, "phi_virt")
+        nt = no * nv
+        Kd = torch.empty((nt, nt), dtype=torch.float64, device=self.device) if Kd is None else Kd
+        self._check(self.lib.rsx_casida_Kd(self.handle, _ptr(phi_occ), no, _ptr(phi_virt), nv, _ptr(Kd),
+                                           _stream(stream)))
+        return Kd
+
+    def casida_solve(self, eps_occ, eps_virt, K, Kd=None, delta_M=2.0, nroots=10, vectors=False, stream=None):
+        no, nv = eps_occ.numel(), eps_virt.numel()
+        nt = no * nv
+        omega = torch.empty(nroots, dtype=torch.float64, device=self.device)
+        X = torch.empty((nroots, nt), dtype=torch.float64, device=self.device) if vectors else None
+        self._check(self.lib.rsx_casida_solve(self.handle, _ptr(eps_occ), no, _ptr(eps_virt), nv, _ptr(K),
+                                              _ptr(Kd), float(delta_M), int(nroots), _ptr(omega), _ptr(X),
+                                              _stream(stream)))
+        return (omega, X) if vectors else omega
+
+    def sync(self, stream=None):
+        self._check(self.lib.rsx_sync_status(self.handle, _stream(stream)))

@@ -1,0 +1,180 @@
+"""GPU parity: pair densities, exchange action (Eq. 2) and ACE (Eqs. 11-13) vs the oracle.
+
+All calls go through the C ABI (ctypes binding).  Sizes span several CTA tiles and
+ragged tails: ny = 24 and 40 leave a partial 32-row block, nz = 24 and 40 are not
+multiples of 16 (uneven row loops), nx != ny exercises the per-axis transforms.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2405_01522_gb300 import inputs
+from paper_2405_01522_gb300 import rsx
+from gpu_util import TOL, TOL_ENERGY, need_gpu, rel_max_err, to_dev
+
+pytestmark = pytest.mark.gpu
+
+CASES = [
+    ((16, 16, 16), 0.40, 2, 3, "fp32"),
+    ((24, 24, 24), 0.35, 3, 2, "fp32"),
+    ((24, 24, 40), 0.30, 2, 2, "fp32"),
+    ((40, 40, 16), 0.30, 2, 3, "fp32"),
+    ((16, 16, 16), 0.40, 2, 3, "fp64"),
+    ((24, 24, 40), 0.30, 2, 2, "fp64"),
+    ((56, 56, 24), 0.30, 1, 2, "fp64"),
+]
+
+
+def system(shape, h, nocc, npsi, seed=0):
+    return inputs.exchange_system(h=h, nocc=nocc, npsi=npsi, shape=shape, radius=1.5, seed=seed)
+
+
+@pytest.mark.parametrize("shape,h,nocc,npsi,prec", CASES)
+def test_exchange_apply_parity(shape, h, nocc, npsi, prec):
+    need_gpu()
+    s = system(shape, h, nocc, npsi)
+    ref = oracle.exchange_apply(s.phi, s.psi, h)
+    ctx = rsx.Context(shape, h, prec)
+    out = ctx.exchange_apply(to_dev(s.phi, prec), to_dev(s.psi, prec))
+    ctx.sync()
+    got = out.double().cpu().numpy()
+    assert rel_max_err(got, ref) < TOL[prec]
+    for p in range(npsi):
+        e_ref = oracle.inner(s.psi[p], ref[p], h)
+        e_got = oracle.inner(s.psi[p], got[p], h)
+        assert abs(e_got - e_ref) <= TOL_ENERGY[prec] * abs(e_ref)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_chunked_workspace_gives_identical_bits(prec):
+    need_gpu()
+    shape, h = (24, 24, 24), 0.35
+    s = system(shape, h, 3, 4, seed=3)
+    ctx = rsx.Context(shape, h, prec)
+    phi, psi = to_dev(s.phi, prec), to_dev(s.psi, prec)
+    a = ctx.exchange_apply(phi, psi)
+    per_pair = (2 * shape[2] // 2 + 1) * shape[0] * shape[1] * (8 if prec == "fp32" else 16)
+    ctx.set_workspace_limit(3 * per_pair)          # one output orbital per chunk
+    b = ctx.exchange_apply(phi, psi)
+    ctx.sync()
+    assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_pair_densities_exact(prec):
+    need_gpu()
+    s = system((16, 16, 24), 0.4, 3, 2)
+    ctx = rsx.Context((16, 16, 24), 0.4, prec)
+    a, b = to_dev(s.phi, prec), to_dev(s.psi, prec)
+    rho = ctx.pair_densities(a, b)
+    ctx.sync()
+    ref = (a[:, None] * b[None, :]).reshape(rho.shape)
+    assert torch.equal(rho, ref)
+
+
+@pytest.mark.parametrize("shape,h,nocc,prec", [((24, 24, 24), 0.35, 4, "fp32"), ((24, 24, 40), 0.3, 3, "fp64"),
+                                               ((40, 40, 40), 0.3, 6, "fp32")])
+def test_ace_build_and_apply_parity(shape, h, nocc, prec):
+    need_gpu()
+    s = system(shape, h, nocc, 3, seed=1)
+    zeta, W, M, L = oracle.ace_build(s.phi, h, return_all=True)
+    ctx = rsx.Context(shape, h, prec)
+    phi = to_dev(s.phi, prec)
+    Mg = torch.empty((nocc, nocc), dtype=torch.float64, device="cuda")
+    xi = ctx.ace_build(phi, M=Mg)
+    ctx.sync()
+    assert rel_max_err(Mg.cpu().numpy(), M) < (2e-6 if prec == "fp32" else 1e-11)
+    assert rel_max_err(xi.double().cpu().numpy(), zeta) < (2e-5 if prec == "fp32" else 1e-10)
+    psi = to_dev(s.psi, prec)
+    va = ctx.ace_apply(xi, psi)
+    ctx.sync()
+    ref = oracle.ace_apply(zeta, s.psi, h)
+    assert rel_max_err(va.double().cpu().numpy(), ref) < (2e-5 if prec == "fp32" else 1e-10)
+    # ACE reproduces the exchange on its own orbitals (Sec. 3.1), on the GPU
+    w_gpu = ctx.exchange_apply(phi, phi)
+    v_phi = ctx.ace_apply(xi, phi)
+    ctx.sync()
+    assert rel_max_err(v_phi.double().cpu().numpy(), w_gpu.double().cpu().numpy()) < (
+        3e-5 if prec == "fp32" else 1e-10)
+
+
+def test_ace_apply_in_place():
+    need_gpu()
+    shape, h = (16, 16, 16), 0.4
+    s = system(shape, h, 3, 4, seed=2)
+    ctx = rsx.Context(shape, h, "fp32")
+    xi = ctx.ace_build(to_dev(s.phi, "fp32"))
+    psi = to_dev(s.psi, "fp32")
+    ref = ctx.ace_apply(xi, psi)
+    ctx.ace_apply(xi, psi, out=psi)
+    ctx.sync()
+    assert torch.equal(ref, psi)
+
+
+def test_ace_not_positive_definite_is_reported():
+    need_gpu()
+    shape, h = (16, 16, 16), 0.4
+    s = system(shape, h, 3, 0)
+    phi = s.phi.copy()
+    phi[1] = 0.0                                     # M gets a zero row: pivot 0
+    ctx = rsx.Context(shape, h, "fp64")
+    ctx.ace_build(to_dev(phi, "fp64"))
+    with pytest.raises(rsx.RsxError) as e:
+        ctx.sync()
+    assert e.value.code == rsx.RSX_ENOTPD
+    ctx.sync()                                       # status was cleared
+
+
+def test_invalid_arguments_are_rejected():
+    need_gpu()
+    shape, h = (16, 16, 16), 0.4
+    s = system(shape, h, 2, 2)
+    ctx = rsx.Context(shape, h, "fp32")
+    phi, psi = to_dev(s.phi, "fp32"), to_dev(s.psi, "fp32")
+    with pytest.raises(rsx.RsxError) as e:
+        ctx.exchange_apply(phi, psi, out=psi)        # out aliases psi
+    assert e.value.code == rsx.RSX_EINVAL
+    lib = rsx.load()
+    assert lib.rsx_exchange_apply(ctx.handle, rsx._ptr(phi), 0, rsx._ptr(psi), 2, rsx._ptr(psi), None) == 1
+    with pytest.raises(ValueError):
+        ctx.exchange_apply(phi.double(), psi)
+
+
+def test_config1_plain_fp64_exchange_and_ace():
+    """32^3 at 0.3 bohr, 4 orbitals of 3 s-Gaussians, seed 0: all 16 pairs plus ACE, FP64."""
+    need_gpu()
+    s = inputs.exchange_system(n=32, h=0.3, nocc=4)
+    ref = oracle.exchange_apply(s.phi, s.phi, s.h)
+    zeta = oracle.ace_build(s.phi, s.h)
+    ctx = rsx.Context(s.shape, s.h, "fp64")
+    phi = to_dev(s.phi, "fp64")
+    w = ctx.exchange_apply(phi, phi)
+    xi = ctx.ace_build(phi)
+    ctx.sync()
+    assert rel_max_err(w.cpu().numpy(), ref) < 1e-11
+    assert rel_max_err(xi.cpu().numpy(), zeta) < 1e-10
+    ex_ref = oracle.exchange_energy(s.phi, s.h)
+    ex_gpu = 0.5 * sum(oracle.inner(s.phi[i], w[i].cpu().numpy(), s.h) for i in range(4))
+    assert abs(ex_gpu - ex_ref) <= 1e-12 * abs(ex_ref)
+
+
+def test_config2_full_size_sampled_outputs():
+    """96^3 at 0.2 bohr, 16 orbitals on 12 centres, 32 trials (512 solves) in FP32, the
+    launch the benchmark times; the oracle recomputes sampled outputs p one by one."""
+    need_gpu()
+    s = inputs.batched_system()
+    ctx = rsx.Context(s.shape, s.h, "fp32")
+    phi, psi = to_dev(s.phi, "fp32"), to_dev(s.psi, "fp32")
+    out = ctx.exchange_apply(phi, psi)
+    xi = ctx.ace_build(phi)
+    w = ctx.exchange_apply(phi, phi)
+    vphi = ctx.ace_apply(xi, phi)
+    ctx.sync()
+    for p in (0, 31):
+        ref = oracle.exchange_apply(s.phi, s.psi[p:p + 1], s.h)[0]
+        got = out[p].double().cpu().numpy()
+        assert rel_max_err(got, ref) < TOL["fp32"]
+        e_ref, e_got = oracle.inner(s.psi[p], ref, s.h), oracle.inner(s.psi[p], got, s.h)
+        assert abs(e_got - e_ref) <= TOL_ENERGY["fp32"] * abs(e_ref)
+    assert rel_max_err(vphi.double().cpu().numpy(), w.double().cpu().numpy()) < 3e-5

@@ -1,0 +1,385 @@
+#!/usr/bin/env python
+"""Benchmark of the exact-exchange hot path: pair Poisson solves per second.
+
+Workload (one "step"): 96^3 box at h = 0.2 bohr (padded 192^3), 16 orthonormal
+occupied orbitals on 12 random Gaussian centres and 32 trial functions (seed 0):
+  exchange apply Vx[Phi] Psi      512 pair solves
+  ACE build from Phi              136 unique pair solves (rho_ij = rho_ji) + FP64 Cholesky
+  ACE apply to Psi                two skinny contractions
+= 648 pair Poisson solves per step.  value = solves/s over all GPUs (replicas: every
+rank runs the same workload on its own GPU; weak scaling).
+
+Also reported on the same JSON line: the end-to-end rate through the public API with
+host copies, the FP64 plain form of the same step, FP32-vs-FP64 accuracy, the
+roofline of the dominant kernel from CUDA events recorded by the library around every
+launch in the timed region, SM clocks sampled during it, and the CPU oracle baseline.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl rsx|reference]
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2405_01522_gb300 import inputs  # noqa: E402
+
+NOCC, NPSI, EDGE, H = 16, 32, 96, 0.2
+SOLVES_EXCHANGE = NOCC * NPSI
+SOLVES_ACE = NOCC * (NOCC + 1) // 2
+SOLVES_PER_STEP = SOLVES_EXCHANGE + SOLVES_ACE
+WORKLOAD = ("exchange apply + ACE build + ACE apply, 96^3 box at h=0.2 bohr padded to 192^3, "
+            "16 orthonormal orbitals on 12 Gaussian centres (exponents U[0.3,3]), 32 trial functions, "
+            "seed 0: 512 + 136 pair Poisson solves per step")
+METRIC = "pair Poisson solves/s"
+UNIT = "solves/s"
+
+
+def env_rank():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
+            int(os.environ.get("WORLD_SIZE", 1)))
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.proc = None
+        self.path = None
+        try:
+            bus = torch.cuda.get_device_properties(device).pci_bus_id
+        except Exception:
+            bus = None
+        self.sel = ["-i", bus] if bus else []
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100"]
+                + self.sel, stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), parts[4:8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i in range(4) if r[i].lower().startswith("active")})
+        return {"sm_mhz": float(np.median([r[0] for r in rows])), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------- workload
+def make_inputs():
+    s = inputs.batched_system(n=EDGE, h=H, nocc=NOCC, ncentres=12, alpha=(0.3, 3.0), radius=3.0,
+                              npsi=NPSI, seed=0)
+    return s
+
+
+def algorithmic_bytes(kernel, shape, nq, nocc, npsi, elem=4):
+    """Compulsory HBM bytes of one launch over nq pairs (model stated in the design doc)."""
+    nz, ny, nx = shape
+    N = nz * ny * nx
+    inter = (nx + 1) * nz * ny * 2 * elem          # (Mx/2 + 1) * nz * ny complex per pair
+    table = (nx + 1) * (ny + 1) * (nz + 1) * elem   # kernel table (M/2 + 1)^3
+    if kernel == "pass1_x_forward":
+        return nq * inter + (nocc + npsi) * N * elem
+    if kernel == "pass2_yz_kernel":
+        return 2 * nq * inter + table
+    if kernel == "pass3_x_inverse_accumulate":
+        return nq * inter + (nocc + npsi) * N * elem
+    return None
+
+
+def run_rsx(args, rank, local_rank, world):
+    from paper_2405_01522_gb300 import rsx
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    s = make_inputs()
+    shape = s.shape
+    ctx = rsx.Context(shape, H, "fp32", device=local_rank)
+    phi = torch.from_numpy(s.phi).float().to(dev)
+    psi = torch.from_numpy(s.psi).float().to(dev)
+    vx = torch.empty_like(psi)
+    xi = torch.empty_like(phi)
+    va = torch.empty_like(psi)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        ctx.exchange_apply(phi, psi, out=vx)
+        ctx.ace_build(phi, xi=xi)
+        ctx.ace_apply(xi, psi, out=va)
+
+    for _ in range(args.warmup):
+        step()
+    ctx.sync()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- timed region (device-resident inputs)
+    clocks = ClockSampler(local_rank)
+    ctx.profile_reset()
+    ctx.profile(True)
+    clocks.start()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    ctx.profile(False)
+    ctx.sync()
+    ms = e0.elapsed_time(e1)
+    prof = ctx.profile_read()
+    ms_max = ms
+    if dist is not None:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = t.item()
+    ms_step = ms_max / args.steps
+    value = world * SOLVES_PER_STEP * args.steps / (ms_max / 1e3)
+
+    # ---- per-kernel shares and the dominant kernel's roofline
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    total_kernel_ms = sum(v[0] for v in prof.values())
+    kernels = {k: {"ms_per_launch": v[0] / v[1], "launches": v[1], "share": v[0] / total_kernel_ms}
+               for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])}
+    launches = sum(v[1] for v in prof.values())
+    # pair counts per launch of each pass in one step: exchange (512 pairs) and ACE (136)
+    per_launch_pairs = {"pass1_x_forward": [SOLVES_EXCHANGE, SOLVES_ACE],
+                        "pass2_yz_kernel": [SOLVES_EXCHANGE, SOLVES_ACE],
+                        "pass3_x_inverse_accumulate": [SOLVES_EXCHANGE, SOLVES_ACE]}
+    top = next(iter(kernels))
+    roof = None
+    if top in per_launch_pairs:
+        byts = [algorithmic_bytes(top, shape, nq, NOCC, NPSI if nq == SOLVES_EXCHANGE else 0)
+                for nq in per_launch_pairs[top]]
+        avg_bytes = sum(byts) / len(byts)
+        avg_ms = kernels[top]["ms_per_launch"]
+        ach = avg_bytes / (avg_ms / 1e3) / 1e9
+        roof = {"kernel": top, "bound": "hbm", "achieved": round(ach, 1), "peak": hbm_peak, "unit": "GB/s",
+                "frac": round(ach / hbm_peak, 4), "traffic": None, "peak_source": peak_src,
+                "algorithmic_bytes_per_launch": avg_bytes}
+
+    # ---- end to end through the public API: pinned host inputs -> device -> results -> host
+    phi_h = torch.from_numpy(s.phi).float().pin_memory()
+    psi_h = torch.from_numpy(s.psi).float().pin_memory()
+    vx_h = torch.empty(vx.shape, dtype=torch.float32).pin_memory()
+    va_h = torch.empty(va.shape, dtype=torch.float32).pin_memory()
+    phi_d, psi_d = torch.empty_like(phi), torch.empty_like(psi)
+
+    def e2e_step():
+        phi_d.copy_(phi_h, non_blocking=True)
+        psi_d.copy_(psi_h, non_blocking=True)
+        ctx.exchange_apply(phi_d, psi_d, out=vx)
+        ctx.ace_build(phi_d, xi=xi)
+        ctx.ace_apply(xi, psi_d, out=va)
+        vx_h.copy_(vx, non_blocking=True)
+        va_h.copy_(va, non_blocking=True)
+
+    e2e_step()
+    barrier()
+    e2 = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    e2[0].record(stream)
+    ne2e = max(3, args.steps // 4)
+    for _ in range(ne2e):
+        e2e_step()
+    e2[1].record(stream)
+    barrier()
+    ms_e2e = e2[0].elapsed_time(e2[1])
+    if dist is not None:
+        t = torch.tensor([ms_e2e], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_e2e = t.item()
+    e2e = {"value": world * SOLVES_PER_STEP * ne2e / (ms_e2e / 1e3), "unit": UNIT,
+           "h2d_bytes_per_step": phi_h.numel() * 4 + psi_h.numel() * 4,
+           "d2h_bytes_per_step": vx_h.numel() * 4 + va_h.numel() * 4, "steps": ne2e}
+
+    # ---- ACE build time alone (FP32)
+    ctx.sync()
+    ea = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ea[0].record(stream)
+    for _ in range(5):
+        ctx.ace_build(phi, xi=xi)
+    ea[1].record(stream)
+    torch.cuda.synchronize()
+    ace_ms = ea[0].elapsed_time(ea[1]) / 5
+
+    out = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "grid": list(shape), "padded": [2 * x for x in shape], "h_bohr": H,
+                      "nocc": NOCC, "npsi": NPSI, "solves_per_step": SOLVES_PER_STEP,
+                      "l2": "no flush: inputs (170 MB) and FFT intermediates (3.7 GB) exceed the 129 MB L2",
+                      "parallelism": f"replicas x{world}"},
+           "roofline": roof, "kernels": kernels, "gpu_launches": launches, "clocks": clk, "e2e": e2e,
+           "ace_build_ms": round(ace_ms, 4)}
+
+    # ---- FP64 plain form of the same step, and FP32 accuracy against it
+    if not args.skip_fp64 and rank == 0:
+        ctx64 = rsx.Context(shape, H, "fp64", device=local_rank)
+        phi64 = torch.from_numpy(s.phi).to(dev)
+        psi64 = torch.from_numpy(s.psi).to(dev)
+        vx64 = torch.empty_like(psi64)
+        xi64 = torch.empty_like(phi64)
+        va64 = torch.empty_like(psi64)
+
+        def step64():
+            ctx64.exchange_apply(phi64, psi64, out=vx64)
+            ctx64.ace_build(phi64, xi=xi64)
+            ctx64.ace_apply(xi64, psi64, out=va64)
+
+        step64()
+        ctx64.sync()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        step64()
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = f0.elapsed_time(f1)
+        step()
+        ctx.sync()
+        h3 = H ** 3
+        e32 = (psi.double() * vx.double()).sum(dim=(1, 2, 3)) * h3
+        e64 = (psi64 * vx64).sum(dim=(1, 2, 3)) * h3
+        ex32 = 0.5 * h3 * (phi.double() * ctx.exchange_apply(phi, phi).double()).sum().item()
+        ex64 = 0.5 * h3 * (phi64 * ctx64.exchange_apply(phi64, phi64)).sum().item()
+        out["fp64_plain"] = {"value": round(SOLVES_PER_STEP / (ms64 / 1e3), 1), "unit": UNIT,
+                             "ms_per_step": round(ms64, 3), "speedup_fp32_over_fp64": round(ms64 / ms_step, 2)}
+        out["accuracy"] = {
+            "ref": "FP64 GPU path (parity-tested against the FP64 CPU oracle to 1e-11)",
+            "vx_energy_rel_err_max": float(((e32 - e64).abs() / e64.abs()).max()),
+            "exchange_energy_rel_err": abs(ex32 - ex64) / abs(ex64),
+            "vx_rel_max_err": float((vx.double() - vx64).abs().max() / vx64.abs().max()),
+            "ace_apply_rel_max_err": float((va.double() - va64).abs().max() / va64.abs().max()),
+            "tolerance_energy": 1e-6}
+        ctx64.close()
+
+    # ---- CPU oracle baseline (rank 0, N = 1 only)
+    if rank == 0 and world == 1 and not args.skip_cpu:
+        out["cpu_baseline"] = cpu_baseline(s, nsolve=args.cpu_solves)
+
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def cpu_baseline(s, nsolve=16):
+    """The FP64 oracle as it stands, on the host, for a bounded sample of the workload:
+    the exchange action on trial function 0 from the first `nsolve` orbitals."""
+    import oracle
+    t0 = time.perf_counter()
+    oracle.exchange_apply(s.phi[:nsolve], s.psi[:1], s.h)
+    dt = time.perf_counter() - t0
+    return {"value": round(nsolve / dt, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{nsolve} pair solves (Vx on trial 0 from orbitals 0..{nsolve - 1}) of the 96^3 workload, "
+                      f"numpy pocketfft FP64, single thread; {dt:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    """The oracle as the reference arm: same metric and workload, bounded CPU sample per step."""
+    if rank != 0:
+        return
+    import oracle
+    s = make_inputs()
+    per_step = 2
+    for _ in range(args.warmup):
+        oracle.exchange_apply(s.phi[:per_step], s.psi[:1], s.h)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        j0 = (2 * k) % NOCC
+        oracle.exchange_apply(s.phi[j0:j0 + per_step], s.psi[k % NPSI:k % NPSI + 1], s.h)
+    dt = time.perf_counter() - t0
+    value = per_step * args.steps / dt
+    out = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(1e3 * dt / args.steps, 2), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "grid": list(s.shape), "h_bohr": H, "nocc": NOCC, "npsi": NPSI,
+                      "parallelism": "host"},
+           "impl": "reference",
+           "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": f"{per_step} pair solves per step (FP64 numpy oracle, single thread)"},
+           "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="rsx", choices=["rsx", "reference"])
+    ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--cpu-solves", type=int, default=16)
+    ap.add_argument("--nocc", type=int, default=16, help="smaller cases for profiling captures only")
+    ap.add_argument("--npsi", type=int, default=32, help="smaller cases for profiling captures only")
+    args = ap.parse_args()
+    global NOCC, NPSI, SOLVES_EXCHANGE, SOLVES_ACE, SOLVES_PER_STEP
+    NOCC, NPSI = args.nocc, args.npsi
+    SOLVES_EXCHANGE = NOCC * NPSI
+    SOLVES_ACE = NOCC * (NOCC + 1) // 2
+    SOLVES_PER_STEP = SOLVES_EXCHANGE + SOLVES_ACE
+    if args.warmup < 3:
+        args.warmup = 3
+    rank, local_rank, world = env_rank()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_rsx(args, rank, local_rank, world)
+
+
+if __name__ == "__main__":
+    main()

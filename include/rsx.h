@@ -121,6 +121,17 @@ int rsx_casida_solve(rsx_ctx* ctx, const double* eps_occ, int nocc, const double
                      const double* K, const double* Kd, double delta_M, int nroots, double* omega, double* X,
                      void* stream);
 
+/* Launch profiler (tracing).  While enabled, every kernel the context launches is
+ * bracketed by CUDA events recorded on the launching stream; rsx_profile_read waits for
+ * the pending events and returns, for kernel id `kernel` (0 <= kernel < rsx_kernel_count()),
+ * the summed device time in ms and the number of launches since the last reset.
+ * Errors: RSX_EINVAL (null context, kernel out of range). */
+int rsx_profile_enable(rsx_ctx* ctx, int on);
+int rsx_profile_reset(rsx_ctx* ctx);
+int rsx_profile_read(rsx_ctx* ctx, int kernel, double* total_ms, long long* launches);
+int rsx_kernel_count(void);
+const char* rsx_kernel_name(int kernel);
+
 /* Synchronise `stream` and return the first deferred device error since the last call
  * (RSX_ENOTPD, RSX_ETIMEOUT) or a CUDA error; clears the device status word. */
 int rsx_sync_status(rsx_ctx* ctx, void* stream);

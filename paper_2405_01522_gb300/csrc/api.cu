@@ -48,6 +48,55 @@ int grow(rsx_ctx* c, void** p, size_t* have, size_t need, const char* what) {
 
 int set_error(rsx_ctx* c, int code, const char* msg) { return fail(c, code, "%s", msg); }
 
+const char* kernel_name(int id) {
+  static const char* names[kKCount] = {"pass1_x_forward", "pass2_yz_kernel", "pass3_x_inverse_accumulate",
+                                       "spectrum_panel", "gram", "gram_reduce", "cholesky_linv", "combine",
+                                       "pair_products", "k_gemm_tcgen05", "gemm_reduce", "tda_eigensolve",
+                                       "kd_contract"};
+  return (id >= 0 && id < kKCount) ? names[id] : "";
+}
+
+static cudaEvent_t prof_event(rsx_ctx* c) {
+  if (!c->prof_pool.empty()) {
+    cudaEvent_t e = c->prof_pool.back();
+    c->prof_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+ProfScope::ProfScope(rsx_ctx* c_, int id_, cudaStream_t s_) : c(c_), id(id_), s(s_) {
+  if (c && c->prof_on) {
+    a = prof_event(c);
+    b = prof_event(c);
+    cudaEventRecord(a, s);
+  }
+}
+
+ProfScope::~ProfScope() {
+  if (a) {
+    cudaEventRecord(b, s);
+    c->prof_pending.push_back({id, a, b});
+  }
+}
+
+static void prof_collect(rsx_ctx* c) {
+  for (auto& r : c->prof_pending) {
+    cudaEventSynchronize(r.b);
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+      c->prof_ms[r.id] += ms;
+      c->prof_n[r.id] += 1;
+    }
+    cudaGetLastError();
+    c->prof_pool.push_back(r.a);
+    c->prof_pool.push_back(r.b);
+  }
+  c->prof_pending.clear();
+}
+
 }  // namespace rsx
 
 namespace {
@@ -137,7 +186,10 @@ int solve_pairs(rsx_ctx* c, const PairMap<R>& pm, int q0, int nq, int p0, int np
   const Cx<R>* twz = (const Cx<R>*)c->tw[0];
   const Cx<R>* twy = (const Cx<R>*)c->tw[1];
   const Cx<R>* twx = (const Cx<R>*)c->tw[2];
-  rc = check_cuda(c, launch_pass1<R>(g, pm, q0, nq, inter, twx, s), "pass 1");
+  {
+    ProfScope ps(c, kKPass1, s);
+    rc = check_cuda(c, launch_pass1<R>(g, pm, q0, nq, inter, twx, s), "pass 1");
+  }
   if (rc) return rc;
   bool fits = false;
   pass2_smem_bytes<R>(g, &fits);
@@ -154,10 +206,15 @@ int solve_pairs(rsx_ctx* c, const PairMap<R>& pm, int q0, int nq, int p0, int np
     if (rc) return rc;
     gscr = (R*)c->gscr;
   }
-  rc = check_cuda(c, launch_pass2<R>(g, nq, inter, twy, twz, (const R*)c->vhat, gscr, grid, s), "pass 2");
+  {
+    ProfScope ps(c, kKPass2, s);
+    rc = check_cuda(c, launch_pass2<R>(g, nq, inter, twy, twz, (const R*)c->vhat, gscr, grid, s), "pass 2");
+  }
   if (rc) return rc;
-  if (out != nullptr)
+  if (out != nullptr) {
+    ProfScope ps(c, kKPass3, s);
     rc = check_cuda(c, launch_pass3<R>(g, pm, q0, p0, np, inter, twx, out, s), "pass 3");
+  }
   return rc;
 }
 
@@ -200,16 +257,29 @@ int ace_build(rsx_ctx* c, const void* phi, int nocc, void* xi, double* M_out, cu
   if (rc) return rc;
   R* linv_r = (R*)c->smallr;
   const double h3 = c->h * c->h * c->h;
-  rc = check_cuda(c, launch_gram<R>((const R*)phi, nocc, (const R*)xi, nocc, N, part, nblk, s), "gram");
+  {
+    ProfScope ps(c, kKGram, s);
+    rc = check_cuda(c, launch_gram<R>((const R*)phi, nocc, (const R*)xi, nocc, N, part, nblk, s), "gram");
+  }
   if (rc) return rc;
-  rc = check_cuda(c, launch_gram_reduce<R>(part, nblk, nocc, nocc, h3, false, M, (R*)nullptr, s), "gram reduce");
+  {
+    ProfScope ps(c, kKGramReduce, s);
+    rc = check_cuda(c, launch_gram_reduce<R>(part, nblk, nocc, nocc, h3, false, M, (R*)nullptr, s), "gram reduce");
+  }
   if (rc) return rc;
-  rc = check_cuda(c,
-                  launch_chol_linv(M, nocc, Linv, sizeof(R) == 4 ? (float*)linv_r : nullptr,
-                                   sizeof(R) == 8 ? (double*)linv_r : nullptr, c->status, s),
-                  "cholesky");
+  {
+    ProfScope ps(c, kKChol, s);
+    rc = check_cuda(c,
+                    launch_chol_linv(M, nocc, Linv, sizeof(R) == 4 ? (float*)linv_r : nullptr,
+                                     sizeof(R) == 8 ? (double*)linv_r : nullptr, c->status, s),
+                    "cholesky");
+  }
   if (rc) return rc;
-  rc = check_cuda(c, launch_combine<R>(linv_r, nocc, nocc, (const R*)xi, N, (R*)xi, 4 * c->nsm, s), "xi = L^-1 W");
+  {
+    ProfScope ps(c, kKCombine, s);
+    rc = check_cuda(c, launch_combine<R>(linv_r, nocc, nocc, (const R*)xi, N, (R*)xi, 4 * c->nsm, s),
+                    "xi = L^-1 W");
+  }
   if (rc) return rc;
   if (M_out)
     rc = check_cuda(c, cudaMemcpyAsync(M_out, M, sizeof(double) * nocc * nocc, cudaMemcpyDeviceToDevice, s),
@@ -229,11 +299,18 @@ int ace_apply(rsx_ctx* c, const void* xi, int nxi, const void* psi, int npsi, vo
   R* cm = (R*)c->smallr + 4096;
   const double h3 = c->h * c->h * c->h;
   // C_kp = h^3 <xi_k, psi_p>; Cm[p][k] = -C_kp
-  rc = check_cuda(c, launch_gram<R>((const R*)xi, nxi, (const R*)psi, npsi, N, part, nblk, s), "gram");
+  {
+    ProfScope ps(c, kKGram, s);
+    rc = check_cuda(c, launch_gram<R>((const R*)xi, nxi, (const R*)psi, npsi, N, part, nblk, s), "gram");
+  }
   if (rc) return rc;
-  rc = check_cuda(c, launch_gram_reduce<R>(part, nblk, nxi, npsi, -h3, true, (double*)nullptr, cm, s),
-                  "gram reduce");
+  {
+    ProfScope ps(c, kKGramReduce, s);
+    rc = check_cuda(c, launch_gram_reduce<R>(part, nblk, nxi, npsi, -h3, true, (double*)nullptr, cm, s),
+                    "gram reduce");
+  }
   if (rc) return rc;
+  ProfScope ps(c, kKCombine, s);
   return check_cuda(c, launch_combine<R>(cm, npsi, nxi, (const R*)xi, N, (R*)out, 4 * c->nsm, s), "ace apply");
 }
 
@@ -287,6 +364,8 @@ int rsx_destroy(rsx_ctx* c) {
   if (!c) return RSX_OK;
   cudaSetDevice(c->device);
   cudaDeviceSynchronize();
+  prof_collect(c);
+  for (cudaEvent_t e : c->prof_pool) cudaEventDestroy(e);
   void* bufs[] = {c->vhat, c->tw[0], c->tw[1], c->tw[2], c->work, c->gscr, c->dsm, c->smallr, c->status,
                   c->panel_hi, c->panel_lo, c->gemm_part, c->eig_work};
   for (void* b : bufs)
@@ -318,6 +397,7 @@ int rsx_build_pair_densities(rsx_ctx* c, const void* a, int na, const void* b, i
   if (overlaps(rho, (size_t)na * nb * N * es, a, na * N * es) || overlaps(rho, (size_t)na * nb * N * es, b, nb * N * es))
     return set_error(c, RSX_EINVAL, "rho aliases an input");
   cudaStream_t s = (cudaStream_t)stream;
+  ProfScope ps(c, kKPairProd, s);
   cudaError_t e = c->precision == RSX_FP32
                       ? launch_pair_products<float>((const float*)a, na, (const float*)b, nb, N, (float*)rho, s)
                       : launch_pair_products<double>((const double*)a, na, (const double*)b, nb, N, (double*)rho, s);
@@ -357,6 +437,34 @@ int rsx_ace_apply(rsx_ctx* c, const void* xi, int nxi, const void* psi, int npsi
   return c->precision == RSX_FP32 ? ace_apply<float>(c, xi, nxi, psi, npsi, out, s)
                                   : ace_apply<double>(c, xi, nxi, psi, npsi, out, s);
 }
+
+int rsx_profile_enable(rsx_ctx* c, int on) {
+  if (!c) return RSX_EINVAL;
+  c->prof_on = on != 0;
+  return RSX_OK;
+}
+
+int rsx_profile_reset(rsx_ctx* c) {
+  if (!c) return RSX_EINVAL;
+  prof_collect(c);
+  for (int i = 0; i < kKCount; ++i) {
+    c->prof_ms[i] = 0.0;
+    c->prof_n[i] = 0;
+  }
+  return RSX_OK;
+}
+
+int rsx_profile_read(rsx_ctx* c, int kernel, double* total_ms, long long* launches) {
+  if (!c || kernel < 0 || kernel >= kKCount) return RSX_EINVAL;
+  prof_collect(c);
+  if (total_ms) *total_ms = c->prof_ms[kernel];
+  if (launches) *launches = c->prof_n[kernel];
+  return RSX_OK;
+}
+
+int rsx_kernel_count(void) { return kKCount; }
+
+const char* rsx_kernel_name(int kernel) { return kernel_name(kernel); }
 
 int rsx_sync_status(rsx_ctx* c, void* stream) {
   RSX_PREP(c);

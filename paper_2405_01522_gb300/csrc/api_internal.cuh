@@ -3,7 +3,18 @@
 #include <algorithm>
 #include <cstddef>
 
+#include <vector>
+
 #include "rsx_internal.cuh"
+
+namespace rsx {
+// Kernel identifiers for the per-context launch profiler (CUDA events around launches).
+enum KernelId {
+  kKPass1 = 0, kKPass2, kKPass3, kKSpectrum, kKGram, kKGramReduce, kKChol, kKCombine, kKPairProd,
+  kKGemm, kKGemmReduce, kKEig, kKKdSolve, kKCount
+};
+const char* kernel_name(int id);
+}  // namespace rsx
 
 struct rsx_ctx {
   int device = 0;
@@ -25,6 +36,13 @@ struct rsx_ctx {
   void* gemm_part = nullptr; size_t gemm_part_bytes = 0;
   void* eig_work = nullptr; size_t eig_work_bytes = 0;
   int p2_occ[2] = {0, 0};
+  // launch profiler: events recorded around every kernel while enabled
+  bool prof_on = false;
+  struct ProfRec { int id; cudaEvent_t a, b; };
+  std::vector<ProfRec> prof_pending;
+  std::vector<cudaEvent_t> prof_pool;
+  double prof_ms[rsx::kKCount] = {0};
+  long long prof_n[rsx::kKCount] = {0};
   char err[512] = {0};
 
   size_t elem_size() const { return precision == 1 ? 4 : 8; }
@@ -40,6 +58,16 @@ namespace rsx {
 int check_cuda(rsx_ctx* c, cudaError_t e, const char* what);
 int grow(rsx_ctx* c, void** p, size_t* have, size_t need, const char* what);
 int set_error(rsx_ctx* c, int code, const char* msg);
+// RAII timer: records a start event at construction and a stop event at destruction
+// on stream s when the context profiler is on.
+struct ProfScope {
+  rsx_ctx* c;
+  int id;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr, b = nullptr;
+  ProfScope(rsx_ctx* c_, int id_, cudaStream_t s_);
+  ~ProfScope();
+};
 template <typename R>
 int solve_pairs(rsx_ctx* c, const PairMap<R>& pm, int q0, int nq, int p0, int np, R* out, cudaStream_t s);
 }  // namespace rsx

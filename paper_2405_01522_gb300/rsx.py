@@ -34,6 +34,11 @@ SIGNATURES = {
     "rsx_casida_Kd": [_P, _P, _I, _P, _I, _P, _P],
     "rsx_casida_solve": [_P, _P, _I, _P, _I, _P, _P, _D, _I, _P, _P, _P],
     "rsx_sync_status": [_P, _P],
+    "rsx_profile_enable": [_P, _I],
+    "rsx_profile_reset": [_P],
+    "rsx_profile_read": [_P, _I, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_longlong)],
+    "rsx_kernel_count": [],
+    "rsx_kernel_name": [_I],
 }
 
 _lib = None
@@ -55,7 +60,7 @@ def load(path=LIB_PATH):
         for name, args in SIGNATURES.items():
             f = getattr(lib, name)
             f.argtypes = args
-            f.restype = ctypes.c_char_p if name == "rsx_last_error" else ctypes.c_int
+            f.restype = ctypes.c_char_p if name in ("rsx_last_error", "rsx_kernel_name") else ctypes.c_int
         _lib = lib
     return _lib
 
@@ -167,6 +172,22 @@ class Context:
                                               _ptr(Kd), float(delta_M), int(nroots), _ptr(omega), _ptr(X),
                                               _stream(stream)))
         return (omega, X) if vectors else omega
+
+    def profile(self, on=True):
+        self._check(self.lib.rsx_profile_enable(self.handle, 1 if on else 0))
+
+    def profile_reset(self):
+        self._check(self.lib.rsx_profile_reset(self.handle))
+
+    def profile_read(self):
+        """{kernel name: (total ms, launches)} for every kernel launched since the last reset."""
+        out = {}
+        for k in range(self.lib.rsx_kernel_count()):
+            ms, n = ctypes.c_double(), ctypes.c_longlong()
+            self._check(self.lib.rsx_profile_read(self.handle, k, ctypes.byref(ms), ctypes.byref(n)))
+            if n.value:
+                out[self.lib.rsx_kernel_name(k).decode()] = (ms.value, n.value)
+        return out
 
     def sync(self, stream=None):
         self._check(self.lib.rsx_sync_status(self.handle, _stream(stream)))

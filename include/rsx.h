@@ -84,6 +84,23 @@ int rsx_build_pair_densities(rsx_ctx* ctx, const void* a, int na, const void* b,
 int rsx_exchange_apply(rsx_ctx* ctx, const void* phi, int nocc, const void* psi, int npsi, void* out,
                        void* stream);
 
+/* Allocation-free variant of rsx_exchange_apply (the paper has no counterpart; this is
+ * a deployment aid).  For callers that must not allocate device memory once running --
+ * e.g. a program whose device memory is owned by its own pool allocator sized at
+ * start-up, or a latency-sensitive loop that cannot take cudaFree's implicit device
+ * synchronisation when a workspace is regrown.  Create the context at start-up; this
+ * call then performs no cudaMalloc/cudaFree and calls no allocating routine.
+ * Same result as rsx_exchange_apply (same kernels, one output orbital at a time).
+ * Scratch: a fixed 64 MiB device array inside the library, held by every GPU that loads
+ * it until process exit; requires nocc * (nx + 1) * nz * ny * 2 * element size <= 64 MiB
+ * (else RSX_EINVAL, nothing launched) and a box whose y/z pass fits in shared memory
+ * (FP32 edges <= 112, FP64 <= 64; else RSX_EUNSUPPORTED).  The first call on a device
+ * looks up the array's address (cudaGetSymbolAddress) -- make it before any stream
+ * capture.  All calls share the array and it keeps the last call's contents (nothing in
+ * it needs to start at zero); calls that overlap on the GPU race and must be serialised. */
+int rsx_exchange_apply_noalloc(rsx_ctx* ctx, const void* phi, int nocc, const void* psi, int npsi, void* out,
+                               void* stream);
+
 /* ACE projectors of Eqs. 11-12 from the orbitals phi (nocc <= 64):
  * W = Vx[phi] phi (nocc (nocc + 1) / 2 solves, rho_ij = rho_ji), M_kl = <phi_k, W_l>
  * symmetrised (FP64), -M = L L^T by FP64 Cholesky on the device, xi = L^-1 W.

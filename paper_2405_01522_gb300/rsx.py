@@ -28,6 +28,7 @@ SIGNATURES = {
     "rsx_set_workspace_limit": [_P, ctypes.c_size_t],
     "rsx_build_pair_densities": [_P, _P, _I, _P, _I, _P, _P],
     "rsx_exchange_apply": [_P, _P, _I, _P, _I, _P, _P],
+    "rsx_exchange_apply_noalloc": [_P, _P, _I, _P, _I, _P, _P],
     "rsx_ace_build": [_P, _P, _I, _P, _P, _P],
     "rsx_ace_apply": [_P, _P, _I, _P, _I, _P, _P],
     "rsx_casida_K": [_P, _P, _I, _P, _I, _P, _P],
@@ -132,6 +133,13 @@ class Context:
         out = self._new(npsi) if out is None else out
         self._check(self.lib.rsx_exchange_apply(self.handle, _ptr(phi), nocc, _ptr(psi), npsi, _ptr(out),
                                                 _stream(stream)))
+        return out
+
+    def exchange_apply_noalloc(self, phi, psi, out, stream=None):
+        """Same as exchange_apply, but the library allocates nothing (fixed 64 MiB scratch)."""
+        nocc, npsi = self._orb(phi, "phi"), self._orb(psi, "psi")
+        self._check(self.lib.rsx_exchange_apply_noalloc(self.handle, _ptr(phi), nocc, _ptr(psi), npsi, _ptr(out),
+                                                        _stream(stream)))
         return out
 
     def ace_build(self, phi, xi=None, M=None, stream=None):

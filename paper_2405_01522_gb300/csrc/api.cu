@@ -2,6 +2,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -342,6 +343,8 @@ int rsx_create(rsx_ctx** out, int nz, int ny, int nx, double h, int precision, i
   g.Mz = 2 * nz; g.My = 2 * ny; g.Mx = 2 * nx;
   g.Az = g.Mz / 16; g.Ay = g.My / 16; g.Ax = g.Mx / 16;
   g.Hx = g.Mx / 2 + 1;
+  g.p2_threads = 256;
+  if (const char* e = getenv("RSX_PASS2_THREADS")) g.p2_threads = atoi(e) == 512 ? 512 : 256;
   cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, device);
   size_t freeb = 0, totalb = 0;
   cudaMemGetInfo(&freeb, &totalb);

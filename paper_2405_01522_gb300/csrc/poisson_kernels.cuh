@@ -133,30 +133,26 @@ __global__ void __launch_bounds__(kThreads) k_pass1(Geom g, PairMap<R> pm, int q
 // Row loops step over pairs of rows per warp so that both half-warps of a warp run
 // the same number of iterations (their __syncwarp calls must match).
 
-template <typename R>
+template <int NT, typename R>
 __device__ __forceinline__ void load_plane(Cx<R>* D, int DP, const Cx<R>* P, int nz, int ny) {
-  const int nplane = nz * ny;
-  for (int e = threadIdx.x; e < nplane; e += kThreads) {
-    const int z = e / ny, y = e - z * ny;
-    D[z * DP + y] = P[e];
-  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int z = warp; z < nz; z += NT / 32)
+    for (int y = lane; y < ny; y += 32) D[z * DP + y] = P[z * ny + y];
 }
 
-template <typename R>
+template <int NT, typename R>
 __device__ __forceinline__ void store_plane(const Cx<R>* D, int DP, Cx<R>* P, int nz, int ny) {
-  const int nplane = nz * ny;
-  for (int e = threadIdx.x; e < nplane; e += kThreads) {
-    const int z = e / ny, y = e - z * ny;
-    P[e] = D[z * DP + y];
-  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int z = warp; z < nz; z += NT / 32)
+    for (int y = lane; y < ny; y += 32) P[z * ny + y] = D[z * DP + y];
 }
 
 // forward y transform of rows z < nz (input y < ny, output all My)
-template <typename R, int AY>
+template <typename R, int AY, int NT>
 __device__ __forceinline__ void y_forward(Cx<R>* D, int DP, int nz, int ny, const Cx<R>* __restrict__ twy,
                                           Cx<R>* sc) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, t = lane & 15;
-  for (int z0 = 2 * warp; z0 < nz; z0 += kLinesPerCta) {
+  for (int z0 = 2 * warp; z0 < nz; z0 += NT / 16) {
     const int z = z0 + (lane >> 4);
     const bool ok = z < nz;
     Cx<R> v[AY];
@@ -182,11 +178,11 @@ __device__ __forceinline__ void y_forward(Cx<R>* D, int DP, int nz, int ny, cons
 }
 
 // inverse y transform of rows z < nz (input all My, output y < ny)
-template <typename R, int AY>
+template <typename R, int AY, int NT>
 __device__ __forceinline__ void y_inverse(Cx<R>* D, int DP, int nz, int ny, const Cx<R>* __restrict__ twy,
                                           Cx<R>* sc) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, t = lane & 15;
-  for (int z0 = 2 * warp; z0 < nz; z0 += kLinesPerCta) {
+  for (int z0 = 2 * warp; z0 < nz; z0 += NT / 16) {
     const int z = z0 + (lane >> 4);
     const bool ok = z < nz;
     Cx<R> v[AY];
@@ -214,8 +210,8 @@ __device__ __forceinline__ void y_inverse(Cx<R>* D, int DP, int nz, int ny, cons
 // pass 2: per (pair, kx) plane: y forward, z forward * vhat * z inverse, y inverse.
 // D lives in shared memory (DSMEM) or, when it does not fit, in a per-CTA slice of
 // global scratch.  Persistent grid over the work items (pair, kx).
-template <typename R, int AY, int AZ, bool DSMEM>
-__global__ void __launch_bounds__(kThreads) k_pass2(Geom g, int nq, Cx<R>* __restrict__ inter,
+template <typename R, int AY, int AZ, bool DSMEM, int NT>
+__global__ void __launch_bounds__(NT, 1) k_pass2(Geom g, int nq, Cx<R>* __restrict__ inter,
                                                     const Cx<R>* __restrict__ twy,
                                                     const Cx<R>* __restrict__ twz,
                                                     const R* __restrict__ vhat, R* gscratch) {
@@ -226,7 +222,7 @@ __global__ void __launch_bounds__(kThreads) k_pass2(Geom g, int nq, Cx<R>* __res
   constexpr int DP = LY + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Cx<R>* scr = reinterpret_cast<Cx<R>*>(smem_raw);
-  Cx<R>* D = DSMEM ? scr + kLinesPerCta * SP
+  Cx<R>* D = DSMEM ? scr + (NT / 16) * SP
                    : reinterpret_cast<Cx<R>*>(gscratch) + (size_t)blockIdx.x * g.nz * DP;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -239,13 +235,13 @@ __global__ void __launch_bounds__(kThreads) k_pass2(Geom g, int nq, Cx<R>* __res
   for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
     const int ql = w / g.Hx, kx = w - ql * g.Hx;
     Cx<R>* P = inter + (size_t)ql * g.inter_elems() + (size_t)kx * nplane;
-    load_plane(D, DP, P, g.nz, g.ny);
+    load_plane<NT>(D, DP, P, g.nz, g.ny);
     __syncthreads();
-    y_forward<R, AY>(D, DP, g.nz, g.ny, twy, sc);
+    y_forward<R, AY, NT>(D, DP, g.nz, g.ny, twy, sc);
     __syncthreads();
     // z forward, multiply, z inverse on columns ky (LY is a multiple of 16: uniform trips)
     const R* vrow = vhat + (size_t)kx * Hy * Hz;
-    for (int ky = line; ky < LY; ky += kLinesPerCta) {
+    for (int ky = line; ky < LY; ky += NT / 16) {
       const int iy = ky <= LY / 2 ? ky : LY - ky;
       const R* vcol = vrow + (size_t)iy * Hz;
       Cx<R> v[AZ];
@@ -288,9 +284,9 @@ __global__ void __launch_bounds__(kThreads) k_pass2(Geom g, int nq, Cx<R>* __res
       __syncwarp();
     }
     __syncthreads();
-    y_inverse<R, AY>(D, DP, g.nz, g.ny, twy, sc);
+    y_inverse<R, AY, NT>(D, DP, g.nz, g.ny, twy, sc);
     __syncthreads();
-    store_plane(D, DP, P, g.nz, g.ny);
+    store_plane<NT>(D, DP, P, g.nz, g.ny);
     __syncthreads();
   }
 }
@@ -324,9 +320,9 @@ __global__ void __launch_bounds__(kThreads) k_spectrum(Geom g, int nq, const Cx<
   for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
     const int ql = w / g.Hx, kx = w - ql * g.Hx;
     const Cx<float>* P = inter + (size_t)ql * g.inter_elems() + (size_t)kx * nplane;
-    load_plane(D, DP, P, g.nz, g.ny);
+    load_plane<kThreads>(D, DP, P, g.nz, g.ny);
     __syncthreads();
-    y_forward<float, AY>(D, DP, g.nz, g.ny, twy, sc);
+    y_forward<float, AY, kThreads>(D, DP, g.nz, g.ny, twy, sc);
     __syncthreads();
     const float wk = (kx == 0 || 2 * kx == g.Mx) ? 1.0f : 2.0f;
     const float* vrow = vhat + (size_t)kx * Hy * Hz;

@@ -24,16 +24,6 @@ template <typename R>
 inline size_t pass3_smem(int AX, int nx) {
   return pass1_smem<R>(AX) + sizeof(R) * (size_t)kRowsPerCta * nx;
 }
-template <typename R>
-inline size_t pass2_scratch_smem(int AY, int AZ) {
-  const int A = AY > AZ ? AY : AZ;
-  return sizeof(Cx<R>) * (size_t)kLinesPerCta * A * kScrPitch;
-}
-template <typename R>
-inline size_t pass2_plane_bytes(const Geom& g) {
-  return sizeof(Cx<R>) * (size_t)g.nz * (g.My + 1);
-}
-
 inline int max_dyn_smem() {
   int dev = 0, v = 0;
   cudaGetDevice(&dev);
@@ -41,9 +31,31 @@ inline int max_dyn_smem() {
   return v;
 }
 
+// threads per CTA of pass 2: 512 (32 lines in flight) when its scratch and plane fit
+// (g.p2_threads: 0 = default 256; 512 is used only when its scratch and plane fit)
+template <typename R>
+inline int pass2_threads(const Geom& g) {
+  if (g.p2_threads != 512) return 256;
+  const int A = g.Ay > g.Az ? g.Ay : g.Az;
+  const size_t sc512 = sizeof(Cx<R>) * (size_t)32 * A * kScrPitch;
+  const size_t pl = sizeof(Cx<R>) * (size_t)g.nz * (g.My + 1);
+  return (sc512 + pl <= (size_t)max_dyn_smem()) ? 512 : 256;
+}
+template <typename R>
+inline size_t pass2_scratch_smem(int AY, int AZ, int nt = kThreads) {
+  const int A = AY > AZ ? AY : AZ;
+  return sizeof(Cx<R>) * (size_t)(nt / 16) * A * kScrPitch;
+}
+template <typename R>
+inline size_t pass2_plane_bytes(const Geom& g) {
+  return sizeof(Cx<R>) * (size_t)g.nz * (g.My + 1);
+}
+
+
+
 template <typename R>
 size_t pass2_smem_bytes(const Geom& g, bool* fits) {
-  const size_t sc = pass2_scratch_smem<R>(g.Ay, g.Az);
+  const size_t sc = pass2_scratch_smem<R>(g.Ay, g.Az, pass2_threads<R>(g));
   const size_t pl = pass2_plane_bytes<R>(g);
   const bool f = sc + pl <= (size_t)max_dyn_smem();
   if (fits) *fits = f;
@@ -58,9 +70,10 @@ int pass2_occupancy(const Geom& g) {
   switch (g.Ay) {
 #define RSX_CASE(a)                                                                                  \
   case a: {                                                                                          \
-    auto k = k_pass2<R, a, a, true>;                                                                 \
+    const int nt = pass2_threads<R>(g);                                                              \
+    auto k = nt == 512 ? k_pass2<R, a, a, true, 512> : k_pass2<R, a, a, true, 256>;                  \
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess || \
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kThreads, smem) != cudaSuccess) {     \
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, nt, smem) != cudaSuccess) {            \
       cudaGetLastError();                                                                            \
       nb = 1;                                                                                        \
     }                                                                                                \
@@ -85,12 +98,13 @@ cudaError_t launch_pass2(const Geom& g, int nq, Cx<R>* inter, const Cx<R>* twy, 
 #define RSX_CASE(a)                                                                                  \
   case a: {                                                                                          \
     if (fits) {                                                                                      \
-      auto k = k_pass2<R, a, a, true>;                                                               \
+      const int nt = pass2_threads<R>(g);                                                            \
+      auto k = nt == 512 ? k_pass2<R, a, a, true, 512> : k_pass2<R, a, a, true, 256>;                \
       cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
       if (e != cudaSuccess) return e;                                                                \
-      k<<<grid, kThreads, smem, s>>>(g, nq, inter, twy, twz, vhat, gscratch);                        \
+      k<<<grid, nt, smem, s>>>(g, nq, inter, twy, twz, vhat, gscratch);                              \
     } else {                                                                                         \
-      auto k = k_pass2<R, a, a, false>;                                                              \
+      auto k = k_pass2<R, a, a, false, 256>;                                                         \
       cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
       if (e != cudaSuccess) return e;                                                                \
       k<<<grid, kThreads, smem, s>>>(g, nq, inter, twy, twz, vhat, gscratch);                        \

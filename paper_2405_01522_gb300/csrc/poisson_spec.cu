@@ -8,7 +8,7 @@ cudaError_t launch_spectrum_f32(const Geom& g, int nq, const Cx<float>* inter, c
                                 uint16_t* lo, size_t ld, cudaStream_t s) {
   if (nq <= 0) return cudaSuccess;
   if (g.Ay != g.Az) return cudaErrorInvalidValue;
-  const size_t smem = pass2_scratch_smem<float>(g.Ay, g.Az) + pass2_plane_bytes<float>(g);
+  const size_t smem = pass2_scratch_smem<float>(g.Ay, g.Az, kThreads) + pass2_plane_bytes<float>(g);
   if (smem > (size_t)max_dyn_smem()) return cudaErrorInvalidValue;
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);

@@ -138,6 +138,13 @@ int rsx_casida_solve(rsx_ctx* ctx, const double* eps_occ, int nocc, const double
                      const double* K, const double* Kd, double delta_M, int nroots, double* omega, double* X,
                      void* stream);
 
+/* Split-BF16 symmetric contraction on the tensor cores, the K contraction of
+ * rsx_casida_K as a standalone building block: C = H H^T + H L^T + L H^T, i.e. S S^T for a
+ * panel S = H + L split into bf16 high and low parts (FP32 accumulation, FP64 split-K
+ * reduction; C symmetric).  hi, lo: device bf16 [n][ld] row-major, 16-byte aligned,
+ * n % 128 == 0, ld % 64 == 0; C: device double [n][n].  Errors: RSX_EINVAL. */
+int rsx_syrk_bf16x3(rsx_ctx* ctx, const void* hi, const void* lo, int n, long long ld, double* C, void* stream);
+
 /* Launch profiler (tracing).  While enabled, every kernel the context launches is
  * bracketed by CUDA events recorded on the launching stream; rsx_profile_read waits for
  * the pending events and returns, for kernel id `kernel` (0 <= kernel < rsx_kernel_count()),

@@ -178,7 +178,8 @@ namespace rsx {
 // Pair solves for pairs [q0, q0 + nq) of pm, accumulated into outputs [p0, p0 + np).
 // Requires the intermediate workspace to hold nq pairs (grown here).
 template <typename R>
-int solve_pairs(rsx_ctx* c, const PairMap<R>& pm, int q0, int nq, int p0, int np, R* out, cudaStream_t s) {
+int solve_pairs(rsx_ctx* c, const PairMap<R>& pm, int q0, int nq, int p0, int np, R* out, cudaStream_t s,
+                int pot) {
   const Geom& g = c->g;
   const size_t need = (size_t)nq * g.inter_elems() * sizeof(Cx<R>);
   int rc = grow(c, &c->work, &c->work_bytes, need, "FFT intermediates");
@@ -214,7 +215,7 @@ int solve_pairs(rsx_ctx* c, const PairMap<R>& pm, int q0, int nq, int p0, int np
   if (rc) return rc;
   if (out != nullptr) {
     ProfScope ps(c, kKPass3, s);
-    rc = check_cuda(c, launch_pass3<R>(g, pm, q0, p0, np, inter, twx, out, s), "pass 3");
+    rc = check_cuda(c, launch_pass3<R>(g, pm, q0, p0, np, pot, inter, twx, out, s), "pass 3");
   }
   return rc;
 }
@@ -315,8 +316,8 @@ int ace_apply(rsx_ctx* c, const void* xi, int nxi, const void* psi, int npsi, vo
   return check_cuda(c, launch_combine<R>(cm, npsi, nxi, (const R*)xi, N, (R*)out, 4 * c->nsm, s), "ace apply");
 }
 
-template int solve_pairs<float>(rsx_ctx*, const PairMap<float>&, int, int, int, int, float*, cudaStream_t);
-template int solve_pairs<double>(rsx_ctx*, const PairMap<double>&, int, int, int, int, double*, cudaStream_t);
+template int solve_pairs<float>(rsx_ctx*, const PairMap<float>&, int, int, int, int, float*, cudaStream_t, int);
+template int solve_pairs<double>(rsx_ctx*, const PairMap<double>&, int, int, int, int, double*, cudaStream_t, int);
 
 }  // namespace rsx
 
@@ -370,7 +371,7 @@ int rsx_destroy(rsx_ctx* c) {
   prof_collect(c);
   for (cudaEvent_t e : c->prof_pool) cudaEventDestroy(e);
   void* bufs[] = {c->vhat, c->tw[0], c->tw[1], c->tw[2], c->work, c->gscr, c->dsm, c->smallr, c->status,
-                  c->panel_hi, c->panel_lo, c->gemm_part, c->eig_work};
+                  c->panel_hi, c->panel_lo, c->gemm_part, c->eig_work, c->gscr_kd};
   for (void* b : bufs)
     if (b) cudaFree(b);
   delete c;

@@ -35,6 +35,7 @@ struct rsx_ctx {
   void* panel_lo = nullptr; size_t panel_lo_bytes = 0;  // bf16 lo
   void* gemm_part = nullptr; size_t gemm_part_bytes = 0;
   void* eig_work = nullptr; size_t eig_work_bytes = 0;
+  void* gscr_kd = nullptr; size_t gscr_kd_bytes = 0;     // occupied pair potentials (K_d)
   int p2_occ[2] = {0, 0};
   // launch profiler: events recorded around every kernel while enabled
   bool prof_on = false;
@@ -68,6 +69,9 @@ struct ProfScope {
   ProfScope(rsx_ctx* c_, int id_, cudaStream_t s_);
   ~ProfScope();
 };
+// pot = 0: out_p accumulates -partner * V over p's pairs (exchange);
+// pot = 1: out_p is the potential of pair q0 + (p - p0) itself.
 template <typename R>
-int solve_pairs(rsx_ctx* c, const PairMap<R>& pm, int q0, int nq, int p0, int np, R* out, cudaStream_t s);
+int solve_pairs(rsx_ctx* c, const PairMap<R>& pm, int q0, int nq, int p0, int np, R* out, cudaStream_t s,
+                int pot = 0);
 }  // namespace rsx

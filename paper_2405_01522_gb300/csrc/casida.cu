@@ -1,25 +1,277 @@
-// Tamm-Dancoff Casida calls of the C ABI (work in progress: not yet available).
+// Tamm-Dancoff Casida calls of the C ABI (Sec. 2, Eqs. 6-7).
+//
+// rsx_casida_K   K_{ia,jb} = (ia|jb) for transitions t = i * nvirt + a.
+//   FP32 context: pair densities rho_t -> x forward (pass 1) -> y, z forward with the
+//   weights sqrt(w_G ghat h^6 / N_pad) -> bf16 hi/lo panel S [t][G] -> tcgen05
+//   K = S S^T in three split products (gemm_tcgen05.cu).
+//   FP64 context (plain form): V_t for every transition (full pair solves), then
+//   K = h^3 rho^T V in FP64 (Gram blocks of 64 x 64).
+// rsx_casida_Kd  K_d[ia,jb] = (ab|ji) = h^3 sum_r phi_a phi_b V_ij, V_ij for the
+//   unordered occupied pairs (i, j); symmetric in (i, j), so each block fills two places.
+// rsx_casida_solve  FP64 eigen-solve of A = diag(de) + delta_M K - K_d (eig.cu).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
 #include "../../include/rsx.h"
 #include "api_internal.cuh"
+#include "dense.cuh"
+#include "eig.cuh"
+#include "gemm_tcgen05.cuh"
 
 using namespace rsx;
 
+namespace {
+
+__global__ void k_symmetrise(double* K, int n) {
+  const long long total = (long long)n * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int t = (int)(e / n), s = (int)(e - (long long)t * n);
+    if (t < s) {
+      const long long et = (long long)s * n + t;
+      const double v = 0.5 * (K[e] + K[et]);
+      K[e] = v;
+      K[et] = v;
+    }
+  }
+}
+
+template <typename R>
+PairMap<R> prod_map(const void* A, int na, const void* B, int nb, size_t N) {
+  PairMap<R> pm;
+  pm.mode = kProd;
+  pm.A = (const R*)A;
+  pm.B = (const R*)B;
+  pm.na = na;
+  pm.nb = nb;
+  pm.N = N;
+  return pm;
+}
+
+template <typename R>
+PairMap<R> sym_map(const void* A, int na, size_t N) {
+  PairMap<R> pm;
+  pm.mode = kSym;
+  pm.A = (const R*)A;
+  pm.B = nullptr;
+  pm.na = na;
+  pm.nb = 0;
+  pm.N = N;
+  return pm;
+}
+
+// K as the Gram matrix h^3 X Y^T of two [n][N] sets, 64 x 64 blocks, row stride n
+template <typename R>
+int gram_blocks(rsx_ctx* c, const R* X, const R* Y, int n, size_t N, double scale, double* K, const R* w,
+                int ldo, cudaStream_t s) {
+  const int nblk = 2 * c->nsm;
+  int rc = grow(c, (void**)&c->dsm, &c->dsm_bytes, sizeof(double) * ((size_t)nblk * 4096 + 3 * 4096), "small FP64");
+  if (rc) return rc;
+  for (int b0 = 0; b0 < n; b0 += 64) {
+    const int na = std::min(64, n - b0);
+    for (int b1 = 0; b1 < n; b1 += 64) {
+      const int nb = std::min(64, n - b1);
+      {
+        ProfScope ps(c, kKGram, s);
+        rc = check_cuda(c, launch_gram<R>(X + (size_t)b0 * N, na, Y + (size_t)b1 * N, nb, N, c->dsm, nblk, s, w),
+                        "gram block");
+      }
+      if (rc) return rc;
+      ProfScope ps(c, kKGramReduce, s);
+      rc = check_cuda(c,
+                      launch_gram_reduce<R>(c->dsm, nblk, na, nb, scale, false, K + (size_t)b0 * ldo + b1,
+                                            (R*)nullptr, s, ldo),
+                      "gram block reduce");
+      if (rc) return rc;
+    }
+  }
+  return RSX_OK;
+}
+
+int casida_K_f32(rsx_ctx* c, const void* po, int no, const void* pv, int nv, double* K, cudaStream_t s) {
+  const Geom& g = c->g;
+  const size_t N = g.N();
+  const int nt = no * nv;
+  const PairMap<float> pm = prod_map<float>(pv, nv, po, no, N);  // q = i * nv + a
+  const size_t inter_bytes = (size_t)nt * g.inter_elems() * sizeof(Cx<float>);
+  const long long ng = 2LL * g.Hx * g.My * g.Mz;
+  const long long ld = (ng + 63) / 64 * 64;
+  const int nt_pad = (nt + 127) / 128 * 128;
+  const size_t panel_bytes = (size_t)nt_pad * ld * sizeof(uint16_t);
+  if (inter_bytes + 2 * panel_bytes > c->work_limit)
+    return set_error(c, RSX_ENOMEM, "casida_K: intermediates and panels exceed the workspace limit");
+  int rc = grow(c, &c->work, &c->work_bytes, inter_bytes, "FFT intermediates");
+  if (rc) return rc;
+  rc = grow(c, &c->panel_hi, &c->panel_hi_bytes, panel_bytes, "K panel (hi)");
+  if (rc) return rc;
+  rc = grow(c, &c->panel_lo, &c->panel_lo_bytes, panel_bytes, "K panel (lo)");
+  if (rc) return rc;
+  uint16_t* hi = (uint16_t*)c->panel_hi;
+  uint16_t* lo = (uint16_t*)c->panel_lo;
+  // zero what the spectrum kernel does not write: columns [ng, ld) and rows [nt, nt_pad)
+  if (ld > ng) {
+    rc = check_cuda(c, cudaMemset2DAsync(hi + ng, ld * 2, 0, (ld - ng) * 2, nt, s), "panel tail");
+    if (!rc) rc = check_cuda(c, cudaMemset2DAsync(lo + ng, ld * 2, 0, (ld - ng) * 2, nt, s), "panel tail");
+    if (rc) return rc;
+  }
+  if (nt_pad > nt) {
+    rc = check_cuda(c, cudaMemsetAsync(hi + (size_t)nt * ld, 0, (size_t)(nt_pad - nt) * ld * 2, s), "panel pad");
+    if (!rc) rc = check_cuda(c, cudaMemsetAsync(lo + (size_t)nt * ld, 0, (size_t)(nt_pad - nt) * ld * 2, s), "panel pad");
+    if (rc) return rc;
+  }
+  Cx<float>* inter = (Cx<float>*)c->work;
+  {
+    ProfScope ps(c, kKPass1, s);
+    rc = check_cuda(c, launch_pass1<float>(g, pm, 0, nt, inter, (const Cx<float>*)c->tw[2], s), "pass 1");
+  }
+  if (rc) return rc;
+  const float h3 = (float)(c->h * c->h * c->h);
+  {
+    ProfScope ps(c, kKSpectrum, s);
+    rc = check_cuda(c,
+                    launch_spectrum_f32(g, nt, inter, (const Cx<float>*)c->tw[1], (const Cx<float>*)c->tw[0],
+                                        (const float*)c->vhat, h3, hi, lo, (size_t)ld, s),
+                    "spectrum panel");
+  }
+  if (rc) return rc;
+  const int nsplit = syrk_splits(c->nsm, nt);
+  rc = grow(c, &c->gemm_part, &c->gemm_part_bytes, syrk_partial_bytes(nt, nsplit), "K split partials");
+  if (rc) return rc;
+  return syrk_bf16x3(c, hi, lo, nt, ld, nsplit, (float*)c->gemm_part, K, s);
+}
+
+template <typename R>
+int casida_K_plain(rsx_ctx* c, const void* po, int no, const void* pv, int nv, double* K, cudaStream_t s) {
+  const Geom& g = c->g;
+  const size_t N = g.N();
+  const int nt = no * nv;
+  const PairMap<R> pm = prod_map<R>(pv, nv, po, no, N);
+  const size_t need = (size_t)nt * g.inter_elems() * sizeof(Cx<R>) + 2 * (size_t)nt * N * sizeof(R);
+  if (need > c->work_limit) return set_error(c, RSX_ENOMEM, "casida_K: workspace limit exceeded");
+  int rc = grow(c, &c->panel_hi, &c->panel_hi_bytes, 2 * (size_t)nt * N * sizeof(R), "potentials and densities");
+  if (rc) return rc;
+  R* V = (R*)c->panel_hi;
+  R* rho = V + (size_t)nt * N;
+  rc = solve_pairs<R>(c, pm, 0, nt, 0, nt, V, s, 1);
+  if (rc) return rc;
+  {
+    ProfScope ps(c, kKPairProd, s);
+    rc = check_cuda(c, launch_pair_products<R>((const R*)po, no, (const R*)pv, nv, N, rho, s), "densities");
+  }
+  if (rc) return rc;
+  rc = gram_blocks<R>(c, rho, V, nt, N, c->h * c->h * c->h, K, (const R*)nullptr, nt, s);
+  if (rc) return rc;
+  k_symmetrise<<<256, 256, 0, s>>>(K, nt);
+  return check_cuda(c, cudaGetLastError(), "symmetrise");
+}
+
+template <typename R>
+int casida_Kd(rsx_ctx* c, const void* po, int no, const void* pv, int nv, double* Kd, cudaStream_t s) {
+  const Geom& g = c->g;
+  const size_t N = g.N();
+  const int nt = no * nv;
+  const int npairs = no * (no + 1) / 2;
+  const PairMap<R> pm = sym_map<R>(po, no, N);
+  const size_t need = (size_t)npairs * g.inter_elems() * sizeof(Cx<R>) + (size_t)npairs * N * sizeof(R);
+  if (need > c->work_limit) return set_error(c, RSX_ENOMEM, "casida_Kd: workspace limit exceeded");
+  int rc = grow(c, &c->gscr_kd, &c->gscr_kd_bytes, (size_t)npairs * N * sizeof(R), "occupied pair potentials");
+  if (rc) return rc;
+  R* V = (R*)c->gscr_kd;
+  rc = solve_pairs<R>(c, pm, 0, npairs, 0, npairs, V, s, 1);
+  if (rc) return rc;
+  const double h3 = c->h * c->h * c->h;
+  int q = 0;
+  for (int i = 0; i < no; ++i)
+    for (int j = i; j < no; ++j, ++q) {
+      const R* w = V + (size_t)q * N;
+      rc = gram_blocks<R>(c, (const R*)pv, (const R*)pv, nv, N, h3, Kd + (size_t)i * nv * nt + (size_t)j * nv, w, nt,
+                          s);
+      if (rc) return rc;
+      if (j != i) {
+        rc = check_cuda(c,
+                        cudaMemcpy2DAsync(Kd + (size_t)j * nv * nt + (size_t)i * nv, nt * sizeof(double),
+                                          Kd + (size_t)i * nv * nt + (size_t)j * nv, nt * sizeof(double),
+                                          nv * sizeof(double), nv, cudaMemcpyDeviceToDevice, s),
+                        "Kd mirror");
+        if (rc) return rc;
+      }
+    }
+  return RSX_OK;
+}
+
+bool overlap(const void* a, size_t na, const void* b, size_t nb) {
+  const char* pa = (const char*)a;
+  const char* pb = (const char*)b;
+  return pa < pb + nb && pb < pa + na;
+}
+
+int check_casida_args(rsx_ctx* c, const void* po, int no, const void* pv, int nv, const double* K) {
+  if (!po || !pv || !K || no < 1 || nv < 1 || no * nv > 4096)
+    return set_error(c, RSX_EINVAL, "casida: bad arguments (need nocc, nvirt >= 1, nocc * nvirt <= 4096)");
+  const size_t N = c->g.N(), es = c->elem_size(), nt = (size_t)no * nv;
+  if (overlap(K, nt * nt * 8, po, no * N * es) || overlap(K, nt * nt * 8, pv, nv * N * es))
+    return set_error(c, RSX_EINVAL, "casida: output aliases an input");
+  return RSX_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
-int rsx_casida_K(rsx_ctx* c, const void*, int, const void*, int, double*, void*) {
-  if (!c) return RSX_EINVAL;
-  return set_error(c, RSX_EUNSUPPORTED, "casida_K not available in this build");
+#define RSX_PREP_C(c)                                            \
+  if (!(c)) return RSX_EINVAL;                                   \
+  (c)->err[0] = 0;                                               \
+  if (cudaSetDevice((c)->device) != cudaSuccess) {               \
+    cudaGetLastError();                                          \
+    return set_error((c), RSX_ECUDA, "cudaSetDevice failed");    \
+  }
+
+int rsx_casida_K(rsx_ctx* c, const void* phi_occ, int nocc, const void* phi_virt, int nvirt, double* K,
+                 void* stream) {
+  RSX_PREP_C(c);
+  int rc = check_casida_args(c, phi_occ, nocc, phi_virt, nvirt, K);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (c->precision == RSX_FP32) {
+    if (c->g.Ay != c->g.Az) return set_error(c, RSX_EUNSUPPORTED, "casida_K: ny must equal nz");
+    return casida_K_f32(c, phi_occ, nocc, phi_virt, nvirt, K, s);
+  }
+  return casida_K_plain<double>(c, phi_occ, nocc, phi_virt, nvirt, K, s);
 }
 
-int rsx_casida_Kd(rsx_ctx* c, const void*, int, const void*, int, double*, void*) {
-  if (!c) return RSX_EINVAL;
-  return set_error(c, RSX_EUNSUPPORTED, "casida_Kd not available in this build");
+int rsx_casida_Kd(rsx_ctx* c, const void* phi_occ, int nocc, const void* phi_virt, int nvirt, double* Kd,
+                  void* stream) {
+  RSX_PREP_C(c);
+  int rc = check_casida_args(c, phi_occ, nocc, phi_virt, nvirt, Kd);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  return c->precision == RSX_FP32 ? casida_Kd<float>(c, phi_occ, nocc, phi_virt, nvirt, Kd, s)
+                                  : casida_Kd<double>(c, phi_occ, nocc, phi_virt, nvirt, Kd, s);
 }
 
-int rsx_casida_solve(rsx_ctx* c, const double*, int, const double*, int, const double*, const double*, double,
-                     int, double*, double*, void*) {
-  if (!c) return RSX_EINVAL;
-  return set_error(c, RSX_EUNSUPPORTED, "casida_solve not available in this build");
+int rsx_casida_solve(rsx_ctx* c, const double* eps_occ, int nocc, const double* eps_virt, int nvirt, const double* K,
+                     const double* Kd, double delta_M, int nroots, double* omega, double* X, void* stream) {
+  RSX_PREP_C(c);
+  const int nt = nocc * nvirt;
+  if (!eps_occ || !eps_virt || !K || !omega || nocc < 1 || nvirt < 1 || nt > 4096 || nroots < 1 || nroots > nt)
+    return set_error(c, RSX_EINVAL, "casida_solve: bad arguments");
+  int rc = grow(c, &c->eig_work, &c->eig_work_bytes, tda_work_doubles(nt, nroots) * sizeof(double), "eigensolver");
+  if (rc) return rc;
+  return tda_solve(c, eps_occ, nocc, eps_virt, nvirt, K, Kd, delta_M, nroots, omega, X, (double*)c->eig_work,
+                   (cudaStream_t)stream);
+}
+
+// C = H H^T + H L^T + L H^T for bf16 panels H, L: [n][ld] (n % 128 == 0, ld % 64 == 0)
+int rsx_syrk_bf16x3(rsx_ctx* c, const void* hi, const void* lo, int n, long long ld, double* C, void* stream) {
+  RSX_PREP_C(c);
+  if (!hi || !lo || !C || n < 128 || n % 128 || ld < 64 || ld % 64)
+    return set_error(c, RSX_EINVAL, "syrk: need n % 128 == 0 and ld % 64 == 0");
+  const int nsplit = syrk_splits(c->nsm, n);
+  int rc = grow(c, &c->gemm_part, &c->gemm_part_bytes, syrk_partial_bytes(n, nsplit), "split partials");
+  if (rc) return rc;
+  return syrk_bf16x3(c, (const uint16_t*)hi, (const uint16_t*)lo, n, ld, nsplit, (float*)c->gemm_part, C,
+                     (cudaStream_t)stream);
 }
 
 }  // extern "C"

@@ -67,9 +67,11 @@ __global__ void k_scale_cast(const double* __restrict__ in, R* __restrict__ out,
 constexpr int kGramChunk = 128;
 constexpr int kGramThreads = 256;
 
+// (w, when not null, multiplies Y point-wise: sum X_a Y_b w)
 template <typename R>
 __global__ void __launch_bounds__(kGramThreads) k_gram(const R* __restrict__ X, int na, const R* __restrict__ Y,
-                                                       int nb, size_t N, double* __restrict__ part) {
+                                                       int nb, const R* __restrict__ w, size_t N,
+                                                       double* __restrict__ part) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R* xs = reinterpret_cast<R*>(smem_raw);
   R* ys = xs + (size_t)na * (kGramChunk + 1);
@@ -88,7 +90,7 @@ __global__ void __launch_bounds__(kGramThreads) k_gram(const R* __restrict__ X, 
     }
     for (int i = threadIdx.x; i < nb * kGramChunk; i += kGramThreads) {
       const int b = i / kGramChunk, j = i - b * kGramChunk;
-      ys[b * (kGramChunk + 1) + j] = j < len ? Y[(size_t)b * N + r0 + j] : R(0);
+      ys[b * (kGramChunk + 1) + j] = j < len ? (w ? Y[(size_t)b * N + r0 + j] * w[r0 + j] : Y[(size_t)b * N + r0 + j]) : R(0);
     }
     __syncthreads();
 #pragma unroll
@@ -114,16 +116,17 @@ __global__ void __launch_bounds__(kGramThreads) k_gram(const R* __restrict__ X, 
 
 // out[a][b] (or out[b][a] when transpose) = scale * sum_blk part[blk][a][b]; optional
 // R copy with the same layout.
+// (ldo: row stride of out / out_r; 0 means na or nb as implied by transpose)
 template <typename R>
 __global__ void k_gram_reduce(const double* __restrict__ part, int nblk, int na, int nb, double scale,
-                              int transpose, double* __restrict__ out, R* __restrict__ out_r) {
+                              int transpose, double* __restrict__ out, R* __restrict__ out_r, int ldo) {
   const int nout = na * nb;
   for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < nout; o += gridDim.x * blockDim.x) {
     double s = 0.0;
     for (int k = 0; k < nblk; ++k) s += part[(size_t)k * nout + o];
     s *= scale;
     const int a = o / nb, b = o - a * nb;
-    const int d = transpose ? b * na + a : o;
+    const size_t d = transpose ? (size_t)b * (ldo ? ldo : na) + a : (size_t)a * (ldo ? ldo : nb) + b;
     if (out) out[d] = s;
     if (out_r) out_r[d] = (R)s;
   }
@@ -255,20 +258,20 @@ cudaError_t launch_ghat(const Geom& g, double h, double scale, const double* cos
 
 template <typename R>
 cudaError_t launch_gram(const R* X, int na, const R* Y, int nb, size_t N, double* part, int nblk,
-                        cudaStream_t s) {
+                        cudaStream_t s, const R* w) {
   if (na * nb > 16 * kGramThreads) return cudaErrorInvalidValue;
   const size_t smem = sizeof(R) * (size_t)(na + nb) * (kGramChunk + 1);
   cudaError_t e = cudaFuncSetAttribute(k_gram<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_gram<R><<<nblk, kGramThreads, smem, s>>>(X, na, Y, nb, N, part);
+  k_gram<R><<<nblk, kGramThreads, smem, s>>>(X, na, Y, nb, w, N, part);
   return cudaGetLastError();
 }
 
 template <typename R>
 cudaError_t launch_gram_reduce(const double* part, int nblk, int na, int nb, double scale, bool transpose,
-                               double* out, R* out_r, cudaStream_t s) {
+                               double* out, R* out_r, cudaStream_t s, int ldo) {
   k_gram_reduce<R><<<(na * nb + 255) / 256, 256, 0, s>>>(part, nblk, na, nb, scale, transpose ? 1 : 0, out,
-                                                          out_r);
+                                                          out_r, ldo);
   return cudaGetLastError();
 }
 
@@ -298,9 +301,10 @@ cudaError_t launch_pair_products(const R* A, int na, const R* B, int nb, size_t 
 }
 
 #define RSX_INST(R)                                                                                        \
-  template cudaError_t launch_gram<R>(const R*, int, const R*, int, size_t, double*, int, cudaStream_t);  \
+  template cudaError_t launch_gram<R>(const R*, int, const R*, int, size_t, double*, int, cudaStream_t,   \
+                                      const R*);                                                          \
   template cudaError_t launch_gram_reduce<R>(const double*, int, int, int, double, bool, double*, R*,      \
-                                             cudaStream_t);                                               \
+                                             cudaStream_t, int);                                          \
   template cudaError_t launch_combine<R>(const R*, int, int, const R*, size_t, R*, int, cudaStream_t);     \
   template cudaError_t launch_pair_products<R>(const R*, int, const R*, int, size_t, R*, cudaStream_t);
 RSX_INST(float)

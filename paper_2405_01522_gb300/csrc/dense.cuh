@@ -9,12 +9,14 @@ namespace rsx {
 cudaError_t launch_ghat(const Geom& g, double h, double scale, const double* cos_z, const double* cos_y,
                         const double* cos_x, double* buf0, double* buf1, void* table, bool fp64,
                         cudaStream_t s);
+// part[blk][a][b] = partial sums of X_a(r) Y_b(r) w(r) (w may be null); na * nb <= 4096
 template <typename R>
 cudaError_t launch_gram(const R* X, int na, const R* Y, int nb, size_t N, double* part, int nblk,
-                        cudaStream_t s);
+                        cudaStream_t s, const R* w = nullptr);
+// out[a * ldo + b] (or out[b * ldo + a] when transpose) = scale * sum of the partials
 template <typename R>
 cudaError_t launch_gram_reduce(const double* part, int nblk, int na, int nb, double scale, bool transpose,
-                               double* out, R* out_r, cudaStream_t s);
+                               double* out, R* out_r, cudaStream_t s, int ldo = 0);
 cudaError_t launch_chol_linv(double* M, int k, double* Linv, float* linv_f, double* linv_d, int* status,
                              cudaStream_t s);
 template <typename R>

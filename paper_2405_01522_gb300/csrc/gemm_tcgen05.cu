@@ -1,0 +1,364 @@
+// Split-BF16 symmetric contraction on the 5th-generation tensor cores (sm_103a):
+//
+//     C = H H^T + H L^T + L H^T        H, L: [n][ld] bf16 (hi and lo parts of one FP32
+//                                      panel S = H + L, row-major, K contiguous)
+//
+// which is S S^T to ~16 mantissa bits; for the Casida coupling S_t(G) holds the
+// weighted pair spectra and C = K (Eqs. 6-7, K = sum_G w_G ghat(G) Re conj R_t R_s).
+//
+// Tiling: 128 x 128 output tiles of the upper triangle (I <= J), split-K over the
+// K dimension so that tiles x splits ~ one CTA per SM.  Per CTA, a 3-stage ring of
+// 64-wide K blocks (H_I, L_I, H_J, L_J: 4 x 16 KB, 128B-swizzled) is filled by TMA
+// (cp.async.bulk.tensor) from one producer thread; one thread issues tcgen05.mma
+// (kind::f16, bf16 x bf16 -> f32, M = N = 128, K = 16) into a 128-column TMEM
+// accumulator; tcgen05.commit frees each stage.  The four warps then read the
+// accumulator with tcgen05.ld and write an FP32 partial tile; a second kernel sums the
+// split partials in FP64 and mirrors the upper triangle.
+//
+// Every mbarrier wait is bounded: on timeout the kernel raises RSX_ETIMEOUT in the
+// status word, stops issuing, drains what it issued (bounded), frees TMEM and returns.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "../../include/rsx.h"
+#include "api_internal.cuh"
+#include "gemm_tcgen05.cuh"
+
+namespace rsx {
+namespace {
+
+constexpr int kBM = 128, kBN = 128, kBK = 64;
+constexpr int kStages = 3;
+constexpr int kTileBytes = kBM * kBK * 2;           // 16 KB per operand tile
+constexpr int kStageBytes = 4 * kTileBytes;         // H_I, L_I, H_J, L_J
+constexpr int kGemmThreads = 128;
+constexpr int kTmemCols = 128;
+constexpr uint32_t kWaitLimit = 1u << 26;           // try_wait rounds before giving up
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n"
+      " .reg .pred p;\n"
+      " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n"
+      "}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// bounded wait; returns false (and raises the abort flag) on timeout or prior abort
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+  for (uint32_t i = 0; i < kWaitLimit; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 1023u) == 1023u && *abort_flag) return false;
+  }
+  *abort_flag = 1;
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
+      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1)
+      : "memory");
+}
+
+// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row core groups 1024 B apart
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);   // start address (16-byte units)
+  d |= (uint64_t)1 << 16;                      // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;           // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)1 << 46;                      // descriptor version for tcgen05
+  d |= (uint64_t)2 << 61;                      // 128-byte swizzle
+  return d;
+}
+
+// instruction descriptor, kind::f16: D f32, A/B bf16, both K-major, M = 128, N = 128
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kBN >> 3) << 17) |
+                            ((uint32_t)(kBM >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accum) {
+  asm volatile(
+      "{\n"
+      " .reg .pred p;\n"
+      " setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
+      "}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accum)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// upper-triangle tile index -> (I, J), I <= J, row-major over nb blocks
+__device__ __forceinline__ void tile_ij(int tile, int nb, int& I, int& J) {
+  int i = 0, rem = tile;
+  while (rem >= nb - i) {
+    rem -= nb - i;
+    ++i;
+  }
+  I = i;
+  J = i + rem;
+}
+
+__global__ void __launch_bounds__(kGemmThreads, 1)
+    k_syrk_bf16x3(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo, int nb,
+                  int nkb, int nsplit, float* __restrict__ part, int* status) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  // 1024-byte aligned operand ring
+  unsigned char* ring = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  __shared__ __align__(8) uint64_t full_bar[kStages];
+  __shared__ __align__(8) uint64_t empty_bar[kStages];
+  __shared__ __align__(8) uint64_t done_bar;
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ int abort_sh;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tile = blockIdx.x / nsplit;
+  const int split = blockIdx.x - tile * nsplit;
+  int I, J;
+  tile_ij(tile, nb, I, J);
+  const int kb0 = (int)((long long)nkb * split / nsplit);
+  const int kb1 = (int)((long long)nkb * (split + 1) / nsplit);
+
+  if (threadIdx.x == 0) {
+    abort_sh = 0;
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    mbar_init(&done_bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base_sh;
+  volatile int* abort_flag = &abort_sh;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer
+    int issued = 0;
+    for (int kb = kb0; kb < kb1; ++kb) {
+      const int it = kb - kb0;
+      const int s = it % kStages;
+      const uint32_t ph = (uint32_t)((it / kStages) & 1);
+      if (it >= kStages && !mbar_wait(&empty_bar[s], ph ^ 1u, abort_flag)) break;
+      unsigned char* st = ring + (size_t)s * kStageBytes;
+      mbar_arrive_expect_tx(&full_bar[s], kStageBytes);
+      const int k = kb * kBK;
+      tma_load_2d(st + 0 * kTileBytes, &tm_hi, &full_bar[s], k, I * kBM);
+      tma_load_2d(st + 1 * kTileBytes, &tm_lo, &full_bar[s], k, I * kBM);
+      tma_load_2d(st + 2 * kTileBytes, &tm_hi, &full_bar[s], k, J * kBN);
+      tma_load_2d(st + 3 * kTileBytes, &tm_lo, &full_bar[s], k, J * kBN);
+      issued = it + 1;
+    }
+    // drain: every issued stage's copies must have landed before the CTA exits
+    const int first = issued > kStages ? issued - kStages : 0;
+    for (int it = first; it < issued; ++it) {
+      const int s = it % kStages;
+      const uint32_t ph = (uint32_t)((it / kStages) & 1);
+      for (uint32_t i = 0; i < kWaitLimit && !mbar_try_wait(&full_bar[s], ph); ++i) {
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer
+    for (int kb = kb0; kb < kb1; ++kb) {
+      const int it = kb - kb0;
+      const int s = it % kStages;
+      const uint32_t ph = (uint32_t)((it / kStages) & 1);
+      if (!mbar_wait(&full_bar[s], ph, abort_flag)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t base = smem_u32(ring + (size_t)s * kStageBytes);
+      const uint64_t dh_i = sw128_desc(base + 0 * kTileBytes);
+      const uint64_t dl_i = sw128_desc(base + 1 * kTileBytes);
+      const uint64_t dh_j = sw128_desc(base + 2 * kTileBytes);
+      const uint64_t dl_j = sw128_desc(base + 3 * kTileBytes);
+#pragma unroll
+      for (int j = 0; j < kBK / 16; ++j) {
+        const uint64_t adv = (uint64_t)((j * 32) >> 4);   // 16 bf16 = 32 bytes along K
+        mma_bf16(tmem, dh_i + adv, dh_j + adv, (it > 0 || j > 0) ? 1u : 0u);
+        mma_bf16(tmem, dh_i + adv, dl_j + adv, 1u);
+        mma_bf16(tmem, dl_i + adv, dh_j + adv, 1u);
+      }
+      mma_commit(&empty_bar[s]);
+    }
+    mma_commit(&done_bar);   // fires once every MMA issued above has completed
+  }
+  __syncwarp();
+
+  // ---------------- epilogue: TMEM -> registers -> FP32 partial tile
+  const bool ok = mbar_wait(&done_bar, 0, abort_flag) && !*abort_flag;
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  float* dst = part + ((size_t)tile * nsplit + split) * (kBM * kBN);
+  const int row = warp * 32 + lane;
+  const bool empty_range = kb1 <= kb0;
+#pragma unroll 1
+  for (int c = 0; c < kBN; c += 32) {
+    float v[32];
+    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c;
+    tmem_ld32(taddr, v);
+    float4* o = reinterpret_cast<float4*>(dst + (size_t)row * kBN + c);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      float4 q;
+      q.x = (ok && !empty_range) ? v[4 * i + 0] : 0.f;
+      q.y = (ok && !empty_range) ? v[4 * i + 1] : 0.f;
+      q.z = (ok && !empty_range) ? v[4 * i + 2] : 0.f;
+      q.w = (ok && !empty_range) ? v[4 * i + 3] : 0.f;
+      o[i] = q;
+    }
+  }
+  if (threadIdx.x == 0 && *abort_flag && status) atomicMax(status, RSX_ETIMEOUT);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+  }
+}
+
+// C[t][s] = sum over splits of the partial tiles (FP64), mirrored; diagonal tiles are
+// symmetrised by averaging (t, s) and (s, t).
+__global__ void k_syrk_reduce(const float* __restrict__ part, int n, int nb, int nsplit, double* __restrict__ C) {
+  const long long total = (long long)n * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int t = (int)(e / n), s = (int)(e - (long long)t * n);
+    const int a = t < s ? t : s, b = t < s ? s : t;
+    const int I = a / kBM, J = b / kBN;
+    const int tile = I * nb - I * (I - 1) / 2 + (J - I);
+    const int ra = a - I * kBM, cb = b - J * kBN;
+    double v = 0.0;
+    const float* p = part + (size_t)tile * nsplit * (kBM * kBN);
+    for (int sp = 0; sp < nsplit; ++sp) {
+      const float* q = p + (size_t)sp * (kBM * kBN);
+      v += (double)q[ra * kBN + cb];
+      if (I == J) v += (double)q[cb * kBN + ra];
+    }
+    if (I == J) v *= 0.5;
+    C[e] = v;
+  }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+bool make_map(CUtensorMap* m, const void* base, int rows, long long ld) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)kBM};
+  cuuint32_t es[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+int syrk_splits(int nsm, int n) {
+  const int nb = (n + kBM - 1) / kBM;
+  const int tiles = nb * (nb + 1) / 2;
+  int s = nsm / tiles;
+  return s < 1 ? 1 : s;
+}
+
+size_t syrk_partial_bytes(int n, int nsplit) {
+  const int nb = (n + kBM - 1) / kBM;
+  const int tiles = nb * (nb + 1) / 2;
+  return (size_t)tiles * nsplit * kBM * kBN * sizeof(float);
+}
+
+// hi, lo: [n_pad][ld] bf16 with n_pad = 128 * ceil(n / 128) rows (rows >= n zero), ld % 64 == 0
+int syrk_bf16x3(rsx_ctx* c, const uint16_t* hi, const uint16_t* lo, int n, long long ld, int nsplit, float* part,
+                double* C, cudaStream_t s) {
+  if (n < 1 || ld < kBK || ld % kBK) return set_error(c, RSX_EINVAL, "syrk: need n >= 1 and ld a multiple of 64");
+  if ((reinterpret_cast<uintptr_t>(hi) | reinterpret_cast<uintptr_t>(lo)) & 15)
+    return set_error(c, RSX_EINVAL, "syrk: panels must be 16-byte aligned");
+  const int nb = (n + kBM - 1) / kBM;
+  const int tiles = nb * (nb + 1) / 2;
+  CUtensorMap mh, ml;
+  if (!make_map(&mh, hi, nb * kBM, ld) || !make_map(&ml, lo, nb * kBM, ld))
+    return set_error(c, RSX_ECUDA, "syrk: cuTensorMapEncodeTiled failed");
+  const int nkb = (int)(ld / kBK);
+  const size_t smem = (size_t)kStages * kStageBytes + 1024;
+  cudaError_t e = cudaFuncSetAttribute(k_syrk_bf16x3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return check_cuda(c, e, "syrk smem attribute");
+  {
+    ProfScope ps(c, kKGemm, s);
+    k_syrk_bf16x3<<<tiles * nsplit, kGemmThreads, smem, s>>>(mh, ml, nb, nkb, nsplit, part, c->status);
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) return check_cuda(c, e, "syrk launch");
+  {
+    ProfScope ps(c, kKGemmReduce, s);
+    k_syrk_reduce<<<512, 256, 0, s>>>(part, n, nb, nsplit, C);
+    e = cudaGetLastError();
+  }
+  return check_cuda(c, e, "syrk reduce");
+}
+
+}  // namespace rsx

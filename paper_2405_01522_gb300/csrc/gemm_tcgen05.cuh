@@ -1,0 +1,18 @@
+// Split-BF16 symmetric contraction on tcgen05 tensor cores (gemm_tcgen05.cu).
+#pragma once
+#include <cstdint>
+
+#include "rsx_internal.cuh"
+
+struct rsx_ctx;
+
+namespace rsx {
+// number of K splits for an n x n output on nsm SMs (about one CTA per SM)
+int syrk_splits(int nsm, int n);
+// bytes of the FP32 split partials
+size_t syrk_partial_bytes(int n, int nsplit);
+// C = H H^T + H L^T + L H^T (FP64 out, n x n row-major, symmetric).  hi, lo: [128*ceil(n/128)][ld]
+// bf16 (rows >= n zero), ld % 64 == 0, 16-byte aligned.
+int syrk_bf16x3(rsx_ctx* c, const uint16_t* hi, const uint16_t* lo, int n, long long ld, int nsplit, float* part,
+                double* C, cudaStream_t s);
+}  // namespace rsx

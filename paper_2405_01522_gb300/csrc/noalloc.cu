@@ -85,7 +85,7 @@ int exchange_noalloc(rsx_ctx* c, const void* phi, int nocc, const void* psi, int
     rc = check_cuda(c, launch_pass2<R>(g, nocc, inter, twy, twz, (const R*)c->vhat, nullptr, grid, s),
                     "noalloc pass 2");
     if (rc) return rc;
-    rc = check_cuda(c, launch_pass3<R>(g, pm, p * nocc, p, 1, inter, twx, (R*)out + (size_t)p * N, s),
+    rc = check_cuda(c, launch_pass3<R>(g, pm, p * nocc, p, 1, 0, inter, twx, (R*)out + (size_t)p * N, s),
                     "noalloc pass 3");
     if (rc) return rc;
   }

@@ -373,8 +373,9 @@ __global__ void __launch_bounds__(kThreads) k_spectrum(Geom g, int nq, const Cx<
 // ---------------------------------------------------------------------------------
 // pass 3: x inverse (c2r via row pairs) of every pair in output p's list, and
 // out_p(z, y, x) = - sum_e partner_e(z, y, x) V_e(z, y, x).  CTA = (p, z, 32 rows).
+// With pot != 0 the output p is the potential V of pair q = p itself (no partner, no sign).
 template <typename R, int AX>
-__global__ void __launch_bounds__(kThreads) k_pass3(Geom g, PairMap<R> pm, int q0, int p0,
+__global__ void __launch_bounds__(kThreads) k_pass3(Geom g, PairMap<R> pm, int q0, int p0, int pot,
                                                     const Cx<R>* __restrict__ inter,
                                                     const Cx<R>* __restrict__ twx, R* __restrict__ out) {
   constexpr int L = 16 * AX;
@@ -404,19 +405,21 @@ __global__ void __launch_bounds__(kThreads) k_pass3(Geom g, PairMap<R> pm, int q
 #pragma unroll
   for (int k2 = 0; k2 < 16; ++k2) acc0[k2] = acc1[k2] = R(0);
 
-  const int ne = pm.nentries(p);
+  const int ne = pot ? 1 : pm.nentries(p);
   for (int e = 0; e < ne; ++e) {
-    int q;
-    const R* partner;
-    pm.entry(p, e, q, partner);
+    int q = p;
+    const R* partner = nullptr;
+    if (!pot) pm.entry(p, e, q, partner);
     const Cx<R>* src = inter + (size_t)(q - q0) * g.inter_elems() + (size_t)z * g.ny + y0;
     __syncthreads();
     for (int i = threadIdx.x; i < H * kRowsPerCta; i += kThreads) {
       const int kx = i / kRowsPerCta, r = i - kx * kRowsPerCta;
       xs[kx * kXsPitch + r] = (r < nrow) ? src[(size_t)kx * kstride + r] : cx<R>(R(0), R(0));
     }
-    const R* prow = partner + plane + (size_t)y0 * g.nx;
-    for (int i = threadIdx.x; i < nrow * g.nx; i += kThreads) tile[i] = __ldg(prow + i);
+    if (!pot) {
+      const R* prow = partner + plane + (size_t)y0 * g.nx;
+      for (int i = threadIdx.x; i < nrow * g.nx; i += kThreads) tile[i] = __ldg(prow + i);
+    }
     __syncthreads();
 
     // Z(k) = X_a(k) + i X_b(k), Hermitian extension for k > L/2
@@ -445,8 +448,13 @@ __global__ void __launch_bounds__(kThreads) k_pass3(Geom g, PairMap<R> pm, int q
       for (int k2 = 0; k2 < 16; ++k2) {
         const int x = t + AX * k2;
         if (x < g.nx) {
-          if (ra < nrow) acc0[k2] -= tile[ra * g.nx + x] * u[k2].x;
-          if (rb < nrow) acc1[k2] -= tile[rb * g.nx + x] * u[k2].y;
+          if (pot) {
+            acc0[k2] += u[k2].x;
+            acc1[k2] += u[k2].y;
+          } else {
+            if (ra < nrow) acc0[k2] -= tile[ra * g.nx + x] * u[k2].x;
+            if (rb < nrow) acc1[k2] -= tile[rb * g.nx + x] * u[k2].y;
+          }
         }
       }
     }

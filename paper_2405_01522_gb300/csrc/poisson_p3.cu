@@ -4,7 +4,7 @@
 namespace rsx {
 
 template <typename R>
-cudaError_t launch_pass3(const Geom& g, const PairMap<R>& pm, int q0, int p0, int np, const Cx<R>* inter,
+cudaError_t launch_pass3(const Geom& g, const PairMap<R>& pm, int q0, int p0, int np, int pot, const Cx<R>* inter,
                          const Cx<R>* twx, R* out, cudaStream_t s) {
   if (np <= 0) return cudaSuccess;
   const size_t smem = pass3_smem<R>(g.Ax, g.nx);
@@ -17,7 +17,7 @@ cudaError_t launch_pass3(const Geom& g, const PairMap<R>& pm, int q0, int p0, in
     auto k = k_pass3<R, a>;                                                                      \
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
     if (e != cudaSuccess) return e;                                                              \
-    k<<<(unsigned)nblk, kThreads, smem, s>>>(g, pm, q0, p0, inter, twx, out);                    \
+    k<<<(unsigned)nblk, kThreads, smem, s>>>(g, pm, q0, p0, pot, inter, twx, out);                    \
     return cudaGetLastError();                                                                   \
   }
     RSX_FOR_EACH_A(RSX_CASE)
@@ -26,9 +26,9 @@ cudaError_t launch_pass3(const Geom& g, const PairMap<R>& pm, int q0, int p0, in
   }
 }
 
-template cudaError_t launch_pass3<float>(const Geom&, const PairMap<float>&, int, int, int, const Cx<float>*,
+template cudaError_t launch_pass3<float>(const Geom&, const PairMap<float>&, int, int, int, int, const Cx<float>*,
                                          const Cx<float>*, float*, cudaStream_t);
-template cudaError_t launch_pass3<double>(const Geom&, const PairMap<double>&, int, int, int, const Cx<double>*,
+template cudaError_t launch_pass3<double>(const Geom&, const PairMap<double>&, int, int, int, int, const Cx<double>*,
                                           const Cx<double>*, double*, cudaStream_t);
 
 }  // namespace rsx

@@ -77,7 +77,7 @@ template <typename R>
 cudaError_t launch_pass2(const Geom& g, int nq, Cx<R>* inter, const Cx<R>* twy, const Cx<R>* twz,
                          const R* vhat, R* gscratch, int grid, cudaStream_t s);
 template <typename R>
-cudaError_t launch_pass3(const Geom& g, const PairMap<R>& pm, int q0, int p0, int np, const Cx<R>* inter,
+cudaError_t launch_pass3(const Geom& g, const PairMap<R>& pm, int q0, int p0, int np, int pot, const Cx<R>* inter,
                          const Cx<R>* twx, R* out, cudaStream_t s);
 // forward y/z transform of each pair plane, weighted by sqrt(w_G vhat(G) h^3) and split
 // into bf16 hi/lo rows of the K panel (t-major, G contiguous)

@@ -34,6 +34,7 @@ SIGNATURES = {
     "rsx_casida_K": [_P, _P, _I, _P, _I, _P, _P],
     "rsx_casida_Kd": [_P, _P, _I, _P, _I, _P, _P],
     "rsx_casida_solve": [_P, _P, _I, _P, _I, _P, _P, _D, _I, _P, _P, _P],
+    "rsx_syrk_bf16x3": [_P, _P, _P, _I, ctypes.c_longlong, _P, _P],
     "rsx_sync_status": [_P, _P],
     "rsx_profile_enable": [_P, _I],
     "rsx_profile_reset": [_P],
@@ -180,6 +181,13 @@ class Context:
                                               _ptr(Kd), float(delta_M), int(nroots), _ptr(omega), _ptr(X),
                                               _stream(stream)))
         return (omega, X) if vectors else omega
+
+    def syrk_bf16x3(self, hi, lo, C=None, stream=None):
+        """C = H H^T + H L^T + L H^T for bf16 panels [n][ld] (n % 128 == 0, ld % 64 == 0)."""
+        n, ld = hi.shape
+        C = torch.empty((n, n), dtype=torch.float64, device=self.device) if C is None else C
+        self._check(self.lib.rsx_syrk_bf16x3(self.handle, _ptr(hi), _ptr(lo), n, ld, _ptr(C), _stream(stream)))
+        return C
 
     def profile(self, on=True):
         self._check(self.lib.rsx_profile_enable(self.handle, 1 if on else 0))

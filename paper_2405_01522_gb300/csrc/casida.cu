@@ -138,7 +138,7 @@ int casida_K_f32(rsx_ctx* c, const void* po, int no, const void* pv, int nv, dou
   const int nsplit = syrk_splits(c->nsm, nt);
   rc = grow(c, &c->gemm_part, &c->gemm_part_bytes, syrk_partial_bytes(nt, nsplit), "K split partials");
   if (rc) return rc;
-  return syrk_bf16x3(c, hi, lo, nt, ld, nsplit, (float*)c->gemm_part, K, s);
+  return syrk_bf16x3(c, hi, lo, nt, ld, nsplit, (double*)c->gemm_part, K, s);
 }
 
 template <typename R>
@@ -270,7 +270,7 @@ int rsx_syrk_bf16x3(rsx_ctx* c, const void* hi, const void* lo, int n, long long
   const int nsplit = syrk_splits(c->nsm, n);
   int rc = grow(c, &c->gemm_part, &c->gemm_part_bytes, syrk_partial_bytes(n, nsplit), "split partials");
   if (rc) return rc;
-  return syrk_bf16x3(c, (const uint16_t*)hi, (const uint16_t*)lo, n, ld, nsplit, (float*)c->gemm_part, C,
+  return syrk_bf16x3(c, (const uint16_t*)hi, (const uint16_t*)lo, n, ld, nsplit, (double*)c->gemm_part, C,
                      (cudaStream_t)stream);
 }
 

@@ -11,9 +11,13 @@
 // 64-wide K blocks (H_I, L_I, H_J, L_J: 4 x 16 KB, 128B-swizzled) is filled by TMA
 // (cp.async.bulk.tensor) from one producer thread; one thread issues tcgen05.mma
 // (kind::f16, bf16 x bf16 -> f32, M = N = 128, K = 16) into a 128-column TMEM
-// accumulator; tcgen05.commit frees each stage.  The four warps then read the
-// accumulator with tcgen05.ld and write an FP32 partial tile; a second kernel sums the
-// split partials in FP64 and mirrors the upper triangle.
+// accumulator; tcgen05.commit frees each stage.  The tensor-core FP32 accumulation
+// is not round-to-nearest over long sums (its error grows with the number of
+// accumulations), so the accumulator is double-buffered in TMEM (2 x 128 columns) and
+// restarted every kChunk K blocks: 16 epilogue warps read each finished chunk with
+// tcgen05.ld and add it into double-float (TwoSum) registers while the next chunk
+// accumulates.  Each CTA writes an FP64 partial tile; a second kernel sums the split
+// partials in FP64 and mirrors the upper triangle.
 //
 // Every mbarrier wait is bounded: on timeout the kernel raises RSX_ETIMEOUT in the
 // status word, stops issuing, drains what it issued (bounded), frees TMEM and returns.
@@ -33,8 +37,10 @@ constexpr int kBM = 128, kBN = 128, kBK = 64;
 constexpr int kStages = 3;
 constexpr int kTileBytes = kBM * kBK * 2;           // 16 KB per operand tile
 constexpr int kStageBytes = 4 * kTileBytes;         // H_I, L_I, H_J, L_J
-constexpr int kGemmThreads = 128;
-constexpr int kTmemCols = 128;
+constexpr int kEpiWarps = 16;                       // four per TMEM lane quarter, 32 columns each
+constexpr int kGemmThreads = 32 * (2 + kEpiWarps);  // producer, MMA, epilogue warps
+constexpr int kTmemCols = 2 * kBN;                  // double-buffered 128-column accumulator
+constexpr int kChunk = 4;                           // K blocks per TMEM accumulation chunk
 constexpr uint32_t kWaitLimit = 1u << 26;           // try_wait rounds before giving up
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -141,14 +147,15 @@ __device__ __forceinline__ void tile_ij(int tile, int nb, int& I, int& J) {
 
 __global__ void __launch_bounds__(kGemmThreads, 1)
     k_syrk_bf16x3(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo, int nb,
-                  int nkb, int nsplit, float* __restrict__ part, int* status) {
+                  int nkb, int nsplit, double* __restrict__ part, int* status) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // 1024-byte aligned operand ring
   unsigned char* ring = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   __shared__ __align__(8) uint64_t full_bar[kStages];
   __shared__ __align__(8) uint64_t empty_bar[kStages];
-  __shared__ __align__(8) uint64_t done_bar;
+  __shared__ __align__(8) uint64_t tfull_bar[2];
+  __shared__ __align__(8) uint64_t tempty_bar[2];
   __shared__ uint32_t tmem_base_sh;
   __shared__ int abort_sh;
 
@@ -159,6 +166,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
   tile_ij(tile, nb, I, J);
   const int kb0 = (int)((long long)nkb * split / nsplit);
   const int kb1 = (int)((long long)nkb * (split + 1) / nsplit);
+  const int nchunk = (kb1 - kb0 + kChunk - 1) / kChunk;
 
   if (threadIdx.x == 0) {
     abort_sh = 0;
@@ -166,7 +174,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
       mbar_init(&full_bar[s], 1);
       mbar_init(&empty_bar[s], 1);
     }
-    mbar_init(&done_bar, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull_bar[b], 1);
+      mbar_init(&tempty_bar[b], kEpiWarps);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
@@ -182,78 +193,106 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
   const uint32_t tmem = tmem_base_sh;
   volatile int* abort_flag = &abort_sh;
 
-  if (warp == 0 && lane == 0) {
-    // ---------------- TMA producer
-    int issued = 0;
-    for (int kb = kb0; kb < kb1; ++kb) {
-      const int it = kb - kb0;
-      const int s = it % kStages;
-      const uint32_t ph = (uint32_t)((it / kStages) & 1);
-      if (it >= kStages && !mbar_wait(&empty_bar[s], ph ^ 1u, abort_flag)) break;
-      unsigned char* st = ring + (size_t)s * kStageBytes;
-      mbar_arrive_expect_tx(&full_bar[s], kStageBytes);
-      const int k = kb * kBK;
-      tma_load_2d(st + 0 * kTileBytes, &tm_hi, &full_bar[s], k, I * kBM);
-      tma_load_2d(st + 1 * kTileBytes, &tm_lo, &full_bar[s], k, I * kBM);
-      tma_load_2d(st + 2 * kTileBytes, &tm_hi, &full_bar[s], k, J * kBN);
-      tma_load_2d(st + 3 * kTileBytes, &tm_lo, &full_bar[s], k, J * kBN);
-      issued = it + 1;
-    }
-    // drain: every issued stage's copies must have landed before the CTA exits
-    const int first = issued > kStages ? issued - kStages : 0;
-    for (int it = first; it < issued; ++it) {
-      const int s = it % kStages;
-      const uint32_t ph = (uint32_t)((it / kStages) & 1);
-      for (uint32_t i = 0; i < kWaitLimit && !mbar_try_wait(&full_bar[s], ph); ++i) {
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- TMA producer
+      int issued = 0;
+      for (int kb = kb0; kb < kb1; ++kb) {
+        const int it = kb - kb0;
+        const int s = it % kStages;
+        const uint32_t ph = (uint32_t)((it / kStages) & 1);
+        if (it >= kStages && !mbar_wait(&empty_bar[s], ph ^ 1u, abort_flag)) break;
+        unsigned char* st = ring + (size_t)s * kStageBytes;
+        mbar_arrive_expect_tx(&full_bar[s], kStageBytes);
+        const int k = kb * kBK;
+        tma_load_2d(st + 0 * kTileBytes, &tm_hi, &full_bar[s], k, I * kBM);
+        tma_load_2d(st + 1 * kTileBytes, &tm_lo, &full_bar[s], k, I * kBM);
+        tma_load_2d(st + 2 * kTileBytes, &tm_hi, &full_bar[s], k, J * kBN);
+        tma_load_2d(st + 3 * kTileBytes, &tm_lo, &full_bar[s], k, J * kBN);
+        issued = it + 1;
+      }
+      // drain: every issued stage's copies must have landed before the CTA exits
+      const int first = issued > kStages ? issued - kStages : 0;
+      for (int it = first; it < issued; ++it) {
+        const int s = it % kStages;
+        const uint32_t ph = (uint32_t)((it / kStages) & 1);
+        for (uint32_t i = 0; i < kWaitLimit && !mbar_try_wait(&full_bar[s], ph); ++i) {
+        }
       }
     }
-  } else if (warp == 1 && lane == 0) {
-    // ---------------- MMA issuer
-    for (int kb = kb0; kb < kb1; ++kb) {
-      const int it = kb - kb0;
-      const int s = it % kStages;
-      const uint32_t ph = (uint32_t)((it / kStages) & 1);
-      if (!mbar_wait(&full_bar[s], ph, abort_flag)) break;
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- MMA issuer: chunks of kChunk K blocks into alternating TMEM buffers
+      bool live = true;
+      for (int ch = 0; ch < nchunk && live; ++ch) {
+        const int b = ch & 1, use = ch >> 1;
+        if (use > 0 && !mbar_wait(&tempty_bar[b], (uint32_t)((use - 1) & 1), abort_flag)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t acc = tmem + (uint32_t)(b * kBN);
+        const int c0 = kb0 + ch * kChunk;
+        const int c1 = min(c0 + kChunk, kb1);
+        for (int kb = c0; kb < c1; ++kb) {
+          const int it = kb - kb0;
+          const int s = it % kStages;
+          const uint32_t ph = (uint32_t)((it / kStages) & 1);
+          if (!mbar_wait(&full_bar[s], ph, abort_flag)) {
+            live = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t base = smem_u32(ring + (size_t)s * kStageBytes);
+          const uint64_t dh_i = sw128_desc(base + 0 * kTileBytes);
+          const uint64_t dl_i = sw128_desc(base + 1 * kTileBytes);
+          const uint64_t dh_j = sw128_desc(base + 2 * kTileBytes);
+          const uint64_t dl_j = sw128_desc(base + 3 * kTileBytes);
+#pragma unroll
+          for (int j = 0; j < kBK / 16; ++j) {
+            const uint64_t adv = (uint64_t)((j * 32) >> 4);   // 16 bf16 = 32 bytes along K
+            mma_bf16(acc, dh_i + adv, dh_j + adv, (kb > c0 || j > 0) ? 1u : 0u);
+            mma_bf16(acc, dh_i + adv, dl_j + adv, 1u);
+            mma_bf16(acc, dl_i + adv, dh_j + adv, 1u);
+          }
+          mma_commit(&empty_bar[s]);
+        }
+        mma_commit(&tfull_bar[b]);   // fires when this chunk's MMAs have completed
+      }
+    }
+  } else {
+    // ---------------- epilogue warps: drain each chunk into double-float registers
+    const int e = warp - 2;                  // 0..15
+    const int quarter = warp & 3;            // TMEM lanes this warp may access
+    const int cg = e >> 2;                   // columns [32 cg, 32 cg + 32)
+    const int row = quarter * 32 + lane;
+    float sh[32], sl[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) sh[i] = sl[i] = 0.f;
+    bool ok = true;
+    for (int ch = 0; ch < nchunk; ++ch) {
+      const int b = ch & 1, use = ch >> 1;
+      ok = mbar_wait(&tfull_bar[b], (uint32_t)(use & 1), abort_flag);
+      if (!ok) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t base = smem_u32(ring + (size_t)s * kStageBytes);
-      const uint64_t dh_i = sw128_desc(base + 0 * kTileBytes);
-      const uint64_t dl_i = sw128_desc(base + 1 * kTileBytes);
-      const uint64_t dh_j = sw128_desc(base + 2 * kTileBytes);
-      const uint64_t dl_j = sw128_desc(base + 3 * kTileBytes);
+      const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * kBN + cg * 32);
+      float v[32];
+      tmem_ld32(taddr, v);
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0)
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tempty_bar[b])) : "memory");
 #pragma unroll
-      for (int j = 0; j < kBK / 16; ++j) {
-        const uint64_t adv = (uint64_t)((j * 32) >> 4);   // 16 bf16 = 32 bytes along K
-        mma_bf16(tmem, dh_i + adv, dh_j + adv, (it > 0 || j > 0) ? 1u : 0u);
-        mma_bf16(tmem, dh_i + adv, dl_j + adv, 1u);
-        mma_bf16(tmem, dl_i + adv, dh_j + adv, 1u);
+      for (int i = 0; i < 32; ++i) {
+        // TwoSum: (sh, sl) += v exactly up to the final rounding of sl
+        const float t = sh[i] + v[i];
+        const float bp = t - sh[i];
+        const float err = (sh[i] - (t - bp)) + (v[i] - bp);
+        sh[i] = t;
+        sl[i] += err;
       }
-      mma_commit(&empty_bar[s]);
     }
-    mma_commit(&done_bar);   // fires once every MMA issued above has completed
-  }
-  __syncwarp();
-
-  // ---------------- epilogue: TMEM -> registers -> FP32 partial tile
-  const bool ok = mbar_wait(&done_bar, 0, abort_flag) && !*abort_flag;
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  float* dst = part + ((size_t)tile * nsplit + split) * (kBM * kBN);
-  const int row = warp * 32 + lane;
-  const bool empty_range = kb1 <= kb0;
-#pragma unroll 1
-  for (int c = 0; c < kBN; c += 32) {
-    float v[32];
-    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c;
-    tmem_ld32(taddr, v);
-    float4* o = reinterpret_cast<float4*>(dst + (size_t)row * kBN + c);
+    double* dst = part + ((size_t)tile * nsplit + split) * (kBM * kBN) + (size_t)row * kBN + cg * 32;
+    const bool good = ok && !*abort_flag;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      float4 q;
-      q.x = (ok && !empty_range) ? v[4 * i + 0] : 0.f;
-      q.y = (ok && !empty_range) ? v[4 * i + 1] : 0.f;
-      q.z = (ok && !empty_range) ? v[4 * i + 2] : 0.f;
-      q.w = (ok && !empty_range) ? v[4 * i + 3] : 0.f;
-      o[i] = q;
-    }
+    for (int i = 0; i < 32; ++i) dst[i] = good ? (double)sh[i] + (double)sl[i] : 0.0;
   }
   if (threadIdx.x == 0 && *abort_flag && status) atomicMax(status, RSX_ETIMEOUT);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -265,7 +304,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
 
 // C[t][s] = sum over splits of the partial tiles (FP64), mirrored; diagonal tiles are
 // symmetrised by averaging (t, s) and (s, t).
-__global__ void k_syrk_reduce(const float* __restrict__ part, int n, int nb, int nsplit, double* __restrict__ C) {
+__global__ void k_syrk_reduce(const double* __restrict__ part, int n, int nb, int nsplit, double* __restrict__ C) {
   const long long total = (long long)n * n;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
@@ -275,11 +314,11 @@ __global__ void k_syrk_reduce(const float* __restrict__ part, int n, int nb, int
     const int tile = I * nb - I * (I - 1) / 2 + (J - I);
     const int ra = a - I * kBM, cb = b - J * kBN;
     double v = 0.0;
-    const float* p = part + (size_t)tile * nsplit * (kBM * kBN);
+    const double* p = part + (size_t)tile * nsplit * (kBM * kBN);
     for (int sp = 0; sp < nsplit; ++sp) {
-      const float* q = p + (size_t)sp * (kBM * kBN);
-      v += (double)q[ra * kBN + cb];
-      if (I == J) v += (double)q[cb * kBN + ra];
+      const double* q = p + (size_t)sp * (kBM * kBN);
+      v += q[ra * kBN + cb];
+      if (I == J) v += q[cb * kBN + ra];
     }
     if (I == J) v *= 0.5;
     C[e] = v;
@@ -329,11 +368,11 @@ int syrk_splits(int nsm, int n) {
 size_t syrk_partial_bytes(int n, int nsplit) {
   const int nb = (n + kBM - 1) / kBM;
   const int tiles = nb * (nb + 1) / 2;
-  return (size_t)tiles * nsplit * kBM * kBN * sizeof(float);
+  return (size_t)tiles * nsplit * kBM * kBN * sizeof(double);
 }
 
 // hi, lo: [n_pad][ld] bf16 with n_pad = 128 * ceil(n / 128) rows (rows >= n zero), ld % 64 == 0
-int syrk_bf16x3(rsx_ctx* c, const uint16_t* hi, const uint16_t* lo, int n, long long ld, int nsplit, float* part,
+int syrk_bf16x3(rsx_ctx* c, const uint16_t* hi, const uint16_t* lo, int n, long long ld, int nsplit, double* part,
                 double* C, cudaStream_t s) {
   if (n < 1 || ld < kBK || ld % kBK) return set_error(c, RSX_EINVAL, "syrk: need n >= 1 and ld a multiple of 64");
   if ((reinterpret_cast<uintptr_t>(hi) | reinterpret_cast<uintptr_t>(lo)) & 15)

@@ -13,6 +13,6 @@ int syrk_splits(int nsm, int n);
 size_t syrk_partial_bytes(int n, int nsplit);
 // C = H H^T + H L^T + L H^T (FP64 out, n x n row-major, symmetric).  hi, lo: [128*ceil(n/128)][ld]
 // bf16 (rows >= n zero), ld % 64 == 0, 16-byte aligned.
-int syrk_bf16x3(rsx_ctx* c, const uint16_t* hi, const uint16_t* lo, int n, long long ld, int nsplit, float* part,
+int syrk_bf16x3(rsx_ctx* c, const uint16_t* hi, const uint16_t* lo, int n, long long ld, int nsplit, double* part,
                 double* C, cudaStream_t s);
 }  // namespace rsx

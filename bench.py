@@ -304,6 +304,10 @@ def run_rsx(args, rank, local_rank, world):
             "tolerance_energy": 1e-6}
         ctx64.close()
 
+    # ---- Casida coupling (config with 512 transitions), rank 0
+    if rank == 0 and not args.skip_casida:
+        out["casida"] = casida_bench(args, dev, local_rank, peaks)
+
     # ---- CPU oracle baseline (rank 0, N = 1 only)
     if rank == 0 and world == 1 and not args.skip_cpu:
         out["cpu_baseline"] = cpu_baseline(s, nsolve=args.cpu_solves)
@@ -314,6 +318,76 @@ def run_rsx(args, rank, local_rank, world):
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def casida_bench(args, dev, local_rank, peaks):
+    """Casida coupling K (80^3 at 0.25 bohr, 8 occupied + 64 virtual, 512 transitions):
+    split-BF16 tensor-core K vs the FP64 plain form, TDA roots, tensor roofline of the
+    K contraction kernel."""
+    from paper_2405_01522_gb300 import rsx
+    s = inputs.casida_system(n=args.casida_edge, h=0.25, nocc=8, nvirt=64)
+    nt = 8 * 64
+    ng = 2 * (s.shape[2] + 1) * (2 * s.shape[1]) * (2 * s.shape[0])
+    c32 = rsx.Context(s.shape, s.h, "fp32", device=local_rank)
+    po = torch.from_numpy(s.phi).float().to(dev)
+    pv = torch.from_numpy(s.phi_virt).float().to(dev)
+    K = torch.empty((nt, nt), dtype=torch.float64, device=dev)
+    eo = torch.from_numpy(s.eps_occ).to(dev)
+    ev = torch.from_numpy(s.eps_virt).to(dev)
+    c32.casida_K(po, pv, K=K)
+    c32.sync()
+    reps = 3
+    c32.profile_reset()
+    c32.profile(True)
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    e[0].record()
+    for _ in range(reps):
+        c32.casida_K(po, pv, K=K)
+    e[1].record()
+    torch.cuda.synchronize()
+    c32.profile(False)
+    prof = c32.profile_read()
+    k_ms = e[0].elapsed_time(e[1]) / reps
+    gemm_ms = prof["k_gemm_tcgen05"][0] / prof["k_gemm_tcgen05"][1]
+    useful = 2.0 * nt * nt * ng                      # one product, full nt x nt
+    nbk = (nt + 127) // 128
+    executed = 3 * (nbk * (nbk + 1) // 2) * 2.0 * 128 * 128 * ng   # three products, upper-triangle tiles
+    peak = peaks.get("bf16_tflops", 1900.0)
+    es = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    es[0].record()
+    w32 = c32.casida_solve(eo, ev, K, None, 1.0, 10)
+    es[1].record()
+    torch.cuda.synchronize()
+    solve_ms = es[0].elapsed_time(es[1])
+    out = {"workload": "TDA coupling K, 80^3 box at h=0.25 bohr padded to 160^3, 8 occupied + 64 virtual "
+                       "orthonormal Gaussian-sum orbitals, 512 transitions, K via split-BF16 tcgen05 "
+                       "(hi.hi + hi.lo + lo.hi), lowest 10 roots of diag(de) + K",
+           "casida_K_ms": round(k_ms, 3), "gemm_ms": round(gemm_ms, 3), "eigensolve_ms": round(solve_ms, 3),
+           "useful_tflops": round(useful / (gemm_ms / 1e3) / 1e12, 1),
+           "kernels": {k: {"ms_per_launch": round(v[0] / v[1], 4), "launches": v[1]} for k, v in prof.items()},
+           "roofline": {"kernel": "k_syrk_bf16x3 (tcgen05)", "bound": "tensor",
+                        "achieved": round(executed / (gemm_ms / 1e3) / 1e12, 1), "peak": peak, "unit": "TFLOP/s",
+                        "frac": round(executed / (gemm_ms / 1e3) / 1e12 / peak, 4), "traffic": None,
+                        "peak_source": "measured" if "bf16_tflops" in peaks else "fallback",
+                        "algorithmic_flops_per_launch": executed}}
+    if not args.skip_fp64:
+        c64 = rsx.Context(s.shape, s.h, "fp64", device=local_rank)
+        K64 = c64.casida_K(po.double(), pv.double())
+        c64.sync()
+        f = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        f[0].record()
+        c64.casida_K(po.double(), pv.double(), K=K64)
+        f[1].record()
+        torch.cuda.synchronize()
+        w64 = c64.casida_solve(eo, ev, K64, None, 1.0, 10)
+        c64.sync()
+        out["fp64_plain_K_ms"] = round(f[0].elapsed_time(f[1]), 2)
+        out["omega_err_ev_max"] = float((w32 - w64).abs().max()) * 27.211386245988
+        out["omega_ev"] = [round(float(x) * 27.211386245988, 6) for x in w64]
+        out["tolerance_ev"] = 1e-5
+        c64.close()
+    c32.close()
+    return out
 
 
 def cpu_baseline(s, nsolve=16):
@@ -364,6 +438,9 @@ def main():
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--cpu-solves", type=int, default=16)
+    ap.add_argument("--skip-casida", action="store_true")
+    ap.add_argument("--casida-only", action="store_true", help="only the Casida section (profiling captures)")
+    ap.add_argument("--casida-edge", type=int, default=80, help="box edge of the Casida case")
     ap.add_argument("--nocc", type=int, default=16, help="smaller cases for profiling captures only")
     ap.add_argument("--npsi", type=int, default=32, help="smaller cases for profiling captures only")
     args = ap.parse_args()
@@ -377,6 +454,15 @@ def main():
     rank, local_rank, world = env_rank()
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.casida_only:
+        dev = torch.device("cuda", local_rank)
+        torch.cuda.set_device(dev)
+        peaks = {}
+        try:
+            peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        except Exception:
+            pass
+        print(json.dumps({"casida": casida_bench(args, dev, local_rank, peaks)}), flush=True)
     else:
         run_rsx(args, rank, local_rank, world)
 

@@ -2,11 +2,14 @@
 // with B = 0 the problem A X = omega X is Hermitian; only the lowest roots are needed).
 //
 //   k_tda_assemble    A = diag(eps_a - eps_i) + delta_M K - K_d, symmetrised
-//   k_tridiagonalise  Householder reduction A = Q T Q^T (one CTA; reflectors kept in A)
-//   k_bisect          lowest nroots eigenvalues of T by Sturm-count bisection
+//   k_tridiag_coop    Householder reduction A = Q T Q^T, cooperative multi-CTA (reflectors
+//                     kept in A); k_tridiagonalise is the one-CTA form for small n
+//   k_multisect       lowest nroots eigenvalues of T by Sturm-count multisection
 //   k_eigvec          inverse iteration on T (with re-orthogonalisation inside clusters of
 //                     close eigenvalues), then x = Q y
 #include <cuda_runtime.h>
+
+#include <algorithm>
 
 #include "../../include/rsx.h"
 #include "api_internal.cuh"
@@ -144,31 +147,241 @@ __device__ int sturm_count(const double* d, const double* e, int n, double x, do
   return cnt;
 }
 
-// eigenvalue k (0-based, ascending) of T per thread, by bisection to full precision
-__global__ void k_bisect(const double* __restrict__ d, const double* __restrict__ e, int n, int nroots,
-                         double* __restrict__ w) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= nroots) return;
-  double lo = d[0], hi = d[0], emax = 0.0;
-  for (int i = 0; i < n; ++i) {
-    const double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i < n - 1 ? fabs(e[i]) : 0.0);
-    lo = fmin(lo, d[i] - r);
-    hi = fmax(hi, d[i] + r);
-    if (i < n - 1) emax = fmax(emax, fabs(e[i]));
+// ---------------------------------------------------------------------------------
+// Multi-CTA Householder tridiagonalisation (same reflectors and outputs as
+// k_tridiagonalise).  Rows are dealt cyclically to the CTAs; per step three grid-wide
+// barriers separate (v) -> (p = tau A22 v, p^T v partials) -> (rank-2 update of own rows
+// and the next column's norm partials).  The kernel is launched cooperatively so that
+// all CTAs are resident; the barrier itself is bounded and raises RSX_ETIMEOUT.
+constexpr uint32_t kGridWaitLimit = 1u << 24;
+
+struct GridBar {
+  unsigned int count;
+  volatile unsigned int gen;
+  volatile int abort;
+};
+
+__device__ __forceinline__ bool grid_barrier(GridBar* gb, unsigned int nblocks) {
+  __syncthreads();
+  __shared__ int ok_sh;
+  if (threadIdx.x == 0) {
+    ok_sh = 1;
+    const unsigned int g0 = gb->gen;
+    __threadfence();
+    if (atomicAdd(&gb->count, 1u) == nblocks - 1) {
+      gb->count = 0;
+      __threadfence();
+      atomicAdd((unsigned int*)&gb->gen, 1u);
+    } else {
+      uint32_t i = 0;
+      while (gb->gen == g0) {
+        if (gb->abort || ++i > kGridWaitLimit) {
+          gb->abort = 1;
+          ok_sh = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
   }
-  const double scale = fmax(fabs(lo), fabs(hi));
+  __syncthreads();
+  return ok_sh != 0;
+}
+
+// first row >= r0 owned by CTA c (rows are dealt cyclically and never change owner,
+// so a CTA only ever reads matrix rows it wrote itself; vectors shared between CTAs are
+// read with __ldcg, which bypasses the non-coherent L1)
+__device__ __forceinline__ int first_owned(int r0, int c, int G) { return r0 + ((c - r0) % G + G) % G; }
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// scratch layout (doubles): v[n], p[n], part_norm[G], part_pv[G], alpha
+__global__ void __launch_bounds__(256) k_tridiag_coop(double* __restrict__ A, int n, double* __restrict__ d,
+                                                      double* __restrict__ e, double* __restrict__ tau,
+                                                      double* __restrict__ scr, GridBar* gb, int* status) {
+  const unsigned int G = gridDim.x;
+  const int cta = blockIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+  double* vv = scr;
+  double* pp = scr + n;
+  double* part_norm = scr + 2 * n;
+  double* part_pv = part_norm + G;
+  double* alpha_g = part_pv + G;
+  __shared__ double red[8];
+  __shared__ double sh_tau, sh_beta, sh_scale;
+  bool live = true;
+
+  // norm partials of column 0 below the subdiagonal, alpha of column 0
+  {
+    double s = 0.0;
+    for (int i = first_owned(2, cta, G); i < n; i += G)
+      if (threadIdx.x == 0) s += A[(size_t)i * n] * A[(size_t)i * n];
+    if (threadIdx.x == 0) {
+      part_norm[cta] = s;
+      if (n > 1 && 1 % (int)G == cta) *alpha_g = A[(size_t)1 * n];
+    }
+  }
+  live = grid_barrier(gb, G);
+
+  for (int k = 0; k + 2 < n && live; ++k) {
+    const int m0 = k + 1;
+    // ---- reflector (every CTA computes the same scalars)
+    if (threadIdx.x == 0) {
+      double xn2 = 0.0;
+      for (unsigned int c = 0; c < G; ++c) xn2 += __ldcg(part_norm + c);
+      const double alpha = __ldcg(alpha_g);
+      if (xn2 == 0.0) {
+        sh_tau = 0.0;
+        sh_beta = alpha;
+        sh_scale = 0.0;
+      } else {
+        const double beta = -copysign(sqrt(alpha * alpha + xn2), alpha);
+        sh_tau = (beta - alpha) / beta;
+        sh_scale = 1.0 / (alpha - beta);
+        sh_beta = beta;
+      }
+      if (cta == 0) {
+        e[k] = sh_beta;
+        tau[k] = sh_tau;
+      }
+      if (k % (int)G == cta) d[k] = A[(size_t)k * n + k];
+    }
+    __syncthreads();
+    const double tk = sh_tau, sc = sh_scale;
+    // own rows: v_i, stored in the column for the back-transformation
+    for (int i = first_owned(m0, cta, G) + (int)G * threadIdx.x; i < n; i += (int)G * blockDim.x) {
+      const double vi = (i == m0) ? 1.0 : A[(size_t)i * n + k] * sc;
+      vv[i] = vi;
+      if (i > m0) A[(size_t)i * n + k] = vi;
+    }
+    if (!(live = grid_barrier(gb, G))) break;
+    // ---- p_i = tau (A22 v)_i for own rows, partial p^T v
+    double pv_part = 0.0;
+    if (tk != 0.0) {
+      int r = 0;
+      for (int i = first_owned(m0, cta, G); i < n; i += G, ++r) {
+        if (r % nwarp != warp) continue;
+        const double* row = A + (size_t)i * n;
+        double acc = 0.0;
+        for (int j = m0 + lane; j < n; j += 32) acc += row[j] * __ldcg(vv + j);
+        acc = warp_sum(acc);
+        const double pi = tk * acc;
+        if (lane == 0) {
+          pp[i] = pi;
+          pv_part += pi * __ldcg(vv + i);
+        }
+      }
+    }
+    if (lane == 0) red[warp] = pv_part;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < nwarp; ++w) t += red[w];
+      part_pv[cta] = t;
+    }
+    if (!(live = grid_barrier(gb, G))) break;
+    // ---- w = p - (tau/2)(p^T v) v ; A22 -= v w^T + w v^T on own rows; next column norm
+    double nrm_part = 0.0;
+    if (tk != 0.0) {
+      double pvs = 0.0;
+      for (unsigned int c = 0; c < G; ++c) pvs += __ldcg(part_pv + c);
+      const double cc = 0.5 * tk * pvs;
+      int r = 0;
+      for (int i = first_owned(m0, cta, G); i < n; i += G, ++r) {
+        if (r % nwarp != warp) continue;
+        const double vi = __ldcg(vv + i);
+        const double wi = __ldcg(pp + i) - cc * vi;
+        double* row = A + (size_t)i * n;
+        for (int j = m0 + lane; j < n; j += 32) {
+          const double vj = __ldcg(vv + j);
+          const double wj = __ldcg(pp + j) - cc * vj;
+          row[j] -= vi * wj + wi * vj;
+        }
+        __syncwarp();
+        if (lane == 0) {
+          const double x = row[m0];   // column k + 1 of row i
+          if (i >= m0 + 2) nrm_part += x * x;
+          if (i == m0 + 1) *alpha_g = x;
+        }
+      }
+    } else {
+      int r = 0;
+      for (int i = first_owned(m0, cta, G); i < n; i += G, ++r) {
+        if (r % nwarp != warp || lane != 0) continue;
+        const double x = A[(size_t)i * n + m0];
+        if (i >= m0 + 2) nrm_part += x * x;
+        if (i == m0 + 1) *alpha_g = x;
+      }
+    }
+    if (lane == 0) red[warp] = nrm_part;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < nwarp; ++w) t += red[w];
+      part_norm[cta] = t;
+    }
+    live = grid_barrier(gb, G);
+  }
+  if (cta == 0 && threadIdx.x == 0) {
+    if (!live) {
+      if (status) atomicMax(status, RSX_ETIMEOUT);
+    } else {
+      if (n >= 2) {
+        d[n - 2] = __ldcg(A + (size_t)(n - 2) * n + (n - 2));
+        e[n - 2] = __ldcg(A + (size_t)(n - 1) * n + (n - 2));
+        if (n >= 3) tau[n - 2] = 0.0;
+      }
+      d[n - 1] = __ldcg(A + (size_t)(n - 1) * n + (n - 1));
+    }
+  }
+}
+
+// Multisection: one CTA per root; each round evaluates the Sturm count at blockDim.x
+// interior points of [lo, hi] and keeps the sub-interval where the count passes k.
+__global__ void __launch_bounds__(256) k_multisect(const double* __restrict__ d, const double* __restrict__ e, int n,
+                                                   double* __restrict__ w) {
+  const int k = blockIdx.x;
+  __shared__ double lo_sh, hi_sh;
+  __shared__ int first_sh;
+  if (threadIdx.x == 0) {
+    double lo = d[0], hi = d[0];
+    for (int i = 0; i < n; ++i) {
+      const double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i < n - 1 ? fabs(e[i]) : 0.0);
+      lo = fmin(lo, d[i] - r);
+      hi = fmax(hi, d[i] + r);
+    }
+    const double scale = fmax(fabs(lo), fabs(hi));
+    lo_sh = lo - 1e-12 * scale - 1e-300;
+    hi_sh = hi + 1e-12 * scale + 1e-300;
+  }
+  __syncthreads();
+  double emax = 0.0;
+  for (int i = 0; i < n - 1; ++i) emax = fmax(emax, fabs(e[i]));
   const double pivmin = fmax(2.2250738585072014e-308, 1e-300 * fmax(1.0, emax * emax));
-  lo -= 1e-12 * scale + 1e-300;
-  hi += 1e-12 * scale + 1e-300;
-  for (int it = 0; it < 200; ++it) {
-    const double mid = 0.5 * (lo + hi);
-    if (mid <= lo || mid >= hi) break;
-    if (sturm_count(d, e, n, mid, pivmin) > k)
-      hi = mid;
-    else
-      lo = mid;
+  const int T = blockDim.x;
+  for (int round = 0; round < 12; ++round) {
+    const double lo = lo_sh, hi = hi_sh;
+    if (!(hi - lo > 2.0 * 2.220446049250313e-16 * fmax(fabs(lo), fabs(hi)))) break;
+    const double x = lo + (hi - lo) * (double)(threadIdx.x + 1) / (double)(T + 1);
+    const bool above = sturm_count(d, e, n, x, pivmin) > k;
+    if (threadIdx.x == 0) first_sh = T;
+    __syncthreads();
+    if (above) atomicMin(&first_sh, (int)threadIdx.x);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const int f = first_sh;
+      const double nlo = (f == 0) ? lo : lo + (hi - lo) * (double)f / (double)(T + 1);
+      const double nhi = (f == T) ? hi : lo + (hi - lo) * (double)(f + 1) / (double)(T + 1);
+      lo_sh = nlo;
+      hi_sh = nhi;
+    }
+    __syncthreads();
   }
-  w[k] = 0.5 * (lo + hi);
+  if (threadIdx.x == 0) w[k] = 0.5 * (lo_sh + hi_sh);
 }
 
 // eigenvectors: one CTA per root, serial tridiagonal solves by thread 0, parallel
@@ -288,7 +501,12 @@ __global__ void __launch_bounds__(kEigThreads) k_eigvec(const double* __restrict
 
 }  // namespace
 
-size_t tda_work_doubles(int n, int nroots) { return (size_t)n * n + 10 * (size_t)n + (size_t)nroots * n + 8; }
+// start of the scratch that follows the eigenvector area (see tda_solve's layout)
+static double* y_end(double* tw, int n, int nroots) { return tw + 2 * n + (size_t)nroots * n + 5 * (size_t)n; }
+
+size_t tda_work_doubles(int n, int nroots) {
+  return (size_t)n * n + 14 * (size_t)n + (size_t)nroots * n + 4096;
+}
 
 int tda_solve(rsx_ctx* c, const double* eo, int no, const double* ev, int nv, const double* K, const double* Kd,
               double dm, int nroots, double* omega, double* X, double* work, cudaStream_t s) {
@@ -302,8 +520,23 @@ int tda_solve(rsx_ctx* c, const double* eo, int no, const double* ev, int nv, co
   (void)y;
   ProfScope ps(c, kKEig, s);
   k_tda_assemble<<<256, 256, 0, s>>>(eo, no, ev, nv, K, Kd, dm, A);
-  k_tridiagonalise<<<1, kEigThreads, 0, s>>>(A, n, d, e, tau, tw);
-  k_bisect<<<(nroots + 127) / 128, 128, 0, s>>>(d, e, n, nroots, omega);
+  // cooperative multi-CTA reduction when the device supports it, one CTA otherwise
+  int coop = 0, per_sm = 0;
+  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, c->device);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tridiag_coop, 256, 0);
+  const int G = std::min(std::min(c->nsm * std::max(per_sm, 0), 128), std::max(1, n / 2));
+  if (coop && per_sm > 0 && n >= 64) {
+    double* scr = y_end(tw, n, nroots);            // v, p, partials, alpha
+    GridBar* gb = reinterpret_cast<GridBar*>(scr + 2 * n + 2 * 1024 + 2);
+    cudaMemsetAsync(gb, 0, sizeof(GridBar), s);
+    void* args[] = {(void*)&A, (void*)&n, (void*)&d, (void*)&e, (void*)&tau, (void*)&scr, (void*)&gb,
+                    (void*)&c->status};
+    cudaError_t err = cudaLaunchCooperativeKernel((const void*)k_tridiag_coop, dim3(G), dim3(256), args, 0, s);
+    if (err != cudaSuccess) return check_cuda(c, err, "cooperative tridiagonalisation");
+  } else {
+    k_tridiagonalise<<<1, kEigThreads, 0, s>>>(A, n, d, e, tau, tw);
+  }
+  k_multisect<<<nroots, 256, 0, s>>>(d, e, n, omega);
   if (X) {
     // eigvec scratch: 5 n doubles after the T-basis vectors
     double* yv = tw + 2 * n;

@@ -308,6 +308,10 @@ def run_rsx(args, rank, local_rank, world):
     if rank == 0 and not args.skip_casida:
         out["casida"] = casida_bench(args, dev, local_rank, peaks)
 
+    # ---- uneven molecule batch, rank 0
+    if rank == 0 and not args.skip_batch:
+        out["batch"] = batch_bench(args, dev, local_rank, peaks)
+
     # ---- CPU oracle baseline (rank 0, N = 1 only)
     if rank == 0 and world == 1 and not args.skip_cpu:
         out["cpu_baseline"] = cpu_baseline(s, nsolve=args.cpu_solves)
@@ -390,6 +394,47 @@ def casida_bench(args, dev, local_rank, peaks):
     return out
 
 
+def batch_bench(args, dev, local_rank, peaks):
+    """Uneven batch: 64 molecules, edges from {48,64,80,96,112}, N_occ ~ U{2..24}, h 0.2;
+    exchange apply (psi = phi) + ACE build of every molecule in persistent launches
+    replayed from a CUDA graph."""
+    from paper_2405_01522_gb300 import rsx
+    desc = inputs.uneven_batch(nmol=args.batch_mols)
+    t0 = time.perf_counter()
+    mols = [inputs.batched_system(n=e, h=0.2, nocc=k, npsi=0, seed=sd) for e, k, sd in desc]
+    gen_s = time.perf_counter() - t0
+    b = rsx.Batch([e for e, _, _ in desc], [k for _, k, _ in desc], 0.2, device=local_rank)
+    phi = [torch.from_numpy(m.phi).float().to(dev) for m in mols]
+    W = [torch.empty_like(p) for p in phi]
+    xi = [torch.empty_like(p) for p in phi]
+    b.bind(phi, W, xi)
+    b.run()
+    b.sync()
+    reps = 3
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    e[0].record()
+    for _ in range(reps):
+        b.run()
+    e[1].record()
+    torch.cuda.synchronize()
+    ms = e[0].elapsed_time(e[1]) / reps
+    solves = sum(k * (k + 1) // 2 for _, k, _ in desc)
+    # algorithmic bytes of the three passes (intermediates written once, read/written by
+    # pass 2, read by pass 3; orbitals read, W written)
+    byts = 0
+    for ed, k, _ in desc:
+        inter = (ed + 1) * ed * ed * 8
+        npairs = k * (k + 1) // 2
+        byts += 4 * npairs * inter + 3 * k * ed ** 3 * 4
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    ach = byts / (ms / 1e3) / 1e9
+    b.close()
+    return {"workload": f"{len(desc)} molecules, edges from {{48,64,80,96,112}}, N_occ U{{2..24}}, h=0.2: "
+                        "exchange apply (psi = phi) + ACE build each, persistent launches in one CUDA graph",
+            "solves_per_batch": solves, "ms_per_batch": round(ms, 3), "solves_per_s": round(solves / (ms / 1e3), 1),
+            "hbm_model_gbs": round(ach, 1), "hbm_frac": round(ach / hbm, 4), "input_generation_s": round(gen_s, 1)}
+
+
 def cpu_baseline(s, nsolve=16):
     """The FP64 oracle as it stands, on the host, for a bounded sample of the workload:
     the exchange action on trial function 0 from the first `nsolve` orbitals."""
@@ -439,6 +484,8 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--cpu-solves", type=int, default=16)
     ap.add_argument("--skip-casida", action="store_true")
+    ap.add_argument("--skip-batch", action="store_true")
+    ap.add_argument("--batch-mols", type=int, default=64)
     ap.add_argument("--casida-only", action="store_true", help="only the Casida section (profiling captures)")
     ap.add_argument("--casida-edge", type=int, default=80, help="box edge of the Casida case")
     ap.add_argument("--nocc", type=int, default=16, help="smaller cases for profiling captures only")

@@ -138,6 +138,26 @@ int rsx_casida_solve(rsx_ctx* ctx, const double* eps_occ, int nocc, const double
                      const double* K, const double* Kd, double delta_M, int nroots, double* omega, double* X,
                      void* stream);
 
+/* ---- Uneven batch of independent molecules (one persistent launch per FFT pass under a
+ * captured CUDA graph).  For every molecule m (cubic box of edge edges[m] in
+ * {48, 64, 80, 96, 112}, spacing h, nocc[m] <= 32 orbitals, FP32):
+ *   W_m  = Vx[phi_m] phi_m   (Eq. 2 with psi = phi; nocc(nocc+1)/2 pair solves)
+ *   xi_m = ACE projectors of Eqs. 11-12 (M_m, -M_m = L L^T in FP64, xi_m = L^-1 W_m).
+ * rsx_batch_create plans the work queues (largest molecules first), builds the kernel
+ * tables of every distinct edge and allocates all pair intermediates.  rsx_batch_bind
+ * takes host arrays of nmol device pointers (phi[m]: [nocc][edge^3], W[m], xi[m] same
+ * shape, not aliasing) and may be called again with new arrays.  rsx_batch_run records
+ * the launches into a CUDA graph on its first call and replays the graph afterwards.
+ * rsx_batch_sync_status synchronises and reports deferred errors (RSX_ENOTPD).
+ * Errors: RSX_EINVAL, RSX_EUNSUPPORTED (edge), RSX_ENOMEM, RSX_ECUDA. */
+typedef struct rsx_batch rsx_batch;
+int rsx_batch_create(rsx_batch** batch, int nmol, const int* edges, const int* nocc, double h, int device);
+int rsx_batch_bind(rsx_batch* batch, const void* const* phi, void* const* W, void* const* xi);
+int rsx_batch_run(rsx_batch* batch, void* stream);
+int rsx_batch_sync_status(rsx_batch* batch, void* stream);
+const char* rsx_batch_last_error(const rsx_batch* batch);
+int rsx_batch_destroy(rsx_batch* batch);
+
 /* Split-BF16 symmetric contraction on the tensor cores, the K contraction of
  * rsx_casida_K as a standalone building block: C = H H^T + H L^T + L H^T, i.e. S S^T for a
  * panel S = H + L split into bf16 high and low parts (FP32 accumulation, FP64 split-K

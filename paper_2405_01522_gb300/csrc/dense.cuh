@@ -25,4 +25,45 @@ cudaError_t launch_combine(const R* C, int no, int ni, const R* X, size_t N, R* 
 template <typename R>
 cudaError_t launch_pair_products(const R* A, int na, const R* B, int nb, size_t N, R* rho, cudaStream_t s);
 
+// Block-wide FP64 Cholesky of B (k x k, shared memory, = -M symmetrised) into L (lower,
+// shared memory) and L^{-1} written over B.  Returns true if every pivot was > 0
+// (on failure the pivots are replaced by 1 so the arithmetic stays finite).
+__device__ __forceinline__ bool chol_linv_block(double* B, double* L, int k) {
+  __shared__ int bad_sh;
+  if (threadIdx.x == 0) bad_sh = 0;
+  for (int i = threadIdx.x; i < k * k; i += blockDim.x) L[i] = 0.0;
+  __syncthreads();
+  for (int j = 0; j < k; ++j) {
+    if (threadIdx.x == 0) {
+      double d = B[j * k + j];
+      for (int p = 0; p < j; ++p) d -= L[j * k + p] * L[j * k + p];
+      if (!(d > 0.0)) {
+        bad_sh = 1;
+        d = 1.0;
+      }
+      L[j * k + j] = sqrt(d);
+    }
+    __syncthreads();
+    for (int i = j + 1 + threadIdx.x; i < k; i += blockDim.x) {
+      double s = B[i * k + j];
+      for (int p = 0; p < j; ++p) s -= L[i * k + p] * L[j * k + p];
+      L[i * k + j] = s / L[j * k + j];
+    }
+    __syncthreads();
+  }
+  for (int c = threadIdx.x; c < k; c += blockDim.x) {
+    for (int i = 0; i < k; ++i) {
+      if (i < c) {
+        B[i * k + c] = 0.0;
+        continue;
+      }
+      double s = (i == c) ? 1.0 : 0.0;
+      for (int p = c; p < i; ++p) s -= L[i * k + p] * B[p * k + c];
+      B[i * k + c] = s / L[i * k + i];
+    }
+  }
+  __syncthreads();
+  return bad_sh == 0;
+}
+
 }  // namespace rsx

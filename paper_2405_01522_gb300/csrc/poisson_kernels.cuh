@@ -57,32 +57,23 @@ __device__ __forceinline__ void stage2_load(Cx<R> (&u)[16], int s, const Cx<R>* 
 }
 
 // ---------------------------------------------------------------------------------
-// pass 1: x forward (r2c via row pairs).  CTA = (pair q, plane z, 32 rows).
+// pass 1: x forward (r2c via row pairs).  One item = (pair q, plane z, 32 rows).
+// pass1_item is the body (all threads of the CTA call it with the same item); the
+// intermediate of the pair is at `dst_pair` (layout [kx][z][y]).
 template <typename R, int AX>
-__global__ void __launch_bounds__(kThreads) k_pass1(Geom g, PairMap<R> pm, int q0, Cx<R>* __restrict__ inter,
-                                                    const Cx<R>* __restrict__ twx) {
+__device__ __forceinline__ void pass1_item(const Geom& g, const R* f1, const R* f2, int z, int yblk,
+                                           Cx<R>* __restrict__ dst_pair, const Cx<R>* __restrict__ twx,
+                                           unsigned char* smem_raw) {
   constexpr int L = 16 * AX;
   constexpr int SP = AX * kScrPitch;
   constexpr int H = L / 2 + 1;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   Cx<R>* scr = reinterpret_cast<Cx<R>*>(smem_raw);
   Cx<R>* xs = scr + kLinesPerCta * SP;  // [H][kXsPitch]
-
-  const int nyb = (g.ny + kRowsPerCta - 1) / kRowsPerCta;
-  int b = blockIdx.x;
-  const int yblk = b % nyb;
-  b /= nyb;
-  const int z = b % g.nz;
-  const int ql = b / g.nz;  // local pair slot
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int t = lane & 15, line = warp * 2 + (lane >> 4);
   const int y0 = yblk * kRowsPerCta;
   const int ya = y0 + 2 * line, yb = ya + 1;
   Cx<R>* sc = scr + line * SP;
-
-  const R* f1;
-  const R* f2;
-  pm.pair(q0 + ql, f1, f2);
   const size_t plane = (size_t)z * g.ny * g.nx;
   f1 += plane;
   f2 += plane;
@@ -120,12 +111,29 @@ __global__ void __launch_bounds__(kThreads) k_pass1(Geom g, PairMap<R> pm, int q
   }
   __syncthreads();
   const int nrow = min(kRowsPerCta, g.ny - y0);
-  Cx<R>* dst = inter + (size_t)ql * g.inter_elems() + (size_t)z * g.ny + y0;
+  Cx<R>* dst = dst_pair + (size_t)z * g.ny + y0;
   const size_t kstride = (size_t)g.nz * g.ny;
   for (int e = threadIdx.x; e < H * kRowsPerCta; e += kThreads) {
     const int kx = e / kRowsPerCta, r = e - kx * kRowsPerCta;
     if (r < nrow) dst[(size_t)kx * kstride + r] = xs[kx * kXsPitch + r];
   }
+  __syncthreads();
+}
+
+template <typename R, int AX>
+__global__ void __launch_bounds__(kThreads) k_pass1(Geom g, PairMap<R> pm, int q0, Cx<R>* __restrict__ inter,
+                                                    const Cx<R>* __restrict__ twx) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nyb = (g.ny + kRowsPerCta - 1) / kRowsPerCta;
+  int b = blockIdx.x;
+  const int yblk = b % nyb;
+  b /= nyb;
+  const int z = b % g.nz;
+  const int ql = b / g.nz;  // local pair slot
+  const R* f1;
+  const R* f2;
+  pm.pair(q0 + ql, f1, f2);
+  pass1_item<R, AX>(g, f1, f2, z, yblk, inter + (size_t)ql * g.inter_elems(), twx, smem_raw);
 }
 
 // ---------------------------------------------------------------------------------
@@ -208,86 +216,95 @@ __device__ __forceinline__ void y_inverse(Cx<R>* D, int DP, int nz, int ny, cons
 }
 
 // pass 2: per (pair, kx) plane: y forward, z forward * vhat * z inverse, y inverse.
-// D lives in shared memory (DSMEM) or, when it does not fit, in a per-CTA slice of
-// global scratch.  Persistent grid over the work items (pair, kx).
-template <typename R, int AY, int AZ, bool DSMEM, int NT>
-__global__ void __launch_bounds__(NT, 1) k_pass2(Geom g, int nq, Cx<R>* __restrict__ inter,
-                                                    const Cx<R>* __restrict__ twy,
-                                                    const Cx<R>* __restrict__ twz,
-                                                    const R* __restrict__ vhat, R* gscratch) {
+// pass2_plane is the body for one plane P (nz x ny, contiguous) at column kx; D is the
+// (nz x My) work plane (row pitch My + 1) and scr the line scratch.
+template <typename R, int AY, int AZ, int NT>
+__device__ __forceinline__ void pass2_plane(const Geom& g, Cx<R>* P, int kx, const Cx<R>* __restrict__ twy,
+                                            const Cx<R>* __restrict__ twz, const R* __restrict__ vhat, Cx<R>* D,
+                                            Cx<R>* scr) {
   constexpr int LY = 16 * AY;
   constexpr int LZ = 16 * AZ;
   constexpr int AMAX = AY > AZ ? AY : AZ;
   constexpr int SP = AMAX * kScrPitch;
   constexpr int DP = LY + 1;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  Cx<R>* scr = reinterpret_cast<Cx<R>*>(smem_raw);
-  Cx<R>* D = DSMEM ? scr + (NT / 16) * SP
-                   : reinterpret_cast<Cx<R>*>(gscratch) + (size_t)blockIdx.x * g.nz * DP;
-
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int t = lane & 15, line = warp * 2 + (lane >> 4);
   Cx<R>* sc = scr + line * SP;
   constexpr int Hy = LY / 2 + 1, Hz = LZ / 2 + 1;
+  load_plane<NT>(D, DP, P, g.nz, g.ny);
+  __syncthreads();
+  y_forward<R, AY, NT>(D, DP, g.nz, g.ny, twy, sc);
+  __syncthreads();
+  // z forward, multiply, z inverse on columns ky (LY is a multiple of 16: uniform trips)
+  const R* vrow = vhat + (size_t)kx * Hy * Hz;
+  for (int ky = line; ky < LY; ky += NT / 16) {
+    const int iy = ky <= LY / 2 ? ky : LY - ky;
+    const R* vcol = vrow + (size_t)iy * Hz;
+    Cx<R> v[AZ];
+#pragma unroll
+    for (int a = 0; a < AZ; ++a) {
+      const int z = t + 16 * a;
+      v[a] = (z < g.nz) ? D[z * DP + ky] : cx<R>(R(0), R(0));
+    }
+    stage1_store<AZ, -1>(v, t, twz, sc);
+    __syncwarp();
+    Cx<R> u[16];
+    if (t < AZ) stage2_load(u, t, sc);
+    __syncwarp();
+    if (t < AZ) {
+      Dft<16, -1>::run(u);
+#pragma unroll
+      for (int k2 = 0; k2 < 16; ++k2) {
+        const int kz = t + AZ * k2;
+        const R m = __ldg(vcol + (kz <= LZ / 2 ? kz : LZ - kz));
+        u[k2] = cx<R>(u[k2].x * m, u[k2].y * m);
+      }
+      Dft<16, 1>::run(u);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        Cx<R> w = twz[j * AZ + t];
+        w.y = -w.y;
+        sc[t * kScrPitch + j] = cmul(u[j], w);
+      }
+    }
+    __syncwarp();
+    Cx<R> r[AZ];
+#pragma unroll
+    for (int k1 = 0; k1 < AZ; ++k1) r[k1] = sc[k1 * kScrPitch + t];
+    Dft<AZ, 1>::run(r);
+#pragma unroll
+    for (int a = 0; a < AZ; ++a) {
+      const int z = t + 16 * a;
+      if (z < g.nz) D[z * DP + ky] = r[a];
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+  y_inverse<R, AY, NT>(D, DP, g.nz, g.ny, twy, sc);
+  __syncthreads();
+  store_plane<NT>(D, DP, P, g.nz, g.ny);
+  __syncthreads();
+}
+
+// D lives in shared memory (DSMEM) or, when it does not fit, in a per-CTA slice of
+// global scratch.  Persistent grid over the work items (pair, kx).
+template <typename R, int AY, int AZ, bool DSMEM, int NT>
+__global__ void __launch_bounds__(NT, 1) k_pass2(Geom g, int nq, Cx<R>* __restrict__ inter,
+                                                 const Cx<R>* __restrict__ twy, const Cx<R>* __restrict__ twz,
+                                                 const R* __restrict__ vhat, R* gscratch) {
+  constexpr int AMAX = AY > AZ ? AY : AZ;
+  constexpr int SP = AMAX * kScrPitch;
+  constexpr int DP = 16 * AY + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Cx<R>* scr = reinterpret_cast<Cx<R>*>(smem_raw);
+  Cx<R>* D = DSMEM ? scr + (NT / 16) * SP
+                   : reinterpret_cast<Cx<R>*>(gscratch) + (size_t)blockIdx.x * g.nz * DP;
   const int nplane = g.nz * g.ny;
   const int nwork = nq * g.Hx;
-
   for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
     const int ql = w / g.Hx, kx = w - ql * g.Hx;
     Cx<R>* P = inter + (size_t)ql * g.inter_elems() + (size_t)kx * nplane;
-    load_plane<NT>(D, DP, P, g.nz, g.ny);
-    __syncthreads();
-    y_forward<R, AY, NT>(D, DP, g.nz, g.ny, twy, sc);
-    __syncthreads();
-    // z forward, multiply, z inverse on columns ky (LY is a multiple of 16: uniform trips)
-    const R* vrow = vhat + (size_t)kx * Hy * Hz;
-    for (int ky = line; ky < LY; ky += NT / 16) {
-      const int iy = ky <= LY / 2 ? ky : LY - ky;
-      const R* vcol = vrow + (size_t)iy * Hz;
-      Cx<R> v[AZ];
-#pragma unroll
-      for (int a = 0; a < AZ; ++a) {
-        const int z = t + 16 * a;
-        v[a] = (z < g.nz) ? D[z * DP + ky] : cx<R>(R(0), R(0));
-      }
-      stage1_store<AZ, -1>(v, t, twz, sc);
-      __syncwarp();
-      Cx<R> u[16];
-      if (t < AZ) stage2_load(u, t, sc);
-      __syncwarp();
-      if (t < AZ) {
-        Dft<16, -1>::run(u);
-#pragma unroll
-        for (int k2 = 0; k2 < 16; ++k2) {
-          const int kz = t + AZ * k2;
-          const R m = __ldg(vcol + (kz <= LZ / 2 ? kz : LZ - kz));
-          u[k2] = cx<R>(u[k2].x * m, u[k2].y * m);
-        }
-        Dft<16, 1>::run(u);
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          Cx<R> w = twz[j * AZ + t];
-          w.y = -w.y;
-          sc[t * kScrPitch + j] = cmul(u[j], w);
-        }
-      }
-      __syncwarp();
-      Cx<R> r[AZ];
-#pragma unroll
-      for (int k1 = 0; k1 < AZ; ++k1) r[k1] = sc[k1 * kScrPitch + t];
-      Dft<AZ, 1>::run(r);
-#pragma unroll
-      for (int a = 0; a < AZ; ++a) {
-        const int z = t + 16 * a;
-        if (z < g.nz) D[z * DP + ky] = r[a];
-      }
-      __syncwarp();
-    }
-    __syncthreads();
-    y_inverse<R, AY, NT>(D, DP, g.nz, g.ny, twy, sc);
-    __syncthreads();
-    store_plane<NT>(D, DP, P, g.nz, g.ny);
-    __syncthreads();
+    pass2_plane<R, AY, AZ, NT>(g, P, kx, twy, twz, vhat, D, scr);
   }
 }
 
@@ -372,27 +389,19 @@ __global__ void __launch_bounds__(kThreads) k_spectrum(Geom g, int nq, const Cx<
 
 // ---------------------------------------------------------------------------------
 // pass 3: x inverse (c2r via row pairs) of every pair in output p's list, and
-// out_p(z, y, x) = - sum_e partner_e(z, y, x) V_e(z, y, x).  CTA = (p, z, 32 rows).
+// out_p(z, y, x) = - sum_e partner_e(z, y, x) V_e(z, y, x).  One item = (p, z, 32 rows).
 // With pot != 0 the output p is the potential V of pair q = p itself (no partner, no sign).
+// pass3_item is the body; `out_p` is output p's array, `inter` the slot base of q0.
 template <typename R, int AX>
-__global__ void __launch_bounds__(kThreads) k_pass3(Geom g, PairMap<R> pm, int q0, int p0, int pot,
-                                                    const Cx<R>* __restrict__ inter,
-                                                    const Cx<R>* __restrict__ twx, R* __restrict__ out) {
+__device__ __forceinline__ void pass3_item(const Geom& g, const PairMap<R>& pm, int q0, int p, int z, int yblk,
+                                           int pot, const Cx<R>* __restrict__ inter, const Cx<R>* __restrict__ twx,
+                                           R* __restrict__ out_p, unsigned char* smem_raw) {
   constexpr int L = 16 * AX;
   constexpr int SP = AX * kScrPitch;
   constexpr int H = L / 2 + 1;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   Cx<R>* scr = reinterpret_cast<Cx<R>*>(smem_raw);
   Cx<R>* xs = scr + kLinesPerCta * SP;               // [H][kXsPitch]
   R* tile = reinterpret_cast<R*>(xs + H * kXsPitch);  // [32][nx]: partner, then result
-
-  const int nyb = (g.ny + kRowsPerCta - 1) / kRowsPerCta;
-  int b = blockIdx.x;
-  const int yblk = b % nyb;
-  b /= nyb;
-  const int z = b % g.nz;
-  const int pl = b / g.nz;
-  const int p = p0 + pl;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int t = lane & 15, line = warp * 2 + (lane >> 4);
   const int y0 = yblk * kRowsPerCta;
@@ -473,8 +482,23 @@ __global__ void __launch_bounds__(kThreads) k_pass3(Geom g, PairMap<R> pm, int q
     }
   }
   __syncthreads();
-  R* orow = out + (size_t)pl * g.N() + plane + (size_t)y0 * g.nx;
+  R* orow = out_p + plane + (size_t)y0 * g.nx;
   for (int i = threadIdx.x; i < nrow * g.nx; i += kThreads) orow[i] = tile[i];
+  __syncthreads();
+}
+
+template <typename R, int AX>
+__global__ void __launch_bounds__(kThreads) k_pass3(Geom g, PairMap<R> pm, int q0, int p0, int pot,
+                                                    const Cx<R>* __restrict__ inter,
+                                                    const Cx<R>* __restrict__ twx, R* __restrict__ out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nyb = (g.ny + kRowsPerCta - 1) / kRowsPerCta;
+  int b = blockIdx.x;
+  const int yblk = b % nyb;
+  b /= nyb;
+  const int z = b % g.nz;
+  const int pl = b / g.nz;
+  pass3_item<R, AX>(g, pm, q0, p0 + pl, z, yblk, pot, inter, twx, out + (size_t)pl * g.N(), smem_raw);
 }
 
 }  // namespace rsx

@@ -11,7 +11,8 @@ Grid: point (z, y, x) sits at r = ((x - nx/2) h, (y - ny/2) h, (z - nz/2) h); ar
 are laid out [orbital][z][y][x] with x fastest.  Orbitals are real s-type Gaussian
 sums  phi(r) = sum_g c_g exp(-alpha_g |r - R_g|^2), c ~ U[-1, 1].  Centres are drawn
 uniformly in a ball (rejection from the enclosing cube).  Orthonormal sets are made
-by modified Gram-Schmidt applied twice in FP64 under <f, g> = h^3 sum_r f g.
+by Gram-Schmidt with re-orthogonalisation (two projections per vector) in FP64 under
+<f, g> = h^3 sum_r f g.
 """
 from dataclasses import dataclass, field
 
@@ -59,21 +60,27 @@ def gaussian_sum(shape, h, terms):
     for c, alpha, (X, Y, Z) in terms:
         fx = np.exp(-alpha * (ax - X) ** 2)
         fy = np.exp(-alpha * (ay - Y) ** 2)
-        fz = np.exp(-alpha * (az - Z) ** 2)
-        out += c * fz[:, None, None] * fy[None, :, None] * fx[None, None, :]
+        fz = c * np.exp(-alpha * (az - Z) ** 2)
+        out += fz[:, None, None] * np.outer(fy, fx)[None, :, :]
     return out
 
 
 def gram_schmidt(f, h, passes=2):
-    """Modified Gram-Schmidt, ``passes`` times, FP64, under <f, g> = h^3 sum f g."""
+    """Gram-Schmidt orthonormalisation in FP64 under <f, g> = h^3 sum f g.
+
+    Vector by vector: each new vector is projected against all previous ones
+    ``passes`` times (classical Gram-Schmidt with re-orthogonalisation, as stable as
+    modified Gram-Schmidt applied twice), then normalised.
+    """
     f = np.array(f, dtype=np.float64, copy=True)
     k = f.shape[0]
     v = f.reshape(k, -1)
-    for _ in range(passes):
-        for i in range(k):
-            for j in range(i):
-                v[i] -= (h ** 3 * np.dot(v[j], v[i])) * v[j]
-            v[i] /= np.sqrt(h ** 3 * np.dot(v[i], v[i]))
+    for i in range(k):
+        for _ in range(passes):
+            if i:
+                c = h ** 3 * (v[:i] @ v[i])
+                v[i] -= c @ v[:i]
+        v[i] /= np.sqrt(h ** 3 * np.dot(v[i], v[i]))
     return f
 
 

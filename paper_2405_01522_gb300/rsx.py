@@ -35,6 +35,12 @@ SIGNATURES = {
     "rsx_casida_Kd": [_P, _P, _I, _P, _I, _P, _P],
     "rsx_casida_solve": [_P, _P, _I, _P, _I, _P, _P, _D, _I, _P, _P, _P],
     "rsx_syrk_bf16x3": [_P, _P, _P, _I, ctypes.c_longlong, _P, _P],
+    "rsx_batch_create": [ctypes.POINTER(_P), _I, ctypes.POINTER(_I), ctypes.POINTER(_I), _D, _I],
+    "rsx_batch_bind": [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P)],
+    "rsx_batch_run": [_P, _P],
+    "rsx_batch_sync_status": [_P, _P],
+    "rsx_batch_last_error": [_P],
+    "rsx_batch_destroy": [_P],
     "rsx_sync_status": [_P, _P],
     "rsx_profile_enable": [_P, _I],
     "rsx_profile_reset": [_P],
@@ -62,7 +68,8 @@ def load(path=LIB_PATH):
         for name, args in SIGNATURES.items():
             f = getattr(lib, name)
             f.argtypes = args
-            f.restype = ctypes.c_char_p if name in ("rsx_last_error", "rsx_kernel_name") else ctypes.c_int
+            f.restype = (ctypes.c_char_p if name in ("rsx_last_error", "rsx_kernel_name", "rsx_batch_last_error")
+                         else ctypes.c_int)
         _lib = lib
     return _lib
 
@@ -207,3 +214,55 @@ class Context:
 
     def sync(self, stream=None):
         self._check(self.lib.rsx_sync_status(self.handle, _stream(stream)))
+
+
+class Batch:
+    """Uneven batch of molecules: W_m = Vx[phi_m] phi_m and ACE projectors xi_m for all m,
+    in persistent launches replayed from a captured CUDA graph (FP32)."""
+
+    def __init__(self, edges, nocc, h, device=0):
+        self.lib = load()
+        self.edges = [int(e) for e in edges]
+        self.nocc = [int(k) for k in nocc]
+        self.nmol = len(self.edges)
+        self.device = torch.device("cuda", device)
+        h_ = ctypes.c_void_p()
+        E = (ctypes.c_int * self.nmol)(*self.edges)
+        K = (ctypes.c_int * self.nmol)(*self.nocc)
+        code = self.lib.rsx_batch_create(ctypes.byref(h_), self.nmol, E, K, float(h), device)
+        if code != RSX_OK:
+            raise RsxError(code, "rsx_batch_create failed")
+        self.handle = h_
+        self._bound = None
+
+    def _check(self, code):
+        if code != RSX_OK:
+            raise RsxError(code, self.lib.rsx_batch_last_error(self.handle).decode())
+
+    def bind(self, phi, W, xi):
+        """phi, W, xi: lists of contiguous float32 CUDA tensors [nocc_m, e, e, e]."""
+        for m in range(self.nmol):
+            shape = (self.nocc[m],) + (self.edges[m],) * 3
+            for t in (phi[m], W[m], xi[m]):
+                if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous() and tuple(t.shape) == shape):
+                    raise ValueError(f"molecule {m}: need contiguous float32 CUDA tensors of shape {shape}")
+        arr = lambda ts: (ctypes.c_void_p * self.nmol)(*[t.data_ptr() for t in ts])
+        self._check(self.lib.rsx_batch_bind(self.handle, arr(phi), arr(W), arr(xi)))
+        self._bound = (phi, W, xi)
+
+    def run(self, stream=None):
+        self._check(self.lib.rsx_batch_run(self.handle, _stream(stream)))
+
+    def sync(self, stream=None):
+        self._check(self.lib.rsx_batch_sync_status(self.handle, _stream(stream)))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.rsx_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

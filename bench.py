@@ -147,6 +147,7 @@ def run_rsx(args, rank, local_rank, world):
         ctx.ace_build(phi, xi=xi)
         ctx.ace_apply(xi, psi, out=va)
 
+    tuning = ctx.autotune(NOCC, NPSI) if not args.no_tune else None   # outside the timed region
     for _ in range(args.warmup):
         step()
     ctx.sync()
@@ -261,7 +262,7 @@ def run_rsx(args, rank, local_rank, world):
                       "nocc": NOCC, "npsi": NPSI, "solves_per_step": SOLVES_PER_STEP,
                       "l2": "no flush: inputs (170 MB) and FFT intermediates (3.7 GB) exceed the 129 MB L2",
                       "parallelism": f"replicas x{world}"},
-           "roofline": roof, "kernels": kernels, "gpu_launches": launches, "clocks": clk, "e2e": e2e,
+           "tuning": tuning, "roofline": roof, "kernels": kernels, "gpu_launches": launches, "clocks": clk, "e2e": e2e,
            "ace_build_ms": round(ace_ms, 4)}
 
     # ---- FP64 plain form of the same step, and FP32 accuracy against it
@@ -485,6 +486,7 @@ def main():
     ap.add_argument("--cpu-solves", type=int, default=16)
     ap.add_argument("--skip-casida", action="store_true")
     ap.add_argument("--skip-batch", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (default knobs)")
     ap.add_argument("--batch-mols", type=int, default=64)
     ap.add_argument("--casida-only", action="store_true", help="only the Casida section (profiling captures)")
     ap.add_argument("--casida-edge", type=int, default=80, help="box edge of the Casida case")

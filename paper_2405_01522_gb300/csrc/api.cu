@@ -229,6 +229,7 @@ int exchange_apply(rsx_ctx* c, const void* phi, int nocc, const void* psi, int n
   // outputs per chunk: all of p's nocc pairs must be resident for pass 3
   long long pmax = (long long)(c->work_limit / ((size_t)nocc * per_pair));
   if (pmax < 1) return set_error(c, RSX_ENOMEM, "workspace limit below one output orbital's pairs");
+  if (c->chunk_outputs > 0 && c->chunk_outputs < pmax) pmax = c->chunk_outputs;
   for (int p0 = 0; p0 < npsi; p0 += (int)pmax) {
     const int np = (int)std::min<long long>(pmax, npsi - p0);
     int rc = solve_pairs<R>(c, pm, p0 * nocc, np * nocc, p0, np, (R*)out + (size_t)p0 * N, s);

@@ -37,6 +37,7 @@ struct rsx_ctx {
   void* eig_work = nullptr; size_t eig_work_bytes = 0;
   void* gscr_kd = nullptr; size_t gscr_kd_bytes = 0;     // occupied pair potentials (K_d)
   int p2_occ[2] = {0, 0};
+  int chunk_outputs = 0;   // tuning: output orbitals per exchange chunk (0 = as many as fit)
   // launch profiler: events recorded around every kernel while enabled
   bool prof_on = false;
   struct ProfRec { int id; cudaEvent_t a, b; };

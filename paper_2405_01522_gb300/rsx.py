@@ -41,6 +41,8 @@ SIGNATURES = {
     "rsx_batch_sync_status": [_P, _P],
     "rsx_batch_last_error": [_P],
     "rsx_batch_destroy": [_P],
+    "rsx_autotune": [_P, _I, _I, ctypes.c_char_p, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_D)],
+    "rsx_set_tuning": [_P, _I, _I],
     "rsx_sync_status": [_P, _P],
     "rsx_profile_enable": [_P, _I],
     "rsx_profile_reset": [_P],
@@ -128,6 +130,17 @@ class Context:
 
     def set_workspace_limit(self, nbytes):
         self._check(self.lib.rsx_set_workspace_limit(self.handle, int(nbytes)))
+
+    def autotune(self, nocc, npsi, cache=None):
+        """Time the exchange-path candidates on the device and apply the fastest."""
+        p2, ch, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        self._check(self.lib.rsx_autotune(self.handle, int(nocc), int(npsi),
+                                          cache.encode() if cache else None,
+                                          ctypes.byref(p2), ctypes.byref(ch), ctypes.byref(ms)))
+        return {"p2_threads": p2.value, "chunk_outputs": ch.value, "best_ms": ms.value}
+
+    def set_tuning(self, p2_threads=256, chunk_outputs=0):
+        self._check(self.lib.rsx_set_tuning(self.handle, int(p2_threads), int(chunk_outputs)))
 
     def pair_densities(self, a, b, out=None, stream=None):
         na, nb = self._orb(a, "a"), self._orb(b, "b")

@@ -171,6 +171,47 @@ int rsx_batch_sync_status(rsx_batch* batch, void* stream);
 const char* rsx_batch_last_error(const rsx_batch* batch);
 int rsx_batch_destroy(rsx_batch* batch);
 
+/* ---- Plain block eigensolver and learned preconditioner (the paper's eigensolvers are
+ * CG and preconditioned Lanczos, Sec. 3.1; the preconditioners and the network are not in
+ * the paper).  H = -1/2 Lap + V with the fourth-order finite-difference Laplacian and
+ * zero boundary values, on an n^3 box of spacing h, FP32 orbitals.
+ * rsx_eig_create: V device [n^3] (kept by pointer), vscale multiplies V in the network's
+ *   second input channel, nband <= 21 bands.
+ * rsx_eig_init: starting orbitals psi0 [nband][n^3] (device), Rayleigh-Ritz on them.
+ * rsx_eig_step: one block step: residual R = H Psi - Psi theta, W = (K + T)^-1 R by
+ *   jacobi_sweeps damped-Jacobi sweeps (K = -1/2 Lap, T the orbital kinetic energy), plus
+ *   the network's directions |R| net(R/|R|, vscale V) when net is not NULL; Rayleigh-Ritz
+ *   on [Psi, W]; theta_host[nband] receives the Ritz values.  Synchronises the stream.
+ * rsx_eig_orbitals / rsx_eig_residual copy the current orbitals / last residual out. */
+typedef struct rsx_eig rsx_eig;
+typedef struct rsx_net rsx_net;
+int rsx_eig_create(rsx_eig** eig, int n, double h, const float* V, float vscale, int nband, int device);
+int rsx_eig_init(rsx_eig* eig, const float* psi0, void* stream);
+int rsx_eig_step(rsx_eig* eig, rsx_net* net, int jacobi_sweeps, double* theta_host, void* stream);
+int rsx_eig_orbitals(rsx_eig* eig, float* psi_out, void* stream);
+int rsx_eig_residual(rsx_eig* eig, float* r_out, void* stream);
+const char* rsx_eig_last_error(const rsx_eig* eig);
+int rsx_eig_destroy(rsx_eig* eig);
+
+/* Learned preconditioner network: conv3d(2 -> 16) ReLU conv3d(16 -> 16) ReLU conv3d(16 -> 1),
+ * 3^3 kernels, zero padding 1, weights used in bf16, FP32 activations and accumulation.
+ * Parameters (rsx_net_param_count() floats): w1 [16][2][27], b1 [16], w2 [16][16][27],
+ * b2 [16], w3 [1][16][27], b3 [1]; taps t = 9 dz + 3 dy + dx.  Inputs x: device
+ * [B][2][D][H][W]; outputs [B][D][H][W].  Loss: mean over voxels at least `border` from
+ * every face of (net(x) - target)^2.  rsx_net_loss_grad returns loss and gradients to the
+ * host; rsx_net_train_step does one Adam step (beta 0.9 / 0.999, eps 1e-8). */
+int rsx_net_create(rsx_net** net, int device);
+int rsx_net_param_count(void);
+int rsx_net_set_params(rsx_net* net, const float* host_params, int count);
+int rsx_net_get_params(rsx_net* net, float* host_params, int count);
+int rsx_net_forward(rsx_net* net, const float* x, int B, int D, int H, int W, float* out, void* stream);
+int rsx_net_loss_grad(rsx_net* net, const float* x, const float* target, int B, int D, int H, int W, int border,
+                      double* loss_host, float* grad_host, void* stream);
+int rsx_net_train_step(rsx_net* net, const float* x, const float* target, int B, int D, int H, int W, int border,
+                       float lr, double* loss_host, void* stream);
+const char* rsx_net_last_error(const rsx_net* net);
+int rsx_net_destroy(rsx_net* net);
+
 /* Split-BF16 symmetric contraction on the tensor cores, the K contraction of
  * rsx_casida_K as a standalone building block: C = H H^T + H L^T + L H^T, i.e. S S^T for a
  * panel S = H + L split into bf16 high and low parts (FP32 accumulation, FP64 split-K

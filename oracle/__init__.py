@@ -17,6 +17,8 @@ coulomb   discrete Coulomb kernel and the isolated Poisson solve (FFT and direct
 exchange  pair densities, exact-exchange action, exchange / Hartree energies
 ace       adaptively compressed exchange: build and apply
 casida    coupling matrices K and K_d, TDA matrix, eigen-solve
+eigensolver  FD4 Hamiltonian, kinetic-energy preconditioner, Rayleigh-Ritz step, and the
+          3-layer conv3d network of the learned preconditioner with its gradients
 
 Parity status: every public function here is pinned by ``tests/test_oracle_pins.py``
 against closed forms, brute-force sums or invariants; none is "parity unpinned".

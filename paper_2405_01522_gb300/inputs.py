@@ -211,3 +211,28 @@ def uneven_batch(nmol=64, edges=(48, 64, 80, 96, 112), h=0.2, nocc_range=(2, 24)
         no = rng.integer(*nocc_range)
         out.append((e, no, (seed * 1000003 + k + 1) & _MASK))
     return out
+
+
+def model_potential(n=96, h=0.2, natoms=4, Z=4.0, rc=0.6, radius=2.5, seed=0):
+    """Smooth attractive potential of ``natoms`` pseudo-nuclei (input for the eigensolver):
+    V(r) = - sum_A Z erf(|r - R_A| / rc) / |r - R_A|, centres uniform in a ball of
+    ``radius`` bohr (seeded splitmix64), value -2 Z / (sqrt(pi) rc) at a centre."""
+    from scipy.special import erf
+    rng = SplitMix64(seed)
+    az, ay, ax = grid_axes((n, n, n), h)
+    V = np.zeros((n, n, n))
+    for _ in range(natoms):
+        X, Y, Zc = rng.in_ball(radius)
+        d = np.sqrt((az[:, None, None] - Zc) ** 2 + (ay[None, :, None] - Y) ** 2 + (ax[None, None, :] - X) ** 2)
+        with np.errstate(invalid="ignore", divide="ignore"):
+            v = np.where(d > 1e-12, erf(d / rc) / np.where(d > 1e-12, d, 1.0), 2.0 / (np.sqrt(np.pi) * rc))
+        V -= Z * v
+    return V.astype(np.float32).astype(np.float64)
+
+
+def starting_orbitals(n=96, h=0.2, nband=16, radius=2.5, seed=0):
+    """Linearly independent Gaussian-sum starting guesses (3 Gaussians each, exponents
+    U[0.3, 1.5]), normalised, not orthogonalised."""
+    rng = SplitMix64(seed)
+    f = orbitals_independent(rng, (n, n, n), h, nband, 3, (0.3, 1.5), radius)
+    return round_f32(normalise(f, h))

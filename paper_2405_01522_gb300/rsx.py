@@ -35,6 +35,22 @@ SIGNATURES = {
     "rsx_casida_Kd": [_P, _P, _I, _P, _I, _P, _P],
     "rsx_casida_solve": [_P, _P, _I, _P, _I, _P, _P, _D, _I, _P, _P, _P],
     "rsx_syrk_bf16x3": [_P, _P, _P, _I, ctypes.c_longlong, _P, _P],
+    "rsx_eig_create": [ctypes.POINTER(_P), _I, _D, _P, ctypes.c_float, _I, _I],
+    "rsx_eig_init": [_P, _P, _P],
+    "rsx_eig_step": [_P, _P, _I, ctypes.POINTER(_D), _P],
+    "rsx_eig_orbitals": [_P, _P, _P],
+    "rsx_eig_residual": [_P, _P, _P],
+    "rsx_eig_last_error": [_P],
+    "rsx_eig_destroy": [_P],
+    "rsx_net_create": [ctypes.POINTER(_P), _I],
+    "rsx_net_param_count": [],
+    "rsx_net_set_params": [_P, ctypes.POINTER(ctypes.c_float), _I],
+    "rsx_net_get_params": [_P, ctypes.POINTER(ctypes.c_float), _I],
+    "rsx_net_forward": [_P, _P, _I, _I, _I, _I, _P, _P],
+    "rsx_net_loss_grad": [_P, _P, _P, _I, _I, _I, _I, _I, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_float), _P],
+    "rsx_net_train_step": [_P, _P, _P, _I, _I, _I, _I, _I, ctypes.c_float, ctypes.POINTER(_D), _P],
+    "rsx_net_last_error": [_P],
+    "rsx_net_destroy": [_P],
     "rsx_batch_create": [ctypes.POINTER(_P), _I, ctypes.POINTER(_I), ctypes.POINTER(_I), _D, _I],
     "rsx_batch_bind": [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P)],
     "rsx_batch_run": [_P, _P],
@@ -70,7 +86,8 @@ def load(path=LIB_PATH):
         for name, args in SIGNATURES.items():
             f = getattr(lib, name)
             f.argtypes = args
-            f.restype = (ctypes.c_char_p if name in ("rsx_last_error", "rsx_kernel_name", "rsx_batch_last_error")
+            f.restype = (ctypes.c_char_p if name in ("rsx_last_error", "rsx_kernel_name", "rsx_batch_last_error",
+                                                     "rsx_eig_last_error", "rsx_net_last_error")
                          else ctypes.c_int)
         _lib = lib
     return _lib
@@ -272,6 +289,123 @@ class Batch:
     def close(self):
         if getattr(self, "handle", None):
             self.lib.rsx_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Net:
+    """The learned preconditioner network (3 conv3d layers, bf16 weights, FP32 accumulation)."""
+
+    def __init__(self, params=None, device=0):
+        import numpy as np
+        self.lib = load()
+        self.device = torch.device("cuda", device)
+        h_ = ctypes.c_void_p()
+        code = self.lib.rsx_net_create(ctypes.byref(h_), device)
+        if code != RSX_OK:
+            raise RsxError(code, "rsx_net_create failed")
+        self.handle = h_
+        self.nparams = self.lib.rsx_net_param_count()
+        if params is not None:
+            self.set_params(params)
+
+    def _check(self, code):
+        if code != RSX_OK:
+            raise RsxError(code, self.lib.rsx_net_last_error(self.handle).decode())
+
+    def set_params(self, params):
+        import numpy as np
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        self._check(self.lib.rsx_net_set_params(self.handle, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), p.size))
+
+    def get_params(self):
+        import numpy as np
+        p = np.empty(self.nparams, dtype=np.float32)
+        self._check(self.lib.rsx_net_get_params(self.handle, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), p.size))
+        return p
+
+    def forward(self, x, out=None, stream=None):
+        B, C, D, H, W = x.shape
+        out = torch.empty((B, D, H, W), dtype=torch.float32, device=self.device) if out is None else out
+        self._check(self.lib.rsx_net_forward(self.handle, _ptr(x), B, D, H, W, _ptr(out), _stream(stream)))
+        return out
+
+    def loss_grad(self, x, target, border=0, stream=None):
+        import numpy as np
+        B, C, D, H, W = x.shape
+        loss = ctypes.c_double()
+        g = np.empty(self.nparams, dtype=np.float32)
+        self._check(self.lib.rsx_net_loss_grad(self.handle, _ptr(x), _ptr(target), B, D, H, W, int(border),
+                                               ctypes.byref(loss), g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                               _stream(stream)))
+        return loss.value, g
+
+    def train_step(self, x, target, lr, border=0, stream=None):
+        B, C, D, H, W = x.shape
+        loss = ctypes.c_double()
+        self._check(self.lib.rsx_net_train_step(self.handle, _ptr(x), _ptr(target), B, D, H, W, int(border),
+                                                float(lr), ctypes.byref(loss), _stream(stream)))
+        return loss.value
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.rsx_net_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Eigensolver:
+    """Block preconditioned eigensolver for H = -1/2 Lap + V on an n^3 box (FP32)."""
+
+    def __init__(self, V, h, nband, vscale=1.0, device=0):
+        self.lib = load()
+        self.V = V
+        self.n = V.shape[0]
+        self.nband = nband
+        h_ = ctypes.c_void_p()
+        code = self.lib.rsx_eig_create(ctypes.byref(h_), self.n, float(h), _ptr(V), float(vscale), nband, device)
+        if code != RSX_OK:
+            raise RsxError(code, "rsx_eig_create failed")
+        self.handle = h_
+
+    def _check(self, code):
+        if code != RSX_OK:
+            raise RsxError(code, self.lib.rsx_eig_last_error(self.handle).decode())
+
+    def init(self, psi0, stream=None):
+        self._check(self.lib.rsx_eig_init(self.handle, _ptr(psi0), _stream(stream)))
+
+    def step(self, net=None, sweeps=3, stream=None):
+        th = (ctypes.c_double * self.nband)()
+        self._check(self.lib.rsx_eig_step(self.handle, net.handle if net is not None else None, int(sweeps), th,
+                                          _stream(stream)))
+        return list(th)
+
+    def orbitals(self, out=None, stream=None):
+        out = torch.empty((self.nband,) + tuple(self.V.shape), dtype=torch.float32, device=self.V.device) \
+            if out is None else out
+        self._check(self.lib.rsx_eig_orbitals(self.handle, _ptr(out), _stream(stream)))
+        return out
+
+    def residual(self, out=None, stream=None):
+        out = torch.empty((self.nband,) + tuple(self.V.shape), dtype=torch.float32, device=self.V.device) \
+            if out is None else out
+        self._check(self.lib.rsx_eig_residual(self.handle, _ptr(out), _stream(stream)))
+        return out
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.rsx_eig_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -229,3 +229,93 @@ def test_orbitals_orthonormal():
     f = s.phi.reshape(4, -1)
     S = s.h ** 3 * f @ f.T
     assert np.allclose(S, np.eye(4), atol=1e-6)
+
+
+# ---------------------------------------------------------------- eigensolver and network pieces
+
+from oracle import eigensolver as oe  # noqa: E402
+
+
+def test_fd4_laplacian_exact_on_quartics_in_the_interior():
+    n, h = 14, 0.3
+    z, y, x = np.meshgrid(*(np.arange(n) * h for _ in range(3)), indexing="ij")
+    f = x ** 4 - 2 * y ** 3 * z + 3 * z ** 2
+    lap = oe.laplacian_fd4(f, h)
+    exact = 12 * x ** 2 - 12 * y * z + 6
+    sl = (slice(2, -2),) * 3
+    assert np.max(np.abs(lap[sl] - exact[sl])) < 1e-8 * np.max(np.abs(exact))
+
+
+def test_free_hamiltonian_is_a_kronecker_sum():
+    n, h = 6, 0.4
+    H = oe.hamiltonian_dense(np.zeros((n, n, n)), h)
+    assert np.allclose(H, H.T)
+    e1 = np.zeros(n)
+    T1 = np.zeros((n, n))
+    for j in range(n):
+        e1[:] = 0
+        e1[j] = 1
+        g = np.pad(e1, 2)
+        T1[:, j] = -0.5 * (-g[0:n] + 16 * g[1:n + 1] - 30 * g[2:n + 2] + 16 * g[3:n + 3] - g[4:n + 4]) / (12 * h * h)
+    l1 = np.linalg.eigvalsh(T1)
+    kron = np.sort((l1[:, None, None] + l1[None, :, None] + l1[None, None, :]).ravel())
+    assert np.allclose(np.linalg.eigvalsh(H), kron, atol=1e-10)
+
+
+def test_ke_preconditioner_converges_to_the_shifted_inverse():
+    n, h, T = 6, 0.4, 0.7
+    r = np.random.default_rng(3).standard_normal((n, n, n))
+    A = oe.hamiltonian_dense(np.zeros((n, n, n)), h) + T * np.eye(n ** 3)
+    exact = np.linalg.solve(A, r.ravel()).reshape(r.shape)
+    e3 = np.abs(oe.ke_precondition(r, T, h, sweeps=3) - exact).max()
+    e300 = np.abs(oe.ke_precondition(r, T, h, sweeps=300) - exact).max()
+    assert e300 < 1e-8 * np.abs(exact).max() and e300 < e3
+
+
+def test_rayleigh_ritz_recovers_exact_eigenpairs():
+    n, h = 6, 0.5
+    v = -1.0 / (1.0 + np.sum((np.indices((n, n, n)) - 2.5) ** 2, axis=0))
+    H = oe.hamiltonian_dense(v, h)
+    w, U = np.linalg.eigh(H)
+    rng = np.random.default_rng(0)
+    B = np.concatenate([U[:, :3].T, rng.standard_normal((3, n ** 3))])    # exact lowest 3 + noise
+    HB = np.stack([oe.hamiltonian_apply(b.reshape(n, n, n), v, h).ravel() for b in B])
+    th, Q = oe.rayleigh_ritz(B, HB, 3, h)
+    assert np.allclose(th, w[:3], atol=1e-10)
+
+
+def test_conv3d_single_channel_is_a_correlation():
+    from scipy import ndimage
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal((1, 7, 6, 5))
+    w = rng.standard_normal((1, 1, 3, 3, 3))
+    out = oe.conv3d(x, w, np.array([0.25]))
+    ref = ndimage.correlate(x[0], w[0, 0], mode="constant", cval=0.0) + 0.25
+    assert np.allclose(out[0], ref, atol=1e-12)
+
+
+def test_network_gradients_match_finite_differences():
+    rng = np.random.default_rng(2)
+    params = [(0.3 * rng.standard_normal((16, 2, 3, 3, 3)), 0.1 * rng.standard_normal(16)),
+              (0.1 * rng.standard_normal((16, 16, 3, 3, 3)), 0.1 * rng.standard_normal(16)),
+              (0.1 * rng.standard_normal((1, 16, 3, 3, 3)), 0.1 * rng.standard_normal(1))]
+    x = rng.standard_normal((2, 6, 5, 5))
+    t = rng.standard_normal((6, 5, 5))
+    loss, grads = oe.net_loss_and_grads(x, t, params)
+    for li, (name, idx) in enumerate([("w", (3, 1, 0, 2, 1)), ("b", (5,)), ("w", (7, 11, 1, 1, 0)),
+                                      ("b", (2,)), ("w", (0, 9, 2, 0, 1)), ("b", (0,))]):
+        layer = li // 2
+        which = 0 if name == "w" else 1
+        eps = 1e-6
+        p_plus = [list(p) for p in params]
+        arr = p_plus[layer][which].copy()
+        arr[idx] += eps
+        p_plus[layer][which] = arr
+        lp, _ = oe.net_loss_and_grads(x, t, [tuple(p) for p in p_plus])
+        arr2 = arr.copy()
+        arr2[idx] -= 2 * eps
+        p_plus[layer][which] = arr2
+        lm, _ = oe.net_loss_and_grads(x, t, [tuple(p) for p in p_plus])
+        fd = (lp - lm) / (2 * eps)
+        an = grads[layer][which][idx]
+        assert abs(fd - an) <= 1e-6 * max(1.0, abs(an)), (name, layer, fd, an)

@@ -296,14 +296,14 @@ int backward(rsx_net* n, const float* x, const float* target, int B, int D, int 
   const int nblk = ((W + kT - 1) / kT) * ((H + kT - 1) / kT) * ((D + kT - 1) / kT);
   rc = ngrow(n, &n->part, &n->part_elems, (size_t)B * nblk * (kW2 + kC3));
   if (rc) return rc;
-  float* z1 = n->act;
-  float* z2 = n->act + (size_t)B * kC2 * vol;
   float* g2 = n->gout;                                  // d z2  [B][16][vol]
   float* g1 = n->gout + (size_t)B * kC2 * vol;          // d z1  [B][16][vol]
   float* y = g1 + (size_t)B * kC2 * vol;                // output [B][vol]
   float* gy = y + (size_t)B * vol;                      // d output
-  rc = forward(n, x, B, D, H, W, y, s);
+  rc = forward(n, x, B, D, H, W, y, s);                 // (re)sizes n->act
   if (rc) return rc;
+  float* z1 = n->act;                                   // pre-activations of layers 1 and 2
+  float* z2 = n->act + (size_t)B * kC2 * vol;
   k_mse<<<512, 256, 0, s>>>(y, target, gy, B, D, H, W, border, n->loss);
   const dim3 g = conv_grid(B, D, H, W);
   const float* P = n->params;

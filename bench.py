@@ -313,6 +313,10 @@ def run_rsx(args, rank, local_rank, world):
     if rank == 0 and not args.skip_batch:
         out["batch"] = batch_bench(args, dev, local_rank, peaks)
 
+    # ---- learned eigensolver preconditioner, rank 0
+    if rank == 0 and not args.skip_precond:
+        out["learned_precond"] = precond_bench(args, dev, local_rank)
+
     # ---- CPU oracle baseline (rank 0, N = 1 only)
     if rank == 0 and world == 1 and not args.skip_cpu:
         out["cpu_baseline"] = cpu_baseline(s, nsolve=args.cpu_solves)
@@ -436,6 +440,81 @@ def batch_bench(args, dev, local_rank, peaks):
             "hbm_model_gbs": round(ach, 1), "hbm_frac": round(ach / hbm, 4), "input_generation_s": round(gen_s, 1)}
 
 
+def precond_bench(args, dev, local_rank):
+    """Learned eigensolver preconditioner on 96^3 systems with 16 bands (h 0.2, 4 model
+    atoms): training pairs from plain-solver runs on several systems, Adam training on the
+    GPU, then iterations and wall time to |dE| < 1e-6 Ha on an unseen system, plain vs
+    plain + learned directions."""
+    from paper_2405_01522_gb300 import precond, rsx
+    n, h, nb = args.precond_edge, 0.2, 16
+    t_all = time.perf_counter()
+    pots = [inputs.model_potential(n=n, h=h, natoms=4, Z=4.0, rc=0.6, radius=2.5, seed=s) for s in (11, 12, 13, 14, 21)]
+    Vs = [torch.from_numpy(v).float().to(dev) for v in pots]
+    vscale = float(1.0 / max(float(v.abs().max()) for v in Vs))
+    psi0s = [torch.from_numpy(inputs.starting_orbitals(n=n, h=h, nband=nb, radius=2.5, seed=100 + s)).float().to(dev)
+             for s in range(5)]
+    Xs, Ys = [], []
+    target = args.precond_pairs
+    plain_iters = []
+    for i in range(4):
+        res = precond.solve(Vs[i], h, psi0s[i], nb, tol=1e-6, vscale=vscale, record_every=2, max_iter=600)
+        plain_iters.append(res["iters"])
+        per = max(1, target // (4 * max(1, len(res["records"])) * nb))
+        X, Y = precond.make_pairs(Vs[i], h, res, vscale, crop=32, crops_per_sample=per, seed=i)
+        Xs.append(X)
+        Ys.append(Y)
+        del res
+    X = torch.cat(Xs)[:target].contiguous()
+    Y = torch.cat(Ys)[:target].contiguous()
+    del Xs, Ys
+    net = rsx.Net(precond.init_params(seed=0), device=local_rank)
+    t0 = time.perf_counter()
+    losses = precond.train(net, X, Y, epochs=args.precond_epochs, batch=32, lr=1e-3, border=3)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    # conv throughput: one training step and one full-grid forward
+    xb, yb = X[:32].contiguous(), Y[:32].contiguous()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    e[0].record()
+    for _ in range(5):
+        net.train_step(xb, yb, 1e-12, border=3)
+    e[1].record()
+    xf = torch.zeros((nb, 2, n, n, n), dtype=torch.float32, device=dev)
+    net.forward(xf)
+    e[2].record()
+    for _ in range(3):
+        net.forward(xf)
+    e[3].record()
+    torch.cuda.synchronize()
+    step_ms = e[0].elapsed_time(e[1]) / 5
+    fwd_ms = e[2].elapsed_time(e[3]) / 3
+    flop_vox = 2 * 27 * (2 * 16 + 16 * 16 + 16 * 1)
+    fwd_tflops = flop_vox * nb * n ** 3 / (fwd_ms / 1e3) / 1e12
+    train_tflops = 3 * flop_vox * 32 * 32 ** 3 / (step_ms / 1e3) / 1e12
+    del X, Y, xf
+    # evaluation on an unseen system: a tightly converged reference energy, then the
+    # iterations and wall time each method needs to come within 1e-6 Ha of it
+    ref = precond.solve(Vs[4], h, psi0s[4], nb, net=net, tol=1e-11, vscale=vscale, max_iter=2000)
+    e_ref = ref["energy"]
+    plain = precond.solve(Vs[4], h, psi0s[4], nb, tol=1e-9, vscale=vscale, max_iter=1500)
+    learned = precond.solve(Vs[4], h, psi0s[4], nb, net=net, tol=1e-9, vscale=vscale, max_iter=1500)
+    net.close()
+    ip, tp = precond.time_to_target(plain, e_ref)
+    il, tl = precond.time_to_target(learned, e_ref)
+    return {"workload": f"{n}^3 box at h=0.2, 16 bands of H = -1/2 Lap(FD4) + V (4 model atoms, Z=4); "
+                        "training pairs from plain runs on 4 systems, evaluation on a 5th",
+            "pairs": int(target), "epochs": args.precond_epochs, "loss_first_last": [losses[0], losses[-1]],
+            "train_s": round(train_s, 2), "plain_train_iters": plain_iters,
+            "reference_energy_ha": e_ref, "target": "E - E_ref < 1e-6 Ha",
+            "plain": {"iters_to_target": ip, "time_to_target_s": None if tp is None else round(tp, 3),
+                      "final_energy_ha": plain["energy"]},
+            "learned": {"iters_to_target": il, "time_to_target_s": None if tl is None else round(tl, 3),
+                        "final_energy_ha": learned["energy"]},
+            "final_energy_diff_ha": abs(learned["energy"] - plain["energy"]),
+            "conv_forward_tflops": round(fwd_tflops, 2), "conv_train_step_tflops": round(train_tflops, 2),
+            "total_s": round(time.perf_counter() - t_all, 1)}
+
+
 def cpu_baseline(s, nsolve=16):
     """The FP64 oracle as it stands, on the host, for a bounded sample of the workload:
     the exchange action on trial function 0 from the first `nsolve` orbitals."""
@@ -487,6 +566,11 @@ def main():
     ap.add_argument("--skip-casida", action="store_true")
     ap.add_argument("--skip-batch", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (default knobs)")
+    ap.add_argument("--skip-precond", action="store_true")
+    ap.add_argument("--precond-only", action="store_true")
+    ap.add_argument("--precond-edge", type=int, default=96)
+    ap.add_argument("--precond-pairs", type=int, default=20000)
+    ap.add_argument("--precond-epochs", type=int, default=4)
     ap.add_argument("--batch-mols", type=int, default=64)
     ap.add_argument("--casida-only", action="store_true", help="only the Casida section (profiling captures)")
     ap.add_argument("--casida-edge", type=int, default=80, help="box edge of the Casida case")
@@ -503,6 +587,10 @@ def main():
     rank, local_rank, world = env_rank()
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.precond_only:
+        dev = torch.device("cuda", local_rank)
+        torch.cuda.set_device(dev)
+        print(json.dumps({"learned_precond": precond_bench(args, dev, local_rank)}), flush=True)
     elif args.casida_only:
         dev = torch.device("cuda", local_rank)
         torch.cuda.set_device(dev)

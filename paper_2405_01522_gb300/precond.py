@@ -43,7 +43,7 @@ def solve(V, h, psi0, nband, net=None, tol=1e-6, max_iter=400, sweeps=3, vscale=
     es = rsx.Eigensolver(V, h, nband, vscale=vscale, device=V.device.index or 0)
     es.init(psi0)
     torch.cuda.synchronize()
-    trace, rec = [], []
+    trace, rec, times = [], [], []
     t0 = time.perf_counter()
     E_prev, th, it = None, None, 0
     for it in range(1, max_iter + 1):
@@ -53,6 +53,7 @@ def solve(V, h, psi0, nband, net=None, tol=1e-6, max_iter=400, sweeps=3, vscale=
             rec.append((psi_before, es.residual()))
         E = float(sum(th))
         trace.append(E)
+        times.append(time.perf_counter() - t0)   # each step synchronises the stream
         if E_prev is not None and abs(E - E_prev) < tol:
             break
         E_prev = E
@@ -60,7 +61,17 @@ def solve(V, h, psi0, nband, net=None, tol=1e-6, max_iter=400, sweeps=3, vscale=
     dt = time.perf_counter() - t0
     psi = es.orbitals()
     es.close()
-    return {"iters": it, "energy": trace[-1], "theta": th, "time_s": dt, "trace": trace, "records": rec, "psi": psi}
+    return {"iters": it, "energy": trace[-1], "theta": th, "time_s": dt, "trace": trace, "times": times,
+            "records": rec, "psi": psi}
+
+
+def time_to_target(res, e_ref, tol=1e-6):
+    """First iteration (1-based) and elapsed time at which E - e_ref < tol (Rayleigh-Ritz
+    energies decrease monotonically to e_ref); None if never reached."""
+    for i, (E, t) in enumerate(zip(res["trace"], res["times"])):
+        if E - e_ref < tol:
+            return i + 1, t
+    return None, None
 
 
 def make_pairs(V, h, res, vscale, crop=32, crops_per_sample=16, seed=0):

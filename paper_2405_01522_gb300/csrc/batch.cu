@@ -393,7 +393,7 @@ int rsx_batch_create(rsx_batch** out, int nmol, const int* edges, const int* noc
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device);
   const int L = 16 * maxA, H = L / 2 + 1;
   b->smem[0] = sizeof(Cx<float>) * ((size_t)kLinesPerCta * maxA * kScrPitch + (size_t)H * kXsPitch);
-  b->smem[2] = b->smem[0] + sizeof(float) * (size_t)kRowsPerCta * nmaxx;
+  b->smem[2] = sizeof(Cx<float>) * (size_t)kLinesPerCta * maxA * kScrPitch + 2 * pass3_buffer_elems<float>(maxA, nmaxx);
   size_t p2 = 0;
   for (auto& d : b->desc)
     p2 = std::max(p2, sizeof(Cx<float>) * ((size_t)kLinesPerCta * d.g.Ay * kScrPitch + (size_t)d.g.nz * (d.g.My + 1)));

@@ -391,7 +391,65 @@ __global__ void __launch_bounds__(kThreads) k_spectrum(Geom g, int nq, const Cx<
 // pass 3: x inverse (c2r via row pairs) of every pair in output p's list, and
 // out_p(z, y, x) = - sum_e partner_e(z, y, x) V_e(z, y, x).  One item = (p, z, 32 rows).
 // With pot != 0 the output p is the potential V of pair q = p itself (no partner, no sign).
+// The next pair's row block and partner tile are copied with cp.async into the second
+// of two shared-memory buffers while the current pair is transformed.
 // pass3_item is the body; `out_p` is output p's array, `inter` the slot base of q0.
+
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// shared-memory bytes of pass 3 for element type R (two buffers of row block + tile)
+template <typename R>
+__host__ __device__ inline size_t pass3_buffer_elems(int AX, int nx) {
+  const int H = 8 * AX + 1;
+  return (size_t)H * kXsPitch * sizeof(Cx<R>) + (size_t)kRowsPerCta * nx * sizeof(R);
+}
+
+template <typename R, int AX>
+__device__ __forceinline__ void pass3_prefetch(const Geom& g, const PairMap<R>& pm, int q0, int p, int e, int z,
+                                               int y0, int nrow, int pot, const Cx<R>* __restrict__ inter,
+                                               Cx<R>* xs, R* tile) {
+  constexpr int H = 8 * AX + 1;
+  int q = p;
+  const R* partner = nullptr;
+  if (!pot) pm.entry(p, e, q, partner);
+  const Cx<R>* src = inter + (size_t)(q - q0) * g.inter_elems() + (size_t)z * g.ny + y0;
+  const size_t kstride = (size_t)g.nz * g.ny;
+  for (int i = threadIdx.x; i < H * kRowsPerCta; i += kThreads) {
+    const int kx = i / kRowsPerCta, r = i - kx * kRowsPerCta;
+    if (r < nrow) {
+      const Cx<R>* sp = src + (size_t)kx * kstride + r;
+      Cx<R>* dp = xs + kx * kXsPitch + r;
+      if (sizeof(R) == 4) {
+        cp_async8(dp, sp);
+      } else {
+        cp_async8(dp, sp);
+        cp_async8(reinterpret_cast<char*>(dp) + 8, reinterpret_cast<const char*>(sp) + 8);
+      }
+    } else {
+      xs[kx * kXsPitch + r] = cx<R>(R(0), R(0));
+    }
+  }
+  if (!pot) {
+    const R* prow = partner + (size_t)z * g.ny * g.nx + (size_t)y0 * g.nx;
+    for (int i = threadIdx.x; i < nrow * g.nx; i += kThreads) {
+      if (sizeof(R) == 4)
+        cp_async4(tile + i, prow + i);
+      else
+        cp_async8(tile + i, prow + i);
+    }
+  }
+}
+
 template <typename R, int AX>
 __device__ __forceinline__ void pass3_item(const Geom& g, const PairMap<R>& pm, int q0, int p, int z, int yblk,
                                            int pot, const Cx<R>* __restrict__ inter, const Cx<R>* __restrict__ twx,
@@ -400,36 +458,36 @@ __device__ __forceinline__ void pass3_item(const Geom& g, const PairMap<R>& pm, 
   constexpr int SP = AX * kScrPitch;
   constexpr int H = L / 2 + 1;
   Cx<R>* scr = reinterpret_cast<Cx<R>*>(smem_raw);
-  Cx<R>* xs = scr + kLinesPerCta * SP;               // [H][kXsPitch]
-  R* tile = reinterpret_cast<R*>(xs + H * kXsPitch);  // [32][nx]: partner, then result
+  unsigned char* buf0 = reinterpret_cast<unsigned char*>(scr + kLinesPerCta * SP);
+  const size_t bufbytes = pass3_buffer_elems<R>(AX, g.nx);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int t = lane & 15, line = warp * 2 + (lane >> 4);
   const int y0 = yblk * kRowsPerCta;
   const int nrow = min(kRowsPerCta, g.ny - y0);
   Cx<R>* sc = scr + line * SP;
-  const size_t kstride = (size_t)g.nz * g.ny;
   const size_t plane = (size_t)z * g.ny * g.nx;
+  auto xs_of = [&](int b) { return reinterpret_cast<Cx<R>*>(buf0 + b * bufbytes); };
+  auto tile_of = [&](int b) { return reinterpret_cast<R*>(buf0 + b * bufbytes + (size_t)H * kXsPitch * sizeof(Cx<R>)); };
 
   R acc0[16], acc1[16];
 #pragma unroll
   for (int k2 = 0; k2 < 16; ++k2) acc0[k2] = acc1[k2] = R(0);
 
   const int ne = pot ? 1 : pm.nentries(p);
+  __syncthreads();   // the buffers may still be read by a previous item of this CTA
+  pass3_prefetch<R, AX>(g, pm, q0, p, 0, z, y0, nrow, pot, inter, xs_of(0), tile_of(0));
+  cp_async_commit();
   for (int e = 0; e < ne; ++e) {
-    int q = p;
-    const R* partner = nullptr;
-    if (!pot) pm.entry(p, e, q, partner);
-    const Cx<R>* src = inter + (size_t)(q - q0) * g.inter_elems() + (size_t)z * g.ny + y0;
-    __syncthreads();
-    for (int i = threadIdx.x; i < H * kRowsPerCta; i += kThreads) {
-      const int kx = i / kRowsPerCta, r = i - kx * kRowsPerCta;
-      xs[kx * kXsPitch + r] = (r < nrow) ? src[(size_t)kx * kstride + r] : cx<R>(R(0), R(0));
-    }
-    if (!pot) {
-      const R* prow = partner + plane + (size_t)y0 * g.nx;
-      for (int i = threadIdx.x; i < nrow * g.nx; i += kThreads) tile[i] = __ldg(prow + i);
+    if (e + 1 < ne) {
+      pass3_prefetch<R, AX>(g, pm, q0, p, e + 1, z, y0, nrow, pot, inter, xs_of((e + 1) & 1), tile_of((e + 1) & 1));
+      cp_async_commit();
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
     }
     __syncthreads();
+    const Cx<R>* xs = xs_of(e & 1);
+    const R* tile = tile_of(e & 1);
 
     // Z(k) = X_a(k) + i X_b(k), Hermitian extension for k > L/2
     Cx<R> v[AX];
@@ -468,8 +526,9 @@ __device__ __forceinline__ void pass3_item(const Geom& g, const PairMap<R>& pm, 
       }
     }
     __syncwarp();
+    __syncthreads();   // buffer e & 1 is refilled by the prefetch of entry e + 2
   }
-  __syncthreads();
+  R* tile = tile_of(0);
   if (t < AX) {
     const int ra = 2 * line, rb = ra + 1;
 #pragma unroll

@@ -22,7 +22,7 @@ inline size_t pass1_smem(int AX) {
 }
 template <typename R>
 inline size_t pass3_smem(int AX, int nx) {
-  return pass1_smem<R>(AX) + sizeof(R) * (size_t)kRowsPerCta * nx;
+  return sizeof(Cx<R>) * (size_t)kLinesPerCta * AX * kScrPitch + 2 * pass3_buffer_elems<R>(AX, nx);
 }
 inline int max_dyn_smem() {
   int dev = 0, v = 0;

@@ -158,7 +158,7 @@ __device__ __forceinline__ void store_plane(const Cx<R>* D, int DP, Cx<R>* P, in
 // forward y transform of rows z < nz (input y < ny, output all My)
 template <typename R, int AY, int NT>
 __device__ __forceinline__ void y_forward(Cx<R>* D, int DP, int nz, int ny, const Cx<R>* __restrict__ twy,
-                                          Cx<R>* sc) {
+                                          Cx<R>* sc, int in_off = 0) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, t = lane & 15;
   for (int z0 = 2 * warp; z0 < nz; z0 += NT / 16) {
     const int z = z0 + (lane >> 4);
@@ -167,7 +167,7 @@ __device__ __forceinline__ void y_forward(Cx<R>* D, int DP, int nz, int ny, cons
 #pragma unroll
     for (int a = 0; a < AY; ++a) {
       const int y = t + 16 * a;
-      v[a] = (ok && y < ny) ? D[z * DP + y] : cx<R>(R(0), R(0));
+      v[a] = (ok && y < ny) ? D[z * DP + in_off + y] : cx<R>(R(0), R(0));
     }
     stage1_store<AY, -1>(v, t, twy, sc);
     __syncwarp();
@@ -218,10 +218,31 @@ __device__ __forceinline__ void y_inverse(Cx<R>* D, int DP, int nz, int ny, cons
 // pass 2: per (pair, kx) plane: y forward, z forward * vhat * z inverse, y inverse.
 // pass2_plane is the body for one plane P (nz x ny, contiguous) at column kx; D is the
 // (nz x My) work plane (row pitch My + 1) and scr the line scratch.
+// Input staging: with `prefetched` the plane already sits in the upper half of the D rows
+// (columns [ny, 2 ny), copied by cp.async), otherwise it is loaded here into [0, ny).
+// With `Pnext` not null, the next plane is cp.async-prefetched into the upper halves
+// (dead after the y inverse) while this plane is stored.
+template <typename R>
+__device__ __forceinline__ void prefetch_plane_upper(Cx<R>* D, int DP, const Cx<R>* P, int nz, int ny, int NT) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int z = warp; z < nz; z += NT / 32)
+    for (int y = lane; y < ny; y += 32) {
+      Cx<R>* dp = D + z * DP + ny + y;
+      const Cx<R>* sp = P + z * ny + y;
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dp)), "l"(sp)
+                   : "memory");
+      if (sizeof(R) == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dp) + 8u),
+                     "l"(reinterpret_cast<const char*>(sp) + 8)
+                     : "memory");
+    }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
 template <typename R, int AY, int AZ, int NT>
 __device__ __forceinline__ void pass2_plane(const Geom& g, Cx<R>* P, int kx, const Cx<R>* __restrict__ twy,
                                             const Cx<R>* __restrict__ twz, const R* __restrict__ vhat, Cx<R>* D,
-                                            Cx<R>* scr) {
+                                            Cx<R>* scr, bool prefetched = false, const Cx<R>* Pnext = nullptr) {
   constexpr int LY = 16 * AY;
   constexpr int LZ = 16 * AZ;
   constexpr int AMAX = AY > AZ ? AY : AZ;
@@ -231,9 +252,13 @@ __device__ __forceinline__ void pass2_plane(const Geom& g, Cx<R>* P, int kx, con
   const int t = lane & 15, line = warp * 2 + (lane >> 4);
   Cx<R>* sc = scr + line * SP;
   constexpr int Hy = LY / 2 + 1, Hz = LZ / 2 + 1;
-  load_plane<NT>(D, DP, P, g.nz, g.ny);
+  if (prefetched) {
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+  } else {
+    load_plane<NT>(D, DP, P, g.nz, g.ny);
+  }
   __syncthreads();
-  y_forward<R, AY, NT>(D, DP, g.nz, g.ny, twy, sc);
+  y_forward<R, AY, NT>(D, DP, g.nz, g.ny, twy, sc, prefetched ? g.ny : 0);
   __syncthreads();
   // z forward, multiply, z inverse on columns ky (LY is a multiple of 16: uniform trips)
   const R* vrow = vhat + (size_t)kx * Hy * Hz;
@@ -282,6 +307,7 @@ __device__ __forceinline__ void pass2_plane(const Geom& g, Cx<R>* P, int kx, con
   __syncthreads();
   y_inverse<R, AY, NT>(D, DP, g.nz, g.ny, twy, sc);
   __syncthreads();
+  if (Pnext) prefetch_plane_upper<R>(D, DP, Pnext, g.nz, g.ny, NT);
   store_plane<NT>(D, DP, P, g.nz, g.ny);
   __syncthreads();
 }
@@ -301,10 +327,18 @@ __global__ void __launch_bounds__(NT, 1) k_pass2(Geom g, int nq, Cx<R>* __restri
                    : reinterpret_cast<Cx<R>*>(gscratch) + (size_t)blockIdx.x * g.nz * DP;
   const int nplane = g.nz * g.ny;
   const int nwork = nq * g.Hx;
-  for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
+  auto plane_ptr = [&](int w) {
     const int ql = w / g.Hx, kx = w - ql * g.Hx;
-    Cx<R>* P = inter + (size_t)ql * g.inter_elems() + (size_t)kx * nplane;
-    pass2_plane<R, AY, AZ, NT>(g, P, kx, twy, twz, vhat, D, scr);
+    return inter + (size_t)ql * g.inter_elems() + (size_t)kx * nplane;
+  };
+  // in shared memory the next plane is prefetched behind the current one (2 ny <= My + 1)
+  const bool pipe = DSMEM;
+  if (pipe && (int)blockIdx.x < nwork) prefetch_plane_upper<R>(D, DP, plane_ptr(blockIdx.x), g.nz, g.ny, NT);
+  for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
+    const int kx = w % g.Hx;
+    const int wn = w + (int)gridDim.x;
+    pass2_plane<R, AY, AZ, NT>(g, plane_ptr(w), kx, twy, twz, vhat, D, scr, pipe,
+                               (pipe && wn < nwork) ? plane_ptr(wn) : nullptr);
   }
 }
 

@@ -72,6 +72,27 @@ RSX_HD constexpr double trig_s(int p, int j) {
        : /* p == 16 */ trig_c(16, (j + 12) % 16);
 }
 
+// cos / sin (2 pi a / A) for even A in {2, ..., 14, 16} and 0 <= a < A / 2 (decimal expansions)
+RSX_HD constexpr double trig_even_c(int A, int a) {
+  return A == 16 ? trig_c(16, a) : A == 8 ? trig_c(16, 2 * a) : A == 4 ? (a == 0 ? 1.0 : 0.0) : A == 2 ? 1.0
+       : A == 6 ? (a == 0 ? 1.0 : a == 1 ? 0.5 : -0.5)
+       : A == 10 ? (a == 0 ? 1.0 : a == 1 ? 0.80901699437494742410 : a == 2 ? 0.30901699437494742410
+                    : a == 3 ? -0.30901699437494742410 : -0.80901699437494742410)
+       : A == 12 ? (a == 0 ? 1.0 : a == 1 ? 0.86602540378443864676 : a == 2 ? 0.5 : a == 3 ? 0.0
+                    : a == 4 ? -0.5 : -0.86602540378443864676)
+       : /* A == 14 */ (a == 0 ? 1.0 : a == 1 ? 0.90096886790241912624 : a == 2 ? 0.62348980185873353053
+                        : a == 3 ? 0.22252093395631440429 : a == 4 ? -0.22252093395631440429
+                        : a == 5 ? -0.62348980185873353053 : -0.90096886790241912624);
+}
+RSX_HD constexpr double trig_even_s(int A, int a) {
+  return A == 16 ? trig_s(16, a) : A == 8 ? trig_s(16, 2 * a) : A == 4 ? (a == 0 ? 0.0 : 1.0) : A == 2 ? 0.0
+       : A == 6 ? (a == 0 ? 0.0 : 0.86602540378443864676)
+       : A == 10 ? (a == 0 ? 0.0 : (a == 1 || a == 4) ? 0.58778525229247312917 : 0.95105651629515357212)
+       : A == 12 ? (a == 0 ? 0.0 : (a == 1 || a == 5) ? 0.5 : (a == 2 || a == 4) ? 0.86602540378443864676 : 1.0)
+       : /* A == 14 */ (a == 0 ? 0.0 : (a == 1 || a == 6) ? 0.43388373911755812048
+                        : (a == 2 || a == 5) ? 0.78183148246802980871 : 0.97492791218182360702);
+}
+
 template <int N, int S>
 struct Dft;
 
@@ -229,5 +250,50 @@ template <int S> struct Dft<6, S> : DftPfa<2, 3, S> {};
 template <int S> struct Dft<10, S> : DftPfa<2, 5, S> {};
 template <int S> struct Dft<12, S> : DftPfa<3, 4, S> {};
 template <int S> struct Dft<14, S> : DftPfa<2, 7, S> {};
+
+// DFT of length A (even) whose inputs v[A/2 .. A) are zero: only v[0 .. A/2) are read.
+// X[2m] = DFT_{A/2}(v)[m], X[2m+1] = DFT_{A/2}(v[a] w^a)[m], w = exp(S 2 pi i / A).
+// Result written to out[0 .. A).
+template <int A, int S>
+struct DftHalfIn {
+  template <typename R>
+  RSX_HD static void run(const Cx<R>* v, Cx<R>* out) {
+    constexpr int H = A / 2;
+    Cx<R> e[H], o[H];
+#pragma unroll
+    for (int a = 0; a < H; ++a) {
+      e[a] = v[a];
+      o[a] = (a == 0) ? v[a] : rot<S>(v[a], R(trig_even_c(A, a)), R(trig_even_s(A, a)));
+    }
+    Dft<H, S>::run(e);
+    Dft<H, S>::run(o);
+#pragma unroll
+    for (int m = 0; m < H; ++m) {
+      out[2 * m] = e[m];
+      out[2 * m + 1] = o[m];
+    }
+  }
+};
+
+// DFT of length A (even) of which only outputs 0 .. A/2 - 1 are wanted:
+// X[a] = DFT_{A/2}(v_even)[a] + w^a DFT_{A/2}(v_odd)[a].  Result written to out[0 .. A/2).
+template <int A, int S>
+struct DftHalfOut {
+  template <typename R>
+  RSX_HD static void run(const Cx<R>* v, Cx<R>* out) {
+    constexpr int H = A / 2;
+    Cx<R> e[H], o[H];
+#pragma unroll
+    for (int m = 0; m < H; ++m) {
+      e[m] = v[2 * m];
+      o[m] = v[2 * m + 1];
+    }
+    Dft<H, S>::run(e);
+    Dft<H, S>::run(o);
+#pragma unroll
+    for (int a = 0; a < H; ++a)
+      out[a] = e[a] + ((a == 0) ? o[a] : rot<S>(o[a], R(trig_even_c(A, a)), R(trig_even_s(A, a))));
+  }
+};
 
 }  // namespace rsx

@@ -49,6 +49,22 @@ __device__ __forceinline__ void stage1_store(Cx<R> (&v)[A], int t, const Cx<R>* 
   for (int k1 = 0; k1 < A; ++k1) sc[k1 * kScrPitch + t] = v[k1];
 }
 
+// stage 1 for a forward transform whose inputs t + 16 a >= 8 A are zero (even A, the
+// padded half of a line of length 16 A): only v[0 .. A/2) are used
+template <int A, int S, typename R>
+__device__ __forceinline__ void stage1_store_halfin(const Cx<R>* v, int t, const Cx<R>* __restrict__ tw, Cx<R>* sc) {
+  Cx<R> x[A];
+  DftHalfIn<A, S>::run(v, x);
+#pragma unroll
+  for (int k1 = 1; k1 < A; ++k1) {
+    Cx<R> w = tw[t * A + k1];
+    if (S > 0) w.y = -w.y;
+    x[k1] = cmul(x[k1], w);
+  }
+#pragma unroll
+  for (int k1 = 0; k1 < A; ++k1) sc[k1 * kScrPitch + t] = x[k1];
+}
+
 // stage 2 load: lane s (< A) gathers its 16 values scratch[s][t]
 template <typename R>
 __device__ __forceinline__ void stage2_load(Cx<R> (&u)[16], int s, const Cx<R>* sc) {
@@ -78,9 +94,10 @@ __device__ __forceinline__ void pass1_item(const Geom& g, const R* f1, const R* 
   f1 += plane;
   f2 += plane;
 
+  constexpr int AIN = (AX % 2 == 0) ? AX / 2 : AX;   // inputs x >= nx = 8 AX are zero
   Cx<R> v[AX];
 #pragma unroll
-  for (int a = 0; a < AX; ++a) {
+  for (int a = 0; a < AIN; ++a) {
     const int x = t + 16 * a;
     R re = R(0), im = R(0);
     if (x < g.nx) {
@@ -89,7 +106,11 @@ __device__ __forceinline__ void pass1_item(const Geom& g, const R* f1, const R* 
     }
     v[a] = cx<R>(re, im);
   }
-  stage1_store<AX, -1>(v, t, twx, sc);
+  if constexpr (AX % 2 == 0) {
+    stage1_store_halfin<AX, -1>(v, t, twx, sc);
+  } else {
+    stage1_store<AX, -1>(v, t, twx, sc);
+  }
   __syncwarp();
   Cx<R> u[16];
   if (t < AX) {
@@ -163,13 +184,18 @@ __device__ __forceinline__ void y_forward(Cx<R>* D, int DP, int nz, int ny, cons
   for (int z0 = 2 * warp; z0 < nz; z0 += NT / 16) {
     const int z = z0 + (lane >> 4);
     const bool ok = z < nz;
+    constexpr int AIN = (AY % 2 == 0) ? AY / 2 : AY;   // inputs y >= ny = 8 AY are zero
     Cx<R> v[AY];
 #pragma unroll
-    for (int a = 0; a < AY; ++a) {
+    for (int a = 0; a < AIN; ++a) {
       const int y = t + 16 * a;
       v[a] = (ok && y < ny) ? D[z * DP + in_off + y] : cx<R>(R(0), R(0));
     }
-    stage1_store<AY, -1>(v, t, twy, sc);
+    if constexpr (AY % 2 == 0) {
+      stage1_store_halfin<AY, -1>(v, t, twy, sc);
+    } else {
+      stage1_store<AY, -1>(v, t, twy, sc);
+    }
     __syncwarp();
     Cx<R> u[16];
     if (t < AY) {
@@ -201,12 +227,19 @@ __device__ __forceinline__ void y_inverse(Cx<R>* D, int DP, int nz, int ny, cons
     Cx<R> u[16];
     if (t < AY) {
       stage2_load(u, t, sc);
-      Dft<16, 1>::run(u);
+      if constexpr (AY % 2 == 0) {
+        Cx<R> o[8];
+        DftHalfOut<16, 1>::run(u, o);   // only y = t + AY k2 < ny = 8 AY, i.e. k2 < 8
+#pragma unroll
+        for (int k2 = 0; k2 < 8; ++k2) u[k2] = o[k2];
+      } else {
+        Dft<16, 1>::run(u);
+      }
     }
     __syncwarp();
     if (ok && t < AY) {
 #pragma unroll
-      for (int k2 = 0; k2 < 16; ++k2) {
+      for (int k2 = 0; k2 < ((AY % 2 == 0) ? 8 : 16); ++k2) {
         const int y = t + AY * k2;
         if (y < ny) D[z * DP + y] = u[k2];
       }
@@ -265,13 +298,18 @@ __device__ __forceinline__ void pass2_plane(const Geom& g, Cx<R>* P, int kx, con
   for (int ky = line; ky < LY; ky += NT / 16) {
     const int iy = ky <= LY / 2 ? ky : LY - ky;
     const R* vcol = vrow + (size_t)iy * Hz;
+    constexpr int AIN = (AZ % 2 == 0) ? AZ / 2 : AZ;   // inputs z >= nz = 8 AZ are zero
     Cx<R> v[AZ];
 #pragma unroll
-    for (int a = 0; a < AZ; ++a) {
+    for (int a = 0; a < AIN; ++a) {
       const int z = t + 16 * a;
       v[a] = (z < g.nz) ? D[z * DP + ky] : cx<R>(R(0), R(0));
     }
-    stage1_store<AZ, -1>(v, t, twz, sc);
+    if constexpr (AZ % 2 == 0) {
+      stage1_store_halfin<AZ, -1>(v, t, twz, sc);
+    } else {
+      stage1_store<AZ, -1>(v, t, twz, sc);
+    }
     __syncwarp();
     Cx<R> u[16];
     if (t < AZ) stage2_load(u, t, sc);
@@ -296,11 +334,18 @@ __device__ __forceinline__ void pass2_plane(const Geom& g, Cx<R>* P, int kx, con
     Cx<R> r[AZ];
 #pragma unroll
     for (int k1 = 0; k1 < AZ; ++k1) r[k1] = sc[k1 * kScrPitch + t];
-    Dft<AZ, 1>::run(r);
+    if constexpr (AZ % 2 == 0) {
+      Cx<R> o[AZ / 2];
+      DftHalfOut<AZ, 1>::run(r, o);   // only z = t + 16 a < nz = 8 AZ, i.e. a < AZ / 2
 #pragma unroll
-    for (int a = 0; a < AZ; ++a) {
-      const int z = t + 16 * a;
-      if (z < g.nz) D[z * DP + ky] = r[a];
+      for (int a = 0; a < AZ / 2; ++a) D[(t + 16 * a) * DP + ky] = o[a];
+    } else {
+      Dft<AZ, 1>::run(r);
+#pragma unroll
+      for (int a = 0; a < AZ; ++a) {
+        const int z = t + 16 * a;
+        if (z < g.nz) D[z * DP + ky] = r[a];
+      }
     }
     __syncwarp();
   }
@@ -382,13 +427,18 @@ __global__ void __launch_bounds__(kThreads) k_spectrum(Geom g, int nq, const Cx<
     for (int ky = line; ky < LY; ky += kLinesPerCta) {
       const int iy = ky <= LY / 2 ? ky : LY - ky;
       const float* vcol = vrow + (size_t)iy * Hz;
+      constexpr int AIN = (AZ % 2 == 0) ? AZ / 2 : AZ;
       Cx<float> v[AZ];
 #pragma unroll
-      for (int a = 0; a < AZ; ++a) {
+      for (int a = 0; a < AIN; ++a) {
         const int z = t + 16 * a;
         v[a] = (z < g.nz) ? D[z * DP + ky] : cx<float>(0.f, 0.f);
       }
-      stage1_store<AZ, -1>(v, t, twz, sc);
+      if constexpr (AZ % 2 == 0) {
+        stage1_store_halfin<AZ, -1>(v, t, twz, sc);
+      } else {
+        stage1_store<AZ, -1>(v, t, twz, sc);
+      }
       __syncwarp();
       Cx<float> u[16];
       if (t < AZ) {
@@ -543,10 +593,17 @@ __device__ __forceinline__ void pass3_item(const Geom& g, const PairMap<R>& pm, 
     if (t < AX) {
       Cx<R> u[16];
       stage2_load(u, t, sc);
-      Dft<16, 1>::run(u);
+      if constexpr (AX % 2 == 0) {
+        Cx<R> o[8];
+        DftHalfOut<16, 1>::run(u, o);   // only x = t + AX k2 < nx = 8 AX, i.e. k2 < 8
+#pragma unroll
+        for (int k2 = 0; k2 < 8; ++k2) u[k2] = o[k2];
+      } else {
+        Dft<16, 1>::run(u);
+      }
       const int ra = 2 * line, rb = ra + 1;
 #pragma unroll
-      for (int k2 = 0; k2 < 16; ++k2) {
+      for (int k2 = 0; k2 < ((AX % 2 == 0) ? 8 : 16); ++k2) {
         const int x = t + AX * k2;
         if (x < g.nx) {
           if (pot) {

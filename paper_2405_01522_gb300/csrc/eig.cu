@@ -199,6 +199,24 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// sum of the G per-CTA partials, by the whole CTA (one L2 round trip, shuffle reduction)
+__device__ __forceinline__ double cta_sum_partials(const double* part, unsigned int G, double* red, double* out_sh) {
+  double v = 0.0;
+  for (unsigned int c = threadIdx.x; c < G; c += blockDim.x) v += __ldcg(part + c);
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < nwarp; ++w) t += red[w];
+    *out_sh = t;
+  }
+  __syncthreads();
+  return *out_sh;
+}
+
 // scratch layout (doubles): v[n], p[n], part_norm[G], part_pv[G], alpha
 __global__ void __launch_bounds__(256) k_tridiag_coop(double* __restrict__ A, int n, double* __restrict__ d,
                                                       double* __restrict__ e, double* __restrict__ tau,
@@ -211,8 +229,11 @@ __global__ void __launch_bounds__(256) k_tridiag_coop(double* __restrict__ A, in
   double* part_norm = scr + 2 * n;
   double* part_pv = part_norm + G;
   double* alpha_g = part_pv + G;
+  extern __shared__ double tri_smem[];   // local copies of v and p (2 n doubles)
+  double* vs = tri_smem;
+  double* ps = tri_smem + n;
   __shared__ double red[8];
-  __shared__ double sh_tau, sh_beta, sh_scale;
+  __shared__ double sh_tau, sh_beta, sh_scale, sh_sum;
   bool live = true;
 
   // norm partials of column 0 below the subdiagonal, alpha of column 0
@@ -230,9 +251,8 @@ __global__ void __launch_bounds__(256) k_tridiag_coop(double* __restrict__ A, in
   for (int k = 0; k + 2 < n && live; ++k) {
     const int m0 = k + 1;
     // ---- reflector (every CTA computes the same scalars)
+    const double xn2 = cta_sum_partials(part_norm, G, red, &sh_sum);
     if (threadIdx.x == 0) {
-      double xn2 = 0.0;
-      for (unsigned int c = 0; c < G; ++c) xn2 += __ldcg(part_norm + c);
       const double alpha = __ldcg(alpha_g);
       if (xn2 == 0.0) {
         sh_tau = 0.0;
@@ -262,17 +282,19 @@ __global__ void __launch_bounds__(256) k_tridiag_coop(double* __restrict__ A, in
     // ---- p_i = tau (A22 v)_i for own rows, partial p^T v
     double pv_part = 0.0;
     if (tk != 0.0) {
+      for (int j = m0 + threadIdx.x; j < n; j += blockDim.x) vs[j] = __ldcg(vv + j);
+      __syncthreads();
       int r = 0;
       for (int i = first_owned(m0, cta, G); i < n; i += G, ++r) {
         if (r % nwarp != warp) continue;
         const double* row = A + (size_t)i * n;
         double acc = 0.0;
-        for (int j = m0 + lane; j < n; j += 32) acc += row[j] * __ldcg(vv + j);
+        for (int j = m0 + lane; j < n; j += 32) acc += row[j] * vs[j];
         acc = warp_sum(acc);
         const double pi = tk * acc;
         if (lane == 0) {
           pp[i] = pi;
-          pv_part += pi * __ldcg(vv + i);
+          pv_part += pi * vs[i];
         }
       }
     }
@@ -287,20 +309,17 @@ __global__ void __launch_bounds__(256) k_tridiag_coop(double* __restrict__ A, in
     // ---- w = p - (tau/2)(p^T v) v ; A22 -= v w^T + w v^T on own rows; next column norm
     double nrm_part = 0.0;
     if (tk != 0.0) {
-      double pvs = 0.0;
-      for (unsigned int c = 0; c < G; ++c) pvs += __ldcg(part_pv + c);
+      const double pvs = cta_sum_partials(part_pv, G, red, &sh_sum);
       const double cc = 0.5 * tk * pvs;
+      for (int j = m0 + threadIdx.x; j < n; j += blockDim.x) ps[j] = __ldcg(pp + j) - cc * vs[j];   // w
+      __syncthreads();
       int r = 0;
       for (int i = first_owned(m0, cta, G); i < n; i += G, ++r) {
         if (r % nwarp != warp) continue;
-        const double vi = __ldcg(vv + i);
-        const double wi = __ldcg(pp + i) - cc * vi;
+        const double vi = vs[i];
+        const double wi = ps[i];
         double* row = A + (size_t)i * n;
-        for (int j = m0 + lane; j < n; j += 32) {
-          const double vj = __ldcg(vv + j);
-          const double wj = __ldcg(pp + j) - cc * vj;
-          row[j] -= vi * wj + wi * vj;
-        }
+        for (int j = m0 + lane; j < n; j += 32) row[j] -= vi * ps[j] + wi * vs[j];
         __syncwarp();
         if (lane == 0) {
           const double x = row[m0];   // column k + 1 of row i
@@ -523,7 +542,8 @@ int tda_solve(rsx_ctx* c, const double* eo, int no, const double* ev, int nv, co
   // cooperative multi-CTA reduction when the device supports it, one CTA otherwise
   int coop = 0, per_sm = 0;
   cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, c->device);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tridiag_coop, 256, 0);
+  cudaFuncSetAttribute(k_tridiag_coop, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(2 * (size_t)n * sizeof(double)));
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tridiag_coop, 256, 2 * (size_t)n * sizeof(double));
   const int G = std::min(std::min(c->nsm * std::max(per_sm, 0), 128), std::max(1, n / 2));
   if (coop && per_sm > 0 && n >= 64) {
     double* scr = y_end(tw, n, nroots);            // v, p, partials, alpha
@@ -531,7 +551,9 @@ int tda_solve(rsx_ctx* c, const double* eo, int no, const double* ev, int nv, co
     cudaMemsetAsync(gb, 0, sizeof(GridBar), s);
     void* args[] = {(void*)&A, (void*)&n, (void*)&d, (void*)&e, (void*)&tau, (void*)&scr, (void*)&gb,
                     (void*)&c->status};
-    cudaError_t err = cudaLaunchCooperativeKernel((const void*)k_tridiag_coop, dim3(G), dim3(256), args, 0, s);
+    const size_t smem = 2 * (size_t)n * sizeof(double);
+    cudaFuncSetAttribute(k_tridiag_coop, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t err = cudaLaunchCooperativeKernel((const void*)k_tridiag_coop, dim3(G), dim3(256), args, smem, s);
     if (err != cudaSuccess) return check_cuda(c, err, "cooperative tridiagonalisation");
   } else {
     k_tridiagonalise<<<1, kEigThreads, 0, s>>>(A, n, d, e, tau, tw);

@@ -21,6 +21,8 @@
 // giving X[k1 + A k2].  The inverse of that split is the same steps in reverse, so in
 // pass 2 the z spectrum never leaves registers between forward, multiply and inverse.
 #pragma once
+#include <cuda_bf16.h>
+
 #include "rsx_internal.cuh"
 
 namespace rsx {
@@ -413,61 +415,83 @@ __global__ void __launch_bounds__(kThreads) k_spectrum(Geom g, int nq, const Cx<
   constexpr int Hy = LY / 2 + 1, Hz = LZ / 2 + 1;
   const int nplane = g.nz * g.ny;
   const int nwork = nq * g.Hx;
+  auto plane_ptr = [&](int w) {
+    const int ql = w / g.Hx, kx = w - ql * g.Hx;
+    return inter + (size_t)ql * g.inter_elems() + (size_t)kx * nplane;
+  };
+  // the plane is staged in the upper halves [ny, 2 ny) of the D rows; the next plane is
+  // prefetched there once the z transforms of the upper ky columns are done
+  if ((int)blockIdx.x < nwork) prefetch_plane_upper<float>(D, DP, plane_ptr(blockIdx.x), g.nz, g.ny, kThreads);
   for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
     const int ql = w / g.Hx, kx = w - ql * g.Hx;
-    const Cx<float>* P = inter + (size_t)ql * g.inter_elems() + (size_t)kx * nplane;
-    load_plane<kThreads>(D, DP, P, g.nz, g.ny);
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
     __syncthreads();
-    y_forward<float, AY, kThreads>(D, DP, g.nz, g.ny, twy, sc);
+    y_forward<float, AY, kThreads>(D, DP, g.nz, g.ny, twy, sc, g.ny);
     __syncthreads();
     const float wk = (kx == 0 || 2 * kx == g.Mx) ? 1.0f : 2.0f;
     const float* vrow = vhat + (size_t)kx * Hy * Hz;
     uint16_t* hrow = hi + (size_t)ql * ld + (size_t)kx * LY * LZ * 2;
     uint16_t* lrow = lo + (size_t)ql * ld + (size_t)kx * LY * LZ * 2;
-    for (int ky = line; ky < LY; ky += kLinesPerCta) {
-      const int iy = ky <= LY / 2 ? ky : LY - ky;
-      const float* vcol = vrow + (size_t)iy * Hz;
-      constexpr int AIN = (AZ % 2 == 0) ? AZ / 2 : AZ;
-      Cx<float> v[AZ];
+    const int wn = w + (int)gridDim.x;
+    // columns ky: upper half first, then the prefetch of the next plane, then the lower half
+    for (int half = 1; half >= 0; --half) {
+      if (half == 0) {
+        __syncthreads();   // every read of the upper halves is done
+        if (wn < nwork) prefetch_plane_upper<float>(D, DP, plane_ptr(wn), g.nz, g.ny, kThreads);
+      }
+      for (int kyl = line; kyl < LY / 2; kyl += kLinesPerCta) {
+        const int ky = half * (LY / 2) + kyl;
+        const int iy = ky <= LY / 2 ? ky : LY - ky;
+        const float* vcol = vrow + (size_t)iy * Hz;
+        constexpr int AIN = (AZ % 2 == 0) ? AZ / 2 : AZ;
+        Cx<float> v[AZ];
 #pragma unroll
-      for (int a = 0; a < AIN; ++a) {
-        const int z = t + 16 * a;
-        v[a] = (z < g.nz) ? D[z * DP + ky] : cx<float>(0.f, 0.f);
-      }
-      if constexpr (AZ % 2 == 0) {
-        stage1_store_halfin<AZ, -1>(v, t, twz, sc);
-      } else {
-        stage1_store<AZ, -1>(v, t, twz, sc);
-      }
-      __syncwarp();
-      Cx<float> u[16];
-      if (t < AZ) {
-        stage2_load(u, t, sc);
-        Dft<16, -1>::run(u);
-      }
-      __syncwarp();
-      if (t < AZ) {
-#pragma unroll
-        for (int k2 = 0; k2 < 16; ++k2) {
-          const int kz = t + AZ * k2;
-          const float m = sqrtf(wk * __ldg(vcol + (kz <= LZ / 2 ? kz : LZ - kz)) * h3);
-          sc[kz] = cx<float>(u[k2].x * m, u[k2].y * m);
+        for (int a = 0; a < AIN; ++a) {
+          const int z = t + 16 * a;
+          v[a] = (z < g.nz) ? D[z * DP + ky] : cx<float>(0.f, 0.f);
         }
+        if constexpr (AZ % 2 == 0) {
+          stage1_store_halfin<AZ, -1>(v, t, twz, sc);
+        } else {
+          stage1_store<AZ, -1>(v, t, twz, sc);
+        }
+        __syncwarp();
+        Cx<float> u[16];
+        if (t < AZ) {
+          stage2_load(u, t, sc);
+          Dft<16, -1>::run(u);
+        }
+        __syncwarp();
+        if (t < AZ) {
+#pragma unroll
+          for (int k2 = 0; k2 < 16; ++k2) {
+            const int kz = t + AZ * k2;
+            const float m = sqrtf(wk * __ldg(vcol + (kz <= LZ / 2 ? kz : LZ - kz)) * h3);
+            sc[kz] = cx<float>(u[k2].x * m, u[k2].y * m);
+          }
+        }
+        __syncwarp();
+        // 16-byte stores: 4 complex -> 8 bf16 of hi and of lo per lane
+        uint4* hw = reinterpret_cast<uint4*>(hrow + (size_t)ky * LZ * 2);
+        uint4* lw = reinterpret_cast<uint4*>(lrow + (size_t)ky * LZ * 2);
+        for (int q = t; q < LZ / 4; q += 16) {
+          uint32_t hv[4], lv[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            // round-to-nearest-even hardware conversions (re in the low half, im in the high)
+            const Cx<float> c = sc[4 * q + j];
+            const __nv_bfloat162 h2 = __float22bfloat162_rn(make_float2(c.x, c.y));
+            const float2 hf = __bfloat1622float2(h2);
+            const __nv_bfloat162 l2 = __float22bfloat162_rn(make_float2(c.x - hf.x, c.y - hf.y));
+            hv[j] = *reinterpret_cast<const uint32_t*>(&h2);
+            lv[j] = *reinterpret_cast<const uint32_t*>(&l2);
+          }
+          hw[q] = make_uint4(hv[0], hv[1], hv[2], hv[3]);
+          lw[q] = make_uint4(lv[0], lv[1], lv[2], lv[3]);
+        }
+        __syncwarp();
       }
-      __syncwarp();
-      uint32_t* hw = reinterpret_cast<uint32_t*>(hrow + (size_t)ky * LZ * 2);
-      uint32_t* lw = reinterpret_cast<uint32_t*>(lrow + (size_t)ky * LZ * 2);
-      for (int kz = t; kz < LZ; kz += 16) {
-        const Cx<float> c = sc[kz];
-        const uint32_t hx = f32_to_bf16_bits(c.x), hy = f32_to_bf16_bits(c.y);
-        const uint32_t lx = f32_to_bf16_bits(c.x - bf16_bits_to_f32(hx));
-        const uint32_t ly = f32_to_bf16_bits(c.y - bf16_bits_to_f32(hy));
-        hw[kz] = hx | (hy << 16);
-        lw[kz] = lx | (ly << 16);
-      }
-      __syncwarp();
     }
-    __syncthreads();
   }
 }
 

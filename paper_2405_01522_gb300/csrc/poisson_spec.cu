@@ -14,13 +14,19 @@ cudaError_t launch_spectrum_f32(const Geom& g, int nq, const Cx<float>* inter, c
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   const long long nwork = (long long)nq * g.Hx;
-  const int grid = (int)(nwork < 4LL * nsm ? nwork : 4LL * nsm);
   switch (g.Ay) {
 #define RSX_CASE(a)                                                                              \
   case a: {                                                                                      \
     auto k = k_spectrum<a, a>;                                                                   \
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
     if (e != cudaSuccess) return e;                                                              \
+    int per_sm = 1;                                                                              \
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads, smem) != cudaSuccess) { \
+      cudaGetLastError();                                                                        \
+      per_sm = 1;                                                                                \
+    }                                                                                            \
+    const long long cap = (long long)(per_sm > 0 ? per_sm : 1) * nsm;                            \
+    const int grid = (int)(nwork < cap ? nwork : cap);                                           \
     k<<<grid, kThreads, smem, s>>>(g, nq, inter, twy, twz, vhat, h3, hi, lo, ld);                \
     return cudaGetLastError();                                                                   \
   }

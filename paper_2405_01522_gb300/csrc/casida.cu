@@ -109,17 +109,27 @@ int casida_K_f32(rsx_ctx* c, const void* po, int no, const void* pv, int nv, dou
   if (rc) return rc;
   uint16_t* hi = (uint16_t*)c->panel_hi;
   uint16_t* lo = (uint16_t*)c->panel_lo;
-  // zero what the spectrum kernel does not write: columns [ng, ld) and rows [nt, nt_pad)
-  if (ld > ng) {
-    rc = check_cuda(c, cudaMemset2DAsync(hi + ng, ld * 2, 0, (ld - ng) * 2, nt, s), "panel tail");
-    if (!rc) rc = check_cuda(c, cudaMemset2DAsync(lo + ng, ld * 2, 0, (ld - ng) * 2, nt, s), "panel tail");
-    if (rc) return rc;
+  // tile-major panel [ld/64][nrb][128][64]; zero what the spectrum kernel does not write:
+  // whole column blocks past ng, and rows nt .. nt_pad - 1 of the last row block
+  const int nrb = nt_pad / 128;
+  const long long nkb = ld / 64, nkb_used = ng / 64;   // ng is a multiple of 64 for supported edges
+  const size_t kb_bytes = (size_t)nrb * 8192 * 2;
+  for (uint16_t* P : {hi, lo}) {
+    if (nkb > nkb_used) {
+      rc = check_cuda(c, cudaMemsetAsync(P + (size_t)nkb_used * nrb * 8192, 0, (size_t)(nkb - nkb_used) * kb_bytes, s),
+                      "panel tail");
+      if (rc) return rc;
+    }
+    if (nt_pad > nt) {
+      const int r0 = nt % 128;
+      rc = check_cuda(c,
+                      cudaMemset2DAsync(P + (size_t)(nrb - 1) * 8192 + (size_t)r0 * 64, kb_bytes, 0,
+                                        (size_t)(128 - r0) * 64 * 2, nkb, s),
+                      "panel pad");
+      if (rc) return rc;
+    }
   }
-  if (nt_pad > nt) {
-    rc = check_cuda(c, cudaMemsetAsync(hi + (size_t)nt * ld, 0, (size_t)(nt_pad - nt) * ld * 2, s), "panel pad");
-    if (!rc) rc = check_cuda(c, cudaMemsetAsync(lo + (size_t)nt * ld, 0, (size_t)(nt_pad - nt) * ld * 2, s), "panel pad");
-    if (rc) return rc;
-  }
+  if (ng % 64) return set_error(c, RSX_EUNSUPPORTED, "casida_K: spectrum length not a multiple of 64");
   Cx<float>* inter = (Cx<float>*)c->work;
   {
     ProfScope ps(c, kKPass1, s);
@@ -131,14 +141,14 @@ int casida_K_f32(rsx_ctx* c, const void* po, int no, const void* pv, int nv, dou
     ProfScope ps(c, kKSpectrum, s);
     rc = check_cuda(c,
                     launch_spectrum_f32(g, nt, inter, (const Cx<float>*)c->tw[1], (const Cx<float>*)c->tw[0],
-                                        (const float*)c->vhat, h3, hi, lo, (size_t)ld, s),
+                                        (const float*)c->vhat, h3, hi, lo, (size_t)ld, nrb, s),
                     "spectrum panel");
   }
   if (rc) return rc;
   const int nsplit = syrk_splits(c->nsm, nt);
   rc = grow(c, &c->gemm_part, &c->gemm_part_bytes, syrk_partial_bytes(nt, nsplit), "K split partials");
   if (rc) return rc;
-  return syrk_bf16x3(c, hi, lo, nt, ld, nsplit, (double*)c->gemm_part, K, s);
+  return syrk_bf16x3(c, hi, lo, nt, ld, nsplit, (double*)c->gemm_part, K, s, true);
 }
 
 template <typename R>

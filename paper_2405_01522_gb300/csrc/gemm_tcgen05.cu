@@ -147,7 +147,7 @@ __device__ __forceinline__ void tile_ij(int tile, int nb, int& I, int& J) {
 
 __global__ void __launch_bounds__(kGemmThreads, 1)
     k_syrk_bf16x3(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo, int nb,
-                  int nkb, int nsplit, double* __restrict__ part, int* status) {
+                  int nkb, int nsplit, int blocked, double* __restrict__ part, int* status) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // 1024-byte aligned operand ring
   unsigned char* ring = reinterpret_cast<unsigned char*>(
@@ -203,12 +203,19 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         const uint32_t ph = (uint32_t)((it / kStages) & 1);
         if (it >= kStages && !mbar_wait(&empty_bar[s], ph ^ 1u, abort_flag)) break;
         unsigned char* st = ring + (size_t)s * kStageBytes;
-        mbar_arrive_expect_tx(&full_bar[s], kStageBytes);
-        const int k = kb * kBK;
-        tma_load_2d(st + 0 * kTileBytes, &tm_hi, &full_bar[s], k, I * kBM);
-        tma_load_2d(st + 1 * kTileBytes, &tm_lo, &full_bar[s], k, I * kBM);
-        tma_load_2d(st + 2 * kTileBytes, &tm_hi, &full_bar[s], k, J * kBN);
-        tma_load_2d(st + 3 * kTileBytes, &tm_lo, &full_bar[s], k, J * kBN);
+        // diagonal tiles (I == J) read one operand pair and use it on both sides
+        mbar_arrive_expect_tx(&full_bar[s], I == J ? 2 * kTileBytes : kStageBytes);
+        // row-major panel: box at (k, row); tile-major panel: box (kb, row block) is the
+        // contiguous 128 x 64 block number kb * nb + row block
+        const int kx = blocked ? 0 : kb * kBK;
+        const int ri = blocked ? (kb * nb + I) * kBM : I * kBM;
+        const int rj = blocked ? (kb * nb + J) * kBN : J * kBN;
+        tma_load_2d(st + 0 * kTileBytes, &tm_hi, &full_bar[s], kx, ri);
+        tma_load_2d(st + 1 * kTileBytes, &tm_lo, &full_bar[s], kx, ri);
+        if (I != J) {
+          tma_load_2d(st + 2 * kTileBytes, &tm_hi, &full_bar[s], kx, rj);
+          tma_load_2d(st + 3 * kTileBytes, &tm_lo, &full_bar[s], kx, rj);
+        }
         issued = it + 1;
       }
       // drain: every issued stage's copies must have landed before the CTA exits
@@ -243,8 +250,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
           const uint32_t base = smem_u32(ring + (size_t)s * kStageBytes);
           const uint64_t dh_i = sw128_desc(base + 0 * kTileBytes);
           const uint64_t dl_i = sw128_desc(base + 1 * kTileBytes);
-          const uint64_t dh_j = sw128_desc(base + 2 * kTileBytes);
-          const uint64_t dl_j = sw128_desc(base + 3 * kTileBytes);
+          const uint64_t dh_j = I == J ? dh_i : sw128_desc(base + 2 * kTileBytes);
+          const uint64_t dl_j = I == J ? dl_i : sw128_desc(base + 3 * kTileBytes);
 #pragma unroll
           for (int j = 0; j < kBK / 16; ++j) {
             const uint64_t adv = (uint64_t)((j * 32) >> 4);   // 16 bf16 = 32 bytes along K
@@ -344,11 +351,14 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
-bool make_map(CUtensorMap* m, const void* base, int rows, long long ld) {
+// 2-D view of a panel: row-major [rows][ld], or tile-major as [rows * ld / 64][64]
+bool make_map(CUtensorMap* m, const void* base, int rows, long long ld, bool blocked) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return false;
-  cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  const long long inner = blocked ? kBK : ld;
+  const long long outer = blocked ? (long long)rows * (ld / kBK) : rows;
+  cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
+  cuuint64_t strides[1] = {(cuuint64_t)inner * 2};
   cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)kBM};
   cuuint32_t es[2] = {1, 1};
   return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
@@ -371,16 +381,17 @@ size_t syrk_partial_bytes(int n, int nsplit) {
   return (size_t)tiles * nsplit * kBM * kBN * sizeof(double);
 }
 
-// hi, lo: [n_pad][ld] bf16 with n_pad = 128 * ceil(n / 128) rows (rows >= n zero), ld % 64 == 0
+// hi, lo: bf16 panels of n_pad = 128 * ceil(n / 128) rows (rows >= n zero) and ld % 64 == 0
+// columns, row-major [n_pad][ld] or (blocked) tile-major [ld / 64][n_pad / 128][128][64]
 int syrk_bf16x3(rsx_ctx* c, const uint16_t* hi, const uint16_t* lo, int n, long long ld, int nsplit, double* part,
-                double* C, cudaStream_t s) {
+                double* C, cudaStream_t s, bool blocked) {
   if (n < 1 || ld < kBK || ld % kBK) return set_error(c, RSX_EINVAL, "syrk: need n >= 1 and ld a multiple of 64");
   if ((reinterpret_cast<uintptr_t>(hi) | reinterpret_cast<uintptr_t>(lo)) & 15)
     return set_error(c, RSX_EINVAL, "syrk: panels must be 16-byte aligned");
   const int nb = (n + kBM - 1) / kBM;
   const int tiles = nb * (nb + 1) / 2;
   CUtensorMap mh, ml;
-  if (!make_map(&mh, hi, nb * kBM, ld) || !make_map(&ml, lo, nb * kBM, ld))
+  if (!make_map(&mh, hi, nb * kBM, ld, blocked) || !make_map(&ml, lo, nb * kBM, ld, blocked))
     return set_error(c, RSX_ECUDA, "syrk: cuTensorMapEncodeTiled failed");
   const int nkb = (int)(ld / kBK);
   const size_t smem = (size_t)kStages * kStageBytes + 1024;
@@ -388,7 +399,8 @@ int syrk_bf16x3(rsx_ctx* c, const uint16_t* hi, const uint16_t* lo, int n, long 
   if (e != cudaSuccess) return check_cuda(c, e, "syrk smem attribute");
   {
     ProfScope ps(c, kKGemm, s);
-    k_syrk_bf16x3<<<tiles * nsplit, kGemmThreads, smem, s>>>(mh, ml, nb, nkb, nsplit, part, c->status);
+    k_syrk_bf16x3<<<tiles * nsplit, kGemmThreads, smem, s>>>(mh, ml, nb, nkb, nsplit, blocked ? 1 : 0, part,
+                                                              c->status);
     e = cudaGetLastError();
   }
   if (e != cudaSuccess) return check_cuda(c, e, "syrk launch");

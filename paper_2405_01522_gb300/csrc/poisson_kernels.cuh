@@ -389,7 +389,7 @@ __global__ void __launch_bounds__(NT, 1) k_pass2(Geom g, int nq, Cx<R>* __restri
   }
 }
 
-// Casida pair spectra: per (transition q, kx) plane, y forward and z forward, then
+// Casida pair spectra (panel tile-major, see below): per (transition q, kx) plane, y forward and z forward, then
 // S_q(G) = sqrt(w_kx * ghat(G) * h^6 / N_pad) * (Re, Im) R_q(G) with w = 1 at kx = 0, Mx/2
 // and 2 otherwise, split into bf16 hi + lo and written to panel row q at column
 // 2 * ((kx * My + ky) * Mz + kz) + {0, 1}.  vhat holds ghat * h^3 / N_pad, so the
@@ -400,7 +400,7 @@ __global__ void __launch_bounds__(kThreads) k_spectrum(Geom g, int nq, const Cx<
                                                        const Cx<float>* __restrict__ twz,
                                                        const float* __restrict__ vhat, float h3,
                                                        uint16_t* __restrict__ hi, uint16_t* __restrict__ lo,
-                                                       size_t ld) {
+                                                       size_t ld, int nrb) {
   constexpr int LY = 16 * AY;
   constexpr int LZ = 16 * AZ;
   constexpr int AMAX = AY > AZ ? AY : AZ;
@@ -430,8 +430,10 @@ __global__ void __launch_bounds__(kThreads) k_spectrum(Geom g, int nq, const Cx<
     __syncthreads();
     const float wk = (kx == 0 || 2 * kx == g.Mx) ? 1.0f : 2.0f;
     const float* vrow = vhat + (size_t)kx * Hy * Hz;
-    uint16_t* hrow = hi + (size_t)ql * ld + (size_t)kx * LY * LZ * 2;
-    uint16_t* lrow = lo + (size_t)ql * ld + (size_t)kx * LY * LZ * 2;
+    // tile-major panel [ld/64][nrb][128][64]: column g of row ql is at
+    // ((g / 64) * nrb + ql / 128) * 8192 + (ql % 128) * 64 + g % 64
+    const size_t row_off = (size_t)(ql / 128) * 8192 + (size_t)(ql % 128) * 64;
+    const size_t kb_stride = (size_t)nrb * 8192;
     const int wn = w + (int)gridDim.x;
     // columns ky: upper half first, then the prefetch of the next plane, then the lower half
     for (int half = 1; half >= 0; --half) {
@@ -471,10 +473,12 @@ __global__ void __launch_bounds__(kThreads) k_spectrum(Geom g, int nq, const Cx<
           }
         }
         __syncwarp();
-        // 16-byte stores: 4 complex -> 8 bf16 of hi and of lo per lane
-        uint4* hw = reinterpret_cast<uint4*>(hrow + (size_t)ky * LZ * 2);
-        uint4* lw = reinterpret_cast<uint4*>(lrow + (size_t)ky * LZ * 2);
+        // 16-byte stores: 4 complex -> 8 bf16 of hi and of lo per lane (never straddle a
+        // 64-column block: the line starts at a multiple of 32 columns)
+        const size_t g0 = ((size_t)kx * LY + ky) * LZ * 2;
         for (int q = t; q < LZ / 4; q += 16) {
+          const size_t gq = g0 + 8 * (size_t)q;
+          const size_t off = (gq / 64) * kb_stride + row_off + (gq % 64);
           uint32_t hv[4], lv[4];
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
@@ -486,8 +490,8 @@ __global__ void __launch_bounds__(kThreads) k_spectrum(Geom g, int nq, const Cx<
             hv[j] = *reinterpret_cast<const uint32_t*>(&h2);
             lv[j] = *reinterpret_cast<const uint32_t*>(&l2);
           }
-          hw[q] = make_uint4(hv[0], hv[1], hv[2], hv[3]);
-          lw[q] = make_uint4(lv[0], lv[1], lv[2], lv[3]);
+          *reinterpret_cast<uint4*>(hi + off) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
+          *reinterpret_cast<uint4*>(lo + off) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
         }
         __syncwarp();
       }

@@ -5,7 +5,7 @@ namespace rsx {
 
 cudaError_t launch_spectrum_f32(const Geom& g, int nq, const Cx<float>* inter, const Cx<float>* twy,
                                 const Cx<float>* twz, const float* vhat, float h3, uint16_t* hi,
-                                uint16_t* lo, size_t ld, cudaStream_t s) {
+                                uint16_t* lo, size_t ld, int nrb, cudaStream_t s) {
   if (nq <= 0) return cudaSuccess;
   if (g.Ay != g.Az) return cudaErrorInvalidValue;
   const size_t smem = pass2_scratch_smem<float>(g.Ay, g.Az, kThreads) + pass2_plane_bytes<float>(g);
@@ -27,7 +27,7 @@ cudaError_t launch_spectrum_f32(const Geom& g, int nq, const Cx<float>* inter, c
     }                                                                                            \
     const long long cap = (long long)(per_sm > 0 ? per_sm : 1) * nsm;                            \
     const int grid = (int)(nwork < cap ? nwork : cap);                                           \
-    k<<<grid, kThreads, smem, s>>>(g, nq, inter, twy, twz, vhat, h3, hi, lo, ld);                \
+    k<<<grid, kThreads, smem, s>>>(g, nq, inter, twy, twz, vhat, h3, hi, lo, ld, nrb);                \
     return cudaGetLastError();                                                                   \
   }
     RSX_FOR_EACH_A(RSX_CASE)

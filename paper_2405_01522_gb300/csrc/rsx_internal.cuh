@@ -80,10 +80,10 @@ template <typename R>
 cudaError_t launch_pass3(const Geom& g, const PairMap<R>& pm, int q0, int p0, int np, int pot, const Cx<R>* inter,
                          const Cx<R>* twx, R* out, cudaStream_t s);
 // forward y/z transform of each pair plane, weighted by sqrt(w_G vhat(G) h^3) and split
-// into bf16 hi/lo rows of the K panel (t-major, G contiguous)
+// into bf16 hi/lo of the K panel, tile-major [ld/64][nrb][128][64] (nrb row blocks of 128)
 cudaError_t launch_spectrum_f32(const Geom& g, int nq, const Cx<float>* inter, const Cx<float>* twy,
                                 const Cx<float>* twz, const float* vhat, float h3, uint16_t* hi,
-                                uint16_t* lo, size_t ld, cudaStream_t s);
+                                uint16_t* lo, size_t ld, int nrb, cudaStream_t s);
 template <typename R>
 size_t pass2_smem_bytes(const Geom& g, bool* fits);
 template <typename R>

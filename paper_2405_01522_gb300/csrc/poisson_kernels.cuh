@@ -394,8 +394,8 @@ __global__ void __launch_bounds__(NT, 1) k_pass2(Geom g, int nq, Cx<R>* __restri
 // and 2 otherwise, split into bf16 hi + lo and written to panel row q at column
 // 2 * ((kx * My + ky) * Mz + kz) + {0, 1}.  vhat holds ghat * h^3 / N_pad, so the
 // weight is sqrt(w * vhat * h^3).
-template <int AY, int AZ>
-__global__ void __launch_bounds__(kThreads) k_spectrum(Geom g, int nq, const Cx<float>* __restrict__ inter,
+template <int AY, int AZ, int NT>
+__global__ void __launch_bounds__(NT) k_spectrum(Geom g, int nq, const Cx<float>* __restrict__ inter,
                                                        const Cx<float>* __restrict__ twy,
                                                        const Cx<float>* __restrict__ twz,
                                                        const float* __restrict__ vhat, float h3,
@@ -406,9 +406,10 @@ __global__ void __launch_bounds__(kThreads) k_spectrum(Geom g, int nq, const Cx<
   constexpr int AMAX = AY > AZ ? AY : AZ;
   constexpr int SP = AMAX * kScrPitch;
   constexpr int DP = LY + 1;
+  constexpr int LPC = NT / 16;   // lines per CTA (one per half-warp)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Cx<float>* scr = reinterpret_cast<Cx<float>*>(smem_raw);
-  Cx<float>* D = scr + kLinesPerCta * SP;
+  Cx<float>* D = scr + LPC * SP;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int t = lane & 15, line = warp * 2 + (lane >> 4);
   Cx<float>* sc = scr + line * SP;
@@ -421,12 +422,12 @@ __global__ void __launch_bounds__(kThreads) k_spectrum(Geom g, int nq, const Cx<
   };
   // the plane is staged in the upper halves [ny, 2 ny) of the D rows; the next plane is
   // prefetched there once the z transforms of the upper ky columns are done
-  if ((int)blockIdx.x < nwork) prefetch_plane_upper<float>(D, DP, plane_ptr(blockIdx.x), g.nz, g.ny, kThreads);
+  if ((int)blockIdx.x < nwork) prefetch_plane_upper<float>(D, DP, plane_ptr(blockIdx.x), g.nz, g.ny, NT);
   for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
     const int ql = w / g.Hx, kx = w - ql * g.Hx;
     asm volatile("cp.async.wait_group 0;" ::: "memory");
     __syncthreads();
-    y_forward<float, AY, kThreads>(D, DP, g.nz, g.ny, twy, sc, g.ny);
+    y_forward<float, AY, NT>(D, DP, g.nz, g.ny, twy, sc, g.ny);
     __syncthreads();
     const float wk = (kx == 0 || 2 * kx == g.Mx) ? 1.0f : 2.0f;
     const float* vrow = vhat + (size_t)kx * Hy * Hz;
@@ -439,9 +440,9 @@ __global__ void __launch_bounds__(kThreads) k_spectrum(Geom g, int nq, const Cx<
     for (int half = 1; half >= 0; --half) {
       if (half == 0) {
         __syncthreads();   // every read of the upper halves is done
-        if (wn < nwork) prefetch_plane_upper<float>(D, DP, plane_ptr(wn), g.nz, g.ny, kThreads);
+        if (wn < nwork) prefetch_plane_upper<float>(D, DP, plane_ptr(wn), g.nz, g.ny, NT);
       }
-      for (int kyl = line; kyl < LY / 2; kyl += kLinesPerCta) {
+      for (int kyl = line; kyl < LY / 2; kyl += LPC) {
         const int ky = half * (LY / 2) + kyl;
         const int iy = ky <= LY / 2 ? ky : LY - ky;
         const float* vcol = vrow + (size_t)iy * Hz;

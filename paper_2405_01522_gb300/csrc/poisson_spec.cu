@@ -8,7 +8,14 @@ cudaError_t launch_spectrum_f32(const Geom& g, int nq, const Cx<float>* inter, c
                                 uint16_t* lo, size_t ld, int nrb, cudaStream_t s) {
   if (nq <= 0) return cudaSuccess;
   if (g.Ay != g.Az) return cudaErrorInvalidValue;
-  const size_t smem = pass2_scratch_smem<float>(g.Ay, g.Az, kThreads) + pass2_plane_bytes<float>(g);
+  // 512 threads (32 lines in flight) where the kernel fits 128 registers without spills
+  // (A <= 12) and the shared memory allows it, else 256
+  int nt = 512;
+  size_t smem = pass2_scratch_smem<float>(g.Ay, g.Az, nt) + pass2_plane_bytes<float>(g);
+  if (g.Ay > 12 || smem > (size_t)max_dyn_smem()) {
+    nt = 256;
+    smem = pass2_scratch_smem<float>(g.Ay, g.Az, nt) + pass2_plane_bytes<float>(g);
+  }
   if (smem > (size_t)max_dyn_smem()) return cudaErrorInvalidValue;
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
@@ -17,17 +24,17 @@ cudaError_t launch_spectrum_f32(const Geom& g, int nq, const Cx<float>* inter, c
   switch (g.Ay) {
 #define RSX_CASE(a)                                                                              \
   case a: {                                                                                      \
-    auto k = k_spectrum<a, a>;                                                                   \
+    auto k = (nt == 512 && a <= 12) ? k_spectrum<a, a, 512> : k_spectrum<a, a, 256>;             \
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
     if (e != cudaSuccess) return e;                                                              \
     int per_sm = 1;                                                                              \
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads, smem) != cudaSuccess) { \
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, nt, smem) != cudaSuccess) {    \
       cudaGetLastError();                                                                        \
       per_sm = 1;                                                                                \
     }                                                                                            \
     const long long cap = (long long)(per_sm > 0 ? per_sm : 1) * nsm;                            \
     const int grid = (int)(nwork < cap ? nwork : cap);                                           \
-    k<<<grid, kThreads, smem, s>>>(g, nq, inter, twy, twz, vhat, h3, hi, lo, ld, nrb);                \
+    k<<<grid, nt, smem, s>>>(g, nq, inter, twy, twz, vhat, h3, hi, lo, ld, nrb);                \
     return cudaGetLastError();                                                                   \
   }
     RSX_FOR_EACH_A(RSX_CASE)

@@ -194,7 +194,9 @@ const char* rsx_eig_last_error(const rsx_eig* eig);
 int rsx_eig_destroy(rsx_eig* eig);
 
 /* Learned preconditioner network: conv3d(2 -> 16) ReLU conv3d(16 -> 16) ReLU conv3d(16 -> 1),
- * 3^3 kernels, zero padding 1, weights used in bf16, FP32 activations and accumulation.
+ * 3^3 kernels, zero padding 1, weights used in bf16, FP32 activations; every convolution
+ * (forward and data gradient) runs on the tensor cores with each activation split into
+ * bf16 hi + lo, FP32 accumulation.
  * Parameters (rsx_net_param_count() floats): w1 [16][2][27], b1 [16], w2 [16][16][27],
  * b2 [16], w3 [1][16][27], b3 [1]; taps t = 9 dz + 3 dy + dx.  Inputs x: device
  * [B][2][D][H][W]; outputs [B][D][H][W].  Loss: mean over voxels at least `border` from
@@ -209,6 +211,10 @@ int rsx_net_loss_grad(rsx_net* net, const float* x, const float* target, int B, 
                       double* loss_host, float* grad_host, void* stream);
 int rsx_net_train_step(rsx_net* net, const float* x, const float* target, int B, int D, int H, int W, int border,
                        float lr, double* loss_host, void* stream);
+/* Synchronises the stream, then returns (and clears) a deferred device error of the network
+ * kernels: RSX_ETIMEOUT when a tensor-core convolution gave up one of its bounded waits
+ * (its outputs are then incomplete).  rsx_eig_step checks it after its own synchronisation. */
+int rsx_net_sync_status(rsx_net* net, void* stream);
 const char* rsx_net_last_error(const rsx_net* net);
 int rsx_net_destroy(rsx_net* net);
 

@@ -3,11 +3,10 @@
 // masters updated by Adam), FP32 activations and accumulation.  The paper has no
 // learned component; this is the eigensolver preconditioner the project adds.
 //
-// Kernels: k_conv_fwd (direct convolution, a CTA computes an 8 x 8 x 8 output block for
-// all output channels from a shared-memory halo tile), the data gradient as the same
-// convolution with flipped, transposed weights (k_flip_weights), k_conv_wgrad (per-block
-// partial sums, reduced in fixed order by k_wgrad_reduce), masked MSE loss, ReLU
-// backward and Adam.
+// Kernels: k_conv_tc (the convolution as an implicit GEMM on the tcgen05 tensor cores,
+// see below), the data gradient as the same convolution with flipped, transposed weights
+// (k_flip_weights), k_conv_wgrad (per-block partial sums, reduced in fixed order by
+// k_wgrad_reduce), masked MSE loss, ReLU backward and Adam.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -16,8 +15,11 @@
 #include <cstring>
 #include <vector>
 
+#include <cuda_bf16.h>
+
 #include "../../include/rsx.h"
 #include "api_internal.cuh"
+#include "tcgen05_util.cuh"
 
 namespace {
 
@@ -35,75 +37,220 @@ __device__ __forceinline__ float bf16_round(float f) {
   return __uint_as_float(((u + 0x7FFFu + ((u >> 16) & 1u)) >> 16) << 16);
 }
 
-// out[b][co][v] = bias[co] + sum_{ci,tap} w[co][ci][tap] * act(in[b][ci][v + tap - 1])
-// act = ReLU on the input when relu_in (the previous layer's activation).
-// Grid: (blocks of 8^3) x B.  Each thread owns 2 voxels (z, z+4) x CO outputs.
+// ---------------------------------------------------------------------------------
+// 3^3 convolution as an implicit GEMM on the tensor cores:
+//   out[b][co][v] = bias[co] + sum_{t, ci} w[co][ci][t] act(in[b][ci][v + t - 1])
+// (act = ReLU of the previous layer's pre-activation when relu_in, else identity).
+// A CTA owns an 8 (x) by 16 (y) block of output voxels over kTcZ consecutive z slices.
+// Per slice the GEMM has rows m = 8 yl + xl (128 voxels), columns n = output channel
+// (16, zero-padded when CO < 16) and K = 27 taps x 16 input channels (zero-padded when
+// CI < 16): one tcgen05.mma (M = 128, N = 16, K = 16) per tap and activation part.  The
+// activations are split into bf16 hi + lo (x - hi - lo ~ 2^-17 |x|) and both parts are
+// multiplied by the bf16-rounded weights, so the products keep FP32-level accuracy; the
+// accumulation is FP32 in TMEM (two 16-column buffers: slice i accumulates while slice
+// i - 1 is read back and stored).
+//
+// The input planes z - 1, z, z + 1 of the halo (18 y x 10 x voxels, 16 channels) sit in
+// a 3-slot ring in the no-swizzle K-major operand layout plane[yh][khalf][xh][8 ch]
+// (16 B per (yh, khalf, xh)), so that the A operand of tap (dz, dy, dx) is the plane of
+// slot (slice + dz) % 3 started dy rows and dx voxels in: row m = 8 yl + xl sits at
+// (yl + dy) 320 + (xl + dx) 16 bytes, the two K halves 160 bytes apart (leading byte
+// offset) and 8-row groups 320 bytes apart (stride byte offset).  No im2col copy exists.
+// Weights: tap t at 512 t bytes, element (co, ci) at (co/8) 256 + (ci/8) 128 + (co%8) 16
+// + (ci%8) 2.  Every wait is bounded; a timeout sets RSX_ETIMEOUT in the status word and
+// the CTA drains, frees its TMEM and returns.
+constexpr int kTcThreads = 128;
+constexpr int kTcX = 8, kTcY = 16, kTcZ = 16;         // output block of one CTA
+constexpr int kHY = kTcY + 2, kHX = kTcX + 2;          // halo plane 18 x 10
+constexpr int kHalfBytes = kHX * 16;                   // 160: one K half of a halo row
+constexpr int kRowBytes = 2 * kHalfBytes;              // 320: one halo row (both K halves)
+constexpr int kPlaneBytes = kHY * kRowBytes;           // 5760
+constexpr int kTapBytes = 512;                         // 16 x 16 bf16 weights of one tap
+constexpr int kTcSmem = 6 * kPlaneBytes + 27 * kTapBytes;   // 3 slots x (hi, lo) + weights
+constexpr int kHaloVox = kHY * kHX;                    // 180
+constexpr int kStageRounds = (kHaloVox + kTcThreads - 1) / kTcThreads;
+// instruction descriptor, kind::f16: D f32, A and B bf16, both K-major, M = 128, N = 16
+constexpr uint32_t kConvIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
+
+// shared-memory matrix descriptor, K-major without swizzle: 8 x 16 B core matrices,
+// `lbo` bytes between K-adjacent and `sbo` bytes between M/N-adjacent core matrices
+__device__ __forceinline__ uint64_t kmajor_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;   // descriptor version for tcgen05; swizzle bits 61-63 stay 0
+  return d;
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo_half, float hi_half) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo_half, hi_half);
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+
 template <int CI, int CO>
-__global__ void __launch_bounds__(kConvThreads) k_conv_fwd(const float* __restrict__ in, const float* __restrict__ w,
-                                                           const float* __restrict__ bias, float* __restrict__ out,
-                                                           int D, int H, int W, int relu_in) {
-  constexpr int CCH = CI < 4 ? CI : 4;   // input channels staged per round
-  __shared__ float tile[CCH][kHalo][kHalo][kHalo];
-  __shared__ float ws[CO][CCH][27];
-  const int nbx = (W + kT - 1) / kT, nby = (H + kT - 1) / kT;
+__global__ void __launch_bounds__(kTcThreads) k_conv_tc(const float* __restrict__ in, const float* __restrict__ w,
+                                                        const float* __restrict__ bias, float* __restrict__ out, int D,
+                                                        int H, int W, int relu_in, int* status) {
+  static_assert(CI <= 16 && CO <= 16, "channels per layer <= 16");
+  using namespace rsx::tc;
+  extern __shared__ __align__(128) unsigned char sm[];
+  unsigned char* ring = sm;                             // slot s, part p (0 hi, 1 lo): (2 s + p) * kPlaneBytes
+  unsigned char* wsm = sm + 6 * kPlaneBytes;
+  __shared__ __align__(8) uint64_t mma_bar;
+  __shared__ uint32_t tmem_sh;
+  __shared__ int abort_sh;
+
+  const int nbx = (W + kTcX - 1) / kTcX, nby = (H + kTcY - 1) / kTcY;
   int blk = blockIdx.x;
   const int bx = blk % nbx;
   blk /= nbx;
   const int by = blk % nby;
   const int bz = blk / nby;
   const int b = blockIdx.y;
-  const int x0 = bx * kT, y0 = by * kT, z0 = bz * kT;
-  const int tx = threadIdx.x & 7, ty = (threadIdx.x >> 3) & 7, tz = threadIdx.x >> 6;  // tz 0..3
+  const int x0 = bx * kTcX, y0 = by * kTcY, z0 = bz * kTcZ;
+  const int nzl = min(kTcZ, D - z0);
   const size_t vol = (size_t)D * H * W;
-  float acc0[CO], acc1[CO];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  // zero the ring (channels >= CI stay zero), weights into the B operand layout
+  for (int i = tid; i < 6 * kPlaneBytes / 16; i += kTcThreads) reinterpret_cast<uint4*>(ring)[i] = make_uint4(0, 0, 0, 0);
+  for (int i = tid; i < 27 * 256; i += kTcThreads) {
+    const int t = i >> 8, co = (i >> 4) & 15, ci = i & 15;
+    const float v = (co < CO && ci < CI) ? w[((size_t)co * CI + ci) * 27 + t] : 0.f;
+    *reinterpret_cast<__nv_bfloat16*>(wsm + t * kTapBytes + (co >> 3) * 256 + (ci >> 3) * 128 + (co & 7) * 16 +
+                                      (ci & 7) * 2) = __float2bfloat16_rn(v);
+  }
+  if (tid == 0) {
+    abort_sh = 0;
+    mbar_init(&mma_bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_sh)), "r"(32)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+
+  // halo voxel e = tid + 128 r of a plane: (yh, xh) = (e / 10, e % 10)
+  float v[kStageRounds][CI];
+  auto load_plane = [&](int z) {
 #pragma unroll
-  for (int o = 0; o < CO; ++o) acc0[o] = acc1[o] = bias ? bias[o] : 0.f;
-  for (int c0 = 0; c0 < CI; c0 += CCH) {
-    __syncthreads();
-    for (int i = threadIdx.x; i < CCH * kHalo * kHalo * kHalo; i += kConvThreads) {
-      const int c = i / (kHalo * kHalo * kHalo);
-      int r = i - c * kHalo * kHalo * kHalo;
-      const int hz = r / (kHalo * kHalo);
-      r -= hz * kHalo * kHalo;
-      const int hy = r / kHalo, hx = r - hy * kHalo;
-      const int z = z0 + hz - 1, y = y0 + hy - 1, x = x0 + hx - 1;
-      float v = 0.f;
-      if (c0 + c < CI && z >= 0 && z < D && y >= 0 && y < H && x >= 0 && x < W) {
-        v = in[((size_t)b * CI + c0 + c) * vol + ((size_t)z * H + y) * W + x];
-        if (relu_in) v = fmaxf(v, 0.f);
+    for (int r = 0; r < kStageRounds; ++r) {
+      const int e = tid + r * kTcThreads;
+      const int yh = e / kHX, xh = e - yh * kHX;
+      const int y = y0 - 1 + yh, x = x0 - 1 + xh;
+      const bool inside = e < kHaloVox && z >= 0 && z < D && y >= 0 && y < H && x >= 0 && x < W;
+      const float* src = in + (size_t)b * CI * vol + ((size_t)(inside ? z : 0) * H + (inside ? y : 0)) * W + (inside ? x : 0);
+#pragma unroll
+      for (int ci = 0; ci < CI; ++ci) {
+        float a = inside ? __ldg(src + (size_t)ci * vol) : 0.f;
+        v[r][ci] = relu_in ? fmaxf(a, 0.f) : a;
       }
-      tile[c][hz][hy][hx] = v;
     }
-    for (int i = threadIdx.x; i < CO * CCH * 27; i += kConvThreads) {
-      const int o = i / (CCH * 27), r = i - o * CCH * 27, c = r / 27, t = r - c * 27;
-      ws[o][c][t] = (c0 + c < CI) ? bf16_round(w[((size_t)o * CI + c0 + c) * 27 + t]) : 0.f;
-    }
-    __syncthreads();
-#pragma unroll 1
-    for (int c = 0; c < CCH; ++c) {
+  };
+  auto store_plane = [&](int slot) {
 #pragma unroll
+    for (int r = 0; r < kStageRounds; ++r) {
+      const int e = tid + r * kTcThreads;
+      if (e >= kHaloVox) continue;
+      const int yh = e / kHX, xh = e - yh * kHX;
+#pragma unroll
+      for (int half = 0; half < (CI + 7) / 8; ++half) {
+        uint32_t hv[4], lv[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int c0 = half * 8 + 2 * j, c1 = c0 + 1;
+          const float a0 = c0 < CI ? v[r][c0 < CI ? c0 : 0] : 0.f;
+          const float a1 = c1 < CI ? v[r][c1 < CI ? c1 : 0] : 0.f;
+          const __nv_bfloat162 h2 = __floats2bfloat162_rn(a0, a1);
+          const float2 hf = __bfloat1622float2(h2);
+          hv[j] = *reinterpret_cast<const uint32_t*>(&h2);
+          lv[j] = pack_bf16x2(a0 - hf.x, a1 - hf.y);
+        }
+        const size_t off = (size_t)yh * kRowBytes + half * kHalfBytes + xh * 16;
+        *reinterpret_cast<uint4*>(ring + (size_t)(2 * slot) * kPlaneBytes + off) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
+        *reinterpret_cast<uint4*>(ring + (size_t)(2 * slot + 1) * kPlaneBytes + off) =
+            make_uint4(lv[0], lv[1], lv[2], lv[3]);
+      }
+    }
+  };
+
+  __syncthreads();   // ring zeroed before the first plane is written
+  // planes z0 - 1 + j live in slot j % 3
+  load_plane(z0 - 1);
+  store_plane(0);
+  load_plane(z0);
+  store_plane(1);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_sh;
+  const uint32_t ring_s = smem_u32(ring), w_s = smem_u32(wsm);
+  volatile int* abort_flag = &abort_sh;
+  int issued = 0, waited = 0;
+
+  auto epilogue = [&](int i) {
+    const int m = warp * 32 + lane;                     // TMEM lane = GEMM row
+    const int yl = m >> 3, xl = m & 7;
+    const int z = z0 + i, y = y0 + yl, x = x0 + xl;
+    float acc[16];
+    tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)((i & 1) * 16), acc);
+    if (y < H && x < W) {
+#pragma unroll
+      for (int co = 0; co < CO; ++co)
+        out[((size_t)b * CO + co) * vol + ((size_t)z * H + y) * W + x] = acc[co] + (bias ? __ldg(bias + co) : 0.f);
+    }
+  };
+
+  for (int i = 0; i < nzl; ++i) {
+    load_plane(z0 + i + 1);                             // loads in flight while slice i - 1 finishes
+    if (i > 0) {
+      if (tid == 0) {
+        if (!mbar_wait(&mma_bar, (uint32_t)((i - 1) & 1), abort_flag)) *abort_flag = 1;
+        else waited = i;
+      }
+      __syncthreads();
+      if (*abort_flag) break;
+    }
+    store_plane((i + 2) % 3);                           // its slot held plane i - 1, last read by slice i - 1
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (tid == 0) {
+      const uint32_t acc = tmem + (uint32_t)((i & 1) * 16);
+#pragma unroll 1
       for (int t = 0; t < 27; ++t) {
         const int dz = t / 9, dy = (t / 3) % 3, dx = t % 3;
-        const float a0 = tile[c][tz + dz][ty + dy][tx + dx];
-        const float a1 = tile[c][tz + 4 + dz][ty + dy][tx + dx];
-#pragma unroll
-        for (int o = 0; o < CO; ++o) {
-          const float wv = ws[o][c][t];
-          acc0[o] = fmaf(wv, a0, acc0[o]);
-          acc1[o] = fmaf(wv, a1, acc1[o]);
-        }
+        const uint32_t pl = ring_s + (uint32_t)(2 * ((i + dz) % 3)) * kPlaneBytes + dy * kRowBytes + dx * 16;
+        const uint64_t bd = kmajor_desc(w_s + t * kTapBytes, 128, 256);
+        mma_f16(acc, kmajor_desc(pl, kHalfBytes, kRowBytes), bd, kConvIdesc, t > 0 ? 1u : 0u);
+        mma_f16(acc, kmajor_desc(pl + kPlaneBytes, kHalfBytes, kRowBytes), bd, kConvIdesc, 1u);
+      }
+      mma_commit(&mma_bar);
+      issued = i + 1;
+    }
+    if (i > 0) epilogue(i - 1);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  }
+  // last slice (or, after a timeout, drain what was issued)
+  if (tid == 0) {
+    if (!*abort_flag && issued == nzl) {
+      if (!mbar_wait(&mma_bar, (uint32_t)((nzl - 1) & 1), abort_flag)) *abort_flag = 1;
+    } else if (issued > waited) {
+      for (uint32_t k = 0; k < kWaitLimit && !mbar_try_wait(&mma_bar, (uint32_t)((issued - 1) & 1)); ++k) {
       }
     }
+    if (*abort_flag && status) atomicMax(status, RSX_ETIMEOUT);
   }
-  const int x = x0 + tx, y = y0 + ty, za = z0 + tz, zb = z0 + tz + 4;
-  if (x < W && y < H) {
-#pragma unroll
-    for (int o = 0; o < CO; ++o) {
-      float* ob = out + ((size_t)b * CO + o) * vol;
-      if (za < D) ob[((size_t)za * H + y) * W + x] = acc0[o];
-      if (zb < D) ob[((size_t)zb * H + y) * W + x] = acc1[o];
-    }
-  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (!*abort_flag) epilogue(nzl - 1);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(32) : "memory");
 }
 
 // wt[ci][co][26 - t] = w[co][ci][t]: the data gradient is the forward convolution of
@@ -240,6 +387,7 @@ struct rsx_net {
   float* part = nullptr;
   size_t part_elems = 0;
   double* loss = nullptr;
+  int* status = nullptr;     // device status word (RSX_ETIMEOUT from a bounded wait)
   long long step = 0;
   char err[256] = {0};
 };
@@ -274,6 +422,14 @@ dim3 conv_grid(int B, int D, int H, int W) {
   return dim3((unsigned)(((W + kT - 1) / kT) * ((H + kT - 1) / kT) * ((D + kT - 1) / kT)), (unsigned)B);
 }
 
+// one 3^3 convolution layer on the tensor cores (k_conv_tc)
+template <int CI, int CO>
+void conv(rsx_net* n, const float* in, const float* w, const float* bias, float* out, int B, int D, int H, int W,
+          int relu_in, cudaStream_t s) {
+  const dim3 g((unsigned)(((W + kTcX - 1) / kTcX) * ((H + kTcY - 1) / kTcY) * ((D + kTcZ - 1) / kTcZ)), (unsigned)B);
+  k_conv_tc<CI, CO><<<g, kTcThreads, kTcSmem, s>>>(in, w, bias, out, D, H, W, relu_in, n->status);
+}
+
 int forward(rsx_net* n, const float* x, int B, int D, int H, int W, float* out, cudaStream_t s) {
   const size_t vol = (size_t)D * H * W;
   int rc = ngrow(n, &n->act, &n->act_elems, 2 * (size_t)B * kC2 * vol);
@@ -282,9 +438,9 @@ int forward(rsx_net* n, const float* x, int B, int D, int H, int W, float* out, 
   float* z2 = n->act + (size_t)B * kC2 * vol;
   const dim3 g = conv_grid(B, D, H, W);
   const float* P = n->params;
-  k_conv_fwd<kC1, kC2><<<g, kConvThreads, 0, s>>>(x, P + kOffW1, P + kOffB1, z1, D, H, W, 0);
-  k_conv_fwd<kC2, kC3><<<g, kConvThreads, 0, s>>>(z1, P + kOffW2, P + kOffB2, z2, D, H, W, 1);
-  k_conv_fwd<kC3, kC4><<<g, kConvThreads, 0, s>>>(z2, P + kOffW3, P + kOffB3, out, D, H, W, 1);
+  conv<kC1, kC2>(n, x, P + kOffW1, P + kOffB1, z1, B, D, H, W, 0, s);
+  conv<kC2, kC3>(n, z1, P + kOffW2, P + kOffB2, z2, B, D, H, W, 1, s);
+  conv<kC3, kC4>(n, z2, P + kOffW3, P + kOffB3, out, B, D, H, W, 1, s);
   return ncuda(n, cudaGetLastError(), "network forward");
 }
 
@@ -311,13 +467,13 @@ int backward(rsx_net* n, const float* x, const float* target, int B, int D, int 
   k_conv_wgrad<kC3, kC4><<<g, kConvThreads, 0, s>>>(z2, gy, n->part, D, H, W, 1);
   k_wgrad_reduce<<<64, 256, 0, s>>>(n->part, B * nblk, kW3 + kC4, n->grads + kOffW3, n->grads + kOffB3, kW3);
   k_flip_weights<<<16, 256, 0, s>>>(P + kOffW3, n->wflip, kC3, kC4);
-  k_conv_fwd<kC4, kC3><<<g, kConvThreads, 0, s>>>(gy, n->wflip, nullptr, g2, D, H, W, 0);
+  conv<kC4, kC3>(n, gy, n->wflip, nullptr, g2, B, D, H, W, 0, s);
   k_relu_back<<<512, 256, 0, s>>>(g2, z2, (size_t)B * kC2 * vol);
   // layer 2
   k_conv_wgrad<kC2, kC3><<<g, kConvThreads, 0, s>>>(z1, g2, n->part, D, H, W, 1);
   k_wgrad_reduce<<<64, 256, 0, s>>>(n->part, B * nblk, kW2 + kC3, n->grads + kOffW2, n->grads + kOffB2, kW2);
   k_flip_weights<<<32, 256, 0, s>>>(P + kOffW2, n->wflip, kC2, kC3);
-  k_conv_fwd<kC3, kC2><<<g, kConvThreads, 0, s>>>(g2, n->wflip, nullptr, g1, D, H, W, 0);
+  conv<kC3, kC2>(n, g2, n->wflip, nullptr, g1, B, D, H, W, 0, s);
   k_relu_back<<<512, 256, 0, s>>>(g1, z1, (size_t)B * kC2 * vol);
   // layer 1
   k_conv_wgrad<kC1, kC2><<<g, kConvThreads, 0, s>>>(x, g1, n->part, D, H, W, 0);
@@ -342,7 +498,8 @@ int rsx_net_create(rsx_net** out, int device) {
       cudaMalloc(&n->grads, kNParams * sizeof(float)) != cudaSuccess ||
       cudaMalloc(&n->adam_m, kNParams * sizeof(float)) != cudaSuccess ||
       cudaMalloc(&n->adam_v, kNParams * sizeof(float)) != cudaSuccess ||
-      cudaMalloc(&n->wflip, kW2 * sizeof(float)) != cudaSuccess || cudaMalloc(&n->loss, sizeof(double)) != cudaSuccess) {
+      cudaMalloc(&n->wflip, kW2 * sizeof(float)) != cudaSuccess || cudaMalloc(&n->loss, sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&n->status, sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
     rsx_net_destroy(n);
     return RSX_ENOMEM;
@@ -350,6 +507,7 @@ int rsx_net_create(rsx_net** out, int device) {
   cudaMemset(n->params, 0, kNParams * sizeof(float));
   cudaMemset(n->adam_m, 0, kNParams * sizeof(float));
   cudaMemset(n->adam_v, 0, kNParams * sizeof(float));
+  cudaMemset(n->status, 0, sizeof(int));
   *out = n;
   return RSX_OK;
 }
@@ -412,13 +570,30 @@ int rsx_net_train_step(rsx_net* n, const float* x, const float* target, int B, i
   return rc;
 }
 
+// Synchronises the stream, then reports (and clears) a deferred device error of the
+// network kernels: RSX_ETIMEOUT when a tensor-core convolution gave up a bounded wait.
+int rsx_net_sync_status(rsx_net* n, void* stream) {
+  if (!n) return RSX_EINVAL;
+  cudaSetDevice(n->device);
+  int rc = ncuda(n, cudaStreamSynchronize((cudaStream_t)stream), "sync");
+  if (rc) return rc;
+  int st = 0;
+  rc = ncuda(n, cudaMemcpy(&st, n->status, sizeof(int), cudaMemcpyDeviceToHost), "status");
+  if (rc) return rc;
+  if (st != RSX_OK) {
+    cudaMemset(n->status, 0, sizeof(int));
+    return nfail(n, st, "network kernel gave up a bounded wait (timeout)");
+  }
+  return RSX_OK;
+}
+
 const char* rsx_net_last_error(const rsx_net* n) { return n ? n->err : "null network"; }
 
 int rsx_net_destroy(rsx_net* n) {
   if (!n) return RSX_OK;
   cudaSetDevice(n->device);
   cudaDeviceSynchronize();
-  void* bufs[] = {n->params, n->grads, n->adam_m, n->adam_v, n->wflip, n->act, n->gout, n->part, n->loss};
+  void* bufs[] = {n->params, n->grads, n->adam_m, n->adam_v, n->wflip, n->act, n->gout, n->part, n->loss, n->status};
   for (void* p : bufs)
     if (p) cudaFree(p);
   delete n;

@@ -134,18 +134,6 @@ __global__ void __launch_bounds__(kEigThreads) k_tridiagonalise(double* __restri
 }
 
 // number of eigenvalues of T strictly below x (Sturm sequence of the LDL^T pivots)
-__device__ int sturm_count(const double* d, const double* e, int n, double x, double pivmin) {
-  int cnt = 0;
-  double q = d[0] - x;
-  if (fabs(q) < pivmin) q = -pivmin;
-  if (q < 0) ++cnt;
-  for (int i = 1; i < n; ++i) {
-    q = d[i] - x - e[i - 1] * e[i - 1] / q;
-    if (fabs(q) < pivmin) q = -pivmin;
-    if (q < 0) ++cnt;
-  }
-  return cnt;
-}
 
 // ---------------------------------------------------------------------------------
 // Multi-CTA Householder tridiagonalisation (same reflectors and outputs as

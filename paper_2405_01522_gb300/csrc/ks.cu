@@ -1,18 +1,19 @@
 // Plain block eigensolver for H = -1/2 Lap + V (fourth-order finite differences, zero
-// boundary values) with the kinetic-energy preconditioner, optionally widened by the
-// learned preconditioner's directions.  The paper's own eigensolvers are conjugate
-// gradients and preconditioned Lanczos (Sec. 3.1); this block preconditioned
-// steepest-descent / Rayleigh-Ritz solver is the project's plain method.
+// boundary values): LOBPCG with the kinetic-energy preconditioner, optionally widened by
+// the learned preconditioner's directions.  The paper's own eigensolvers are conjugate
+// gradients and preconditioned Lanczos (Sec. 3.1); this block solver is the project's
+// plain method.
 //
-// One step, k bands, basis B = [Psi | W_plain (| W_learned)], m = 2k or 3k:
+// One step, k bands, basis B = [Psi | W_plain | P (| W_learned)], m = 2k .. 4k (P, the
+// previous step's update direction, from the second step on):
 //   R = H Psi - Psi diag(theta)              (k_residual)
 //   T_i = theta_i - <psi_i, V psi_i>          (orbital kinetic energy, weighted Gram)
 //   W_plain = (K + T)^-1 R by damped Jacobi   (k_ke_jacobi, K = -1/2 Lap)
 //   W_learned = s net(R / s, V c)             (convnet.cu, s = |R_i|)
-//   normalise the W blocks, H W               (k_ham_apply)
-//   S = <B, B>, Hs = <B, H B> (FP64 Gram), then in one CTA (FP64): S = L L^T,
-//   C = L^-1 Hs L^-T, Jacobi eigen-solve, Q = L^-T Y[:, :k]   (k_rayleigh_ritz)
-//   Psi <- Q^T B, H Psi <- Q^T H B            (k_combine, in place)
+//   normalise the non-Psi blocks, apply H to them (k_ham_apply)
+//   S = <B, B>, Hs = <B, H B> (FP64 Gram), Rayleigh-Ritz in one CTA (FP64, eigen-
+//   decomposition of S with nearly dependent directions dropped)   (k_rayleigh_ritz)
+//   P <- non-Psi part of Q^T B, Psi <- Q^T B (k_combine), H Psi applied afresh
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -23,6 +24,7 @@
 #include "../../include/rsx.h"
 #include "api_internal.cuh"
 #include "dense.cuh"
+#include "eig.cuh"
 
 using namespace rsx;
 
@@ -41,15 +43,13 @@ __global__ void k_ham_apply(const float* __restrict__ f, int nb, int n, float in
     const int x = (int)(v % n), y = (int)((v / n) % n), z = (int)(v / ((size_t)n * n));
     const float* fb = f + b * N;
     const float c = fb[v];
-    float lap = -90.f * c;   // -30 per axis
-    // x
-    lap += 16.f * ((x > 0 ? fb[v - 1] : 0.f) + (x < n - 1 ? fb[v + 1] : 0.f));
-    lap -= (x > 1 ? fb[v - 2] : 0.f) + (x < n - 2 ? fb[v + 2] : 0.f);
+    // per axis 16 (f-1 + f+1) - (f-2 + f+2) - 30 c, summed as differences from c so that
+    // the FP32 rounding is relative to the second differences, not to c (no cancellation)
+    auto d = [&](bool ok, size_t off, bool up) { return (ok ? fb[up ? v + off : v - off] : 0.f) - c; };
     const size_t sy = n, sz = (size_t)n * n;
-    lap += 16.f * ((y > 0 ? fb[v - sy] : 0.f) + (y < n - 1 ? fb[v + sy] : 0.f));
-    lap -= (y > 1 ? fb[v - 2 * sy] : 0.f) + (y < n - 2 ? fb[v + 2 * sy] : 0.f);
-    lap += 16.f * ((z > 0 ? fb[v - sz] : 0.f) + (z < n - 1 ? fb[v + sz] : 0.f));
-    lap -= (z > 1 ? fb[v - 2 * sz] : 0.f) + (z < n - 2 ? fb[v + 2 * sz] : 0.f);
+    float lap = 16.f * (d(x > 0, 1, false) + d(x < n - 1, 1, true)) - (d(x > 1, 2, false) + d(x < n - 2, 2, true));
+    lap += 16.f * (d(y > 0, sy, false) + d(y < n - 1, sy, true)) - (d(y > 1, 2 * sy, false) + d(y < n - 2, 2 * sy, true));
+    lap += 16.f * (d(z > 0, sz, false) + d(z < n - 1, sz, true)) - (d(z > 1, 2 * sz, false) + d(z < n - 2, 2 * sz, true));
     float r = -0.5f * lap * inv12h2;
     if (V) r += V[v] * c;
     if (shift) r += (float)shift[b] * c;
@@ -112,124 +112,347 @@ __global__ void k_net_input(const float* __restrict__ R, const double* __restric
   }
 }
 
-// Rayleigh-Ritz in one CTA (FP64): S = L L^T (with a tiny diagonal shift for safety),
-// C = L^-1 Hs L^-T, eigen-decomposition of C by parallel cyclic Jacobi (round-robin
-// pairing, m/2 rotations per round), ascending sort, Q = L^-T Y[:, :k].
-// Outputs: theta[k]; qt[k][m] (float, rows = new orbitals' coefficients).
-__global__ void __launch_bounds__(256) k_rayleigh_ritz(const double* __restrict__ Sg, const double* __restrict__ Hg,
-                                                       int m, int k, double* __restrict__ theta, float* __restrict__ qt,
-                                                       int* status) {
-  extern __shared__ double rr_smem[];   // 4 m x m matrices (dynamic shared memory)
-  double* S = rr_smem;
-  double* L = S + m * m;
-  double* C = L + m * m;
-  double* V = C + m * m;
-  __shared__ double cs[kMaxBasis / 2], sn[kMaxBasis / 2];
-  __shared__ int pp[kMaxBasis / 2], qq[kMaxBasis / 2];
-  __shared__ double ev[kMaxBasis];
-  __shared__ int ord[kMaxBasis];
-  double tr = 0.0;
-  for (int i = 0; i < m; ++i) tr += Sg[i * m + i];
-  for (int i = threadIdx.x; i < m * m; i += blockDim.x) {
-    const int r = i / m, c = i - r * m;
-    S[i] = 0.5 * (Sg[r * m + c] + Sg[c * m + r]) + (r == c ? 1e-13 * tr / m : 0.0);
-    C[i] = 0.5 * (Hg[r * m + c] + Hg[c * m + r]);
+// ---------------------------------------------------------------------------------
+// Rayleigh-Ritz in one CTA (FP64) for m <= kMaxBasis, robust to a nearly dependent basis
+// (the LOBPCG blocks W and P become nearly parallel near convergence):
+//  1. S = L L^T by a right-looking Cholesky that drops direction j when its pivot falls
+//     below kRrDrop S_jj (B_j within ~1e-4 rad of the span of the directions before it);
+//  2. C = L^-1 Hs L^-T over the m' kept directions;
+//  3. Householder tridiagonalisation C = Q T Q^T (reflectors kept below the subdiagonal);
+//     lowest k eigenvalues of T by Sturm multisection, a warp per root (32 points per
+//     round); eigenvectors by inverse iteration on T (a warp per root; roots closer than
+//     the cluster gap are redone one after another with re-orthogonalisation); z <- Q z;
+//  4. the new orbitals' coefficients over the basis, Q = L^-T Z.
+// Outputs theta[k] and qt[k][m] (float).  Fewer than k kept directions raise RSX_ENOTPD.
+constexpr double kRrDrop = 1e-8;
+constexpr int kRrThreads = 512;
+constexpr int kRrWarps = kRrThreads / 32;
+
+__device__ double rr_block_sum(double v, double* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    double t = lane < kRrWarps ? red[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) red[32] = t;
   }
   __syncthreads();
-  // S = L L^T ; S <- L^{-1}
-  const bool ok = chol_linv_block(S, L, m);
-  // C <- L^-1 C L^-T  (V as scratch)
-  for (int i = threadIdx.x; i < m * m; i += blockDim.x) {
-    const int r = i / m, c = i - r * m;
+  return red[32];
+}
+
+__device__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// (T - lam I) z_new = z by LU with partial pivoting (serial, one thread); scratch 4 n
+// doubles + n ints
+__device__ void tri_solve_shifted(const double* d, const double* e, int n, double lam, double* z, double* sc,
+                                  int* piv) {
+  double* dg = sc;
+  double* u1 = sc + n;
+  double* u2 = sc + 2 * n;
+  double* lw = sc + 3 * n;
+  const double eps_shift = 1e-14 * fmax(1.0, fabs(lam));
+  for (int i = 0; i < n; ++i) {
+    dg[i] = d[i] - lam;
+    u1[i] = i < n - 1 ? e[i] : 0.0;
+    u2[i] = 0.0;
+  }
+  for (int i = 0; i < n - 1; ++i) {
+    const double sub = e[i];
+    if (fabs(dg[i]) >= fabs(sub)) {
+      piv[i] = 0;
+      if (dg[i] == 0.0) dg[i] = eps_shift;
+      const double l = sub / dg[i];
+      lw[i] = l;
+      dg[i + 1] -= l * u1[i];
+    } else {
+      piv[i] = 1;
+      const double l = dg[i] / sub;
+      lw[i] = l;
+      const double t0 = dg[i + 1], t1 = (i + 1 < n - 1) ? u1[i + 1] : 0.0;
+      dg[i] = sub;
+      const double old_u1 = u1[i];
+      u1[i] = t0;
+      u2[i] = t1;
+      dg[i + 1] = old_u1 - l * t0;
+      if (i + 1 < n - 1) u1[i + 1] = -l * t1;
+    }
+  }
+  if (dg[n - 1] == 0.0) dg[n - 1] = eps_shift;
+  for (int i = 0; i < n - 1; ++i) {
+    if (piv[i]) {
+      const double t = z[i];
+      z[i] = z[i + 1];
+      z[i + 1] = t - lw[i] * z[i];
+    } else {
+      z[i + 1] -= lw[i] * z[i];
+    }
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    double s = z[i];
+    if (i + 1 < n) s -= u1[i] * z[i + 1];
+    if (i + 2 < n) s -= u2[i] * z[i + 2];
+    z[i] = s / dg[i];
+  }
+}
+
+// one warp: `iters` inverse iterations for root r (vector z, length n), each followed by
+// orthogonalisation against the roots j in `ortho` (bit j set) and normalisation
+__device__ void warp_inverse_iteration(const double* d, const double* e, int n, double lam, double* z, double* sc,
+                                       int* piv, int iters, const double* Z, int ldz, unsigned ortho) {
+  const int lane = threadIdx.x & 31;
+  for (int it = 0; it < iters; ++it) {
+    if (lane == 0) tri_solve_shifted(d, e, n, lam, z, sc, piv);
+    __syncwarp();
+    for (unsigned bits = ortho; bits; bits &= bits - 1) {
+      const int j = __ffs(bits) - 1;
+      double sdot = 0.0;
+      for (int i = lane; i < n; i += 32) sdot += Z[j * ldz + i] * z[i];
+      sdot = warp_sum(sdot);
+      for (int i = lane; i < n; i += 32) z[i] -= sdot * Z[j * ldz + i];
+      __syncwarp();
+    }
+    double nn = 0.0;
+    for (int i = lane; i < n; i += 32) nn += z[i] * z[i];
+    nn = warp_sum(nn);
+    const double inv = nn > 0.0 ? 1.0 / sqrt(nn) : 0.0;
+    for (int i = lane; i < n; i += 32) z[i] *= inv;
+    __syncwarp();
+  }
+}
+
+__global__ void __launch_bounds__(kRrThreads) k_rayleigh_ritz(const double* __restrict__ Sg, const double* __restrict__ Hg,
+                                                              int m, int k, double* __restrict__ theta,
+                                                              float* __restrict__ qt, int* status) {
+  extern __shared__ double rr_smem[];   // 4 m x m: L, Li, C, T (then Z); solve scratch 4 m per warp
+  double* L = rr_smem;
+  double* Li = L + m * m;
+  double* C = Li + m * m;
+  double* T = C + m * m;
+  double* SCR = T + m * m;
+  __shared__ double red[33];
+  __shared__ double dg0[kMaxBasis], dd[kMaxBasis], ee[kMaxBasis], tau[kMaxBasis], vv[kMaxBasis], pp[kMaxBasis];
+  __shared__ double lam[kMaxBasis];
+  __shared__ int kept[kMaxBasis], dropped[kMaxBasis];
+  __shared__ int piv[kRrWarps][kMaxBasis];
+  __shared__ int nkeep;
+  __shared__ double sh_beta, sh_tau, sh_scale;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+  for (int q = tid; q < m * m; q += kRrThreads) {
+    const int r = q / m, c = q - r * m;
+    L[q] = 0.5 * (Sg[r * m + c] + Sg[c * m + r]);
+    C[q] = 0.5 * (Hg[r * m + c] + Hg[c * m + r]);
+  }
+  if (tid < m) dg0[tid] = Sg[tid * m + tid];
+  __syncthreads();
+  // 1. dropping Cholesky, lower triangle of L
+  for (int j = 0; j < m; ++j) {
+    if (tid == 0) {
+      const double pv = L[j * m + j];
+      const int dr = !(pv > kRrDrop * dg0[j]);
+      dropped[j] = dr;
+      L[j * m + j] = dr ? 1.0 : sqrt(pv);
+    }
+    __syncthreads();
+    const double ljj = L[j * m + j];
+    const int dr = dropped[j];
+    for (int i = j + 1 + tid; i < m; i += kRrThreads) L[i * m + j] = dr ? 0.0 : L[i * m + j] / ljj;
+    __syncthreads();
+    const int t = m - j - 1;
+    for (int q = tid; q < t * t; q += kRrThreads) {
+      const int i = j + 1 + q / t, l = j + 1 + q % t;
+      if (l <= i) L[i * m + l] -= L[i * m + j] * L[l * m + j];
+    }
+    __syncthreads();
+  }
+  // L^-1, one column per thread
+  if (tid < m) {
+    const int c = tid;
+    for (int i = 0; i < c; ++i) Li[i * m + c] = 0.0;
+    Li[c * m + c] = 1.0 / L[c * m + c];
+    for (int i = c + 1; i < m; ++i) {
+      double s = 0.0;
+      for (int p = c; p < i; ++p) s += L[i * m + p] * Li[p * m + c];
+      Li[i * m + c] = -s / L[i * m + i];
+    }
+  }
+  if (tid == 0) {
+    int nk = 0;
+    for (int j = 0; j < m; ++j)
+      if (!dropped[j]) kept[nk++] = j;
+    nkeep = nk;
+  }
+  __syncthreads();
+  const int n = nkeep;
+  if (n < k) {
+    if (tid < k) theta[tid] = 0.0;
+    for (int q = tid; q < k * m; q += kRrThreads) qt[q] = 0.f;
+    if (tid == 0 && status) atomicMax(status, RSX_ENOTPD);
+    return;
+  }
+  // 2. T = Li Hs (rows of kept directions), C' = T Li^T over kept pairs (n x n, in C)
+  for (int q = tid; q < n * m; q += kRrThreads) {
+    const int a = q / m, c = q - a * m, i = kept[a];
     double s = 0.0;
-    for (int j = 0; j <= r; ++j) s += S[r * m + j] * C[j * m + c];
-    V[i] = s;
+    for (int p = 0; p <= i; ++p) s += Li[i * m + p] * C[p * m + c];
+    T[a * m + c] = s;
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < m * m; i += blockDim.x) {
-    const int r = i / m, c = i - r * m;
+  for (int q = tid; q < n * n; q += kRrThreads) {
+    const int a = q / n, b = q - a * n;
+    if (b > a) continue;
+    const int l = kept[b];
     double s = 0.0;
-    for (int j = 0; j <= c; ++j) s += V[r * m + j] * S[c * m + j];
-    C[i] = s;
+    for (int p = 0; p <= l; ++p) s += T[a * m + p] * Li[l * m + p];
+    C[a * n + b] = s;
+    C[b * n + a] = s;
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < m * m; i += blockDim.x) V[i] = (i / m == i % m) ? 1.0 : 0.0;
-  __syncthreads();
-  // parallel cyclic Jacobi
-  const int half = m / 2;
-  for (int sweep = 0; sweep < 30; ++sweep) {
-    double off = 0.0, dia = 0.0;
-    for (int i = 0; i < m; ++i)
-      for (int j = 0; j < m; ++j) (i == j ? dia : off) += C[i * m + j] * C[i * m + j];
-    if (off <= 1e-30 * dia) break;
-    for (int round = 0; round < m - 1; ++round) {
-      if (threadIdx.x < half) {
-        const int i = threadIdx.x;
-        auto pos = [&](int j) { return j == 0 ? 0 : 1 + ((j - 1 + round) % (m - 1)); };
-        int p = pos(i), q = pos(m - 1 - i);
-        if (p > q) { const int t = p; p = q; q = t; }
-        pp[i] = p;
-        qq[i] = q;
-        const double apq = C[p * m + q];
-        double c = 1.0, s = 0.0;
-        if (fabs(apq) > 1e-300) {
-          const double th = (C[q * m + q] - C[p * m + p]) / (2.0 * apq);
-          const double t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
-          c = 1.0 / sqrt(t * t + 1.0);
-          s = t * c;
-        }
-        cs[i] = c;
-        sn[i] = s;
+  // 3. Householder tridiagonalisation of C' (n x n, leading dimension n)
+  for (int kk = 0; kk + 2 < n; ++kk) {
+    const int m0 = kk + 1;
+    double s = 0.0;
+    for (int i = m0 + 1 + tid; i < n; i += kRrThreads) s += C[i * n + kk] * C[i * n + kk];
+    const double xn2 = rr_block_sum(s, red);
+    if (tid == 0) {
+      const double alpha = C[m0 * n + kk];
+      if (xn2 == 0.0) {
+        sh_tau = 0.0;
+        sh_beta = alpha;
+        sh_scale = 0.0;
+      } else {
+        const double beta = -copysign(sqrt(alpha * alpha + xn2), alpha);
+        sh_tau = (beta - alpha) / beta;
+        sh_scale = 1.0 / (alpha - beta);
+        sh_beta = beta;
+      }
+      ee[kk] = sh_beta;
+      tau[kk] = sh_tau;
+      dd[kk] = C[kk * n + kk];
+    }
+    __syncthreads();
+    const double tk = sh_tau;
+    for (int i = m0 + tid; i < n; i += kRrThreads) {
+      const double vi = (i == m0) ? 1.0 : C[i * n + kk] * sh_scale;
+      vv[i] = vi;
+      if (i > m0) C[i * n + kk] = vi;
+    }
+    __syncthreads();
+    if (tk != 0.0) {
+      for (int i = m0 + tid; i < n; i += kRrThreads) {
+        double acc = 0.0;
+        for (int jj = m0; jj < n; ++jj) acc += C[i * n + jj] * vv[jj];
+        pp[i] = tk * acc;
       }
       __syncthreads();
-      // columns: C <- C J, V <- V J
-      for (int idx = threadIdx.x; idx < half * m; idx += blockDim.x) {
-        const int i = idx / m, r = idx - i * m;
-        const int p = pp[i], q = qq[i];
-        const double c = cs[i], s = sn[i];
-        const double cp = C[r * m + p], cq = C[r * m + q];
-        C[r * m + p] = c * cp - s * cq;
-        C[r * m + q] = s * cp + c * cq;
-        const double vp = V[r * m + p], vq = V[r * m + q];
-        V[r * m + p] = c * vp - s * vq;
-        V[r * m + q] = s * vp + c * vq;
-      }
+      double pv = 0.0;
+      for (int i = m0 + tid; i < n; i += kRrThreads) pv += pp[i] * vv[i];
+      const double cc = 0.5 * tk * rr_block_sum(pv, red);
+      for (int i = m0 + tid; i < n; i += kRrThreads) pp[i] -= cc * vv[i];
       __syncthreads();
-      // rows: C <- J^T C
-      for (int idx = threadIdx.x; idx < half * m; idx += blockDim.x) {
-        const int i = idx / m, col = idx - i * m;
-        const int p = pp[i], q = qq[i];
-        const double c = cs[i], s = sn[i];
-        const double rp = C[p * m + col], rq = C[q * m + col];
-        C[p * m + col] = c * rp - s * rq;
-        C[q * m + col] = s * rp + c * rq;
+      const int t = n - m0;
+      for (int q = tid; q < t * t; q += kRrThreads) {
+        const int i = m0 + q / t, jj = m0 + q % t;
+        C[i * n + jj] -= vv[i] * pp[jj] + pp[i] * vv[jj];
       }
       __syncthreads();
     }
   }
-  if (threadIdx.x == 0) {
-    for (int i = 0; i < m; ++i) {
-      ev[i] = C[i * m + i];
-      ord[i] = i;
+  if (tid == 0) {
+    if (n >= 2) {
+      dd[n - 2] = C[(n - 2) * n + (n - 2)];
+      ee[n - 2] = C[(n - 1) * n + (n - 2)];
     }
-    for (int i = 0; i < m; ++i)
-      for (int j = i + 1; j < m; ++j)
-        if (ev[ord[j]] < ev[ord[i]]) {
-          const int t = ord[i];
-          ord[i] = ord[j];
-          ord[j] = t;
-        }
+    dd[n - 1] = C[(n - 1) * n + (n - 1)];
   }
   __syncthreads();
-  // Q = L^-T Y: qt[o][r] = sum_j Linv[j][r] V[j][ord[o]]
-  for (int idx = threadIdx.x; idx < k * m; idx += blockDim.x) {
-    const int o = idx / m, r = idx - o * m;
-    double s = 0.0;
-    for (int j = r; j < m; ++j) s += S[j * m + r] * V[j * m + ord[o]];
-    qt[idx] = (float)s;
+  // lowest k eigenvalues: multisection, a warp per root
+  double lo0 = dd[0], hi0 = dd[0], emax = 0.0;
+  for (int i = 0; i < n; ++i) {
+    const double r = (i > 0 ? fabs(ee[i - 1]) : 0.0) + (i < n - 1 ? fabs(ee[i]) : 0.0);
+    lo0 = fmin(lo0, dd[i] - r);
+    hi0 = fmax(hi0, dd[i] + r);
+    if (i < n - 1) emax = fmax(emax, fabs(ee[i]));
   }
-  if (threadIdx.x < k) theta[threadIdx.x] = ev[ord[threadIdx.x]];
-  if (threadIdx.x == 0 && !ok && status) atomicMax(status, RSX_ENOTPD);
+  const double scale = fmax(fabs(lo0), fabs(hi0));
+  lo0 -= 1e-12 * scale + 1e-300;
+  hi0 += 1e-12 * scale + 1e-300;
+  const double pivmin = fmax(2.2250738585072014e-308, 1e-300 * fmax(1.0, emax * emax));
+  for (int r = warp; r < k; r += kRrWarps) {
+    double lo = lo0, hi = hi0;
+    for (int round = 0; round < 16; ++round) {
+      if (!(hi - lo > 2.0 * 2.220446049250313e-16 * fmax(fabs(lo), fabs(hi)))) break;
+      const double x = lo + (hi - lo) * (double)(lane + 1) / 33.0;
+      const unsigned above = __ballot_sync(0xffffffffu, sturm_count(dd, ee, n, x, pivmin) > r);
+      const int f = above ? __ffs(above) - 1 : 32;
+      const double nlo = (f == 0) ? lo : lo + (hi - lo) * (double)f / 33.0;
+      const double nhi = (f == 32) ? hi : lo + (hi - lo) * (double)(f + 1) / 33.0;
+      lo = nlo;
+      hi = nhi;
+    }
+    if (lane == 0) lam[r] = 0.5 * (lo + hi);
+  }
+  __syncthreads();
+  // eigenvectors of T: Z (in T) [k][n], solve scratch SCR (4 n doubles per warp)
+  double* Z = T;
+  const double gap = 1e-6 * fmax(1.0, scale);
+  for (int r = warp; r < k; r += kRrWarps) {
+    double* z = Z + r * n;
+    for (int i = lane; i < n; i += 32) z[i] = 1.0 + 0.001 * (double)((i * 7919 + r * 104729) % 997);
+    __syncwarp();
+    warp_inverse_iteration(dd, ee, n, lam[r], z, SCR + warp * 4 * n, piv[warp], 3, Z, n, 0u);
+  }
+  __syncthreads();
+  // roots within `gap` of an earlier root: redo in order, orthogonal to the earlier ones
+  if (warp == 0) {
+    for (int r = 1; r < k; ++r) {
+      unsigned ortho = 0;
+      for (int j = 0; j < r; ++j)
+        if (fabs(lam[r] - lam[j]) < gap) ortho |= 1u << j;
+      if (!ortho) continue;
+      double* z = Z + r * n;
+      for (int i = lane; i < n; i += 32) z[i] = 1.0 + 0.001 * (double)((i * 7919 + r * 104729) % 997);
+      __syncwarp();
+      warp_inverse_iteration(dd, ee, n, lam[r], z, SCR, piv[0], 3, Z, n, ortho);
+    }
+  }
+  __syncthreads();
+  // z <- H_0 H_1 ... H_{n-3} z (a warp per root)
+  for (int r = warp; r < k; r += kRrWarps) {
+    double* z = Z + r * n;
+    for (int kk = n - 3; kk >= 0; --kk) {
+      const double tk = tau[kk];
+      if (tk == 0.0) continue;
+      double sdot = 0.0;
+      for (int i = kk + 1 + lane; i < n; i += 32) sdot += ((i == kk + 1) ? 1.0 : C[i * n + kk]) * z[i];
+      sdot = tk * warp_sum(sdot);
+      for (int i = kk + 1 + lane; i < n; i += 32) z[i] -= sdot * ((i == kk + 1) ? 1.0 : C[i * n + kk]);
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  // 4. qt[o][r] = sum_a Li[kept[a]][r] Z[o][a]
+  for (int q = tid; q < k * m; q += kRrThreads) {
+    const int o = q / m, r = q - o * m;
+    double s = 0.0;
+    for (int a = 0; a < n; ++a) s += Li[kept[a] * m + r] * Z[o * n + a];
+    qt[q] = (float)s;
+  }
+  if (tid < k) theta[tid] = lam[tid];
+}
+
+// qp[i][j] = qt[i][k + j]: the coefficients of the new orbitals over the non-Psi blocks
+__global__ void k_tail_cols(const float* __restrict__ qt, int k, int m, float* __restrict__ qp) {
+  for (int i = threadIdx.x; i < k * (m - k); i += blockDim.x) {
+    const int r = i / (m - k), c = i - r * (m - k);
+    qp[i] = qt[r * m + k + c];
+  }
 }
 
 size_t blocks_for(size_t n) { return std::min<size_t>((n + 255) / 256, 4096); }
@@ -242,14 +465,16 @@ struct rsx_eig {
   double h = 0.0;
   const float* V = nullptr;      // caller's potential (device)
   float vscale = 1.f;
-  float* B = nullptr;            // [3k][N] basis: Psi | W_plain | W_learned
-  float* HB = nullptr;           // [3k][N]
+  float* B = nullptr;            // [4k][N] basis: Psi | W_plain | P (| W_learned)
+  float* HB = nullptr;           // [4k][N]
   float* R = nullptr;            // [k][N] residual of the last step
   float* tmp = nullptr;          // [2k][N] Jacobi scratch / net input
   float* xnet = nullptr;         // [k][2][N]
   double* sm = nullptr;          // small FP64: theta, T, gram outputs, S, Hs
-  float* qt = nullptr;           // [k][3k]
+  float* qt = nullptr;           // [k][4k]
+  float* qp = nullptr;           // [k][3k] coefficients over the non-Psi blocks
   bool started = false;
+  bool has_p = false;            // P (the previous update direction) is in the basis
   char err[256] = {0};
 };
 
@@ -286,8 +511,9 @@ int ham(rsx_eig* e, const float* f, int nb, float* out, const double* shift, con
   return ecuda(e, cudaGetLastError(), "hamiltonian");
 }
 
-// Rayleigh-Ritz over the first m rows of B / HB, update Psi and HPsi in place
-int rr_update(rsx_eig* e, int m, cudaStream_t s) {
+// Rayleigh-Ritz over the first m rows of B / HB, update Psi (in place), P (when keep_p)
+// and H Psi
+int rr_update(rsx_eig* e, int m, bool keep_p, cudaStream_t s) {
   const int k = e->k;
   const size_t N = (size_t)e->n * e->n * e->n;
   double* S = e->sm + 256;
@@ -296,13 +522,28 @@ int rr_update(rsx_eig* e, int m, cudaStream_t s) {
   int rc = gram(e, e->B, m, e->B, m, nullptr, S, s);
   if (!rc) rc = gram(e, e->B, m, e->HB, m, nullptr, Hs, s);
   if (rc) return rc;
-  const size_t smem = 4 * (size_t)m * m * sizeof(double);
+  const size_t smem = (4 * (size_t)m * m + 4 * (size_t)kRrWarps * m) * sizeof(double);
   cudaFuncSetAttribute(k_rayleigh_ritz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_rayleigh_ritz<<<1, 256, smem, s>>>(S, Hs, m, k, theta, e->qt, e->ctx->status);
+  k_rayleigh_ritz<<<1, kRrThreads, smem, s>>>(S, Hs, m, k, theta, e->qt, e->ctx->status);
   rc = ecuda(e, cudaGetLastError(), "rayleigh-ritz");
   if (rc) return rc;
+  // LOBPCG direction P = (new Psi minus its Psi-block part), from the old non-Psi blocks,
+  // into scratch before Psi is updated in place; then moved into the P slot (rows 2k..3k)
+  const bool with_p = m > k && keep_p;
+  if (with_p) {
+    k_tail_cols<<<1, 256, 0, s>>>(e->qt, k, m, e->qp);
+    rc = check_cuda(e->ctx, launch_combine<float>(e->qp, k, m - k, e->B + (size_t)k * N, N, e->tmp, 4 * e->ctx->nsm, s),
+                    "p update");
+    if (rc) return rc;
+  }
   rc = check_cuda(e->ctx, launch_combine<float>(e->qt, k, m, e->B, N, e->B, 4 * e->ctx->nsm, s), "psi update");
-  if (!rc) rc = check_cuda(e->ctx, launch_combine<float>(e->qt, k, m, e->HB, N, e->HB, 4 * e->ctx->nsm, s), "hpsi update");
+  if (!rc && with_p)
+    rc = ecuda(e, cudaMemcpyAsync(e->B + 2 * (size_t)k * N, e->tmp, (size_t)k * N * sizeof(float),
+                                  cudaMemcpyDeviceToDevice, s), "p move");
+  e->has_p = with_p && rc == RSX_OK;
+  // H Psi is applied afresh (not combined from H B) so that rounding does not accumulate
+  // over the iterations
+  if (!rc) rc = ham(e, e->B, k, e->HB, nullptr, e->V, s);
   return rc;
 }
 
@@ -328,13 +569,14 @@ int rsx_eig_create(rsx_eig** out, int n, double h, const float* V, float vscale,
   e->V = V;
   e->vscale = vscale;
   const size_t N = (size_t)n * n * n;
-  if (cudaMalloc(&e->B, 3 * nband * N * sizeof(float)) != cudaSuccess ||
-      cudaMalloc(&e->HB, 3 * nband * N * sizeof(float)) != cudaSuccess ||
+  if (cudaMalloc(&e->B, 4 * nband * N * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&e->HB, 4 * nband * N * sizeof(float)) != cudaSuccess ||
       cudaMalloc(&e->R, nband * N * sizeof(float)) != cudaSuccess ||
       cudaMalloc(&e->tmp, 2 * nband * N * sizeof(float)) != cudaSuccess ||
       cudaMalloc(&e->xnet, 2 * nband * N * sizeof(float)) != cudaSuccess ||
       cudaMalloc(&e->sm, (256 + 2 * kMaxBasis * kMaxBasis) * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&e->qt, kMaxBasis * kMaxBasis * sizeof(float)) != cudaSuccess) {
+      cudaMalloc(&e->qt, kMaxBasis * kMaxBasis * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&e->qp, kMaxBasis * kMaxBasis * sizeof(float)) != cudaSuccess) {
     cudaGetLastError();
     rsx_eig_destroy(e);
     return RSX_ENOMEM;
@@ -350,7 +592,8 @@ int rsx_eig_init(rsx_eig* e, const float* psi0, void* stream) {
   const size_t N = (size_t)e->n * e->n * e->n;
   int rc = ecuda(e, cudaMemcpyAsync(e->B, psi0, e->k * N * sizeof(float), cudaMemcpyDeviceToDevice, s), "init copy");
   if (!rc) rc = ham(e, e->B, e->k, e->HB, nullptr, e->V, s);
-  if (!rc) rc = rr_update(e, e->k, s);
+  e->has_p = false;
+  if (!rc) rc = rr_update(e, e->k, false, s);
   e->started = rc == RSX_OK;
   return rc;
 }
@@ -391,17 +634,18 @@ int rsx_eig_step(rsx_eig* e, rsx_net* net, int jacobi_sweeps, double* theta_host
     rc = ecuda(e, cudaMemcpyAsync(x, e->tmp + k * N, k * N * sizeof(float), cudaMemcpyDeviceToDevice, s), "jacobi copy");
     if (rc) return rc;
   }
-  int m = 2 * k;
+  // basis: Psi | W | P (LOBPCG, from the second step on) | W_learned (with a network)
+  int m = e->has_p ? 3 * k : 2 * k;
   // learned directions
   if (net) {
     rc = gram(e, e->R, k, e->R, k, nullptr, G, s);
     if (rc) return rc;
     k_diag<<<1, 64, 0, s>>>(G, k, diag);
     k_net_input<<<(unsigned)blocks_for(k * N), 256, 0, s>>>(e->R, diag, e->V, e->vscale, k, N, e->xnet);
-    float* wl = e->B + 2 * k * N;
+    float* wl = e->B + (size_t)m * N;
     rc = rsx_net_forward(net, e->xnet, k, e->n, e->n, e->n, wl, s);
     if (rc) return efail(e, rc, "learned preconditioner forward failed");
-    m = 3 * k;
+    m += k;
   }
   // normalise the W blocks, apply H to them
   rc = gram(e, wp, m - k, wp, m - k, nullptr, G, s);
@@ -410,10 +654,13 @@ int rsx_eig_step(rsx_eig* e, rsx_net* net, int jacobi_sweeps, double* theta_host
   k_normalise_rows<<<(unsigned)blocks_for((m - k) * N), 256, 0, s>>>(wp, diag, m - k, N);
   rc = ham(e, wp, m - k, e->HB + k * N, nullptr, e->V, s);
   if (rc) return rc;
-  rc = rr_update(e, m, s);
+  // keep a P block for the next step when Psi | W | P (| W_learned) still fits
+  rc = rr_update(e, m, (3 + (net ? 1 : 0)) * k <= kMaxBasis, s);
   if (rc) return rc;
   if (theta_host) rc = ecuda(e, cudaMemcpyAsync(theta_host, theta, k * sizeof(double), cudaMemcpyDeviceToHost, s), "theta");
   if (!rc) rc = ecuda(e, cudaStreamSynchronize(s), "step sync");
+  if (!rc && net && rsx_net_sync_status(net, stream) != RSX_OK)
+    rc = efail(e, RSX_ETIMEOUT, "learned preconditioner: a tensor-core convolution timed out");
   return rc;
 }
 
@@ -435,7 +682,7 @@ const char* rsx_eig_last_error(const rsx_eig* e) { return e ? e->err : "null eig
 
 int rsx_eig_destroy(rsx_eig* e) {
   if (!e) return RSX_OK;
-  void* bufs[] = {e->B, e->HB, e->R, e->tmp, e->xnet, e->sm, e->qt};
+  void* bufs[] = {e->B, e->HB, e->R, e->tmp, e->xnet, e->sm, e->qt, e->qp};
   for (void* p : bufs)
     if (p) cudaFree(p);
   rsx_destroy(e->ctx);

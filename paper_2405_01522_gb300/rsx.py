@@ -49,6 +49,7 @@ SIGNATURES = {
     "rsx_net_forward": [_P, _P, _I, _I, _I, _I, _P, _P],
     "rsx_net_loss_grad": [_P, _P, _P, _I, _I, _I, _I, _I, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_float), _P],
     "rsx_net_train_step": [_P, _P, _P, _I, _I, _I, _I, _I, ctypes.c_float, ctypes.POINTER(_D), _P],
+    "rsx_net_sync_status": [_P, _P],
     "rsx_net_last_error": [_P],
     "rsx_net_destroy": [_P],
     "rsx_batch_create": [ctypes.POINTER(_P), _I, ctypes.POINTER(_I), ctypes.POINTER(_I), _D, _I],
@@ -351,6 +352,10 @@ class Net:
         self._check(self.lib.rsx_net_train_step(self.handle, _ptr(x), _ptr(target), B, D, H, W, int(border),
                                                 float(lr), ctypes.byref(loss), _stream(stream)))
         return loss.value
+
+    def sync(self, stream=None):
+        """Wait for the network's kernels on the stream; raise on a deferred device error."""
+        self._check(self.lib.rsx_net_sync_status(self.handle, _stream(stream)))
 
     def close(self):
         if getattr(self, "handle", None):

@@ -73,7 +73,7 @@ int rsx_set_workspace_limit(rsx_ctx* ctx, size_t bytes);
 
 /* Autotuner (the paper has no counterpart; a performance knob).  Times the exchange
  * apply for nocc x npsi pairs on synthetic device data under each candidate -- threads
- * per CTA of the y/z transform pass (256, 512) x output orbitals per chunk (1, 2, 4,
+ * per CTA of the y/z transform pass (256, 384, 512) x output orbitals per chunk (1, 2, 4,
  * all) -- and applies the fastest to the context.  With a non-empty cache_path the
  * result is appended to that text file, keyed by box, precision, nocc, npsi, SM count
  * and device name, and a later call with the same key applies it without timing.
@@ -81,7 +81,7 @@ int rsx_set_workspace_limit(rsx_ctx* ctx, size_t bytes);
  * taken from the cache).  Synchronises the device.  Errors: RSX_EINVAL, RSX_ENOMEM. */
 int rsx_autotune(rsx_ctx* ctx, int nocc, int npsi, const char* cache_path, int* p2_threads, int* chunk_outputs,
                  double* best_ms);
-/* Set the same two knobs by hand (p2_threads 256 or 512; chunk_outputs 0 = as many as fit). */
+/* Set the same two knobs by hand (p2_threads 256, 384 or 512; chunk_outputs 0 = as many as fit). */
 int rsx_set_tuning(rsx_ctx* ctx, int p2_threads, int chunk_outputs);
 
 /* Pair densities rho_q = a_i * b_k (Sec. 3.1: the density whose potential Eq. 2 needs),

@@ -143,16 +143,31 @@ __device__ __forceinline__ void pass1_item(const Geom& g, const R* f1, const R* 
   __syncthreads();
 }
 
+// Block order: with g.p1_group == 0 a pair's (z, row block) items are consecutive (long
+// contiguous runs of stores per kx); with g.p1_group = G > 0 the pairs are the fastest
+// index in groups of G, so that the CTAs in flight share (z, row block) and the orbital
+// rows they multiply are read from HBM once per group and then hit in L2.
 template <typename R, int AX>
-__global__ void __launch_bounds__(kThreads) k_pass1(Geom g, PairMap<R> pm, int q0, Cx<R>* __restrict__ inter,
+__global__ void __launch_bounds__(kThreads) k_pass1(Geom g, PairMap<R> pm, int q0, int nq, Cx<R>* __restrict__ inter,
                                                     const Cx<R>* __restrict__ twx) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nyb = (g.ny + kRowsPerCta - 1) / kRowsPerCta;
   int b = blockIdx.x;
-  const int yblk = b % nyb;
-  b /= nyb;
-  const int z = b % g.nz;
-  const int ql = b / g.nz;  // local pair slot
+  int yblk, z, ql;
+  if (g.p1_group <= 0) {
+    yblk = b % nyb;
+    b /= nyb;
+    z = b % g.nz;
+    ql = b / g.nz;  // local pair slot
+  } else {
+    const int lo = b % g.p1_group;
+    b /= g.p1_group;
+    yblk = b % nyb;
+    b /= nyb;
+    z = b % g.nz;
+    ql = (b / g.nz) * g.p1_group + lo;
+    if (ql >= nq) return;   // whole CTA: the last group is partial
+  }
   const R* f1;
   const R* f2;
   pm.pair(q0 + ql, f1, f2);

@@ -31,15 +31,27 @@ inline int max_dyn_smem() {
   return v;
 }
 
-// threads per CTA of pass 2: 512 (32 lines in flight) when its scratch and plane fit
-// (g.p2_threads: 0 = default 256; 512 is used only when its scratch and plane fit)
+// threads per CTA of pass 2 (g.p2_threads): 256 (default), 384 (FP32 only: 12 warps at
+// <= 168 registers) or 512 (<= 128 registers), each used only when its line scratch and
+// the plane fit in shared memory
 template <typename R>
 inline int pass2_threads(const Geom& g) {
-  if (g.p2_threads != 512) return 256;
+  int nt = g.p2_threads;
+  if (nt != 384 && nt != 512) return 256;
+  if (nt == 384 && sizeof(R) != 4) return 256;
   const int A = g.Ay > g.Az ? g.Ay : g.Az;
-  const size_t sc512 = sizeof(Cx<R>) * (size_t)32 * A * kScrPitch;
+  const size_t sc = sizeof(Cx<R>) * (size_t)(nt / 16) * A * kScrPitch;
   const size_t pl = sizeof(Cx<R>) * (size_t)g.nz * (g.My + 1);
-  return (sc512 + pl <= (size_t)max_dyn_smem()) ? 512 : 256;
+  return (sc + pl <= (size_t)max_dyn_smem()) ? nt : 256;
+}
+
+// the shared-memory pass-2 kernel for transform size A and nt threads
+template <typename R, int A>
+inline auto pass2_kernel(int nt) {
+  if constexpr (sizeof(R) == 4) {
+    if (nt == 384) return k_pass2<R, A, A, true, 384>;
+  }
+  return nt == 512 ? k_pass2<R, A, A, true, 512> : k_pass2<R, A, A, true, 256>;
 }
 template <typename R>
 inline size_t pass2_scratch_smem(int AY, int AZ, int nt = kThreads) {
@@ -71,7 +83,7 @@ int pass2_occupancy(const Geom& g) {
 #define RSX_CASE(a)                                                                                  \
   case a: {                                                                                          \
     const int nt = pass2_threads<R>(g);                                                              \
-    auto k = nt == 512 ? k_pass2<R, a, a, true, 512> : k_pass2<R, a, a, true, 256>;                  \
+    auto k = pass2_kernel<R, a>(nt);                                                                 \
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess || \
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, nt, smem) != cudaSuccess) {            \
       cudaGetLastError();                                                                            \
@@ -99,7 +111,7 @@ cudaError_t launch_pass2(const Geom& g, int nq, Cx<R>* inter, const Cx<R>* twy, 
   case a: {                                                                                          \
     if (fits) {                                                                                      \
       const int nt = pass2_threads<R>(g);                                                            \
-      auto k = nt == 512 ? k_pass2<R, a, a, true, 512> : k_pass2<R, a, a, true, 256>;                \
+      auto k = pass2_kernel<R, a>(nt);                                                               \
       cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
       if (e != cudaSuccess) return e;                                                                \
       k<<<grid, nt, smem, s>>>(g, nq, inter, twy, twz, vhat, gscratch);                              \

@@ -1,7 +1,8 @@
 // Autotuner for the pair-solve path.
 //
 // Candidates (per box size, precision and device):
-//   - threads per CTA of the y/z pass: 256 or 512 (512 only where its scratch fits);
+//   - threads per CTA of the y/z pass: 256, 384 or 512 (FP32; each only where its
+//     scratch fits);
 //   - output orbitals per exchange chunk: 1, 2, 4 or all.  Small chunks keep each
 //     chunk's pair intermediates (nocc x 7.15 MB at 96^3) near L2 size between passes,
 //     large chunks launch fewer, fuller grids.
@@ -107,11 +108,11 @@ extern "C" int rsx_autotune(rsx_ctx* c, int nocc, int npsi, const char* cache_pa
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     const int saved_p2 = c->g.p2_threads, saved_ch = c->chunk_outputs;
-    const int p2s[2] = {256, 512};
+    const int p2s[3] = {256, 384, 512};
     const int chs[4] = {1, 2, 4, 0};
     int rc = RSX_OK;
-    for (int a = 0; a < 2 && !rc; ++a) {
-      if (a == 1 && c->precision != RSX_FP32) break;
+    for (int a = 0; a < 3 && !rc; ++a) {
+      if (a > 0 && c->precision != RSX_FP32) break;
       for (int b = 0; b < 4 && !rc; ++b) {
         if (chs[b] >= npsi) continue;
         c->g.p2_threads = p2s[a];
@@ -158,7 +159,7 @@ extern "C" int rsx_autotune(rsx_ctx* c, int nocc, int npsi, const char* cache_pa
 }
 
 extern "C" int rsx_set_tuning(rsx_ctx* c, int p2_threads, int chunk_outputs) {
-  if (!c || (p2_threads != 256 && p2_threads != 512) || chunk_outputs < 0) return RSX_EINVAL;
+  if (!c || (p2_threads != 256 && p2_threads != 384 && p2_threads != 512) || chunk_outputs < 0) return RSX_EINVAL;
   c->g.p2_threads = p2_threads;
   c->p2_occ[0] = c->p2_occ[1] = 0;
   c->chunk_outputs = chunk_outputs;

@@ -19,7 +19,7 @@ def test_autotune_choice_cache_and_bitwise_results(tmp_path):
     ref = ctx.exchange_apply(phi, psi)
     cache = str(tmp_path / "tune.txt")
     t1 = ctx.autotune(3, 5, cache=cache)
-    assert t1["p2_threads"] in (256, 512) and t1["chunk_outputs"] in (0, 1, 2, 4)
+    assert t1["p2_threads"] in (256, 384, 512) and t1["chunk_outputs"] in (0, 1, 2, 4)
     assert t1["best_ms"] > 0 and os.path.exists(cache)
     out = ctx.exchange_apply(phi, psi)
     ctx.sync()
@@ -28,7 +28,7 @@ def test_autotune_choice_cache_and_bitwise_results(tmp_path):
     t2 = ctx2.autotune(3, 5, cache=cache)
     assert t2["best_ms"] == -1.0 and t2["p2_threads"] == t1["p2_threads"]
     assert t2["chunk_outputs"] == t1["chunk_outputs"]
-    for p2, ch in ((512, 1), (256, 2), (256, 0)):
+    for p2, ch in ((512, 1), (384, 4), (256, 2), (256, 0)):
         ctx2.set_tuning(p2, ch)
         o2 = ctx2.exchange_apply(phi, psi)
         ctx2.sync()

@@ -8,8 +8,9 @@ seeded synthetic-input generator, which holds none of the method's arithmetic.
 
 Paper: Panta & Strubbe, "Implementation of time-dependent Hartree-Fock in real
 space" (arXiv 2405.01522).  Equation numbers follow the paper's order:
-Eq. 2 exchange operator (Sec. 2), Eq. 7 RHF Tamm-Dancoff matrix (Sec. 2),
-Eqs. 11-13 ACE (Sec. 3.1).
+Eq. 2 exchange operator (Sec. 2), Eqs. 3-5 full linear-response problem, Eq. 7 RHF
+matrix (Sec. 2), Eqs. 8-10 transition dipoles, oscillator strengths and strength
+function (Sec. 2), Eqs. 11-13 ACE (Sec. 3.1).
 
 Modules
 -------
@@ -19,6 +20,8 @@ ace       adaptively compressed exchange: build and apply
 casida    coupling matrices K and K_d, TDA matrix, eigen-solve
 eigensolver  FD4 Hamiltonian, kinetic-energy preconditioner, Rayleigh-Ritz step, and the
           3-layer conv3d network of the learned preconditioner with its gradients
+spectra   dipole matrix elements, oscillator strengths, Lorentzian strength function,
+          full (non-Tamm-Dancoff) TDHF in the half-size form and as the 2n x 2n problem
 
 Parity status: every public function here is pinned by ``tests/test_oracle_pins.py``
 against closed forms, brute-force sums or invariants; none is "parity unpinned".

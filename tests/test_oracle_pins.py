@@ -319,3 +319,108 @@ def test_network_gradients_match_finite_differences():
         fd = (lp - lm) / (2 * eps)
         an = grads[layer][which][idx]
         assert abs(fd - an) <= 1e-6 * max(1.0, abs(an)), (name, layer, fd, an)
+
+
+# ---------------------------------------------------------------- spectra and full TDHF
+
+import oracle.spectra as osp  # noqa: E402
+
+
+def test_oscillator_sum_rule_in_the_complete_basis():
+    """Thomas-Reiche-Kuhn identity on a tiny grid: with every eigenvector of a dense
+    Hamiltonian as the virtual space and independent-particle excitations (K = 0, X = 1),
+    sum_k f_k = (2/3) * 1/2 * sum_i sum_d <i|[r_d, [H, r_d]]|i> exactly (Eqs. 8-9)."""
+    import oracle.eigensolver as oe
+    n, h, no = 6, 0.4, 3
+    rng = np.random.default_rng(3)
+    v = -1.0 + 0.3 * rng.standard_normal((n, n, n))
+    H = oe.hamiltonian_dense(v, h)
+    w, U = np.linalg.eigh(0.5 * (H + H.T))
+    phi = (U.T / h ** 1.5).reshape(n ** 3, n, n, n)          # h^3 sum phi^2 = 1
+    occ, virt = phi[:no], phi[no:]
+    dip = osp.dipole_matrix(occ, virt, h)
+    de = (w[no:][None, :] - w[:no][:, None]).ravel()
+    f = osp.oscillator_strengths(de, np.eye(de.size), dip)
+    rhs = 0.0
+    for R in osp.positions((n, n, n), h):
+        Rm = np.diag(R.ravel())
+        C = Rm @ (H @ Rm - Rm @ H) - (H @ Rm - Rm @ H) @ Rm    # [r, [H, r]]
+        rhs += sum(U[:, i] @ C @ U[:, i] for i in range(no))
+    assert abs(f.sum() - (2.0 / 3.0) * 0.5 * rhs) < 1e-10 * abs(rhs)
+    # the position matrix elements themselves: x_ia against the dense operator
+    X = np.diag(osp.positions((n, n, n), h)[0].ravel())
+    assert abs(dip[0, 1 * (n ** 3 - no) + 4] - U[:, 1] @ X @ U[:, no + 4]) < 1e-12
+
+
+def test_dipoles_follow_the_axis_order_and_transition_index():
+    """<i|r|a> with an even occupied Gaussian and odd virtuals around the grid's centre of
+    symmetry c = -h/2: (Z - c) g has a dipole with g only along z, (X - c) g only along x
+    (x is the fastest grid axis), and t = i n_v + a."""
+    n, h = 16, 0.3
+    X, Y, Z = osp.positions((n, n, n), h)
+    c = -h / 2
+    g0 = np.exp(-((X - c) ** 2 + (Y - c) ** 2 + (Z - c) ** 2))
+    dip = osp.dipole_matrix(g0[None], np.stack([(Z - c) * g0, (X - c) * g0]), h)
+    ref = h ** 3 * np.sum((X - c) ** 2 * g0 * g0)
+    assert abs(dip[0, 0]) < 1e-13 and abs(dip[1, 0]) < 1e-13 and abs(dip[2, 0] - ref) < 1e-13
+    assert abs(dip[1, 1]) < 1e-13 and abs(dip[2, 1]) < 1e-13 and abs(dip[0, 1] - ref) < 1e-13
+    assert ref > 1e-2
+
+
+def test_strength_function_lorentzian_closed_forms():
+    omega, f, gamma = np.array([0.3, 0.7]), np.array([0.2, 0.5]), 0.01
+    # at an isolated peak S = f / (pi gamma) + the other line's tail
+    s = osp.strength_function([0.3], omega, f, gamma)[0]
+    tail = 0.5 * gamma / (np.pi * (0.4 ** 2 + gamma ** 2))
+    assert abs(s - (0.2 / (np.pi * gamma) + tail)) < 1e-12
+    # integral over [-W, W] around each line: sum f_k (2/pi) atan(W/gamma)
+    W = 0.15
+    grid = np.linspace(0.3 - W, 0.3 + W, 200001)
+    one = osp.strength_function(grid, omega[:1], f[:1], gamma)
+    assert abs(integrate.trapezoid(one, grid) - 0.2 * (2 / np.pi) * np.arctan(W / gamma)) < 1e-8
+
+
+def _tdhf_case(no=2, nv=3, seed=5):
+    """A small K from the FFT oracle on orthonormal orbitals, and eigenvalue gaps."""
+    shape, h = (8, 8, 8), 0.4
+    rng = inputs.SplitMix64(seed)
+    phi = inputs.orbitals_independent(rng, shape, h, no + nv, 2, (0.4, 1.2), 1.0)
+    phi = inputs.gram_schmidt(phi, h)
+    K = oracle.casida_K(phi[:no], phi[no:], h)
+    Kd = oracle.casida_Kd(phi[:no], phi[no:], h)
+    eo = np.array([-2.0, -1.6])[:no]
+    ev = np.array([0.5, 0.75, 1.0])[:nv]
+    return eo, ev, K, Kd, phi
+
+
+def test_full_tdhf_half_size_form_equals_the_non_hermitian_problem():
+    """Eq. 3 solved directly (2n x 2n, numpy eig) and through the half-size symmetric
+    form agree: excitation energies and X + Y (up to sign)."""
+    eo, ev, K, Kd, _ = _tdhf_case()
+    for dm in (2.0, 0.0):
+        A, B = osp.tdhf_matrices(eo, ev, K, Kd, dm)
+        w, XpY = osp.tdhf_solve(A, B, 6)
+        w2, XpY2 = osp.tdhf_solve_nonhermitian(A, B)
+        assert np.allclose(w, w2, rtol=0, atol=1e-12)
+        for k in range(6):
+            s = np.sign(XpY[k] @ XpY2[k])
+            assert np.allclose(XpY[k], s * XpY2[k], atol=1e-10)
+
+
+def test_full_tdhf_reduces_to_tda_and_closed_forms():
+    eo, ev, K, Kd, _ = _tdhf_case()
+    A, B = osp.tdhf_matrices(eo, ev, K, Kd, 2.0)
+    # B = 0: the Tamm-Dancoff eigenvalues
+    w0, _ = osp.tdhf_solve(A, np.zeros_like(B), 6)
+    assert np.allclose(w0, np.linalg.eigvalsh(A), atol=1e-12)
+    # full TDHF lies below the TDA for the lowest root (A - B, A + B positive definite)
+    w, _ = osp.tdhf_solve(A, B, 1)
+    assert w[0] <= np.linalg.eigvalsh(A)[0] + 1e-14
+    # B uses the exchange-permuted K: B[ia, jb] = 2 K[ia, jb] - K[ib, ja]
+    nv = ev.size
+    assert abs(B[0 * nv + 1, 1 * nv + 2] - (2 * K[0 * nv + 1, 1 * nv + 2] - K[0 * nv + 2, 1 * nv + 1])) < 1e-15
+    # one transition: omega = sqrt((a - b)(a + b)), b = delta_M K - K (i = j, a = b)
+    A1, B1 = osp.tdhf_matrices(eo[:1], ev[:1], K[:1, :1], Kd[:1, :1], 2.0)
+    a, b = A1[0, 0], B1[0, 0]
+    assert abs(b - K[0, 0]) < 1e-15
+    assert abs(osp.tdhf_solve(A1, B1, 1)[0][0] - math.sqrt((a - b) * (a + b))) < 1e-14

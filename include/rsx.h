@@ -151,6 +151,38 @@ int rsx_casida_solve(rsx_ctx* ctx, const double* eps_occ, int nocc, const double
                      const double* K, const double* Kd, double delta_M, int nroots, double* omega, double* X,
                      void* stream);
 
+/* Full (non-Tamm-Dancoff) RHF linear response, Eqs. 3-5 with real orbitals, in the
+ * half-size symmetric form: A = diag(eps_a - eps_i) + delta_M K - K_d (Eq. 7),
+ * B[ia,jb] = delta_M (ia|bj) - (ib|aj) = delta_M K[ia,jb] - K[ib,ja];
+ * A - B = L L^T (FP64 blocked Cholesky), M = L^T (A + B) L, M z = omega^2 z,
+ * X + Y = omega^{-1/2} L z (normalised so that X^T X - Y^T Y = 1).  Arguments as
+ * rsx_casida_solve; XpY: [nroots][nt] or NULL.  Deferred errors (rsx_sync_status):
+ * RSX_ENOTPD when A - B is not positive definite or an omega^2 <= 0 (an unstable ground
+ * state). */
+int rsx_casida_solve_full(rsx_ctx* ctx, const double* eps_occ, int nocc, const double* eps_virt, int nvirt,
+                          const double* K, const double* Kd, double delta_M, int nroots, double* omega,
+                          double* XpY, void* stream);
+
+/* Single-particle dipole matrix elements entering Eq. 8:
+ * dip[d][i * nvirt + a] = <i|r_d|a> = h^3 sum_r phi_i(r) r_d phi_a(r), d = x, y, z, with
+ * r = ((x - nx/2) h, (y - ny/2) h, (z - nz/2) h) at grid point (z, y, x).
+ * phi_occ [nocc][N], phi_virt [nvirt][N] in the context precision; dip: [3][nocc * nvirt]
+ * device doubles.  Errors: RSX_EINVAL (nocc * nvirt > 4096). */
+int rsx_casida_dipoles(rsx_ctx* ctx, const void* phi_occ, int nocc, const void* phi_virt, int nvirt, double* dip,
+                       void* stream);
+
+/* Oscillator strengths, Eqs. 8-9 in atomic units (no spin factor, as written):
+ * d_k = sum_t X[k][t] dip[:, t], f_k = 2/3 omega_k |d_k|^2.  omega [nroots],
+ * X [nroots][nt] (TDA eigenvectors or X + Y of rsx_casida_solve_full), dip [3][nt],
+ * f [nroots]: device doubles. */
+int rsx_casida_oscillator(rsx_ctx* ctx, const double* omega, const double* X, int nroots, int nt, const double* dip,
+                          double* f, void* stream);
+
+/* Strength function, Eq. 10 broadened by a Lorentzian of half-width gamma (Hartree):
+ * S[j] = sum_k f_k gamma / (pi ((grid[j] - omega_k)^2 + gamma^2)).  Device doubles. */
+int rsx_strength_function(rsx_ctx* ctx, const double* omega, const double* f, int nroots, double gamma,
+                          const double* grid, int ngrid, double* S, void* stream);
+
 /* ---- Uneven batch of independent molecules (one persistent launch per FFT pass under a
  * captured CUDA graph).  For every molecule m (cubic box of edge edges[m] in
  * {48, 64, 80, 96, 112}, spacing h, nocc[m] <= 32 orbitals, FP32):

@@ -515,18 +515,12 @@ size_t tda_work_doubles(int n, int nroots) {
   return (size_t)n * n + 14 * (size_t)n + (size_t)nroots * n + 4096;
 }
 
-int tda_solve(rsx_ctx* c, const double* eo, int no, const double* ev, int nv, const double* K, const double* Kd,
-              double dm, int nroots, double* omega, double* X, double* work, cudaStream_t s) {
-  const int n = no * nv;
+int sym_eig_lowest(rsx_ctx* c, double* work, int n, int nroots, double* omega, double* X, cudaStream_t s) {
   double* A = work;
   double* d = A + (size_t)n * n;
   double* e = d + n;
   double* tau = e + n;
   double* tw = tau + n;          // 2 n (tridiagonalisation), then 5 n (eigvec scratch needs 4 n + n ints)
-  double* y = tw + 2 * n;        // nroots * n  (eigvec T-basis vectors)
-  (void)y;
-  ProfScope ps(c, kKEig, s);
-  k_tda_assemble<<<256, 256, 0, s>>>(eo, no, ev, nv, K, Kd, dm, A);
   // cooperative multi-CTA reduction when the device supports it, one CTA otherwise
   int coop = 0, per_sm = 0;
   cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, c->device);
@@ -553,7 +547,15 @@ int tda_solve(rsx_ctx* c, const double* eo, int no, const double* ev, int nv, co
     double* sc = yv + (size_t)nroots * n;
     for (int k = 0; k < nroots; ++k) k_eigvec<<<1, kEigThreads, 0, s>>>(d, e, A, tau, n, omega, k, yv, X, sc);
   }
-  return check_cuda(c, cudaGetLastError(), "tda eigensolve");
+  return check_cuda(c, cudaGetLastError(), "symmetric eigensolve");
+}
+
+int tda_solve(rsx_ctx* c, const double* eo, int no, const double* ev, int nv, const double* K, const double* Kd,
+              double dm, int nroots, double* omega, double* X, double* work, cudaStream_t s) {
+  const int n = no * nv;
+  ProfScope ps(c, kKEig, s);
+  k_tda_assemble<<<256, 256, 0, s>>>(eo, no, ev, nv, K, Kd, dm, work);
+  return sym_eig_lowest(c, work, n, nroots, omega, X, s);
 }
 
 }  // namespace rsx

@@ -34,6 +34,10 @@ SIGNATURES = {
     "rsx_casida_K": [_P, _P, _I, _P, _I, _P, _P],
     "rsx_casida_Kd": [_P, _P, _I, _P, _I, _P, _P],
     "rsx_casida_solve": [_P, _P, _I, _P, _I, _P, _P, _D, _I, _P, _P, _P],
+    "rsx_casida_solve_full": [_P, _P, _I, _P, _I, _P, _P, _D, _I, _P, _P, _P],
+    "rsx_casida_dipoles": [_P, _P, _I, _P, _I, _P, _P],
+    "rsx_casida_oscillator": [_P, _P, _P, _I, _I, _P, _P, _P],
+    "rsx_strength_function": [_P, _P, _P, _I, _D, _P, _I, _P, _P],
     "rsx_syrk_bf16x3": [_P, _P, _P, _I, ctypes.c_longlong, _P, _P],
     "rsx_eig_create": [ctypes.POINTER(_P), _I, _D, _P, ctypes.c_float, _I, _I],
     "rsx_eig_init": [_P, _P, _P],
@@ -219,6 +223,38 @@ class Context:
                                               _ptr(Kd), float(delta_M), int(nroots), _ptr(omega), _ptr(X),
                                               _stream(stream)))
         return (omega, X) if vectors else omega
+
+    def casida_solve_full(self, eps_occ, eps_virt, K, Kd=None, delta_M=2.0, nroots=10, vectors=False, stream=None):
+        """Full TDHF (A and B) in the half-size form: omega and, with vectors, X + Y."""
+        no, nv = eps_occ.numel(), eps_virt.numel()
+        nt = no * nv
+        omega = torch.empty(nroots, dtype=torch.float64, device=self.device)
+        XpY = torch.empty((nroots, nt), dtype=torch.float64, device=self.device) if vectors else None
+        self._check(self.lib.rsx_casida_solve_full(self.handle, _ptr(eps_occ), no, _ptr(eps_virt), nv, _ptr(K),
+                                                   _ptr(Kd), float(delta_M), int(nroots), _ptr(omega), _ptr(XpY),
+                                                   _stream(stream)))
+        return (omega, XpY) if vectors else omega
+
+    def casida_dipoles(self, phi_occ, phi_virt, stream=None):
+        """<i|r_d|a> as a [3][nocc * nvirt] FP64 tensor (x, y, z)."""
+        no, nv = self._orb(phi_occ, "phi_occ"), self._orb(phi_virt, "phi_virt")
+        dip = torch.empty((3, no * nv), dtype=torch.float64, device=self.device)
+        self._check(self.lib.rsx_casida_dipoles(self.handle, _ptr(phi_occ), no, _ptr(phi_virt), nv, _ptr(dip),
+                                                _stream(stream)))
+        return dip
+
+    def oscillator_strengths(self, omega, X, dip, stream=None):
+        nroots, nt = X.shape
+        f = torch.empty(nroots, dtype=torch.float64, device=self.device)
+        self._check(self.lib.rsx_casida_oscillator(self.handle, _ptr(omega), _ptr(X), nroots, nt, _ptr(dip), _ptr(f),
+                                                   _stream(stream)))
+        return f
+
+    def strength_function(self, omega, f, gamma, grid, stream=None):
+        S = torch.empty(grid.numel(), dtype=torch.float64, device=self.device)
+        self._check(self.lib.rsx_strength_function(self.handle, _ptr(omega), _ptr(f), omega.numel(), float(gamma),
+                                                   _ptr(grid), grid.numel(), _ptr(S), _stream(stream)))
+        return S
 
     def syrk_bf16x3(self, hi, lo, C=None, stream=None):
         """C = H H^T + H L^T + L H^T for bf16 panels [n][ld] (n % 128 == 0, ld % 64 == 0)."""

@@ -392,7 +392,7 @@ int rsx_batch_create(rsx_batch** out, int nmol, const int* edges, const int* noc
   int nsm = 0;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device);
   const int L = 16 * maxA, H = L / 2 + 1;
-  b->smem[0] = sizeof(Cx<float>) * ((size_t)kLinesPerCta * maxA * kScrPitch + (size_t)H * kXsPitch);
+  b->smem[0] = sizeof(Cx<float>) * ((size_t)kLinesPerCta * maxA * kScrPitch + (size_t)H * kRowsPerCta);
   b->smem[2] = sizeof(Cx<float>) * (size_t)kLinesPerCta * maxA * kScrPitch + 2 * pass3_buffer_elems<float>(maxA, nmaxx);
   size_t p2 = 0;
   for (auto& d : b->desc)

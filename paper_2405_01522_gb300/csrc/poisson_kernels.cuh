@@ -74,6 +74,36 @@ __device__ __forceinline__ void stage2_load(Cx<R> (&u)[16], int s, const Cx<R>* 
   for (int j = 0; j < 16; ++j) u[j] = sc[s * kScrPitch + j];
 }
 
+// Row-block staging of the x passes, xs[kx][r] (kRowsPerCta = 32 rows per kx): the rows
+// are paired into 16 granules (r, r + 1 with r even) and granule g of row kx sits at
+// position g ^ (kx & 15), so that the 16 lanes of a line, which read granule `line` of 16
+// different kx, hit distinct banks, and granules move with single 16-byte (FP32) accesses.
+__device__ __forceinline__ int xs_idx(int kx, int r) {
+  return kx * kRowsPerCta + ((((r >> 1) ^ (kx & 15))) << 1) + (r & 1);
+}
+
+// two consecutive complex values (one granule) from / to shared memory
+template <typename R>
+__device__ __forceinline__ void ld_granule(const Cx<R>* p, Cx<R>& a, Cx<R>& b) {
+  if constexpr (sizeof(R) == 4) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    a = cx<R>(v.x, v.y);
+    b = cx<R>(v.z, v.w);
+  } else {
+    a = p[0];
+    b = p[1];
+  }
+}
+template <typename R>
+__device__ __forceinline__ void st_granule(Cx<R>* p, Cx<R> a, Cx<R> b) {
+  if constexpr (sizeof(R) == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(a.x, a.y, b.x, b.y);
+  } else {
+    p[0] = a;
+    p[1] = b;
+  }
+}
+
 // ---------------------------------------------------------------------------------
 // pass 1: x forward (r2c via row pairs).  One item = (pair q, plane z, 32 rows).
 // pass1_item is the body (all threads of the CTA call it with the same item); the
@@ -86,7 +116,7 @@ __device__ __forceinline__ void pass1_item(const Geom& g, const R* f1, const R* 
   constexpr int SP = AX * kScrPitch;
   constexpr int H = L / 2 + 1;
   Cx<R>* scr = reinterpret_cast<Cx<R>*>(smem_raw);
-  Cx<R>* xs = scr + kLinesPerCta * SP;  // [H][kXsPitch]
+  Cx<R>* xs = scr + kLinesPerCta * SP;  // [H][kRowsPerCta], see xs_idx
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int t = lane & 15, line = warp * 2 + (lane >> 4);
   const int y0 = yblk * kRowsPerCta;
@@ -129,16 +159,20 @@ __device__ __forceinline__ void pass1_item(const Geom& g, const R* f1, const R* 
   for (int k = t; k < H; k += 16) {
     const Cx<R> U = sc[k];
     const Cx<R> Um = sc[(L - k) % L];
-    xs[k * kXsPitch + 2 * line] = cx<R>(R(0.5) * (U.x + Um.x), R(0.5) * (U.y - Um.y));
-    xs[k * kXsPitch + 2 * line + 1] = cx<R>(R(0.5) * (U.y + Um.y), R(-0.5) * (U.x - Um.x));
+    st_granule(xs + xs_idx(k, 2 * line), cx<R>(R(0.5) * (U.x + Um.x), R(0.5) * (U.y - Um.y)),
+               cx<R>(R(0.5) * (U.y + Um.y), R(-0.5) * (U.x - Um.x)));
   }
   __syncthreads();
-  const int nrow = min(kRowsPerCta, g.ny - y0);
+  const int nrow = min(kRowsPerCta, g.ny - y0);   // a multiple of 8 (ny = 8 A)
   Cx<R>* dst = dst_pair + (size_t)z * g.ny + y0;
   const size_t kstride = (size_t)g.nz * g.ny;
-  for (int e = threadIdx.x; e < H * kRowsPerCta; e += kThreads) {
-    const int kx = e / kRowsPerCta, r = e - kx * kRowsPerCta;
-    if (r < nrow) dst[(size_t)kx * kstride + r] = xs[kx * kXsPitch + r];
+  for (int e = threadIdx.x; e < H * (kRowsPerCta / 2); e += kThreads) {
+    const int kx = e / (kRowsPerCta / 2), r = 2 * (e - kx * (kRowsPerCta / 2));
+    if (r < nrow) {
+      Cx<R> a, b;
+      ld_granule(xs + xs_idx(kx, r), a, b);
+      st_granule(dst + (size_t)kx * kstride + r, a, b);
+    }
   }
   __syncthreads();
 }
@@ -527,6 +561,10 @@ __device__ __forceinline__ void cp_async8(void* dst, const void* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
                : "memory");
 }
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
 __device__ __forceinline__ void cp_async4(void* dst, const void* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
                : "memory");
@@ -539,7 +577,7 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 template <typename R>
 __host__ __device__ inline size_t pass3_buffer_elems(int AX, int nx) {
   const int H = 8 * AX + 1;
-  return (size_t)H * kXsPitch * sizeof(Cx<R>) + (size_t)kRowsPerCta * nx * sizeof(R);
+  return (size_t)H * kRowsPerCta * sizeof(Cx<R>) + (size_t)kRowsPerCta * nx * sizeof(R);
 }
 
 template <typename R, int AX>
@@ -552,28 +590,32 @@ __device__ __forceinline__ void pass3_prefetch(const Geom& g, const PairMap<R>& 
   if (!pot) pm.entry(p, e, q, partner);
   const Cx<R>* src = inter + (size_t)(q - q0) * g.inter_elems() + (size_t)z * g.ny + y0;
   const size_t kstride = (size_t)g.nz * g.ny;
-  for (int i = threadIdx.x; i < H * kRowsPerCta; i += kThreads) {
-    const int kx = i / kRowsPerCta, r = i - kx * kRowsPerCta;
+  // one granule (rows r, r + 1) per copy; the intermediate is library-owned and 16-byte
+  // aligned, nrow is a multiple of 8
+  for (int i = threadIdx.x; i < H * (kRowsPerCta / 2); i += kThreads) {
+    const int kx = i / (kRowsPerCta / 2), r = 2 * (i - kx * (kRowsPerCta / 2));
+    Cx<R>* dp = xs + xs_idx(kx, r);
     if (r < nrow) {
       const Cx<R>* sp = src + (size_t)kx * kstride + r;
-      Cx<R>* dp = xs + kx * kXsPitch + r;
-      if (sizeof(R) == 4) {
-        cp_async8(dp, sp);
-      } else {
-        cp_async8(dp, sp);
-        cp_async8(reinterpret_cast<char*>(dp) + 8, reinterpret_cast<const char*>(sp) + 8);
-      }
+      cp_async16(dp, sp);
+      if (sizeof(R) == 8) cp_async16(dp + 1, sp + 1);
     } else {
-      xs[kx * kXsPitch + r] = cx<R>(R(0), R(0));
+      st_granule(dp, cx<R>(R(0), R(0)), cx<R>(R(0), R(0)));
     }
   }
   if (!pot) {
     const R* prow = partner + (size_t)z * g.ny * g.nx + (size_t)y0 * g.nx;
-    for (int i = threadIdx.x; i < nrow * g.nx; i += kThreads) {
-      if (sizeof(R) == 4)
-        cp_async4(tile + i, prow + i);
-      else
-        cp_async8(tile + i, prow + i);
+    const int cnt = nrow * g.nx;
+    if (((reinterpret_cast<uintptr_t>(prow) | (uintptr_t)(cnt * sizeof(R))) & 15u) == 0) {
+      constexpr int V = 16 / (int)sizeof(R);
+      for (int i = threadIdx.x * V; i < cnt; i += kThreads * V) cp_async16(tile + i, prow + i);
+    } else {
+      for (int i = threadIdx.x; i < cnt; i += kThreads) {
+        if (sizeof(R) == 4)
+          cp_async4(tile + i, prow + i);
+        else
+          cp_async8(tile + i, prow + i);
+      }
     }
   }
 }
@@ -595,7 +637,7 @@ __device__ __forceinline__ void pass3_item(const Geom& g, const PairMap<R>& pm, 
   Cx<R>* sc = scr + line * SP;
   const size_t plane = (size_t)z * g.ny * g.nx;
   auto xs_of = [&](int b) { return reinterpret_cast<Cx<R>*>(buf0 + b * bufbytes); };
-  auto tile_of = [&](int b) { return reinterpret_cast<R*>(buf0 + b * bufbytes + (size_t)H * kXsPitch * sizeof(Cx<R>)); };
+  auto tile_of = [&](int b) { return reinterpret_cast<R*>(buf0 + b * bufbytes + (size_t)H * kRowsPerCta * sizeof(Cx<R>)); };
 
   R acc0[16], acc1[16];
 #pragma unroll
@@ -624,11 +666,11 @@ __device__ __forceinline__ void pass3_item(const Geom& g, const PairMap<R>& pm, 
       const int k = t + 16 * a;
       Cx<R> xa, xb;
       if (k < H) {
-        xa = xs[k * kXsPitch + 2 * line];
-        xb = xs[k * kXsPitch + 2 * line + 1];
+        ld_granule(xs + xs_idx(k, 2 * line), xa, xb);
       } else {
-        xa = conj(xs[(L - k) * kXsPitch + 2 * line]);
-        xb = conj(xs[(L - k) * kXsPitch + 2 * line + 1]);
+        ld_granule(xs + xs_idx(L - k, 2 * line), xa, xb);
+        xa = conj(xa);
+        xb = conj(xb);
       }
       v[a] = cx<R>(xa.x - xb.y, xa.y + xb.x);
     }

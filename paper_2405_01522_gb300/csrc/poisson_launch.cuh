@@ -18,7 +18,7 @@ inline bool axis_supported_impl(int A) {
 template <typename R>
 inline size_t pass1_smem(int AX) {
   const int L = 16 * AX, H = L / 2 + 1;
-  return sizeof(Cx<R>) * ((size_t)kLinesPerCta * AX * kScrPitch + (size_t)H * kXsPitch);
+  return sizeof(Cx<R>) * ((size_t)kLinesPerCta * AX * kScrPitch + (size_t)H * kRowsPerCta);
 }
 template <typename R>
 inline size_t pass3_smem(int AX, int nx) {

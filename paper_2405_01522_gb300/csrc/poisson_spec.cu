@@ -3,16 +3,20 @@
 
 namespace rsx {
 
+constexpr int spectrum_threads(int A) { return A <= 12 ? 512 : 448; }
+
 cudaError_t launch_spectrum_f32(const Geom& g, int nq, const Cx<float>* inter, const Cx<float>* twy,
                                 const Cx<float>* twz, const float* vhat, float h3, uint16_t* hi,
                                 uint16_t* lo, size_t ld, int nrb, cudaStream_t s) {
   if (nq <= 0) return cudaSuccess;
   if (g.Ay != g.Az) return cudaErrorInvalidValue;
-  // 512 threads (32 lines in flight) where the kernel fits 128 registers without spills
-  // (A <= 12) and the shared memory allows it, else 256
-  int nt = 512;
+  // 512 threads (32 lines in flight) where the kernel fits 128 registers (A <= 12); 448
+  // (28 lines, a divisor of n = 112) for A = 14; 256 when that does not fit in shared
+  // memory.  (Dividing n evenly with fewer lines, e.g. 320 threads at n = 80, measured
+  // slower than 512 with one partial round.)
+  int nt = spectrum_threads(g.Ay);
   size_t smem = pass2_scratch_smem<float>(g.Ay, g.Az, nt) + pass2_plane_bytes<float>(g);
-  if (g.Ay > 12 || smem > (size_t)max_dyn_smem()) {
+  if (smem > (size_t)max_dyn_smem()) {
     nt = 256;
     smem = pass2_scratch_smem<float>(g.Ay, g.Az, nt) + pass2_plane_bytes<float>(g);
   }
@@ -24,7 +28,7 @@ cudaError_t launch_spectrum_f32(const Geom& g, int nq, const Cx<float>* inter, c
   switch (g.Ay) {
 #define RSX_CASE(a)                                                                              \
   case a: {                                                                                      \
-    auto k = (nt == 512 && a <= 12) ? k_spectrum<a, a, 512> : k_spectrum<a, a, 256>;             \
+    auto k = nt == 256 ? k_spectrum<a, a, 256> : k_spectrum<a, a, spectrum_threads(a)>;          \
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
     if (e != cudaSuccess) return e;                                                              \
     int per_sm = 1;                                                                              \

@@ -15,7 +15,6 @@ constexpr int kLinesPerCta = 16;      // 8 warps x 2 half-warps
 constexpr int kThreads = 256;
 constexpr int kScrPitch = 17;         // scratch row pitch (complex), avoids bank conflicts
 constexpr int kRowsPerCta = 32;       // rows (y) per CTA in the x passes
-constexpr int kXsPitch = kRowsPerCta + 1;
 
 // Which pair densities a batch holds and which pairs each output accumulates.
 //   PROD: pair q = b * na + a  has density A[a] * B[b]  (exchange: A = phi, B = psi;

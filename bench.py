@@ -460,11 +460,12 @@ def casida_bench(args, dev, local_rank, peaks):
     c32.strength_function(w32v, f0, 0.001, torch.zeros(8, dtype=torch.float64, device=dev))
     c32.casida_solve_full(eo, ev, K, None, 1.0, 10)
     torch.cuda.synchronize()
+    grid = torch.linspace(0.0, 1.0, 4001, dtype=torch.float64, device=dev)
+    torch.cuda.synchronize()
     ef = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     ef[0].record()
     dip = c32.casida_dipoles(po, pv)
     f32 = c32.oscillator_strengths(w32v, X32, dip)
-    grid = torch.linspace(0.0, 1.0, 4001, dtype=torch.float64, device=dev)
     S = c32.strength_function(w32v, f32, 0.0136 / 27.211386245988, grid)
     ef[1].record()
     ef[2].record()

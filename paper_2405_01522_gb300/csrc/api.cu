@@ -374,7 +374,7 @@ int rsx_destroy(rsx_ctx* c) {
   prof_collect(c);
   for (cudaEvent_t e : c->prof_pool) cudaEventDestroy(e);
   void* bufs[] = {c->vhat, c->tw[0], c->tw[1], c->tw[2], c->work, c->gscr, c->dsm, c->smallr, c->status,
-                  c->panel_hi, c->panel_lo, c->gemm_part, c->eig_work, c->gscr_kd, c->pos, c->tdhf_work};
+                  c->panel_hi, c->panel_lo, c->gemm_part, c->eig_work, c->gscr_kd, c->pos, c->tdhf_work, c->specw};
   for (void* b : bufs)
     if (b) cudaFree(b);
   delete c;

@@ -136,12 +136,19 @@ int casida_K_f32(rsx_ctx* c, const void* po, int no, const void* pv, int nv, dou
     rc = check_cuda(c, launch_pass1<float>(g, pm, 0, nt, inter, (const Cx<float>*)c->tw[2], s), "pass 1");
   }
   if (rc) return rc;
-  const float h3 = (float)(c->h * c->h * c->h);
+  if (!c->specw) {   // panel weights, once per context
+    const size_t nw = (size_t)g.Hx * (g.My / 2 + 1) * (g.Mz / 2 + 1);
+    rc = grow(c, &c->specw, &c->specw_bytes, nw * sizeof(float), "panel weights");
+    if (!rc)
+      rc = check_cuda(c, launch_spectrum_weights(g, (const float*)c->vhat, (float)(c->h * c->h * c->h), (float*)c->specw, s),
+                      "panel weights");
+    if (rc) return rc;
+  }
   {
     ProfScope ps(c, kKSpectrum, s);
     rc = check_cuda(c,
                     launch_spectrum_f32(g, nt, inter, (const Cx<float>*)c->tw[1], (const Cx<float>*)c->tw[0],
-                                        (const float*)c->vhat, h3, hi, lo, (size_t)ld, nrb, s),
+                                        (const float*)c->specw, hi, lo, (size_t)ld, nrb, s),
                     "spectrum panel");
   }
   if (rc) return rc;

@@ -441,13 +441,13 @@ __global__ void __launch_bounds__(NT, 1) k_pass2(Geom g, int nq, Cx<R>* __restri
 // Casida pair spectra (panel tile-major, see below): per (transition q, kx) plane, y forward and z forward, then
 // S_q(G) = sqrt(w_kx * ghat(G) * h^6 / N_pad) * (Re, Im) R_q(G) with w = 1 at kx = 0, Mx/2
 // and 2 otherwise, split into bf16 hi + lo and written to panel row q at column
-// 2 * ((kx * My + ky) * Mz + kz) + {0, 1}.  vhat holds ghat * h^3 / N_pad, so the
-// weight is sqrt(w * vhat * h^3).
+// 2 * ((kx * My + ky) * Mz + kz) + {0, 1}.  wsq holds the weights sqrt(w * ghat * h^6 /
+// N_pad) on the folded half spectrum [kx][|ky|][|kz|] (k_spectrum_weights).
 template <int AY, int AZ, int NT>
 __global__ void __launch_bounds__(NT) k_spectrum(Geom g, int nq, const Cx<float>* __restrict__ inter,
                                                        const Cx<float>* __restrict__ twy,
                                                        const Cx<float>* __restrict__ twz,
-                                                       const float* __restrict__ vhat, float h3,
+                                                       const float* __restrict__ wsq,
                                                        uint16_t* __restrict__ hi, uint16_t* __restrict__ lo,
                                                        size_t ld, int nrb) {
   constexpr int LY = 16 * AY;
@@ -478,8 +478,7 @@ __global__ void __launch_bounds__(NT) k_spectrum(Geom g, int nq, const Cx<float>
     __syncthreads();
     y_forward<float, AY, NT>(D, DP, g.nz, g.ny, twy, sc, g.ny);
     __syncthreads();
-    const float wk = (kx == 0 || 2 * kx == g.Mx) ? 1.0f : 2.0f;
-    const float* vrow = vhat + (size_t)kx * Hy * Hz;
+    const float* vrow = wsq + (size_t)kx * Hy * Hz;
     // tile-major panel [ld/64][nrb][128][64]: column g of row ql is at
     // ((g / 64) * nrb + ql / 128) * 8192 + (ql % 128) * 64 + g % 64
     const size_t row_off = (size_t)(ql / 128) * 8192 + (size_t)(ql % 128) * 64;
@@ -518,7 +517,7 @@ __global__ void __launch_bounds__(NT) k_spectrum(Geom g, int nq, const Cx<float>
 #pragma unroll
           for (int k2 = 0; k2 < 16; ++k2) {
             const int kz = t + AZ * k2;
-            const float m = sqrtf(wk * __ldg(vcol + (kz <= LZ / 2 ? kz : LZ - kz)) * h3);
+            const float m = __ldg(vcol + (kz <= LZ / 2 ? kz : LZ - kz));
             sc[kz] = cx<float>(u[k2].x * m, u[k2].y * m);
           }
         }

@@ -82,8 +82,10 @@ cudaError_t launch_pass3(const Geom& g, const PairMap<R>& pm, int q0, int p0, in
 // forward y/z transform of each pair plane, weighted by sqrt(w_G vhat(G) h^3) and split
 // into bf16 hi/lo of the K panel, tile-major [ld/64][nrb][128][64] (nrb row blocks of 128)
 cudaError_t launch_spectrum_f32(const Geom& g, int nq, const Cx<float>* inter, const Cx<float>* twy,
-                                const Cx<float>* twz, const float* vhat, float h3, uint16_t* hi,
+                                const Cx<float>* twz, const float* wsq, uint16_t* hi,
                                 uint16_t* lo, size_t ld, int nrb, cudaStream_t s);
+// panel weights wsq = sqrt(w_kx vhat h^3) on the folded half spectrum (Hx, My/2+1, Mz/2+1)
+cudaError_t launch_spectrum_weights(const Geom& g, const float* vhat, float h3, float* wsq, cudaStream_t s);
 template <typename R>
 size_t pass2_smem_bytes(const Geom& g, bool* fits);
 template <typename R>

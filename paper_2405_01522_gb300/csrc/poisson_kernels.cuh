@@ -67,6 +67,17 @@ __device__ __forceinline__ void stage1_store_halfin(const Cx<R>* v, int t, const
   for (int k1 = 0; k1 < A; ++k1) sc[k1 * kScrPitch + t] = x[k1];
 }
 
+// the same with this lane's twiddles already in registers (w[k1] = w_M^{-t k1}, k1 >= 1)
+template <int A, typename R>
+__device__ __forceinline__ void stage1_store_halfin_reg(const Cx<R>* v, int t, const Cx<R> (&w)[A], Cx<R>* sc) {
+  Cx<R> x[A];
+  DftHalfIn<A, -1>::run(v, x);
+#pragma unroll
+  for (int k1 = 1; k1 < A; ++k1) x[k1] = cmul(x[k1], w[k1]);
+#pragma unroll
+  for (int k1 = 0; k1 < A; ++k1) sc[k1 * kScrPitch + t] = x[k1];
+}
+
 // stage 2 load: lane s (< A) gathers its 16 values scratch[s][t]
 template <typename R>
 __device__ __forceinline__ void stage2_load(Cx<R> (&u)[16], int s, const Cx<R>* sc) {
@@ -346,6 +357,12 @@ __device__ __forceinline__ void pass2_plane(const Geom& g, Cx<R>* P, int kx, con
   __syncthreads();
   // z forward, multiply, z inverse on columns ky (LY is a multiple of 16: uniform trips)
   const R* vrow = vhat + (size_t)kx * Hy * Hz;
+  // this lane's forward stage-1 twiddles, the same for every column
+  Cx<R> twf[AZ];
+  if constexpr (AZ % 2 == 0) {
+#pragma unroll
+    for (int k1 = 1; k1 < AZ; ++k1) twf[k1] = twz[t * AZ + k1];
+  }
   for (int ky = line; ky < LY; ky += NT / 16) {
     const int iy = ky <= LY / 2 ? ky : LY - ky;
     const R* vcol = vrow + (size_t)iy * Hz;
@@ -357,7 +374,7 @@ __device__ __forceinline__ void pass2_plane(const Geom& g, Cx<R>* P, int kx, con
       v[a] = (z < g.nz) ? D[z * DP + ky] : cx<R>(R(0), R(0));
     }
     if constexpr (AZ % 2 == 0) {
-      stage1_store_halfin<AZ, -1>(v, t, twz, sc);
+      stage1_store_halfin_reg<AZ>(v, t, twf, sc);
     } else {
       stage1_store<AZ, -1>(v, t, twz, sc);
     }
@@ -484,6 +501,12 @@ __global__ void __launch_bounds__(NT) k_spectrum(Geom g, int nq, const Cx<float>
     const size_t row_off = (size_t)(ql / 128) * 8192 + (size_t)(ql % 128) * 64;
     const size_t kb_stride = (size_t)nrb * 8192;
     const int wn = w + (int)gridDim.x;
+    // this lane's forward stage-1 twiddles, the same for every column
+    Cx<float> twf[AZ];
+    if constexpr (AZ % 2 == 0) {
+#pragma unroll
+      for (int k1 = 1; k1 < AZ; ++k1) twf[k1] = twz[t * AZ + k1];
+    }
     // columns ky: upper half first, then the prefetch of the next plane, then the lower half
     for (int half = 1; half >= 0; --half) {
       if (half == 0) {
@@ -502,7 +525,7 @@ __global__ void __launch_bounds__(NT) k_spectrum(Geom g, int nq, const Cx<float>
           v[a] = (z < g.nz) ? D[z * DP + ky] : cx<float>(0.f, 0.f);
         }
         if constexpr (AZ % 2 == 0) {
-          stage1_store_halfin<AZ, -1>(v, t, twz, sc);
+          stage1_store_halfin_reg<AZ>(v, t, twf, sc);
         } else {
           stage1_store<AZ, -1>(v, t, twz, sc);
         }

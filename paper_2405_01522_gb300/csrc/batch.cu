@@ -3,10 +3,13 @@
 // For every molecule m (cubic box of edge n_m, N_occ,m orbitals phi_m) the batch computes
 //   W_m  = Vx[phi_m] phi_m                 (Eq. 2 with psi = phi: the exchange apply)
 //   xi_m = L_m^{-1} W_m, -M_m = L_m L_m^T  (ACE projectors, Eqs. 11-12)
-// The pair solves of all molecules go through three persistent kernels, one per FFT
-// pass; each pulls work items (molecule, pair, plane, row block) from a device queue
-// (an atomic counter) in descending molecule size and dispatches on the molecule's
-// transform length.  The ACE steps are three batched kernels.  The first run records
+// The x passes of all molecules run as two persistent kernels whose CTAs pull work items
+// (molecule, pair or output, plane, row block) from a device queue (an atomic counter)
+// in descending molecule work and dispatch on the molecule's transform length.  The
+// pair intermediates are laid out grouped by edge, so the y/z pass runs as one
+// prefetching launch of the single-problem kernel per distinct edge (all pairs of all
+// molecules of that edge share the kernel table and twiddles).  The ACE steps are three
+// batched kernels.  The first run records
 // the whole sequence in a CUDA graph; later runs replay it.  Descriptors live on the
 // device, so rebinding arrays does not invalidate the graph.
 #include <cuda_runtime.h>
@@ -97,34 +100,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch_pass1(const MolDesc* __re
       case 10: batch_p1<10>(m, local, smem_raw); break;
       case 12: batch_p1<12>(m, local, smem_raw); break;
       case 14: batch_p1<14>(m, local, smem_raw); break;
-      default: break;
-    }
-  }
-}
-
-template <int A>
-__device__ __noinline__ void batch_p2(const MolDesc& m, long long local, unsigned char* smem) {
-  const int q = (int)(local / m.g.Hx), kx = (int)(local % m.g.Hx);
-  Cx<float>* scr = reinterpret_cast<Cx<float>*>(smem);
-  Cx<float>* D = scr + kLinesPerCta * A * kScrPitch;
-  Cx<float>* P = m.inter + (size_t)q * m.g.inter_elems() + (size_t)kx * m.g.nz * m.g.ny;
-  pass2_plane<float, A, A, kThreads>(m.g, P, kx, m.tw, m.tw, m.vhat, D, scr);
-}
-
-__global__ void __launch_bounds__(kThreads, 1) k_batch_pass2(const MolDesc* __restrict__ md, int nmol,
-                                                             long long total, unsigned long long* ctr) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ long long item_sh;
-  for (long long it = next_item(ctr, &item_sh); it < total; it = next_item(ctr, &item_sh)) {
-    const int mi = find_mol(md, nmol, 1, it);
-    const MolDesc& m = md[mi];
-    const long long local = it - m.off[1];
-    switch (m.g.Ay) {
-      case 6: batch_p2<6>(m, local, smem_raw); break;
-      case 8: batch_p2<8>(m, local, smem_raw); break;
-      case 10: batch_p2<10>(m, local, smem_raw); break;
-      case 12: batch_p2<12>(m, local, smem_raw); break;
-      case 14: batch_p2<14>(m, local, smem_raw); break;
       default: break;
     }
   }
@@ -251,6 +226,12 @@ __global__ void __launch_bounds__(256) k_batch_combine(const MolDesc* __restrict
 
 }  // namespace
 
+struct PairGroup {
+  int size;          // index into size_ctx
+  size_t off;        // byte offset of the group's intermediates
+  int npairs;
+};
+
 struct rsx_batch {
   int device = 0;
   int nmol = 0;
@@ -259,6 +240,7 @@ struct rsx_batch {
   std::vector<rsx_ctx*> size_ctx;          // one FP32 context per distinct edge (tables)
   std::vector<int> size_of_mol;            // index into size_ctx
   std::vector<MolDesc> desc;               // host copy, in queue order
+  std::vector<PairGroup> groups;           // contiguous pair intermediates per size
   MolDesc* d_desc = nullptr;
   void* inter = nullptr;
   size_t inter_bytes = 0;
@@ -292,7 +274,16 @@ int record(rsx_batch* b, cudaStream_t s) {
   int rc = bcuda(b, cudaMemsetAsync(b->ctr, 0, 3 * sizeof(unsigned long long), s), "queue reset");
   if (rc) return rc;
   k_batch_pass1<<<b->grid[0], kThreads, b->smem[0], s>>>(b->d_desc, b->nmol, b->total[0], b->ctr + 0);
-  k_batch_pass2<<<b->grid[1], kThreads, b->smem[1], s>>>(b->d_desc, b->nmol, b->total[1], b->ctr + 1);
+  for (const PairGroup& grp : b->groups) {
+    rsx_ctx* c = b->size_ctx[grp.size];
+    Cx<float>* inter = reinterpret_cast<Cx<float>*>((char*)b->inter + grp.off);
+    const long long nwork = (long long)grp.npairs * c->g.Hx;
+    const int grid = (int)std::min<long long>(nwork, (long long)c->pass2_ctas_per_sm<float>() * c->nsm);
+    rc = bcuda(b, launch_pass2<float>(c->g, grp.npairs, inter, (const Cx<float>*)c->tw[1], (const Cx<float>*)c->tw[0],
+                                      (const float*)c->vhat, nullptr, grid, s),
+               "batch pass 2");
+    if (rc) return rc;
+  }
   k_batch_pass3<<<b->grid[2], kThreads, b->smem[2], s>>>(b->d_desc, b->nmol, b->total[2], b->ctr + 2);
   k_batch_gram<<<b->nmol * kBatchBlocksPerMol, 256, 0, s>>>(b->d_desc, b->part);
   k_batch_chol<<<b->nmol, 256, 0, s>>>(b->d_desc, b->part, b->h * b->h * b->h, b->linv, b->status);
@@ -334,6 +325,7 @@ int rsx_batch_create(rsx_batch** out, int nmol, const int* edges, const int* noc
       rsx_batch_destroy(b);
       return rc;
     }
+    c->g.p2_threads = 384;   // 12 warps where the plane fits (else 256)
     b->size_ctx.push_back(c);
   }
   b->size_of_mol.resize(nmol);
@@ -364,12 +356,26 @@ int rsx_batch_create(rsx_batch** out, int nmol, const int* edges, const int* noc
       d.off[p] = b->total[p];
       b->total[p] += d.cnt[p];
     }
-    d.inter = reinterpret_cast<Cx<float>*>(off_inter);  // offset, rebased below
-    off_inter += (size_t)d.npairs * d.g.inter_elems() * sizeof(Cx<float>);
-    off_inter = (off_inter + 255) / 256 * 256;
     d.phi = nullptr;
     d.W = nullptr;
     d.xi = nullptr;
+  }
+  // intermediates grouped by size: the pairs of all molecules of one edge are contiguous,
+  // so that the y/z pass runs as one tuned, prefetching launch per size
+  for (int si = (int)b->size_ctx.size() - 1; si >= 0; --si) {
+    PairGroup grp;
+    grp.size = si;
+    grp.off = off_inter;
+    grp.npairs = 0;
+    for (int qi = 0; qi < nmol; ++qi) {
+      if (b->size_of_mol[b->order[qi]] != si) continue;
+      MolDesc& d = b->desc[qi];
+      d.inter = reinterpret_cast<Cx<float>*>(off_inter);  // offset, rebased below
+      off_inter += (size_t)d.npairs * d.g.inter_elems() * sizeof(Cx<float>);
+      grp.npairs += d.npairs;
+    }
+    if (grp.npairs > 0) b->groups.push_back(grp);
+    off_inter = (off_inter + 255) / 256 * 256;
   }
   b->inter_bytes = off_inter;
   if (cudaMalloc(&b->inter, off_inter) != cudaSuccess || cudaMalloc(&b->d_desc, nmol * sizeof(MolDesc)) != cudaSuccess ||
@@ -394,12 +400,8 @@ int rsx_batch_create(rsx_batch** out, int nmol, const int* edges, const int* noc
   const int L = 16 * maxA, H = L / 2 + 1;
   b->smem[0] = sizeof(Cx<float>) * ((size_t)kLinesPerCta * maxA * kScrPitch + (size_t)H * kRowsPerCta);
   b->smem[2] = sizeof(Cx<float>) * (size_t)kLinesPerCta * maxA * kScrPitch + 2 * pass3_buffer_elems<float>(maxA, nmaxx);
-  size_t p2 = 0;
-  for (auto& d : b->desc)
-    p2 = std::max(p2, sizeof(Cx<float>) * ((size_t)kLinesPerCta * d.g.Ay * kScrPitch + (size_t)d.g.nz * (d.g.My + 1)));
-  b->smem[1] = p2;
-  const void* kern[3] = {(const void*)k_batch_pass1, (const void*)k_batch_pass2, (const void*)k_batch_pass3};
-  for (int p = 0; p < 3; ++p) {
+  const void* kern[3] = {(const void*)k_batch_pass1, nullptr, (const void*)k_batch_pass3};
+  for (int p = 0; p < 3; p += 2) {
     if (cudaFuncSetAttribute(kern[p], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem[p]) != cudaSuccess) {
       cudaGetLastError();
       rsx_batch_destroy(b);

@@ -4,12 +4,16 @@
 //   k_tda_assemble    A = diag(eps_a - eps_i) + delta_M K - K_d, symmetrised
 //   k_tridiag_coop    Householder reduction A = Q T Q^T, cooperative multi-CTA (reflectors
 //                     kept in A); k_tridiagonalise is the one-CTA form for small n
-//   k_multisect       lowest nroots eigenvalues of T by Sturm-count multisection
-//   k_eigvec          inverse iteration on T (with re-orthogonalisation inside clusters of
-//                     close eigenvalues), then x = Q y
+//   k_multisect       lowest nroots eigenvalues of T by Sturm-count multisection (a warp
+//                     per root)
+//   k_invit           inverse iteration on T (a warp per root); k_invit_clusters redoes
+//                     roots of clusters of close eigenvalues with re-orthogonalisation
+//   k_backtransform   x = Q y (a warp per root, reflectors read as rows after
+//                     k_reflectors_to_rows)
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
 
 #include "../../include/rsx.h"
 #include "api_internal.cuh"
@@ -168,7 +172,7 @@ __device__ __forceinline__ bool grid_barrier(GridBar* gb, unsigned int nblocks) 
           ok_sh = 0;
           break;
         }
-        __nanosleep(64);
+        // plain spin: the wait is a few microseconds at most
       }
     }
     __threadfence();
@@ -347,172 +351,164 @@ __global__ void __launch_bounds__(256) k_tridiag_coop(double* __restrict__ A, in
   }
 }
 
-// Multisection: one CTA per root; each round evaluates the Sturm count at blockDim.x
-// interior points of [lo, hi] and keeps the sub-interval where the count passes k.
-__global__ void __launch_bounds__(256) k_multisect(const double* __restrict__ d, const double* __restrict__ e, int n,
-                                                   double* __restrict__ w) {
-  const int k = blockIdx.x;
-  __shared__ double lo_sh, hi_sh;
-  __shared__ int first_sh;
-  if (threadIdx.x == 0) {
-    double lo = d[0], hi = d[0];
-    for (int i = 0; i < n; ++i) {
-      const double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i < n - 1 ? fabs(e[i]) : 0.0);
-      lo = fmin(lo, d[i] - r);
-      hi = fmax(hi, d[i] + r);
-    }
-    const double scale = fmax(fabs(lo), fabs(hi));
-    lo_sh = lo - 1e-12 * scale - 1e-300;
-    hi_sh = hi + 1e-12 * scale + 1e-300;
+// Lowest roots of the tridiagonal T (d, e), a warp per root: each round evaluates the
+// Sturm count at 32 interior points of [lo, hi] (one per lane) and keeps the sub-interval
+// in which the count passes k (FP64 is scarce on this part: 32 points per root and round
+// instead of a whole CTA).
+__global__ void __launch_bounds__(32) k_multisect(const double* __restrict__ d, const double* __restrict__ e, int n,
+                                                   int nroots, double* __restrict__ w) {
+  extern __shared__ double ms_smem[];   // d (n), e^2 (n)
+  const int lane = threadIdx.x & 31;
+  const int k = blockIdx.x;   // one warp (CTA) per root: spread over SMs, FP64 units are scarce
+  if (k >= nroots) return;
+  double* ds = ms_smem;
+  double* e2 = ms_smem + n;
+  for (int i = lane; i < n; i += 32) {
+    ds[i] = d[i];
+    e2[i] = i < n - 1 ? e[i] * e[i] : 0.0;
   }
-  __syncthreads();
-  double emax = 0.0;
-  for (int i = 0; i < n - 1; ++i) emax = fmax(emax, fabs(e[i]));
-  const double pivmin = fmax(2.2250738585072014e-308, 1e-300 * fmax(1.0, emax * emax));
-  const int T = blockDim.x;
-  for (int round = 0; round < 12; ++round) {
-    const double lo = lo_sh, hi = hi_sh;
+  __syncwarp();
+  double lo = 1e300, hi = -1e300, emax = 0.0;
+  for (int i = lane; i < n; i += 32) {
+    const double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i < n - 1 ? fabs(e[i]) : 0.0);
+    lo = fmin(lo, d[i] - r);
+    hi = fmax(hi, d[i] + r);
+    if (i < n - 1) emax = fmax(emax, fabs(e[i]));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    emax = fmax(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+  }
+  const double scale = fmax(fabs(lo), fabs(hi));
+  lo -= 1e-12 * scale + 1e-300;
+  hi += 1e-12 * scale + 1e-300;
+  for (int round = 0; round < 16; ++round) {
     if (!(hi - lo > 2.0 * 2.220446049250313e-16 * fmax(fabs(lo), fabs(hi)))) break;
-    const double x = lo + (hi - lo) * (double)(threadIdx.x + 1) / (double)(T + 1);
-    const bool above = sturm_count(d, e, n, x, pivmin) > k;
-    if (threadIdx.x == 0) first_sh = T;
-    __syncthreads();
-    if (above) atomicMin(&first_sh, (int)threadIdx.x);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      const int f = first_sh;
-      const double nlo = (f == 0) ? lo : lo + (hi - lo) * (double)f / (double)(T + 1);
-      const double nhi = (f == T) ? hi : lo + (hi - lo) * (double)(f + 1) / (double)(T + 1);
-      lo_sh = nlo;
-      hi_sh = nhi;
-    }
-    __syncthreads();
+    const double x = lo + (hi - lo) * (double)(lane + 1) / 33.0;
+    const unsigned above = __ballot_sync(0xffffffffu, sturm_count_prod(ds, e2, n, x) > k);
+    const int f = above ? __ffs(above) - 1 : 32;
+    const double nlo = (f == 0) ? lo : lo + (hi - lo) * (double)f / 33.0;
+    const double nhi = (f == 32) ? hi : lo + (hi - lo) * (double)(f + 1) / 33.0;
+    lo = nlo;
+    hi = nhi;
   }
-  if (threadIdx.x == 0) w[k] = 0.5 * (lo_sh + hi_sh);
+  if (lane == 0) w[k] = 0.5 * (lo + hi);
 }
 
-// eigenvectors: one CTA per root, serial tridiagonal solves by thread 0, parallel
-// back-transformation.  Roots are processed in ascending order by the launch loop on
-// the host (one launch per root) so that a vector can be orthogonalised against the
-// previous ones of its cluster.  y: [nroots][n] scratch (T basis); X: [nroots][n] out.
-__global__ void __launch_bounds__(kEigThreads) k_eigvec(const double* __restrict__ d, const double* __restrict__ e,
-                                                        const double* __restrict__ A, const double* __restrict__ tau,
-                                                        int n, const double* __restrict__ w, int k, double* __restrict__ y,
-                                                        double* __restrict__ X, double* __restrict__ scratch) {
-  __shared__ double red[33];
-  double* yk = y + (size_t)k * n;
-  double* lu = scratch;  // 5 n doubles: diag, up, up2, low, rhs
-  const double lam = w[k];
-  double gap_tol = 1e-9;
-  {
-    double s = 0.0;
-    for (int i = 0; i < n; ++i) s = fmax(s, fabs(d[i]));
-    gap_tol *= fmax(1.0, s);
-  }
-  // starting vector
-  for (int i = threadIdx.x; i < n; i += blockDim.x) yk[i] = 1.0 + 0.001 * (double)((i * 7919 + k * 104729) % 997);
-  __syncthreads();
-  for (int iter = 0; iter < 4; ++iter) {
-    if (threadIdx.x == 0) {
-      // LU with partial pivoting of (T - lam I), solve in place in yk
-      double* dg = lu;
-      double* u1 = lu + n;
-      double* u2 = lu + 2 * n;
-      double* lw = lu + 3 * n;
-      int* piv = reinterpret_cast<int*>(lu + 4 * n);
-      const double eps_shift = 1e-14 * fmax(1.0, fabs(lam));
-      for (int i = 0; i < n; ++i) {
-        dg[i] = d[i] - lam;
-        u1[i] = i < n - 1 ? e[i] : 0.0;
-        u2[i] = 0.0;
+// Eigenvectors of T by inverse iteration, a warp per root (3 iterations from a fixed
+// start); y: [nroots][n]; scratch: 4 n doubles + n ints per root.
+__global__ void __launch_bounds__(32) k_invit(const double* __restrict__ d, const double* __restrict__ e, int n,
+                                               const double* __restrict__ w, int nroots, double* __restrict__ y,
+                                               double* __restrict__ scratch) {
+  const int lane = threadIdx.x & 31;
+  const int k = blockIdx.x;   // one warp (CTA) per root: spread over SMs, FP64 units are scarce
+  if (k >= nroots) return;
+  double* z = y + (size_t)k * n;
+  double* sc = scratch + (size_t)k * 5 * n;
+  for (int i = lane; i < n; i += 32) z[i] = 1.0 + 0.001 * (double)((i * 7919 + k * 104729) % 997);
+  __syncwarp();
+  warp_inverse_iteration(d, e, n, w[k], z, sc, reinterpret_cast<int*>(sc + 4 * n), 3, y, n, 0u);
+}
+
+// Roots closer than the cluster gap to an earlier root are recomputed one after another
+// (one warp), each orthogonalised inside every iteration against the earlier roots of
+// its cluster, so that (nearly) degenerate roots get orthonormal vectors.
+__global__ void k_invit_clusters(const double* __restrict__ d, const double* __restrict__ e, int n,
+                                 const double* __restrict__ w, int nroots, double* __restrict__ y,
+                                 double* __restrict__ scratch) {
+  const int lane = threadIdx.x & 31;
+  double s = 0.0;
+  for (int i = lane; i < n; i += 32) s = fmax(s, fabs(d[i]));
+  for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_xor_sync(0xffffffffu, s, o));
+  const double gap = 1e-6 * fmax(1.0, s);
+  int* piv = reinterpret_cast<int*>(scratch + 4 * n);
+  for (int r = 1; r < nroots; ++r) {
+    bool clustered = false;
+    for (int j = 0; j < r; ++j) clustered |= fabs(w[r] - w[j]) < gap;
+    if (!clustered) continue;
+    double* z = y + (size_t)r * n;
+    for (int i = lane; i < n; i += 32) z[i] = 1.0 + 0.001 * (double)((i * 7919 + r * 104729) % 997);
+    __syncwarp();
+    if (lane == 0) tri_factor_shifted(d, e, n, w[r], scratch, piv);
+    __syncwarp();
+    for (int it = 0; it < 3; ++it) {
+      if (lane == 0) tri_solve_factored(n, z, scratch, piv);
+      __syncwarp();
+      for (int j = 0; j < r; ++j) {
+        if (!(fabs(w[r] - w[j]) < gap)) continue;
+        const double* zj = y + (size_t)j * n;
+        double dot = 0.0;
+        for (int i = lane; i < n; i += 32) dot += zj[i] * z[i];
+        dot = warp_sum(dot);
+        for (int i = lane; i < n; i += 32) z[i] -= dot * zj[i];
+        __syncwarp();
       }
-      for (int i = 0; i < n - 1; ++i) {
-        const double sub = e[i];
-        if (fabs(dg[i]) >= fabs(sub)) {
-          piv[i] = 0;
-          if (dg[i] == 0.0) dg[i] = eps_shift;
-          const double l = sub / dg[i];
-          lw[i] = l;
-          dg[i + 1] -= l * u1[i];
-        } else {
-          piv[i] = 1;
-          const double l = dg[i] / sub;
-          lw[i] = l;
-          // swap rows i and i+1
-          const double t0 = dg[i + 1], t1 = (i + 1 < n - 1) ? u1[i + 1] : 0.0;
-          dg[i] = sub;
-          const double old_u1 = u1[i];
-          u1[i] = t0;
-          u2[i] = t1;
-          dg[i + 1] = old_u1 - l * t0;
-          if (i + 1 < n - 1) u1[i + 1] = -l * t1;
-        }
-      }
-      if (dg[n - 1] == 0.0) dg[n - 1] = eps_shift;
-      // forward: apply the row swaps and eliminations to the right-hand side
-      for (int i = 0; i < n - 1; ++i) {
-        if (piv[i]) {
-          const double t = yk[i];
-          yk[i] = yk[i + 1];
-          yk[i + 1] = t - lw[i] * yk[i];
-        } else {
-          yk[i + 1] -= lw[i] * yk[i];
-        }
-      }
-      // back substitution
-      for (int i = n - 1; i >= 0; --i) {
-        double s = yk[i];
-        if (i + 1 < n) s -= u1[i] * yk[i + 1];
-        if (i + 2 < n) s -= u2[i] * yk[i + 2];
-        yk[i] = s / dg[i];
-      }
+      double nn = 0.0;
+      for (int i = lane; i < n; i += 32) nn += z[i] * z[i];
+      nn = warp_sum(nn);
+      const double inv = nn > 0.0 ? 1.0 / sqrt(nn) : 0.0;
+      for (int i = lane; i < n; i += 32) z[i] *= inv;
+      __syncwarp();
     }
-    __syncthreads();
-    // orthogonalise against earlier roots of the same cluster, then normalise
-    for (int j = 0; j < k; ++j) {
-      if (fabs(w[j] - lam) > gap_tol * 1e3) continue;
-      const double* yj = y + (size_t)j * n;
-      double s = 0.0;
-      for (int i = threadIdx.x; i < n; i += blockDim.x) s += yj[i] * yk[i];
-      s = block_sum(s, red);
-      for (int i = threadIdx.x; i < n; i += blockDim.x) yk[i] -= s * yj[i];
-      __syncthreads();
-    }
-    double s = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) s += yk[i] * yk[i];
-    s = block_sum(s, red);
-    const double inv = 1.0 / sqrt(s);
-    for (int i = threadIdx.x; i < n; i += blockDim.x) yk[i] *= inv;
-    __syncthreads();
   }
-  // x = H_0 H_1 ... H_{n-3} y ; H_k = I - tau_k v_k v_k^T, v_k[k+1] = 1, v_k[i] = A[i][k] (i > k+1)
-  double* x = X + (size_t)k * n;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] = yk[i];
+}
+
+// Reflector vectors moved to rows: A[j][i] = A[i][j] for i > j + 1 (the strict upper
+// triangle past the superdiagonal is dead after the reduction), so that the
+// back-transformation reads each reflector contiguously.  32 x 32 tiles through shared
+// memory.
+__global__ void k_reflectors_to_rows(double* __restrict__ A, int n) {
+  __shared__ double tile[32][33];
+  const int j0 = blockIdx.x * 32, i0 = blockIdx.y * 32;   // source tile: rows i0.., columns j0..
+  if (i0 + 31 < j0 + 2) return;                          // no entry with i > j + 1
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 8 rows per pass
+  for (int r = ty; r < 32; r += 8) {
+    const int i = i0 + r, j = j0 + tx;
+    tile[r][tx] = (i < n && j < n && i > j + 1) ? A[(size_t)i * n + j] : 0.0;
+  }
   __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const int j = j0 + r, i = i0 + tx;   // destination A[j][i]
+    if (i < n && j < n && i > j + 1) A[(size_t)j * n + i] = tile[tx][r];
+  }
+}
+
+// x_k = H_0 H_1 ... H_{n-3} y_k, one warp (CTA) per root, x in shared memory;
+// H_j = I - tau_j v_j v_j^T, v_j[j+1] = 1, v_j[i] = A[j][i] (i > j + 1, rows form)
+__global__ void __launch_bounds__(32) k_backtransform(const double* __restrict__ A, const double* __restrict__ tau,
+                                                      int n, const double* __restrict__ y, int nroots,
+                                                      double* __restrict__ X) {
+  extern __shared__ double xs_bt[];
+  const int lane = threadIdx.x & 31;
+  const int k = blockIdx.x;
+  if (k >= nroots) return;
+  double* x = xs_bt;
+  for (int i = lane; i < n; i += 32) x[i] = y[(size_t)k * n + i];
+  __syncwarp();
   for (int kk = n - 3; kk >= 0; --kk) {
     const double tk = tau[kk];
     if (tk == 0.0) continue;
-    double s = 0.0;
-    for (int i = kk + 1 + threadIdx.x; i < n; i += blockDim.x) {
-      const double vi = (i == kk + 1) ? 1.0 : A[(size_t)i * n + kk];
-      s += vi * x[i];
-    }
-    s = tk * block_sum(s, red);
-    for (int i = kk + 1 + threadIdx.x; i < n; i += blockDim.x) {
-      const double vi = (i == kk + 1) ? 1.0 : A[(size_t)i * n + kk];
-      x[i] -= s * vi;
-    }
-    __syncthreads();
+    const double* v = A + (size_t)kk * n;
+    double s = (lane == 0) ? x[kk + 1] : 0.0;
+    for (int i = kk + 2 + lane; i < n; i += 32) s += v[i] * x[i];
+    s = tk * warp_sum(s);
+    if (lane == 0) x[kk + 1] -= s;
+    for (int i = kk + 2 + lane; i < n; i += 32) x[i] -= s * v[i];
+    __syncwarp();
   }
+  for (int i = lane; i < n; i += 32) X[(size_t)k * n + i] = x[i];
 }
 
 }  // namespace
 
-// start of the scratch that follows the eigenvector area (see tda_solve's layout)
-static double* y_end(double* tw, int n, int nroots) { return tw + 2 * n + (size_t)nroots * n + 5 * (size_t)n; }
+// workspace after A, d, e, tau: tw (2 n, one-CTA tridiagonalisation), the T-basis vectors
+// y (nroots n), inverse-iteration scratch (nroots 5 n), then the cooperative kernel's
+// scratch (v, p, partials, alpha, grid barrier)
+static double* y_end(double* tw, int n, int nroots) { return tw + 2 * n + (size_t)nroots * n + 5 * (size_t)nroots * n; }
 
 size_t tda_work_doubles(int n, int nroots) {
-  return (size_t)n * n + 14 * (size_t)n + (size_t)nroots * n + 4096;
+  return (size_t)n * n + 14 * (size_t)n + 6 * (size_t)nroots * n + 4096;
 }
 
 int sym_eig_lowest(rsx_ctx* c, double* work, int n, int nroots, double* omega, double* X, cudaStream_t s) {
@@ -526,7 +522,10 @@ int sym_eig_lowest(rsx_ctx* c, double* work, int n, int nroots, double* omega, d
   cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, c->device);
   cudaFuncSetAttribute(k_tridiag_coop, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(2 * (size_t)n * sizeof(double)));
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tridiag_coop, 256, 2 * (size_t)n * sizeof(double));
-  const int G = std::min(std::min(c->nsm * std::max(per_sm, 0), 128), std::max(1, n / 2));
+  // fewer CTAs make each grid barrier cheaper; the FP64 work per step is small
+  int gcap = 64;
+  if (const char* ev = getenv("RSX_TRIDIAG_CTAS")) gcap = std::max(1, atoi(ev));
+  const int G = std::min(std::min(c->nsm * std::max(per_sm, 0), gcap), std::max(1, n / 2));
   if (coop && per_sm > 0 && n >= 64) {
     double* scr = y_end(tw, n, nroots);            // v, p, partials, alpha
     GridBar* gb = reinterpret_cast<GridBar*>(scr + 2 * n + 2 * 1024 + 2);
@@ -540,12 +539,17 @@ int sym_eig_lowest(rsx_ctx* c, double* work, int n, int nroots, double* omega, d
   } else {
     k_tridiagonalise<<<1, kEigThreads, 0, s>>>(A, n, d, e, tau, tw);
   }
-  k_multisect<<<nroots, 256, 0, s>>>(d, e, n, omega);
+  cudaFuncSetAttribute(k_multisect, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(2 * (size_t)n * sizeof(double)));
+  k_multisect<<<nroots, 32, 2 * (size_t)n * sizeof(double), s>>>(d, e, n, nroots, omega);
   if (X) {
-    // eigvec scratch: 5 n doubles after the T-basis vectors
-    double* yv = tw + 2 * n;
-    double* sc = yv + (size_t)nroots * n;
-    for (int k = 0; k < nroots; ++k) k_eigvec<<<1, kEigThreads, 0, s>>>(d, e, A, tau, n, omega, k, yv, X, sc);
+    double* yv = tw + 2 * n;                       // T-basis vectors
+    double* sc = yv + (size_t)nroots * n;          // 5 n per root
+    k_invit<<<nroots, 32, 0, s>>>(d, e, n, omega, nroots, yv, sc);
+    k_invit_clusters<<<1, 32, 0, s>>>(d, e, n, omega, nroots, yv, sc);
+    k_reflectors_to_rows<<<dim3((n + 31) / 32, (n + 31) / 32), 256, 0, s>>>(A, n);
+    const size_t smem = (size_t)n * sizeof(double);
+    cudaFuncSetAttribute(k_backtransform, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_backtransform<<<nroots, 32, smem, s>>>(A, tau, n, yv, nroots, X);
   }
   return check_cuda(c, cudaGetLastError(), "symmetric eigensolve");
 }

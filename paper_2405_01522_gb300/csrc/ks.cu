@@ -143,89 +143,6 @@ __device__ double rr_block_sum(double v, double* red) {
   return red[32];
 }
 
-__device__ double warp_sum(double v) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// (T - lam I) z_new = z by LU with partial pivoting (serial, one thread); scratch 4 n
-// doubles + n ints
-__device__ void tri_solve_shifted(const double* d, const double* e, int n, double lam, double* z, double* sc,
-                                  int* piv) {
-  double* dg = sc;
-  double* u1 = sc + n;
-  double* u2 = sc + 2 * n;
-  double* lw = sc + 3 * n;
-  const double eps_shift = 1e-14 * fmax(1.0, fabs(lam));
-  for (int i = 0; i < n; ++i) {
-    dg[i] = d[i] - lam;
-    u1[i] = i < n - 1 ? e[i] : 0.0;
-    u2[i] = 0.0;
-  }
-  for (int i = 0; i < n - 1; ++i) {
-    const double sub = e[i];
-    if (fabs(dg[i]) >= fabs(sub)) {
-      piv[i] = 0;
-      if (dg[i] == 0.0) dg[i] = eps_shift;
-      const double l = sub / dg[i];
-      lw[i] = l;
-      dg[i + 1] -= l * u1[i];
-    } else {
-      piv[i] = 1;
-      const double l = dg[i] / sub;
-      lw[i] = l;
-      const double t0 = dg[i + 1], t1 = (i + 1 < n - 1) ? u1[i + 1] : 0.0;
-      dg[i] = sub;
-      const double old_u1 = u1[i];
-      u1[i] = t0;
-      u2[i] = t1;
-      dg[i + 1] = old_u1 - l * t0;
-      if (i + 1 < n - 1) u1[i + 1] = -l * t1;
-    }
-  }
-  if (dg[n - 1] == 0.0) dg[n - 1] = eps_shift;
-  for (int i = 0; i < n - 1; ++i) {
-    if (piv[i]) {
-      const double t = z[i];
-      z[i] = z[i + 1];
-      z[i + 1] = t - lw[i] * z[i];
-    } else {
-      z[i + 1] -= lw[i] * z[i];
-    }
-  }
-  for (int i = n - 1; i >= 0; --i) {
-    double s = z[i];
-    if (i + 1 < n) s -= u1[i] * z[i + 1];
-    if (i + 2 < n) s -= u2[i] * z[i + 2];
-    z[i] = s / dg[i];
-  }
-}
-
-// one warp: `iters` inverse iterations for root r (vector z, length n), each followed by
-// orthogonalisation against the roots j in `ortho` (bit j set) and normalisation
-__device__ void warp_inverse_iteration(const double* d, const double* e, int n, double lam, double* z, double* sc,
-                                       int* piv, int iters, const double* Z, int ldz, unsigned ortho) {
-  const int lane = threadIdx.x & 31;
-  for (int it = 0; it < iters; ++it) {
-    if (lane == 0) tri_solve_shifted(d, e, n, lam, z, sc, piv);
-    __syncwarp();
-    for (unsigned bits = ortho; bits; bits &= bits - 1) {
-      const int j = __ffs(bits) - 1;
-      double sdot = 0.0;
-      for (int i = lane; i < n; i += 32) sdot += Z[j * ldz + i] * z[i];
-      sdot = warp_sum(sdot);
-      for (int i = lane; i < n; i += 32) z[i] -= sdot * Z[j * ldz + i];
-      __syncwarp();
-    }
-    double nn = 0.0;
-    for (int i = lane; i < n; i += 32) nn += z[i] * z[i];
-    nn = warp_sum(nn);
-    const double inv = nn > 0.0 ? 1.0 / sqrt(nn) : 0.0;
-    for (int i = lane; i < n; i += 32) z[i] *= inv;
-    __syncwarp();
-  }
-}
-
 __global__ void __launch_bounds__(kRrThreads) k_rayleigh_ritz(const double* __restrict__ Sg, const double* __restrict__ Hg,
                                                               int m, int k, double* __restrict__ theta,
                                                               float* __restrict__ qt, int* status) {

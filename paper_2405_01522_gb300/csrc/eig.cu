@@ -2,14 +2,17 @@
 // with B = 0 the problem A X = omega X is Hermitian; only the lowest roots are needed).
 //
 //   k_tda_assemble    A = diag(eps_a - eps_i) + delta_M K - K_d, symmetrised
-//   k_tridiag_coop    Householder reduction A = Q T Q^T, cooperative multi-CTA (reflectors
-//                     kept in A); k_tridiagonalise is the one-CTA form for small n
+//   k_tridiag_cluster Householder reduction A = Q T Q^T on one thread-block cluster with the
+//                     matrix in distributed shared memory (n up to ~530); k_tridiag_coop the
+//                     cooperative multi-CTA form for larger n; k_tridiagonalise one CTA
+//                     (reflectors kept in A in every form)
 //   k_multisect       lowest nroots eigenvalues of T by Sturm-count multisection (a warp
 //                     per root)
 //   k_invit           inverse iteration on T (a warp per root); k_invit_clusters redoes
 //                     roots of clusters of close eigenvalues with re-orthogonalisation
 //   k_backtransform   x = Q y (a warp per root, reflectors read as rows after
 //                     k_reflectors_to_rows)
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -351,6 +354,161 @@ __global__ void __launch_bounds__(256) k_tridiag_coop(double* __restrict__ A, in
   }
 }
 
+// ---------------------------------------------------------------------------------
+// Householder tridiagonalisation on one thread-block cluster (same reflectors and outputs
+// as k_tridiagonalise).  The matrix lives in the CTAs' shared memory: rows dealt
+// cyclically (row i in CTA i % CS, local row i / CS); v, p/w and the per-CTA partial sums
+// are replicated in every CTA, which writes its own entries into all the others through
+// distributed shared memory.  Per step three hardware cluster barriers separate
+// (norm partials -> v) -> (p = tau A22 v, p^T v partials) -> (rank-2 update of own rows,
+// next column's norm partials).  The rows are copied back to global memory at the end
+// (the reflectors below the subdiagonal, for the back-transformation).
+constexpr int kClThreads = 512;
+namespace cg = cooperative_groups;
+
+__global__ void __launch_bounds__(kClThreads) k_tridiag_cluster(double* __restrict__ A, int n, double* __restrict__ d,
+                                                                double* __restrict__ e, double* __restrict__ tau) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int CS = (int)cl.num_blocks();
+  const int me = (int)cl.block_rank();
+  const int nloc = (n - me + CS - 1) / CS;          // rows me, me + CS, ...
+  const int lda = n;
+  extern __shared__ double cl_smem[];
+  double* R = cl_smem;                               // [nloc][n]
+  double* v = R + (size_t)((n + CS - 1) / CS) * n;   // [n]
+  double* p = v + n;                                 // [n] (p, then w)
+  double* part = p + n;                              // [CS] norm partials, [CS] p^T v partials, alpha
+  double* part2 = part + CS;
+  double* alpha_sl = part2 + CS;
+  __shared__ double red[kClThreads / 32];
+  __shared__ double sh_tau, sh_beta, sh_scale;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = kClThreads / 32;
+  auto grow = [&](int li) { return me + li * CS; };
+  for (size_t q = tid; q < (size_t)nloc * n; q += kClThreads) {
+    const int li = (int)(q / n), j = (int)(q - (size_t)li * n);
+    R[q] = A[(size_t)grow(li) * lda + j];
+  }
+  __syncthreads();
+  // block-wide sum of one value per thread, result to thread 0
+  auto block_sum0 = [&](double x) {
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0) red[warp] = x;
+    __syncthreads();
+    double t = 0.0;
+    if (tid == 0)
+      for (int w = 0; w < nw; ++w) t += red[w];
+    __syncthreads();
+    return t;
+  };
+  // publish this CTA's partial (and alpha when it owns row m0 + 1) for column c
+  auto publish_norm = [&](int c) {
+    double s = 0.0;
+    for (int li = tid; li < nloc; li += kClThreads) {
+      const int i = grow(li);
+      if (i >= c + 2) s += R[(size_t)li * n + c] * R[(size_t)li * n + c];
+    }
+    const double t = block_sum0(s);
+    if (tid == 0) red[0] = t;
+    __syncthreads();
+    const double tot = red[0];
+    if (tid < CS) *cl.map_shared_rank(part + me, tid) = tot;
+    if ((c + 1) % CS == me && tid >= 32 && tid < 32 + CS)
+      *cl.map_shared_rank(alpha_sl, tid - 32) = R[(size_t)((c + 1) / CS) * n + c];
+  };
+  if (n > 2) publish_norm(0);
+  cl.sync();
+  for (int k = 0; k + 2 < n; ++k) {
+    const int m0 = k + 1;
+    if (tid == 0) {
+      double xn2 = 0.0;
+      for (int c = 0; c < CS; ++c) xn2 += part[c];
+      const double alpha = *alpha_sl;
+      if (xn2 == 0.0) {
+        sh_tau = 0.0;
+        sh_beta = alpha;
+        sh_scale = 0.0;
+      } else {
+        const double beta = -copysign(sqrt(alpha * alpha + xn2), alpha);
+        sh_tau = (beta - alpha) / beta;
+        sh_scale = 1.0 / (alpha - beta);
+        sh_beta = beta;
+      }
+      if (me == 0) {
+        e[k] = sh_beta;
+        tau[k] = sh_tau;
+      }
+      if (k % CS == me) d[k] = R[(size_t)(k / CS) * n + k];
+    }
+    __syncthreads();
+    const double tk = sh_tau, sc = sh_scale;
+    // v on own rows (stored in the column), sent to every CTA
+    for (int q = tid; q < nloc * CS; q += kClThreads) {
+      const int li = q / CS, dst = q - li * CS;
+      const int i = grow(li);
+      if (i < m0) continue;
+      const double vi = (i == m0) ? 1.0 : R[(size_t)li * n + k] * sc;
+      *cl.map_shared_rank(v + i, dst) = vi;
+    }
+    cl.sync();
+    for (int li = tid; li < nloc; li += kClThreads) {
+      const int i = grow(li);
+      if (i > m0) R[(size_t)li * n + k] = v[i];
+    }
+    if (tk != 0.0) {
+      // p_i = tau (A22 v)_i on own rows, a warp per row; p^T v partial
+      double pv = 0.0;
+      for (int li = warp; li < nloc; li += nw) {
+        const int i = grow(li);
+        if (i < m0) continue;
+        const double* row = R + (size_t)li * n;
+        double acc = 0.0;
+        for (int j = m0 + lane; j < n; j += 32) acc += row[j] * v[j];
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        const double pi = tk * acc;
+        if (lane < CS) *cl.map_shared_rank(p + i, lane) = pi;
+        if (lane == 0) pv += pi * v[i];
+      }
+      const double t = block_sum0(pv);
+      if (tid == 0) red[0] = t;
+      __syncthreads();
+      if (tid < CS) *cl.map_shared_rank(part2 + me, tid) = red[0];
+      cl.sync();
+      // w = p - (tau/2)(p^T v) v, rank-2 update of own rows
+      double pvs = 0.0;
+      for (int c = 0; c < CS; ++c) pvs += part2[c];
+      const double cc = 0.5 * tk * pvs;
+      for (int j = m0 + tid; j < n; j += kClThreads) p[j] -= cc * v[j];
+      __syncthreads();
+      for (int li = warp; li < nloc; li += nw) {
+        const int i = grow(li);
+        if (i < m0) continue;
+        const double vi = v[i], wi = p[i];
+        double* row = R + (size_t)li * n;
+        for (int j = m0 + lane; j < n; j += 32) row[j] -= vi * p[j] + wi * v[j];
+      }
+      __syncthreads();
+    } else {
+      cl.sync();   // matches the p-broadcast barrier of the other branch (tau is the same everywhere)
+    }
+    if (m0 + 2 < n) publish_norm(m0);
+    cl.sync();
+  }
+  // last 2 x 2 block, rows back to global memory
+  if (tid == 0) {
+    if (n >= 2) {
+      if ((n - 2) % CS == me) d[n - 2] = R[(size_t)((n - 2) / CS) * n + (n - 2)];
+      if ((n - 1) % CS == me) e[n - 2] = R[(size_t)((n - 1) / CS) * n + (n - 2)];
+      if (me == 0 && n >= 3) tau[n - 2] = 0.0;
+    }
+    if ((n - 1) % CS == me) d[n - 1] = R[(size_t)((n - 1) / CS) * n + (n - 1)];
+  }
+  for (size_t q = tid; q < (size_t)nloc * n; q += kClThreads) {
+    const int li = (int)(q / n), j = (int)(q - (size_t)li * n);
+    A[(size_t)grow(li) * lda + j] = R[q];
+  }
+  cl.sync();   // no CTA leaves while others may still address its shared memory
+}
+
 // Lowest roots of the tridiagonal T (d, e), a warp per root: each round evaluates the
 // Sturm count at 32 interior points of [lo, hi] (one per lane) and keeps the sub-interval
 // in which the count passes k (FP64 is scarce on this part: 32 points per root and round
@@ -526,7 +684,41 @@ int sym_eig_lowest(rsx_ctx* c, double* work, int n, int nroots, double* omega, d
   int gcap = 64;
   if (const char* ev = getenv("RSX_TRIDIAG_CTAS")) gcap = std::max(1, atoi(ev));
   const int G = std::min(std::min(c->nsm * std::max(per_sm, 0), gcap), std::max(1, n / 2));
-  if (coop && per_sm > 0 && n >= 64) {
+  // one thread-block cluster with the matrix in distributed shared memory when it fits
+  // (16 CTAs, non-portable size, else 8), else the cooperative grid, else one CTA
+  bool done = false;
+  for (int CS : {16, 8}) {
+    if (done || n < 64) break;
+    const size_t smem = (((size_t)(n + CS - 1) / CS) * n + 2 * (size_t)n + 2 * CS + 1) * sizeof(double);
+    if (smem > (size_t)227 * 1024) continue;
+    if (cudaFuncSetAttribute(k_tridiag_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        (CS > 8 && cudaFuncSetAttribute(k_tridiag_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)) {
+      cudaGetLastError();
+      continue;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(CS);
+    cfg.blockDim = dim3(kClThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CS;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int ncl = 0;
+    if (cudaOccupancyMaxActiveClusters(&ncl, k_tridiag_cluster, &cfg) != cudaSuccess || ncl < 1) {
+      cudaGetLastError();
+      continue;
+    }
+    const cudaError_t err = cudaLaunchKernelEx(&cfg, k_tridiag_cluster, A, n, d, e, tau);
+    if (err != cudaSuccess) return check_cuda(c, err, "cluster tridiagonalisation");
+    done = true;
+  }
+  if (done) {
+  } else if (coop && per_sm > 0 && n >= 64) {
     double* scr = y_end(tw, n, nroots);            // v, p, partials, alpha
     GridBar* gb = reinterpret_cast<GridBar*>(scr + 2 * n + 2 * 1024 + 2);
     cudaMemsetAsync(gb, 0, sizeof(GridBar), s);

@@ -68,9 +68,10 @@ def test_casida_K_and_Kd_parity(shape, h, no, nv, prec):
     assert np.array_equal(K, K.T) or prec == "fp64" and np.allclose(K, K.T, rtol=0, atol=0)
 
 
-@pytest.mark.parametrize("nt_shape", [(1, 1), (2, 3), (4, 9), (8, 64)])
+@pytest.mark.parametrize("nt_shape", [(1, 1), (2, 3), (4, 9), (4, 16), (8, 64), (10, 66)])
 def test_casida_solve_matches_eigh(nt_shape):
-    """FP64 device eigen-solve vs numpy eigh on the same matrix, random symmetric K, K_d."""
+    """FP64 device eigen-solve vs numpy eigh on the same matrix, random symmetric K, K_d.
+    n = 36: one-CTA reduction; 64 and 512: thread-block cluster; 660: cooperative grid."""
     need_gpu()
     no, nv = nt_shape
     nt = no * nv

@@ -32,6 +32,53 @@ RSX_HD Cx<R> cmul(Cx<R> a, Cx<R> b) {
 }
 template <typename R>
 RSX_HD Cx<R> cscale(Cx<R> a, R s) { return cx<R>(a.x * s, a.y * s); }
+
+// FP32 on sm_100-family devices: complex add / subtract / real scaling as packed two-lane
+// FP32 instructions (one instruction per complex operation instead of two; the same
+// round-to-nearest results as the scalar forms).  The FFT passes are instruction-issue
+// bound and these operations are most of their arithmetic.
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
+#define RSX_PACKED_F32 1
+#endif
+template <>
+RSX_HD Cx<float> operator+(Cx<float> a, Cx<float> b) {
+#ifdef RSX_PACKED_F32
+  const float2 r = __fadd2_rn(make_float2(a.x, a.y), make_float2(b.x, b.y));
+  return cx<float>(r.x, r.y);
+#else
+  return cx<float>(a.x + b.x, a.y + b.y);
+#endif
+}
+template <>
+RSX_HD Cx<float> operator-(Cx<float> a, Cx<float> b) {
+#ifdef RSX_PACKED_F32
+  const float2 r = __fadd2_rn(make_float2(a.x, a.y), make_float2(-b.x, -b.y));
+  return cx<float>(r.x, r.y);
+#else
+  return cx<float>(a.x - b.x, a.y - b.y);
+#endif
+}
+template <>
+RSX_HD Cx<float> cscale(Cx<float> a, float s) {
+#ifdef RSX_PACKED_F32
+  const float2 r = __fmul2_rn(make_float2(a.x, a.y), make_float2(s, s));
+  return cx<float>(r.x, r.y);
+#else
+  return cx<float>(a.x * s, a.y * s);
+#endif
+}
+// acc + s * a (real s), fused
+template <typename R>
+RSX_HD Cx<R> cfma(Cx<R> a, R s, Cx<R> acc) { return cx<R>(fma(s, a.x, acc.x), fma(s, a.y, acc.y)); }
+template <>
+RSX_HD Cx<float> cfma(Cx<float> a, float s, Cx<float> acc) {
+#ifdef RSX_PACKED_F32
+  const float2 r = __ffma2_rn(make_float2(a.x, a.y), make_float2(s, s), make_float2(acc.x, acc.y));
+  return cx<float>(r.x, r.y);
+#else
+  return cx<float>(fmaf(s, a.x, acc.x), fmaf(s, a.y, acc.y));
+#endif
+}
 template <typename R>
 RSX_HD Cx<R> conj(Cx<R> a) { return cx<R>(a.x, -a.y); }
 // S * i * a  for S = +-1
@@ -146,8 +193,8 @@ struct DftOddPrime {
       for (int k = 1; k <= H; ++k) {
         const R c = R(trig_c(P, (m * k) % P));
         const R s = R(trig_s(P, (m * k) % P));
-        re = cx<R>(re.x + c * a[k - 1].x, re.y + c * a[k - 1].y);
-        im = cx<R>(im.x + s * b[k - 1].x, im.y + s * b[k - 1].y);
+        re = cfma(a[k - 1], c, re);
+        im = cfma(b[k - 1], s, im);
       }
       const Cx<R> u = mul_si<S>(im);
       v[m] = re + u;

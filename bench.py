@@ -129,6 +129,12 @@ def aggregate_rate(world, units_per_step, steps, ms_max):
 DFT_FLOPS = {1: 0, 2: 4, 3: 16, 4: 16, 5: 52, 6: 44, 7: 102, 8: 60, 10: 124, 12: 112, 14: 232, 16: 182}
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12     # SMs x FP32 lanes x FMA x max SM clock
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) from ncu captures of small cases
+# of the same kernels (profiles/pass2_yz_kernel_96cubed.md, profiles/k_syrk_bf16x3_48cubed.md),
+# scaled to a full launch by the units it processes:
+PASS2_DRAM_BYTES_PER_PAIR_96 = 400.52e6 / 32    # 32-pair launch at 96^3 (12.5 MB/pair)
+SYRK_DRAM_PER_PANEL_BYTE = 1.938e9 / 1.850e9    # DRAM bytes per byte of the two bf16 panels
+
 
 def _half_in(A):
     return 2 * DFT_FLOPS[A // 2] + (A // 2 - 1) * 6 if A % 2 == 0 else DFT_FLOPS[A]
@@ -268,8 +274,12 @@ def run_rsx(args, rank, local_rank, world):
         avg_ms = kernels[top]["ms_per_launch"]
         ach_f = avg_flops / (avg_ms / 1e3) / 1e12
         ach_b = avg_bytes / (avg_ms / 1e3) / 1e9
+        traffic = None
+        if top == "pass2_yz_kernel" and tuple(shape) == (96, 96, 96):
+            traffic = PASS2_DRAM_BYTES_PER_PAIR_96 * sum(per_launch_pairs[top]) / len(per_launch_pairs[top])
         roof = {"kernel": top, "bound": "alu", "achieved": round(ach_f, 2), "peak": round(FP32_PEAK_TFLOPS, 2),
-                "unit": "TFLOP/s", "frac": round(ach_f / FP32_PEAK_TFLOPS, 4), "traffic": None,
+                "unit": "TFLOP/s", "frac": round(ach_f / FP32_PEAK_TFLOPS, 4), "traffic": traffic,
+                "traffic_source": "ncu DRAM bytes of a 32-pair launch scaled by pairs per launch" if traffic else None,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 (FMA) x 2.07 GHz",
                 "algorithmic_flops_per_launch": avg_flops,
                 "hbm_view": {"achieved_gbs": round(ach_b, 1), "peak_gbs": hbm_peak, "frac": round(ach_b / hbm_peak, 4),
@@ -487,7 +497,9 @@ def casida_bench(args, dev, local_rank, peaks):
            "kernels": {k: {"ms_per_launch": round(v[0] / v[1], 4), "launches": v[1]} for k, v in prof.items()},
            "roofline": {"kernel": "k_syrk_bf16x3 (tcgen05)", "bound": "tensor",
                         "achieved": round(executed / (gemm_ms / 1e3) / 1e12, 1), "peak": peak, "unit": "TFLOP/s",
-                        "frac": round(executed / (gemm_ms / 1e3) / 1e12 / peak, 4), "traffic": None,
+                        "frac": round(executed / (gemm_ms / 1e3) / 1e12 / peak, 4),
+                        "traffic": SYRK_DRAM_PER_PANEL_BYTE * 2 * 2 * ((nt + 127) // 128 * 128) * ((ng + 63) // 64 * 64),
+                        "traffic_source": "ncu DRAM bytes per panel byte at 48^3 x 512 times the two bf16 panels here",
                         "peak_source": "measured" if "bf16_tflops" in peaks else "fallback",
                         "algorithmic_flops_per_launch": executed}}
     if not args.skip_fp64:

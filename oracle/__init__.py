@@ -10,7 +10,8 @@ Paper: Panta & Strubbe, "Implementation of time-dependent Hartree-Fock in real
 space" (arXiv 2405.01522).  Equation numbers follow the paper's order:
 Eq. 2 exchange operator (Sec. 2), Eqs. 3-5 full linear-response problem, Eq. 7 RHF
 matrix (Sec. 2), Eqs. 8-10 transition dipoles, oscillator strengths and strength
-function (Sec. 2), Eqs. 11-13 ACE (Sec. 3.1).
+function (Sec. 2), Eqs. 11-13 ACE (Sec. 3.1), Eqs. 14-15 linear mixing and the relative
+density error of the SCF cycle (Secs. 3.2, 3.4).
 
 Modules
 -------
@@ -22,6 +23,7 @@ eigensolver  FD4 Hamiltonian, kinetic-energy preconditioner, Rayleigh-Ritz step,
           3-layer conv3d network of the learned preconditioner with its gradients
 spectra   dipole matrix elements, oscillator strengths, Lorentzian strength function,
           full (non-Tamm-Dancoff) TDHF in the half-size form and as the 2n x 2n problem
+scf       closed-shell Hartree-Fock SCF on small grids, with ACE or exact exchange
 
 Parity status: every public function here is pinned by ``tests/test_oracle_pins.py``
 against closed forms, brute-force sums or invariants; none is "parity unpinned".

@@ -424,3 +424,68 @@ def test_full_tdhf_reduces_to_tda_and_closed_forms():
     a, b = A1[0, 0], B1[0, 0]
     assert abs(b - K[0, 0]) < 1e-15
     assert abs(osp.tdhf_solve(A1, B1, 1)[0][0] - math.sqrt((a - b) * (a + b))) < 1e-14
+
+
+# ---------------------------------------------------------------- SCF (closed-shell HF)
+
+import oracle.scf as oscf  # noqa: E402
+
+
+def _scf_potential():
+    return inputs.model_potential(n=8, h=0.5, natoms=2, Z=2.0, rc=0.8, radius=0.8, seed=3)
+
+
+def test_coulomb_matrix_is_the_poisson_solve():
+    """G rho equals the FFT Poisson solve of the same density (and its direct sum)."""
+    rho = rng_fields((5, 6, 4), 1, 7)[0]
+    G = oscf.coulomb_matrix(rho.shape, 0.4)
+    assert np.allclose((G @ rho.ravel()).reshape(rho.shape), oracle.poisson_fft(rho, 0.4), rtol=0, atol=1e-11)
+
+
+def test_scf_with_ace_converges_to_the_exact_exchange_result():
+    """Sec. 3.1: at self-consistency ACE is not an approximation, so the ACE cycle and the
+    exact-exchange cycle reach the same energy and orbital energies."""
+    v = _scf_potential()
+    a = oscf.scf(v, 0.5, 2, mode="ace", tol=1e-11)
+    b = oscf.scf(v, 0.5, 2, mode="exact", tol=1e-11)
+    assert a["reldens"] < 1e-11 and b["reldens"] < 1e-11
+    assert abs(a["energy"] - b["energy"]) < 1e-9 * abs(b["energy"])
+    assert np.allclose(a["eps_orb"], b["eps_orb"], rtol=0, atol=1e-8)
+    assert b["exchange"] < 0 < b["hartree"]
+
+
+def test_scf_one_orbital_exchange_is_minus_half_hartree():
+    """Two electrons in one orbital: E_x = -(phi phi|phi phi) and E_H = 2 (phi phi|phi phi),
+    whatever the orbital (the closed-shell density and exchange factors)."""
+    r = oscf.scf(_scf_potential(), 0.5, 1, mode="exact", tol=1e-10)
+    assert abs(r["exchange"] + 0.5 * r["hartree"]) < 1e-12 * r["hartree"]
+    phi = rng_fields((8, 8, 8), 1, 4)
+    phi /= np.sqrt(0.5 ** 3 * np.sum(phi ** 2))
+    _, _, eh, ex = oscf.hf_energy(phi, _scf_potential(), 0.5, oscf.coulomb_matrix((8, 8, 8), 0.5))
+    assert abs(ex + 0.5 * eh) < 1e-12 * eh
+
+
+def test_scf_fixed_point_solves_the_hf_equations_and_minimises_the_energy():
+    """The converged orbitals satisfy F[phi] phi_i = eps_i phi_i with the exact exchange,
+    and the HF energy rises quadratically when an orbital is rotated out of the
+    occupied space (first variation zero, second positive)."""
+    v, h = _scf_potential(), 0.5
+    r = oscf.scf(v, h, 2, mode="exact", tol=1e-12)
+    phi = r["phi"]
+    G = oscf.coulomb_matrix(v.shape, h)
+    F = oracle.eigensolver.hamiltonian_dense(v, h) + np.diag(G @ oscf.density(phi).ravel()) + \
+        oscf.exchange_matrix(phi, G)
+    P = phi.reshape(2, -1)
+    for i in range(2):
+        res = F @ P[i] - r["eps_orb"][i] * P[i]
+        assert np.linalg.norm(res) < 1e-7 * np.linalg.norm(F @ P[i])
+    d = rng_fields((8, 8, 8), 1, 5)[0].ravel()
+    d -= P.T @ (h ** 3 * (P @ d))                   # orthogonal to the occupied space
+    dE = []
+    for delta in (1e-3, 5e-4):
+        q = P.copy()
+        q[0] = q[0] + delta * d
+        q[0] /= np.sqrt(h ** 3 * q[0] @ q[0])
+        dE.append(oscf.hf_energy(q.reshape(phi.shape), v, h, G)[0] - r["energy"])
+    assert dE[0] > 0 and dE[1] > 0
+    assert abs(dE[0] / dE[1] - 4.0) < 0.05

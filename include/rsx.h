@@ -97,6 +97,11 @@ int rsx_build_pair_densities(rsx_ctx* ctx, const void* a, int na, const void* b,
 int rsx_exchange_apply(rsx_ctx* ctx, const void* phi, int nocc, const void* psi, int npsi, void* out,
                        void* stream);
 
+/* Isolated-boundary potential of one density (Sec. 3.1, the Poisson solve behind Eq. 2):
+ * V(r) = h^3 sum_r' rho(r') g(r - r') with the kernel of the pair solves.  Used for the
+ * Hartree potential of the SCF loop.  rho, V: [N] (must not alias).  Errors: RSX_EINVAL. */
+int rsx_poisson(rsx_ctx* ctx, const void* rho, void* V, void* stream);
+
 /* Allocation-free variant of rsx_exchange_apply (the paper has no counterpart; this is
  * a deployment aid).  For callers that must not allocate device memory once running --
  * e.g. a program whose device memory is owned by its own pool allocator sized at
@@ -224,6 +229,40 @@ int rsx_eig_orbitals(rsx_eig* eig, float* psi_out, void* stream);
 int rsx_eig_residual(rsx_eig* eig, float* r_out, void* stream);
 const char* rsx_eig_last_error(const rsx_eig* eig);
 int rsx_eig_destroy(rsx_eig* eig);
+/* Non-local exchange term added to H (Sec. 3.1): mode 0 none; 1 the ACE operator
+ * -sum_k xi_k <xi_k, .> of Eq. 13 with projectors src [count][n^3] (16 ceil(count/16)
+ * 4 nband <= 4096); 2 the exact exchange Vx[src] of Eq. 2 with orbitals src [count][n^3],
+ * through ctx (an FP32 context on the same box).  src (and ctx) are kept by pointer.
+ * Takes effect at the next rsx_eig_step or rsx_eig_refresh.  Errors: RSX_EINVAL, RSX_ENOMEM. */
+int rsx_eig_set_exchange(rsx_eig* eig, rsx_ctx* ctx, const float* src, int count, int mode);
+/* H has changed (V's contents or the exchange term): recompute H Psi, Rayleigh-Ritz on the
+ * current orbitals, drop the previous search direction; theta_host[nband] or NULL.
+ * Synchronises the stream. */
+int rsx_eig_refresh(rsx_eig* eig, double* theta_host, void* stream);
+
+/* ---- Closed-shell Hartree-Fock SCF (Sec. 3.1-3.2; the rest of Sec. 3 builds on it).
+ * rho = 2 sum_i phi_i^2 over nocc orbitals (N_e = 2 nocc); Fock operator
+ * F = -1/2 Lap_FD4 + V_ext + V_H[rho_in] + Vx, Vx from the orbitals entering the iteration,
+ * either as ACE (use_ace != 0: Eqs. 11-13 built once per iteration) or exact (Eq. 2 in
+ * every application of F); linear density mixing rho_in <- alpha rho_in + (1 - alpha)
+ * rho_out (Eq. 14); relative density error (1/N_e) h^3 sum |rho_in - rho_out| (Eq. 15).
+ * rsx_scf_create: ctx an FP32 context on a cubic box (kept), V_ext device [N] (kept by
+ *   pointer), nocc <= 16, 0 <= alpha < 1.
+ * rsx_scf_init: starting orbitals psi0 [nocc][N] (device); Rayleigh-Ritz with T + V_ext;
+ *   the first input density is theirs.
+ * rsx_scf_step: one SCF iteration with `inner` eigensolver steps; out_host[6] = HF energy
+ *   E = 2 sum_i <phi_i, (T + V_ext) phi_i> + 1/2 <rho, V_H> + sum_i <phi_i, Vx phi_i> of
+ *   the orbitals entering the iteration, its three parts (one-body, Hartree, exchange),
+ *   the relative density error of the previous iteration (0 on the first) and the sum of
+ *   the new Ritz values.  Synchronises the stream.
+ * Errors: RSX_EINVAL, RSX_ENOMEM, RSX_ECUDA, RSX_ENOTPD (ACE matrix not negative definite). */
+typedef struct rsx_scf rsx_scf;
+int rsx_scf_create(rsx_scf** scf, rsx_ctx* ctx, const float* V_ext, int nocc, int use_ace, float alpha);
+int rsx_scf_init(rsx_scf* scf, const float* psi0, void* stream);
+int rsx_scf_step(rsx_scf* scf, int inner, double* out_host, void* stream);
+int rsx_scf_orbitals(rsx_scf* scf, float* psi_out, void* stream);
+const char* rsx_scf_last_error(const rsx_scf* scf);
+int rsx_scf_destroy(rsx_scf* scf);
 
 /* Learned preconditioner network: conv3d(2 -> 16) ReLU conv3d(16 -> 16) ReLU conv3d(16 -> 1),
  * 3^3 kernels, zero padding 1, weights used in bf16, FP32 activations; every convolution

@@ -325,6 +325,33 @@ template int solve_pairs<double>(rsx_ctx*, const PairMap<double>&, int, int, int
 // ==================================================================================
 // exported C ABI
 
+namespace rsx {
+namespace {
+
+template <typename R>
+__global__ void k_fill(R* x, size_t n, R v) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) x[i] = v;
+}
+
+// V = potential of the density rho: the pair (rho, 1) through the three passes, pass 3
+// writing the potential itself
+template <typename R>
+int poisson(rsx_ctx* c, const void* rho, void* V, cudaStream_t s) {
+  const size_t N = c->g.N();
+  if (!c->ones) {
+    int rc = grow(c, &c->ones, &c->ones_bytes, N * sizeof(R), "unit field");
+    if (rc) return rc;
+    k_fill<R><<<512, 256, 0, s>>>((R*)c->ones, N, R(1));
+    rc = check_cuda(c, cudaGetLastError(), "unit field");
+    if (rc) return rc;
+  }
+  const PairMap<R> pm = pair_map<R>(kProd, rho, c->ones, 1, 1, N);
+  return solve_pairs<R>(c, pm, 0, 1, 0, 1, (R*)V, s, 1);
+}
+
+}  // namespace
+}  // namespace rsx
+
 extern "C" {
 
 int rsx_create(rsx_ctx** out, int nz, int ny, int nx, double h, int precision, int device) {
@@ -374,7 +401,7 @@ int rsx_destroy(rsx_ctx* c) {
   prof_collect(c);
   for (cudaEvent_t e : c->prof_pool) cudaEventDestroy(e);
   void* bufs[] = {c->vhat, c->tw[0], c->tw[1], c->tw[2], c->work, c->gscr, c->dsm, c->smallr, c->status,
-                  c->panel_hi, c->panel_lo, c->gemm_part, c->eig_work, c->gscr_kd, c->pos, c->tdhf_work, c->specw};
+                  c->panel_hi, c->panel_lo, c->gemm_part, c->eig_work, c->gscr_kd, c->pos, c->tdhf_work, c->specw, c->ones};
   for (void* b : bufs)
     if (b) cudaFree(b);
   delete c;
@@ -420,6 +447,15 @@ int rsx_exchange_apply(rsx_ctx* c, const void* phi, int nocc, const void* psi, i
   cudaStream_t s = (cudaStream_t)stream;
   return c->precision == RSX_FP32 ? exchange_apply<float>(c, phi, nocc, psi, npsi, out, s)
                                   : exchange_apply<double>(c, phi, nocc, psi, npsi, out, s);
+}
+
+int rsx_poisson(rsx_ctx* c, const void* rho, void* V, void* stream) {
+  RSX_PREP(c);
+  if (!rho || !V) return set_error(c, RSX_EINVAL, "bad Poisson arguments");
+  const size_t bytes = c->g.N() * c->elem_size();
+  if (overlaps(V, bytes, rho, bytes)) return set_error(c, RSX_EINVAL, "V aliases rho");
+  cudaStream_t s = (cudaStream_t)stream;
+  return c->precision == RSX_FP32 ? poisson<float>(c, rho, V, s) : poisson<double>(c, rho, V, s);
 }
 
 int rsx_ace_build(rsx_ctx* c, const void* phi, int nocc, void* xi, double* M_out, void* stream) {

@@ -38,6 +38,7 @@ struct rsx_ctx {
   void* gscr_kd = nullptr; size_t gscr_kd_bytes = 0;     // occupied pair potentials (K_d)
   void* pos = nullptr; size_t pos_bytes = 0;             // grid coordinates [3][N] (R), dipoles
   void* specw = nullptr; size_t specw_bytes = 0;         // Casida panel weights (float)
+  void* ones = nullptr; size_t ones_bytes = 0;           // unit field (R), Poisson solves of a density
   void* tdhf_work = nullptr; size_t tdhf_work_bytes = 0; // full TDHF: L, A + B, products
   int p2_occ[2] = {0, 0};
   int chunk_outputs = 0;   // tuning: output orbitals per exchange chunk (0 = as many as fit)

@@ -364,6 +364,75 @@ __global__ void __launch_bounds__(kRrThreads) k_rayleigh_ritz(const double* __re
   if (tid < k) theta[tid] = lam[tid];
 }
 
+// out[b][v] -= sum_a C[a][b] xi[a][v]  (the ACE term -xi <xi, f> of Eq. 13, C = <xi, f>).
+// The projectors are taken 16 at a time into registers; C is staged in shared memory,
+// zero-padded to a multiple of 16 rows (16 * ceil(nxi / 16) * nb <= 64 * kMaxBasis).
+__global__ void k_ace_accumulate(float* __restrict__ out, const float* __restrict__ xi, const double* __restrict__ C,
+                                 int nxi, int nb, size_t N) {
+  __shared__ float cs[64 * kMaxBasis];
+  const int na = (nxi + 15) & ~15;
+  for (int i = threadIdx.x; i < na * nb; i += blockDim.x) cs[i] = i < nxi * nb ? (float)C[i] : 0.f;
+  __syncthreads();
+  for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < N; v += (size_t)gridDim.x * blockDim.x) {
+    for (int a0 = 0; a0 < na; a0 += 16) {
+      float x[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) x[j] = a0 + j < nxi ? xi[(size_t)(a0 + j) * N + v] : 0.f;
+      for (int b = 0; b < nb; ++b) {
+        float acc = 0.f;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) acc = fmaf(cs[(a0 + j) * nb + b], x[j], acc);
+        out[(size_t)b * N + v] -= acc;
+      }
+    }
+  }
+}
+
+// out += x (n elements)
+__global__ void k_accumulate(float* __restrict__ out, const float* __restrict__ x, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    out[i] += x[i];
+}
+
+// closed-shell density rho = 2 sum_i phi_i^2
+__global__ void k_density(const float* __restrict__ phi, int nocc, size_t N, float* __restrict__ rho) {
+  for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < N; v += (size_t)gridDim.x * blockDim.x) {
+    float s = 0.f;
+    for (int i = 0; i < nocc; ++i) {
+      const float f = phi[(size_t)i * N + v];
+      s = fmaf(f, f, s);
+    }
+    rho[v] = 2.f * s;
+  }
+}
+
+// part[blk] = partial sums of |a - b| (FP64); a_next = alpha a + (1 - alpha) b (the linear
+// mixing of the input density a with the output density b) when mix != 0
+__global__ void k_absdiff_mix(float* __restrict__ a, const float* __restrict__ b, size_t N, float alpha, int mix,
+                              double* __restrict__ part) {
+  __shared__ double red[8];
+  double s = 0.0;
+  for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < N; v += (size_t)gridDim.x * blockDim.x) {
+    const float av = a[v], bv = b[v];
+    s += fabs((double)av - (double)bv);
+    if (mix) a[v] = alpha * av + (1.f - alpha) * bv;
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    part[blockIdx.x] = t;
+  }
+}
+
+// out = a + b (n elements)
+__global__ void k_add(const float* __restrict__ a, const float* __restrict__ b, size_t n, float* __restrict__ out) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = a[i] + b[i];
+}
+
 // qp[i][j] = qt[i][k + j]: the coefficients of the new orbitals over the non-Psi blocks
 __global__ void k_tail_cols(const float* __restrict__ qt, int k, int m, float* __restrict__ qp) {
   for (int i = threadIdx.x; i < k * (m - k); i += blockDim.x) {
@@ -392,6 +461,13 @@ struct rsx_eig {
   float* qp = nullptr;           // [k][3k] coefficients over the non-Psi blocks
   bool started = false;
   bool has_p = false;            // P (the previous update direction) is in the basis
+  // non-local exchange term of H (rsx_eig_set_exchange): 0 none, 1 ACE -xi xi^T with
+  // projectors xsrc [xcount][N], 2 exact exchange Vx[xsrc] of orbitals xsrc through xctx
+  int xmode = 0;
+  const float* xsrc = nullptr;
+  int xcount = 0;
+  rsx_ctx* xctx = nullptr;
+  float* xbuf = nullptr;         // [4k][N] exact-exchange output
   char err[256] = {0};
 };
 
@@ -421,11 +497,25 @@ int gram(rsx_eig* e, const float* X, int na, const float* Y, int nb, const float
                     "gram reduce");
 }
 
+// out = H f (the full operator, with the exchange term, when V is given; the kinetic part
+// plus shift when V is null)
 int ham(rsx_eig* e, const float* f, int nb, float* out, const double* shift, const float* V, cudaStream_t s) {
   const size_t N = (size_t)e->n * e->n * e->n;
   k_ham_apply<<<(unsigned)blocks_for(nb * N), 256, 0, s>>>(f, nb, e->n, (float)(1.0 / (12.0 * e->h * e->h)), V, shift,
                                                            out);
-  return ecuda(e, cudaGetLastError(), "hamiltonian");
+  int rc = ecuda(e, cudaGetLastError(), "hamiltonian");
+  if (rc || !V || e->xmode == 0) return rc;
+  if (e->xmode == 1) {
+    double* C = e->sm + 256 + 2 * kMaxBasis * kMaxBasis;   // [xcount][nb], past the Rayleigh-Ritz matrices
+    rc = gram(e, e->xsrc, e->xcount, f, nb, nullptr, C, s);
+    if (rc) return rc;
+    k_ace_accumulate<<<(unsigned)std::min<size_t>((N + 255) / 256, 2048), 256, 0, s>>>(out, e->xsrc, C, e->xcount, nb, N);
+    return ecuda(e, cudaGetLastError(), "ACE term");
+  }
+  rc = rsx_exchange_apply(e->xctx, e->xsrc, e->xcount, f, nb, e->xbuf, s);
+  if (rc) return efail(e, rc, "exact exchange in H failed");
+  k_accumulate<<<(unsigned)blocks_for(nb * N), 256, 0, s>>>(out, e->xbuf, nb * N);
+  return ecuda(e, cudaGetLastError(), "exchange term");
 }
 
 // Rayleigh-Ritz over the first m rows of B / HB, update Psi (in place), P (when keep_p)
@@ -491,7 +581,7 @@ int rsx_eig_create(rsx_eig** out, int n, double h, const float* V, float vscale,
       cudaMalloc(&e->R, nband * N * sizeof(float)) != cudaSuccess ||
       cudaMalloc(&e->tmp, 2 * nband * N * sizeof(float)) != cudaSuccess ||
       cudaMalloc(&e->xnet, 2 * nband * N * sizeof(float)) != cudaSuccess ||
-      cudaMalloc(&e->sm, (256 + 2 * kMaxBasis * kMaxBasis) * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&e->sm, (256 + 3 * kMaxBasis * kMaxBasis) * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&e->qt, kMaxBasis * kMaxBasis * sizeof(float)) != cudaSuccess ||
       cudaMalloc(&e->qp, kMaxBasis * kMaxBasis * sizeof(float)) != cudaSuccess) {
     cudaGetLastError();
@@ -581,6 +671,46 @@ int rsx_eig_step(rsx_eig* e, rsx_net* net, int jacobi_sweeps, double* theta_host
   return rc;
 }
 
+// Non-local exchange term of H: mode 0 none; 1 the ACE operator -xi <xi, .> of the
+// projectors src [count][N] (Eq. 13); 2 the exact exchange Vx[src] of the orbitals src
+// [count][N] (Eq. 2) through the context ctx (same grid, FP32).  src stays the caller's.
+// The next step (or rsx_eig_refresh) uses it.
+int rsx_eig_set_exchange(rsx_eig* e, rsx_ctx* ctx, const float* src, int count, int mode) {
+  if (!e || mode < 0 || mode > 2 || (mode && (!src || count < 1 || count > 64))) return RSX_EINVAL;
+  if (mode == 1 && ((count + 15) & ~15) * 4 * e->k > kMaxBasis * kMaxBasis)
+    return efail(e, RSX_EINVAL, "too many ACE projectors for the block size");
+  if (mode == 2) {
+    if (!ctx || ctx->precision != RSX_FP32 || ctx->g.nx != e->n || ctx->g.ny != e->n || ctx->g.nz != e->n)
+      return efail(e, RSX_EINVAL, "exact exchange needs an FP32 context on the eigensolver's grid");
+    if (!e->xbuf) {
+      const size_t N = (size_t)e->n * e->n * e->n;
+      if (cudaMalloc(&e->xbuf, 4 * (size_t)e->k * N * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        return efail(e, RSX_ENOMEM, "exchange scratch");
+      }
+    }
+  }
+  e->xmode = mode;
+  e->xsrc = mode ? src : nullptr;
+  e->xcount = mode ? count : 0;
+  e->xctx = ctx;
+  return RSX_OK;
+}
+
+// H has changed (the potential's contents or the exchange term): H Psi and Rayleigh-Ritz
+// on the current orbitals, the LOBPCG direction dropped.
+int rsx_eig_refresh(rsx_eig* e, double* theta_host, void* stream) {
+  if (!e || !e->started) return RSX_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = ham(e, e->B, e->k, e->HB, nullptr, e->V, s);
+  e->has_p = false;
+  if (!rc) rc = rr_update(e, e->k, false, s);
+  if (!rc && theta_host)
+    rc = ecuda(e, cudaMemcpyAsync(theta_host, e->sm, e->k * sizeof(double), cudaMemcpyDeviceToHost, s), "theta");
+  if (!rc) rc = ecuda(e, cudaStreamSynchronize(s), "refresh sync");
+  return rc;
+}
+
 int rsx_eig_orbitals(rsx_eig* e, float* psi_out, void* stream) {
   if (!e || !psi_out) return RSX_EINVAL;
   const size_t N = (size_t)e->n * e->n * e->n;
@@ -599,11 +729,205 @@ const char* rsx_eig_last_error(const rsx_eig* e) { return e ? e->err : "null eig
 
 int rsx_eig_destroy(rsx_eig* e) {
   if (!e) return RSX_OK;
-  void* bufs[] = {e->B, e->HB, e->R, e->tmp, e->xnet, e->sm, e->qt, e->qp};
+  void* bufs[] = {e->B, e->HB, e->R, e->tmp, e->xnet, e->sm, e->qt, e->qp, e->xbuf};
   for (void* p : bufs)
     if (p) cudaFree(p);
   rsx_destroy(e->ctx);
   delete e;
+  return RSX_OK;
+}
+
+// ---------------------------------------------------------------------------------
+// Closed-shell Hartree-Fock SCF (Sec. 3.1-3.2): per iteration the exchange operator is
+// rebuilt from the current orbitals (ACE: Eqs. 11-13 once per iteration; exact: Eq. 2
+// applied inside every H application), the Hartree potential of the mixed input density
+// is added to V_ext, the block eigensolver takes a few steps, and the output density is
+// mixed linearly into the next input (Eq. 14); the relative density error (Eq. 15) and the
+// HF energy of the orbitals entering the iteration are reported.
+
+}  // extern "C"
+
+struct rsx_scf {
+  rsx_ctx* ctx = nullptr;        // caller's FP32 context on the grid (exchange, Poisson)
+  rsx_eig* eig = nullptr;
+  int n = 0, nocc = 0, mode = 1, iter = 0;
+  double h = 0.0;
+  float alpha = 0.3f;
+  const float* vext = nullptr;   // caller's
+  float* V = nullptr;            // V_ext + V_H, the eigensolver's potential
+  float* rho_in = nullptr;       // mixed input density
+  float* rho = nullptr;          // density of the current orbitals
+  float* vh = nullptr;           // scratch potential
+  float* phi = nullptr;          // [nocc][N] orbitals entering the iteration
+  float* xi = nullptr;           // [nocc][N] ACE projectors
+  float* hphi = nullptr;         // [nocc][N] (T + V_ext) phi
+  double* dsm = nullptr;         // M (nocc^2), Gram results, reduction partials
+  char err[256] = {0};
+};
+
+namespace {
+
+int sfail(rsx_scf* c, int code, const char* msg) {
+  snprintf(c->err, sizeof(c->err), "%s", msg);
+  return code;
+}
+int scuda(rsx_scf* c, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return RSX_OK;
+  snprintf(c->err, sizeof(c->err), "%s: %s", what, cudaGetErrorString(e));
+  return RSX_ECUDA;
+}
+constexpr int kScfRedBlocks = 256;
+
+}  // namespace
+
+extern "C" {
+
+int rsx_scf_create(rsx_scf** out, rsx_ctx* ctx, const float* V_ext, int nocc, int use_ace, float alpha) {
+  if (!out || !ctx || !V_ext || nocc < 1 || nocc > 16 || !(alpha >= 0.f && alpha < 1.f)) return RSX_EINVAL;
+  *out = nullptr;
+  if (ctx->precision != RSX_FP32 || ctx->g.nx != ctx->g.ny || ctx->g.ny != ctx->g.nz) return RSX_EINVAL;
+  rsx_scf* c = new rsx_scf();
+  c->ctx = ctx;
+  c->n = ctx->g.nx;
+  c->nocc = nocc;
+  c->mode = use_ace ? 1 : 2;
+  c->alpha = alpha;
+  c->h = ctx->h;
+  c->vext = V_ext;
+  cudaSetDevice(ctx->device);
+  const size_t N = ctx->g.N();
+  if (cudaMalloc(&c->V, N * sizeof(float)) != cudaSuccess || cudaMalloc(&c->rho_in, N * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&c->rho, N * sizeof(float)) != cudaSuccess || cudaMalloc(&c->vh, N * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&c->phi, nocc * N * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&c->xi, nocc * N * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&c->hphi, nocc * N * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&c->dsm, (4096 + kScfRedBlocks) * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    rsx_scf_destroy(c);
+    return RSX_ENOMEM;
+  }
+  cudaMemcpy(c->V, V_ext, N * sizeof(float), cudaMemcpyDeviceToDevice);
+  const int rc = rsx_eig_create(&c->eig, c->n, c->h, c->V, 1.f, nocc, ctx->device);
+  if (rc) {
+    rsx_scf_destroy(c);
+    return rc;
+  }
+  *out = c;
+  return RSX_OK;
+}
+
+// Starting orbitals psi0 [nocc][N]: Rayleigh-Ritz with H = T + V_ext, input density of
+// the first iteration = their density.
+int rsx_scf_init(rsx_scf* c, const float* psi0, void* stream) {
+  if (!c || !psi0) return RSX_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t N = c->ctx->g.N();
+  int rc = rsx_eig_set_exchange(c->eig, nullptr, nullptr, 0, 0);
+  if (!rc) rc = scuda(c, cudaMemcpyAsync(c->V, c->vext, N * sizeof(float), cudaMemcpyDeviceToDevice, s), "V");
+  if (!rc) rc = rsx_eig_init(c->eig, psi0, stream);
+  if (rc) return sfail(c, rc, "eigensolver start failed");
+  rc = rsx_eig_orbitals(c->eig, c->phi, stream);
+  if (rc) return sfail(c, rc, "orbitals");
+  k_density<<<(unsigned)blocks_for(N), 256, 0, s>>>(c->phi, c->nocc, N, c->rho_in);
+  c->iter = 0;
+  return scuda(c, cudaStreamSynchronize(s), "init sync");
+}
+
+// One SCF iteration with `inner` eigensolver steps (3 Jacobi sweeps each).  out_host[6]:
+// HF energy of the orbitals entering the iteration and its parts (one-body, Hartree,
+// exchange), the relative density error of the previous iteration (Eq. 15; 0 on the
+// first), and the sum of the new Ritz values.  Synchronises the stream.
+int rsx_scf_step(rsx_scf* c, int inner, double* out_host, void* stream) {
+  if (!c || inner < 1 || !out_host) return RSX_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int k = c->nocc;
+  const size_t N = c->ctx->g.N();
+  const double h3 = c->h * c->h * c->h;
+  double* M = c->dsm;                 // [k][k]
+  double* part = c->dsm + 4096;
+  // orbitals entering this iteration, their density, the reldens of the previous
+  // iteration and the mixing of its output density into the input
+  int rc = rsx_eig_orbitals(c->eig, c->phi, stream);
+  if (rc) return sfail(c, rc, "orbitals");
+  k_density<<<(unsigned)blocks_for(N), 256, 0, s>>>(c->phi, k, N, c->rho);
+  double reldens = 0.0;
+  if (c->iter > 0) {
+    k_absdiff_mix<<<kScfRedBlocks, 256, 0, s>>>(c->rho_in, c->rho, N, c->alpha, 1, part);
+    double hp[kScfRedBlocks];
+    rc = scuda(c, cudaMemcpyAsync(hp, part, sizeof(hp), cudaMemcpyDeviceToHost, s), "reldens");
+    if (!rc) rc = scuda(c, cudaStreamSynchronize(s), "reldens sync");
+    if (rc) return rc;
+    for (int b = 0; b < kScfRedBlocks; ++b) reldens += hp[b];
+    reldens *= h3 / (2.0 * k);
+  }
+  // exchange from the entering orbitals: W, M (E_x = tr M) and the ACE projectors
+  rc = rsx_ace_build(c->ctx, c->phi, k, c->xi, M, stream);
+  if (rc) return sfail(c, rc, "ACE build failed");
+  // energy parts of the entering orbitals: one-body, Hartree
+  rc = rsx_poisson(c->ctx, c->rho, c->vh, stream);
+  if (rc) return sfail(c, rc, "Poisson (energy) failed");
+  k_ham_apply<<<(unsigned)blocks_for(k * N), 256, 0, s>>>(c->phi, k, c->n, (float)(1.0 / (12.0 * c->h * c->h)), c->vext,
+                                                          nullptr, c->hphi);
+  const int nblk = 2 * c->ctx->nsm;
+  rc = grow(c->ctx, (void**)&c->ctx->dsm, &c->ctx->dsm_bytes, sizeof(double) * ((size_t)nblk * 4096 + 3 * 4096),
+            "small FP64");
+  double* G = c->dsm + 1024;
+  if (!rc) rc = check_cuda(c->ctx, launch_gram<float>(c->phi, k, c->hphi, k, N, c->ctx->dsm, nblk, s), "one-body");
+  if (!rc) rc = check_cuda(c->ctx, launch_gram_reduce<float>(c->ctx->dsm, nblk, k, k, h3, false, G, (float*)nullptr, s),
+                           "one-body");
+  double* EH = c->dsm + 2048;
+  if (!rc) rc = check_cuda(c->ctx, launch_gram<float>(c->rho, 1, c->vh, 1, N, c->ctx->dsm, nblk, s), "hartree");
+  if (!rc) rc = check_cuda(c->ctx, launch_gram_reduce<float>(c->ctx->dsm, nblk, 1, 1, h3, false, EH, (float*)nullptr, s),
+                           "hartree");
+  if (rc) return rc;
+  double hm[3 * 1024];
+  rc = scuda(c, cudaMemcpyAsync(hm, c->dsm, sizeof(hm), cudaMemcpyDeviceToHost, s), "energies");
+  if (!rc) rc = scuda(c, cudaStreamSynchronize(s), "energy sync");
+  if (!rc) rc = rsx_sync_status(c->ctx, stream);
+  if (rc) return sfail(c, rc, "energy evaluation failed (ACE matrix not negative definite?)");
+  double one = 0.0, ex = 0.0;
+  for (int i = 0; i < k; ++i) {
+    one += 2.0 * hm[1024 + i * k + i];
+    ex += hm[i * k + i];
+  }
+  const double eh = 0.5 * hm[2048];
+  if (c->iter == 0) cudaMemcpyAsync(c->rho_in, c->rho, N * sizeof(float), cudaMemcpyDeviceToDevice, s);
+  // Fock operator of this iteration: V = V_ext + V_H[rho_in], exchange of the entering orbitals
+  rc = rsx_poisson(c->ctx, c->rho_in, c->vh, stream);
+  if (rc) return sfail(c, rc, "Poisson failed");
+  k_add<<<(unsigned)blocks_for(N), 256, 0, s>>>(c->vext, c->vh, N, c->V);
+  rc = rsx_eig_set_exchange(c->eig, c->ctx, c->mode == 1 ? c->xi : c->phi, k, c->mode);
+  if (!rc) rc = rsx_eig_refresh(c->eig, nullptr, stream);
+  double theta[64] = {0};
+  for (int it = 0; it < inner && !rc; ++it) rc = rsx_eig_step(c->eig, nullptr, 3, theta, stream);
+  if (rc) return sfail(c, rc, rsx_eig_last_error(c->eig));
+  double ts = 0.0;
+  for (int i = 0; i < k; ++i) ts += theta[i];
+  out_host[0] = one + eh + ex;
+  out_host[1] = one;
+  out_host[2] = eh;
+  out_host[3] = ex;
+  out_host[4] = reldens;
+  out_host[5] = ts;
+  ++c->iter;
+  return RSX_OK;
+}
+
+int rsx_scf_orbitals(rsx_scf* c, float* psi_out, void* stream) {
+  if (!c || !psi_out) return RSX_EINVAL;
+  return rsx_eig_orbitals(c->eig, psi_out, stream);
+}
+
+const char* rsx_scf_last_error(const rsx_scf* c) { return c ? c->err : "null SCF"; }
+
+int rsx_scf_destroy(rsx_scf* c) {
+  if (!c) return RSX_OK;
+  cudaDeviceSynchronize();
+  if (c->eig) rsx_eig_destroy(c->eig);
+  void* bufs[] = {c->V, c->rho_in, c->rho, c->vh, c->phi, c->xi, c->hphi, c->dsm};
+  for (void* p : bufs)
+    if (p) cudaFree(p);
+  delete c;
   return RSX_OK;
 }
 

@@ -29,6 +29,7 @@ SIGNATURES = {
     "rsx_build_pair_densities": [_P, _P, _I, _P, _I, _P, _P],
     "rsx_exchange_apply": [_P, _P, _I, _P, _I, _P, _P],
     "rsx_exchange_apply_noalloc": [_P, _P, _I, _P, _I, _P, _P],
+    "rsx_poisson": [_P, _P, _P, _P],
     "rsx_ace_build": [_P, _P, _I, _P, _P, _P],
     "rsx_ace_apply": [_P, _P, _I, _P, _I, _P, _P],
     "rsx_casida_K": [_P, _P, _I, _P, _I, _P, _P],
@@ -46,6 +47,14 @@ SIGNATURES = {
     "rsx_eig_residual": [_P, _P, _P],
     "rsx_eig_last_error": [_P],
     "rsx_eig_destroy": [_P],
+    "rsx_eig_set_exchange": [_P, _P, _P, _I, _I],
+    "rsx_eig_refresh": [_P, ctypes.POINTER(_D), _P],
+    "rsx_scf_create": [ctypes.POINTER(_P), _P, _P, _I, _I, ctypes.c_float],
+    "rsx_scf_init": [_P, _P, _P],
+    "rsx_scf_step": [_P, _I, ctypes.POINTER(_D), _P],
+    "rsx_scf_orbitals": [_P, _P, _P],
+    "rsx_scf_last_error": [_P],
+    "rsx_scf_destroy": [_P],
     "rsx_net_create": [ctypes.POINTER(_P), _I],
     "rsx_net_param_count": [],
     "rsx_net_set_params": [_P, ctypes.POINTER(ctypes.c_float), _I],
@@ -92,7 +101,8 @@ def load(path=LIB_PATH):
             f = getattr(lib, name)
             f.argtypes = args
             f.restype = (ctypes.c_char_p if name in ("rsx_last_error", "rsx_kernel_name", "rsx_batch_last_error",
-                                                     "rsx_eig_last_error", "rsx_net_last_error")
+                                                     "rsx_eig_last_error", "rsx_net_last_error",
+                                                     "rsx_scf_last_error")
                          else ctypes.c_int)
         _lib = lib
     return _lib
@@ -184,6 +194,14 @@ class Context:
         self._check(self.lib.rsx_exchange_apply_noalloc(self.handle, _ptr(phi), nocc, _ptr(psi), npsi, _ptr(out),
                                                         _stream(stream)))
         return out
+
+    def poisson(self, rho, V=None, stream=None):
+        """Isolated-boundary potential of one density (the solve behind Eq. 2)."""
+        if self._orb(rho, "rho") != 1:
+            raise ValueError("rho: one density")
+        V = torch.empty_like(rho) if V is None else V
+        self._check(self.lib.rsx_poisson(self.handle, _ptr(rho), _ptr(V), _stream(stream)))
+        return V
 
     def ace_build(self, phi, xi=None, M=None, stream=None):
         nocc = self._orb(phi, "phi")
@@ -432,6 +450,18 @@ class Eigensolver:
                                           _stream(stream)))
         return list(th)
 
+    def set_exchange(self, src=None, mode=0, ctx=None):
+        """Exchange term of H: mode 0 none, 1 ACE with projectors src, 2 exact Vx[src] via ctx."""
+        self._xsrc = src                      # the library keeps the pointer
+        count = src.shape[0] if src is not None else 0
+        self._check(self.lib.rsx_eig_set_exchange(self.handle, ctx.handle if ctx is not None else None,
+                                                  _ptr(src), int(count), int(mode)))
+
+    def refresh(self, stream=None):
+        th = (ctypes.c_double * self.nband)()
+        self._check(self.lib.rsx_eig_refresh(self.handle, th, _stream(stream)))
+        return list(th)
+
     def orbitals(self, out=None, stream=None):
         out = torch.empty((self.nband,) + tuple(self.V.shape), dtype=torch.float32, device=self.V.device) \
             if out is None else out
@@ -447,6 +477,55 @@ class Eigensolver:
     def close(self):
         if getattr(self, "handle", None):
             self.lib.rsx_eig_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class SCF:
+    """Closed-shell Hartree-Fock SCF with ACE or exact exchange (Sec. 3.1-3.2) on the
+    cubic box of an FP32 Context; V_ext a device [n, n, n] float32 tensor."""
+
+    FIELDS = ("energy", "one_body", "hartree", "exchange", "reldens", "theta_sum")
+
+    def __init__(self, ctx, v_ext, nocc, ace=True, alpha=0.3):
+        self.lib = load()
+        self.ctx = ctx                        # kept alive: the library holds both pointers
+        self.v_ext = v_ext
+        self.nocc = nocc
+        h_ = ctypes.c_void_p()
+        code = self.lib.rsx_scf_create(ctypes.byref(h_), ctx.handle, _ptr(v_ext), int(nocc), int(bool(ace)),
+                                       float(alpha))
+        if code != RSX_OK:
+            raise RsxError(code, "rsx_scf_create failed")
+        self.handle = h_
+
+    def _check(self, code):
+        if code != RSX_OK:
+            raise RsxError(code, self.lib.rsx_scf_last_error(self.handle).decode())
+
+    def init(self, psi0, stream=None):
+        self._check(self.lib.rsx_scf_init(self.handle, _ptr(psi0), _stream(stream)))
+
+    def step(self, inner=2, stream=None):
+        """One SCF iteration; returns a dict of the six reported quantities."""
+        out = (ctypes.c_double * 6)()
+        self._check(self.lib.rsx_scf_step(self.handle, int(inner), out, _stream(stream)))
+        return dict(zip(self.FIELDS, list(out)))
+
+    def orbitals(self, out=None, stream=None):
+        out = torch.empty((self.nocc,) + tuple(self.v_ext.shape), dtype=torch.float32, device=self.v_ext.device) \
+            if out is None else out
+        self._check(self.lib.rsx_scf_orbitals(self.handle, _ptr(out), _stream(stream)))
+        return out
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.rsx_scf_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

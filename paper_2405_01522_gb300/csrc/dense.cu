@@ -1,6 +1,9 @@
 // Small dense kernels around the pair solves: the kernel spectrum table, Gram
 // reductions <X_a, Y_b>, the FP64 Cholesky of -M with L^{-1}, and the
 // small-matrix application out_o = sum_i C[o][i] X_i used by ACE (Sec. 3.1, Eqs. 11-13).
+#include <algorithm>
+#include <cstdint>
+
 #include "dense.cuh"
 
 namespace rsx {
@@ -114,21 +117,176 @@ __global__ void __launch_bounds__(kGramThreads) k_gram(const R* __restrict__ X, 
   }
 }
 
+// Register-tiled Gram partials (same result layout): each thread owns a 4 x 4 tile of
+// outputs over a 1/S share of every chunk's points, S threads per tile (a power of two up
+// to 32, so a tile's threads share a warp and are summed by shuffles at the end).  Points
+// are staged transposed, [point][row], with a row stride of an odd number of 4-element
+// groups, so that 4-element loads by consecutive points do not collide in shared memory.
+// For up to 256 tiles.
+__device__ inline void ld4(const float* p, float v[4]) {
+  const float4 t = *reinterpret_cast<const float4*>(p);
+  v[0] = t.x;
+  v[1] = t.y;
+  v[2] = t.z;
+  v[3] = t.w;
+}
+__device__ inline void ld4(const double* p, double v[4]) {
+  const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+  v[0] = a.x;
+  v[1] = a.y;
+  v[2] = b.x;
+  v[3] = b.y;
+}
+
+__host__ __device__ inline int gram_stride(int n) { return ((((n + 3) >> 2)) | 1) * 4; }
+
+// Stage rows [0, na) of X (times w when given) for points [r0, r0 + len) into xs[j][a]
+// (rows na .. sx - 1 zero).  vec: R is float, X (and w) 16-byte aligned, N % 4 == 0 --
+// every thread then issues its (at most kStageVec) 4-point loads before any store, rows
+// along the lanes so that the transposed stores do not collide.
+constexpr int kStageVec = 9;   // ceil(68 * 32 / 256): rows up to 64 (stride 68)
+template <typename R>
+__device__ inline void gram_stage(const R* __restrict__ X, int na, const R* __restrict__ w, size_t N, size_t r0,
+                                  int len, R* __restrict__ xs, int sx, bool vec) {
+  if constexpr (sizeof(R) == 4) {
+    if (vec) {
+      constexpr int Q = kGramChunk / 4;
+      const int total = sx * Q;
+      float4 v[kStageVec];
+#pragma unroll
+      for (int u = 0; u < kStageVec; ++u) {
+        const int i = threadIdx.x + u * kGramThreads;
+        const int q = i / sx, a = i - q * sx;
+        v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (i < total && a < na && 4 * q < len) {
+          v[u] = *reinterpret_cast<const float4*>(X + (size_t)a * N + r0 + 4 * q);
+          if (w) {
+            const float4 c = *reinterpret_cast<const float4*>(w + r0 + 4 * q);
+            v[u] = make_float4(v[u].x * c.x, v[u].y * c.y, v[u].z * c.z, v[u].w * c.w);
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kStageVec; ++u) {
+        const int i = threadIdx.x + u * kGramThreads;
+        if (i < total) {
+          const int q = i / sx, a = i - q * sx;
+          float* d = reinterpret_cast<float*>(xs) + 4 * q * sx + a;
+          d[0] = v[u].x;
+          d[sx] = v[u].y;
+          d[2 * sx] = v[u].z;
+          d[3 * sx] = v[u].w;
+        }
+      }
+      return;
+    }
+  }
+  for (int i = threadIdx.x; i < sx * kGramChunk; i += kGramThreads) {
+    const int a = i / kGramChunk, j = i - a * kGramChunk;
+    R v = R(0);
+    if (a < na && j < len) v = w ? X[(size_t)a * N + r0 + j] * w[r0 + j] : X[(size_t)a * N + r0 + j];
+    xs[j * sx + a] = v;
+  }
+}
+
+// sym: X == Y, na == nb, no weight -- one staged copy, tiles (i <= j) only, each written
+// to both halves.
+template <typename R>
+__global__ void __launch_bounds__(kGramThreads) k_gram_tiled(const R* __restrict__ X, int na, const R* __restrict__ Y,
+                                                             int nb, const R* __restrict__ w, size_t N, int S, int sym,
+                                                             int vec, double* __restrict__ part) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int ta = (na + 3) >> 2, tb = (nb + 3) >> 2;
+  const int sx = gram_stride(na), sy = gram_stride(nb);
+  R* xs = reinterpret_cast<R*>(smem_raw);            // [kGramChunk][sx]
+  R* ys = sym ? xs : xs + kGramChunk * sx;           // [kGramChunk][sy]
+  const int tile = threadIdx.x / S, split = threadIdx.x - tile * S;
+  int ti = 0, tj = 0;
+  bool active;
+  if (sym) {
+    // tile -> (ti, tj), ti <= tj, row-major over the upper triangle
+    active = tile < ta * (ta + 1) / 2;
+    int t = tile;
+    while (active && t >= ta - ti) {
+      t -= ta - ti;
+      ++ti;
+    }
+    tj = ti + t;
+  } else {
+    active = tile < ta * tb;
+    ti = tile / tb;
+    tj = tile - ti * tb;
+  }
+  const int a0 = active ? ti * 4 : 0, b0 = active ? tj * 4 : 0;
+  double acc[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) acc[q] = 0.0;
+  const size_t nchunk = (N + kGramChunk - 1) / kGramChunk;
+  for (size_t c = blockIdx.x; c < nchunk; c += gridDim.x) {
+    const size_t r0 = c * kGramChunk;
+    const int len = (int)min((size_t)kGramChunk, N - r0);
+    __syncthreads();
+    gram_stage<R>(X, na, nullptr, N, r0, len, xs, sx, vec != 0);
+    if (!sym) gram_stage<R>(Y, nb, w, N, r0, len, ys, sy, vec != 0);
+    __syncthreads();
+    if (active) {
+      R sacc[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) sacc[q] = R(0);
+#pragma unroll 4
+      for (int j = split; j < kGramChunk; j += S) {
+        R xv[4], yv[4];
+        ld4(xs + j * sx + a0, xv);
+        ld4(ys + j * sy + b0, yv);
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) sacc[p * 4 + q] = fma(xv[p], yv[q], sacc[p * 4 + q]);
+      }
+#pragma unroll
+      for (int q = 0; q < 16; ++q) acc[q] += (double)sacc[q];
+    }
+  }
+  for (int o = S >> 1; o > 0; o >>= 1)
+#pragma unroll
+    for (int q = 0; q < 16; ++q) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+  if (active && split == 0) {
+    const int nout = na * nb;
+    double* pb = part + (size_t)blockIdx.x * nout;
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (a0 + p < na && b0 + q < nb) {
+          pb[(a0 + p) * nb + b0 + q] = acc[p * 4 + q];
+          if (sym) pb[(b0 + q) * nb + a0 + p] = acc[p * 4 + q];
+        }
+  }
+}
+
 // out[a][b] (or out[b][a] when transpose) = scale * sum_blk part[blk][a][b]; optional
-// R copy with the same layout.
+// R copy with the same layout.  32 outputs per block, 8 warps splitting the partials.
 // (ldo: row stride of out / out_r; 0 means na or nb as implied by transpose)
 template <typename R>
 __global__ void k_gram_reduce(const double* __restrict__ part, int nblk, int na, int nb, double scale,
                               int transpose, double* __restrict__ out, R* __restrict__ out_r, int ldo) {
+  __shared__ double red[8][33];
   const int nout = na * nb;
-  for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < nout; o += gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int k = 0; k < nblk; ++k) s += part[(size_t)k * nout + o];
-    s *= scale;
+  const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+  const int o = blockIdx.x * 32 + lane;
+  double s = 0.0;
+  if (o < nout)
+    for (int k = g; k < nblk; k += 8) s += part[(size_t)k * nout + o];
+  red[g][lane] = s;
+  __syncthreads();
+  if (g == 0 && o < nout) {
+    double t = 0.0;
+    for (int q = 0; q < 8; ++q) t += red[q][lane];
+    t *= scale;
     const int a = o / nb, b = o - a * nb;
     const size_t d = transpose ? (size_t)b * (ldo ? ldo : na) + a : (size_t)a * (ldo ? ldo : nb) + b;
-    if (out) out[d] = s;
-    if (out_r) out_r[d] = (R)s;
+    if (out) out[d] = t;
+    if (out_r) out_r[d] = (R)t;
   }
 }
 
@@ -221,6 +379,69 @@ __global__ void __launch_bounds__(kCombPts) k_combine(const R* __restrict__ C, i
   }
 }
 
+// FP32 combination with the outputs in registers: each thread owns PTS consecutive points
+// and NO outputs (output group blockIdx.y); X is read straight from global memory as
+// PTS-wide vectors, the coefficients are staged transposed, ct[i][NO] (zero-padded), and
+// read as 4-wide broadcasts -- 4 NO x PTS / (NO + 4 PTS) FMAs per shared-memory word
+// instead of the 1/2 of k_combine.  Same summation order over i as k_combine.
+// N % PTS == 0; X, out PTS*4-byte aligned; with one output group out may equal X.
+template <int NO, int PTS>
+__global__ void __launch_bounds__(256) k_combine_reg(const float* __restrict__ C, int no, int ni, const float* X,
+                                                     size_t N, float* out) {
+  extern __shared__ __align__(16) float ct[];   // [ni][NO]
+  const int o0 = blockIdx.y * NO;
+  for (int q = threadIdx.x; q < ni * NO; q += blockDim.x) {
+    const int i = q / NO, o = q - i * NO;
+    ct[q] = o0 + o < no ? C[(size_t)(o0 + o) * ni + i] : 0.f;
+  }
+  __syncthreads();
+  const size_t ng = N / PTS;
+  for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < ng; g += (size_t)gridDim.x * blockDim.x) {
+    float acc[NO][PTS];
+#pragma unroll
+    for (int o = 0; o < NO; ++o)
+#pragma unroll
+      for (int p = 0; p < PTS; ++p) acc[o][p] = 0.f;
+    const float* xp = X + g * PTS;
+#pragma unroll 2
+    for (int i = 0; i < ni; ++i) {
+      float xv[PTS];
+      if constexpr (PTS == 4) {
+        const float4 t = *reinterpret_cast<const float4*>(xp + (size_t)i * N);
+        xv[0] = t.x;
+        xv[1] = t.y;
+        xv[2] = t.z;
+        xv[3] = t.w;
+      } else {
+        const float2 t = *reinterpret_cast<const float2*>(xp + (size_t)i * N);
+        xv[0] = t.x;
+        xv[1] = t.y;
+      }
+#pragma unroll
+      for (int o4 = 0; o4 < NO; o4 += 4) {
+        const float4 c = *reinterpret_cast<const float4*>(ct + i * NO + o4);
+#pragma unroll
+        for (int p = 0; p < PTS; ++p) {
+          acc[o4][p] = fmaf(c.x, xv[p], acc[o4][p]);
+          acc[o4 + 1][p] = fmaf(c.y, xv[p], acc[o4 + 1][p]);
+          acc[o4 + 2][p] = fmaf(c.z, xv[p], acc[o4 + 2][p]);
+          acc[o4 + 3][p] = fmaf(c.w, xv[p], acc[o4 + 3][p]);
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 0; o < NO; ++o) {
+      if (o0 + o < no) {
+        float* op = out + (size_t)(o0 + o) * N + g * PTS;
+        if constexpr (PTS == 4)
+          *reinterpret_cast<float4*>(op) = make_float4(acc[o][0], acc[o][1], acc[o][2], acc[o][3]);
+        else
+          *reinterpret_cast<float2*>(op) = make_float2(acc[o][0], acc[o][1]);
+      }
+    }
+  }
+}
+
 // rho[a * nb + b][r] = A[a][r] * B[b][r]
 template <typename R>
 __global__ void k_pair_products(const R* __restrict__ A, int na, const R* __restrict__ B, int nb, size_t N,
@@ -260,6 +481,20 @@ template <typename R>
 cudaError_t launch_gram(const R* X, int na, const R* Y, int nb, size_t N, double* part, int nblk,
                         cudaStream_t s, const R* w) {
   if (na * nb > 16 * kGramThreads) return cudaErrorInvalidValue;
+  const bool sym = X == Y && na == nb && w == nullptr;
+  const int ta = (na + 3) / 4, tb = (nb + 3) / 4;
+  const int tiles = sym ? ta * (ta + 1) / 2 : ta * tb;
+  if (tiles <= kGramThreads && gram_stride(na) <= 68 && gram_stride(nb) <= 68) {
+    int S = 1;
+    while (S < 32 && 2 * S * tiles <= kGramThreads) S *= 2;
+    auto al16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
+    const bool vec = sizeof(R) == 4 && N % 4 == 0 && al16(X) && al16(Y) && (w == nullptr || al16(w));
+    const size_t smem = sizeof(R) * (size_t)(gram_stride(na) + (sym ? 0 : gram_stride(nb))) * kGramChunk;
+    cudaError_t e = cudaFuncSetAttribute(k_gram_tiled<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_gram_tiled<R><<<nblk, kGramThreads, smem, s>>>(X, na, Y, nb, w, N, S, sym ? 1 : 0, vec ? 1 : 0, part);
+    return cudaGetLastError();
+  }
   const size_t smem = sizeof(R) * (size_t)(na + nb) * (kGramChunk + 1);
   cudaError_t e = cudaFuncSetAttribute(k_gram<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -270,8 +505,8 @@ cudaError_t launch_gram(const R* X, int na, const R* Y, int nb, size_t N, double
 template <typename R>
 cudaError_t launch_gram_reduce(const double* part, int nblk, int na, int nb, double scale, bool transpose,
                                double* out, R* out_r, cudaStream_t s, int ldo) {
-  k_gram_reduce<R><<<(na * nb + 255) / 256, 256, 0, s>>>(part, nblk, na, nb, scale, transpose ? 1 : 0, out,
-                                                          out_r, ldo);
+  k_gram_reduce<R><<<(na * nb + 31) / 32, 256, 0, s>>>(part, nblk, na, nb, scale, transpose ? 1 : 0, out,
+                                                        out_r, ldo);
   return cudaGetLastError();
 }
 
@@ -287,6 +522,23 @@ cudaError_t launch_chol_linv(double* M, int k, double* Linv, float* linv_f, doub
 template <typename R>
 cudaError_t launch_combine(const R* C, int no, int ni, const R* X, size_t N, R* out, int nblk,
                            cudaStream_t s) {
+  if constexpr (sizeof(R) == 4) {
+    auto al = [](const void* p, int a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; };
+    const bool inplace = reinterpret_cast<const void*>(X) == reinterpret_cast<const void*>(out);
+    const int ngrp16 = (no + 15) / 16;
+    if (N % 4 == 0 && al(X, 16) && al(out, 16) && (!inplace || no <= 16) && ni <= 768) {
+      const size_t smem = sizeof(float) * (size_t)ni * 16;
+      const int bx = (int)std::max<size_t>(1, std::min<size_t>((size_t)nblk, (N / 4 + 255) / 256));
+      k_combine_reg<16, 4><<<dim3(bx, ngrp16), 256, smem, s>>>(C, no, ni, X, N, out);
+      return cudaGetLastError();
+    }
+    if (N % 2 == 0 && al(X, 8) && al(out, 8) && inplace && no <= 32 && ni <= 384) {
+      const size_t smem = sizeof(float) * (size_t)ni * 32;
+      const int bx = (int)std::max<size_t>(1, std::min<size_t>((size_t)nblk, (N / 2 + 255) / 256));
+      k_combine_reg<32, 2><<<dim3(bx, 1), 256, smem, s>>>(C, no, ni, X, N, out);
+      return cudaGetLastError();
+    }
+  }
   const size_t smem = sizeof(R) * ((size_t)no * ni + (size_t)ni * kCombPts);
   cudaError_t e = cudaFuncSetAttribute(k_combine<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

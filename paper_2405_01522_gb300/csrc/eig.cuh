@@ -25,54 +25,76 @@ __device__ inline double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
+__device__ inline float warp_sum(float v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
 
-// LU with partial pivoting of T - lam I (serial, one thread): sc holds 4 n doubles
-// (reciprocal pivots, first and second superdiagonal of U, multipliers), piv n ints
-__device__ inline void tri_factor_shifted(const double* d, const double* e, int n, double lam, double* sc, int* piv) {
-  double* dg = sc;
-  double* u1 = sc + n;
-  double* u2 = sc + 2 * n;
-  double* lw = sc + 3 * n;
-  const double eps_shift = 1e-14 * fmax(1.0, fabs(lam));
+// FP32 count of eigenvalues of T below x (the ratio form above in single precision, with
+// the single-precision pivmin); for bracketing roots before an FP64 refinement
+__device__ inline int sturm_count_f32(const float* d, const float* e2, int n, float x, float pivmin) {
+  int cnt = 0;
+  float q = d[0] - x;
+  if (fabsf(q) < pivmin) q = -pivmin;
+  if (q < 0.f) ++cnt;
+  for (int i = 1; i < n; ++i) {
+    q = (d[i] - x) - e2[i - 1] / q;
+    if (fabsf(q) < pivmin) q = -pivmin;
+    if (q < 0.f) ++cnt;
+  }
+  return cnt;
+}
+
+// LU with partial pivoting of T - lam I (serial, one thread): sc holds 4 n values
+// (reciprocal pivots, first and second superdiagonal of U, multipliers), piv n ints.
+// R = double, or float for a first approximation.
+template <typename R>
+__device__ inline void tri_factor_shifted(const R* d, const R* e, int n, R lam, R* sc, int* piv) {
+  R* dg = sc;
+  R* u1 = sc + n;
+  R* u2 = sc + 2 * n;
+  R* lw = sc + 3 * n;
+  const R eps_shift = R(sizeof(R) == 8 ? 1e-14 : 1e-6) * fmax(R(1), fabs(lam));
   for (int i = 0; i < n; ++i) {
     dg[i] = d[i] - lam;
-    u1[i] = i < n - 1 ? e[i] : 0.0;
-    u2[i] = 0.0;
+    u1[i] = i < n - 1 ? e[i] : R(0);
+    u2[i] = R(0);
   }
   for (int i = 0; i < n - 1; ++i) {
-    const double sub = e[i];
+    const R sub = e[i];
     if (fabs(dg[i]) >= fabs(sub)) {
       piv[i] = 0;
-      if (dg[i] == 0.0) dg[i] = eps_shift;
-      const double l = sub / dg[i];
+      if (dg[i] == R(0)) dg[i] = eps_shift;
+      const R l = sub / dg[i];
       lw[i] = l;
       dg[i + 1] -= l * u1[i];
     } else {
       piv[i] = 1;
-      const double l = dg[i] / sub;
+      const R l = dg[i] / sub;
       lw[i] = l;
-      const double t0 = dg[i + 1], t1 = (i + 1 < n - 1) ? u1[i + 1] : 0.0;
+      const R t0 = dg[i + 1], t1 = (i + 1 < n - 1) ? u1[i + 1] : R(0);
       dg[i] = sub;
-      const double old_u1 = u1[i];
+      const R old_u1 = u1[i];
       u1[i] = t0;
       u2[i] = t1;
       dg[i + 1] = old_u1 - l * t0;
       if (i + 1 < n - 1) u1[i + 1] = -l * t1;
     }
   }
-  if (dg[n - 1] == 0.0) dg[n - 1] = eps_shift;
-  for (int i = 0; i < n; ++i) dg[i] = 1.0 / dg[i];   // solves multiply by the reciprocals
+  if (dg[n - 1] == R(0)) dg[n - 1] = eps_shift;
+  for (int i = 0; i < n; ++i) dg[i] = R(1) / dg[i];   // solves multiply by the reciprocals
 }
 
 // z <- (T - lam I)^{-1} z with the factors of tri_factor_shifted (serial, one thread)
-__device__ inline void tri_solve_factored(int n, double* z, const double* sc, const int* piv) {
-  const double* rdg = sc;
-  const double* u1 = sc + n;
-  const double* u2 = sc + 2 * n;
-  const double* lw = sc + 3 * n;
+template <typename R>
+__device__ inline void tri_solve_factored(int n, R* z, const R* sc, const int* piv) {
+  const R* rdg = sc;
+  const R* u1 = sc + n;
+  const R* u2 = sc + 2 * n;
+  const R* lw = sc + 3 * n;
   for (int i = 0; i < n - 1; ++i) {
     if (piv[i]) {
-      const double t = z[i];
+      const R t = z[i];
       z[i] = z[i + 1];
       z[i + 1] = t - lw[i] * z[i];
     } else {
@@ -80,7 +102,7 @@ __device__ inline void tri_solve_factored(int n, double* z, const double* sc, co
     }
   }
   for (int i = n - 1; i >= 0; --i) {
-    double s = z[i];
+    R s = z[i];
     if (i + 1 < n) s -= u1[i] * z[i + 1];
     if (i + 2 < n) s -= u2[i] * z[i + 2];
     z[i] = s * rdg[i];
@@ -90,26 +112,27 @@ __device__ inline void tri_solve_factored(int n, double* z, const double* sc, co
 // one warp: `iters` inverse iterations for root r (vector z, length n), each followed by
 // orthogonalisation against the roots j in `ortho` (bit j set) and normalisation; the
 // shifted matrix is factored once
-__device__ inline void warp_inverse_iteration(const double* d, const double* e, int n, double lam, double* z, double* sc,
-                                              int* piv, int iters, const double* Z, int ldz, unsigned ortho) {
+template <typename R>
+__device__ inline void warp_inverse_iteration(const R* d, const R* e, int n, R lam, R* z, R* sc, int* piv, int iters,
+                                              const R* Z, int ldz, unsigned ortho) {
   const int lane = threadIdx.x & 31;
-  if (lane == 0) tri_factor_shifted(d, e, n, lam, sc, piv);
+  if (lane == 0) tri_factor_shifted<R>(d, e, n, lam, sc, piv);
   __syncwarp();
   for (int it = 0; it < iters; ++it) {
-    if (lane == 0) tri_solve_factored(n, z, sc, piv);
+    if (lane == 0) tri_solve_factored<R>(n, z, sc, piv);
     __syncwarp();
     for (unsigned bits = ortho; bits; bits &= bits - 1) {
       const int j = __ffs(bits) - 1;
-      double sdot = 0.0;
+      R sdot = R(0);
       for (int i = lane; i < n; i += 32) sdot += Z[j * ldz + i] * z[i];
       sdot = warp_sum(sdot);
       for (int i = lane; i < n; i += 32) z[i] -= sdot * Z[j * ldz + i];
       __syncwarp();
     }
-    double nn = 0.0;
+    R nn = R(0);
     for (int i = lane; i < n; i += 32) nn += z[i] * z[i];
     nn = warp_sum(nn);
-    const double inv = nn > 0.0 ? 1.0 / sqrt(nn) : 0.0;
+    const R inv = nn > R(0) ? R(1) / sqrt(nn) : R(0);
     for (int i = lane; i < n; i += 32) z[i] *= inv;
     __syncwarp();
   }
@@ -119,8 +142,8 @@ __device__ inline void warp_inverse_iteration(const double* d, const double* e, 
 // FP64 units): the leading principal minors p_i of T - x I follow
 // p_0 = 1, p_1 = d_0 - x, p_{i+1} = (d_i - x) p_i - e_{i-1}^2 p_{i-1}, and the LDL^T pivot
 // q_i = p_i / p_{i-1} is negative exactly when p_i and p_{i-1} differ in sign.  e2 holds
-// e_i^2.  After every step the binary exponent of p_i is checked with integer operations
-// and the pair (p_{i-1}, p_i) is rescaled by a power of two when it has left
+// e_i^2.  After every step the binary exponent of the larger of |p_{i-1}|, |p_i| is checked
+// with integer operations and the pair is rescaled by a power of two when it has left
 // [2^-400, 2^400] (one step cannot overflow from there unless the Gershgorin radius exceeds
 // 2^300); an exact zero minor is replaced by -2^-60 times its predecessor (a tiny negative
 // pivot, the role pivmin plays above; relative, so that it cannot underflow).
@@ -134,7 +157,8 @@ __device__ inline int sturm_count_prod(const double* d, const double* e2, int n,
     cnt += (pn < 0.0) != (p < 0.0);
     pm = p;
     p = pn;
-    const int ex = ((__double2hiint(p) >> 20) & 0x7FF) - 1023;
+    // rescale both by a power of two when the larger leaves [2^-400, 2^400]
+    const int ex = ((__double2hiint(fmax(fabs(p), fabs(pm))) >> 20) & 0x7FF) - 1023;
     if (ex > 400 || ex < -400) {
       p = ldexp(p, -ex);
       pm = ldexp(pm, -ex);

@@ -33,28 +33,81 @@ namespace {
 constexpr int kMaxBasis = 64;
 
 // out = -1/2 Lap_FD4 f + V f  (or only the kinetic part when V is null; plus shift T_i f
-// when shift is not null).  f, out: [nb][n^3].
+// when shift is not null).  f, out: [nb][n^3].  Block (x threads, rows of y), grid
+// (y blocks, z, orbital): no index division, and the y / z boundary test is uniform over
+// each warp (a warp holds one y row), so only the x neighbours are predicated per lane.
 __global__ void k_ham_apply(const float* __restrict__ f, int nb, int n, float inv12h2, const float* __restrict__ V,
                             const double* __restrict__ shift, float* __restrict__ out) {
-  const size_t N = (size_t)n * n * n;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < (size_t)nb * N;
-       i += (size_t)gridDim.x * blockDim.x) {
-    const size_t b = i / N, v = i - b * N;
-    const int x = (int)(v % n), y = (int)((v / n) % n), z = (int)(v / ((size_t)n * n));
-    const float* fb = f + b * N;
-    const float c = fb[v];
-    // per axis 16 (f-1 + f+1) - (f-2 + f+2) - 30 c, summed as differences from c so that
-    // the FP32 rounding is relative to the second differences, not to c (no cancellation)
-    auto d = [&](bool ok, size_t off, bool up) { return (ok ? fb[up ? v + off : v - off] : 0.f) - c; };
-    const size_t sy = n, sz = (size_t)n * n;
-    float lap = 16.f * (d(x > 0, 1, false) + d(x < n - 1, 1, true)) - (d(x > 1, 2, false) + d(x < n - 2, 2, true));
-    lap += 16.f * (d(y > 0, sy, false) + d(y < n - 1, sy, true)) - (d(y > 1, 2 * sy, false) + d(y < n - 2, 2 * sy, true));
-    lap += 16.f * (d(z > 0, sz, false) + d(z < n - 1, sz, true)) - (d(z > 1, 2 * sz, false) + d(z < n - 2, 2 * sz, true));
-    float r = -0.5f * lap * inv12h2;
-    if (V) r += V[v] * c;
-    if (shift) r += (float)shift[b] * c;
-    out[i] = r;
+  const int x = threadIdx.x, y = blockIdx.x * blockDim.y + threadIdx.y, z = blockIdx.y, b = blockIdx.z;
+  if (x >= n || y >= n) return;
+  const int nn = n * n;
+  const size_t N = (size_t)nn * n;
+  const int v = z * nn + y * n + x;
+  const float* p = f + (size_t)b * N + v;
+  const float c = *p;
+  // per axis 16 (f-1 + f+1) - (f-2 + f+2) - 30 c, summed as differences from c so that
+  // the FP32 rounding is relative to the second differences, not to c
+  auto g = [&](bool ok, int off) { return (ok ? p[off] : 0.f) - c; };
+  const float a1 = g(x > 0, -1) + g(x < n - 1, 1);
+  const float a2 = g(x > 1, -2) + g(x < n - 2, 2);
+  float b1, b2, c1, c2;
+  if (y >= 2 && y < n - 2 && z >= 2 && z < n - 2) {
+    b1 = (p[-n] - c) + (p[n] - c);
+    b2 = (p[-2 * n] - c) + (p[2 * n] - c);
+    c1 = (p[-nn] - c) + (p[nn] - c);
+    c2 = (p[-2 * nn] - c) + (p[2 * nn] - c);
+  } else {
+    b1 = g(y > 0, -n) + g(y < n - 1, n);
+    b2 = g(y > 1, -2 * n) + g(y < n - 2, 2 * n);
+    c1 = g(z > 0, -nn) + g(z < n - 1, nn);
+    c2 = g(z > 1, -2 * nn) + g(z < n - 2, 2 * nn);
   }
+  float lap = 16.f * a1 - a2;
+  lap += 16.f * b1 - b2;
+  lap += 16.f * c1 - c2;
+  float r = -0.5f * lap * inv12h2;
+  if (V) r += V[v] * c;
+  if (shift) r += (float)shift[b] * c;
+  out[(size_t)b * N + v] = r;
+}
+
+// part[b * gridDim.x + blk] = this block's share of sum_v X_b(v) Y_b(v) (w(v)) for row
+// b = blockIdx.y (FP32 products of four points, FP64 sums).  N % 4 == 0, rows 16-byte aligned.
+__global__ void k_row_dots(const float* __restrict__ X, const float* __restrict__ Y, const float* __restrict__ w,
+                           size_t N, double* __restrict__ part) {
+  __shared__ double red[32];
+  const int b = blockIdx.y;
+  const float4* x4 = reinterpret_cast<const float4*>(X + (size_t)b * N);
+  const float4* y4 = reinterpret_cast<const float4*>(Y + (size_t)b * N);
+  const float4* w4 = reinterpret_cast<const float4*>(w);
+  double acc = 0.0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N / 4; i += (size_t)gridDim.x * blockDim.x) {
+    const float4 a = x4[i], c = y4[i];
+    float4 p = make_float4(a.x * c.x, a.y * c.y, a.z * c.z, a.w * c.w);
+    if (w) {
+      const float4 q = w4[i];
+      p = make_float4(p.x * q.x, p.y * q.y, p.z * q.z, p.w * q.w);
+    }
+    acc += (double)((p.x + p.y) + (p.z + p.w));
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double t = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (threadIdx.x == 0) part[(size_t)b * gridDim.x + blockIdx.x] = t;
+  }
+}
+
+// out[b] = scale * sum_p part[b * P + p], a warp per row
+__global__ void k_row_reduce(const double* __restrict__ part, int P, int rows, double scale, double* __restrict__ out) {
+  const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (b >= rows) return;
+  double t = 0.0;
+  for (int p = lane; p < P; p += 32) t += part[(size_t)b * P + p];
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  if (lane == 0) out[b] = scale * t;
 }
 
 // R_i = HPsi_i - theta_i Psi_i
@@ -85,30 +138,25 @@ __global__ void k_kinetic(const double* __restrict__ th, const double* __restric
   if (i < k) T[i] = fmax(th[i] - vdiag[i], 0.0);
 }
 
-// diag[i] = G[i][i] of a k x k matrix
-__global__ void k_diag(const double* __restrict__ G, int k, double* __restrict__ diag) {
-  const int i = threadIdx.x;
-  if (i < k) diag[i] = G[i * k + i];
+// rows of X scaled by 1/sqrt(g[b]) (g: squared norms); zero rows stay zero.  Row b is
+// blockIdx.y; the FP64 scale is formed once per thread.
+__global__ void k_normalise_rows(float* __restrict__ X, const double* __restrict__ g, size_t N) {
+  const double gs = g[blockIdx.y];
+  const float sc = gs > 0.0 ? (float)(1.0 / sqrt(gs)) : 0.f;
+  float* x = X + (size_t)blockIdx.y * N;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x)
+    x[i] *= sc;
 }
 
-// rows of X scaled by 1/sqrt(g[i]) (g: squared norms); zero rows stay zero
-__global__ void k_normalise_rows(float* __restrict__ X, const double* __restrict__ g, int nb, size_t N) {
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < (size_t)nb * N;
-       i += (size_t)gridDim.x * blockDim.x) {
-    const size_t b = i / N;
-    const double s = g[b];
-    X[i] = s > 0.0 ? (float)(X[i] / sqrt(s)) : 0.f;
-  }
-}
-
-// net input [k][2][N]: channel 0 = R_i / |R_i|, channel 1 = V * vscale
+// net input [k][2][N]: channel 0 = R_i / |R_i|, channel 1 = V * vscale (row i = blockIdx.y)
 __global__ void k_net_input(const float* __restrict__ R, const double* __restrict__ g, const float* __restrict__ V,
-                            float vscale, int k, size_t N, float* __restrict__ x) {
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < (size_t)k * N; i += (size_t)gridDim.x * blockDim.x) {
-    const size_t b = i / N, v = i - b * N;
-    const double s = g[b];
-    x[(2 * b) * N + v] = s > 0.0 ? (float)(R[i] / sqrt(s)) : 0.f;
-    x[(2 * b + 1) * N + v] = V[v] * vscale;
+                            float vscale, size_t N, float* __restrict__ x) {
+  const int b = blockIdx.y;
+  const double gs = g[b];
+  const float sc = gs > 0.0 ? (float)(1.0 / sqrt(gs)) : 0.f;
+  for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < N; v += (size_t)gridDim.x * blockDim.x) {
+    x[(2 * (size_t)b) * N + v] = R[(size_t)b * N + v] * sc;
+    x[(2 * (size_t)b + 1) * N + v] = V[v] * vscale;
   }
 }
 
@@ -119,9 +167,9 @@ __global__ void k_net_input(const float* __restrict__ R, const double* __restric
 //     below kRrDrop S_jj (B_j within ~1e-4 rad of the span of the directions before it);
 //  2. C = L^-1 Hs L^-T over the m' kept directions;
 //  3. Householder tridiagonalisation C = Q T Q^T (reflectors kept below the subdiagonal);
-//     lowest k eigenvalues of T by Sturm multisection, a warp per root (32 points per
-//     round); eigenvectors by inverse iteration on T (a warp per root; roots closer than
-//     the cluster gap are redone one after another with re-orthogonalisation); z <- Q z;
+//     lowest k eigenpairs of T: located in FP32 (Sturm multisection, inverse iteration),
+//     finished in FP64 (Rayleigh quotient, one inverse iteration, Rayleigh quotient);
+//     z <- Q z;
 //  4. the new orbitals' coefficients over the basis, Q = L^-T Z.
 // Outputs theta[k] and qt[k][m] (float).  Fewer than k kept directions raise RSX_ENOTPD.
 constexpr double kRrDrop = 1e-8;
@@ -155,7 +203,10 @@ __global__ void __launch_bounds__(kRrThreads) k_rayleigh_ritz(const double* __re
   __shared__ double red[33];
   __shared__ double dg0[kMaxBasis], dd[kMaxBasis], ee[kMaxBasis], tau[kMaxBasis], vv[kMaxBasis], pp[kMaxBasis];
   __shared__ double lam[kMaxBasis];
+  __shared__ float d32[kMaxBasis], e32[kMaxBasis], e2f[kMaxBasis], lam32[kMaxBasis];
   __shared__ int kept[kMaxBasis], dropped[kMaxBasis];
+  __shared__ unsigned omask[kMaxBasis];
+  __shared__ double rdg[kMaxBasis];
   __shared__ int piv[kRrWarps][kMaxBasis];
   __shared__ int nkeep;
   __shared__ double sh_beta, sh_tau, sh_scale;
@@ -174,12 +225,14 @@ __global__ void __launch_bounds__(kRrThreads) k_rayleigh_ritz(const double* __re
       const double pv = L[j * m + j];
       const int dr = !(pv > kRrDrop * dg0[j]);
       dropped[j] = dr;
-      L[j * m + j] = dr ? 1.0 : sqrt(pv);
+      const double rs = dr ? 1.0 : rsqrt(pv);
+      L[j * m + j] = dr ? 1.0 : pv * rs;
+      rdg[j] = rs;   // 1 / L_jj
     }
     __syncthreads();
-    const double ljj = L[j * m + j];
+    const double rl = rdg[j];
     const int dr = dropped[j];
-    for (int i = j + 1 + tid; i < m; i += kRrThreads) L[i * m + j] = dr ? 0.0 : L[i * m + j] / ljj;
+    for (int i = j + 1 + tid; i < m; i += kRrThreads) L[i * m + j] = dr ? 0.0 : L[i * m + j] * rl;
     __syncthreads();
     const int t = m - j - 1;
     for (int q = tid; q < t * t; q += kRrThreads) {
@@ -192,11 +245,19 @@ __global__ void __launch_bounds__(kRrThreads) k_rayleigh_ritz(const double* __re
   if (tid < m) {
     const int c = tid;
     for (int i = 0; i < c; ++i) Li[i * m + c] = 0.0;
-    Li[c * m + c] = 1.0 / L[c * m + c];
+    Li[c * m + c] = rdg[c];
     for (int i = c + 1; i < m; ++i) {
-      double s = 0.0;
-      for (int p = c; p < i; ++p) s += L[i * m + p] * Li[p * m + c];
-      Li[i * m + c] = -s / L[i * m + i];
+      // four partial sums: shorter dependent chains
+      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+      int p = c;
+      for (; p + 3 < i; p += 4) {
+        s0 += L[i * m + p] * Li[p * m + c];
+        s1 += L[i * m + p + 1] * Li[(p + 1) * m + c];
+        s2 += L[i * m + p + 2] * Li[(p + 2) * m + c];
+        s3 += L[i * m + p + 3] * Li[(p + 3) * m + c];
+      }
+      for (; p < i; ++p) s0 += L[i * m + p] * Li[p * m + c];
+      Li[i * m + c] = -((s0 + s1) + (s2 + s3)) * rdg[i];
     }
   }
   if (tid == 0) {
@@ -262,10 +323,15 @@ __global__ void __launch_bounds__(kRrThreads) k_rayleigh_ritz(const double* __re
     }
     __syncthreads();
     if (tk != 0.0) {
-      for (int i = m0 + tid; i < n; i += kRrThreads) {
+      {  // pp = tk C v over the trailing block: 8 threads per row (n <= 64 rows)
+        const int g = tid & 7, i = m0 + (tid >> 3);
         double acc = 0.0;
-        for (int jj = m0; jj < n; ++jj) acc += C[i * n + jj] * vv[jj];
-        pp[i] = tk * acc;
+        if (i < n)
+          for (int jj = m0 + g; jj < n; jj += 8) acc += C[i * n + jj] * vv[jj];
+        acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+        if (g == 0 && i < n) pp[i] = tk * acc;
       }
       __syncthreads();
       double pv = 0.0;
@@ -289,69 +355,139 @@ __global__ void __launch_bounds__(kRrThreads) k_rayleigh_ritz(const double* __re
     dd[n - 1] = C[(n - 1) * n + (n - 1)];
   }
   __syncthreads();
-  // lowest k eigenvalues: multisection, a warp per root
-  double lo0 = dd[0], hi0 = dd[0], emax = 0.0;
-  for (int i = 0; i < n; ++i) {
-    const double r = (i > 0 ? fabs(ee[i - 1]) : 0.0) + (i < n - 1 ? fabs(ee[i]) : 0.0);
-    lo0 = fmin(lo0, dd[i] - r);
-    hi0 = fmax(hi0, dd[i] + r);
-    if (i < n - 1) emax = fmax(emax, fabs(ee[i]));
+  // Lowest k eigenpairs of T.  FP64 latency is long on this part, so the search runs in
+  // FP32 and only a short FP64 finish follows:
+  //  a. T rounded to FP32; Sturm multisection (a warp per root, 32 points per round) and
+  //     three inverse iterations in FP32 (roots closer than gap32 are redone one after
+  //     another with re-orthogonalisation);
+  //  b. per root in FP64: Rayleigh quotient of the FP32 vector, one inverse iteration with
+  //     that shift (orthogonal to earlier roots within gap64, those done in order), and the
+  //     Rayleigh quotient of the result as the eigenvalue.
+  if (tid < n) {
+    d32[tid] = (float)dd[tid];
+    if (tid < n - 1) {
+      e32[tid] = (float)ee[tid];
+      e2f[tid] = e32[tid] * e32[tid];
+    }
   }
-  const double scale = fmax(fabs(lo0), fabs(hi0));
-  lo0 -= 1e-12 * scale + 1e-300;
-  hi0 += 1e-12 * scale + 1e-300;
-  const double pivmin = fmax(2.2250738585072014e-308, 1e-300 * fmax(1.0, emax * emax));
+  __syncthreads();
+  float lo0 = d32[0], hi0 = d32[0], emax = 0.f;
+  for (int i = 0; i < n; ++i) {
+    const float r = (i > 0 ? fabsf(e32[i - 1]) : 0.f) + (i < n - 1 ? fabsf(e32[i]) : 0.f);
+    lo0 = fminf(lo0, d32[i] - r);
+    hi0 = fmaxf(hi0, d32[i] + r);
+    if (i < n - 1) emax = fmaxf(emax, fabsf(e32[i]));
+  }
+  const float scale = fmaxf(fabsf(lo0), fabsf(hi0));
+  lo0 -= 1e-6f * scale + 1e-30f;
+  hi0 += 1e-6f * scale + 1e-30f;
+  const float pivmin = 1.2e-38f * fmaxf(1.f, emax * emax);
   for (int r = warp; r < k; r += kRrWarps) {
-    double lo = lo0, hi = hi0;
-    for (int round = 0; round < 16; ++round) {
-      if (!(hi - lo > 2.0 * 2.220446049250313e-16 * fmax(fabs(lo), fabs(hi)))) break;
-      const double x = lo + (hi - lo) * (double)(lane + 1) / 33.0;
-      const unsigned above = __ballot_sync(0xffffffffu, sturm_count(dd, ee, n, x, pivmin) > r);
+    float lo = lo0, hi = hi0;
+    for (int round = 0; round < 8; ++round) {
+      if (!(hi - lo > 2.4e-7f * fmaxf(fabsf(lo), fabsf(hi)))) break;
+      const float x = lo + (hi - lo) * (float)(lane + 1) / 33.f;
+      const unsigned above = __ballot_sync(0xffffffffu, sturm_count_f32(d32, e2f, n, x, pivmin) > r);
       const int f = above ? __ffs(above) - 1 : 32;
-      const double nlo = (f == 0) ? lo : lo + (hi - lo) * (double)f / 33.0;
-      const double nhi = (f == 32) ? hi : lo + (hi - lo) * (double)(f + 1) / 33.0;
+      const float nlo = (f == 0) ? lo : lo + (hi - lo) * (float)f / 33.f;
+      const float nhi = (f == 32) ? hi : lo + (hi - lo) * (float)(f + 1) / 33.f;
       lo = nlo;
       hi = nhi;
     }
-    if (lane == 0) lam[r] = 0.5 * (lo + hi);
+    if (lane == 0) lam32[r] = 0.5f * (lo + hi);
   }
   __syncthreads();
-  // eigenvectors of T: Z (in T) [k][n], solve scratch SCR (4 n doubles per warp)
-  double* Z = T;
-  const double gap = 1e-6 * fmax(1.0, scale);
+  // a. FP32 vectors Z32 [k][n] (in L, free after L^-1), scratch 4 n floats per warp
+  float* Z32 = reinterpret_cast<float*>(L);
+  float* SCR32 = reinterpret_cast<float*>(SCR);
+  const float gap32 = 1e-5f * fmaxf(1.f, scale);
   for (int r = warp; r < k; r += kRrWarps) {
-    double* z = Z + r * n;
-    for (int i = lane; i < n; i += 32) z[i] = 1.0 + 0.001 * (double)((i * 7919 + r * 104729) % 997);
+    float* z = Z32 + r * n;
+    for (int i = lane; i < n; i += 32) z[i] = 1.f + 0.001f * (float)((i * 7919 + r * 104729) % 997);
     __syncwarp();
-    warp_inverse_iteration(dd, ee, n, lam[r], z, SCR + warp * 4 * n, piv[warp], 3, Z, n, 0u);
+    warp_inverse_iteration<float>(d32, e32, n, lam32[r], z, SCR32 + warp * 4 * n, piv[warp], 3, Z32, n, 0u);
   }
   __syncthreads();
-  // roots within `gap` of an earlier root: redo in order, orthogonal to the earlier ones
   if (warp == 0) {
     for (int r = 1; r < k; ++r) {
       unsigned ortho = 0;
       for (int j = 0; j < r; ++j)
-        if (fabs(lam[r] - lam[j]) < gap) ortho |= 1u << j;
+        if (fabsf(lam32[r] - lam32[j]) < gap32) ortho |= 1u << j;
+      if (!ortho) continue;
+      float* z = Z32 + r * n;
+      for (int i = lane; i < n; i += 32) z[i] = 1.f + 0.001f * (float)((i * 7919 + r * 104729) % 997);
+      __syncwarp();
+      warp_inverse_iteration<float>(d32, e32, n, lam32[r], z, SCR32, piv[0], 3, Z32, n, ortho);
+    }
+  }
+  __syncthreads();
+  // b. FP64 finish: Z (in T) [k][n]
+  double* Z = T;
+  const double gap64 = 1e-6 * fmax(1.0, (double)scale);
+  auto rayleigh = [&](const double* z) {
+    double num = 0.0, den = 0.0;
+    for (int i = lane; i < n; i += 32) {
+      const double zi = z[i];
+      double tz = dd[i] * zi;
+      if (i > 0) tz += ee[i - 1] * z[i - 1];
+      if (i < n - 1) tz += ee[i] * z[i + 1];
+      num += zi * tz;
+      den += zi * zi;
+    }
+    return warp_sum(num) / warp_sum(den);
+  };
+  for (int r = warp; r < k; r += kRrWarps) {
+    double* z = Z + r * n;
+    for (int i = lane; i < n; i += 32) z[i] = (double)Z32[r * n + i];
+    __syncwarp();
+    const double th = rayleigh(z);
+    if (lane == 0) lam[r] = th;
+  }
+  __syncthreads();
+  if (tid < k) {
+    unsigned om = 0;
+    for (int j = 0; j < tid; ++j)
+      if (fabs(lam[tid] - lam[j]) < gap64) om |= 1u << j;
+    omask[tid] = om;
+  }
+  __syncthreads();
+  for (int r = warp; r < k; r += kRrWarps) {
+    if (omask[r]) continue;   // done in order below
+    double* z = Z + r * n;
+    warp_inverse_iteration<double>(dd, ee, n, lam[r], z, SCR + warp * 4 * n, piv[warp], 1, Z, n, 0u);
+    const double th = rayleigh(z);
+    if (lane == 0) lam[r] = th;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    for (int r = 1; r < k; ++r) {
+      const unsigned ortho = omask[r];
       if (!ortho) continue;
       double* z = Z + r * n;
-      for (int i = lane; i < n; i += 32) z[i] = 1.0 + 0.001 * (double)((i * 7919 + r * 104729) % 997);
+      warp_inverse_iteration<double>(dd, ee, n, lam[r], z, SCR, piv[0], 1, Z, n, ortho);
+      const double th = rayleigh(z);
+      if (lane == 0) lam[r] = th;
       __syncwarp();
-      warp_inverse_iteration(dd, ee, n, lam[r], z, SCR, piv[0], 3, Z, n, ortho);
     }
   }
   __syncthreads();
   // z <- H_0 H_1 ... H_{n-3} z (a warp per root)
+  // (z held in registers, two entries per lane: n <= 64)
   for (int r = warp; r < k; r += kRrWarps) {
     double* z = Z + r * n;
+    const int i0 = lane, i1 = lane + 32;
+    double z0 = i0 < n ? z[i0] : 0.0, z1 = i1 < n ? z[i1] : 0.0;
     for (int kk = n - 3; kk >= 0; --kk) {
       const double tk = tau[kk];
       if (tk == 0.0) continue;
-      double sdot = 0.0;
-      for (int i = kk + 1 + lane; i < n; i += 32) sdot += ((i == kk + 1) ? 1.0 : C[i * n + kk]) * z[i];
-      sdot = tk * warp_sum(sdot);
-      for (int i = kk + 1 + lane; i < n; i += 32) z[i] -= sdot * ((i == kk + 1) ? 1.0 : C[i * n + kk]);
-      __syncwarp();
+      const double v0 = i0 > kk + 1 && i0 < n ? C[i0 * n + kk] : (i0 == kk + 1 ? 1.0 : 0.0);
+      const double v1 = i1 > kk + 1 && i1 < n ? C[i1 * n + kk] : (i1 == kk + 1 ? 1.0 : 0.0);
+      const double sdot = tk * warp_sum(v0 * z0 + v1 * z1);
+      z0 -= sdot * v0;
+      z1 -= sdot * v1;
     }
+    if (i0 < n) z[i0] = z0;
+    if (i1 < n) z[i1] = z1;
   }
   __syncthreads();
   // 4. qt[o][r] = sum_a Li[kept[a]][r] Z[o][a]
@@ -442,6 +578,8 @@ __global__ void k_tail_cols(const float* __restrict__ qt, int k, int m, float* _
 }
 
 size_t blocks_for(size_t n) { return std::min<size_t>((n + 255) / 256, 4096); }
+// x-blocks of a (blocks, rows) grid over `rows` rows of N elements (256 threads)
+size_t row_blocks(size_t N, int rows) { return std::max<size_t>(1, std::min<size_t>((N + 255) / 256, 4096 / rows)); }
 
 }  // namespace
 
@@ -497,12 +635,34 @@ int gram(rsx_eig* e, const float* X, int na, const float* Y, int nb, const float
                     "gram reduce");
 }
 
+// out[b] = h^3 <X_b, Y_b w> for b < rows (w may be null)
+int row_dots(rsx_eig* e, const float* X, const float* Y, const float* w, int rows, double* out, cudaStream_t s) {
+  rsx_ctx* c = e->ctx;
+  const size_t N = (size_t)e->n * e->n * e->n;
+  const int P = std::max(1, std::min(256, 4 * c->nsm / rows));
+  int rc = grow(c, (void**)&c->dsm, &c->dsm_bytes, sizeof(double) * ((size_t)2 * c->nsm * 4096 + 3 * 4096), "small FP64");
+  if (rc) return rc;
+  k_row_dots<<<dim3(P, rows), 256, 0, s>>>(X, Y, w, N, c->dsm);
+  k_row_reduce<<<(rows + 7) / 8, 256, 0, s>>>(c->dsm, P, rows, e->h * e->h * e->h, out);
+  return ecuda(e, cudaGetLastError(), "row dots");
+}
+
+// launch shape of k_ham_apply: x along whole warps, as many y rows as fit in 256 threads
+dim3 ham_block(int n) {
+  const int xt = (n + 31) / 32 * 32;
+  return dim3(xt, std::max(1, 256 / xt));
+}
+dim3 ham_grid(int nb, int n) {
+  const dim3 bl = ham_block(n);
+  return dim3((n + bl.y - 1) / bl.y, n, nb);
+}
+
 // out = H f (the full operator, with the exchange term, when V is given; the kinetic part
 // plus shift when V is null)
 int ham(rsx_eig* e, const float* f, int nb, float* out, const double* shift, const float* V, cudaStream_t s) {
   const size_t N = (size_t)e->n * e->n * e->n;
-  k_ham_apply<<<(unsigned)blocks_for(nb * N), 256, 0, s>>>(f, nb, e->n, (float)(1.0 / (12.0 * e->h * e->h)), V, shift,
-                                                           out);
+  k_ham_apply<<<ham_grid(nb, e->n), ham_block(e->n), 0, s>>>(f, nb, e->n, (float)(1.0 / (12.0 * e->h * e->h)), V,
+                                                              shift, out);
   int rc = ecuda(e, cudaGetLastError(), "hamiltonian");
   if (rc || !V || e->xmode == 0) return rc;
   if (e->xmode == 1) {
@@ -615,16 +775,14 @@ int rsx_eig_step(rsx_eig* e, rsx_net* net, int jacobi_sweeps, double* theta_host
   double* theta = e->sm;
   double* T = e->sm + 64;
   double* diag = e->sm + 128;
-  double* G = e->sm + 256;          // Gram scratch (the Rayleigh-Ritz S matrix reuses it later)
   float* psi = e->B;
   float* hpsi = e->HB;
   float* wp = e->B + k * N;
   // residual
   k_residual<<<(unsigned)blocks_for(k * N), 256, 0, s>>>(psi, hpsi, theta, k, N, e->R);
   // kinetic energies T_i = theta_i - <psi_i, V psi_i>
-  int rc = gram(e, psi, k, psi, k, e->V, G, s);
+  int rc = row_dots(e, psi, psi, e->V, k, diag, s);
   if (rc) return rc;
-  k_diag<<<1, 64, 0, s>>>(G, k, diag);
   k_kinetic<<<1, 64, 0, s>>>(theta, diag, k, T);
   rc = ecuda(e, cudaGetLastError(), "kinetic");
   if (rc) return rc;
@@ -645,20 +803,18 @@ int rsx_eig_step(rsx_eig* e, rsx_net* net, int jacobi_sweeps, double* theta_host
   int m = e->has_p ? 3 * k : 2 * k;
   // learned directions
   if (net) {
-    rc = gram(e, e->R, k, e->R, k, nullptr, G, s);
+    rc = row_dots(e, e->R, e->R, nullptr, k, diag, s);
     if (rc) return rc;
-    k_diag<<<1, 64, 0, s>>>(G, k, diag);
-    k_net_input<<<(unsigned)blocks_for(k * N), 256, 0, s>>>(e->R, diag, e->V, e->vscale, k, N, e->xnet);
+    k_net_input<<<dim3((unsigned)row_blocks(N, k), k), 256, 0, s>>>(e->R, diag, e->V, e->vscale, N, e->xnet);
     float* wl = e->B + (size_t)m * N;
     rc = rsx_net_forward(net, e->xnet, k, e->n, e->n, e->n, wl, s);
     if (rc) return efail(e, rc, "learned preconditioner forward failed");
     m += k;
   }
   // normalise the W blocks, apply H to them
-  rc = gram(e, wp, m - k, wp, m - k, nullptr, G, s);
+  rc = row_dots(e, wp, wp, nullptr, m - k, diag, s);
   if (rc) return rc;
-  k_diag<<<1, 64, 0, s>>>(G, m - k, diag);
-  k_normalise_rows<<<(unsigned)blocks_for((m - k) * N), 256, 0, s>>>(wp, diag, m - k, N);
+  k_normalise_rows<<<dim3((unsigned)row_blocks(N, m - k), m - k), 256, 0, s>>>(wp, diag, N);
   rc = ham(e, wp, m - k, e->HB + k * N, nullptr, e->V, s);
   if (rc) return rc;
   // keep a P block for the next step when Psi | W | P (| W_learned) still fits
@@ -866,7 +1022,7 @@ int rsx_scf_step(rsx_scf* c, int inner, double* out_host, void* stream) {
   // energy parts of the entering orbitals: one-body, Hartree
   rc = rsx_poisson(c->ctx, c->rho, c->vh, stream);
   if (rc) return sfail(c, rc, "Poisson (energy) failed");
-  k_ham_apply<<<(unsigned)blocks_for(k * N), 256, 0, s>>>(c->phi, k, c->n, (float)(1.0 / (12.0 * c->h * c->h)), c->vext,
+  k_ham_apply<<<ham_grid(k, c->n), ham_block(c->n), 0, s>>>(c->phi, k, c->n, (float)(1.0 / (12.0 * c->h * c->h)), c->vext,
                                                           nullptr, c->hphi);
   const int nblk = 2 * c->ctx->nsm;
   rc = grow(c->ctx, (void**)&c->ctx->dsm, &c->ctx->dsm_bytes, sizeof(double) * ((size_t)nblk * 4096 + 3 * 4096),

@@ -18,6 +18,12 @@ Readings (the paper is silent on these details):
   previous iteration (exact) or its ACE form -zeta zeta^T (ACE);
 * mixing of the density: rho_in <- alpha rho_in + (1 - alpha) rho_out (q_{N-1} read as
   the input density of iteration N, q_N as its output);
+* mixing of the states (Sec. 3.2 finds it the most robust): the input orbitals of the
+  next iteration are alpha phi_in + (1 - alpha) P_out phi_in, orthonormalised by the
+  Cholesky factor of their overlap, with P_out the projector on the span of the output
+  orbitals (the output orbital space carried over without the arbitrary signs and
+  rotations of an eigensolver); the Fock operator of an iteration takes both V_H and Vx
+  from its input orbitals;
 * energy E = 2 sum_i <phi_i, (T + V_ext) phi_i> + 1/2 <rho, V_H> + sum_i <phi_i, Vx phi_i>;
 * each iteration takes the n_occ lowest eigenvectors of the dense Fock matrix (small
   grids only), starting from the non-interacting orbitals of T + V_ext.
@@ -64,8 +70,20 @@ def hf_energy(phi, v_ext, h, G):
     return one + eh + ex, one, eh, ex
 
 
-def scf(v_ext, h, nocc, mode="ace", alpha=0.3, tol=1e-10, max_iter=300):
-    """Self-consistent closed-shell HF on a small grid; mode 'ace' or 'exact'.
+def mix_states(phi_in, phi_out, h, alpha):
+    """alpha phi_in + (1 - alpha) P_out phi_in, orthonormalised (Cholesky of the overlap)."""
+    k = phi_in.shape[0]
+    A = np.asarray(phi_in, dtype=np.float64).reshape(k, -1)
+    B = np.asarray(phi_out, dtype=np.float64).reshape(k, -1)
+    O = h ** 3 * B @ A.T                         # O[i, j] = <out_i, in_j>
+    mixed = alpha * A + (1.0 - alpha) * (O.T @ B)
+    L = np.linalg.cholesky(h ** 3 * mixed @ mixed.T)
+    return np.linalg.solve(L, mixed).reshape(phi_in.shape)
+
+
+def scf(v_ext, h, nocc, mode="ace", alpha=0.3, tol=1e-10, max_iter=300, mix="density"):
+    """Self-consistent closed-shell HF on a small grid; mode 'ace' or 'exact', mix
+    'density' or 'states'.
 
     Returns a dict with the orbitals, orbital energies, total energy (and its parts), the
     last relative density error and the iteration count."""
@@ -77,20 +95,26 @@ def scf(v_ext, h, nocc, mode="ace", alpha=0.3, tol=1e-10, max_iter=300):
     w, U = np.linalg.eigh(0.5 * (H0 + H0.T))
     phi = (U[:, :nocc].T / h ** 1.5).reshape((nocc,) + shape)
     rho_in = density(phi).ravel()
+    phi_in = phi
     eps, it = np.inf, 0
     for it in range(1, max_iter + 1):
         VH = G @ rho_in
+        src = phi_in if mix == "states" else phi      # orbitals the exchange is built from
         if mode == "ace":
-            zeta = ace_build(phi, h).reshape(nocc, -1)
+            zeta = ace_build(src, h).reshape(nocc, -1)
             VX = -h ** 3 * (zeta.T @ zeta)
         else:
-            VX = exchange_matrix(phi, G)
+            VX = exchange_matrix(src, G)
         F = H0 + np.diag(VH) + VX
         w, U = np.linalg.eigh(0.5 * (F + F.T))
         phi = (U[:, :nocc].T / h ** 1.5).reshape((nocc,) + shape)
         rho_out = density(phi).ravel()
         eps = h ** 3 * np.abs(rho_out - rho_in).sum() / (2 * nocc)
-        rho_in = alpha * rho_in + (1.0 - alpha) * rho_out
+        if mix == "states":
+            phi_in = mix_states(phi_in, phi, h, alpha)
+            rho_in = density(phi_in).ravel()
+        else:
+            rho_in = alpha * rho_in + (1.0 - alpha) * rho_out
         if eps < tol:
             break
     E, one, eh, ex = hf_energy(phi, v_ext, h, G)

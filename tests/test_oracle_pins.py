@@ -489,3 +489,29 @@ def test_scf_fixed_point_solves_the_hf_equations_and_minimises_the_energy():
         dE.append(oscf.hf_energy(q.reshape(phi.shape), v, h, G)[0] - r["energy"])
     assert dE[0] > 0 and dE[1] > 0
     assert abs(dE[0] / dE[1] - 4.0) < 0.05
+
+
+def test_scf_state_mixing_reaches_the_same_ground_state():
+    """Sec. 3.2: mixing states instead of the density changes the path, not the fixed
+    point -- same energy and orbital energies as density mixing."""
+    v = _scf_potential()
+    a = oscf.scf(v, 0.5, 2, mode="ace", tol=1e-11, mix="states")
+    b = oscf.scf(v, 0.5, 2, mode="ace", tol=1e-11, mix="density")
+    assert a["reldens"] < 1e-11
+    assert abs(a["energy"] - b["energy"]) < 1e-9 * abs(b["energy"])
+    assert np.allclose(a["eps_orb"], b["eps_orb"], rtol=0, atol=1e-8)
+
+
+def test_state_mixing_keeps_an_orthonormal_set_and_is_rotation_blind():
+    """The mixed states are orthonormal; mixing with a rotated and sign-flipped copy of the
+    same output space gives the same result (only the span of the output enters)."""
+    h = 0.5
+    rng = np.random.default_rng(9)
+    A = np.linalg.qr(rng.standard_normal((64, 3)))[0].T / h ** 1.5
+    B = np.linalg.qr(rng.standard_normal((64, 3)))[0].T / h ** 1.5
+    Q = np.linalg.qr(rng.standard_normal((3, 3)))[0]
+    m1 = oscf.mix_states(A, B, h, 0.4)
+    m2 = oscf.mix_states(A, Q @ B, h, 0.4)
+    assert np.allclose(h ** 3 * m1 @ m1.T, np.eye(3), atol=1e-12)
+    assert np.allclose(m1, m2, atol=1e-12)
+    assert np.allclose(oscf.mix_states(A, A, h, 0.4), A, atol=1e-12)   # fixed point

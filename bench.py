@@ -622,32 +622,42 @@ def precond_bench(args, dev, local_rank):
     # evaluation on an unseen system: a tightly converged reference energy, then the
     # iterations and wall time each method needs to come within 1e-6 Ha of it
     ref = precond.solve(Vs[4], h, psi0s[4], nb, net=net, tol=1e-11, vscale=vscale, max_iter=2000)
-    e_ref = ref["energy"]
     plain = precond.solve(Vs[4], h, psi0s[4], nb, tol=1e-9, vscale=vscale, max_iter=1500)
     learned = precond.solve(Vs[4], h, psi0s[4], nb, net=net, tol=1e-9, vscale=vscale, max_iter=1500)
     net.close()
+    # reference: the lowest energy any of the three runs settles at (Rayleigh-Ritz energies
+    # are variational; the FP32 vectors leave a ~1e-6 Ha floor that differs run to run)
+    e_ref = min(ref["energy"], plain["energy"], learned["energy"])
     ip, tp = precond.time_to_target(plain, e_ref)
     il, tl = precond.time_to_target(learned, e_ref)
+    ip5, tp5 = precond.time_to_target(plain, e_ref, tol=1e-5)
+    il5, tl5 = precond.time_to_target(learned, e_ref, tol=1e-5)
     return {"workload": f"{n}^3 box at h=0.2, 16 bands of H = -1/2 Lap(FD4) + V (4 model atoms, Z=4); "
                         "training pairs from plain runs on 4 systems, evaluation on a 5th",
             "pairs": int(target), "epochs": args.precond_epochs, "loss_first_last": [losses[0], losses[-1]],
             "train_s": round(train_s, 2), "plain_train_iters": plain_iters,
-            "reference_energy_ha": e_ref, "target": "E - E_ref < 1e-6 Ha",
+            "reference_energy_ha": e_ref, "target": "E - E_ref < 1e-6 Ha (and 1e-5 Ha)",
             "plain": {"iters_to_target": ip, "time_to_target_s": None if tp is None else round(tp, 3),
-                      "final_energy_ha": plain["energy"]},
+                      "iters_to_1e-5": ip5, "time_to_1e-5_s": None if tp5 is None else round(tp5, 3),
+                      "final_energy_ha": plain["energy"], "min_energy_ha": min(plain["trace"]),
+                      "iters": plain["iters"]},
             "learned": {"iters_to_target": il, "time_to_target_s": None if tl is None else round(tl, 3),
-                        "final_energy_ha": learned["energy"]},
+                        "iters_to_1e-5": il5, "time_to_1e-5_s": None if tl5 is None else round(tl5, 3),
+                        "final_energy_ha": learned["energy"], "min_energy_ha": min(learned["trace"]),
+                        "iters": learned["iters"]},
+            "reference_runs_ha": {"learned_tight": ref["energy"], "plain": plain["energy"],
+                                  "learned": learned["energy"]},
             "final_energy_diff_ha": abs(learned["energy"] - plain["energy"]),
             "conv_forward_tflops": round(fwd_tflops, 2), "conv_train_step_tflops": round(train_tflops, 2),
             "total_s": round(time.perf_counter() - t_all, 1)}
 
 
-def scf_bench(args, dev, iters=10, inner=2):
+def scf_bench(args, dev, iters=10, inner=2, max_iter=300):
     """Closed-shell HF SCF on a 96^3 box at h = 0.2 with 16 doubly occupied orbitals (8 model
     atoms, Z = 4): wall time per SCF iteration over the first `iters` iterations with the
     exact exchange in every Fock application and with ACE (Sec. 3.1 compares the two the
-    same way), both from the same start; then the ACE cycle continued to a relative
-    density error (Eq. 15) below 1e-6."""
+    same way), both from the same start; then ACE cycles run towards a relative density
+    error (Eq. 15) below 1e-6 with density mixing and with state mixing (Sec. 3.2)."""
     from paper_2405_01522_gb300 import rsx
     n, h, nocc = args.scf_edge, 0.2, 16
     v = torch.from_numpy(inputs.model_potential(n=n, h=h, natoms=8, Z=4.0, rc=0.6, radius=3.0, seed=41)).float().to(dev)
@@ -665,22 +675,31 @@ def scf_bench(args, dev, iters=10, inner=2):
         dt = (time.perf_counter() - t0) / iters
         res[name] = {"s_per_iteration": round(dt, 5), "energy_after_ha": hist[-1]["energy"],
                      "reldens_after": hist[-1]["reldens"], "exchange_ha": hist[-1]["exchange"]}
-        if ace:
-            t1 = time.perf_counter()
-            k = iters + 1
-            while hist[-1]["reldens"] >= 1e-6 and k < 400:
-                hist.append(scf.step(inner=inner))
-                k += 1
-            res["ace_converged"] = {"iterations": k, "reldens": hist[-1]["reldens"], "energy_ha": hist[-1]["energy"],
-                                    "one_body_ha": hist[-1]["one_body"], "hartree_ha": hist[-1]["hartree"],
-                                    "exchange_ha": hist[-1]["exchange"],
-                                    "extra_s": round(time.perf_counter() - t1, 3)}
+        scf.close()
+    res["speedup_ace"] = round(res["exact"]["s_per_iteration"] / res["ace"]["s_per_iteration"], 2)
+    for mix in ("density", "states"):
+        scf = rsx.SCF(ctx, v, nocc, ace=True, alpha=0.3, mix=mix)
+        scf.init(psi0)
+        t0 = time.perf_counter()
+        hist, first = [], {}
+        while len(hist) < max_iter:
+            hist.append(scf.step(inner=inner))
+            r = hist[-1]["reldens"]
+            for tol in (1e-4, 1e-5, 1e-6):
+                if len(hist) > 1 and r < tol and tol not in first:
+                    first[tol] = len(hist)
+            if len(hist) > 1 and r < 1e-6:
+                break
+        last = hist[-1]
+        res[f"ace_{mix}_mixing"] = {
+            "iterations": len(hist), "iterations_to": {f"{t:g}": first.get(t) for t in (1e-4, 1e-5, 1e-6)},
+            "reldens": last["reldens"], "energy_ha": last["energy"], "one_body_ha": last["one_body"],
+            "hartree_ha": last["hartree"], "exchange_ha": last["exchange"], "s": round(time.perf_counter() - t0, 3)}
         scf.close()
     ctx.close()
-    res["speedup_ace"] = round(res["exact"]["s_per_iteration"] / res["ace"]["s_per_iteration"], 2)
-    res["workload"] = (f"{n}^3 box at h=0.2, 16 occupied orbitals (8 model atoms, Z=4), linear density mixing 0.3, "
+    res["workload"] = (f"{n}^3 box at h=0.2, 16 occupied orbitals (8 model atoms, Z=4), mixing parameter 0.3, "
                        f"{inner} block eigensolver steps per SCF iteration; time per iteration averaged over "
-                       f"iterations 2..{iters + 1}")
+                       f"iterations 2..{iters + 1}; convergence runs capped at {max_iter} iterations")
     return res
 
 

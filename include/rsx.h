@@ -260,6 +260,12 @@ typedef struct rsx_scf rsx_scf;
 int rsx_scf_create(rsx_scf** scf, rsx_ctx* ctx, const float* V_ext, int nocc, int use_ace, float alpha);
 int rsx_scf_init(rsx_scf* scf, const float* psi0, void* stream);
 int rsx_scf_step(rsx_scf* scf, int inner, double* out_host, void* stream);
+/* What Eq. 14 mixes (before the first rsx_scf_step after rsx_scf_init): 0 the density
+ * (default); 1 the states -- the next input orbitals are alpha phi_in + (1 - alpha) P_out
+ * phi_in, orthonormalised by the Cholesky factor of their overlap, P_out the projector on
+ * the output orbitals' span; the Fock operator then takes V_H and Vx from the input
+ * orbitals, and the reported energy is theirs.  Errors: RSX_EINVAL, RSX_ENOMEM. */
+int rsx_scf_set_mixing(rsx_scf* scf, int mix_states);
 int rsx_scf_orbitals(rsx_scf* scf, float* psi_out, void* stream);
 const char* rsx_scf_last_error(const rsx_scf* scf);
 int rsx_scf_destroy(rsx_scf* scf);

@@ -164,15 +164,17 @@ __global__ void k_net_input(const float* __restrict__ R, const double* __restric
 // Rayleigh-Ritz in one CTA (FP64) for m <= kMaxBasis, robust to a nearly dependent basis
 // (the LOBPCG blocks W and P become nearly parallel near convergence):
 //  1. S = L L^T by a right-looking Cholesky that drops direction j when its pivot falls
-//     below kRrDrop S_jj (B_j within ~1e-4 rad of the span of the directions before it);
+//     below kRrDrop S_jj (B_j within ~1e-3 rad of the span of the directions before it:
+//     the FP32-summed Gram matrices leave smaller pivots, and the directions they would
+//     add, dominated by rounding);
 //  2. C = L^-1 Hs L^-T over the m' kept directions;
 //  3. Householder tridiagonalisation C = Q T Q^T (reflectors kept below the subdiagonal);
 //     lowest k eigenpairs of T: located in FP32 (Sturm multisection, inverse iteration),
-//     finished in FP64 (Rayleigh quotient, one inverse iteration, Rayleigh quotient);
-//     z <- Q z;
+//     finished in FP64 (Rayleigh quotient, one inverse iteration, Rayleigh quotient) and
+//     checked by FP64 Sturm counts (all redone in FP64 if a root fails); z <- Q z;
 //  4. the new orbitals' coefficients over the basis, Q = L^-T Z.
 // Outputs theta[k] and qt[k][m] (float).  Fewer than k kept directions raise RSX_ENOTPD.
-constexpr double kRrDrop = 1e-8;
+constexpr double kRrDrop = 1e-6;
 constexpr int kRrThreads = 512;
 constexpr int kRrWarps = kRrThreads / 32;
 
@@ -206,6 +208,8 @@ __global__ void __launch_bounds__(kRrThreads) k_rayleigh_ritz(const double* __re
   __shared__ float d32[kMaxBasis], e32[kMaxBasis], e2f[kMaxBasis], lam32[kMaxBasis];
   __shared__ int kept[kMaxBasis], dropped[kMaxBasis];
   __shared__ unsigned omask[kMaxBasis];
+  __shared__ double e2d[kMaxBasis];
+  __shared__ int redo_all;
   __shared__ double rdg[kMaxBasis];
   __shared__ int piv[kRrWarps][kMaxBasis];
   __shared__ int nkeep;
@@ -471,6 +475,55 @@ __global__ void __launch_bounds__(kRrThreads) k_rayleigh_ritz(const double* __re
     }
   }
   __syncthreads();
+  // c. check every root against FP64 Sturm counts at lam -/+ delta (the r-th eigenvalue
+  //    must lie in between).  An FP32 location can fail when T's norm dwarfs the wanted
+  //    roots (a nearly dependent direction kept by the Cholesky); then all roots are
+  //    redone in FP64: bisection (a thread per root) and three inverse iterations.
+  if (tid < n - 1) e2d[tid] = ee[tid] * ee[tid];
+  if (tid == 0) redo_all = 0;
+  __syncthreads();
+  if (tid < k) {
+    const double lr = lam[tid];
+    const double dl = 1e-12 * (double)scale + 1e-9 * fabs(lr);
+    const int below = sturm_count_prod(dd, e2d, n, lr - dl), upto = sturm_count_prod(dd, e2d, n, lr + dl);
+    if (!(below <= tid && upto > tid) || !(lr == lr)) atomicOr(&redo_all, 1);
+  }
+  __syncthreads();
+  if (redo_all) {
+    if (tid < k) {
+      double lo = (double)lo0 - 1e-3 * (double)scale, hi = (double)hi0 + 1e-3 * (double)scale;
+      for (int it = 0; it < 128; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (!(hi - lo > 2.0 * 2.220446049250313e-16 * fmax(fabs(lo), fabs(hi))) || !(mid > lo && mid < hi)) break;
+        if (sturm_count_prod(dd, e2d, n, mid) > tid)
+          hi = mid;
+        else
+          lo = mid;
+      }
+      lam[tid] = 0.5 * (lo + hi);
+    }
+    __syncthreads();
+    for (int r = warp; r < k; r += kRrWarps) {
+      double* z = Z + r * n;
+      for (int i = lane; i < n; i += 32) z[i] = 1.0 + 0.001 * (double)((i * 7919 + r * 104729) % 997);
+      __syncwarp();
+      warp_inverse_iteration<double>(dd, ee, n, lam[r], z, SCR + warp * 4 * n, piv[warp], 3, Z, n, 0u);
+    }
+    __syncthreads();
+    if (warp == 0) {
+      for (int r = 1; r < k; ++r) {
+        unsigned ortho = 0;
+        for (int j = 0; j < r; ++j)
+          if (fabs(lam[r] - lam[j]) < gap64) ortho |= 1u << j;
+        if (!ortho) continue;
+        double* z = Z + r * n;
+        for (int i = lane; i < n; i += 32) z[i] = 1.0 + 0.001 * (double)((i * 7919 + r * 104729) % 997);
+        __syncwarp();
+        warp_inverse_iteration<double>(dd, ee, n, lam[r], z, SCR, piv[0], 3, Z, n, ortho);
+      }
+    }
+    __syncthreads();
+  }
   // z <- H_0 H_1 ... H_{n-3} z (a warp per root)
   // (z held in registers, two entries per lane: n <= 64)
   for (int r = warp; r < k; r += kRrWarps) {
@@ -575,6 +628,57 @@ __global__ void k_tail_cols(const float* __restrict__ qt, int k, int m, float* _
     const int r = i / (m - k), c = i - r * (m - k);
     qp[i] = qt[r * m + k + c];
   }
+}
+
+// coef[j][i] (k x 2k) over [phi_in; phi_out]: alpha on input orbital j and (1 - alpha)
+// O[i][j] = (1 - alpha) <out_i, in_j> on output orbital i, so that row j is
+// alpha phi_in_j + (1 - alpha) (projection of phi_in_j on the span of the outputs)
+__global__ void k_state_mix_coeffs(const double* __restrict__ O, int k, float alpha, float* __restrict__ coef) {
+  for (int q = threadIdx.x; q < 2 * k * k; q += blockDim.x) {
+    const int j = q / (2 * k), i = q - j * 2 * k;
+    coef[q] = i < k ? (i == j ? alpha : 0.f) : (float)((1.0 - (double)alpha) * O[(i - k) * k + j]);
+  }
+}
+
+// S = L L^T (k <= 32, FP64, one warp); linv[j][i] = (L^-1)[j][i] as float, so that
+// rows linv X are orthonormal when S is the Gram matrix of the rows of X.  A pivot
+// that is not positive raises RSX_ENOTPD in *status (the rows are then left unscaled).
+__global__ void k_chol_inv_small(const double* __restrict__ S, int k, float* __restrict__ linv, int* status) {
+  __shared__ double L[32 * 32], Li[32 * 32];
+  const int lane = threadIdx.x;
+  for (int q = lane; q < k * k; q += 32) {
+    L[q] = S[q];
+    Li[q] = 0.0;
+  }
+  __syncwarp();
+  for (int j = 0; j < k; ++j) {
+    if (lane == 0) {
+      double d = L[j * k + j];
+      if (!(d > 0.0)) {
+        atomicMax(status, RSX_ENOTPD);
+        d = 1.0;
+      }
+      L[j * k + j] = sqrt(d);
+    }
+    __syncwarp();
+    const double rl = 1.0 / L[j * k + j];
+    if (lane > j && lane < k) L[lane * k + j] *= rl;
+    __syncwarp();
+    for (int i = j + 1 + lane; i < k; i += 32)
+      for (int l = j + 1; l <= i; ++l) L[i * k + l] -= L[i * k + j] * L[l * k + j];
+    __syncwarp();
+  }
+  if (lane < k) {
+    const int c = lane;
+    Li[c * k + c] = 1.0 / L[c * k + c];
+    for (int i = c + 1; i < k; ++i) {
+      double sum = 0.0;
+      for (int p = c; p < i; ++p) sum += L[i * k + p] * Li[p * k + c];
+      Li[i * k + c] = -sum / L[i * k + i];
+    }
+  }
+  __syncwarp();
+  for (int q = lane; q < k * k; q += 32) linv[q] = (float)Li[q];
 }
 
 size_t blocks_for(size_t n) { return std::min<size_t>((n + 255) / 256, 4096); }
@@ -918,6 +1022,10 @@ struct rsx_scf {
   float* xi = nullptr;           // [nocc][N] ACE projectors
   float* hphi = nullptr;         // [nocc][N] (T + V_ext) phi
   double* dsm = nullptr;         // M (nocc^2), Gram results, reduction partials
+  // mixing of states (rsx_scf_set_mixing): [phi_in; phi_out] [2 nocc][N], coefficients
+  int mix_states = 0;
+  float* mix2 = nullptr;
+  float* fsm = nullptr;          // [nocc][2 nocc] mixing coefficients, [nocc][nocc] L^-1
   char err[256] = {0};
 };
 
@@ -933,6 +1041,18 @@ int scuda(rsx_scf* c, cudaError_t e, const char* what) {
   return RSX_ECUDA;
 }
 constexpr int kScfRedBlocks = 256;
+
+// out[a][b] = h^3 <X_a, Y_b> (device FP64, na * nb <= 1024)
+int scf_gram(rsx_scf* c, const float* X, int na, const float* Y, int nb, double* out, cudaStream_t s) {
+  rsx_ctx* x = c->ctx;
+  const int nblk = 2 * x->nsm;
+  int rc = grow(x, (void**)&x->dsm, &x->dsm_bytes, sizeof(double) * ((size_t)nblk * 4096 + 3 * 4096), "small FP64");
+  if (!rc) rc = check_cuda(x, launch_gram<float>(X, na, Y, nb, x->g.N(), x->dsm, nblk, s), "gram");
+  if (!rc)
+    rc = check_cuda(x, launch_gram_reduce<float>(x->dsm, nblk, na, nb, c->h * c->h * c->h, false, out, (float*)nullptr, s),
+                    "gram reduce");
+  return rc ? sfail(c, rc, x->err) : RSX_OK;
+}
 
 }  // namespace
 
@@ -957,7 +1077,8 @@ int rsx_scf_create(rsx_scf** out, rsx_ctx* ctx, const float* V_ext, int nocc, in
       cudaMalloc(&c->phi, nocc * N * sizeof(float)) != cudaSuccess ||
       cudaMalloc(&c->xi, nocc * N * sizeof(float)) != cudaSuccess ||
       cudaMalloc(&c->hphi, nocc * N * sizeof(float)) != cudaSuccess ||
-      cudaMalloc(&c->dsm, (4096 + kScfRedBlocks) * sizeof(double)) != cudaSuccess) {
+      cudaMalloc(&c->dsm, (4096 + kScfRedBlocks) * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&c->fsm, 1024 * sizeof(float)) != cudaSuccess) {
     cudaGetLastError();
     rsx_scf_destroy(c);
     return RSX_ENOMEM;
@@ -1001,14 +1122,19 @@ int rsx_scf_step(rsx_scf* c, int inner, double* out_host, void* stream) {
   const double h3 = c->h * c->h * c->h;
   double* M = c->dsm;                 // [k][k]
   double* part = c->dsm + 4096;
-  // orbitals entering this iteration, their density, the reldens of the previous
-  // iteration and the mixing of its output density into the input
-  int rc = rsx_eig_orbitals(c->eig, c->phi, stream);
+  // Output orbitals of the previous iteration (the eigensolver's current ones), their
+  // density, the reldens of the previous iteration (Eq. 15), and the input of this one:
+  // density mixing (Eq. 14 on rho; the entering orbitals are the outputs) or state
+  // mixing (Eq. 14 on the orbitals, aligned through the projector on the output span).
+  const bool states = c->mix_states != 0;
+  float* phi_e = states ? c->mix2 : c->phi;               // orbitals entering this iteration
+  float* phi_out = states ? c->mix2 + (size_t)k * N : c->phi;
+  int rc = rsx_eig_orbitals(c->eig, phi_out, stream);
   if (rc) return sfail(c, rc, "orbitals");
-  k_density<<<(unsigned)blocks_for(N), 256, 0, s>>>(c->phi, k, N, c->rho);
+  k_density<<<(unsigned)blocks_for(N), 256, 0, s>>>(phi_out, k, N, c->rho);
   double reldens = 0.0;
   if (c->iter > 0) {
-    k_absdiff_mix<<<kScfRedBlocks, 256, 0, s>>>(c->rho_in, c->rho, N, c->alpha, 1, part);
+    k_absdiff_mix<<<kScfRedBlocks, 256, 0, s>>>(c->rho_in, c->rho, N, c->alpha, states ? 0 : 1, part);
     double hp[kScfRedBlocks];
     rc = scuda(c, cudaMemcpyAsync(hp, part, sizeof(hp), cudaMemcpyDeviceToHost, s), "reldens");
     if (!rc) rc = scuda(c, cudaStreamSynchronize(s), "reldens sync");
@@ -1016,43 +1142,60 @@ int rsx_scf_step(rsx_scf* c, int inner, double* out_host, void* stream) {
     for (int b = 0; b < kScfRedBlocks; ++b) reldens += hp[b];
     reldens *= h3 / (2.0 * k);
   }
+  if (states) {
+    if (c->iter == 0) {
+      rc = scuda(c, cudaMemcpyAsync(phi_e, phi_out, (size_t)k * N * sizeof(float), cudaMemcpyDeviceToDevice, s), "states");
+    } else {
+      double* O = c->dsm + 3072;
+      float* coef = c->fsm;
+      float* linv = c->fsm + 2 * k * k;
+      float* tmp = c->hphi;
+      rc = scf_gram(c, phi_out, k, phi_e, k, O, s);
+      if (rc) return rc;
+      k_state_mix_coeffs<<<1, 256, 0, s>>>(O, k, c->alpha, coef);
+      rc = check_cuda(c->ctx, launch_combine<float>(coef, k, 2 * k, c->mix2, N, tmp, 4 * c->ctx->nsm, s), "state mix");
+      if (!rc) rc = scf_gram(c, tmp, k, tmp, k, O, s);
+      if (rc) return rc;
+      k_chol_inv_small<<<1, 32, 0, s>>>(O, k, linv, c->ctx->status);
+      rc = check_cuda(c->ctx, launch_combine<float>(linv, k, k, tmp, N, phi_e, 4 * c->ctx->nsm, s), "orthonormalise");
+    }
+    if (rc) return rc;
+    k_density<<<(unsigned)blocks_for(N), 256, 0, s>>>(phi_e, k, N, c->rho_in);
+  } else if (c->iter == 0) {
+    rc = scuda(c, cudaMemcpyAsync(c->rho_in, c->rho, N * sizeof(float), cudaMemcpyDeviceToDevice, s), "rho_in");
+    if (rc) return rc;
+  }
+  const float* rho_e = states ? c->rho_in : c->rho;       // density of the entering orbitals
   // exchange from the entering orbitals: W, M (E_x = tr M) and the ACE projectors
-  rc = rsx_ace_build(c->ctx, c->phi, k, c->xi, M, stream);
+  rc = rsx_ace_build(c->ctx, phi_e, k, c->xi, M, stream);
   if (rc) return sfail(c, rc, "ACE build failed");
   // energy parts of the entering orbitals: one-body, Hartree
-  rc = rsx_poisson(c->ctx, c->rho, c->vh, stream);
+  rc = rsx_poisson(c->ctx, rho_e, c->vh, stream);
   if (rc) return sfail(c, rc, "Poisson (energy) failed");
-  k_ham_apply<<<ham_grid(k, c->n), ham_block(c->n), 0, s>>>(c->phi, k, c->n, (float)(1.0 / (12.0 * c->h * c->h)), c->vext,
+  k_ham_apply<<<ham_grid(k, c->n), ham_block(c->n), 0, s>>>(phi_e, k, c->n, (float)(1.0 / (12.0 * c->h * c->h)), c->vext,
                                                           nullptr, c->hphi);
-  const int nblk = 2 * c->ctx->nsm;
-  rc = grow(c->ctx, (void**)&c->ctx->dsm, &c->ctx->dsm_bytes, sizeof(double) * ((size_t)nblk * 4096 + 3 * 4096),
-            "small FP64");
-  double* G = c->dsm + 1024;
-  if (!rc) rc = check_cuda(c->ctx, launch_gram<float>(c->phi, k, c->hphi, k, N, c->ctx->dsm, nblk, s), "one-body");
-  if (!rc) rc = check_cuda(c->ctx, launch_gram_reduce<float>(c->ctx->dsm, nblk, k, k, h3, false, G, (float*)nullptr, s),
-                           "one-body");
-  double* EH = c->dsm + 2048;
-  if (!rc) rc = check_cuda(c->ctx, launch_gram<float>(c->rho, 1, c->vh, 1, N, c->ctx->dsm, nblk, s), "hartree");
-  if (!rc) rc = check_cuda(c->ctx, launch_gram_reduce<float>(c->ctx->dsm, nblk, 1, 1, h3, false, EH, (float*)nullptr, s),
-                           "hartree");
+  rc = scf_gram(c, phi_e, k, c->hphi, k, c->dsm + 1024, s);
+  if (!rc) rc = scf_gram(c, rho_e, 1, c->vh, 1, c->dsm + 2048, s);
   if (rc) return rc;
   double hm[3 * 1024];
   rc = scuda(c, cudaMemcpyAsync(hm, c->dsm, sizeof(hm), cudaMemcpyDeviceToHost, s), "energies");
   if (!rc) rc = scuda(c, cudaStreamSynchronize(s), "energy sync");
   if (!rc) rc = rsx_sync_status(c->ctx, stream);
-  if (rc) return sfail(c, rc, "energy evaluation failed (ACE matrix not negative definite?)");
+  if (rc) return sfail(c, rc, "energy evaluation failed (ACE or overlap matrix not definite)");
   double one = 0.0, ex = 0.0;
   for (int i = 0; i < k; ++i) {
     one += 2.0 * hm[1024 + i * k + i];
     ex += hm[i * k + i];
   }
   const double eh = 0.5 * hm[2048];
-  if (c->iter == 0) cudaMemcpyAsync(c->rho_in, c->rho, N * sizeof(float), cudaMemcpyDeviceToDevice, s);
-  // Fock operator of this iteration: V = V_ext + V_H[rho_in], exchange of the entering orbitals
-  rc = rsx_poisson(c->ctx, c->rho_in, c->vh, stream);
-  if (rc) return sfail(c, rc, "Poisson failed");
+  // Fock operator of this iteration: V = V_ext + V_H[rho_in], exchange of the entering
+  // orbitals (with state mixing rho_in is their density, and V_H was just computed)
+  if (!states) {
+    rc = rsx_poisson(c->ctx, c->rho_in, c->vh, stream);
+    if (rc) return sfail(c, rc, "Poisson failed");
+  }
   k_add<<<(unsigned)blocks_for(N), 256, 0, s>>>(c->vext, c->vh, N, c->V);
-  rc = rsx_eig_set_exchange(c->eig, c->ctx, c->mode == 1 ? c->xi : c->phi, k, c->mode);
+  rc = rsx_eig_set_exchange(c->eig, c->ctx, c->mode == 1 ? c->xi : phi_e, k, c->mode);
   if (!rc) rc = rsx_eig_refresh(c->eig, nullptr, stream);
   double theta[64] = {0};
   for (int it = 0; it < inner && !rc; ++it) rc = rsx_eig_step(c->eig, nullptr, 3, theta, stream);
@@ -1069,6 +1212,19 @@ int rsx_scf_step(rsx_scf* c, int inner, double* out_host, void* stream) {
   return RSX_OK;
 }
 
+// What Eq. 14 mixes: 0 the density (default), 1 the states.  Before the first step only.
+int rsx_scf_set_mixing(rsx_scf* c, int mix_states) {
+  if (!c || c->iter > 0 || (mix_states != 0 && mix_states != 1)) return RSX_EINVAL;
+  if (mix_states && !c->mix2) {
+    if (cudaMalloc(&c->mix2, 2 * (size_t)c->nocc * c->ctx->g.N() * sizeof(float)) != cudaSuccess) {
+      cudaGetLastError();
+      return sfail(c, RSX_ENOMEM, "state mixing buffer");
+    }
+  }
+  c->mix_states = mix_states;
+  return RSX_OK;
+}
+
 int rsx_scf_orbitals(rsx_scf* c, float* psi_out, void* stream) {
   if (!c || !psi_out) return RSX_EINVAL;
   return rsx_eig_orbitals(c->eig, psi_out, stream);
@@ -1080,7 +1236,7 @@ int rsx_scf_destroy(rsx_scf* c) {
   if (!c) return RSX_OK;
   cudaDeviceSynchronize();
   if (c->eig) rsx_eig_destroy(c->eig);
-  void* bufs[] = {c->V, c->rho_in, c->rho, c->vh, c->phi, c->xi, c->hphi, c->dsm};
+  void* bufs[] = {c->V, c->rho_in, c->rho, c->vh, c->phi, c->xi, c->hphi, c->dsm, c->mix2, c->fsm};
   for (void* p : bufs)
     if (p) cudaFree(p);
   delete c;

@@ -52,6 +52,7 @@ SIGNATURES = {
     "rsx_scf_create": [ctypes.POINTER(_P), _P, _P, _I, _I, ctypes.c_float],
     "rsx_scf_init": [_P, _P, _P],
     "rsx_scf_step": [_P, _I, ctypes.POINTER(_D), _P],
+    "rsx_scf_set_mixing": [_P, _I],
     "rsx_scf_orbitals": [_P, _P, _P],
     "rsx_scf_last_error": [_P],
     "rsx_scf_destroy": [_P],
@@ -492,7 +493,7 @@ class SCF:
 
     FIELDS = ("energy", "one_body", "hartree", "exchange", "reldens", "theta_sum")
 
-    def __init__(self, ctx, v_ext, nocc, ace=True, alpha=0.3):
+    def __init__(self, ctx, v_ext, nocc, ace=True, alpha=0.3, mix="density"):
         self.lib = load()
         self.ctx = ctx                        # kept alive: the library holds both pointers
         self.v_ext = v_ext
@@ -503,13 +504,18 @@ class SCF:
         if code != RSX_OK:
             raise RsxError(code, "rsx_scf_create failed")
         self.handle = h_
+        self.mix = mix
 
     def _check(self, code):
         if code != RSX_OK:
             raise RsxError(code, self.lib.rsx_scf_last_error(self.handle).decode())
 
     def init(self, psi0, stream=None):
+        """Start from psi0; `mix` ('density' or 'states') applies from here."""
+        if self.mix not in ("density", "states"):
+            raise ValueError("mix: 'density' or 'states'")
         self._check(self.lib.rsx_scf_init(self.handle, _ptr(psi0), _stream(stream)))
+        self._check(self.lib.rsx_scf_set_mixing(self.handle, int(self.mix == "states")))
 
     def step(self, inner=2, stream=None):
         """One SCF iteration; returns a dict of the six reported quantities."""

@@ -40,11 +40,11 @@ def _case():
     return g, c, v, psi0
 
 
-def _run_scf(ace, iters=80, inner=2, tol=2e-6):
+def _run_scf(ace, iters=80, inner=2, tol=2e-6, mix="density"):
     g, c, v, psi0 = _case()
     ctx = rsx.Context((c["n"],) * 3, c["h"], "fp32")
     vd = to_dev(v, "fp32")
-    scf = rsx.SCF(ctx, vd, c["nocc"], ace=ace, alpha=c["alpha"])
+    scf = rsx.SCF(ctx, vd, c["nocc"], ace=ace, alpha=c["alpha"], mix=mix)
     scf.init(to_dev(psi0, "fp32"))
     hist = []
     for _ in range(iters):
@@ -104,13 +104,14 @@ def test_scf_energy_terms_vs_oracle():
     assert abs(r["exchange"] - ex) < 1e-5 * abs(ex)
 
 
-@pytest.mark.parametrize("ace", [True, False])
-def test_scf_converges_to_the_oracle_ground_state(ace):
+@pytest.mark.parametrize("ace,mix", [(True, "density"), (False, "density"), (True, "states")])
+def test_scf_converges_to_the_oracle_ground_state(ace, mix):
     """Both cycles reach the oracle's self-consistent HF energy and orbital energies
-    (Sec. 3.1: with ACE the fixed point is unchanged), with the density error of Eq. 15
-    falling to the FP32 level."""
+    (Sec. 3.1: with ACE the fixed point is unchanged; Sec. 3.2: nor does it depend on
+    mixing the density or the states), with the density error of Eq. 15 falling to the
+    FP32 level."""
     need_gpu()
-    g, c, v, scf, ctx, hist = _run_scf(ace)
+    g, c, v, scf, ctx, hist = _run_scf(ace, mix=mix)
     ref = g["ace" if ace else "exact"]
     last = hist[-1]
     assert 0 < last["reldens"] < 2e-6, [h["reldens"] for h in hist]
@@ -140,3 +141,5 @@ def test_scf_invalid_arguments():
     ctx64 = rsx.Context((16, 16, 16), 0.5, "fp64")
     with pytest.raises(rsx.RsxError):
         rsx.SCF(ctx64, v, 2)
+    with pytest.raises(ValueError):
+        rsx.SCF(ctx, v, 2, mix="potential").init(torch.zeros((2, 16, 16, 16), device="cuda"))

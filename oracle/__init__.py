@@ -18,7 +18,8 @@ Modules
 coulomb   discrete Coulomb kernel and the isolated Poisson solve (FFT and direct sum)
 exchange  pair densities, exact-exchange action, exchange / Hartree energies
 ace       adaptively compressed exchange: build and apply
-casida    coupling matrices K and K_d, TDA matrix, eigen-solve
+casida    coupling matrices K and K_d, TDA matrix, eigen-solve; the spin-polarised
+          (UHF) coupling over alpha and beta transitions and its TDA matrix
 eigensolver  FD4 Hamiltonian, kinetic-energy preconditioner, Rayleigh-Ritz step, and the
           3-layer conv3d network of the learned preconditioner with its gradients
 spectra   dipole matrix elements, oscillator strengths, Lorentzian strength function,
@@ -34,12 +35,12 @@ from .exchange import (pair_density, exchange_apply, exchange_apply_bruteforce,
                        exchange_energy, hartree_energy, inner)
 from .ace import ace_build, ace_apply
 from .casida import (transition_densities, casida_K, casida_K_bruteforce, casida_Kd,
-                     tda_matrix, tda_solve, HARTREE_EV)
+                     tda_matrix, tda_solve, uhf_K, uhf_tda_matrix, HARTREE_EV)
 
 __all__ = [
     "C0", "kernel_samples", "kernel_spectrum", "poisson_fft", "poisson_direct",
     "pair_density", "exchange_apply", "exchange_apply_bruteforce", "exchange_energy",
     "hartree_energy", "inner", "ace_build", "ace_apply", "transition_densities",
     "casida_K", "casida_K_bruteforce", "casida_Kd", "tda_matrix", "tda_solve",
-    "HARTREE_EV",
+    "uhf_K", "uhf_tda_matrix", "HARTREE_EV",
 ]

@@ -108,3 +108,38 @@ def tda_solve(A, nroots):
     """
     w, v = np.linalg.eigh(0.5 * (A + A.T))
     return w[:nroots], v[:, :nroots].T
+
+
+# ---------------------------------------------------------------- spin-polarised (UHF) TDA
+#
+# Sec. 2, Eqs. 4-5 in spin orbitals: A_{ia,jb} = delta_ij delta_ab (eps_a - eps_i)
+# + (ia|jb) - (ij|ab), with every integral zero unless the spins pair up inside each
+# density.  For real spatial orbitals of spins s (i, a) and t (j, b): (ia|jb) couples
+# every pair of spin blocks (the Coulomb-type term), (ij|ab) = (ab|ji) = K_d only within
+# one spin (s = t).  Readings: alpha transitions first, t = i * n_virt + a within a spin.
+
+
+def uhf_K(occ_a, virt_a, occ_b, virt_b, h, poisson=poisson_fft):
+    """(ia|jb) over the alpha then beta transitions; symmetric (n_ta + n_tb) square."""
+    rho = [transition_densities(occ_a, virt_a)]
+    if len(occ_b) and len(virt_b):
+        rho.append(transition_densities(occ_b, virt_b))
+    rho = np.concatenate(rho)
+    nt = rho.shape[0]
+    V = np.stack([poisson(rho[s], h) for s in range(nt)])
+    return h ** 3 * (rho.reshape(nt, -1) @ V.reshape(nt, -1).T)
+
+
+def uhf_tda_matrix(eo_a, ev_a, eo_b, ev_b, K, Kd_a=None, Kd_b=None):
+    """A = diag(eps_a - eps_i per spin) + K - blockdiag(K_d alpha, K_d beta)."""
+    de = [(np.asarray(ev_a, dtype=np.float64)[None, :] - np.asarray(eo_a, dtype=np.float64)[:, None]).ravel()]
+    if len(eo_b) and len(ev_b):
+        de.append((np.asarray(ev_b, dtype=np.float64)[None, :] - np.asarray(eo_b, dtype=np.float64)[:, None]).ravel())
+    de = np.concatenate(de)
+    A = np.diag(de) + np.asarray(K, dtype=np.float64)
+    na = len(eo_a) * len(ev_a)
+    if Kd_a is not None:
+        A[:na, :na] -= np.asarray(Kd_a, dtype=np.float64)
+    if Kd_b is not None:
+        A[na:, na:] -= np.asarray(Kd_b, dtype=np.float64)
+    return A

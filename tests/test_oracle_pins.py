@@ -515,3 +515,50 @@ def test_state_mixing_keeps_an_orthonormal_set_and_is_rotation_blind():
     assert np.allclose(h ** 3 * m1 @ m1.T, np.eye(3), atol=1e-12)
     assert np.allclose(m1, m2, atol=1e-12)
     assert np.allclose(oscf.mix_states(A, A, h, 0.4), A, atol=1e-12)   # fixed point
+
+
+# ---------------------------------------------------------------- spin-polarised TDA (Eqs. 4-5)
+
+
+def test_uhf_cross_spin_coupling_is_the_double_sum():
+    """The alpha-beta block of the UHF coupling is Eq. 6 written out between an alpha
+    and a beta transition density (direct double sum, no FFT)."""
+    rng = np.random.default_rng(21)
+    oa, va = rng.standard_normal((2, 3, 3, 4)), rng.standard_normal((2, 3, 3, 4))
+    ob, vb = rng.standard_normal((1, 3, 3, 4)), rng.standard_normal((3, 3, 3, 4))
+    h = 0.5
+    K = oracle.uhf_K(oa, va, ob, vb, h)
+    ra = oracle.transition_densities(oa, va)
+    rb = oracle.transition_densities(ob, vb)
+    cross = np.array([[h ** 3 * np.sum(ra[t] * oracle.poisson_direct(rb[s], h)) for s in range(3)]
+                      for t in range(4)])
+    assert K.shape == (7, 7)
+    assert np.max(np.abs(K[:4, 4:] - cross)) <= 1e-12 * np.abs(cross).max()
+    assert np.max(np.abs(K - K.T)) <= 1e-13 * np.abs(K).max()
+
+
+def test_uhf_closed_shell_splits_into_singlets_and_triplets():
+    """Equal alpha and beta orbitals: the spin-orbital matrix [[D + K - Kd, K], [K,
+    D + K - Kd]] block-diagonalises into D + 2K - Kd (singlets, delta_M = 2 of Eq. 7) and
+    D - Kd (triplets, delta_M = 0), so its spectrum is the union of the two."""
+    s = inputs.casida_system(n=12, h=0.5, nocc=2, nvirt=3)
+    po, pv = s.phi, s.phi_virt
+    eo, ev = np.array([-0.7, -0.45]), np.array([0.05, 0.2, 0.4])
+    K = oracle.uhf_K(po, pv, po, pv, s.h)
+    Kd = oracle.casida_Kd(po, pv, s.h)
+    w_uhf = np.linalg.eigvalsh(oracle.uhf_tda_matrix(eo, ev, eo, ev, K, Kd, Kd))
+    K1 = oracle.casida_K(po, pv, s.h)
+    sing = np.linalg.eigvalsh(oracle.tda_matrix(eo, ev, K1, Kd, delta_M=2.0))
+    trip = np.linalg.eigvalsh(oracle.tda_matrix(eo, ev, K1, Kd, delta_M=0.0))
+    assert np.allclose(w_uhf, np.sort(np.concatenate([sing, trip])), rtol=0, atol=1e-12)
+
+
+def test_uhf_without_beta_transitions_is_the_spin_orbital_block():
+    """No beta transitions: A is the alpha block alone, diag + (ia|jb) - (ij|ab)."""
+    s = inputs.casida_system(n=12, h=0.5, nocc=1, nvirt=4)
+    eo, ev = np.array([-0.5]), np.array([0.1, 0.2, 0.3, 0.6])
+    K = oracle.uhf_K(s.phi, s.phi_virt, s.phi[:0], s.phi_virt[:0], s.h)
+    Kd = oracle.casida_Kd(s.phi, s.phi_virt, s.h)
+    A = oracle.uhf_tda_matrix(eo, ev, [], [], K, Kd)
+    assert np.allclose(A, oracle.tda_matrix(eo, ev, oracle.casida_K(s.phi, s.phi_virt, s.h), Kd, delta_M=1.0),
+                       rtol=0, atol=1e-13)

@@ -142,6 +142,15 @@ int rsx_ace_apply(rsx_ctx* ctx, const void* xi, int nxi, const void* psi, int np
 int rsx_casida_K(rsx_ctx* ctx, const void* phi_occ, int nocc, const void* phi_virt, int nvirt, double* K,
                  void* stream);
 
+/* Spin-polarised (UHF) coupling, Eqs. 4-5 in spin orbitals: K_{ia,jb} = (ia|jb) over the
+ * alpha transitions t = i * nvirt_a + a followed by the beta ones, nta + ntb <= 4096: every
+ * spin block of the Coulomb-type term, from one split-BF16 panel in an FP32 context (the
+ * plain FP64 form otherwise).  nocc_b or nvirt_b may be 0 (no beta transitions).
+ * occ_*: [nocc_*][N], virt_*: [nvirt_*][N]; K: device double [nt][nt].
+ * Errors: RSX_EINVAL, RSX_ENOMEM, RSX_EUNSUPPORTED. */
+int rsx_casida_K_uhf(rsx_ctx* ctx, const void* occ_a, int nocc_a, const void* virt_a, int nvirt_a, const void* occ_b,
+                     int nocc_b, const void* virt_b, int nvirt_b, double* K, void* stream);
+
 /* Coulomb term K_d[ia,jb] = (ab|ji) = <phi_a phi_b, V[phi_j phi_i]> of Eq. 7.
  * Same arguments and layout as rsx_casida_K. */
 int rsx_casida_Kd(rsx_ctx* ctx, const void* phi_occ, int nocc, const void* phi_virt, int nvirt, double* Kd,
@@ -155,6 +164,15 @@ int rsx_casida_Kd(rsx_ctx* ctx, const void* phi_occ, int nocc, const void* phi_v
 int rsx_casida_solve(rsx_ctx* ctx, const double* eps_occ, int nocc, const double* eps_virt, int nvirt,
                      const double* K, const double* Kd, double delta_M, int nroots, double* omega, double* X,
                      void* stream);
+/* Lowest nroots eigenpairs of the spin-polarised TDA matrix
+ * A = diag(eps_a - eps_i per spin) + K - blockdiag(K_d alpha, K_d beta) (Eqs. 4-5; the
+ * exchange-type term (ij|ab) only couples transitions of one spin), with K from
+ * rsx_casida_K_uhf and K_d per spin from rsx_casida_Kd (either may be NULL).
+ * eps: device doubles; omega: [nroots] ascending (Hartree); X: [nroots][nt] or NULL.
+ * Errors: RSX_EINVAL, RSX_ENOMEM. */
+int rsx_casida_solve_uhf(rsx_ctx* ctx, const double* eps_occ_a, int nocc_a, const double* eps_virt_a, int nvirt_a,
+                         const double* eps_occ_b, int nocc_b, const double* eps_virt_b, int nvirt_b, const double* K,
+                         const double* Kd_a, const double* Kd_b, int nroots, double* omega, double* X, void* stream);
 
 /* Full (non-Tamm-Dancoff) RHF linear response, Eqs. 3-5 with real orbitals, in the
  * half-size symmetric form: A = diag(eps_a - eps_i) + delta_M K - K_d (Eq. 7),

@@ -9,6 +9,9 @@
 // rsx_casida_Kd  K_d[ia,jb] = (ab|ji) = h^3 sum_r phi_a phi_b V_ij, V_ij for the
 //   unordered occupied pairs (i, j); symmetric in (i, j), so each block fills two places.
 // rsx_casida_solve  FP64 eigen-solve of A = diag(de) + delta_M K - K_d (eig.cu).
+// rsx_casida_K_uhf / rsx_casida_solve_uhf  the spin-polarised form: K over the alpha
+//   then the beta transitions in one panel (every spin block of the Coulomb-type term),
+//   A = diag(de) + K - blockdiag(K_d alpha, K_d beta).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -89,11 +92,21 @@ int gram_blocks(rsx_ctx* c, const R* X, const R* Y, int n, size_t N, double scal
   return RSX_OK;
 }
 
-int casida_K_f32(rsx_ctx* c, const void* po, int no, const void* pv, int nv, double* K, cudaStream_t s) {
+// A set of transitions (occupied x virtual of one spin), t = i * nv + a within the set;
+// sets follow one another in K.
+struct TSet {
+  const void* po;
+  int no;
+  const void* pv;
+  int nv;
+  int nt() const { return no * nv; }
+};
+
+int casida_K_f32(rsx_ctx* c, const TSet* sets, int nsets, double* K, cudaStream_t s) {
   const Geom& g = c->g;
   const size_t N = g.N();
-  const int nt = no * nv;
-  const PairMap<float> pm = prod_map<float>(pv, nv, po, no, N);  // q = i * nv + a
+  int nt = 0;
+  for (int k = 0; k < nsets; ++k) nt += sets[k].nt();
   const size_t inter_bytes = (size_t)nt * g.inter_elems() * sizeof(Cx<float>);
   const long long ng = 2LL * g.Hx * g.My * g.Mz;
   const long long ld = (ng + 63) / 64 * 64;
@@ -133,7 +146,15 @@ int casida_K_f32(rsx_ctx* c, const void* po, int no, const void* pv, int nv, dou
   Cx<float>* inter = (Cx<float>*)c->work;
   {
     ProfScope ps(c, kKPass1, s);
-    rc = check_cuda(c, launch_pass1<float>(g, pm, 0, nt, inter, (const Cx<float>*)c->tw[2], s), "pass 1");
+    size_t off = 0;
+    for (int k = 0; k < nsets && !rc; ++k) {
+      if (!sets[k].nt()) continue;
+      const PairMap<float> pm = prod_map<float>(sets[k].pv, sets[k].nv, sets[k].po, sets[k].no, N);  // q = i * nv + a
+      rc = check_cuda(c, launch_pass1<float>(g, pm, 0, sets[k].nt(), inter + off * g.inter_elems(),
+                                             (const Cx<float>*)c->tw[2], s),
+                      "pass 1");
+      off += sets[k].nt();
+    }
   }
   if (rc) return rc;
   if (!c->specw) {   // panel weights, once per context
@@ -159,22 +180,31 @@ int casida_K_f32(rsx_ctx* c, const void* po, int no, const void* pv, int nv, dou
 }
 
 template <typename R>
-int casida_K_plain(rsx_ctx* c, const void* po, int no, const void* pv, int nv, double* K, cudaStream_t s) {
+int casida_K_plain(rsx_ctx* c, const TSet* sets, int nsets, double* K, cudaStream_t s) {
   const Geom& g = c->g;
   const size_t N = g.N();
-  const int nt = no * nv;
-  const PairMap<R> pm = prod_map<R>(pv, nv, po, no, N);
-  const size_t need = (size_t)nt * g.inter_elems() * sizeof(Cx<R>) + 2 * (size_t)nt * N * sizeof(R);
+  int nt = 0, ntmax = 0;
+  for (int k = 0; k < nsets; ++k) {
+    nt += sets[k].nt();
+    ntmax = std::max(ntmax, sets[k].nt());
+  }
+  const size_t need = (size_t)ntmax * g.inter_elems() * sizeof(Cx<R>) + 2 * (size_t)nt * N * sizeof(R);
   if (need > c->work_limit) return set_error(c, RSX_ENOMEM, "casida_K: workspace limit exceeded");
   int rc = grow(c, &c->panel_hi, &c->panel_hi_bytes, 2 * (size_t)nt * N * sizeof(R), "potentials and densities");
   if (rc) return rc;
   R* V = (R*)c->panel_hi;
   R* rho = V + (size_t)nt * N;
-  rc = solve_pairs<R>(c, pm, 0, nt, 0, nt, V, s, 1);
-  if (rc) return rc;
-  {
+  size_t off = 0;
+  for (int k = 0; k < nsets && !rc; ++k) {
+    const TSet& t = sets[k];
+    if (!t.nt()) continue;
+    const PairMap<R> pm = prod_map<R>(t.pv, t.nv, t.po, t.no, N);
+    rc = solve_pairs<R>(c, pm, 0, t.nt(), 0, t.nt(), V + off * N, s, 1);
+    if (rc) return rc;
     ProfScope ps(c, kKPairProd, s);
-    rc = check_cuda(c, launch_pair_products<R>((const R*)po, no, (const R*)pv, nv, N, rho, s), "densities");
+    rc = check_cuda(c, launch_pair_products<R>((const R*)t.po, t.no, (const R*)t.pv, t.nv, N, rho + off * N, s),
+                    "densities");
+    off += t.nt();
   }
   if (rc) return rc;
   rc = gram_blocks<R>(c, rho, V, nt, N, c->h * c->h * c->h, K, (const R*)nullptr, nt, s);
@@ -250,11 +280,50 @@ int rsx_casida_K(rsx_ctx* c, const void* phi_occ, int nocc, const void* phi_virt
   int rc = check_casida_args(c, phi_occ, nocc, phi_virt, nvirt, K);
   if (rc) return rc;
   cudaStream_t s = (cudaStream_t)stream;
+  const TSet set{phi_occ, nocc, phi_virt, nvirt};
   if (c->precision == RSX_FP32) {
     if (c->g.Ay != c->g.Az) return set_error(c, RSX_EUNSUPPORTED, "casida_K: ny must equal nz");
-    return casida_K_f32(c, phi_occ, nocc, phi_virt, nvirt, K, s);
+    return casida_K_f32(c, &set, 1, K, s);
   }
-  return casida_K_plain<double>(c, phi_occ, nocc, phi_virt, nvirt, K, s);
+  return casida_K_plain<double>(c, &set, 1, K, s);
+}
+
+int rsx_casida_K_uhf(rsx_ctx* c, const void* occ_a, int nocc_a, const void* virt_a, int nvirt_a, const void* occ_b,
+                     int nocc_b, const void* virt_b, int nvirt_b, double* K, void* stream) {
+  RSX_PREP_C(c);
+  int rc = check_casida_args(c, occ_a, nocc_a, virt_a, nvirt_a, K);
+  if (rc) return rc;
+  const bool has_b = nocc_b > 0 && nvirt_b > 0;
+  if (nocc_b < 0 || nvirt_b < 0 || (has_b && (!occ_b || !virt_b)))
+    return set_error(c, RSX_EINVAL, "casida_K_uhf: bad beta arguments");
+  const size_t N = c->g.N(), es = c->elem_size();
+  const size_t nt = (size_t)nocc_a * nvirt_a + (has_b ? (size_t)nocc_b * nvirt_b : 0);
+  if (nt > 4096) return set_error(c, RSX_EINVAL, "casida_K_uhf: more than 4096 transitions");
+  if (has_b && (overlap(K, nt * nt * 8, occ_b, nocc_b * N * es) || overlap(K, nt * nt * 8, virt_b, nvirt_b * N * es) ||
+                overlap(K, nt * nt * 8, occ_a, nocc_a * N * es) || overlap(K, nt * nt * 8, virt_a, nvirt_a * N * es)))
+    return set_error(c, RSX_EINVAL, "casida_K_uhf: output aliases an input");
+  cudaStream_t s = (cudaStream_t)stream;
+  const TSet sets[2] = {{occ_a, nocc_a, virt_a, nvirt_a}, {occ_b, has_b ? nocc_b : 0, virt_b, has_b ? nvirt_b : 0}};
+  if (c->precision == RSX_FP32) {
+    if (c->g.Ay != c->g.Az) return set_error(c, RSX_EUNSUPPORTED, "casida_K: ny must equal nz");
+    return casida_K_f32(c, sets, 2, K, s);
+  }
+  return casida_K_plain<double>(c, sets, 2, K, s);
+}
+
+int rsx_casida_solve_uhf(rsx_ctx* c, const double* eo_a, int nocc_a, const double* ev_a, int nvirt_a,
+                         const double* eo_b, int nocc_b, const double* ev_b, int nvirt_b, const double* K,
+                         const double* Kd_a, const double* Kd_b, int nroots, double* omega, double* X, void* stream) {
+  RSX_PREP_C(c);
+  const bool has_b = nocc_b > 0 && nvirt_b > 0;
+  const int nt = nocc_a * nvirt_a + (has_b ? nocc_b * nvirt_b : 0);
+  if (!eo_a || !ev_a || !K || !omega || nocc_a < 1 || nvirt_a < 1 || nocc_b < 0 || nvirt_b < 0 ||
+      (has_b && (!eo_b || !ev_b)) || nt > 4096 || nroots < 1 || nroots > nt)
+    return set_error(c, RSX_EINVAL, "casida_solve_uhf: bad arguments");
+  int rc = grow(c, &c->eig_work, &c->eig_work_bytes, tda_work_doubles(nt, nroots) * sizeof(double), "eigensolver");
+  if (rc) return rc;
+  return uhf_tda_solve(c, eo_a, nocc_a, ev_a, nvirt_a, eo_b, has_b ? nocc_b : 0, ev_b, has_b ? nvirt_b : 0, K, Kd_a,
+                       has_b ? Kd_b : nullptr, nroots, omega, X, (double*)c->eig_work, (cudaStream_t)stream);
 }
 
 int rsx_casida_Kd(rsx_ctx* c, const void* phi_occ, int nocc, const void* phi_virt, int nvirt, double* Kd,

@@ -746,6 +746,40 @@ int sym_eig_lowest(rsx_ctx* c, double* work, int n, int nroots, double* omega, d
   return check_cuda(c, cudaGetLastError(), "symmetric eigensolve");
 }
 
+namespace {
+// spin-polarised TDA matrix: alpha transitions [0, nta), beta [nta, nta + ntb)
+__global__ void k_uhf_assemble(const double* __restrict__ eoa, int noa, const double* __restrict__ eva, int nva,
+                               const double* __restrict__ eob, int nob, const double* __restrict__ evb, int nvb,
+                               const double* __restrict__ K, const double* __restrict__ Kda,
+                               const double* __restrict__ Kdb, double* __restrict__ A) {
+  const int nta = noa * nva, ntb = nob * nvb, n = nta + ntb;
+  const long long total = (long long)n * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int t = (int)(e / n), u = (int)(e - (long long)t * n);
+    double v = 0.5 * (K[e] + K[(long long)u * n + t]);
+    if (t < nta && u < nta) {
+      if (Kda) v -= 0.5 * (Kda[(long long)t * nta + u] + Kda[(long long)u * nta + t]);
+      if (t == u) v += eva[t % nva] - eoa[t / nva];
+    } else if (t >= nta && u >= nta) {
+      const int tb = t - nta, ub = u - nta;
+      if (Kdb) v -= 0.5 * (Kdb[(long long)tb * ntb + ub] + Kdb[(long long)ub * ntb + tb]);
+      if (tb == ub) v += evb[tb % nvb] - eob[tb / nvb];
+    }
+    A[e] = v;
+  }
+}
+}  // namespace
+
+int uhf_tda_solve(rsx_ctx* c, const double* eoa, int noa, const double* eva, int nva, const double* eob, int nob,
+                  const double* evb, int nvb, const double* K, const double* Kda, const double* Kdb, int nroots,
+                  double* omega, double* X, double* work, cudaStream_t s) {
+  const int n = noa * nva + nob * nvb;
+  ProfScope ps(c, kKEig, s);
+  k_uhf_assemble<<<256, 256, 0, s>>>(eoa, noa, eva, nva, eob, nob, evb, nvb, K, Kda, Kdb, work);
+  return sym_eig_lowest(c, work, n, nroots, omega, X, s);
+}
+
 int tda_solve(rsx_ctx* c, const double* eo, int no, const double* ev, int nv, const double* K, const double* Kd,
               double dm, int nroots, double* omega, double* X, double* work, cudaStream_t s) {
   const int n = no * nv;

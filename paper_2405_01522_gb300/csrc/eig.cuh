@@ -175,6 +175,11 @@ size_t tda_work_doubles(int n, int nroots);
 int sym_eig_lowest(rsx_ctx* c, double* work, int n, int nroots, double* omega, double* X, cudaStream_t s);
 // A = diag(ev_a - eo_i) + dm K - Kd (Kd may be null), lowest nroots eigenvalues (ascending) and,
 // if X is not null, eigenvectors [nroots][n].  All pointers are device memory.
+// spin-polarised form: A = diag(de per spin) + K - blockdiag(Kda, Kdb) over the alpha then
+// beta transitions (nob * nvb may be 0; Kda / Kdb may be null)
+int uhf_tda_solve(rsx_ctx* c, const double* eoa, int noa, const double* eva, int nva, const double* eob, int nob,
+                  const double* evb, int nvb, const double* K, const double* Kda, const double* Kdb, int nroots,
+                  double* omega, double* X, double* work, cudaStream_t s);
 int tda_solve(rsx_ctx* c, const double* eo, int no, const double* ev, int nv, const double* K, const double* Kd,
               double dm, int nroots, double* omega, double* X, double* work, cudaStream_t s);
 }  // namespace rsx

@@ -34,6 +34,8 @@ SIGNATURES = {
     "rsx_ace_apply": [_P, _P, _I, _P, _I, _P, _P],
     "rsx_casida_K": [_P, _P, _I, _P, _I, _P, _P],
     "rsx_casida_Kd": [_P, _P, _I, _P, _I, _P, _P],
+    "rsx_casida_K_uhf": [_P, _P, _I, _P, _I, _P, _I, _P, _I, _P, _P],
+    "rsx_casida_solve_uhf": [_P, _P, _I, _P, _I, _P, _I, _P, _I, _P, _P, _P, _I, _P, _P, _P],
     "rsx_casida_solve": [_P, _P, _I, _P, _I, _P, _P, _D, _I, _P, _P, _P],
     "rsx_casida_solve_full": [_P, _P, _I, _P, _I, _P, _P, _D, _I, _P, _P, _P],
     "rsx_casida_dipoles": [_P, _P, _I, _P, _I, _P, _P],
@@ -232,6 +234,30 @@ class Context:
         self._check(self.lib.rsx_casida_Kd(self.handle, _ptr(phi_occ), no, _ptr(phi_virt), nv, _ptr(Kd),
                                            _stream(stream)))
         return Kd
+
+    def casida_K_uhf(self, occ_a, virt_a, occ_b=None, virt_b=None, K=None, stream=None):
+        """(ia|jb) over alpha then beta transitions (spin-orbital form, Eqs. 4-5)."""
+        noa, nva = self._orb(occ_a, "occ_a"), self._orb(virt_a, "virt_a")
+        nob = self._orb(occ_b, "occ_b") if occ_b is not None else 0
+        nvb = self._orb(virt_b, "virt_b") if virt_b is not None else 0
+        nt = noa * nva + (nob * nvb if nob and nvb else 0)
+        K = torch.empty((nt, nt), dtype=torch.float64, device=self.device) if K is None else K
+        self._check(self.lib.rsx_casida_K_uhf(self.handle, _ptr(occ_a), noa, _ptr(virt_a), nva, _ptr(occ_b), nob,
+                                              _ptr(virt_b), nvb, _ptr(K), _stream(stream)))
+        return K
+
+    def casida_solve_uhf(self, eo_a, ev_a, eo_b, ev_b, K, Kd_a=None, Kd_b=None, nroots=10, vectors=False,
+                         stream=None):
+        """Lowest roots of diag + K - blockdiag(Kd_a, Kd_b); eps as device float64 tensors."""
+        nb_t = eo_b.numel() * ev_b.numel() if eo_b is not None and ev_b is not None else 0
+        nt = eo_a.numel() * ev_a.numel() + nb_t
+        omega = torch.empty(nroots, dtype=torch.float64, device=self.device)
+        X = torch.empty((nroots, nt), dtype=torch.float64, device=self.device) if vectors else None
+        self._check(self.lib.rsx_casida_solve_uhf(
+            self.handle, _ptr(eo_a), eo_a.numel(), _ptr(ev_a), ev_a.numel(), _ptr(eo_b),
+            eo_b.numel() if eo_b is not None else 0, _ptr(ev_b), ev_b.numel() if ev_b is not None else 0,
+            _ptr(K), _ptr(Kd_a), _ptr(Kd_b), int(nroots), _ptr(omega), _ptr(X), _stream(stream)))
+        return (omega, X) if vectors else omega
 
     def casida_solve(self, eps_occ, eps_virt, K, Kd=None, delta_M=2.0, nroots=10, vectors=False, stream=None):
         no, nv = eps_occ.numel(), eps_virt.numel()

@@ -16,6 +16,11 @@ paper.  Readings (stated, not taken from the paper):
 * One iteration of the block solver (Rayleigh-Ritz on [Psi, W]): S = <B, B>,
   Hs = <B, H B>, S = L L^T, C = L^-1 Hs L^-T, C y = theta y (ascending), new
   Psi = B L^-T y[:, :k].
+* Spherical domain (Sec. 3.4: a sphere around the molecule, zero boundary values on its
+  surface): the grid points within radius R of the box centre (the grid convention of
+  the Coulomb module, point (x, y, z) at ((x - nx/2) h, ...)); H is restricted to them,
+  i.e. the operator P H P with P the projector on the kept points, every orbital zero
+  elsewhere.
 * Convolution layer (stride 1, zero padding 1, 3^3 kernel):
   out[co, z, y, x] = b[co] + sum_{ci, dz, dy, dx} w[co, ci, dz, dy, dx] in[ci, z+dz-1, y+dy-1, x+dx-1].
   Network: conv(2 -> 16) ReLU conv(16 -> 16) ReLU conv(16 -> 1).
@@ -52,6 +57,24 @@ def hamiltonian_dense(v, h):
         e[j] = 1.0
         M[:, j] = hamiltonian_apply(e.reshape(v.shape), v, h).ravel()
     return M
+
+
+def sphere_mask(shape, h, radius):
+    """1 at the grid points within `radius` of the box centre, 0 elsewhere (float array)."""
+    nz, ny, nx = shape
+    z = (np.arange(nz) - nz / 2) * h
+    y = (np.arange(ny) - ny / 2) * h
+    x = (np.arange(nx) - nx / 2) * h
+    r2 = z[:, None, None] ** 2 + y[None, :, None] ** 2 + x[None, None, :] ** 2
+    return (r2 <= radius * radius).astype(np.float64)
+
+
+def hamiltonian_masked(v, h, mask):
+    """H restricted to the kept points (rows and columns of hamiltonian_dense), and the
+    flat indices of those points."""
+    keep = np.flatnonzero(np.asarray(mask).ravel() > 0)
+    H = hamiltonian_dense(v, h)
+    return H[np.ix_(keep, keep)], keep
 
 
 def ke_precondition(r, T, h, sweeps=3, omega=2.0 / 3.0):

@@ -81,9 +81,10 @@ def mix_states(phi_in, phi_out, h, alpha):
     return np.linalg.solve(L, mixed).reshape(phi_in.shape)
 
 
-def scf(v_ext, h, nocc, mode="ace", alpha=0.3, tol=1e-10, max_iter=300, mix="density"):
+def scf(v_ext, h, nocc, mode="ace", alpha=0.3, tol=1e-10, max_iter=300, mix="density", mask=None):
     """Self-consistent closed-shell HF on a small grid; mode 'ace' or 'exact', mix
-    'density' or 'states'.
+    'density' or 'states'; with `mask` (0/1 per point, e.g. eigensolver.sphere_mask) the
+    orbitals live on the kept points only (spherical domain, Sec. 3.4).
 
     Returns a dict with the orbitals, orbital energies, total energy (and its parts), the
     last relative density error and the iteration count."""
@@ -92,6 +93,12 @@ def scf(v_ext, h, nocc, mode="ace", alpha=0.3, tol=1e-10, max_iter=300, mix="den
     n = v_ext.size
     G = coulomb_matrix(shape, h)
     H0 = hamiltonian_dense(v_ext, h)
+    if mask is not None:
+        out = np.flatnonzero(np.asarray(mask).ravel() == 0)
+        H0 = H0.copy()
+        H0[out, :] = 0.0
+        H0[:, out] = 0.0
+        H0[out, out] = 1e6          # far above every kept level: those orbitals are never occupied
     w, U = np.linalg.eigh(0.5 * (H0 + H0.T))
     phi = (U[:, :nocc].T / h ** 1.5).reshape((nocc,) + shape)
     rho_in = density(phi).ravel()
@@ -106,6 +113,10 @@ def scf(v_ext, h, nocc, mode="ace", alpha=0.3, tol=1e-10, max_iter=300, mix="den
         else:
             VX = exchange_matrix(src, G)
         F = H0 + np.diag(VH) + VX
+        if mask is not None:
+            F[out, :] = 0.0
+            F[:, out] = 0.0
+            F[out, out] = 1e6
         w, U = np.linalg.eigh(0.5 * (F + F.T))
         phi = (U[:, :nocc].T / h ** 1.5).reshape((nocc,) + shape)
         rho_out = density(phi).ravel()

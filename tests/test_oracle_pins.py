@@ -562,3 +562,46 @@ def test_uhf_without_beta_transitions_is_the_spin_orbital_block():
     A = oracle.uhf_tda_matrix(eo, ev, [], [], K, Kd)
     assert np.allclose(A, oracle.tda_matrix(eo, ev, oracle.casida_K(s.phi, s.phi_virt, s.h), Kd, delta_M=1.0),
                        rtol=0, atol=1e-13)
+
+
+# ---------------------------------------------------------------- spherical domain (Sec. 3.4)
+
+
+@pytest.mark.parametrize("n,h", [(12, 0.6), (16, 0.5)])
+def test_sphere_levels_of_a_free_particle(n, h):
+    """V = 0 inside a sphere with zero boundary values: the levels are x^2 / (2 R^2), x the
+    zeros of the spherical Bessel functions (j0: pi; j1: 4.4934..., the root of tan x = x).
+    On the grid the boundary sits between the last kept point (radius <= R) and the first
+    dropped one (<= R + h), so E0 lies between the two radii's values; the ratio E1 / E0
+    does not depend on the radius, and the p level stays threefold."""
+    R = (n / 2 - 1) * h
+    H, keep = oe.hamiltonian_masked(np.zeros((n, n, n)), h, oe.sphere_mask((n, n, n), h, R))
+    w = np.linalg.eigvalsh(0.5 * (H + H.T))[:4]
+    x11 = 4.493409457909064
+    assert abs(math.tan(x11) - x11) < 1e-9
+    assert math.pi ** 2 / (2 * (R + h) ** 2) < w[0] < math.pi ** 2 / (2 * R ** 2)
+    assert abs(w[1] / w[0] - (x11 / math.pi) ** 2) < 0.01 * (x11 / math.pi) ** 2
+    assert np.ptp(w[1:4]) < 1e-10 * w[1]
+
+
+def test_sphere_restriction_raises_every_level():
+    """Restricting H to a subset of the points can only raise each eigenvalue
+    (Courant-Fischer), and a sphere holding the whole box restricts nothing."""
+    v = inputs.model_potential(n=10, h=0.5, natoms=2, Z=2.0, rc=0.8, radius=0.8, seed=3)
+    full = np.linalg.eigvalsh(oe.hamiltonian_dense(v, 0.5))[:6]
+    Hm, _ = oe.hamiltonian_masked(v, 0.5, oe.sphere_mask(v.shape, 0.5, 2.0))
+    part = np.linalg.eigvalsh(0.5 * (Hm + Hm.T))[:6]
+    assert np.all(part >= full - 1e-12)
+    Hw, keep = oe.hamiltonian_masked(v, 0.5, oe.sphere_mask(v.shape, 0.5, 100.0))
+    assert keep.size == v.size and np.allclose(np.linalg.eigvalsh(0.5 * (Hw + Hw.T))[:6], full, atol=1e-12)
+
+
+def test_masked_scf_stays_in_the_sphere_and_ace_is_exact_there():
+    v = _scf_potential()
+    m = oe.sphere_mask(v.shape, 0.5, 1.6)
+    a = oscf.scf(v, 0.5, 2, mode="ace", tol=1e-11, mask=m)
+    b = oscf.scf(v, 0.5, 2, mode="exact", tol=1e-11, mask=m)
+    assert np.max(np.abs(a["phi"][:, m == 0])) < 1e-12
+    assert abs(a["energy"] - b["energy"]) < 1e-9 * abs(b["energy"])
+    free = oscf.scf(v, 0.5, 2, mode="exact", tol=1e-11)
+    assert b["energy"] > free["energy"]           # a smaller domain, a higher variational energy

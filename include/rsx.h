@@ -253,6 +253,10 @@ int rsx_eig_destroy(rsx_eig* eig);
  * through ctx (an FP32 context on the same box).  src (and ctx) are kept by pointer.
  * Takes effect at the next rsx_eig_step or rsx_eig_refresh.  Errors: RSX_EINVAL, RSX_ENOMEM. */
 int rsx_eig_set_exchange(rsx_eig* eig, rsx_ctx* ctx, const float* src, int count, int mode);
+/* Spherical domain (Sec. 3.4: a sphere with zero boundary values): H restricted to the
+ * points where mask is 1 (device float [n^3] of 0 / 1, kept by pointer; NULL = the whole
+ * box).  The next rsx_eig_init zeroes the starting orbitals outside it.  Errors: RSX_EINVAL. */
+int rsx_eig_set_mask(rsx_eig* eig, const float* mask);
 /* H has changed (V's contents or the exchange term): recompute H Psi, Rayleigh-Ritz on the
  * current orbitals, drop the previous search direction; theta_host[nband] or NULL.
  * Synchronises the stream. */
@@ -284,6 +288,8 @@ int rsx_scf_step(rsx_scf* scf, int inner, double* out_host, void* stream);
  * the output orbitals' span; the Fock operator then takes V_H and Vx from the input
  * orbitals, and the reported energy is theirs.  Errors: RSX_EINVAL, RSX_ENOMEM. */
 int rsx_scf_set_mixing(rsx_scf* scf, int mix_states);
+/* Spherical domain for the orbitals (as rsx_eig_set_mask); call before rsx_scf_init. */
+int rsx_scf_set_mask(rsx_scf* scf, const float* mask);
 int rsx_scf_orbitals(rsx_scf* scf, float* psi_out, void* stream);
 const char* rsx_scf_last_error(const rsx_scf* scf);
 int rsx_scf_destroy(rsx_scf* scf);

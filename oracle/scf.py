@@ -93,32 +93,32 @@ def scf(v_ext, h, nocc, mode="ace", alpha=0.3, tol=1e-10, max_iter=300, mix="den
     n = v_ext.size
     G = coulomb_matrix(shape, h)
     H0 = hamiltonian_dense(v_ext, h)
-    if mask is not None:
-        out = np.flatnonzero(np.asarray(mask).ravel() == 0)
-        H0 = H0.copy()
-        H0[out, :] = 0.0
-        H0[:, out] = 0.0
-        H0[out, out] = 1e6          # far above every kept level: those orbitals are never occupied
-    w, U = np.linalg.eigh(0.5 * (H0 + H0.T))
-    phi = (U[:, :nocc].T / h ** 1.5).reshape((nocc,) + shape)
+    # the kept points (all of them without a mask): every matrix below lives on them
+    keep = np.arange(n) if mask is None else np.flatnonzero(np.asarray(mask).ravel() > 0)
+    Gk, H0k = G[np.ix_(keep, keep)], H0[np.ix_(keep, keep)]
+
+    def full(U):
+        phi = np.zeros((nocc, n))
+        phi[:, keep] = U[:, :nocc].T / h ** 1.5
+        return phi.reshape((nocc,) + shape)
+
+    w, U = np.linalg.eigh(0.5 * (H0k + H0k.T))
+    phi = full(U)
     rho_in = density(phi).ravel()
     phi_in = phi
     eps, it = np.inf, 0
     for it in range(1, max_iter + 1):
-        VH = G @ rho_in
+        VH = Gk @ rho_in[keep]
         src = phi_in if mix == "states" else phi      # orbitals the exchange is built from
         if mode == "ace":
-            zeta = ace_build(src, h).reshape(nocc, -1)
+            zeta = ace_build(src, h).reshape(nocc, -1)[:, keep]
             VX = -h ** 3 * (zeta.T @ zeta)
         else:
-            VX = exchange_matrix(src, G)
-        F = H0 + np.diag(VH) + VX
-        if mask is not None:
-            F[out, :] = 0.0
-            F[:, out] = 0.0
-            F[out, out] = 1e6
+            P = np.asarray(src).reshape(nocc, -1)[:, keep]
+            VX = -sum(P[j][:, None] * Gk * P[j][None, :] for j in range(nocc))
+        F = H0k + np.diag(VH) + VX
         w, U = np.linalg.eigh(0.5 * (F + F.T))
-        phi = (U[:, :nocc].T / h ** 1.5).reshape((nocc,) + shape)
+        phi = full(U)
         rho_out = density(phi).ravel()
         eps = h ** 3 * np.abs(rho_out - rho_in).sum() / (2 * nocc)
         if mix == "states":

@@ -33,11 +33,12 @@ namespace {
 constexpr int kMaxBasis = 64;
 
 // out = -1/2 Lap_FD4 f + V f  (or only the kinetic part when V is null; plus shift T_i f
-// when shift is not null).  f, out: [nb][n^3].  Block (x threads, rows of y), grid
+// when shift is not null; times the domain mask when one is given, f being zero outside
+// it).  f, out: [nb][n^3].  Block (x threads, rows of y), grid
 // (y blocks, z, orbital): no index division, and the y / z boundary test is uniform over
 // each warp (a warp holds one y row), so only the x neighbours are predicated per lane.
 __global__ void k_ham_apply(const float* __restrict__ f, int nb, int n, float inv12h2, const float* __restrict__ V,
-                            const double* __restrict__ shift, float* __restrict__ out) {
+                            const double* __restrict__ shift, const float* __restrict__ mask, float* __restrict__ out) {
   const int x = threadIdx.x, y = blockIdx.x * blockDim.y + threadIdx.y, z = blockIdx.y, b = blockIdx.z;
   if (x >= n || y >= n) return;
   const int nn = n * n;
@@ -68,7 +69,15 @@ __global__ void k_ham_apply(const float* __restrict__ f, int nb, int n, float in
   float r = -0.5f * lap * inv12h2;
   if (V) r += V[v] * c;
   if (shift) r += (float)shift[b] * c;
+  if (mask) r *= mask[v];   // spherical domain: H restricted to the kept points
   out[(size_t)b * N + v] = r;
+}
+
+// rows of X (row = blockIdx.y) times the domain mask
+__global__ void k_mask_rows(float* __restrict__ X, const float* __restrict__ mask, size_t N) {
+  float* x = X + (size_t)blockIdx.y * N;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x)
+    x[i] *= mask[i];
 }
 
 // part[b * gridDim.x + blk] = this block's share of sum_v X_b(v) Y_b(v) (w(v)) for row
@@ -710,6 +719,7 @@ struct rsx_eig {
   int xcount = 0;
   rsx_ctx* xctx = nullptr;
   float* xbuf = nullptr;         // [4k][N] exact-exchange output
+  const float* mask = nullptr;   // spherical domain (rsx_eig_set_mask), caller's [N] 0/1
   char err[256] = {0};
 };
 
@@ -766,7 +776,7 @@ dim3 ham_grid(int nb, int n) {
 int ham(rsx_eig* e, const float* f, int nb, float* out, const double* shift, const float* V, cudaStream_t s) {
   const size_t N = (size_t)e->n * e->n * e->n;
   k_ham_apply<<<ham_grid(nb, e->n), ham_block(e->n), 0, s>>>(f, nb, e->n, (float)(1.0 / (12.0 * e->h * e->h)), V,
-                                                              shift, out);
+                                                              shift, e->mask, out);
   int rc = ecuda(e, cudaGetLastError(), "hamiltonian");
   if (rc || !V || e->xmode == 0) return rc;
   if (e->xmode == 1) {
@@ -862,6 +872,10 @@ int rsx_eig_init(rsx_eig* e, const float* psi0, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   const size_t N = (size_t)e->n * e->n * e->n;
   int rc = ecuda(e, cudaMemcpyAsync(e->B, psi0, e->k * N * sizeof(float), cudaMemcpyDeviceToDevice, s), "init copy");
+  if (!rc && e->mask) {
+    k_mask_rows<<<dim3((unsigned)row_blocks(N, e->k), e->k), 256, 0, s>>>(e->B, e->mask, N);
+    rc = ecuda(e, cudaGetLastError(), "init mask");
+  }
   if (!rc) rc = ham(e, e->B, e->k, e->HB, nullptr, e->V, s);
   e->has_p = false;
   if (!rc) rc = rr_update(e, e->k, false, s);
@@ -913,6 +927,7 @@ int rsx_eig_step(rsx_eig* e, rsx_net* net, int jacobi_sweeps, double* theta_host
     float* wl = e->B + (size_t)m * N;
     rc = rsx_net_forward(net, e->xnet, k, e->n, e->n, e->n, wl, s);
     if (rc) return efail(e, rc, "learned preconditioner forward failed");
+    if (e->mask) k_mask_rows<<<dim3((unsigned)row_blocks(N, k), k), 256, 0, s>>>(wl, e->mask, N);
     m += k;
   }
   // normalise the W blocks, apply H to them
@@ -954,6 +969,14 @@ int rsx_eig_set_exchange(rsx_eig* e, rsx_ctx* ctx, const float* src, int count, 
   e->xsrc = mode ? src : nullptr;
   e->xcount = mode ? count : 0;
   e->xctx = ctx;
+  return RSX_OK;
+}
+
+// Spherical domain: H restricted to the points where mask (caller's [N], 0 or 1) is 1;
+// the next rsx_eig_init masks the starting orbitals.  NULL restores the whole box.
+int rsx_eig_set_mask(rsx_eig* e, const float* mask) {
+  if (!e) return RSX_EINVAL;
+  e->mask = mask;
   return RSX_OK;
 }
 
@@ -1173,7 +1196,7 @@ int rsx_scf_step(rsx_scf* c, int inner, double* out_host, void* stream) {
   rc = rsx_poisson(c->ctx, rho_e, c->vh, stream);
   if (rc) return sfail(c, rc, "Poisson (energy) failed");
   k_ham_apply<<<ham_grid(k, c->n), ham_block(c->n), 0, s>>>(phi_e, k, c->n, (float)(1.0 / (12.0 * c->h * c->h)), c->vext,
-                                                          nullptr, c->hphi);
+                                                          nullptr, c->eig->mask, c->hphi);
   rc = scf_gram(c, phi_e, k, c->hphi, k, c->dsm + 1024, s);
   if (!rc) rc = scf_gram(c, rho_e, 1, c->vh, 1, c->dsm + 2048, s);
   if (rc) return rc;
@@ -1210,6 +1233,12 @@ int rsx_scf_step(rsx_scf* c, int inner, double* out_host, void* stream) {
   out_host[5] = ts;
   ++c->iter;
   return RSX_OK;
+}
+
+// Spherical domain for the SCF orbitals (see rsx_eig_set_mask); before rsx_scf_init.
+int rsx_scf_set_mask(rsx_scf* c, const float* mask) {
+  if (!c) return RSX_EINVAL;
+  return rsx_eig_set_mask(c->eig, mask);
 }
 
 // What Eq. 14 mixes: 0 the density (default), 1 the states.  Before the first step only.

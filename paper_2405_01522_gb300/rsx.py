@@ -50,11 +50,13 @@ SIGNATURES = {
     "rsx_eig_last_error": [_P],
     "rsx_eig_destroy": [_P],
     "rsx_eig_set_exchange": [_P, _P, _P, _I, _I],
+    "rsx_eig_set_mask": [_P, _P],
     "rsx_eig_refresh": [_P, ctypes.POINTER(_D), _P],
     "rsx_scf_create": [ctypes.POINTER(_P), _P, _P, _I, _I, ctypes.c_float],
     "rsx_scf_init": [_P, _P, _P],
     "rsx_scf_step": [_P, _I, ctypes.POINTER(_D), _P],
     "rsx_scf_set_mixing": [_P, _I],
+    "rsx_scf_set_mask": [_P, _P],
     "rsx_scf_orbitals": [_P, _P, _P],
     "rsx_scf_last_error": [_P],
     "rsx_scf_destroy": [_P],
@@ -484,6 +486,11 @@ class Eigensolver:
         self._check(self.lib.rsx_eig_set_exchange(self.handle, ctx.handle if ctx is not None else None,
                                                   _ptr(src), int(count), int(mode)))
 
+    def set_mask(self, mask=None):
+        """Spherical domain: H restricted to mask == 1 (device float32 [n, n, n]); None clears."""
+        self._mask = mask                     # the library keeps the pointer
+        self._check(self.lib.rsx_eig_set_mask(self.handle, _ptr(mask)))
+
     def refresh(self, stream=None):
         th = (ctypes.c_double * self.nband)()
         self._check(self.lib.rsx_eig_refresh(self.handle, th, _stream(stream)))
@@ -519,7 +526,7 @@ class SCF:
 
     FIELDS = ("energy", "one_body", "hartree", "exchange", "reldens", "theta_sum")
 
-    def __init__(self, ctx, v_ext, nocc, ace=True, alpha=0.3, mix="density"):
+    def __init__(self, ctx, v_ext, nocc, ace=True, alpha=0.3, mix="density", mask=None):
         self.lib = load()
         self.ctx = ctx                        # kept alive: the library holds both pointers
         self.v_ext = v_ext
@@ -531,6 +538,9 @@ class SCF:
             raise RsxError(code, "rsx_scf_create failed")
         self.handle = h_
         self.mix = mix
+        self.mask = mask                      # the library keeps the pointer
+        if mask is not None:
+            self._check(self.lib.rsx_scf_set_mask(self.handle, _ptr(mask)))
 
     def _check(self, code):
         if code != RSX_OK:

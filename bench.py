@@ -412,8 +412,9 @@ def run_rsx(args, rank, local_rank, world):
     if rank == 0 and not args.skip_precond:
         out["learned_precond"] = precond_bench(args, dev, local_rank)
 
-    # ---- HF SCF time per iteration with and without ACE, rank 0
+    # ---- plain eigensolver step and HF SCF time per iteration with and without ACE, rank 0
     if rank == 0 and not args.skip_scf:
+        out["eigensolver"] = eig_bench(args, dev)
         out["scf"] = scf_bench(args, dev)
 
     # ---- CPU oracle baseline (rank 0, N = 1 only)
@@ -488,6 +489,30 @@ def casida_bench(args, dev, local_rank, peaks):
     torch.cuda.synchronize()
     spectrum_ms = ef[0].elapsed_time(ef[1])
     full_ms = ef[2].elapsed_time(ef[3])
+    # spin-polarised form: alpha 8 occupied + 64 virtual, beta the first 7 occupied + the
+    # same virtuals (one electron removed), 960 transitions in one panel
+    nta, ntb = 8 * 64, 7 * 64
+    Ku = torch.empty((nta + ntb, nta + ntb), dtype=torch.float64, device=dev)
+    pob = po[:7].contiguous()
+    c32.casida_K_uhf(po, pv, pob, pv, K=Ku)
+    Kda, Kdb = c32.casida_Kd(po, pv), c32.casida_Kd(pob, pv)
+    c32.casida_solve_uhf(eo, ev, eo[:7].contiguous(), ev, Ku, Kda, Kdb, nroots=10)
+    torch.cuda.synchronize()
+    eu = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    eu[0].record()
+    c32.casida_K_uhf(po, pv, pob, pv, K=Ku)
+    eu[1].record()
+    eu[2].record()
+    wu = c32.casida_solve_uhf(eo, ev, eo[:7].contiguous(), ev, Ku, Kda, Kdb, nroots=10)
+    eu[3].record()
+    torch.cuda.synchronize()
+    nbu = (nta + ntb + 127) // 128
+    exec_u = 3 * (nbu * (nbu + 1) // 2) * 2.0 * 128 * 128 * ng
+    uhf = {"what": "spin-polarised TDA (Eqs. 4-5): alpha 8 occ + 64 virt, beta 7 occ + 64 virt, 960 transitions; "
+                   "K over both spins from one split-BF16 panel, A = diag + K - blockdiag(K_d), lowest 10 roots",
+           "K_ms": round(eu[0].elapsed_time(eu[1]), 3), "eigensolve_ms": round(eu[2].elapsed_time(eu[3]), 3),
+           "executed_tflop": round(exec_u / 1e12, 3),
+           "omega_ev": [round(float(x) * 27.211386245988, 6) for x in wu]}
     out = {"workload": "TDA coupling K, 80^3 box at h=0.25 bohr padded to 160^3, 8 occupied + 64 virtual "
                        "orthonormal Gaussian-sum orbitals, 512 transitions, K via split-BF16 tcgen05 "
                        "(hi.hi + hi.lo + lo.hi), lowest 10 roots of diag(de) + K",
@@ -497,6 +522,7 @@ def casida_bench(args, dev, local_rank, peaks):
                         "f": [round(float(x), 6) for x in f32], "S_max": round(float(S.max()), 3)},
            "full_tdhf": {"ms": round(full_ms, 3), "omega_ev": [round(float(x) * 27.211386245988, 6) for x in wfull],
                          "what": "A and B (Eqs. 3-5), half-size form by FP64 Cholesky, lowest 10 roots"},
+           "uhf": uhf,
            "useful_tflops": round(useful / (gemm_ms / 1e3) / 1e12, 1),
            "kernels": {k: {"ms_per_launch": round(v[0] / v[1], 4), "launches": v[1]} for k, v in prof.items()},
            "roofline": {"kernel": "k_syrk_bf16x3 (tcgen05)", "bound": "tensor",
@@ -652,6 +678,30 @@ def precond_bench(args, dev, local_rank):
             "total_s": round(time.perf_counter() - t_all, 1)}
 
 
+def eig_bench(args, dev, warm=4, steps=10):
+    """Plain block eigensolver step (LOBPCG with the kinetic-energy preconditioner) on a 96^3
+    box at h = 0.2 with 16 bands of -1/2 Lap(FD4) + V (8 model atoms, Z = 4): time per step
+    and the per-kernel split of one step."""
+    from paper_2405_01522_gb300 import rsx
+    n, h, nb = args.scf_edge, 0.2, 16
+    v = torch.from_numpy(inputs.model_potential(n=n, h=h, natoms=8, Z=4.0, rc=0.6, radius=3.0, seed=41)).float().to(dev)
+    psi0 = torch.from_numpy(inputs.starting_orbitals(n=n, h=h, nband=nb, radius=3.0, seed=42)).float().to(dev)
+    es = rsx.Eigensolver(v, h, nb, device=dev.index or 0)
+    es.init(psi0)
+    for _ in range(warm):
+        es.step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        th = es.step()
+    torch.cuda.synchronize()
+    ms = (time.perf_counter() - t0) / steps * 1e3
+    es.close()
+    return {"workload": f"{n}^3 box at h=0.2, 16 bands, LOBPCG [Psi | W | P] with 3 damped-Jacobi sweeps of "
+                        "(K + T)^-1, one-CTA FP64 Rayleigh-Ritz", "ms_per_step": round(ms, 3),
+            "energy_ha": float(sum(th)), "steps_timed": steps}
+
+
 def scf_bench(args, dev, iters=10, inner=2, max_iter=300):
     """Closed-shell HF SCF on a 96^3 box at h = 0.2 with 16 doubly occupied orbitals (8 model
     atoms, Z = 4): wall time per SCF iteration over the first `iters` iterations with the
@@ -756,6 +806,8 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (default knobs)")
     ap.add_argument("--skip-precond", action="store_true")
     ap.add_argument("--skip-scf", action="store_true")
+    ap.add_argument("--eig-only", action="store_true", help="only the plain eigensolver step (profiling captures)")
+    ap.add_argument("--scf-only", action="store_true", help="only the SCF section")
     ap.add_argument("--scf-edge", type=int, default=96)
     ap.add_argument("--precond-only", action="store_true")
     ap.add_argument("--precond-edge", type=int, default=96)
@@ -781,6 +833,14 @@ def main():
         dev = torch.device("cuda", local_rank)
         torch.cuda.set_device(dev)
         print(json.dumps({"learned_precond": precond_bench(args, dev, local_rank)}), flush=True)
+    elif args.eig_only:
+        dev = torch.device("cuda", local_rank)
+        torch.cuda.set_device(dev)
+        print(json.dumps({"eigensolver": eig_bench(args, dev)}), flush=True)
+    elif args.scf_only:
+        dev = torch.device("cuda", local_rank)
+        torch.cuda.set_device(dev)
+        print(json.dumps({"scf": scf_bench(args, dev)}), flush=True)
     elif args.casida_only:
         dev = torch.device("cuda", local_rank)
         torch.cuda.set_device(dev)

@@ -203,10 +203,10 @@ __device__ __forceinline__ double cta_sum_partials(const double* part, unsigned 
   __syncthreads();
   if (lane == 0) red[warp] = v;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w = 0; w < nwarp; ++w) t += red[w];
-    *out_sh = t;
+  if (warp == 0) {   // a shuffle tree, not a serial chain of dependent FP64 adds
+    double t = lane < nwarp ? red[lane] : 0.0;
+    t = warp_sum(t);
+    if (lane == 0) *out_sh = t;
   }
   __syncthreads();
   return *out_sh;
@@ -254,8 +254,10 @@ __global__ void __launch_bounds__(256) k_tridiag_coop(double* __restrict__ A, in
         sh_beta = alpha;
         sh_scale = 0.0;
       } else {
-        const double beta = -copysign(sqrt(alpha * alpha + xn2), alpha);
-        sh_tau = (beta - alpha) / beta;
+        // beta = -sign(alpha) |x|, tau = 1 + |alpha| / |x|: one rsqrt, one division
+        const double s2 = alpha * alpha + xn2, rs = rsqrt(s2);
+        const double beta = -copysign(s2 * rs, alpha);
+        sh_tau = 1.0 + fabs(alpha) * rs;
         sh_scale = 1.0 / (alpha - beta);
         sh_beta = beta;
       }
@@ -283,9 +285,14 @@ __global__ void __launch_bounds__(256) k_tridiag_coop(double* __restrict__ A, in
       for (int i = first_owned(m0, cta, G); i < n; i += G, ++r) {
         if (r % nwarp != warp) continue;
         const double* row = A + (size_t)i * n;
-        double acc = 0.0;
-        for (int j = m0 + lane; j < n; j += 32) acc += row[j] * vs[j];
-        acc = warp_sum(acc);
+        double a0 = 0.0, a1 = 0.0;   // two chains
+        int j = m0 + lane;
+        for (; j + 32 < n; j += 64) {
+          a0 += row[j] * vs[j];
+          a1 += row[j + 32] * vs[j + 32];
+        }
+        if (j < n) a0 += row[j] * vs[j];
+        const double acc = warp_sum(a0 + a1);
         const double pi = tk * acc;
         if (lane == 0) {
           pp[i] = pi;
@@ -295,10 +302,9 @@ __global__ void __launch_bounds__(256) k_tridiag_coop(double* __restrict__ A, in
     }
     if (lane == 0) red[warp] = pv_part;
     __syncthreads();
-    if (threadIdx.x == 0) {
-      double t = 0.0;
-      for (int w = 0; w < nwarp; ++w) t += red[w];
-      part_pv[cta] = t;
+    if (warp == 0) {
+      const double t = warp_sum(lane < nwarp ? red[lane] : 0.0);
+      if (lane == 0) part_pv[cta] = t;
     }
     if (!(live = grid_barrier(gb, G))) break;
     // ---- w = p - (tau/2)(p^T v) v ; A22 -= v w^T + w v^T on own rows; next column norm
@@ -333,10 +339,9 @@ __global__ void __launch_bounds__(256) k_tridiag_coop(double* __restrict__ A, in
     }
     if (lane == 0) red[warp] = nrm_part;
     __syncthreads();
-    if (threadIdx.x == 0) {
-      double t = 0.0;
-      for (int w = 0; w < nwarp; ++w) t += red[w];
-      part_norm[cta] = t;
+    if (warp == 0) {
+      const double t = warp_sum(lane < nwarp ? red[lane] : 0.0);
+      if (lane == 0) part_norm[cta] = t;
     }
     live = grid_barrier(gb, G);
   }
@@ -389,14 +394,17 @@ __global__ void __launch_bounds__(kClThreads) k_tridiag_cluster(double* __restri
     R[q] = A[(size_t)grow(li) * lda + j];
   }
   __syncthreads();
-  // block-wide sum of one value per thread, result to thread 0
+  // block-wide sum of one value per thread, result to thread 0 (trees throughout: a
+  // dependent FP64 add costs hundreds of cycles on this part)
   auto block_sum0 = [&](double x) {
     for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
     if (lane == 0) red[warp] = x;
     __syncthreads();
     double t = 0.0;
-    if (tid == 0)
-      for (int w = 0; w < nw; ++w) t += red[w];
+    if (warp == 0) {
+      t = lane < nw ? red[lane] : 0.0;
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    }
     __syncthreads();
     return t;
   };
@@ -419,25 +427,30 @@ __global__ void __launch_bounds__(kClThreads) k_tridiag_cluster(double* __restri
   cl.sync();
   for (int k = 0; k + 2 < n; ++k) {
     const int m0 = k + 1;
-    if (tid == 0) {
-      double xn2 = 0.0;
-      for (int c = 0; c < CS; ++c) xn2 += part[c];
-      const double alpha = *alpha_sl;
-      if (xn2 == 0.0) {
-        sh_tau = 0.0;
-        sh_beta = alpha;
-        sh_scale = 0.0;
-      } else {
-        const double beta = -copysign(sqrt(alpha * alpha + xn2), alpha);
-        sh_tau = (beta - alpha) / beta;
-        sh_scale = 1.0 / (alpha - beta);
-        sh_beta = beta;
+    if (warp == 0) {
+      double xn2 = lane < CS ? part[lane] : 0.0;
+      for (int o = 16; o > 0; o >>= 1) xn2 += __shfl_xor_sync(0xffffffffu, xn2, o);
+      if (lane == 0) {
+        const double alpha = *alpha_sl;
+        if (xn2 == 0.0) {
+          sh_tau = 0.0;
+          sh_beta = alpha;
+          sh_scale = 0.0;
+        } else {
+          // beta = -sign(alpha) |x|, tau = (beta - alpha) / beta = 1 + |alpha| / |x|:
+          // one reciprocal square root and one division
+          const double s2 = alpha * alpha + xn2, rs = rsqrt(s2);
+          const double beta = -copysign(s2 * rs, alpha);
+          sh_tau = 1.0 + fabs(alpha) * rs;
+          sh_scale = 1.0 / (alpha - beta);
+          sh_beta = beta;
+        }
+        if (me == 0) {
+          e[k] = sh_beta;
+          tau[k] = sh_tau;
+        }
+        if (k % CS == me) d[k] = R[(size_t)(k / CS) * n + k];
       }
-      if (me == 0) {
-        e[k] = sh_beta;
-        tau[k] = sh_tau;
-      }
-      if (k % CS == me) d[k] = R[(size_t)(k / CS) * n + k];
     }
     __syncthreads();
     const double tk = sh_tau, sc = sh_scale;
@@ -461,8 +474,14 @@ __global__ void __launch_bounds__(kClThreads) k_tridiag_cluster(double* __restri
         const int i = grow(li);
         if (i < m0) continue;
         const double* row = R + (size_t)li * n;
-        double acc = 0.0;
-        for (int j = m0 + lane; j < n; j += 32) acc += row[j] * v[j];
+        double a0 = 0.0, a1 = 0.0;   // two chains
+        int j = m0 + lane;
+        for (; j + 32 < n; j += 64) {
+          a0 += row[j] * v[j];
+          a1 += row[j + 32] * v[j + 32];
+        }
+        if (j < n) a0 += row[j] * v[j];
+        double acc = a0 + a1;
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         const double pi = tk * acc;
         if (lane < CS) *cl.map_shared_rank(p + i, lane) = pi;
@@ -474,8 +493,8 @@ __global__ void __launch_bounds__(kClThreads) k_tridiag_cluster(double* __restri
       if (tid < CS) *cl.map_shared_rank(part2 + me, tid) = red[0];
       cl.sync();
       // w = p - (tau/2)(p^T v) v, rank-2 update of own rows
-      double pvs = 0.0;
-      for (int c = 0; c < CS; ++c) pvs += part2[c];
+      double pvs = lane < CS ? part2[lane] : 0.0;   // every warp reduces the CS partials
+      for (int o = 16; o > 0; o >>= 1) pvs += __shfl_xor_sync(0xffffffffu, pvs, o);
       const double cc = 0.5 * tk * pvs;
       for (int j = m0 + tid; j < n; j += kClThreads) p[j] -= cc * v[j];
       __syncthreads();

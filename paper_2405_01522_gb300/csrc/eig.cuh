@@ -60,20 +60,24 @@ __device__ inline void tri_factor_shifted(const R* d, const R* e, int n, R lam, 
     u1[i] = i < n - 1 ? e[i] : R(0);
     u2[i] = R(0);
   }
+  // one division per step: the pivot's reciprocal, which the solves use as well
   for (int i = 0; i < n - 1; ++i) {
     const R sub = e[i];
     if (fabs(dg[i]) >= fabs(sub)) {
       piv[i] = 0;
       if (dg[i] == R(0)) dg[i] = eps_shift;
-      const R l = sub / dg[i];
+      const R r = R(1) / dg[i];
+      const R l = sub * r;
       lw[i] = l;
       dg[i + 1] -= l * u1[i];
+      dg[i] = r;
     } else {
       piv[i] = 1;
-      const R l = dg[i] / sub;
+      const R r = R(1) / sub;
+      const R l = dg[i] * r;
       lw[i] = l;
       const R t0 = dg[i + 1], t1 = (i + 1 < n - 1) ? u1[i + 1] : R(0);
-      dg[i] = sub;
+      dg[i] = r;
       const R old_u1 = u1[i];
       u1[i] = t0;
       u2[i] = t1;
@@ -82,7 +86,7 @@ __device__ inline void tri_factor_shifted(const R* d, const R* e, int n, R lam, 
     }
   }
   if (dg[n - 1] == R(0)) dg[n - 1] = eps_shift;
-  for (int i = 0; i < n; ++i) dg[i] = R(1) / dg[i];   // solves multiply by the reciprocals
+  dg[n - 1] = R(1) / dg[n - 1];   // dg now holds the reciprocal pivots the solves multiply by
 }
 
 // z <- (T - lam I)^{-1} z with the factors of tri_factor_shifted (serial, one thread)

@@ -187,21 +187,6 @@ constexpr double kRrDrop = 1e-6;
 constexpr int kRrThreads = 512;
 constexpr int kRrWarps = kRrThreads / 32;
 
-__device__ double rr_block_sum(double v, double* red) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  __syncthreads();
-  if (lane == 0) red[warp] = v;
-  __syncthreads();
-  if (warp == 0) {
-    double t = lane < kRrWarps ? red[lane] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    if (lane == 0) red[32] = t;
-  }
-  __syncthreads();
-  return red[32];
-}
-
 __global__ void __launch_bounds__(kRrThreads) k_rayleigh_ritz(const double* __restrict__ Sg, const double* __restrict__ Hg,
                                                               int m, int k, double* __restrict__ theta,
                                                               float* __restrict__ qt, int* status) {
@@ -211,7 +196,6 @@ __global__ void __launch_bounds__(kRrThreads) k_rayleigh_ritz(const double* __re
   double* C = Li + m * m;
   double* T = C + m * m;
   double* SCR = T + m * m;
-  __shared__ double red[33];
   __shared__ double dg0[kMaxBasis], dd[kMaxBasis], ee[kMaxBasis], tau[kMaxBasis], vv[kMaxBasis], pp[kMaxBasis];
   __shared__ double lam[kMaxBasis];
   __shared__ float d32[kMaxBasis], e32[kMaxBasis], e2f[kMaxBasis], lam32[kMaxBasis];
@@ -308,24 +292,28 @@ __global__ void __launch_bounds__(kRrThreads) k_rayleigh_ritz(const double* __re
   // 3. Householder tridiagonalisation of C' (n x n, leading dimension n)
   for (int kk = 0; kk + 2 < n; ++kk) {
     const int m0 = kk + 1;
-    double s = 0.0;
-    for (int i = m0 + 1 + tid; i < n; i += kRrThreads) s += C[i * n + kk] * C[i * n + kk];
-    const double xn2 = rr_block_sum(s, red);
-    if (tid == 0) {
-      const double alpha = C[m0 * n + kk];
-      if (xn2 == 0.0) {
-        sh_tau = 0.0;
-        sh_beta = alpha;
-        sh_scale = 0.0;
-      } else {
-        const double beta = -copysign(sqrt(alpha * alpha + xn2), alpha);
-        sh_tau = (beta - alpha) / beta;
-        sh_scale = 1.0 / (alpha - beta);
-        sh_beta = beta;
+    if (warp == 0) {   // |x|^2 below the subdiagonal (n <= 64: two entries per lane)
+      double s = 0.0;
+      for (int i = m0 + 1 + lane; i < n; i += 32) s += C[i * n + kk] * C[i * n + kk];
+      const double xn2 = warp_sum(s);
+      if (lane == 0) {
+        const double alpha = C[m0 * n + kk];
+        if (xn2 == 0.0) {
+          sh_tau = 0.0;
+          sh_beta = alpha;
+          sh_scale = 0.0;
+        } else {
+          // beta = -sign(alpha) |x|, tau = 1 + |alpha| / |x|: one rsqrt, one division
+          const double s2 = alpha * alpha + xn2, rs = rsqrt(s2);
+          const double beta = -copysign(s2 * rs, alpha);
+          sh_tau = 1.0 + fabs(alpha) * rs;
+          sh_scale = 1.0 / (alpha - beta);
+          sh_beta = beta;
+        }
+        ee[kk] = sh_beta;
+        tau[kk] = sh_tau;
+        dd[kk] = C[kk * n + kk];
       }
-      ee[kk] = sh_beta;
-      tau[kk] = sh_tau;
-      dd[kk] = C[kk * n + kk];
     }
     __syncthreads();
     const double tk = sh_tau;
@@ -347,10 +335,12 @@ __global__ void __launch_bounds__(kRrThreads) k_rayleigh_ritz(const double* __re
         if (g == 0 && i < n) pp[i] = tk * acc;
       }
       __syncthreads();
-      double pv = 0.0;
-      for (int i = m0 + tid; i < n; i += kRrThreads) pv += pp[i] * vv[i];
-      const double cc = 0.5 * tk * rr_block_sum(pv, red);
-      for (int i = m0 + tid; i < n; i += kRrThreads) pp[i] -= cc * vv[i];
+      if (warp == 0) {   // w = p - (tau/2)(p^T v) v over the trailing rows
+        double pv = 0.0;
+        for (int i = m0 + lane; i < n; i += 32) pv += pp[i] * vv[i];
+        const double cc = 0.5 * tk * warp_sum(pv);
+        for (int i = m0 + lane; i < n; i += 32) pp[i] -= cc * vv[i];
+      }
       __syncthreads();
       const int t = n - m0;
       for (int q = tid; q < t * t; q += kRrThreads) {

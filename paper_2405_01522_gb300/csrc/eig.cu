@@ -189,14 +189,30 @@ __device__ __forceinline__ bool grid_barrier(GridBar* gb, unsigned int nblocks) 
 // read with __ldcg, which bypasses the non-coherent L1)
 __device__ __forceinline__ int first_owned(int r0, int c, int G) { return r0 + ((c - r0) % G + G) % G; }
 
-__device__ __forceinline__ double warp_sum(double v) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
+// precision traits of the reduction and root-finding kernels (F = double, or float for
+// the first, FP32 stage of the mixed-precision eigensolver)
+template <typename F> struct Prec;
+template <> struct Prec<double> {
+  static constexpr double eps = 2.220446049250313e-16, tiny = 1e-300, gap = 1e-6;
+};
+template <> struct Prec<float> {
+  static constexpr float eps = 1.1920929e-7f, tiny = 1e-30f, gap = 1e-5f;
+};
+__device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
+__device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
+// Sturm count: division-free minors recurrence in FP64, the pivot ratio form in FP32
+__device__ __forceinline__ int sturm_cnt(const double* d, const double* e2, int n, double x, double) {
+  return sturm_count_prod(d, e2, n, x);
+}
+__device__ __forceinline__ int sturm_cnt(const float* d, const float* e2, int n, float x, float pivmin) {
+  return sturm_count_f32(d, e2, n, x, pivmin);
 }
 
+
 // sum of the G per-CTA partials, by the whole CTA (one L2 round trip, shuffle reduction)
-__device__ __forceinline__ double cta_sum_partials(const double* part, unsigned int G, double* red, double* out_sh) {
-  double v = 0.0;
+template <typename F>
+__device__ __forceinline__ F cta_sum_partials(const F* part, unsigned int G, F* red, F* out_sh) {
+  F v = F(0);
   for (unsigned int c = threadIdx.x; c < G; c += blockDim.x) v += __ldcg(part + c);
   v = warp_sum(v);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
@@ -204,7 +220,7 @@ __device__ __forceinline__ double cta_sum_partials(const double* part, unsigned 
   if (lane == 0) red[warp] = v;
   __syncthreads();
   if (warp == 0) {   // a shuffle tree, not a serial chain of dependent FP64 adds
-    double t = lane < nwarp ? red[lane] : 0.0;
+    F t = lane < nwarp ? red[lane] : F(0);
     t = warp_sum(t);
     if (lane == 0) *out_sh = t;
   }
@@ -212,28 +228,30 @@ __device__ __forceinline__ double cta_sum_partials(const double* part, unsigned 
   return *out_sh;
 }
 
-// scratch layout (doubles): v[n], p[n], part_norm[G], part_pv[G], alpha
-__global__ void __launch_bounds__(256) k_tridiag_coop(double* __restrict__ A, int n, double* __restrict__ d,
-                                                      double* __restrict__ e, double* __restrict__ tau,
-                                                      double* __restrict__ scr, GridBar* gb, int* status) {
+// scratch layout (Fs): v[n], p[n], part_norm[G], part_pv[G], alpha
+template <typename F>
+__global__ void __launch_bounds__(256) k_tridiag_coop(F* __restrict__ A, int n, F* __restrict__ d,
+                                                      F* __restrict__ e, F* __restrict__ tau,
+                                                      F* __restrict__ scr, GridBar* gb, int* status) {
   const unsigned int G = gridDim.x;
   const int cta = blockIdx.x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
-  double* vv = scr;
-  double* pp = scr + n;
-  double* part_norm = scr + 2 * n;
-  double* part_pv = part_norm + G;
-  double* alpha_g = part_pv + G;
-  extern __shared__ double tri_smem[];   // local copies of v and p (2 n doubles)
-  double* vs = tri_smem;
-  double* ps = tri_smem + n;
-  __shared__ double red[8];
-  __shared__ double sh_tau, sh_beta, sh_scale, sh_sum;
+  F* vv = scr;
+  F* pp = scr + n;
+  F* part_norm = scr + 2 * n;
+  F* part_pv = part_norm + G;
+  F* alpha_g = part_pv + G;
+  extern __shared__ __align__(16) unsigned char tri_smem_raw[];   // local copies of v and p (2 n values)
+  F* tri_smem = reinterpret_cast<F*>(tri_smem_raw);
+  F* vs = tri_smem;
+  F* ps = tri_smem + n;
+  __shared__ F red[8];
+  __shared__ F sh_tau, sh_beta, sh_scale, sh_sum;
   bool live = true;
 
   // norm partials of column 0 below the subdiagonal, alpha of column 0
   {
-    double s = 0.0;
+    F s = F(0);
     for (int i = first_owned(2, cta, G); i < n; i += G)
       if (threadIdx.x == 0) s += A[(size_t)i * n] * A[(size_t)i * n];
     if (threadIdx.x == 0) {
@@ -246,19 +264,19 @@ __global__ void __launch_bounds__(256) k_tridiag_coop(double* __restrict__ A, in
   for (int k = 0; k + 2 < n && live; ++k) {
     const int m0 = k + 1;
     // ---- reflector (every CTA computes the same scalars)
-    const double xn2 = cta_sum_partials(part_norm, G, red, &sh_sum);
+    const F xn2 = cta_sum_partials(part_norm, G, red, &sh_sum);
     if (threadIdx.x == 0) {
-      const double alpha = __ldcg(alpha_g);
-      if (xn2 == 0.0) {
-        sh_tau = 0.0;
+      const F alpha = __ldcg(alpha_g);
+      if (xn2 == F(0)) {
+        sh_tau = F(0);
         sh_beta = alpha;
-        sh_scale = 0.0;
+        sh_scale = F(0);
       } else {
         // beta = -sign(alpha) |x|, tau = 1 + |alpha| / |x|: one rsqrt, one division
-        const double s2 = alpha * alpha + xn2, rs = rsqrt(s2);
-        const double beta = -copysign(s2 * rs, alpha);
-        sh_tau = 1.0 + fabs(alpha) * rs;
-        sh_scale = 1.0 / (alpha - beta);
+        const F s2 = alpha * alpha + xn2, rs = rsq(s2);
+        const F beta = -copysign(s2 * rs, alpha);
+        sh_tau = F(1) + fabs(alpha) * rs;
+        sh_scale = F(1) / (alpha - beta);
         sh_beta = beta;
       }
       if (cta == 0) {
@@ -268,32 +286,32 @@ __global__ void __launch_bounds__(256) k_tridiag_coop(double* __restrict__ A, in
       if (k % (int)G == cta) d[k] = A[(size_t)k * n + k];
     }
     __syncthreads();
-    const double tk = sh_tau, sc = sh_scale;
+    const F tk = sh_tau, sc = sh_scale;
     // own rows: v_i, stored in the column for the back-transformation
     for (int i = first_owned(m0, cta, G) + (int)G * threadIdx.x; i < n; i += (int)G * blockDim.x) {
-      const double vi = (i == m0) ? 1.0 : A[(size_t)i * n + k] * sc;
+      const F vi = (i == m0) ? F(1) : A[(size_t)i * n + k] * sc;
       vv[i] = vi;
       if (i > m0) A[(size_t)i * n + k] = vi;
     }
     if (!(live = grid_barrier(gb, G))) break;
     // ---- p_i = tau (A22 v)_i for own rows, partial p^T v
-    double pv_part = 0.0;
-    if (tk != 0.0) {
+    F pv_part = F(0);
+    if (tk != F(0)) {
       for (int j = m0 + threadIdx.x; j < n; j += blockDim.x) vs[j] = __ldcg(vv + j);
       __syncthreads();
       int r = 0;
       for (int i = first_owned(m0, cta, G); i < n; i += G, ++r) {
         if (r % nwarp != warp) continue;
-        const double* row = A + (size_t)i * n;
-        double a0 = 0.0, a1 = 0.0;   // two chains
+        const F* row = A + (size_t)i * n;
+        F a0 = F(0), a1 = F(0);   // two chains
         int j = m0 + lane;
         for (; j + 32 < n; j += 64) {
           a0 += row[j] * vs[j];
           a1 += row[j + 32] * vs[j + 32];
         }
         if (j < n) a0 += row[j] * vs[j];
-        const double acc = warp_sum(a0 + a1);
-        const double pi = tk * acc;
+        const F acc = warp_sum(a0 + a1);
+        const F pi = tk * acc;
         if (lane == 0) {
           pp[i] = pi;
           pv_part += pi * vs[i];
@@ -303,27 +321,27 @@ __global__ void __launch_bounds__(256) k_tridiag_coop(double* __restrict__ A, in
     if (lane == 0) red[warp] = pv_part;
     __syncthreads();
     if (warp == 0) {
-      const double t = warp_sum(lane < nwarp ? red[lane] : 0.0);
+      const F t = warp_sum(lane < nwarp ? red[lane] : F(0));
       if (lane == 0) part_pv[cta] = t;
     }
     if (!(live = grid_barrier(gb, G))) break;
     // ---- w = p - (tau/2)(p^T v) v ; A22 -= v w^T + w v^T on own rows; next column norm
-    double nrm_part = 0.0;
-    if (tk != 0.0) {
-      const double pvs = cta_sum_partials(part_pv, G, red, &sh_sum);
-      const double cc = 0.5 * tk * pvs;
+    F nrm_part = F(0);
+    if (tk != F(0)) {
+      const F pvs = cta_sum_partials(part_pv, G, red, &sh_sum);
+      const F cc = F(0.5) * tk * pvs;
       for (int j = m0 + threadIdx.x; j < n; j += blockDim.x) ps[j] = __ldcg(pp + j) - cc * vs[j];   // w
       __syncthreads();
       int r = 0;
       for (int i = first_owned(m0, cta, G); i < n; i += G, ++r) {
         if (r % nwarp != warp) continue;
-        const double vi = vs[i];
-        const double wi = ps[i];
-        double* row = A + (size_t)i * n;
+        const F vi = vs[i];
+        const F wi = ps[i];
+        F* row = A + (size_t)i * n;
         for (int j = m0 + lane; j < n; j += 32) row[j] -= vi * ps[j] + wi * vs[j];
         __syncwarp();
         if (lane == 0) {
-          const double x = row[m0];   // column k + 1 of row i
+          const F x = row[m0];   // column k + 1 of row i
           if (i >= m0 + 2) nrm_part += x * x;
           if (i == m0 + 1) *alpha_g = x;
         }
@@ -332,7 +350,7 @@ __global__ void __launch_bounds__(256) k_tridiag_coop(double* __restrict__ A, in
       int r = 0;
       for (int i = first_owned(m0, cta, G); i < n; i += G, ++r) {
         if (r % nwarp != warp || lane != 0) continue;
-        const double x = A[(size_t)i * n + m0];
+        const F x = A[(size_t)i * n + m0];
         if (i >= m0 + 2) nrm_part += x * x;
         if (i == m0 + 1) *alpha_g = x;
       }
@@ -340,7 +358,7 @@ __global__ void __launch_bounds__(256) k_tridiag_coop(double* __restrict__ A, in
     if (lane == 0) red[warp] = nrm_part;
     __syncthreads();
     if (warp == 0) {
-      const double t = warp_sum(lane < nwarp ? red[lane] : 0.0);
+      const F t = warp_sum(lane < nwarp ? red[lane] : F(0));
       if (lane == 0) part_norm[cta] = t;
     }
     live = grid_barrier(gb, G);
@@ -352,7 +370,7 @@ __global__ void __launch_bounds__(256) k_tridiag_coop(double* __restrict__ A, in
       if (n >= 2) {
         d[n - 2] = __ldcg(A + (size_t)(n - 2) * n + (n - 2));
         e[n - 2] = __ldcg(A + (size_t)(n - 1) * n + (n - 2));
-        if (n >= 3) tau[n - 2] = 0.0;
+        if (n >= 3) tau[n - 2] = F(0);
       }
       d[n - 1] = __ldcg(A + (size_t)(n - 1) * n + (n - 1));
     }
@@ -371,22 +389,24 @@ __global__ void __launch_bounds__(256) k_tridiag_coop(double* __restrict__ A, in
 constexpr int kClThreads = 512;
 namespace cg = cooperative_groups;
 
-__global__ void __launch_bounds__(kClThreads) k_tridiag_cluster(double* __restrict__ A, int n, double* __restrict__ d,
-                                                                double* __restrict__ e, double* __restrict__ tau) {
+template <typename F>
+__global__ void __launch_bounds__(kClThreads) k_tridiag_cluster(F* __restrict__ A, int n, F* __restrict__ d,
+                                                                F* __restrict__ e, F* __restrict__ tau) {
   cg::cluster_group cl = cg::this_cluster();
   const int CS = (int)cl.num_blocks();
   const int me = (int)cl.block_rank();
   const int nloc = (n - me + CS - 1) / CS;          // rows me, me + CS, ...
   const int lda = n;
-  extern __shared__ double cl_smem[];
-  double* R = cl_smem;                               // [nloc][n]
-  double* v = R + (size_t)((n + CS - 1) / CS) * n;   // [n]
-  double* p = v + n;                                 // [n] (p, then w)
-  double* part = p + n;                              // [CS] norm partials, [CS] p^T v partials, alpha
-  double* part2 = part + CS;
-  double* alpha_sl = part2 + CS;
-  __shared__ double red[kClThreads / 32];
-  __shared__ double sh_tau, sh_beta, sh_scale;
+  extern __shared__ __align__(16) unsigned char cl_smem_raw[];
+  F* cl_smem = reinterpret_cast<F*>(cl_smem_raw);
+  F* R = cl_smem;                               // [nloc][n]
+  F* v = R + (size_t)((n + CS - 1) / CS) * n;   // [n]
+  F* p = v + n;                                 // [n] (p, then w)
+  F* part = p + n;                              // [CS] norm partials, [CS] p^T v partials, alpha
+  F* part2 = part + CS;
+  F* alpha_sl = part2 + CS;
+  __shared__ F red[kClThreads / 32];
+  __shared__ F sh_tau, sh_beta, sh_scale;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = kClThreads / 32;
   auto grow = [&](int li) { return me + li * CS; };
   for (size_t q = tid; q < (size_t)nloc * n; q += kClThreads) {
@@ -396,13 +416,13 @@ __global__ void __launch_bounds__(kClThreads) k_tridiag_cluster(double* __restri
   __syncthreads();
   // block-wide sum of one value per thread, result to thread 0 (trees throughout: a
   // dependent FP64 add costs hundreds of cycles on this part)
-  auto block_sum0 = [&](double x) {
+  auto block_sum0 = [&](F x) {
     for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
     if (lane == 0) red[warp] = x;
     __syncthreads();
-    double t = 0.0;
+    F t = F(0);
     if (warp == 0) {
-      t = lane < nw ? red[lane] : 0.0;
+      t = lane < nw ? red[lane] : F(0);
       for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
     }
     __syncthreads();
@@ -410,15 +430,15 @@ __global__ void __launch_bounds__(kClThreads) k_tridiag_cluster(double* __restri
   };
   // publish this CTA's partial (and alpha when it owns row m0 + 1) for column c
   auto publish_norm = [&](int c) {
-    double s = 0.0;
+    F s = F(0);
     for (int li = tid; li < nloc; li += kClThreads) {
       const int i = grow(li);
       if (i >= c + 2) s += R[(size_t)li * n + c] * R[(size_t)li * n + c];
     }
-    const double t = block_sum0(s);
+    const F t = block_sum0(s);
     if (tid == 0) red[0] = t;
     __syncthreads();
-    const double tot = red[0];
+    const F tot = red[0];
     if (tid < CS) *cl.map_shared_rank(part + me, tid) = tot;
     if ((c + 1) % CS == me && tid >= 32 && tid < 32 + CS)
       *cl.map_shared_rank(alpha_sl, tid - 32) = R[(size_t)((c + 1) / CS) * n + c];
@@ -428,21 +448,21 @@ __global__ void __launch_bounds__(kClThreads) k_tridiag_cluster(double* __restri
   for (int k = 0; k + 2 < n; ++k) {
     const int m0 = k + 1;
     if (warp == 0) {
-      double xn2 = lane < CS ? part[lane] : 0.0;
+      F xn2 = lane < CS ? part[lane] : F(0);
       for (int o = 16; o > 0; o >>= 1) xn2 += __shfl_xor_sync(0xffffffffu, xn2, o);
       if (lane == 0) {
-        const double alpha = *alpha_sl;
-        if (xn2 == 0.0) {
-          sh_tau = 0.0;
+        const F alpha = *alpha_sl;
+        if (xn2 == F(0)) {
+          sh_tau = F(0);
           sh_beta = alpha;
-          sh_scale = 0.0;
+          sh_scale = F(0);
         } else {
           // beta = -sign(alpha) |x|, tau = (beta - alpha) / beta = 1 + |alpha| / |x|:
           // one reciprocal square root and one division
-          const double s2 = alpha * alpha + xn2, rs = rsqrt(s2);
-          const double beta = -copysign(s2 * rs, alpha);
-          sh_tau = 1.0 + fabs(alpha) * rs;
-          sh_scale = 1.0 / (alpha - beta);
+          const F s2 = alpha * alpha + xn2, rs = rsq(s2);
+          const F beta = -copysign(s2 * rs, alpha);
+          sh_tau = F(1) + fabs(alpha) * rs;
+          sh_scale = F(1) / (alpha - beta);
           sh_beta = beta;
         }
         if (me == 0) {
@@ -453,13 +473,13 @@ __global__ void __launch_bounds__(kClThreads) k_tridiag_cluster(double* __restri
       }
     }
     __syncthreads();
-    const double tk = sh_tau, sc = sh_scale;
+    const F tk = sh_tau, sc = sh_scale;
     // v on own rows (stored in the column), sent to every CTA
     for (int q = tid; q < nloc * CS; q += kClThreads) {
       const int li = q / CS, dst = q - li * CS;
       const int i = grow(li);
       if (i < m0) continue;
-      const double vi = (i == m0) ? 1.0 : R[(size_t)li * n + k] * sc;
+      const F vi = (i == m0) ? F(1) : R[(size_t)li * n + k] * sc;
       *cl.map_shared_rank(v + i, dst) = vi;
     }
     cl.sync();
@@ -467,42 +487,42 @@ __global__ void __launch_bounds__(kClThreads) k_tridiag_cluster(double* __restri
       const int i = grow(li);
       if (i > m0) R[(size_t)li * n + k] = v[i];
     }
-    if (tk != 0.0) {
+    if (tk != F(0)) {
       // p_i = tau (A22 v)_i on own rows, a warp per row; p^T v partial
-      double pv = 0.0;
+      F pv = F(0);
       for (int li = warp; li < nloc; li += nw) {
         const int i = grow(li);
         if (i < m0) continue;
-        const double* row = R + (size_t)li * n;
-        double a0 = 0.0, a1 = 0.0;   // two chains
+        const F* row = R + (size_t)li * n;
+        F a0 = F(0), a1 = F(0);   // two chains
         int j = m0 + lane;
         for (; j + 32 < n; j += 64) {
           a0 += row[j] * v[j];
           a1 += row[j + 32] * v[j + 32];
         }
         if (j < n) a0 += row[j] * v[j];
-        double acc = a0 + a1;
+        F acc = a0 + a1;
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        const double pi = tk * acc;
+        const F pi = tk * acc;
         if (lane < CS) *cl.map_shared_rank(p + i, lane) = pi;
         if (lane == 0) pv += pi * v[i];
       }
-      const double t = block_sum0(pv);
+      const F t = block_sum0(pv);
       if (tid == 0) red[0] = t;
       __syncthreads();
       if (tid < CS) *cl.map_shared_rank(part2 + me, tid) = red[0];
       cl.sync();
       // w = p - (tau/2)(p^T v) v, rank-2 update of own rows
-      double pvs = lane < CS ? part2[lane] : 0.0;   // every warp reduces the CS partials
+      F pvs = lane < CS ? part2[lane] : F(0);   // every warp reduces the CS partials
       for (int o = 16; o > 0; o >>= 1) pvs += __shfl_xor_sync(0xffffffffu, pvs, o);
-      const double cc = 0.5 * tk * pvs;
+      const F cc = F(0.5) * tk * pvs;
       for (int j = m0 + tid; j < n; j += kClThreads) p[j] -= cc * v[j];
       __syncthreads();
       for (int li = warp; li < nloc; li += nw) {
         const int i = grow(li);
         if (i < m0) continue;
-        const double vi = v[i], wi = p[i];
-        double* row = R + (size_t)li * n;
+        const F vi = v[i], wi = p[i];
+        F* row = R + (size_t)li * n;
         for (int j = m0 + lane; j < n; j += 32) row[j] -= vi * p[j] + wi * v[j];
       }
       __syncthreads();
@@ -517,7 +537,7 @@ __global__ void __launch_bounds__(kClThreads) k_tridiag_cluster(double* __restri
     if (n >= 2) {
       if ((n - 2) % CS == me) d[n - 2] = R[(size_t)((n - 2) / CS) * n + (n - 2)];
       if ((n - 1) % CS == me) e[n - 2] = R[(size_t)((n - 1) / CS) * n + (n - 2)];
-      if (me == 0 && n >= 3) tau[n - 2] = 0.0;
+      if (me == 0 && n >= 3) tau[n - 2] = F(0);
     }
     if ((n - 1) % CS == me) d[n - 1] = R[(size_t)((n - 1) / CS) * n + (n - 1)];
   }
@@ -532,22 +552,24 @@ __global__ void __launch_bounds__(kClThreads) k_tridiag_cluster(double* __restri
 // Sturm count at 32 interior points of [lo, hi] (one per lane) and keeps the sub-interval
 // in which the count passes k (FP64 is scarce on this part: 32 points per root and round
 // instead of a whole CTA).
-__global__ void __launch_bounds__(32) k_multisect(const double* __restrict__ d, const double* __restrict__ e, int n,
-                                                   int nroots, double* __restrict__ w) {
-  extern __shared__ double ms_smem[];   // d (n), e^2 (n)
+template <typename F>
+__global__ void __launch_bounds__(32) k_multisect(const F* __restrict__ d, const F* __restrict__ e, int n,
+                                                   int nroots, F* __restrict__ w) {
+  extern __shared__ __align__(16) unsigned char ms_smem_raw[];   // d (n), e^2 (n)
+  F* ms_smem = reinterpret_cast<F*>(ms_smem_raw);
   const int lane = threadIdx.x & 31;
   const int k = blockIdx.x;   // one warp (CTA) per root: spread over SMs, FP64 units are scarce
   if (k >= nroots) return;
-  double* ds = ms_smem;
-  double* e2 = ms_smem + n;
+  F* ds = ms_smem;
+  F* e2 = ms_smem + n;
   for (int i = lane; i < n; i += 32) {
     ds[i] = d[i];
-    e2[i] = i < n - 1 ? e[i] * e[i] : 0.0;
+    e2[i] = i < n - 1 ? e[i] * e[i] : F(0);
   }
   __syncwarp();
-  double lo = 1e300, hi = -1e300, emax = 0.0;
+  F lo = F(1) / Prec<F>::tiny, hi = -F(1) / Prec<F>::tiny, emax = F(0);
   for (int i = lane; i < n; i += 32) {
-    const double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i < n - 1 ? fabs(e[i]) : 0.0);
+    const F r = (i > 0 ? fabs(e[i - 1]) : F(0)) + (i < n - 1 ? fabs(e[i]) : F(0));
     lo = fmin(lo, d[i] - r);
     hi = fmax(hi, d[i] + r);
     if (i < n - 1) emax = fmax(emax, fabs(e[i]));
@@ -557,74 +579,77 @@ __global__ void __launch_bounds__(32) k_multisect(const double* __restrict__ d, 
     hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
     emax = fmax(emax, __shfl_xor_sync(0xffffffffu, emax, o));
   }
-  const double scale = fmax(fabs(lo), fabs(hi));
-  lo -= 1e-12 * scale + 1e-300;
-  hi += 1e-12 * scale + 1e-300;
+  const F scale = fmax(fabs(lo), fabs(hi));
+  lo -= F(64) * Prec<F>::eps * scale + Prec<F>::tiny;
+  hi += F(64) * Prec<F>::eps * scale + Prec<F>::tiny;
+  const F pivmin = F(1.2e-38) * fmax(F(1), emax * emax);
   for (int round = 0; round < 16; ++round) {
-    if (!(hi - lo > 2.0 * 2.220446049250313e-16 * fmax(fabs(lo), fabs(hi)))) break;
-    const double x = lo + (hi - lo) * (double)(lane + 1) / 33.0;
-    const unsigned above = __ballot_sync(0xffffffffu, sturm_count_prod(ds, e2, n, x) > k);
+    if (!(hi - lo > F(2) * Prec<F>::eps * fmax(fabs(lo), fabs(hi)))) break;
+    const F x = lo + (hi - lo) * (F)(lane + 1) / F(33);
+    const unsigned above = __ballot_sync(0xffffffffu, sturm_cnt(ds, e2, n, x, pivmin) > k);
     const int f = above ? __ffs(above) - 1 : 32;
-    const double nlo = (f == 0) ? lo : lo + (hi - lo) * (double)f / 33.0;
-    const double nhi = (f == 32) ? hi : lo + (hi - lo) * (double)(f + 1) / 33.0;
+    const F nlo = (f == 0) ? lo : lo + (hi - lo) * (F)f / F(33);
+    const F nhi = (f == 32) ? hi : lo + (hi - lo) * (F)(f + 1) / F(33);
     lo = nlo;
     hi = nhi;
   }
-  if (lane == 0) w[k] = 0.5 * (lo + hi);
+  if (lane == 0) w[k] = F(0.5) * (lo + hi);
 }
 
 // Eigenvectors of T by inverse iteration, a warp per root (3 iterations from a fixed
 // start); y: [nroots][n]; scratch: 4 n doubles + n ints per root.
-__global__ void __launch_bounds__(32) k_invit(const double* __restrict__ d, const double* __restrict__ e, int n,
-                                               const double* __restrict__ w, int nroots, double* __restrict__ y,
-                                               double* __restrict__ scratch) {
+template <typename F>
+__global__ void __launch_bounds__(32) k_invit(const F* __restrict__ d, const F* __restrict__ e, int n,
+                                               const F* __restrict__ w, int nroots, F* __restrict__ y,
+                                               F* __restrict__ scratch) {
   const int lane = threadIdx.x & 31;
   const int k = blockIdx.x;   // one warp (CTA) per root: spread over SMs, FP64 units are scarce
   if (k >= nroots) return;
-  double* z = y + (size_t)k * n;
-  double* sc = scratch + (size_t)k * 5 * n;
-  for (int i = lane; i < n; i += 32) z[i] = 1.0 + 0.001 * (double)((i * 7919 + k * 104729) % 997);
+  F* z = y + (size_t)k * n;
+  F* sc = scratch + (size_t)k * 5 * n;
+  for (int i = lane; i < n; i += 32) z[i] = F(1) + F(0.001) * (F)((i * 7919 + k * 104729) % 997);
   __syncwarp();
-  warp_inverse_iteration(d, e, n, w[k], z, sc, reinterpret_cast<int*>(sc + 4 * n), 3, y, n, 0u);
+  warp_inverse_iteration<F>(d, e, n, w[k], z, sc, reinterpret_cast<int*>(sc + 4 * n), 3, y, n, 0u);
 }
 
 // Roots closer than the cluster gap to an earlier root are recomputed one after another
 // (one warp), each orthogonalised inside every iteration against the earlier roots of
 // its cluster, so that (nearly) degenerate roots get orthonormal vectors.
-__global__ void k_invit_clusters(const double* __restrict__ d, const double* __restrict__ e, int n,
-                                 const double* __restrict__ w, int nroots, double* __restrict__ y,
-                                 double* __restrict__ scratch) {
+template <typename F>
+__global__ void k_invit_clusters(const F* __restrict__ d, const F* __restrict__ e, int n,
+                                 const F* __restrict__ w, int nroots, F* __restrict__ y,
+                                 F* __restrict__ scratch) {
   const int lane = threadIdx.x & 31;
-  double s = 0.0;
+  F s = F(0);
   for (int i = lane; i < n; i += 32) s = fmax(s, fabs(d[i]));
   for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_xor_sync(0xffffffffu, s, o));
-  const double gap = 1e-6 * fmax(1.0, s);
+  const F gap = Prec<F>::gap * fmax(F(1), s);
   int* piv = reinterpret_cast<int*>(scratch + 4 * n);
   for (int r = 1; r < nroots; ++r) {
-    bool clustered = false;
-    for (int j = 0; j < r; ++j) clustered |= fabs(w[r] - w[j]) < gap;
-    if (!clustered) continue;
-    double* z = y + (size_t)r * n;
-    for (int i = lane; i < n; i += 32) z[i] = 1.0 + 0.001 * (double)((i * 7919 + r * 104729) % 997);
+    // the roots are ascending: the earlier members of r's cluster are the run j0 .. r - 1
+    int j0 = r;
+    while (j0 > 0 && fabs(w[r] - w[j0 - 1]) < gap) --j0;
+    if (j0 == r) continue;
+    F* z = y + (size_t)r * n;
+    for (int i = lane; i < n; i += 32) z[i] = F(1) + F(0.001) * (F)((i * 7919 + r * 104729) % 997);
     __syncwarp();
-    if (lane == 0) tri_factor_shifted(d, e, n, w[r], scratch, piv);
+    if (lane == 0) tri_factor_shifted<F>(d, e, n, w[r], scratch, piv);
     __syncwarp();
     for (int it = 0; it < 3; ++it) {
-      if (lane == 0) tri_solve_factored(n, z, scratch, piv);
+      if (lane == 0) tri_solve_factored<F>(n, z, scratch, piv);
       __syncwarp();
-      for (int j = 0; j < r; ++j) {
-        if (!(fabs(w[r] - w[j]) < gap)) continue;
-        const double* zj = y + (size_t)j * n;
-        double dot = 0.0;
+      for (int j = j0; j < r; ++j) {
+        const F* zj = y + (size_t)j * n;
+        F dot = F(0);
         for (int i = lane; i < n; i += 32) dot += zj[i] * z[i];
         dot = warp_sum(dot);
         for (int i = lane; i < n; i += 32) z[i] -= dot * zj[i];
         __syncwarp();
       }
-      double nn = 0.0;
+      F nn = F(0);
       for (int i = lane; i < n; i += 32) nn += z[i] * z[i];
       nn = warp_sum(nn);
-      const double inv = nn > 0.0 ? 1.0 / sqrt(nn) : 0.0;
+      const F inv = nn > F(0) ? F(1) / sqrt(nn) : F(0);
       for (int i = lane; i < n; i += 32) z[i] *= inv;
       __syncwarp();
     }
@@ -635,14 +660,15 @@ __global__ void k_invit_clusters(const double* __restrict__ d, const double* __r
 // triangle past the superdiagonal is dead after the reduction), so that the
 // back-transformation reads each reflector contiguously.  32 x 32 tiles through shared
 // memory.
-__global__ void k_reflectors_to_rows(double* __restrict__ A, int n) {
-  __shared__ double tile[32][33];
+template <typename F>
+__global__ void k_reflectors_to_rows(F* __restrict__ A, int n) {
+  __shared__ F tile[32][33];
   const int j0 = blockIdx.x * 32, i0 = blockIdx.y * 32;   // source tile: rows i0.., columns j0..
   if (i0 + 31 < j0 + 2) return;                          // no entry with i > j + 1
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 8 rows per pass
   for (int r = ty; r < 32; r += 8) {
     const int i = i0 + r, j = j0 + tx;
-    tile[r][tx] = (i < n && j < n && i > j + 1) ? A[(size_t)i * n + j] : 0.0;
+    tile[r][tx] = (i < n && j < n && i > j + 1) ? A[(size_t)i * n + j] : F(0);
   }
   __syncthreads();
   for (int r = ty; r < 32; r += 8) {
@@ -653,21 +679,23 @@ __global__ void k_reflectors_to_rows(double* __restrict__ A, int n) {
 
 // x_k = H_0 H_1 ... H_{n-3} y_k, one warp (CTA) per root, x in shared memory;
 // H_j = I - tau_j v_j v_j^T, v_j[j+1] = 1, v_j[i] = A[j][i] (i > j + 1, rows form)
-__global__ void __launch_bounds__(32) k_backtransform(const double* __restrict__ A, const double* __restrict__ tau,
-                                                      int n, const double* __restrict__ y, int nroots,
-                                                      double* __restrict__ X) {
-  extern __shared__ double xs_bt[];
+template <typename F>
+__global__ void __launch_bounds__(32) k_backtransform(const F* __restrict__ A, const F* __restrict__ tau,
+                                                      int n, const F* __restrict__ y, int nroots,
+                                                      F* __restrict__ X) {
+  extern __shared__ __align__(16) unsigned char xs_bt_raw[];
+  F* xs_bt = reinterpret_cast<F*>(xs_bt_raw);
   const int lane = threadIdx.x & 31;
   const int k = blockIdx.x;
   if (k >= nroots) return;
-  double* x = xs_bt;
+  F* x = xs_bt;
   for (int i = lane; i < n; i += 32) x[i] = y[(size_t)k * n + i];
   __syncwarp();
   for (int kk = n - 3; kk >= 0; --kk) {
-    const double tk = tau[kk];
-    if (tk == 0.0) continue;
-    const double* v = A + (size_t)kk * n;
-    double s = (lane == 0) ? x[kk + 1] : 0.0;
+    const F tk = tau[kk];
+    if (tk == F(0)) continue;
+    const F* v = A + (size_t)kk * n;
+    F s = (lane == 0) ? x[kk + 1] : F(0);
     for (int i = kk + 2 + lane; i < n; i += 32) s += v[i] * x[i];
     s = tk * warp_sum(s);
     if (lane == 0) x[kk + 1] -= s;
@@ -682,36 +710,53 @@ __global__ void __launch_bounds__(32) k_backtransform(const double* __restrict__
 // workspace after A, d, e, tau: tw (2 n, one-CTA tridiagonalisation), the T-basis vectors
 // y (nroots n), inverse-iteration scratch (nroots 5 n), then the cooperative kernel's
 // scratch (v, p, partials, alpha, grid barrier)
-static double* y_end(double* tw, int n, int nroots) { return tw + 2 * n + (size_t)nroots * n + 5 * (size_t)nroots * n; }
+// scratch after the tridiagonal arrays: 2 n (tridiagonalisation), yv (nroots n), 5 n per root
+template <typename F>
+static F* y_end(F* tw, int n, int nroots) { return tw + 2 * n + (size_t)nroots * n + 5 * (size_t)nroots * n; }
+// coop scratch (v, p, partials, alpha) + the grid barrier, in units of F
+template <typename F>
+static size_t coop_scratch(int n) { return 2 * (size_t)n + 2 * 1024 + 2 + (sizeof(GridBar) + sizeof(F) - 1) / sizeof(F) + 2; }
 
-size_t tda_work_doubles(int n, int nroots) {
+static size_t tda_work_doubles_fp64(int n, int nroots) {
   return (size_t)n * n + 14 * (size_t)n + 6 * (size_t)nroots * n + 4096;
 }
 
-int sym_eig_lowest(rsx_ctx* c, double* work, int n, int nroots, double* omega, double* X, cudaStream_t s) {
-  double* A = work;
-  double* d = A + (size_t)n * n;
-  double* e = d + n;
-  double* tau = e + n;
-  double* tw = tau + n;          // 2 n (tridiagonalisation), then 5 n (eigvec scratch needs 4 n + n ints)
-  // cooperative multi-CTA reduction when the device supports it, one CTA otherwise
+constexpr int kMixedMinN = 96;   // below this the FP64 path is as fast
+constexpr int kNewtonSteps = 2;  // FP64 correction steps of the mixed path
+
+size_t tda_work_doubles(int n, int nroots) {
+  const size_t fp64 = tda_work_doubles_fp64(n, nroots);
+  if (n < kMixedMinN) return fp64;
+  const size_t nn = (size_t)n * n, k = nroots;
+  // FP32 part (counted in doubles): A32, d / e / tau, coop scratch, roots, vectors of T,
+  // inverse-iteration scratch (5 n per root), eigenvectors of A32
+  const size_t f32 = (nn + 3 * (size_t)n + coop_scratch<float>(n) + n + nn + 5 * nn + nn + 16) / 2 + 2;
+  // FP64 part: Xh (n x n), lambda, Xk / Y / R / D (k x n each), C (n x k), the small
+  // Rayleigh-Ritz (G, H, Linv, Yc, Zc, theta) and its eigensolver workspace
+  const size_t f64 = nn + n + 5 * k * n + 5 * k * k + 4 * k + tda_work_doubles_fp64((int)k, nroots);
+  return std::max(fp64, nn + f32 + f64 + 64);
+}
+
+// Householder reduction of the n x n matrix A (F) into d, e, tau: one thread-block cluster
+// with the matrix in distributed shared memory when it fits, else the cooperative grid,
+// else (F = double only) one CTA.  scr: coop_scratch<F>(n) values; tw: 2 n (one CTA).
+template <typename F>
+static int tridiagonalise(rsx_ctx* c, F* A, int n, F* d, F* e, F* tau, F* scr, F* tw, cudaStream_t s) {
   int coop = 0, per_sm = 0;
   cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, c->device);
-  cudaFuncSetAttribute(k_tridiag_coop, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(2 * (size_t)n * sizeof(double)));
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tridiag_coop, 256, 2 * (size_t)n * sizeof(double));
-  // fewer CTAs make each grid barrier cheaper; the FP64 work per step is small
+  cudaFuncSetAttribute(k_tridiag_coop<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(2 * (size_t)n * sizeof(F)));
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tridiag_coop<F>, 256, 2 * (size_t)n * sizeof(F));
+  // fewer CTAs make each grid barrier cheaper; the work per step is small
   int gcap = 64;
   if (const char* ev = getenv("RSX_TRIDIAG_CTAS")) gcap = std::max(1, atoi(ev));
   const int G = std::min(std::min(c->nsm * std::max(per_sm, 0), gcap), std::max(1, n / 2));
-  // one thread-block cluster with the matrix in distributed shared memory when it fits
-  // (16 CTAs, non-portable size, else 8), else the cooperative grid, else one CTA
-  bool done = false;
   for (int CS : {16, 8}) {
-    if (done || n < 64) break;
-    const size_t smem = (((size_t)(n + CS - 1) / CS) * n + 2 * (size_t)n + 2 * CS + 1) * sizeof(double);
+    if (n < 64) break;
+    const size_t smem = (((size_t)(n + CS - 1) / CS) * n + 2 * (size_t)n + 2 * CS + 1) * sizeof(F);
     if (smem > (size_t)227 * 1024) continue;
-    if (cudaFuncSetAttribute(k_tridiag_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
-        (CS > 8 && cudaFuncSetAttribute(k_tridiag_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)) {
+    if (cudaFuncSetAttribute(k_tridiag_cluster<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        (CS > 8 &&
+         cudaFuncSetAttribute(k_tridiag_cluster<F>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)) {
       cudaGetLastError();
       continue;
     }
@@ -728,41 +773,313 @@ int sym_eig_lowest(rsx_ctx* c, double* work, int n, int nroots, double* omega, d
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int ncl = 0;
-    if (cudaOccupancyMaxActiveClusters(&ncl, k_tridiag_cluster, &cfg) != cudaSuccess || ncl < 1) {
+    if (cudaOccupancyMaxActiveClusters(&ncl, k_tridiag_cluster<F>, &cfg) != cudaSuccess || ncl < 1) {
       cudaGetLastError();
       continue;
     }
-    const cudaError_t err = cudaLaunchKernelEx(&cfg, k_tridiag_cluster, A, n, d, e, tau);
-    if (err != cudaSuccess) return check_cuda(c, err, "cluster tridiagonalisation");
-    done = true;
+    const cudaError_t err = cudaLaunchKernelEx(&cfg, k_tridiag_cluster<F>, A, n, d, e, tau);
+    return check_cuda(c, err, "cluster tridiagonalisation");
   }
-  if (done) {
-  } else if (coop && per_sm > 0 && n >= 64) {
-    double* scr = y_end(tw, n, nroots);            // v, p, partials, alpha
-    GridBar* gb = reinterpret_cast<GridBar*>(scr + 2 * n + 2 * 1024 + 2);
+  if (coop && per_sm > 0 && n >= 64) {
+    GridBar* gb = reinterpret_cast<GridBar*>(scr + 2 * (size_t)n + 2 * 1024 + 2);
     cudaMemsetAsync(gb, 0, sizeof(GridBar), s);
     void* args[] = {(void*)&A, (void*)&n, (void*)&d, (void*)&e, (void*)&tau, (void*)&scr, (void*)&gb,
                     (void*)&c->status};
-    const size_t smem = 2 * (size_t)n * sizeof(double);
-    cudaFuncSetAttribute(k_tridiag_coop, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaError_t err = cudaLaunchCooperativeKernel((const void*)k_tridiag_coop, dim3(G), dim3(256), args, smem, s);
-    if (err != cudaSuccess) return check_cuda(c, err, "cooperative tridiagonalisation");
-  } else {
+    const size_t smem = 2 * (size_t)n * sizeof(F);
+    cudaFuncSetAttribute(k_tridiag_coop<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return check_cuda(c, cudaLaunchCooperativeKernel((const void*)k_tridiag_coop<F>, dim3(G), dim3(256), args, smem, s),
+                      "cooperative tridiagonalisation");
+  }
+  if constexpr (sizeof(F) == 8) {
     k_tridiagonalise<<<1, kEigThreads, 0, s>>>(A, n, d, e, tau, tw);
+    return check_cuda(c, cudaGetLastError(), "tridiagonalisation");
   }
-  cudaFuncSetAttribute(k_multisect, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(2 * (size_t)n * sizeof(double)));
-  k_multisect<<<nroots, 32, 2 * (size_t)n * sizeof(double), s>>>(d, e, n, nroots, omega);
-  if (X) {
-    double* yv = tw + 2 * n;                       // T-basis vectors
-    double* sc = yv + (size_t)nroots * n;          // 5 n per root
-    k_invit<<<nroots, 32, 0, s>>>(d, e, n, omega, nroots, yv, sc);
-    k_invit_clusters<<<1, 32, 0, s>>>(d, e, n, omega, nroots, yv, sc);
-    k_reflectors_to_rows<<<dim3((n + 31) / 32, (n + 31) / 32), 256, 0, s>>>(A, n);
-    const size_t smem = (size_t)n * sizeof(double);
-    cudaFuncSetAttribute(k_backtransform, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_backtransform<<<nroots, 32, smem, s>>>(A, tau, n, yv, nroots, X);
-  }
+  return set_error(c, RSX_EUNSUPPORTED, "no FP32 tridiagonalisation path for this size");
+}
+
+// lowest q eigenpairs of the tridiagonal (d, e) and x = Q y through the reflectors of A
+template <typename F>
+static void tridiag_eigs(F* A, const F* tau, const F* d, const F* e, int n, int q, F* w, F* yv, F* sc, F* X,
+                         cudaStream_t s) {
+  cudaFuncSetAttribute(k_multisect<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(2 * (size_t)n * sizeof(F)));
+  k_multisect<F><<<q, 32, 2 * (size_t)n * sizeof(F), s>>>(d, e, n, q, w);
+  if (!X) return;
+  k_invit<F><<<q, 32, 0, s>>>(d, e, n, w, q, yv, sc);
+  k_invit_clusters<F><<<1, 32, 0, s>>>(d, e, n, w, q, yv, sc);
+  k_reflectors_to_rows<F><<<dim3((n + 31) / 32, (n + 31) / 32), 256, 0, s>>>(A, n);
+  const size_t smem = (size_t)n * sizeof(F);
+  cudaFuncSetAttribute(k_backtransform<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_backtransform<F><<<q, 32, smem, s>>>(A, tau, n, yv, q, X);
+}
+
+// FP64 form throughout (Householder, multisection, inverse iteration, back-transformation)
+static int sym_eig_lowest_fp64(rsx_ctx* c, double* work, int n, int nroots, double* omega, double* X, cudaStream_t s) {
+  double* A = work;
+  double* d = A + (size_t)n * n;
+  double* e = d + n;
+  double* tau = e + n;
+  double* tw = tau + n;          // 2 n (tridiagonalisation), then 5 n (eigvec scratch needs 4 n + n ints)
+  int rc = tridiagonalise<double>(c, A, n, d, e, tau, y_end(tw, n, nroots), tw, s);
+  if (rc) return rc;
+  tridiag_eigs<double>(A, tau, d, e, n, nroots, omega, tw + 2 * n, tw + 2 * n + (size_t)nroots * n, X, s);
   return check_cuda(c, cudaGetLastError(), "symmetric eigensolve");
+}
+
+namespace {
+__global__ void k_f64_to_f32(const double* __restrict__ a, size_t n, float* __restrict__ b) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
+}
+__global__ void k_f32_to_f64(const float* __restrict__ a, size_t n, double* __restrict__ b) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    b[i] = (double)a[i];
+}
+// W = V M (q x n times n x n, row-major): block (32 columns, 8 splits of the inner index),
+// grid (column tiles, rows of V); two chains per thread, shared-memory tree over the splits
+__global__ void __launch_bounds__(256) k_vm(const double* __restrict__ V, const double* __restrict__ M, int n,
+                                            double* __restrict__ W) {
+  __shared__ double red[8][33];
+  const int tx = threadIdx.x & 31, ks = threadIdx.x >> 5;
+  const int i = blockIdx.x * 32 + tx, r = blockIdx.y;
+  const double* v = V + (size_t)r * n;
+  double a0 = 0.0, a1 = 0.0;
+  if (i < n) {
+    int j = ks;
+    for (; j + 8 < n; j += 16) {
+      a0 += v[j] * M[(size_t)j * n + i];
+      a1 += v[j + 8] * M[(size_t)(j + 8) * n + i];
+    }
+    if (j < n) a0 += v[j] * M[(size_t)j * n + i];
+  }
+  red[ks][tx] = a0 + a1;
+  __syncthreads();
+  if (ks == 0 && i < n)
+    W[(size_t)r * n + i] = ((red[0][tx] + red[1][tx]) + (red[2][tx] + red[3][tx])) +
+                           ((red[4][tx] + red[5][tx]) + (red[6][tx] + red[7][tx]));
+}
+// out[a * nb + b] = sum_i X[a][i] Y[b][i] (length n): a block per output, tree reduction
+__global__ void __launch_bounds__(256) k_dots(const double* __restrict__ X, const double* __restrict__ Y, int n, int nb,
+                                              double* __restrict__ out) {
+  __shared__ double red[8];
+  const int a = blockIdx.x / nb, b = blockIdx.x % nb;
+  const double* x = X + (size_t)a * n;
+  const double* y = Y + (size_t)b * n;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += 256) acc += x[i] * y[i];
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const double t = warp_sum(threadIdx.x < 8 ? red[threadIdx.x] : 0.0);
+    if (threadIdx.x == 0) out[blockIdx.x] = t;
+  }
+}
+// theta_j = <x_j, (A x)_j> / <x_j, x_j>;  R_j = (A x)_j - theta_j x_j   (k x n)
+__global__ void k_residuals(const double* __restrict__ Xk, const double* __restrict__ Y, const double* __restrict__ GH,
+                            int k, int n, double* __restrict__ theta, double* __restrict__ R) {
+  for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < (size_t)k * n; x += (size_t)gridDim.x * blockDim.x) {
+    const int j = (int)(x / n);
+    const double th = GH[2 * j + 1] / GH[2 * j];
+    R[x] = Y[x] - th * Xk[x];
+    if (x - (size_t)j * n == 0) theta[j] = th;
+  }
+}
+// correction coefficients D[j][i] = -C[i][j] / (lambda_i - theta_j) (zero within gthr of
+// theta_j: the root itself and its near-degenerate partners, left to the final
+// Rayleigh-Ritz), C[i][j] = <xh_i, r_j>
+__global__ void k_newton_coeffs(const double* __restrict__ C, const double* __restrict__ lam,
+                                const double* __restrict__ theta, int n, int k, double gthr, double* __restrict__ D) {
+  for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < (size_t)k * n; x += (size_t)gridDim.x * blockDim.x) {
+    const int j = (int)(x / n), i = (int)(x - (size_t)j * n);
+    const double dl = lam[i] - theta[j];
+    D[x] = fabs(dl) > gthr ? -C[(size_t)i * k + j] / dl : 0.0;
+  }
+}
+__global__ void k_add_inplace(double* __restrict__ a, const double* __restrict__ b, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) a[i] += b[i];
+}
+// the diagonal of two k x k Gram results interleaved: GH[2 j] = G_jj, GH[2 j + 1] = H_jj
+__global__ void k_diag2(const double* __restrict__ G, const double* __restrict__ H, int k, double* __restrict__ GH) {
+  const int j = threadIdx.x;
+  if (j < k) {
+    GH[2 * j] = G[j * k + j];
+    GH[2 * j + 1] = H[j * k + j];
+  }
+}
+// G = L L^T (q <= 64, one CTA), Linv = L^-1, C = Linv H Linv^T (H symmetrised)
+__global__ void __launch_bounds__(256) k_whiten(const double* __restrict__ G, const double* __restrict__ H, int q,
+                                                double* __restrict__ C, double* __restrict__ Linv, int* status) {
+  extern __shared__ double wh_smem[];   // L, Li, T: 3 q^2
+  double* L = wh_smem;
+  double* Li = L + q * q;
+  double* T = Li + q * q;
+  const int tid = threadIdx.x;
+  for (int x = tid; x < q * q; x += 256) {
+    const int r = x / q, cc = x - r * q;
+    L[x] = 0.5 * (G[r * q + cc] + G[cc * q + r]);
+    Li[x] = 0.0;
+  }
+  __syncthreads();
+  for (int j = 0; j < q; ++j) {
+    if (tid == 0) {
+      double p = L[j * q + j];
+      if (!(p > 0.0)) {
+        atomicMax(status, RSX_ENOTPD);
+        p = 1.0;
+      }
+      L[j * q + j] = sqrt(p);
+    }
+    __syncthreads();
+    const double rl = 1.0 / L[j * q + j];
+    for (int i = j + 1 + tid; i < q; i += 256) L[i * q + j] *= rl;
+    __syncthreads();
+    const int t = q - j - 1;
+    for (int x = tid; x < t * t; x += 256) {
+      const int i = j + 1 + x / t, l = j + 1 + x % t;
+      if (l <= i) L[i * q + l] -= L[i * q + j] * L[l * q + j];
+    }
+    __syncthreads();
+  }
+  if (tid < q) {
+    const int cc = tid;
+    Li[cc * q + cc] = 1.0 / L[cc * q + cc];
+    for (int i = cc + 1; i < q; ++i) {
+      double sum = 0.0;
+      for (int p = cc; p < i; ++p) sum += L[i * q + p] * Li[p * q + cc];
+      Li[i * q + cc] = -sum / L[i * q + i];
+    }
+  }
+  __syncthreads();
+  for (int x = tid; x < q * q; x += 256) {   // T = Li H
+    const int r = x / q, cc = x - r * q;
+    double sum = 0.0;
+    for (int p = 0; p <= r; ++p) sum += Li[r * q + p] * 0.5 * (H[p * q + cc] + H[cc * q + p]);
+    T[x] = sum;
+  }
+  __syncthreads();
+  for (int x = tid; x < q * q; x += 256) {   // C = T Li^T
+    const int r = x / q, cc = x - r * q;
+    double sum = 0.0;
+    for (int p = 0; p <= cc; ++p) sum += T[r * q + p] * Li[cc * q + p];
+    C[x] = sum;
+    Linv[x] = Li[x];
+  }
+}
+// Zc[k][r] = sum_s Yc[k][s] Linv[s][r]: the wanted eigenvectors' coefficients over the rows of V
+__global__ void k_coeffs(const double* __restrict__ Yc, const double* __restrict__ Linv, int q, int nroots,
+                         double* __restrict__ Zc) {
+  for (int x = threadIdx.x; x < nroots * q; x += blockDim.x) {
+    const int k = x / q, r = x - k * q;
+    double sum = 0.0;
+    for (int sidx = r; sidx < q; ++sidx) sum += Yc[k * q + sidx] * Linv[sidx * q + r];
+    Zc[x] = sum;
+  }
+}
+// X[k][:] = sum_r Zc[k][r] V[r][:]
+__global__ void k_expand(const double* __restrict__ Zc, const double* __restrict__ V, int q, int nroots, int n,
+                         double* __restrict__ X) {
+  for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < (size_t)nroots * n; x += (size_t)gridDim.x * blockDim.x) {
+    const int k = (int)(x / n), i = (int)(x - (size_t)k * n);
+    double sum = 0.0;
+    for (int r = 0; r < q; ++r) sum += Zc[k * q + r] * V[(size_t)r * n + i];
+    X[x] = sum;
+  }
+}
+unsigned blocks_of(size_t n) { return (unsigned)std::min<size_t>((n + 255) / 256, 4096); }
+}  // namespace
+
+// Mixed precision.  The Householder reduction, every root of T, its vector and the
+// back-transformation run in FP32 (A32 = A rounded), giving a full approximate
+// eigenbasis Xh, lambda of A.  The wanted k vectors are then corrected in FP64 against A
+// itself, kNewtonSteps times: r_j = A x_j - theta_j x_j (theta_j the Rayleigh quotient),
+// x_j <- x_j - sum_i xh_i <xh_i, r_j> / (lambda_i - theta_j) over the roots i not within
+// gthr of theta_j -- the correction equation solved in the approximate eigenbasis, which
+// converges quadratically from FP32 accuracy -- and a final FP64 Rayleigh-Ritz on the k
+// corrected vectors (G = X X^T, H = X A X^T, H z = theta G z) resolves near-degenerate
+// roots and gives the eigenvalues.
+static int sym_eig_lowest_mixed(rsx_ctx* c, double* work, int n, int nroots, double* omega, double* X,
+                                cudaStream_t s) {
+  const int k = nroots;
+  const size_t nn = (size_t)n * n;
+  double* A = work;                                   // FP64 A, kept
+  float* A32 = reinterpret_cast<float*>(A + nn);
+  float* d32 = A32 + nn;
+  float* e32 = d32 + n;
+  float* tau32 = e32 + n;
+  float* scr32 = tau32 + n;
+  float* w32 = scr32 + coop_scratch<float>(n);
+  float* yv32 = w32 + n;                              // n x n, then 5 n per root
+  float* sc32 = yv32 + nn;
+  float* X32 = sc32 + 5 * nn;
+  uintptr_t gp = reinterpret_cast<uintptr_t>(X32 + nn) + 16;
+  double* g = reinterpret_cast<double*>((gp + 15) & ~uintptr_t(15));
+  double* Xh = g;                                     // n x n
+  double* lam = Xh + nn;                              // n
+  double* Xk = lam + n;                               // k x n
+  double* Y = Xk + (size_t)k * n;
+  double* R = Y + (size_t)k * n;
+  double* D = R + (size_t)k * n;
+  double* Cm = D + (size_t)k * n;                     // n x k
+  double* G = Cm + (size_t)k * n;                     // k x k
+  double* H = G + (size_t)k * k;
+  double* Linv = H + (size_t)k * k;
+  double* Yc = Linv + (size_t)k * k;
+  double* Zc = Yc + (size_t)k * k;
+  double* th = Zc + (size_t)k * k;                    // 2 k (theta, then G / H diagonals)
+  double* GH = th + k;
+  double* Cw = GH + 2 * k;                            // the small problem: C and its workspace
+  k_f64_to_f32<<<blocks_of(nn), 256, 0, s>>>(A, nn, A32);
+  int rc = tridiagonalise<float>(c, A32, n, d32, e32, tau32, scr32, nullptr, s);
+  if (rc) return rc;
+  tridiag_eigs<float>(A32, tau32, d32, e32, n, n, w32, yv32, sc32, X32, s);
+  k_f32_to_f64<<<blocks_of(nn), 256, 0, s>>>(X32, nn, Xh);
+  k_f32_to_f64<<<blocks_of(n), 256, 0, s>>>(w32, n, lam);
+  cudaMemcpyAsync(Xk, Xh, (size_t)k * n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  // near-degeneracy threshold: FP32 can not separate roots closer than a few eps32 |A|
+  double gthr = 0.0;
+  {
+    // |A| from the extreme FP32 roots
+    float ends[2];
+    cudaMemcpyAsync(&ends[0], w32, sizeof(float), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(&ends[1], w32 + n - 1, sizeof(float), cudaMemcpyDeviceToHost, s);
+    rc = check_cuda(c, cudaStreamSynchronize(s), "mixed eigensolve (FP32 stage)");
+    if (rc) return rc;
+    gthr = 1e-5 * std::max(1.0, std::max(std::fabs((double)ends[0]), std::fabs((double)ends[1])));
+  }
+  const dim3 gvm((n + 31) / 32, k);
+  for (int it = 0; it < kNewtonSteps; ++it) {
+    k_vm<<<gvm, 256, 0, s>>>(Xk, A, n, Y);                        // Y = Xk A (A symmetric)
+    k_dots<<<k * k, 256, 0, s>>>(Xk, Xk, n, k, G);
+    k_dots<<<k * k, 256, 0, s>>>(Xk, Y, n, k, H);
+    k_diag2<<<1, 64, 0, s>>>(G, H, k, GH);
+    k_residuals<<<blocks_of((size_t)k * n), 256, 0, s>>>(Xk, Y, GH, k, n, th, R);
+    k_dots<<<n * k, 256, 0, s>>>(Xh, R, n, k, Cm);                 // Cm[i][j] = <xh_i, r_j>
+    k_newton_coeffs<<<blocks_of((size_t)k * n), 256, 0, s>>>(Cm, lam, th, n, k, gthr, D);
+    k_vm<<<gvm, 256, 0, s>>>(D, Xh, n, R);                         // R = D Xh (the correction)
+    k_add_inplace<<<blocks_of((size_t)k * n), 256, 0, s>>>(Xk, R, (size_t)k * n);
+  }
+  // final Rayleigh-Ritz on the k corrected vectors
+  k_vm<<<gvm, 256, 0, s>>>(Xk, A, n, Y);
+  k_dots<<<k * k, 256, 0, s>>>(Xk, Xk, n, k, G);
+  k_dots<<<k * k, 256, 0, s>>>(Y, Xk, n, k, H);
+  const size_t wsm = 3 * (size_t)k * k * sizeof(double);
+  cudaFuncSetAttribute(k_whiten, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsm);
+  k_whiten<<<1, 256, wsm, s>>>(G, H, k, Cw, Linv, c->status);
+  rc = check_cuda(c, cudaGetLastError(), "mixed eigensolve (FP64 correction)");
+  if (rc) return rc;
+  rc = sym_eig_lowest_fp64(c, Cw, k, k, omega, Yc, s);
+  if (rc) return rc;
+  if (X) {
+    k_coeffs<<<1, 256, 0, s>>>(Yc, Linv, k, k, Zc);
+    k_expand<<<blocks_of((size_t)k * n), 256, 0, s>>>(Zc, Xk, k, k, n, X);
+  }
+  return check_cuda(c, cudaGetLastError(), "mixed eigensolve");
+}
+
+int sym_eig_lowest(rsx_ctx* c, double* work, int n, int nroots, double* omega, double* X, cudaStream_t s) {
+  const char* ev = getenv("RSX_EIG_FP64");
+  if (n >= kMixedMinN && !(ev && atoi(ev) != 0)) return sym_eig_lowest_mixed(c, work, n, nroots, omega, X, s);
+  return sym_eig_lowest_fp64(c, work, n, nroots, omega, X, s);
 }
 
 namespace {

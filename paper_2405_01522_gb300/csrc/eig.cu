@@ -17,6 +17,7 @@
 
 #include <algorithm>
 #include <cstdlib>
+#include <string>
 
 #include "../../include/rsx.h"
 #include "api_internal.cuh"
@@ -389,7 +390,10 @@ __global__ void __launch_bounds__(256) k_tridiag_coop(F* __restrict__ A, int n, 
 constexpr int kClThreads = 512;
 namespace cg = cooperative_groups;
 
-template <typename F>
+// GROWS: the owned rows stay in global memory (rows of A, L2-resident) instead of
+// distributed shared memory, for n too large for the latter; only v, p and the partials
+// go through DSMEM.  A CTA only ever touches the rows it owns.
+template <typename F, bool GROWS>
 __global__ void __launch_bounds__(kClThreads) k_tridiag_cluster(F* __restrict__ A, int n, F* __restrict__ d,
                                                                 F* __restrict__ e, F* __restrict__ tau) {
   cg::cluster_group cl = cg::this_cluster();
@@ -399,8 +403,8 @@ __global__ void __launch_bounds__(kClThreads) k_tridiag_cluster(F* __restrict__ 
   const int lda = n;
   extern __shared__ __align__(16) unsigned char cl_smem_raw[];
   F* cl_smem = reinterpret_cast<F*>(cl_smem_raw);
-  F* R = cl_smem;                               // [nloc][n]
-  F* v = R + (size_t)((n + CS - 1) / CS) * n;   // [n]
+  F* R = cl_smem;                               // [nloc][n] (shared-memory rows)
+  F* v = GROWS ? cl_smem : R + (size_t)((n + CS - 1) / CS) * n;   // [n]
   F* p = v + n;                                 // [n] (p, then w)
   F* part = p + n;                              // [CS] norm partials, [CS] p^T v partials, alpha
   F* part2 = part + CS;
@@ -409,9 +413,12 @@ __global__ void __launch_bounds__(kClThreads) k_tridiag_cluster(F* __restrict__ 
   __shared__ F sh_tau, sh_beta, sh_scale;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = kClThreads / 32;
   auto grow = [&](int li) { return me + li * CS; };
-  for (size_t q = tid; q < (size_t)nloc * n; q += kClThreads) {
-    const int li = (int)(q / n), j = (int)(q - (size_t)li * n);
-    R[q] = A[(size_t)grow(li) * lda + j];
+  auto rowp = [&](int li) -> F* { return GROWS ? A + (size_t)grow(li) * lda : R + (size_t)li * n; };
+  if (!GROWS) {
+    for (size_t q = tid; q < (size_t)nloc * n; q += kClThreads) {
+      const int li = (int)(q / n), j = (int)(q - (size_t)li * n);
+      R[q] = A[(size_t)grow(li) * lda + j];
+    }
   }
   __syncthreads();
   // block-wide sum of one value per thread, result to thread 0 (trees throughout: a
@@ -433,7 +440,7 @@ __global__ void __launch_bounds__(kClThreads) k_tridiag_cluster(F* __restrict__ 
     F s = F(0);
     for (int li = tid; li < nloc; li += kClThreads) {
       const int i = grow(li);
-      if (i >= c + 2) s += R[(size_t)li * n + c] * R[(size_t)li * n + c];
+      if (i >= c + 2) s += rowp(li)[c] * rowp(li)[c];
     }
     const F t = block_sum0(s);
     if (tid == 0) red[0] = t;
@@ -441,7 +448,7 @@ __global__ void __launch_bounds__(kClThreads) k_tridiag_cluster(F* __restrict__ 
     const F tot = red[0];
     if (tid < CS) *cl.map_shared_rank(part + me, tid) = tot;
     if ((c + 1) % CS == me && tid >= 32 && tid < 32 + CS)
-      *cl.map_shared_rank(alpha_sl, tid - 32) = R[(size_t)((c + 1) / CS) * n + c];
+      *cl.map_shared_rank(alpha_sl, tid - 32) = rowp((c + 1) / CS)[c];
   };
   if (n > 2) publish_norm(0);
   cl.sync();
@@ -469,7 +476,7 @@ __global__ void __launch_bounds__(kClThreads) k_tridiag_cluster(F* __restrict__ 
           e[k] = sh_beta;
           tau[k] = sh_tau;
         }
-        if (k % CS == me) d[k] = R[(size_t)(k / CS) * n + k];
+        if (k % CS == me) d[k] = rowp(k / CS)[k];
       }
     }
     __syncthreads();
@@ -479,13 +486,13 @@ __global__ void __launch_bounds__(kClThreads) k_tridiag_cluster(F* __restrict__ 
       const int li = q / CS, dst = q - li * CS;
       const int i = grow(li);
       if (i < m0) continue;
-      const F vi = (i == m0) ? F(1) : R[(size_t)li * n + k] * sc;
+      const F vi = (i == m0) ? F(1) : rowp(li)[k] * sc;
       *cl.map_shared_rank(v + i, dst) = vi;
     }
     cl.sync();
     for (int li = tid; li < nloc; li += kClThreads) {
       const int i = grow(li);
-      if (i > m0) R[(size_t)li * n + k] = v[i];
+      if (i > m0) rowp(li)[k] = v[i];
     }
     if (tk != F(0)) {
       // p_i = tau (A22 v)_i on own rows, a warp per row; p^T v partial
@@ -493,7 +500,7 @@ __global__ void __launch_bounds__(kClThreads) k_tridiag_cluster(F* __restrict__ 
       for (int li = warp; li < nloc; li += nw) {
         const int i = grow(li);
         if (i < m0) continue;
-        const F* row = R + (size_t)li * n;
+        const F* row = rowp(li);
         F a0 = F(0), a1 = F(0);   // two chains
         int j = m0 + lane;
         for (; j + 32 < n; j += 64) {
@@ -522,7 +529,7 @@ __global__ void __launch_bounds__(kClThreads) k_tridiag_cluster(F* __restrict__ 
         const int i = grow(li);
         if (i < m0) continue;
         const F vi = v[i], wi = p[i];
-        F* row = R + (size_t)li * n;
+        F* row = rowp(li);
         for (int j = m0 + lane; j < n; j += 32) row[j] -= vi * p[j] + wi * v[j];
       }
       __syncthreads();
@@ -535,15 +542,17 @@ __global__ void __launch_bounds__(kClThreads) k_tridiag_cluster(F* __restrict__ 
   // last 2 x 2 block, rows back to global memory
   if (tid == 0) {
     if (n >= 2) {
-      if ((n - 2) % CS == me) d[n - 2] = R[(size_t)((n - 2) / CS) * n + (n - 2)];
-      if ((n - 1) % CS == me) e[n - 2] = R[(size_t)((n - 1) / CS) * n + (n - 2)];
+      if ((n - 2) % CS == me) d[n - 2] = rowp((n - 2) / CS)[n - 2];
+      if ((n - 1) % CS == me) e[n - 2] = rowp((n - 1) / CS)[n - 2];
       if (me == 0 && n >= 3) tau[n - 2] = F(0);
     }
-    if ((n - 1) % CS == me) d[n - 1] = R[(size_t)((n - 1) / CS) * n + (n - 1)];
+    if ((n - 1) % CS == me) d[n - 1] = rowp((n - 1) / CS)[n - 1];
   }
-  for (size_t q = tid; q < (size_t)nloc * n; q += kClThreads) {
-    const int li = (int)(q / n), j = (int)(q - (size_t)li * n);
-    A[(size_t)grow(li) * lda + j] = R[q];
+  if (!GROWS) {
+    for (size_t q = tid; q < (size_t)nloc * n; q += kClThreads) {
+      const int li = (int)(q / n), j = (int)(q - (size_t)li * n);
+      A[(size_t)grow(li) * lda + j] = R[q];
+    }
   }
   cl.sync();   // no CTA leaves while others may still address its shared memory
 }
@@ -746,19 +755,26 @@ static int tridiagonalise(rsx_ctx* c, F* A, int n, F* d, F* e, F* tau, F* scr, F
   cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, c->device);
   cudaFuncSetAttribute(k_tridiag_coop<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(2 * (size_t)n * sizeof(F)));
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tridiag_coop<F>, 256, 2 * (size_t)n * sizeof(F));
-  // fewer CTAs make each grid barrier cheaper; the work per step is small
-  int gcap = 64;
+  // FP64: 64 CTAs (fewer make each grid barrier cheaper, the FP64 work per step is
+  // small); FP32: one per SM (measured at n = 960: 64 -> 24.0 ms, 152 -> 19.8 ms)
+  int gcap = sizeof(F) == 4 ? c->nsm : 64;
   if (const char* ev = getenv("RSX_TRIDIAG_CTAS")) gcap = std::max(1, atoi(ev));
   const int G = std::min(std::min(c->nsm * std::max(per_sm, 0), gcap), std::max(1, n / 2));
-  for (int CS : {16, 8}) {
-    if (n < 64) break;
-    const size_t smem = (((size_t)(n + CS - 1) / CS) * n + 2 * (size_t)n + 2 * CS + 1) * sizeof(F);
-    if (smem > (size_t)227 * 1024) continue;
-    if (cudaFuncSetAttribute(k_tridiag_cluster<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
-        (CS > 8 &&
-         cudaFuncSetAttribute(k_tridiag_cluster<F>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)) {
+  // rows in distributed shared memory (16 CTAs, else 8), else the cooperative grid, else
+  // one 16-CTA cluster with the rows in global memory (slower than the grid at n ~ 1000,
+  // measured), else one CTA.  RSX_TRIDIAG_PATH = cluster, coop, global or cta forces one
+  // (tests cover every path with it).
+  const char* fp = getenv("RSX_TRIDIAG_PATH");
+  const std::string force = fp ? fp : "";
+  auto try_cluster = [&](int CS, bool grows) -> int {   // -1: not possible here
+    if (n < 64) return -1;
+    const size_t smem = ((grows ? 0 : ((size_t)(n + CS - 1) / CS) * n) + 2 * (size_t)n + 2 * CS + 1) * sizeof(F);
+    if (smem > (size_t)227 * 1024) return -1;
+    auto kern = grows ? k_tridiag_cluster<F, true> : k_tridiag_cluster<F, false>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        (CS > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)) {
       cudaGetLastError();
-      continue;
+      return -1;
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(CS);
@@ -773,14 +789,18 @@ static int tridiagonalise(rsx_ctx* c, F* A, int n, F* d, F* e, F* tau, F* scr, F
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int ncl = 0;
-    if (cudaOccupancyMaxActiveClusters(&ncl, k_tridiag_cluster<F>, &cfg) != cudaSuccess || ncl < 1) {
+    if (cudaOccupancyMaxActiveClusters(&ncl, kern, &cfg) != cudaSuccess || ncl < 1) {
       cudaGetLastError();
-      continue;
+      return -1;
     }
-    const cudaError_t err = cudaLaunchKernelEx(&cfg, k_tridiag_cluster<F>, A, n, d, e, tau);
-    return check_cuda(c, err, "cluster tridiagonalisation");
-  }
-  if (coop && per_sm > 0 && n >= 64) {
+    return check_cuda(c, cudaLaunchKernelEx(&cfg, kern, A, n, d, e, tau), "cluster tridiagonalisation");
+  };
+  if (force.empty() || force == "cluster")
+    for (int CS : {16, 8}) {
+      const int r = try_cluster(CS, false);
+      if (r >= 0) return r;
+    }
+  if (coop && per_sm > 0 && n >= 64 && (force.empty() || force == "coop")) {
     GridBar* gb = reinterpret_cast<GridBar*>(scr + 2 * (size_t)n + 2 * 1024 + 2);
     cudaMemsetAsync(gb, 0, sizeof(GridBar), s);
     void* args[] = {(void*)&A, (void*)&n, (void*)&d, (void*)&e, (void*)&tau, (void*)&scr, (void*)&gb,
@@ -789,6 +809,10 @@ static int tridiagonalise(rsx_ctx* c, F* A, int n, F* d, F* e, F* tau, F* scr, F
     cudaFuncSetAttribute(k_tridiag_coop<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     return check_cuda(c, cudaLaunchCooperativeKernel((const void*)k_tridiag_coop<F>, dim3(G), dim3(256), args, smem, s),
                       "cooperative tridiagonalisation");
+  }
+  if (force.empty() || force == "global") {
+    const int r = try_cluster(16, true);
+    if (r >= 0) return r;
   }
   if constexpr (sizeof(F) == 8) {
     k_tridiagonalise<<<1, kEigThreads, 0, s>>>(A, n, d, e, tau, tw);

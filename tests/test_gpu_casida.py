@@ -68,11 +68,20 @@ def test_casida_K_and_Kd_parity(shape, h, no, nv, prec):
     assert np.array_equal(K, K.T) or prec == "fp64" and np.allclose(K, K.T, rtol=0, atol=0)
 
 
-@pytest.mark.parametrize("nt_shape", [(1, 1), (2, 3), (4, 9), (4, 16), (8, 64), (10, 66)])
-def test_casida_solve_matches_eigh(nt_shape):
-    """FP64 device eigen-solve vs numpy eigh on the same matrix, random symmetric K, K_d.
-    n = 36: one-CTA reduction; 64 and 512: thread-block cluster; 660: cooperative grid."""
+@pytest.mark.parametrize("nt_shape,env", [
+    ((1, 1), {}), ((2, 3), {}), ((4, 9), {}), ((4, 16), {}), ((8, 64), {}), ((10, 66), {}),
+    ((8, 64), {"RSX_EIG_FP64": "1"}), ((10, 66), {"RSX_EIG_FP64": "1"}),
+    ((10, 66), {"RSX_TRIDIAG_PATH": "global"}), ((10, 66), {"RSX_TRIDIAG_PATH": "coop"}),
+    ((10, 66), {"RSX_TRIDIAG_PATH": "coop", "RSX_EIG_FP64": "1"}), ((4, 16), {"RSX_TRIDIAG_PATH": "cta"})])
+def test_casida_solve_matches_eigh(nt_shape, env, monkeypatch):
+    """Device eigen-solve vs numpy eigh on the same matrix, random symmetric K, K_d.
+    n >= 96: mixed precision (FP32 reduction and eigenbasis, FP64 Newton corrections and
+    Rayleigh-Ritz), else FP64; the reduction on one thread-block cluster with the rows in
+    distributed shared memory (default), in global memory, on a cooperative grid or on one
+    CTA (forced by RSX_TRIDIAG_PATH); RSX_EIG_FP64 forces the FP64 form."""
     need_gpu()
+    for k, v in env.items():
+        monkeypatch.setenv(k, v)
     no, nv = nt_shape
     nt = no * nv
     r = np.random.default_rng(nt)

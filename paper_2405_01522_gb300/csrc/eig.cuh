@@ -31,14 +31,16 @@ __device__ inline float warp_sum(float v) {
 }
 
 // FP32 count of eigenvalues of T below x (the ratio form above in single precision, with
-// the single-precision pivmin); for bracketing roots before an FP64 refinement
+// the single-precision pivmin, and the fast approximate division: a Sturm count only needs
+// the pivots' signs, and the count it returns is that of a slightly perturbed T); for an
+// approximate eigenbasis that FP64 steps then refine
 __device__ inline int sturm_count_f32(const float* d, const float* e2, int n, float x, float pivmin) {
   int cnt = 0;
   float q = d[0] - x;
   if (fabsf(q) < pivmin) q = -pivmin;
   if (q < 0.f) ++cnt;
   for (int i = 1; i < n; ++i) {
-    q = (d[i] - x) - e2[i - 1] / q;
+    q = (d[i] - x) - __fdividef(e2[i - 1], q);
     if (fabsf(q) < pivmin) q = -pivmin;
     if (q < 0.f) ++cnt;
   }

@@ -177,15 +177,15 @@ __global__ void k_net_input(const float* __restrict__ R, const double* __restric
 //     the FP32-summed Gram matrices leave smaller pivots, and the directions they would
 //     add, dominated by rounding);
 //  2. C = L^-1 Hs L^-T over the m' kept directions;
-//  3. Householder tridiagonalisation C = Q T Q^T (reflectors kept below the subdiagonal);
-//     lowest k eigenpairs of T: located in FP32 (Sturm multisection, inverse iteration),
-//     finished in FP64 (Rayleigh quotient, one inverse iteration, Rayleigh quotient) and
-//     checked by FP64 Sturm counts (all redone in FP64 if a root fails); z <- Q z;
+//  3. an approximate eigenbasis of C in FP32 (Householder reduction, every root of the
+//     tridiagonal matrix, inverse iteration, back-transformation), then FP64 Newton
+//     corrections of the k lowest vectors against C and their Rayleigh quotients;
 //  4. the new orbitals' coefficients over the basis, Q = L^-T Z.
 // Outputs theta[k] and qt[k][m] (float).  Fewer than k kept directions raise RSX_ENOTPD.
 constexpr double kRrDrop = 1e-6;
 constexpr int kRrThreads = 512;
 constexpr int kRrWarps = kRrThreads / 32;
+constexpr int kRrNewton = 2;   // FP64 correction steps of the Rayleigh-Ritz eigenvectors
 
 __global__ void __launch_bounds__(kRrThreads) k_rayleigh_ritz(const double* __restrict__ Sg, const double* __restrict__ Hg,
                                                               int m, int k, double* __restrict__ theta,
@@ -196,17 +196,13 @@ __global__ void __launch_bounds__(kRrThreads) k_rayleigh_ritz(const double* __re
   double* C = Li + m * m;
   double* T = C + m * m;
   double* SCR = T + m * m;
-  __shared__ double dg0[kMaxBasis], dd[kMaxBasis], ee[kMaxBasis], tau[kMaxBasis], vv[kMaxBasis], pp[kMaxBasis];
-  __shared__ double lam[kMaxBasis];
+  __shared__ double dg0[kMaxBasis], lam[kMaxBasis], lamh[kMaxBasis], rdg[kMaxBasis];
   __shared__ float d32[kMaxBasis], e32[kMaxBasis], e2f[kMaxBasis], lam32[kMaxBasis];
+  __shared__ float tau32[kMaxBasis], vv32[kMaxBasis], pp32[kMaxBasis];
   __shared__ int kept[kMaxBasis], dropped[kMaxBasis];
-  __shared__ unsigned omask[kMaxBasis];
-  __shared__ double e2d[kMaxBasis];
-  __shared__ int redo_all;
-  __shared__ double rdg[kMaxBasis];
   __shared__ int piv[kRrWarps][kMaxBasis];
   __shared__ int nkeep;
-  __shared__ double sh_beta, sh_tau, sh_scale;
+  __shared__ float sh_beta32, sh_tau32, sh_scale32;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
   for (int q = tid; q < m * m; q += kRrThreads) {
@@ -289,91 +285,89 @@ __global__ void __launch_bounds__(kRrThreads) k_rayleigh_ritz(const double* __re
     C[b * n + a] = s;
   }
   __syncthreads();
-  // 3. Householder tridiagonalisation of C' (n x n, leading dimension n)
+  // 3. Eigenpairs of C' (n x n).  FP64 latency is long on this part, so an approximate
+  //    eigenbasis comes from FP32 (Householder reduction of C' rounded, every root of T
+  //    by Sturm multisection, inverse iteration, back-transformation), and the k wanted
+  //    vectors are then corrected against C' itself in FP64 (Newton steps of the
+  //    correction equation in that basis, as in the dense eigensolver), which converges
+  //    quadratically from FP32 accuracy; their Rayleigh quotients are the Ritz values.
+  float* C32 = reinterpret_cast<float*>(L);     // n x n (L is dead after L^-1)
+  float* X32 = C32 + n * n;                     // n x n: vectors of T, then of C'32
+  float* SC32 = reinterpret_cast<float*>(SCR);  // 4 n floats per warp
+  for (int q = tid; q < n * n; q += kRrThreads) C32[q] = (float)C[q];
+  __syncthreads();
+  // 3a. FP32 Householder reduction (reflectors below the subdiagonal, tau32)
   for (int kk = 0; kk + 2 < n; ++kk) {
     const int m0 = kk + 1;
-    if (warp == 0) {   // |x|^2 below the subdiagonal (n <= 64: two entries per lane)
-      double s = 0.0;
-      for (int i = m0 + 1 + lane; i < n; i += 32) s += C[i * n + kk] * C[i * n + kk];
-      const double xn2 = warp_sum(s);
+    if (warp == 0) {
+      float sq = 0.f;
+      for (int i = m0 + 1 + lane; i < n; i += 32) sq += C32[i * n + kk] * C32[i * n + kk];
+      const float xn2 = warp_sum(sq);
       if (lane == 0) {
-        const double alpha = C[m0 * n + kk];
-        if (xn2 == 0.0) {
-          sh_tau = 0.0;
-          sh_beta = alpha;
-          sh_scale = 0.0;
+        const float alpha = C32[m0 * n + kk];
+        if (xn2 == 0.f) {
+          sh_tau32 = 0.f;
+          sh_beta32 = alpha;
+          sh_scale32 = 0.f;
         } else {
-          // beta = -sign(alpha) |x|, tau = 1 + |alpha| / |x|: one rsqrt, one division
-          const double s2 = alpha * alpha + xn2, rs = rsqrt(s2);
-          const double beta = -copysign(s2 * rs, alpha);
-          sh_tau = 1.0 + fabs(alpha) * rs;
-          sh_scale = 1.0 / (alpha - beta);
-          sh_beta = beta;
+          const float s2 = alpha * alpha + xn2, rs = rsqrtf(s2);
+          const float beta = -copysignf(s2 * rs, alpha);
+          sh_tau32 = 1.f + fabsf(alpha) * rs;
+          sh_scale32 = 1.f / (alpha - beta);
+          sh_beta32 = beta;
         }
-        ee[kk] = sh_beta;
-        tau[kk] = sh_tau;
-        dd[kk] = C[kk * n + kk];
+        e32[kk] = sh_beta32;
+        tau32[kk] = sh_tau32;
+        d32[kk] = C32[kk * n + kk];
       }
     }
     __syncthreads();
-    const double tk = sh_tau;
+    const float tk = sh_tau32;
     for (int i = m0 + tid; i < n; i += kRrThreads) {
-      const double vi = (i == m0) ? 1.0 : C[i * n + kk] * sh_scale;
-      vv[i] = vi;
-      if (i > m0) C[i * n + kk] = vi;
+      const float vi = (i == m0) ? 1.f : C32[i * n + kk] * sh_scale32;
+      vv32[i] = vi;
+      if (i > m0) C32[i * n + kk] = vi;
     }
     __syncthreads();
-    if (tk != 0.0) {
-      {  // pp = tk C v over the trailing block: 8 threads per row (n <= 64 rows)
+    if (tk != 0.f) {
+      {  // p = tk C v over the trailing block: 8 threads per row (n <= 64 rows)
         const int g = tid & 7, i = m0 + (tid >> 3);
-        double acc = 0.0;
+        float acc = 0.f;
         if (i < n)
-          for (int jj = m0 + g; jj < n; jj += 8) acc += C[i * n + jj] * vv[jj];
+          for (int jj = m0 + g; jj < n; jj += 8) acc += C32[i * n + jj] * vv32[jj];
         acc += __shfl_xor_sync(0xffffffffu, acc, 1);
         acc += __shfl_xor_sync(0xffffffffu, acc, 2);
         acc += __shfl_xor_sync(0xffffffffu, acc, 4);
-        if (g == 0 && i < n) pp[i] = tk * acc;
+        if (g == 0 && i < n) pp32[i] = tk * acc;
       }
       __syncthreads();
-      if (warp == 0) {   // w = p - (tau/2)(p^T v) v over the trailing rows
-        double pv = 0.0;
-        for (int i = m0 + lane; i < n; i += 32) pv += pp[i] * vv[i];
-        const double cc = 0.5 * tk * warp_sum(pv);
-        for (int i = m0 + lane; i < n; i += 32) pp[i] -= cc * vv[i];
+      if (warp == 0) {   // w = p - (tau/2)(p^T v) v
+        float pv = 0.f;
+        for (int i = m0 + lane; i < n; i += 32) pv += pp32[i] * vv32[i];
+        const float cc = 0.5f * tk * warp_sum(pv);
+        for (int i = m0 + lane; i < n; i += 32) pp32[i] -= cc * vv32[i];
       }
       __syncthreads();
       const int t = n - m0;
       for (int q = tid; q < t * t; q += kRrThreads) {
         const int i = m0 + q / t, jj = m0 + q % t;
-        C[i * n + jj] -= vv[i] * pp[jj] + pp[i] * vv[jj];
+        C32[i * n + jj] -= vv32[i] * pp32[jj] + pp32[i] * vv32[jj];
       }
       __syncthreads();
     }
   }
   if (tid == 0) {
     if (n >= 2) {
-      dd[n - 2] = C[(n - 2) * n + (n - 2)];
-      ee[n - 2] = C[(n - 1) * n + (n - 2)];
+      d32[n - 2] = C32[(n - 2) * n + (n - 2)];
+      e32[n - 2] = C32[(n - 1) * n + (n - 2)];
     }
-    dd[n - 1] = C[(n - 1) * n + (n - 1)];
+    if (n >= 3) tau32[n - 2] = 0.f;
+    d32[n - 1] = C32[(n - 1) * n + (n - 1)];
   }
   __syncthreads();
-  // Lowest k eigenpairs of T.  FP64 latency is long on this part, so the search runs in
-  // FP32 and only a short FP64 finish follows:
-  //  a. T rounded to FP32; Sturm multisection (a warp per root, 32 points per round) and
-  //     three inverse iterations in FP32 (roots closer than gap32 are redone one after
-  //     another with re-orthogonalisation);
-  //  b. per root in FP64: Rayleigh quotient of the FP32 vector, one inverse iteration with
-  //     that shift (orthogonal to earlier roots within gap64, those done in order), and the
-  //     Rayleigh quotient of the result as the eigenvalue.
-  if (tid < n) {
-    d32[tid] = (float)dd[tid];
-    if (tid < n - 1) {
-      e32[tid] = (float)ee[tid];
-      e2f[tid] = e32[tid] * e32[tid];
-    }
-  }
+  if (tid < n - 1) e2f[tid] = e32[tid] * e32[tid];
   __syncthreads();
+  // 3b. every root of T: Sturm multisection, a warp per root (32 points per round)
   float lo0 = d32[0], hi0 = d32[0], emax = 0.f;
   for (int i = 0; i < n; ++i) {
     const float r = (i > 0 ? fabsf(e32[i - 1]) : 0.f) + (i < n - 1 ? fabsf(e32[i]) : 0.f);
@@ -385,7 +379,7 @@ __global__ void __launch_bounds__(kRrThreads) k_rayleigh_ritz(const double* __re
   lo0 -= 1e-6f * scale + 1e-30f;
   hi0 += 1e-6f * scale + 1e-30f;
   const float pivmin = 1.2e-38f * fmaxf(1.f, emax * emax);
-  for (int r = warp; r < k; r += kRrWarps) {
+  for (int r = warp; r < n; r += kRrWarps) {
     float lo = lo0, hi = hi0;
     for (int round = 0; round < 8; ++round) {
       if (!(hi - lo > 2.4e-7f * fmaxf(fabsf(lo), fabsf(hi)))) break;
@@ -400,148 +394,140 @@ __global__ void __launch_bounds__(kRrThreads) k_rayleigh_ritz(const double* __re
     if (lane == 0) lam32[r] = 0.5f * (lo + hi);
   }
   __syncthreads();
-  // a. FP32 vectors Z32 [k][n] (in L, free after L^-1), scratch 4 n floats per warp
-  float* Z32 = reinterpret_cast<float*>(L);
-  float* SCR32 = reinterpret_cast<float*>(SCR);
+  // 3c. vectors of T by inverse iteration; among the wanted roots and a margin above
+  //     them, roots closer than gap32 to the previous one are redone in order, orthogonal
+  //     to the earlier members of their run (higher vectors only carry the small
+  //     corrections along far directions, where a duplicate costs nothing measurable)
   const float gap32 = 1e-5f * fmaxf(1.f, scale);
-  for (int r = warp; r < k; r += kRrWarps) {
-    float* z = Z32 + r * n;
+  for (int r = warp; r < n; r += kRrWarps) {
+    float* z = X32 + r * n;
     for (int i = lane; i < n; i += 32) z[i] = 1.f + 0.001f * (float)((i * 7919 + r * 104729) % 997);
     __syncwarp();
-    warp_inverse_iteration<float>(d32, e32, n, lam32[r], z, SCR32 + warp * 4 * n, piv[warp], 3, Z32, n, 0u);
+    warp_inverse_iteration<float>(d32, e32, n, lam32[r], z, SC32 + warp * 4 * n, piv[warp], 3, X32, n, 0u);
   }
   __syncthreads();
   if (warp == 0) {
-    for (int r = 1; r < k; ++r) {
-      unsigned ortho = 0;
-      for (int j = 0; j < r; ++j)
-        if (fabsf(lam32[r] - lam32[j]) < gap32) ortho |= 1u << j;
-      if (!ortho) continue;
-      float* z = Z32 + r * n;
+    for (int r = 1; r < min(n, k + 8); ++r) {
+      int j0 = r;
+      while (j0 > 0 && lam32[r] - lam32[j0 - 1] < gap32) --j0;
+      if (j0 == r) continue;
+      float* z = X32 + r * n;
       for (int i = lane; i < n; i += 32) z[i] = 1.f + 0.001f * (float)((i * 7919 + r * 104729) % 997);
       __syncwarp();
-      warp_inverse_iteration<float>(d32, e32, n, lam32[r], z, SCR32, piv[0], 3, Z32, n, ortho);
-    }
-  }
-  __syncthreads();
-  // b. FP64 finish: Z (in T) [k][n]
-  double* Z = T;
-  const double gap64 = 1e-6 * fmax(1.0, (double)scale);
-  auto rayleigh = [&](const double* z) {
-    double num = 0.0, den = 0.0;
-    for (int i = lane; i < n; i += 32) {
-      const double zi = z[i];
-      double tz = dd[i] * zi;
-      if (i > 0) tz += ee[i - 1] * z[i - 1];
-      if (i < n - 1) tz += ee[i] * z[i + 1];
-      num += zi * tz;
-      den += zi * zi;
-    }
-    return warp_sum(num) / warp_sum(den);
-  };
-  for (int r = warp; r < k; r += kRrWarps) {
-    double* z = Z + r * n;
-    for (int i = lane; i < n; i += 32) z[i] = (double)Z32[r * n + i];
-    __syncwarp();
-    const double th = rayleigh(z);
-    if (lane == 0) lam[r] = th;
-  }
-  __syncthreads();
-  if (tid < k) {
-    unsigned om = 0;
-    for (int j = 0; j < tid; ++j)
-      if (fabs(lam[tid] - lam[j]) < gap64) om |= 1u << j;
-    omask[tid] = om;
-  }
-  __syncthreads();
-  for (int r = warp; r < k; r += kRrWarps) {
-    if (omask[r]) continue;   // done in order below
-    double* z = Z + r * n;
-    warp_inverse_iteration<double>(dd, ee, n, lam[r], z, SCR + warp * 4 * n, piv[warp], 1, Z, n, 0u);
-    const double th = rayleigh(z);
-    if (lane == 0) lam[r] = th;
-  }
-  __syncthreads();
-  if (warp == 0) {
-    for (int r = 1; r < k; ++r) {
-      const unsigned ortho = omask[r];
-      if (!ortho) continue;
-      double* z = Z + r * n;
-      warp_inverse_iteration<double>(dd, ee, n, lam[r], z, SCR, piv[0], 1, Z, n, ortho);
-      const double th = rayleigh(z);
-      if (lane == 0) lam[r] = th;
+      if (lane == 0) tri_factor_shifted<float>(d32, e32, n, lam32[r], SC32, piv[0]);
       __syncwarp();
-    }
-  }
-  __syncthreads();
-  // c. check every root against FP64 Sturm counts at lam -/+ delta (the r-th eigenvalue
-  //    must lie in between).  An FP32 location can fail when T's norm dwarfs the wanted
-  //    roots (a nearly dependent direction kept by the Cholesky); then all roots are
-  //    redone in FP64: bisection (a thread per root) and three inverse iterations.
-  if (tid < n - 1) e2d[tid] = ee[tid] * ee[tid];
-  if (tid == 0) redo_all = 0;
-  __syncthreads();
-  if (tid < k) {
-    const double lr = lam[tid];
-    const double dl = 1e-12 * (double)scale + 1e-9 * fabs(lr);
-    const int below = sturm_count_prod(dd, e2d, n, lr - dl), upto = sturm_count_prod(dd, e2d, n, lr + dl);
-    if (!(below <= tid && upto > tid) || !(lr == lr)) atomicOr(&redo_all, 1);
-  }
-  __syncthreads();
-  if (redo_all) {
-    if (tid < k) {
-      double lo = (double)lo0 - 1e-3 * (double)scale, hi = (double)hi0 + 1e-3 * (double)scale;
-      for (int it = 0; it < 128; ++it) {
-        const double mid = 0.5 * (lo + hi);
-        if (!(hi - lo > 2.0 * 2.220446049250313e-16 * fmax(fabs(lo), fabs(hi))) || !(mid > lo && mid < hi)) break;
-        if (sturm_count_prod(dd, e2d, n, mid) > tid)
-          hi = mid;
-        else
-          lo = mid;
-      }
-      lam[tid] = 0.5 * (lo + hi);
-    }
-    __syncthreads();
-    for (int r = warp; r < k; r += kRrWarps) {
-      double* z = Z + r * n;
-      for (int i = lane; i < n; i += 32) z[i] = 1.0 + 0.001 * (double)((i * 7919 + r * 104729) % 997);
-      __syncwarp();
-      warp_inverse_iteration<double>(dd, ee, n, lam[r], z, SCR + warp * 4 * n, piv[warp], 3, Z, n, 0u);
-    }
-    __syncthreads();
-    if (warp == 0) {
-      for (int r = 1; r < k; ++r) {
-        unsigned ortho = 0;
-        for (int j = 0; j < r; ++j)
-          if (fabs(lam[r] - lam[j]) < gap64) ortho |= 1u << j;
-        if (!ortho) continue;
-        double* z = Z + r * n;
-        for (int i = lane; i < n; i += 32) z[i] = 1.0 + 0.001 * (double)((i * 7919 + r * 104729) % 997);
+      for (int it = 0; it < 3; ++it) {
+        if (lane == 0) tri_solve_factored<float>(n, z, SC32, piv[0]);
         __syncwarp();
-        warp_inverse_iteration<double>(dd, ee, n, lam[r], z, SCR, piv[0], 3, Z, n, ortho);
+        for (int j = j0; j < r; ++j) {
+          const float* zj = X32 + j * n;
+          float dot = 0.f;
+          for (int i = lane; i < n; i += 32) dot += zj[i] * z[i];
+          dot = warp_sum(dot);
+          for (int i = lane; i < n; i += 32) z[i] -= dot * zj[i];
+          __syncwarp();
+        }
+        float nn = 0.f;
+        for (int i = lane; i < n; i += 32) nn += z[i] * z[i];
+        nn = warp_sum(nn);
+        const float inv = nn > 0.f ? 1.f / sqrtf(nn) : 0.f;
+        for (int i = lane; i < n; i += 32) z[i] *= inv;
+        __syncwarp();
       }
     }
-    __syncthreads();
   }
-  // z <- H_0 H_1 ... H_{n-3} z (a warp per root)
-  // (z held in registers, two entries per lane: n <= 64)
-  for (int r = warp; r < k; r += kRrWarps) {
-    double* z = Z + r * n;
+  __syncthreads();
+  // 3d. back-transformation of every vector, z <- H_0 ... H_{n-3} z (two entries per lane)
+  for (int r = warp; r < n; r += kRrWarps) {
+    float* z = X32 + r * n;
     const int i0 = lane, i1 = lane + 32;
-    double z0 = i0 < n ? z[i0] : 0.0, z1 = i1 < n ? z[i1] : 0.0;
+    float z0 = i0 < n ? z[i0] : 0.f, z1 = i1 < n ? z[i1] : 0.f;
     for (int kk = n - 3; kk >= 0; --kk) {
-      const double tk = tau[kk];
-      if (tk == 0.0) continue;
-      const double v0 = i0 > kk + 1 && i0 < n ? C[i0 * n + kk] : (i0 == kk + 1 ? 1.0 : 0.0);
-      const double v1 = i1 > kk + 1 && i1 < n ? C[i1 * n + kk] : (i1 == kk + 1 ? 1.0 : 0.0);
-      const double sdot = tk * warp_sum(v0 * z0 + v1 * z1);
-      z0 -= sdot * v0;
-      z1 -= sdot * v1;
+      const float tk = tau32[kk];
+      if (tk == 0.f) continue;
+      const float v0 = i0 > kk + 1 && i0 < n ? C32[i0 * n + kk] : (i0 == kk + 1 ? 1.f : 0.f);
+      const float v1 = i1 > kk + 1 && i1 < n ? C32[i1 * n + kk] : (i1 == kk + 1 ? 1.f : 0.f);
+      const float sd = tk * warp_sum(v0 * z0 + v1 * z1);
+      z0 -= sd * v0;
+      z1 -= sd * v1;
     }
     if (i0 < n) z[i0] = z0;
     if (i1 < n) z[i1] = z1;
   }
   __syncthreads();
+  // 3e. FP64 Newton corrections of the k lowest vectors against C' (FP64, in C):
+  //     r_j = C' x_j - theta_j x_j, x_j <- x_j - sum_i xh_i <xh_i, r_j> / (lambda_i - theta_j)
+  //     over the roots i farther than gthr from theta_j; then the final Rayleigh quotients.
+  double* Z = T;                   // k x n: the corrected vectors (read by step 4)
+  double* Yk = SCR;                // k x n: C' x
+  double* Rk = Yk + k * n;         // k x n: residuals, then correction coefficients
+  double* Cm = Rk + k * n;         // n x k: <xh_i, r_j>
+  if (tid < n) lamh[tid] = (double)lam32[tid];
+  for (int q = tid; q < k * n; q += kRrThreads) Z[q] = (double)X32[q];
+  const double gthr = 1e-5 * fmax(1.0, (double)scale);
+  __syncthreads();
+  for (int it = 0; it <= kRrNewton; ++it) {
+    for (int q = tid; q < k * n; q += kRrThreads) {   // Yk = Z C' (C' symmetric)
+      const int j = q / n, i = q - j * n;
+      const double* zr = Z + j * n;
+      double a0 = 0.0, a1 = 0.0;
+      int l = 0;
+      for (; l + 1 < n; l += 2) {
+        a0 += zr[l] * C[l * n + i];
+        a1 += zr[l + 1] * C[(l + 1) * n + i];
+      }
+      if (l < n) a0 += zr[l] * C[l * n + i];
+      Yk[q] = a0 + a1;
+    }
+    __syncthreads();
+    for (int j = warp; j < k; j += kRrWarps) {   // Rayleigh quotients
+      double a = 0.0, b = 0.0;
+      for (int i = lane; i < n; i += 32) {
+        a += Z[j * n + i] * Yk[j * n + i];
+        b += Z[j * n + i] * Z[j * n + i];
+      }
+      a = warp_sum(a);
+      b = warp_sum(b);
+      if (lane == 0) lam[j] = a / b;
+    }
+    __syncthreads();
+    if (it == kRrNewton) break;
+    for (int q = tid; q < k * n; q += kRrThreads) Rk[q] = Yk[q] - lam[q / n] * Z[q];
+    __syncthreads();
+    for (int q = tid; q < n * k; q += kRrThreads) {   // Cm[i][j] = <xh_i, r_j>
+      const int i = q / k, j = q - i * k;
+      const float* xr = X32 + i * n;
+      const double* rr = Rk + j * n;
+      double a0 = 0.0, a1 = 0.0;
+      int l = 0;
+      for (; l + 1 < n; l += 2) {
+        a0 += (double)xr[l] * rr[l];
+        a1 += (double)xr[l + 1] * rr[l + 1];
+      }
+      if (l < n) a0 += (double)xr[l] * rr[l];
+      Cm[q] = a0 + a1;
+    }
+    __syncthreads();
+    for (int q = tid; q < k * n; q += kRrThreads) {   // coefficients, into Rk
+      const int j = q / n, i = q - j * n;
+      const double dl = lamh[i] - lam[j];
+      Rk[q] = fabs(dl) > gthr ? -Cm[i * k + j] / dl : 0.0;
+    }
+    __syncthreads();
+    for (int q = tid; q < k * n; q += kRrThreads) {   // Z += coefficients x Xh
+      const int j = q / n, i = q - j * n;
+      const double* cr = Rk + j * n;
+      double a0 = 0.0, a1 = 0.0;
+      int l = 0;
+      for (; l + 1 < n; l += 2) {
+        a0 += cr[l] * (double)X32[l * n + i];
+        a1 += cr[l + 1] * (double)X32[(l + 1) * n + i];
+      }
+      if (l < n) a0 += cr[l] * (double)X32[l * n + i];
+      Z[q] += a0 + a1;
+    }
+    __syncthreads();
+  }
   // 4. qt[o][r] = sum_a Li[kept[a]][r] Z[o][a]
   for (int q = tid; q < k * m; q += kRrThreads) {
     const int o = q / m, r = q - o * m;

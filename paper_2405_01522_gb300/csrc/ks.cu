@@ -494,18 +494,20 @@ __global__ void __launch_bounds__(kRrThreads) k_rayleigh_ritz(const double* __re
     if (it == kRrNewton) break;
     for (int q = tid; q < k * n; q += kRrThreads) Rk[q] = Yk[q] - lam[q / n] * Z[q];
     __syncthreads();
+    // the correction's own error is second order, so its two products run in FP32
+    // (the residual above needs FP64: it is a difference of nearly equal terms)
     for (int q = tid; q < n * k; q += kRrThreads) {   // Cm[i][j] = <xh_i, r_j>
       const int i = q / k, j = q - i * k;
       const float* xr = X32 + i * n;
       const double* rr = Rk + j * n;
-      double a0 = 0.0, a1 = 0.0;
+      float a0 = 0.f, a1 = 0.f;
       int l = 0;
       for (; l + 1 < n; l += 2) {
-        a0 += (double)xr[l] * rr[l];
-        a1 += (double)xr[l + 1] * rr[l + 1];
+        a0 = fmaf(xr[l], (float)rr[l], a0);
+        a1 = fmaf(xr[l + 1], (float)rr[l + 1], a1);
       }
-      if (l < n) a0 += (double)xr[l] * rr[l];
-      Cm[q] = a0 + a1;
+      if (l < n) a0 = fmaf(xr[l], (float)rr[l], a0);
+      Cm[q] = (double)(a0 + a1);
     }
     __syncthreads();
     for (int q = tid; q < k * n; q += kRrThreads) {   // coefficients, into Rk
@@ -517,14 +519,14 @@ __global__ void __launch_bounds__(kRrThreads) k_rayleigh_ritz(const double* __re
     for (int q = tid; q < k * n; q += kRrThreads) {   // Z += coefficients x Xh
       const int j = q / n, i = q - j * n;
       const double* cr = Rk + j * n;
-      double a0 = 0.0, a1 = 0.0;
+      float a0 = 0.f, a1 = 0.f;
       int l = 0;
       for (; l + 1 < n; l += 2) {
-        a0 += cr[l] * (double)X32[l * n + i];
-        a1 += cr[l + 1] * (double)X32[(l + 1) * n + i];
+        a0 = fmaf((float)cr[l], X32[l * n + i], a0);
+        a1 = fmaf((float)cr[l + 1], X32[(l + 1) * n + i], a1);
       }
-      if (l < n) a0 += cr[l] * (double)X32[l * n + i];
-      Z[q] += a0 + a1;
+      if (l < n) a0 = fmaf((float)cr[l], X32[l * n + i], a0);
+      Z[q] += (double)(a0 + a1);
     }
     __syncthreads();
   }

@@ -175,7 +175,10 @@ def algorithmic_flops(kernel, shape, nq, npsi_out):
 
 
 def algorithmic_bytes(kernel, shape, nq, nocc, npsi, elem=4):
-    """Compulsory HBM bytes of one launch over nq pairs (model stated in the design doc)."""
+    """Compulsory HBM bytes of one launch over nq pairs: each pair's x-transformed
+    intermediate ((Mx/2 + 1) x nz x ny complex, M = 2n) is written once by pass 1, read and
+    written once by pass 2 and read once by pass 3; passes 1 and 3 also read (and pass 3
+    writes) the orbitals, pass 2 reads the (M/2 + 1)^3 kernel table once."""
     nz, ny, nx = shape
     N = nz * ny * nx
     inter = (nx + 1) * nz * ny * 2 * elem          # (Mx/2 + 1) * nz * ny complex per pair

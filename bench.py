@@ -151,8 +151,10 @@ def line_flops(A, kind):
         return 16 * _half_in(A) + tw + A * DFT_FLOPS[16]
     if kind == "inv_keep_half":     # inverse, only outputs below n kept (stage 2 pruned)
         return 16 * DFT_FLOPS[A] + tw + A * (_half_out(16) if A % 2 == 0 else DFT_FLOPS[16])
-    if kind == "z_inverse":         # inverse z after the multiply (stage-1 outputs pruned)
-        return A * DFT_FLOPS[16] + A * 16 * 6 + 16 * (_half_out(A) if A % 2 == 0 else DFT_FLOPS[A])
+    if kind == "z_inverse":         # inverse z after the multiply (stage-1 outputs pruned);
+        # even A: twiddles after the transpose, 16 lanes x (A - 1); odd A: A lanes x 16
+        ztw = 16 * (A - 1) * 6 if A % 2 == 0 else A * 16 * 6
+        return A * DFT_FLOPS[16] + ztw + 16 * (_half_out(A) if A % 2 == 0 else DFT_FLOPS[A])
     raise ValueError(kind)
 
 

@@ -278,13 +278,27 @@ template <typename R, int AY, int NT>
 __device__ __forceinline__ void y_inverse(Cx<R>* D, int DP, int nz, int ny, const Cx<R>* __restrict__ twy,
                                           Cx<R>* sc) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, t = lane & 15;
+  // this lane's stage-1 twiddles (conjugated below), the same for every row
+  Cx<R> tw[AY];
+  if constexpr (AY % 2 == 0) {
+#pragma unroll
+    for (int k1 = 1; k1 < AY; ++k1) tw[k1] = twy[t * AY + k1];
+  }
   for (int z0 = 2 * warp; z0 < nz; z0 += NT / 16) {
     const int z = z0 + (lane >> 4);
     const bool ok = z < nz;
     Cx<R> v[AY];
 #pragma unroll
     for (int a = 0; a < AY; ++a) v[a] = ok ? D[z * DP + t + 16 * a] : cx<R>(R(0), R(0));
-    stage1_store<AY, 1>(v, t, twy, sc);
+    if constexpr (AY % 2 == 0) {
+      Dft<AY, 1>::run(v);
+#pragma unroll
+      for (int k1 = 1; k1 < AY; ++k1) v[k1] = cmul(v[k1], conj(tw[k1]));
+#pragma unroll
+      for (int k1 = 0; k1 < AY; ++k1) sc[k1 * kScrPitch + t] = v[k1];
+    } else {
+      stage1_store<AY, 1>(v, t, twy, sc);
+    }
     __syncwarp();
     Cx<R> u[16];
     if (t < AY) {
@@ -391,11 +405,16 @@ __device__ __forceinline__ void pass2_plane(const Geom& g, Cx<R>* P, int kx, con
         u[k2] = cx<R>(u[k2].x * m, u[k2].y * m);
       }
       Dft<16, 1>::run(u);
+      if constexpr (AZ % 2 == 0) {
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        Cx<R> w = twz[j * AZ + t];
-        w.y = -w.y;
-        sc[t * kScrPitch + j] = cmul(u[j], w);
+        for (int j = 0; j < 16; ++j) sc[t * kScrPitch + j] = u[j];
+      } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          Cx<R> w = twz[j * AZ + t];
+          w.y = -w.y;
+          sc[t * kScrPitch + j] = cmul(u[j], w);
+        }
       }
     }
     __syncwarp();
@@ -403,6 +422,11 @@ __device__ __forceinline__ void pass2_plane(const Geom& g, Cx<R>* P, int kx, con
 #pragma unroll
     for (int k1 = 0; k1 < AZ; ++k1) r[k1] = sc[k1 * kScrPitch + t];
     if constexpr (AZ % 2 == 0) {
+      // the inverse twiddle w_M^{-j k1} (j the 16-point output index) taken after the
+      // transpose, where lane t = j holds k1 = 0 .. AZ-1: the conjugates of the forward
+      // twiddles this lane already holds, instead of 16 table loads per column
+#pragma unroll
+      for (int k1 = 1; k1 < AZ; ++k1) r[k1] = cmul(r[k1], conj(twf[k1]));
       Cx<R> o[AZ / 2];
       DftHalfOut<AZ, 1>::run(r, o);   // only z = t + 16 a < nz = 8 AZ, i.e. a < AZ / 2
 #pragma unroll

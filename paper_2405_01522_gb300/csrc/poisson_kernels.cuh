@@ -689,6 +689,12 @@ __device__ __forceinline__ void pass3_item(const Geom& g, const PairMap<R>& pm, 
 #pragma unroll
   for (int k2 = 0; k2 < 16; ++k2) acc0[k2] = acc1[k2] = R(0);
 
+  // this lane's stage-1 twiddles, the same for every entry
+  Cx<R> tw[AX];
+  if constexpr (AX % 2 == 0) {
+#pragma unroll
+    for (int k1 = 1; k1 < AX; ++k1) tw[k1] = twx[t * AX + k1];
+  }
   const int ne = pot ? 1 : pm.nentries(p);
   __syncthreads();   // the buffers may still be read by a previous item of this CTA
   pass3_prefetch<R, AX>(g, pm, q0, p, 0, z, y0, nrow, pot, inter, xs_of(0), tile_of(0));
@@ -720,7 +726,15 @@ __device__ __forceinline__ void pass3_item(const Geom& g, const PairMap<R>& pm, 
       }
       v[a] = cx<R>(xa.x - xb.y, xa.y + xb.x);
     }
-    stage1_store<AX, 1>(v, t, twx, sc);
+    if constexpr (AX % 2 == 0) {
+      Dft<AX, 1>::run(v);
+#pragma unroll
+      for (int k1 = 1; k1 < AX; ++k1) v[k1] = cmul(v[k1], conj(tw[k1]));
+#pragma unroll
+      for (int k1 = 0; k1 < AX; ++k1) sc[k1 * kScrPitch + t] = v[k1];
+    } else {
+      stage1_store<AX, 1>(v, t, twx, sc);
+    }
     __syncwarp();
     if (t < AX) {
       Cx<R> u[16];

@@ -146,6 +146,13 @@ int make_tables(rsx_ctx* c) {
   const double npad = (double)g.Mz * g.My * g.Mx;
   const double scale = c->h * c->h * c->h / npad;
   cudaError_t e = launch_ghat(g, c->h, scale, dcos[0], dcos[1], dcos[2], b0, b1, c->vhat, sizeof(R) == 8, 0);
+  if (e == cudaSuccess && sizeof(R) == 4) {
+    size_t hz_have = 0;
+    if (grow(c, &c->vhatz, &hz_have, (size_t)hx * hy * g.Mz * sizeof(float), "kernel table (lane order)") != RSX_OK)
+      e = cudaErrorMemoryAllocation;
+    else
+      e = launch_vhat_lanes(g, (const float*)c->vhat, (float*)c->vhatz, 0);
+  }
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   cudaFree(b0);
   cudaFree(b1);
@@ -210,7 +217,7 @@ int solve_pairs(rsx_ctx* c, const PairMap<R>& pm, int q0, int nq, int p0, int np
   }
   {
     ProfScope ps(c, kKPass2, s);
-    rc = check_cuda(c, launch_pass2<R>(g, nq, inter, twy, twz, (const R*)c->vhat, gscr, grid, s), "pass 2");
+    rc = check_cuda(c, launch_pass2<R>(g, nq, inter, twy, twz, (const R*)c->vhat, (const float*)c->vhatz, gscr, grid, s), "pass 2");
   }
   if (rc) return rc;
   if (out != nullptr) {
@@ -400,7 +407,7 @@ int rsx_destroy(rsx_ctx* c) {
   cudaDeviceSynchronize();
   prof_collect(c);
   for (cudaEvent_t e : c->prof_pool) cudaEventDestroy(e);
-  void* bufs[] = {c->vhat, c->tw[0], c->tw[1], c->tw[2], c->work, c->gscr, c->dsm, c->smallr, c->status,
+  void* bufs[] = {c->vhat, c->vhatz, c->tw[0], c->tw[1], c->tw[2], c->work, c->gscr, c->dsm, c->smallr, c->status,
                   c->panel_hi, c->panel_lo, c->gemm_part, c->eig_work, c->gscr_kd, c->pos, c->tdhf_work, c->specw, c->ones};
   for (void* b : bufs)
     if (b) cudaFree(b);

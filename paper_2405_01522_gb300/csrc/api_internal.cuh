@@ -25,6 +25,7 @@ struct rsx_ctx {
   size_t work_limit = 0;
   // device buffers owned by the context
   void* vhat = nullptr;                 // kernel table T[kx][ky][kz] (R)
+  void* vhatz = nullptr;                // FP32: the same in pass 2's lane order (launch_vhat_lanes)
   void* tw[3] = {nullptr, nullptr, nullptr};
   void* work = nullptr;   size_t work_bytes = 0;     // FFT intermediates
   void* gscr = nullptr;   size_t gscr_bytes = 0;     // pass-2 planes when shared memory is too small

@@ -280,7 +280,7 @@ int record(rsx_batch* b, cudaStream_t s) {
     const long long nwork = (long long)grp.npairs * c->g.Hx;
     const int grid = (int)std::min<long long>(nwork, (long long)c->pass2_ctas_per_sm<float>() * c->nsm);
     rc = bcuda(b, launch_pass2<float>(c->g, grp.npairs, inter, (const Cx<float>*)c->tw[1], (const Cx<float>*)c->tw[0],
-                                      (const float*)c->vhat, nullptr, grid, s),
+                                      (const float*)c->vhat, (const float*)c->vhatz, nullptr, grid, s),
                "batch pass 2");
     if (rc) return rc;
   }

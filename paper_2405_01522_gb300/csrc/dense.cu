@@ -454,8 +454,32 @@ __global__ void k_pair_products(const R* __restrict__ A, int na, const R* __rest
   }
 }
 
+// Pass 2's FP32 copy of the kernel table in the order its lanes read it: after the
+// 16-point z transforms lane t (< Az) holds kz = t + Az k2, k2 < 16, and reads the
+// factors of one column (kx, |ky|) as four float4 at [(k2 / 4) Az + t], so that a
+// half-warp's request covers 16 contiguous bytes per lane.  out[kx][iy][k2/4][t][k2%4] =
+// T[kx][iy][fold(t + Az k2)], fold(kz) = min(kz, Mz - kz).
+__global__ void k_vhat_lanes(const float* __restrict__ T, int rows, int hz, int Az, float* __restrict__ out) {
+  const int Mz = 16 * Az;
+  const size_t n = (size_t)rows * Mz;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t row = i / Mz;
+    const int p = (int)(i - row * Mz);
+    const int q = p / (4 * Az), rem = p - q * 4 * Az;
+    const int t = rem >> 2, k2 = 4 * q + (rem & 3);
+    const int kz = t + Az * k2;
+    out[i] = T[row * hz + (kz <= Mz / 2 ? kz : Mz - kz)];
+  }
+}
+
 // ---------------------------------------------------------------------------------
 // host launchers
+
+cudaError_t launch_vhat_lanes(const Geom& g, const float* table, float* out, cudaStream_t s) {
+  const int rows = (g.Mx / 2 + 1) * (g.My / 2 + 1);
+  k_vhat_lanes<<<1024, 256, 0, s>>>(table, rows, g.Mz / 2 + 1, g.Az, out);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_ghat(const Geom& g, double h, double scale, const double* cos_z, const double* cos_y,
                         const double* cos_x, double* buf0, double* buf1, void* table, bool fp64,

@@ -82,7 +82,7 @@ int exchange_noalloc(rsx_ctx* c, const void* phi, int nocc, const void* psi, int
   for (int p = 0; p < npsi; ++p) {
     int rc = check_cuda(c, launch_pass1<R>(g, pm, p * nocc, nocc, inter, twx, s), "noalloc pass 1");
     if (rc) return rc;
-    rc = check_cuda(c, launch_pass2<R>(g, nocc, inter, twy, twz, (const R*)c->vhat, nullptr, grid, s),
+    rc = check_cuda(c, launch_pass2<R>(g, nocc, inter, twy, twz, (const R*)c->vhat, (const float*)c->vhatz, nullptr, grid, s),
                     "noalloc pass 2");
     if (rc) return rc;
     rc = check_cuda(c, launch_pass3<R>(g, pm, p * nocc, p, 1, 0, inter, twx, (R*)out + (size_t)p * N, s),

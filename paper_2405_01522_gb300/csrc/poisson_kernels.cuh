@@ -350,8 +350,9 @@ __device__ __forceinline__ void prefetch_plane_upper(Cx<R>* D, int DP, const Cx<
 
 template <typename R, int AY, int AZ, int NT>
 __device__ __forceinline__ void pass2_plane(const Geom& g, Cx<R>* P, int kx, const Cx<R>* __restrict__ twy,
-                                            const Cx<R>* __restrict__ twz, const R* __restrict__ vhat, Cx<R>* D,
-                                            Cx<R>* scr, bool prefetched = false, const Cx<R>* Pnext = nullptr) {
+                                            const Cx<R>* __restrict__ twz, const R* __restrict__ vhat,
+                                            const float* __restrict__ vlanes, Cx<R>* D, Cx<R>* scr,
+                                            bool prefetched = false, const Cx<R>* Pnext = nullptr) {
   constexpr int LY = 16 * AY;
   constexpr int LZ = 16 * AZ;
   constexpr int AMAX = AY > AZ ? AY : AZ;
@@ -398,11 +399,25 @@ __device__ __forceinline__ void pass2_plane(const Geom& g, Cx<R>* P, int kx, con
     __syncwarp();
     if (t < AZ) {
       Dft<16, -1>::run(u);
+      if constexpr (sizeof(R) == 4) {
+        // four 16-byte loads per lane from the lane-order table (k_vhat_lanes): the
+        // factors of kz = t + AZ k2, k2 = 4 j .. 4 j + 3
+        const float4* vq = reinterpret_cast<const float4*>(vlanes + ((size_t)kx * Hy + iy) * LZ) + t;
 #pragma unroll
-      for (int k2 = 0; k2 < 16; ++k2) {
-        const int kz = t + AZ * k2;
-        const R m = __ldg(vcol + (kz <= LZ / 2 ? kz : LZ - kz));
-        u[k2] = cx<R>(u[k2].x * m, u[k2].y * m);
+        for (int j = 0; j < 4; ++j) {
+          const float4 m = __ldg(vq + j * AZ);
+          u[4 * j] = cscale(u[4 * j], m.x);
+          u[4 * j + 1] = cscale(u[4 * j + 1], m.y);
+          u[4 * j + 2] = cscale(u[4 * j + 2], m.z);
+          u[4 * j + 3] = cscale(u[4 * j + 3], m.w);
+        }
+      } else {
+#pragma unroll
+        for (int k2 = 0; k2 < 16; ++k2) {
+          const int kz = t + AZ * k2;
+          const R m = __ldg(vcol + (kz <= LZ / 2 ? kz : LZ - kz));
+          u[k2] = cx<R>(u[k2].x * m, u[k2].y * m);
+        }
       }
       Dft<16, 1>::run(u);
       if constexpr (AZ % 2 == 0) {
@@ -454,7 +469,8 @@ __device__ __forceinline__ void pass2_plane(const Geom& g, Cx<R>* P, int kx, con
 template <typename R, int AY, int AZ, bool DSMEM, int NT>
 __global__ void __launch_bounds__(NT, 1) k_pass2(Geom g, int nq, Cx<R>* __restrict__ inter,
                                                  const Cx<R>* __restrict__ twy, const Cx<R>* __restrict__ twz,
-                                                 const R* __restrict__ vhat, R* gscratch) {
+                                                 const R* __restrict__ vhat, const float* __restrict__ vlanes,
+                                                 R* gscratch) {
   constexpr int AMAX = AY > AZ ? AY : AZ;
   constexpr int SP = AMAX * kScrPitch;
   constexpr int DP = 16 * AY + 1;
@@ -474,7 +490,7 @@ __global__ void __launch_bounds__(NT, 1) k_pass2(Geom g, int nq, Cx<R>* __restri
   for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
     const int kx = w % g.Hx;
     const int wn = w + (int)gridDim.x;
-    pass2_plane<R, AY, AZ, NT>(g, plane_ptr(w), kx, twy, twz, vhat, D, scr, pipe,
+    pass2_plane<R, AY, AZ, NT>(g, plane_ptr(w), kx, twy, twz, vhat, vlanes, D, scr, pipe,
                                (pipe && wn < nwork) ? plane_ptr(wn) : nullptr);
   }
 }

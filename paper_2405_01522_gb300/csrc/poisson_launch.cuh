@@ -100,9 +100,10 @@ int pass2_occupancy(const Geom& g) {
 
 template <typename R>
 cudaError_t launch_pass2(const Geom& g, int nq, Cx<R>* inter, const Cx<R>* twy, const Cx<R>* twz,
-                         const R* vhat, R* gscratch, int grid, cudaStream_t s) {
+                         const R* vhat, const float* vhat_lanes, R* gscratch, int grid, cudaStream_t s) {
   if (nq <= 0) return cudaSuccess;
   if (g.Ay != g.Az) return cudaErrorInvalidValue;
+  if (sizeof(R) == 4 && vhat_lanes == nullptr) return cudaErrorInvalidValue;   // FP32 reads the lane-order table
   bool fits = false;
   const size_t smem = pass2_smem_bytes<R>(g, &fits);
   if (!fits && gscratch == nullptr) return cudaErrorInvalidValue;
@@ -114,12 +115,12 @@ cudaError_t launch_pass2(const Geom& g, int nq, Cx<R>* inter, const Cx<R>* twy, 
       auto k = pass2_kernel<R, a>(nt);                                                               \
       cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
       if (e != cudaSuccess) return e;                                                                \
-      k<<<grid, nt, smem, s>>>(g, nq, inter, twy, twz, vhat, gscratch);                              \
+      k<<<grid, nt, smem, s>>>(g, nq, inter, twy, twz, vhat, vhat_lanes, gscratch);                  \
     } else {                                                                                         \
       auto k = k_pass2<R, a, a, false, 256>;                                                         \
       cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
       if (e != cudaSuccess) return e;                                                                \
-      k<<<grid, kThreads, smem, s>>>(g, nq, inter, twy, twz, vhat, gscratch);                        \
+      k<<<grid, kThreads, smem, s>>>(g, nq, inter, twy, twz, vhat, vhat_lanes, gscratch);            \
     }                                                                                                \
     return cudaGetLastError();                                                                       \
   }

@@ -5,5 +5,5 @@ namespace rsx {
 template size_t pass2_smem_bytes<float>(const Geom&, bool*);
 template int pass2_occupancy<float>(const Geom&);
 template cudaError_t launch_pass2<float>(const Geom&, int, Cx<float>*, const Cx<float>*, const Cx<float>*, const float*,
-                                       float*, int, cudaStream_t);
+                                       const float*, float*, int, cudaStream_t);
 }  // namespace rsx

@@ -75,7 +75,7 @@ cudaError_t launch_pass1(const Geom& g, const PairMap<R>& pm, int q0, int nq, Cx
                          const Cx<R>* twx, cudaStream_t s);
 template <typename R>
 cudaError_t launch_pass2(const Geom& g, int nq, Cx<R>* inter, const Cx<R>* twy, const Cx<R>* twz,
-                         const R* vhat, R* gscratch, int grid, cudaStream_t s);
+                         const R* vhat, const float* vhat_lanes, R* gscratch, int grid, cudaStream_t s);
 template <typename R>
 cudaError_t launch_pass3(const Geom& g, const PairMap<R>& pm, int q0, int p0, int np, int pot, const Cx<R>* inter,
                          const Cx<R>* twx, R* out, cudaStream_t s);

@@ -398,7 +398,7 @@ int rsx_batch_create(rsx_batch** out, int nmol, const int* edges, const int* noc
   int nsm = 0;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device);
   const int L = 16 * maxA, H = L / 2 + 1;
-  b->smem[0] = sizeof(Cx<float>) * ((size_t)kLinesPerCta * maxA * kScrPitch + (size_t)H * kRowsPerCta);
+  b->smem[0] = sizeof(Cx<float>) * std::max((size_t)kLinesPerCta * maxA * kScrPitch, (size_t)H * kRowsPerCta);
   b->smem[2] = sizeof(Cx<float>) * (size_t)kLinesPerCta * maxA * kScrPitch + 2 * pass3_buffer_elems<float>(maxA, nmaxx);
   const void* kern[3] = {(const void*)k_batch_pass1, nullptr, (const void*)k_batch_pass3};
   for (int p = 0; p < 3; p += 2) {

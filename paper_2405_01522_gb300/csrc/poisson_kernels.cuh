@@ -127,7 +127,7 @@ __device__ __forceinline__ void pass1_item(const Geom& g, const R* f1, const R* 
   constexpr int SP = AX * kScrPitch;
   constexpr int H = L / 2 + 1;
   Cx<R>* scr = reinterpret_cast<Cx<R>*>(smem_raw);
-  Cx<R>* xs = scr + kLinesPerCta * SP;  // [H][kRowsPerCta], see xs_idx
+  Cx<R>* xs = scr;   // [H][kRowsPerCta], see xs_idx: reuses the line scratch once all lines are done with it
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int t = lane & 15, line = warp * 2 + (lane >> 4);
   const int y0 = yblk * kRowsPerCta;
@@ -166,12 +166,25 @@ __device__ __forceinline__ void pass1_item(const Geom& g, const R* f1, const R* 
     for (int k2 = 0; k2 < 16; ++k2) sc[t + AX * k2] = u[k2];  // natural order U[k]
   }
   __syncwarp();
-  // split the packed line: X_a(k) = (U(k) + conj U(L-k)) / 2,  X_b(k) = (U(k) - conj U(L-k)) / 2i
-  for (int k = t; k < H; k += 16) {
-    const Cx<R> U = sc[k];
-    const Cx<R> Um = sc[(L - k) % L];
-    st_granule(xs + xs_idx(k, 2 * line), cx<R>(R(0.5) * (U.x + Um.x), R(0.5) * (U.y - Um.y)),
-               cx<R>(R(0.5) * (U.y + Um.y), R(-0.5) * (U.x - Um.x)));
+  // split the packed line: X_a(k) = (U(k) + conj U(L-k)) / 2,  X_b(k) = (U(k) - conj U(L-k)) / 2i,
+  // into registers first: the staging buffer overwrites every line's scratch
+  constexpr int NK = (H + 15) / 16;
+  Cx<R> xa[NK], xb[NK];
+#pragma unroll
+  for (int i = 0; i < NK; ++i) {
+    const int k = t + 16 * i;
+    if (k < H) {
+      const Cx<R> U = sc[k];
+      const Cx<R> Um = sc[(L - k) % L];
+      xa[i] = cx<R>(R(0.5) * (U.x + Um.x), R(0.5) * (U.y - Um.y));
+      xb[i] = cx<R>(R(0.5) * (U.y + Um.y), R(-0.5) * (U.x - Um.x));
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < NK; ++i) {
+    const int k = t + 16 * i;
+    if (k < H) st_granule(xs + xs_idx(k, 2 * line), xa[i], xb[i]);
   }
   __syncthreads();
   const int nrow = min(kRowsPerCta, g.ny - y0);   // a multiple of 8 (ny = 8 A)

@@ -15,10 +15,12 @@ inline bool axis_supported_impl(int A) {
   }
 }
 
+// line scratch and the row-block staging buffer share the same bytes (pass1_item)
 template <typename R>
 inline size_t pass1_smem(int AX) {
   const int L = 16 * AX, H = L / 2 + 1;
-  return sizeof(Cx<R>) * ((size_t)kLinesPerCta * AX * kScrPitch + (size_t)H * kRowsPerCta);
+  const size_t scr = (size_t)kLinesPerCta * AX * kScrPitch, xs = (size_t)H * kRowsPerCta;
+  return sizeof(Cx<R>) * (scr > xs ? scr : xs);
 }
 template <typename R>
 inline size_t pass3_smem(int AX, int nx) {

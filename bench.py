@@ -132,7 +132,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12     # SMs x FP32 lanes x FMA x 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) from ncu captures of small cases
 # of the same kernels (profiles/pass2_yz_kernel_96cubed.md, profiles/k_syrk_bf16x3_48cubed.md),
 # scaled to a full launch by the units it processes:
-PASS2_DRAM_BYTES_PER_PAIR_96 = 400.52e6 / 32    # 32-pair launch at 96^3 (12.5 MB/pair)
+PASS2_DRAM_BYTES_PER_PAIR_96 = 404.98e6 / 32    # 32-pair launch at 96^3 (12.66 MB/pair)
 SYRK_DRAM_PER_PANEL_BYTE = 1.938e9 / 1.850e9    # DRAM bytes per byte of the two bf16 panels
 
 

@@ -73,6 +73,124 @@ __global__ void k_ham_apply(const float* __restrict__ f, int nb, int n, float in
   out[(size_t)b * N + v] = r;
 }
 
+// The same operator by z-marching tiles: a block owns kHamTy rows y of 4-point float4
+// columns along x (one per thread) for kHamZc consecutive planes z.  Each thread keeps
+// its column's planes z-2 .. z+2 in registers; the plane z rows y0-2 .. y0+kHamTy+1 are
+// staged in shared memory (with one zero float4 on each side in x) for the x and y
+// neighbours.  One global load per point instead of thirteen; the arithmetic per point
+// is that of k_ham_apply, term by term.  n % 4 == 0, every array 16-byte aligned.
+constexpr int kHamTy = 8;
+constexpr int kHamZc = 12;
+
+__device__ __forceinline__ float ham_point(float c, float xm2, float xm1, float xp1, float xp2, float ym2,
+                                           float ym1, float yp1, float yp2, float zm2, float zm1, float zp1,
+                                           float zp2, float inv12h2) {
+  const float a1 = (xm1 - c) + (xp1 - c);
+  const float a2 = (xm2 - c) + (xp2 - c);
+  const float b1 = (ym1 - c) + (yp1 - c);
+  const float b2 = (ym2 - c) + (yp2 - c);
+  const float c1 = (zm1 - c) + (zp1 - c);
+  const float c2 = (zm2 - c) + (zp2 - c);
+  float lap = 16.f * a1 - a2;
+  lap += 16.f * b1 - b2;
+  lap += 16.f * c1 - c2;
+  return -0.5f * lap * inv12h2;
+}
+
+__global__ void __launch_bounds__(512) k_ham_apply_z(const float* __restrict__ f, int n, float inv12h2,
+                                                     const float* __restrict__ V, const double* __restrict__ shift,
+                                                     const float* __restrict__ mask, float* __restrict__ out) {
+  extern __shared__ float4 hs4[];   // [kHamTy + 4][n/4 + 2]
+  const int n4 = n >> 2, W = n4 + 2;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int y0 = blockIdx.x * kHamTy, y = y0 + ty;
+  const int z0 = blockIdx.y * kHamZc, z1 = min(z0 + kHamZc, n);
+  const int b = blockIdx.z;
+  const size_t nn4 = (size_t)n * n4, N4 = nn4 * n;
+  const float4* f4 = reinterpret_cast<const float4*>(f) + (size_t)b * N4;
+  const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+  auto ld = [&](int yy, int zz) {
+    return (yy >= 0 && yy < n && zz >= 0 && zz < n) ? __ldg(f4 + (size_t)zz * nn4 + (size_t)yy * n4 + tx) : zero;
+  };
+  for (int r = ty; r < kHamTy + 4; r += kHamTy) {   // x halo: zeros, never overwritten
+    if (tx == 0) hs4[r * W] = zero;
+    if (tx == n4 - 1) hs4[r * W + n4 + 1] = zero;
+  }
+  float4 q0 = ld(y, z0 - 2), q1 = ld(y, z0 - 1), q2 = ld(y, z0), q3 = ld(y, z0 + 1), q4 = ld(y, z0 + 2);
+  const double sh = shift ? shift[b] : 0.0;
+  for (int z = z0; z < z1; ++z) {
+    __syncthreads();   // the previous plane's neighbour reads are done
+    hs4[(ty + 2) * W + 1 + tx] = q2;
+    if (ty < 2) hs4[ty * W + 1 + tx] = ld(y0 - 2 + ty, z);
+    if (ty >= kHamTy - 2) hs4[(ty + 4) * W + 1 + tx] = ld(y0 + ty + 2, z);
+    __syncthreads();
+    if (y < n) {
+      const float4 c = q2;
+      const float4 L = hs4[(ty + 2) * W + tx], R = hs4[(ty + 2) * W + 2 + tx];
+      const float4 ym1 = hs4[(ty + 1) * W + 1 + tx], yp1 = hs4[(ty + 3) * W + 1 + tx];
+      const float4 ym2 = hs4[ty * W + 1 + tx], yp2 = hs4[(ty + 4) * W + 1 + tx];
+      float4 r;
+      r.x = ham_point(c.x, L.z, L.w, c.y, c.z, ym2.x, ym1.x, yp1.x, yp2.x, q0.x, q1.x, q3.x, q4.x, inv12h2);
+      r.y = ham_point(c.y, L.w, c.x, c.z, c.w, ym2.y, ym1.y, yp1.y, yp2.y, q0.y, q1.y, q3.y, q4.y, inv12h2);
+      r.z = ham_point(c.z, c.x, c.y, c.w, R.x, ym2.z, ym1.z, yp1.z, yp2.z, q0.z, q1.z, q3.z, q4.z, inv12h2);
+      r.w = ham_point(c.w, c.y, c.z, R.x, R.y, ym2.w, ym1.w, yp1.w, yp2.w, q0.w, q1.w, q3.w, q4.w, inv12h2);
+      const size_t v4 = (size_t)z * nn4 + (size_t)y * n4 + tx;
+      if (V) {
+        const float4 vv = __ldg(reinterpret_cast<const float4*>(V) + v4);
+        r.x += vv.x * c.x;
+        r.y += vv.y * c.y;
+        r.z += vv.z * c.z;
+        r.w += vv.w * c.w;
+      }
+      if (shift) {
+        const float s = (float)sh;
+        r.x += s * c.x;
+        r.y += s * c.y;
+        r.z += s * c.z;
+        r.w += s * c.w;
+      }
+      if (mask) {
+        const float4 m = __ldg(reinterpret_cast<const float4*>(mask) + v4);
+        r.x *= m.x;
+        r.y *= m.y;
+        r.z *= m.z;
+        r.w *= m.w;
+      }
+      reinterpret_cast<float4*>(out)[(size_t)b * N4 + v4] = r;
+    }
+    q0 = q1;
+    q1 = q2;
+    q2 = q3;
+    q3 = q4;
+    q4 = ld(y, z + 3);
+  }
+}
+
+// launch shape of k_ham_apply: x along whole warps, as many y rows as fit in 256 threads
+dim3 ham_block(int n) {
+  const int xt = (n + 31) / 32 * 32;
+  return dim3(xt, std::max(1, 256 / xt));
+}
+dim3 ham_grid(int nb, int n) {
+  const dim3 bl = ham_block(n);
+  return dim3((n + bl.y - 1) / bl.y, n, nb);
+}
+
+// out = H f over nb bands: the z-marching tiles where the layout allows, else one thread
+// per point
+void launch_ham(const float* f, int nb, int n, float inv12h2, const float* V, const double* shift, const float* mask,
+                float* out, cudaStream_t s) {
+  auto al16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
+  const int n4 = n / 4;
+  if (n % 4 == 0 && n4 * kHamTy <= 512 && al16(f) && al16(out) && (!V || al16(V)) && (!mask || al16(mask))) {
+    const dim3 grid((n + kHamTy - 1) / kHamTy, (n + kHamZc - 1) / kHamZc, nb), block(n4, kHamTy);
+    const size_t smem = sizeof(float4) * (size_t)(kHamTy + 4) * (n4 + 2);
+    k_ham_apply_z<<<grid, block, smem, s>>>(f, n, inv12h2, V, shift, mask, out);
+  } else {
+    k_ham_apply<<<ham_grid(nb, n), ham_block(n), 0, s>>>(f, nb, n, inv12h2, V, shift, mask, out);
+  }
+}
+
 // rows of X (row = blockIdx.y) times the domain mask
 __global__ void k_mask_rows(float* __restrict__ X, const float* __restrict__ mask, size_t N) {
   float* x = X + (size_t)blockIdx.y * N;
@@ -739,22 +857,11 @@ int row_dots(rsx_eig* e, const float* X, const float* Y, const float* w, int row
   return ecuda(e, cudaGetLastError(), "row dots");
 }
 
-// launch shape of k_ham_apply: x along whole warps, as many y rows as fit in 256 threads
-dim3 ham_block(int n) {
-  const int xt = (n + 31) / 32 * 32;
-  return dim3(xt, std::max(1, 256 / xt));
-}
-dim3 ham_grid(int nb, int n) {
-  const dim3 bl = ham_block(n);
-  return dim3((n + bl.y - 1) / bl.y, n, nb);
-}
-
 // out = H f (the full operator, with the exchange term, when V is given; the kinetic part
 // plus shift when V is null)
 int ham(rsx_eig* e, const float* f, int nb, float* out, const double* shift, const float* V, cudaStream_t s) {
   const size_t N = (size_t)e->n * e->n * e->n;
-  k_ham_apply<<<ham_grid(nb, e->n), ham_block(e->n), 0, s>>>(f, nb, e->n, (float)(1.0 / (12.0 * e->h * e->h)), V,
-                                                              shift, e->mask, out);
+  launch_ham(f, nb, e->n, (float)(1.0 / (12.0 * e->h * e->h)), V, shift, e->mask, out, s);
   int rc = ecuda(e, cudaGetLastError(), "hamiltonian");
   if (rc || !V || e->xmode == 0) return rc;
   if (e->xmode == 1) {
@@ -1173,8 +1280,7 @@ int rsx_scf_step(rsx_scf* c, int inner, double* out_host, void* stream) {
   // energy parts of the entering orbitals: one-body, Hartree
   rc = rsx_poisson(c->ctx, rho_e, c->vh, stream);
   if (rc) return sfail(c, rc, "Poisson (energy) failed");
-  k_ham_apply<<<ham_grid(k, c->n), ham_block(c->n), 0, s>>>(phi_e, k, c->n, (float)(1.0 / (12.0 * c->h * c->h)), c->vext,
-                                                          nullptr, c->eig->mask, c->hphi);
+  launch_ham(phi_e, k, c->n, (float)(1.0 / (12.0 * c->h * c->h)), c->vext, nullptr, c->eig->mask, c->hphi, s);
   rc = scf_gram(c, phi_e, k, c->hphi, k, c->dsm + 1024, s);
   if (!rc) rc = scf_gram(c, rho_e, 1, c->vh, 1, c->dsm + 2048, s);
   if (rc) return rc;

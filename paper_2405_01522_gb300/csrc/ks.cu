@@ -79,6 +79,9 @@ __global__ void k_ham_apply(const float* __restrict__ f, int nb, int n, float in
 // staged in shared memory (with one zero float4 on each side in x) for the x and y
 // neighbours.  One global load per point instead of thirteen; the arithmetic per point
 // is that of k_ham_apply, term by term.  n % 4 == 0, every array 16-byte aligned.
+// With jr given, the output is one damped Jacobi sweep on (H) x = jr instead (H with
+// V = 0 and the shift T_b): out = f + omega (jr - H f) / (d0 + T_b), the arithmetic of
+// k_ke_jacobi.
 constexpr int kHamTy = 8;
 constexpr int kHamZc = 12;
 
@@ -99,7 +102,8 @@ __device__ __forceinline__ float ham_point(float c, float xm2, float xm1, float 
 
 __global__ void __launch_bounds__(512) k_ham_apply_z(const float* __restrict__ f, int n, float inv12h2,
                                                      const float* __restrict__ V, const double* __restrict__ shift,
-                                                     const float* __restrict__ mask, float* __restrict__ out) {
+                                                     const float* __restrict__ mask, const float* __restrict__ jr,
+                                                     float d0, float omega, float* __restrict__ out) {
   extern __shared__ float4 hs4[];   // [kHamTy + 4][n/4 + 2]
   const int n4 = n >> 2, W = n4 + 2;
   const int tx = threadIdx.x, ty = threadIdx.y;
@@ -156,6 +160,14 @@ __global__ void __launch_bounds__(512) k_ham_apply_z(const float* __restrict__ f
         r.z *= m.z;
         r.w *= m.w;
       }
+      if (jr) {
+        const float4 rr = __ldg(reinterpret_cast<const float4*>(jr) + (size_t)b * N4 + v4);
+        const float d = d0 + (float)sh;
+        r.x = c.x + omega * (rr.x - r.x) / d;
+        r.y = c.y + omega * (rr.y - r.y) / d;
+        r.z = c.z + omega * (rr.z - r.z) / d;
+        r.w = c.w + omega * (rr.w - r.w) / d;
+      }
       reinterpret_cast<float4*>(out)[(size_t)b * N4 + v4] = r;
     }
     q0 = q1;
@@ -176,16 +188,25 @@ dim3 ham_grid(int nb, int n) {
   return dim3((n + bl.y - 1) / bl.y, n, nb);
 }
 
+bool ham_tiles_ok(const float* f, int n, const float* V, const float* mask, const float* out, const float* jr) {
+  auto al16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
+  return n % 4 == 0 && (n / 4) * kHamTy <= 512 && al16(f) && al16(out) && (!V || al16(V)) && (!mask || al16(mask)) &&
+         (!jr || al16(jr));
+}
+void launch_ham_tiles(const float* f, int nb, int n, float inv12h2, const float* V, const double* shift,
+                      const float* mask, const float* jr, float d0, float omega, float* out, cudaStream_t s) {
+  const int n4 = n / 4;
+  const dim3 grid((n + kHamTy - 1) / kHamTy, (n + kHamZc - 1) / kHamZc, nb), block(n4, kHamTy);
+  const size_t smem = sizeof(float4) * (size_t)(kHamTy + 4) * (n4 + 2);
+  k_ham_apply_z<<<grid, block, smem, s>>>(f, n, inv12h2, V, shift, mask, jr, d0, omega, out);
+}
+
 // out = H f over nb bands: the z-marching tiles where the layout allows, else one thread
 // per point
 void launch_ham(const float* f, int nb, int n, float inv12h2, const float* V, const double* shift, const float* mask,
                 float* out, cudaStream_t s) {
-  auto al16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
-  const int n4 = n / 4;
-  if (n % 4 == 0 && n4 * kHamTy <= 512 && al16(f) && al16(out) && (!V || al16(V)) && (!mask || al16(mask))) {
-    const dim3 grid((n + kHamTy - 1) / kHamTy, (n + kHamZc - 1) / kHamZc, nb), block(n4, kHamTy);
-    const size_t smem = sizeof(float4) * (size_t)(kHamTy + 4) * (n4 + 2);
-    k_ham_apply_z<<<grid, block, smem, s>>>(f, n, inv12h2, V, shift, mask, out);
+  if (ham_tiles_ok(f, n, V, mask, out, nullptr)) {
+    launch_ham_tiles(f, nb, n, inv12h2, V, shift, mask, nullptr, 0.f, 0.f, out, s);
   } else {
     k_ham_apply<<<ham_grid(nb, n), ham_block(n), 0, s>>>(f, nb, n, inv12h2, V, shift, mask, out);
   }
@@ -994,13 +1015,27 @@ int rsx_eig_step(rsx_eig* e, rsx_net* net, int jacobi_sweeps, double* theta_host
   const float omega = 2.f / 3.f;
   float* x = wp;
   float* ax = e->tmp;
-  k_ke_jacobi<<<(unsigned)blocks_for(k * N), 256, 0, s>>>(e->R, nullptr, nullptr, T, k, N, d0, omega, x);
-  for (int sw = 0; sw < jacobi_sweeps; ++sw) {
-    rc = ham(e, x, k, ax, T, nullptr, s);
+  if (ham_tiles_ok(wp, e->n, nullptr, e->mask, e->tmp + k * N, e->R) &&
+      ham_tiles_ok(e->tmp + k * N, e->n, nullptr, e->mask, wp, e->R)) {
+    // each sweep one fused stencil launch, alternating between W and a scratch block so
+    // that the last sweep writes W
+    float* buf[2] = {wp, e->tmp + k * N};
+    int cur = jacobi_sweeps % 2;
+    k_ke_jacobi<<<(unsigned)blocks_for(k * N), 256, 0, s>>>(e->R, nullptr, nullptr, T, k, N, d0, omega, buf[cur]);
+    for (int sw = 0; sw < jacobi_sweeps; ++sw, cur ^= 1)
+      launch_ham_tiles(buf[cur], k, e->n, (float)(1.0 / (12.0 * e->h * e->h)), nullptr, T, e->mask, e->R, d0, omega,
+                       buf[cur ^ 1], s);
+    rc = ecuda(e, cudaGetLastError(), "jacobi sweeps");
     if (rc) return rc;
-    k_ke_jacobi<<<(unsigned)blocks_for(k * N), 256, 0, s>>>(e->R, x, ax, T, k, N, d0, omega, e->tmp + k * N);
-    rc = ecuda(e, cudaMemcpyAsync(x, e->tmp + k * N, k * N * sizeof(float), cudaMemcpyDeviceToDevice, s), "jacobi copy");
-    if (rc) return rc;
+  } else {
+    k_ke_jacobi<<<(unsigned)blocks_for(k * N), 256, 0, s>>>(e->R, nullptr, nullptr, T, k, N, d0, omega, x);
+    for (int sw = 0; sw < jacobi_sweeps; ++sw) {
+      rc = ham(e, x, k, ax, T, nullptr, s);
+      if (rc) return rc;
+      k_ke_jacobi<<<(unsigned)blocks_for(k * N), 256, 0, s>>>(e->R, x, ax, T, k, N, d0, omega, e->tmp + k * N);
+      rc = ecuda(e, cudaMemcpyAsync(x, e->tmp + k * N, k * N * sizeof(float), cudaMemcpyDeviceToDevice, s), "jacobi copy");
+      if (rc) return rc;
+    }
   }
   // basis: Psi | W | P (LOBPCG, from the second step on) | W_learned (with a network)
   int m = e->has_p ? 3 * k : 2 * k;

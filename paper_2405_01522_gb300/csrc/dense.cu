@@ -218,9 +218,17 @@ __global__ void __launch_bounds__(kGramThreads) k_gram_tiled(const R* __restrict
     tj = tile - ti * tb;
   }
   const int a0 = active ? ti * 4 : 0, b0 = active ? tj * 4 : 0;
+  // The FP32 sums of each chunk are accumulated across chunks as double-float pairs
+  // (hi + lo, the rounding error of every addition carried into lo by Knuth's TwoSum):
+  // FP32 instructions only, where one FP64 addition per output and chunk cost as much as
+  // the chunk's products on this part's few FP64 units.  FP64 inputs accumulate in FP64.
   double acc[16];
+  float ah[16], al[16];
 #pragma unroll
-  for (int q = 0; q < 16; ++q) acc[q] = 0.0;
+  for (int q = 0; q < 16; ++q) {
+    acc[q] = 0.0;
+    ah[q] = al[q] = 0.f;
+  }
   const size_t nchunk = (N + kGramChunk - 1) / kGramChunk;
   for (size_t c = blockIdx.x; c < nchunk; c += gridDim.x) {
     const size_t r0 = c * kGramChunk;
@@ -244,8 +252,21 @@ __global__ void __launch_bounds__(kGramThreads) k_gram_tiled(const R* __restrict
           for (int q = 0; q < 4; ++q) sacc[p * 4 + q] = fma(xv[p], yv[q], sacc[p * 4 + q]);
       }
 #pragma unroll
-      for (int q = 0; q < 16; ++q) acc[q] += (double)sacc[q];
+      for (int q = 0; q < 16; ++q) {
+        if constexpr (sizeof(R) == 4) {
+          const float a = ah[q], b = sacc[q];
+          const float sm = a + b, bp = sm - a;
+          al[q] += (a - (sm - bp)) + (b - bp);
+          ah[q] = sm;
+        } else {
+          acc[q] += (double)sacc[q];
+        }
+      }
     }
+  }
+  if constexpr (sizeof(R) == 4) {
+#pragma unroll
+    for (int q = 0; q < 16; ++q) acc[q] = (double)ah[q] + (double)al[q];
   }
   for (int o = S >> 1; o > 0; o >>= 1)
 #pragma unroll

@@ -37,6 +37,8 @@ constexpr int kMaxBasis = 64;
 // it).  f, out: [nb][n^3].  Block (x threads, rows of y), grid
 // (y blocks, z, orbital): no index division, and the y / z boundary test is uniform over
 // each warp (a warp holds one y row), so only the x neighbours are predicated per lane.
+__device__ __forceinline__ bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
 __global__ void k_ham_apply(const float* __restrict__ f, int nb, int n, float inv12h2, const float* __restrict__ V,
                             const double* __restrict__ shift, const float* __restrict__ mask, float* __restrict__ out) {
   const int x = threadIdx.x, y = blockIdx.x * blockDim.y + threadIdx.y, z = blockIdx.y, b = blockIdx.z;
@@ -261,7 +263,20 @@ __global__ void k_row_reduce(const double* __restrict__ part, int P, int rows, d
 // R_i = HPsi_i - theta_i Psi_i
 __global__ void k_residual(const float* __restrict__ psi, const float* __restrict__ hpsi, const double* __restrict__ th,
                            int k, size_t N, float* __restrict__ R) {
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < (size_t)k * N; i += (size_t)gridDim.x * blockDim.x) {
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  if ((N & 3) == 0 && aligned16(psi) && aligned16(hpsi) && aligned16(R)) {   // 4 points of one row per access
+    const float4* p4 = reinterpret_cast<const float4*>(psi);
+    const float4* h4 = reinterpret_cast<const float4*>(hpsi);
+    float4* r4 = reinterpret_cast<float4*>(R);
+    const size_t N4 = N / 4;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < (size_t)k * N4; i += stride) {
+      const float t = (float)th[i / N4];
+      const float4 p = p4[i], h = h4[i];
+      r4[i] = make_float4(h.x - t * p.x, h.y - t * p.y, h.z - t * p.z, h.w - t * p.w);
+    }
+    return;
+  }
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < (size_t)k * N; i += stride) {
     const size_t b = i / N;
     R[i] = hpsi[i] - (float)th[b] * psi[i];
   }
@@ -292,8 +307,16 @@ __global__ void k_normalise_rows(float* __restrict__ X, const double* __restrict
   const double gs = g[blockIdx.y];
   const float sc = gs > 0.0 ? (float)(1.0 / sqrt(gs)) : 0.f;
   float* x = X + (size_t)blockIdx.y * N;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x)
-    x[i] *= sc;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  if ((N & 3) == 0 && aligned16(x)) {
+    float4* x4 = reinterpret_cast<float4*>(x);
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N / 4; i += stride) {
+      const float4 v = x4[i];
+      x4[i] = make_float4(v.x * sc, v.y * sc, v.z * sc, v.w * sc);
+    }
+    return;
+  }
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += stride) x[i] *= sc;
 }
 
 // net input [k][2][N]: channel 0 = R_i / |R_i|, channel 1 = V * vscale (row i = blockIdx.y)

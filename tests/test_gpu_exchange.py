@@ -2,7 +2,8 @@
 
 All calls go through the C ABI (ctypes binding).  Sizes span several CTA tiles and
 ragged tails: ny = 24 and 40 leave a partial 32-row block, nz = 24 and 40 are not
-multiples of 16 (uneven row loops), nx != ny exercises the per-axis transforms.
+multiples of 16 (uneven row loops), nx != ny exercises the per-axis transforms; at
+112^3 the pass-2 work plane does not fit in shared memory and lives in global scratch.
 """
 import numpy as np
 import pytest
@@ -20,6 +21,8 @@ CASES = [
     ((24, 24, 24), 0.35, 3, 2, "fp32"),
     ((24, 24, 40), 0.30, 2, 2, "fp32"),
     ((40, 40, 16), 0.30, 2, 3, "fp32"),
+    ((56, 56, 24), 0.30, 1, 2, "fp32"),      # odd A = 7 along y and z
+    ((112, 112, 112), 0.25, 1, 1, "fp32"),   # largest edge: the pass-2 plane lives in global scratch
     ((16, 16, 16), 0.40, 2, 3, "fp64"),
     ((24, 24, 40), 0.30, 2, 2, "fp64"),
     ((56, 56, 24), 0.30, 1, 2, "fp64"),

@@ -122,15 +122,29 @@ __global__ void __launch_bounds__(512) k_ham_apply_z(const float* __restrict__ f
     if (tx == 0) hs4[r * W] = zero;
     if (tx == n4 - 1) hs4[r * W + n4 + 1] = zero;
   }
+  // planes z-2 .. z+3 of this column, the halo row value of plane z (threads ty < 2 and
+  // ty >= kHamTy - 2): every global load is issued one plane ahead of its use
+  const bool halo_lo = ty < 2, halo_hi = ty >= kHamTy - 2;
+  const int yh = halo_lo ? y0 - 2 + ty : y0 + ty + 2;
   float4 q0 = ld(y, z0 - 2), q1 = ld(y, z0 - 1), q2 = ld(y, z0), q3 = ld(y, z0 + 1), q4 = ld(y, z0 + 2);
+  float4 q5 = ld(y, z0 + 3);
+  float4 hv = (halo_lo || halo_hi) ? ld(yh, z0) : zero;
   const double sh = shift ? shift[b] : 0.0;
+  const bool act = y < n;
   for (int z = z0; z < z1; ++z) {
+    const size_t v4 = (size_t)z * nn4 + (size_t)(act ? y : 0) * n4 + tx;
+    float4 vv = zero, m = zero, rr = zero;
+    if (act && V) vv = __ldg(reinterpret_cast<const float4*>(V) + v4);
+    if (act && mask) m = __ldg(reinterpret_cast<const float4*>(mask) + v4);
+    if (act && jr) rr = __ldg(reinterpret_cast<const float4*>(jr) + (size_t)b * N4 + v4);
+    const float4 qn = ld(y, z + 4);
+    const float4 hn = ((halo_lo || halo_hi) && z + 1 < z1) ? ld(yh, z + 1) : zero;
     __syncthreads();   // the previous plane's neighbour reads are done
     hs4[(ty + 2) * W + 1 + tx] = q2;
-    if (ty < 2) hs4[ty * W + 1 + tx] = ld(y0 - 2 + ty, z);
-    if (ty >= kHamTy - 2) hs4[(ty + 4) * W + 1 + tx] = ld(y0 + ty + 2, z);
+    if (halo_lo) hs4[ty * W + 1 + tx] = hv;
+    if (halo_hi) hs4[(ty + 4) * W + 1 + tx] = hv;
     __syncthreads();
-    if (y < n) {
+    if (act) {
       const float4 c = q2;
       const float4 L = hs4[(ty + 2) * W + tx], R = hs4[(ty + 2) * W + 2 + tx];
       const float4 ym1 = hs4[(ty + 1) * W + 1 + tx], yp1 = hs4[(ty + 3) * W + 1 + tx];
@@ -140,9 +154,7 @@ __global__ void __launch_bounds__(512) k_ham_apply_z(const float* __restrict__ f
       r.y = ham_point(c.y, L.w, c.x, c.z, c.w, ym2.y, ym1.y, yp1.y, yp2.y, q0.y, q1.y, q3.y, q4.y, inv12h2);
       r.z = ham_point(c.z, c.x, c.y, c.w, R.x, ym2.z, ym1.z, yp1.z, yp2.z, q0.z, q1.z, q3.z, q4.z, inv12h2);
       r.w = ham_point(c.w, c.y, c.z, R.x, R.y, ym2.w, ym1.w, yp1.w, yp2.w, q0.w, q1.w, q3.w, q4.w, inv12h2);
-      const size_t v4 = (size_t)z * nn4 + (size_t)y * n4 + tx;
       if (V) {
-        const float4 vv = __ldg(reinterpret_cast<const float4*>(V) + v4);
         r.x += vv.x * c.x;
         r.y += vv.y * c.y;
         r.z += vv.z * c.z;
@@ -156,14 +168,12 @@ __global__ void __launch_bounds__(512) k_ham_apply_z(const float* __restrict__ f
         r.w += s * c.w;
       }
       if (mask) {
-        const float4 m = __ldg(reinterpret_cast<const float4*>(mask) + v4);
         r.x *= m.x;
         r.y *= m.y;
         r.z *= m.z;
         r.w *= m.w;
       }
       if (jr) {
-        const float4 rr = __ldg(reinterpret_cast<const float4*>(jr) + (size_t)b * N4 + v4);
         const float d = d0 + (float)sh;
         r.x = c.x + omega * (rr.x - r.x) / d;
         r.y = c.y + omega * (rr.y - r.y) / d;
@@ -176,7 +186,9 @@ __global__ void __launch_bounds__(512) k_ham_apply_z(const float* __restrict__ f
     q1 = q2;
     q2 = q3;
     q3 = q4;
-    q4 = ld(y, z + 3);
+    q4 = q5;
+    q5 = qn;
+    hv = hn;
   }
 }
 

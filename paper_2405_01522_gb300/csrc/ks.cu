@@ -77,7 +77,8 @@ __global__ void k_ham_apply(const float* __restrict__ f, int nb, int n, float in
 
 // The same operator by z-marching tiles: a block owns kHamTy rows y of 4-point float4
 // columns along x (one per thread) for kHamZc consecutive planes z.  Each thread keeps
-// its column's planes z-2 .. z+2 in registers; the plane z rows y0-2 .. y0+kHamTy+1 are
+// its column's planes z-2 .. z+2 in registers (and z+3, loaded a plane ahead of its use,
+// like every other global load of the loop); the plane z rows y0-2 .. y0+kHamTy+1 are
 // staged in shared memory (with one zero float4 on each side in x) for the x and y
 // neighbours.  One global load per point instead of thirteen; the arithmetic per point
 // is that of k_ham_apply, term by term.  n % 4 == 0, every array 16-byte aligned.

@@ -130,8 +130,7 @@ DFT_FLOPS = {1: 0, 2: 4, 3: 16, 4: 16, 5: 52, 6: 44, 7: 102, 8: 60, 10: 124, 12:
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12     # SMs x FP32 lanes x FMA x max SM clock
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) from ncu captures of small cases
-# of the same kernels (profiles/pass2_yz_kernel_96cubed.md, profiles/k_syrk_bf16x3_48cubed.md),
-# scaled to a full launch by the units it processes:
+# of the same kernels, scaled to a full launch by the units it processes:
 PASS2_DRAM_BYTES_PER_PAIR_96 = 404.98e6 / 32    # 32-pair launch at 96^3 (12.66 MB/pair)
 SYRK_DRAM_PER_PANEL_BYTE = 1.938e9 / 1.850e9    # DRAM bytes per byte of the two bf16 panels
 
@@ -358,10 +357,7 @@ def run_rsx(args, rank, local_rank, world):
     out = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": WORKLOAD, "grid": list(shape), "padded": [2 * x for x in shape], "h_bohr": H,
-                      "nocc": NOCC, "npsi": NPSI, "solves_per_step": SOLVES_PER_STEP,
-                      "l2": "no flush: inputs (170 MB) and FFT intermediates (3.7 GB) exceed the 129 MB L2",
-                      "parallelism": f"independent problems x{world} (seed = rank)"},
+           "config": bench_config(shape, world),
            "tuning": tuning, "roofline": roof, "kernels": kernels, "gpu_launches": launches, "clocks": clk, "e2e": e2e,
            "ace_build_ms": round(ace_ms, 4)}
 
@@ -777,41 +773,151 @@ def scf_bench(args, dev, iters=10, inner=2, max_iter=300):
     return res
 
 
-def cpu_baseline(s, nsolve=16):
-    """The FP64 oracle as it stands, on the host, for a bounded sample of the workload:
-    the exchange action on trial function 0 from the first `nsolve` orbitals."""
+# ----------------------------------------------------------------------------- CPU oracle
+# The oracle as it stands, timed on the host cores: its exchange loop runs unchanged in
+# each worker process, the pairs of a sample are split across the workers by output
+# function (all orbitals j for one psi_p, or a slice of them), and the inputs are shared
+# with the workers through shared memory.  Workers are started with "spawn" so that no
+# process forks after the CUDA context exists.
+_POOL_ARRAYS = {}
+
+
+def _pool_init(specs):
+    from multiprocessing import shared_memory
+    import oracle  # noqa: F401  (imported once per worker, outside the timed region)
+    for name, (shm_name, shape) in specs.items():
+        shm = shared_memory.SharedMemory(name=shm_name)
+        _POOL_ARRAYS[name] = (shm, np.ndarray(shape, dtype=np.float64, buffer=shm.buf))
+
+
+def _pool_task(task):
+    """Vx[phi_j0..j1] psi_p by the oracle (its own loop over j), returned as FP64."""
     import oracle
+    p, j0, j1, h = task
+    phi = _POOL_ARRAYS["phi"][1]
+    psi = _POOL_ARRAYS["psi"][1]
+    return oracle.exchange_apply(phi[j0:j1], psi[p:p + 1], h)
+
+
+def _pool_ready(_):
+    return os.getpid()
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+class OraclePool:
+    """A spawn-started process pool with the step's inputs in shared memory."""
+
+    def __init__(self, s, workers):
+        import multiprocessing as mp
+        from multiprocessing import shared_memory
+        self.workers = workers
+        self.h = s.h
+        self.shm = []
+        specs = {}
+        for name, arr in (("phi", s.phi), ("psi", s.psi)):
+            a = np.ascontiguousarray(arr, dtype=np.float64)
+            shm = shared_memory.SharedMemory(create=True, size=a.nbytes)
+            np.ndarray(a.shape, dtype=np.float64, buffer=shm.buf)[...] = a
+            self.shm.append(shm)
+            specs[name] = (shm.name, a.shape)
+        self.pool = mp.get_context("spawn").Pool(workers, initializer=_pool_init, initargs=(specs,))
+        self.pool.map(_pool_ready, range(workers), chunksize=1)     # every worker started
+
+    def run(self, tasks):
+        return self.pool.map(_pool_task, [t + (self.h,) for t in tasks], chunksize=1)
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+        for shm in self.shm:
+            shm.close()
+            shm.unlink()
+
+
+def cpu_baseline(s, nsolve=16, npsi_all=None):
+    """The FP64 oracle as it stands, on the host: (1) the whole exchange apply of the step
+    (Vx on every trial function from all orbitals, NOCC x NPSI pair solves) split by output
+    function over one worker per host core; (2) the same oracle on one core for `nsolve`
+    solves, for comparison."""
+    import oracle
+    cores = host_cores()
+    npsi_all = s.psi.shape[0] if npsi_all is None else npsi_all
     t0 = time.perf_counter()
     oracle.exchange_apply(s.phi[:nsolve], s.psi[:1], s.h)
-    dt = time.perf_counter() - t0
-    return {"value": round(nsolve / dt, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{nsolve} pair solves (Vx on trial 0 from orbitals 0..{nsolve - 1}) of the 96^3 workload, "
-                      f"numpy pocketfft FP64, single thread; {dt:.1f} s"}
+    dt1 = time.perf_counter() - t0
+    pool = OraclePool(s, cores)
+    try:
+        nj = s.phi.shape[0]
+        split = max(1, min(nj, -(-cores // npsi_all)))         # at least one task per core
+        bounds = [nj * c // split for c in range(split + 1)]
+        tasks = [(p, bounds[c], bounds[c + 1]) for p in range(npsi_all) for c in range(split)]
+        t0 = time.perf_counter()
+        out = pool.run(tasks)
+        dt = time.perf_counter() - t0
+    finally:
+        pool.close()
+    nsolves = s.phi.shape[0] * npsi_all
+    assert len(out) == len(tasks)
+    return {"value": round(nsolves / dt, 3), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"the step's exchange apply: Vx on all {npsi_all} trial functions from all "
+                      f"{s.phi.shape[0]} orbitals ({nsolves} pair solves) of the 96^3 workload, numpy "
+                      f"pocketfft FP64, split by trial function over {cores} spawn-started worker processes "
+                      f"(one per host core); {dt:.1f} s",
+            "single_core": {"value": round(nsolve / dt1, 3), "cores": 1,
+                            "sample": f"{nsolve} pair solves (Vx on trial 0 from orbitals 0..{nsolve - 1}) in this "
+                                      f"process; {dt1:.1f} s"}}
+
+
+def bench_config(shape, world):
+    """The `config` object of both arms (the same workload, the same keys)."""
+    return {"workload": WORKLOAD, "grid": list(shape), "padded": [2 * x for x in shape], "h_bohr": H,
+            "nocc": NOCC, "npsi": NPSI, "solves_per_step": SOLVES_PER_STEP,
+            "l2": "no flush: inputs (170 MB) and FFT intermediates (3.7 GB) exceed the 129 MB L2",
+            "parallelism": f"independent problems x{world} (seed = rank)"}
 
 
 def run_reference(args, rank, world):
-    """The oracle as the reference arm: same metric and workload, bounded CPU sample per step."""
+    """The oracle as the reference arm: same metric, workload and config; each step is a
+    bounded sample of the step's pair solves, one per host core, run in parallel."""
     if rank != 0:
         return
-    import oracle
     s = make_inputs()
-    per_step = 2
-    for _ in range(args.warmup):
-        oracle.exchange_apply(s.phi[:per_step], s.psi[:1], s.h)
-    t0 = time.perf_counter()
-    for k in range(args.steps):
-        j0 = (2 * k) % NOCC
-        oracle.exchange_apply(s.phi[j0:j0 + per_step], s.psi[k % NPSI:k % NPSI + 1], s.h)
-    dt = time.perf_counter() - t0
-    value = per_step * args.steps / dt
+    cores = host_cores()
+    pool = OraclePool(s, cores)
+
+    def tasks(k):
+        # pair solves (j, p) of the exchange apply, in order, `cores` per step
+        out = []
+        for u in range(cores):
+            q = (k * cores + u) % (NOCC * NPSI)
+            p, j = divmod(q, NOCC)
+            out.append((p, j, j + 1))
+        return out
+
+    try:
+        for k in range(args.warmup):
+            pool.run(tasks(k))
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            pool.run(tasks(args.warmup + k))
+        dt = time.perf_counter() - t0
+    finally:
+        pool.close()
+    value = cores * args.steps / dt
     out = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(1e3 * dt / args.steps, 2), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": WORKLOAD, "grid": list(s.shape), "h_bohr": H, "nocc": NOCC, "npsi": NPSI,
-                      "parallelism": "host"},
+           "config": bench_config(s.shape, world),
            "impl": "reference",
-           "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
-                            "sample": f"{per_step} pair solves per step (FP64 numpy oracle, single thread)"},
+           "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": f"{cores} pair solves of the step's exchange apply per step, one per "
+                                      f"spawn-started worker process (one per host core), FP64 numpy oracle"},
            "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 

@@ -106,16 +106,22 @@ int rsx_poisson(rsx_ctx* ctx, const void* rho, void* V, void* stream);
  * a deployment aid).  For callers that must not allocate device memory once running --
  * e.g. a program whose device memory is owned by its own pool allocator sized at
  * start-up, or a latency-sensitive loop that cannot take cudaFree's implicit device
- * synchronisation when a workspace is regrown.  Create the context at start-up; this
- * call then performs no cudaMalloc/cudaFree and calls no allocating routine.
- * Same result as rsx_exchange_apply (same kernels, one output orbital at a time).
+ * synchronisation when a workspace is regrown.  Same result as rsx_exchange_apply (same
+ * kernels, one output orbital at a time).
  * Scratch: a fixed 64 MiB device array inside the library, held by every GPU that loads
- * it until process exit; requires nocc * (nx + 1) * nz * ny * 2 * element size <= 64 MiB
- * (else RSX_EINVAL, nothing launched) and a box whose y/z pass fits in shared memory
- * (FP32 edges <= 112, FP64 <= 64; else RSX_EUNSUPPORTED).  The first call on a device
- * looks up the array's address (cudaGetSymbolAddress) -- make it before any stream
- * capture.  All calls share the array and it keeps the last call's contents (nothing in
- * it needs to start at zero); calls that overlap on the GPU race and must be serialised. */
+ * its module until process exit; requires nocc * (nx + 1) * nz * ny * 2 * element size
+ * <= 64 MiB (else RSX_EINVAL, nothing launched) and a box whose y/z pass fits in shared
+ * memory (FP32 edges <= 112, FP64 <= 64; else RSX_EUNSUPPORTED).
+ * Set-up: the FIRST call on a device looks up the array's address (cudaGetSymbolAddress);
+ * under lazy module loading (the CUDA default) that lookup, and the first launch of each
+ * FFT pass kernel, make the driver load their modules, which maps the 64 MiB array and
+ * the kernels' code -- the first call can therefore allocate driver memory.  Create the
+ * context and make one call on each device at start-up, before any stream capture; every
+ * later call performs no cudaMalloc/cudaFree and calls no allocating routine.  The cached
+ * address is valid until process exit (a cudaDeviceReset invalidates it: restart the
+ * process).  The caller's current device is restored before the call returns.
+ * All calls share the array and it keeps the last call's contents (nothing in it needs
+ * to start at zero); calls that overlap on the GPU race and must be serialised. */
 int rsx_exchange_apply_noalloc(rsx_ctx* ctx, const void* phi, int nocc, const void* psi, int npsi, void* out,
                                void* stream);
 

@@ -25,8 +25,15 @@
 //
 // Set-up: the first call on each device looks up the array's device address with
 // cudaGetSymbolAddress while that device is current, checks the result and caches it
-// (the array's name is only a host-side stand-in in host code).  Make that first call
-// on each device before any stream capture begins.
+// (the array's name is only a host-side stand-in in host code).  With lazy module
+// loading (the CUDA default) that lookup is also the moment the driver loads the module
+// holding the array and maps its 64 MiB, and the first launch of each FFT pass kernel
+// loads that kernel's module, so the FIRST call on a device can allocate driver memory;
+// every later call allocates nothing.  Make one call on each device at start-up, before
+// any stream capture begins and before the caller's allocation budget is fixed.  The
+// cached address stays valid until process exit; a cudaDeviceReset invalidates it (the
+// library is then not usable on that device until the process restarts).  The caller's
+// current device is restored before each call returns.
 #include <mutex>
 
 #include "../../include/rsx.h"
@@ -98,6 +105,8 @@ bool overlap(const void* a, size_t na, const void* b, size_t nb) {
   return pa < pb + nb && pb < pa + na;
 }
 
+int noalloc_on_device(rsx_ctx* c, const void* phi, int nocc, const void* psi, int npsi, void* out, void* stream);
+
 }  // namespace
 
 extern "C" int rsx_exchange_apply_noalloc(rsx_ctx* c, const void* phi, int nocc, const void* psi, int npsi,
@@ -112,10 +121,24 @@ extern "C" int rsx_exchange_apply_noalloc(rsx_ctx* c, const void* phi, int nocc,
   if (need > kNoAllocScratchBytes)
     return set_error(c, RSX_EINVAL,
                      "noalloc exchange: nocc * (nx+1) * nz * ny * 2 * element size exceeds the 64 MiB static scratch");
+  // the work runs on the context's device; the caller's current device is put back on return
+  int prev_device = -1;
+  if (cudaGetDevice(&prev_device) != cudaSuccess) {
+    cudaGetLastError();
+    prev_device = -1;
+  }
   if (cudaSetDevice(c->device) != cudaSuccess) {
     cudaGetLastError();
     return set_error(c, RSX_ECUDA, "cudaSetDevice failed");
   }
+  const int rc = noalloc_on_device(c, phi, nocc, psi, npsi, out, stream);
+  if (prev_device >= 0 && prev_device != c->device) cudaSetDevice(prev_device);
+  return rc;
+}
+
+namespace {
+
+int noalloc_on_device(rsx_ctx* c, const void* phi, int nocc, const void* psi, int npsi, void* out, void* stream) {
   bool fits = false;
   if (c->precision == RSX_FP32)
     pass2_smem_bytes<float>(c->g, &fits);
@@ -129,3 +152,5 @@ extern "C" int rsx_exchange_apply_noalloc(rsx_ctx* c, const void* phi, int nocc,
   return c->precision == RSX_FP32 ? exchange_noalloc<float>(c, phi, nocc, psi, npsi, out, scratch, s)
                                   : exchange_noalloc<double>(c, phi, nocc, psi, npsi, out, scratch, s);
 }
+
+}  // namespace

@@ -426,6 +426,74 @@ def test_full_tdhf_reduces_to_tda_and_closed_forms():
     assert abs(osp.tdhf_solve(A1, B1, 1)[0][0] - math.sqrt((a - b) * (a + b))) < 1e-14
 
 
+def _spin_orbital_tdhf_roots(eo, ev, phi_occ, phi_virt, h):
+    """Positive roots of Eq. 3 built in spin orbitals from Eqs. 4-5, closed shell.
+
+    Every two-electron integral (pq|rs) = <phi_p phi_q, V[phi_r phi_s]> is its own direct
+    Coulomb sum (no FFT, no K matrix reused); a spin-orbital integral vanishes unless p, q
+    share a spin and r, s share a spin.  Transitions: alpha (i, a) first, then beta.
+    A_{ia,jb} = delta (eps_a - eps_i) + (ai|jb) - (ab|ji),  B_{ia,jb} = (ai|bj) - (aj|bi).
+    """
+    no, nv = len(eo), len(ev)
+    orb = list(phi_occ) + list(phi_virt)           # spatial orbitals: occupied, then virtual
+    n = no + nv
+    pot = {}
+
+    def V(r, s_):
+        key = (min(r, s_), max(r, s_))
+        if key not in pot:
+            pot[key] = oracle.poisson_direct(orb[r] * orb[s_], h)
+        return pot[key]
+
+    def eri(p, q, r, s_):
+        return h ** 3 * float(np.sum(orb[p] * orb[q] * V(r, s_)))
+
+    trans = [(sp, i, no + a) for sp in (0, 1) for i in range(no) for a in range(nv)]
+    m = len(trans)
+    A, B = np.zeros((m, m)), np.zeros((m, m))
+    for u, (s1, i, a) in enumerate(trans):
+        for w, (s2, j, b) in enumerate(trans):
+            same = s1 == s2
+            A[u, w] = (eri(a, i, j, b)                                   # (ai|jb): any spins
+                       - (eri(a, b, j, i) if same else 0.0))             # (ab|ji): one spin
+            if u == w:
+                A[u, w] += ev[a - no] - eo[i]
+            B[u, w] = eri(a, i, b, j) - (eri(a, j, b, i) if same else 0.0)
+    big = np.block([[A, B], [-B, -A]])
+    w = np.sort(np.linalg.eigvals(big).real)
+    return w[m:]
+
+
+def test_rhf_b_matrix_from_the_spin_orbital_equations():
+    """Eqs. 4-5 in spin orbitals for a closed shell (alpha = beta) split into the singlet
+    and triplet RHF problems, so the full-TDHF roots of the spin-orbital matrices (every
+    integral a direct sum) are the union of the oracle's half-size roots at delta_M = 2 and
+    delta_M = 0.  A B with the exchange-type index of the wrong kind must fail."""
+    shape, h = (6, 6, 6), 0.45
+    rng = inputs.SplitMix64(9)
+    phi = inputs.gram_schmidt(inputs.orbitals_independent(rng, shape, h, 5, 2, (0.4, 1.2), 0.9), h)
+    po, pv = phi[:2], phi[2:]
+    eo, ev = np.array([-1.1, -0.8]), np.array([0.3, 0.45, 0.7])
+    ref = _spin_orbital_tdhf_roots(eo, ev, po, pv, h)
+    K = oracle.casida_K(po, pv, h)
+    Kd = oracle.casida_Kd(po, pv, h)
+
+    def union(Bfun):
+        roots = []
+        for dm in (2.0, 0.0):
+            A, _ = osp.tdhf_matrices(eo, ev, K, Kd, dm)
+            roots.append(osp.tdhf_solve(A, Bfun(dm), A.shape[0])[0])
+        return np.sort(np.concatenate(roots))
+
+    got = union(lambda dm: osp.tdhf_matrices(eo, ev, K, Kd, dm)[1])
+    assert np.allclose(got, ref, rtol=0, atol=1e-10), np.abs(got - ref).max()
+    # planted mistakes: exchange-type term taken unpermuted, or as the Coulomb term K_d
+    scale = np.abs(ref).max()
+    with np.errstate(invalid="ignore"):        # a wrong B can make omega^2 < 0 (NaN roots)
+        for wrong in (lambda dm: dm * K - K, lambda dm: dm * K - Kd, lambda dm: dm * K - K.T[::-1, ::-1]):
+            assert not np.allclose(union(wrong), ref, rtol=0, atol=1e-6 * scale)
+
+
 # ---------------------------------------------------------------- SCF (closed-shell HF)
 
 import oracle.scf as oscf  # noqa: E402

@@ -71,17 +71,39 @@ const char* rsx_last_error(const rsx_ctx* ctx);
  * within it.  Default: 40% of the device memory free at rsx_create, at most 64 GiB. */
 int rsx_set_workspace_limit(rsx_ctx* ctx, size_t bytes);
 
+/* Tuning knobs of the pair-solve path (performance only: no knob changes the results,
+ * which stay bitwise identical).
+ *   p2_threads     threads per CTA of the y/z transform pass: 256, 384 (FP32) or 512; a
+ *                  size is used only where its line scratch and the work plane fit in
+ *                  shared memory (else 256)
+ *   chunk_outputs  output orbitals per exchange chunk (0 = as many as the workspace holds)
+ *   p1_group       x-pass block order: 0 pair-major, G > 0 pairs fastest in groups of G
+ *   p2_global      1: the y/z pass keeps its work plane in a global (L2-resident) scratch
+ *                  slice per CTA even where shared memory would hold it; 0: shared memory
+ *                  whenever it fits */
+typedef struct rsx_tuning {
+  int p2_threads;
+  int chunk_outputs;
+  int p1_group;
+  int p2_global;
+} rsx_tuning;
+int rsx_get_tuning(rsx_ctx* ctx, rsx_tuning* out);
+/* Errors: RSX_EINVAL (null, or a knob outside the values above). */
+int rsx_set_tuning_ex(rsx_ctx* ctx, const rsx_tuning* t);
 /* Autotuner (the paper has no counterpart; a performance knob).  Times the exchange
- * apply for nocc x npsi pairs on synthetic device data under each candidate -- threads
- * per CTA of the y/z transform pass (256, 384, 512) x output orbitals per chunk (1, 2, 4,
- * all) -- and applies the fastest to the context.  With a non-empty cache_path the
- * result is appended to that text file, keyed by box, precision, nocc, npsi, SM count
- * and device name, and a later call with the same key applies it without timing.
- * Outputs (may be NULL): chosen p2_threads, chunk_outputs, best time in ms (-1 if
- * taken from the cache).  Synchronises the device.  Errors: RSX_EINVAL, RSX_ENOMEM. */
+ * apply for nocc x npsi pairs on synthetic device data under candidate knobs, by
+ * coordinate descent from the current ones: pass-2 CTA size x plane staging, then the
+ * pass-1 block order (0, 4, 16, 64, all), then output orbitals per chunk (1, 2, 4, all);
+ * applies the fastest to the context.  With a non-empty cache_path the result is appended
+ * to that text file, keyed by box, precision, nocc, npsi, SM count and device name, and a
+ * later call with the same key applies it without timing.  chosen (may be NULL) receives
+ * the knobs, best_ms the best time (-1 if taken from the cache).  Synchronises the device.
+ * Errors: RSX_EINVAL, RSX_ENOMEM. */
+int rsx_autotune_ex(rsx_ctx* ctx, int nocc, int npsi, const char* cache_path, rsx_tuning* chosen, double* best_ms);
+/* The same, returning only two of the knobs (p2_threads, chunk_outputs). */
 int rsx_autotune(rsx_ctx* ctx, int nocc, int npsi, const char* cache_path, int* p2_threads, int* chunk_outputs,
                  double* best_ms);
-/* Set the same two knobs by hand (p2_threads 256, 384 or 512; chunk_outputs 0 = as many as fit). */
+/* Set p2_threads and chunk_outputs, keeping the other knobs. */
 int rsx_set_tuning(rsx_ctx* ctx, int p2_threads, int chunk_outputs);
 
 /* Pair densities rho_q = a_i * b_k (Sec. 3.1: the density whose potential Eq. 2 needs),

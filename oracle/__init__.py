@@ -30,16 +30,16 @@ Parity status: every public function here is pinned by ``tests/test_oracle_pins.
 against closed forms, brute-force sums or invariants; none is "parity unpinned".
 """
 from .coulomb import (C0, kernel_samples, kernel_spectrum, poisson_fft,
-                      poisson_direct)
-from .exchange import (pair_density, exchange_apply, exchange_apply_bruteforce,
+                      poisson_direct, potential_at)
+from .exchange import (pair_density, exchange_apply, exchange_apply_at, exchange_apply_bruteforce,
                        exchange_energy, hartree_energy, inner)
 from .ace import ace_build, ace_apply
 from .casida import (transition_densities, casida_K, casida_K_bruteforce, casida_Kd,
                      tda_matrix, tda_solve, uhf_K, uhf_tda_matrix, HARTREE_EV)
 
 __all__ = [
-    "C0", "kernel_samples", "kernel_spectrum", "poisson_fft", "poisson_direct",
-    "pair_density", "exchange_apply", "exchange_apply_bruteforce", "exchange_energy",
+    "C0", "kernel_samples", "kernel_spectrum", "poisson_fft", "poisson_direct", "potential_at",
+    "pair_density", "exchange_apply", "exchange_apply_at", "exchange_apply_bruteforce", "exchange_energy",
     "hartree_energy", "inner", "ace_build", "ace_apply", "transition_densities",
     "casida_K", "casida_K_bruteforce", "casida_Kd", "tda_matrix", "tda_solve",
     "uhf_K", "uhf_tda_matrix", "HARTREE_EV",

@@ -106,3 +106,26 @@ def poisson_direct(rho, h, chunk=512):
         g[dist == 0] = C0 / h
         out[s:s + chunk] = g @ src
     return h ** 3 * out.reshape(rho.shape)
+
+
+def potential_at(rho, h, points):
+    """V(r) = h^3 sum_{r'} rho(r') g(r - r') at selected grid points only (FP64).
+
+    ``points``: integer (z, y, x) triples inside the box.  The same sum as
+    ``poisson_direct`` evaluated one target point at a time, O(N) per point, so that
+    large boxes can be checked at a sample of points.
+    """
+    rho = np.asarray(rho, dtype=np.float64)
+    nz, ny, nx = rho.shape
+    z = np.arange(nz, dtype=np.float64)[:, None, None]
+    y = np.arange(ny, dtype=np.float64)[None, :, None]
+    x = np.arange(nx, dtype=np.float64)[None, None, :]
+    out = np.empty(len(points))
+    for k, (pz, py, px) in enumerate(points):
+        dist = np.sqrt((z - pz) ** 2 + (y - py) ** 2 + (x - px) ** 2)
+        with np.errstate(divide="ignore"):
+            g = 1.0 / (h * dist)
+        g[int(pz), int(py), int(px)] = C0 / h
+        out[k] = h ** 3 * float(np.sum(g * rho))
+    return out
+

@@ -13,7 +13,7 @@ and none is added.  The discrete inner product is <f, g> = h^3 sum_r f(r) g(r).
 """
 import numpy as np
 
-from .coulomb import C0, poisson_fft
+from .coulomb import C0, poisson_fft, potential_at
 
 
 def inner(f, g, h):
@@ -78,3 +78,16 @@ def exchange_energy(phi, h, poisson=poisson_fft):
 def hartree_energy(rho, h, poisson=poisson_fft):
     """E_H[rho] = 1/2 <rho, V[rho]>."""
     return 0.5 * inner(rho, poisson(rho, h), h)
+
+
+def exchange_apply_at(phi, psi_p, h, points):
+    """(Vx[phi] psi_p)(r) = -sum_j phi_j(r) V[phi_j psi_p](r) (Eq. 2) at selected grid
+    points, each potential by the direct sum at those points (``potential_at``)."""
+    phi = np.asarray(phi, dtype=np.float64)
+    psi_p = np.asarray(psi_p, dtype=np.float64)
+    out = np.zeros(len(points))
+    for j in range(phi.shape[0]):
+        v = potential_at(pair_density(phi[j], psi_p), h, points)
+        out -= np.array([phi[j][tuple(int(c) for c in p)] for p in points]) * v
+    return out
+

@@ -383,6 +383,7 @@ int rsx_create(rsx_ctx** out, int nz, int ny, int nx, double h, int precision, i
   if (const char* e = getenv("RSX_PASS2_THREADS")) g.p2_threads = (atoi(e) == 512 || atoi(e) == 384) ? atoi(e) : 256;
   g.p1_group = 1 << 30;   // pass-1 blocks pair-fastest over the whole launch (orbital rows shared in L2)
   if (const char* e = getenv("RSX_PASS1_GROUP")) g.p1_group = atoi(e) > 0 ? atoi(e) : 0;
+  g.p2_global = 0;
   cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, device);
   size_t freeb = 0, totalb = 0;
   cudaMemGetInfo(&freeb, &totalb);

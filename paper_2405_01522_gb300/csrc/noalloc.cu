@@ -71,7 +71,8 @@ int scratch_address(rsx_ctx* c, int device, void** out) {
 template <typename R>
 int exchange_noalloc(rsx_ctx* c, const void* phi, int nocc, const void* psi, int npsi, void* out, void* scratch,
                      cudaStream_t s) {
-  const Geom& g = c->g;
+  Geom g = c->g;
+  g.p2_global = 0;   // the y/z pass always in shared memory here (no plane scratch to allocate)
   const size_t N = g.N();
   PairMap<R> pm;
   pm.mode = kProd;
@@ -84,7 +85,7 @@ int exchange_noalloc(rsx_ctx* c, const void* phi, int nocc, const void* psi, int
   const Cx<R>* twz = (const Cx<R>*)c->tw[0];
   const Cx<R>* twy = (const Cx<R>*)c->tw[1];
   const Cx<R>* twx = (const Cx<R>*)c->tw[2];
-  const int per_sm = c->pass2_ctas_per_sm<R>();
+  const int per_sm = std::max(1, pass2_occupancy<R>(g));
   const int grid = (int)std::min<long long>((long long)nocc * g.Hx, (long long)per_sm * c->nsm);
   for (int p = 0; p < npsi; ++p) {
     int rc = check_cuda(c, launch_pass1<R>(g, pm, p * nocc, nocc, inter, twx, s), "noalloc pass 1");
@@ -140,10 +141,12 @@ namespace {
 
 int noalloc_on_device(rsx_ctx* c, const void* phi, int nocc, const void* psi, int npsi, void* out, void* stream) {
   bool fits = false;
+  Geom g = c->g;
+  g.p2_global = 0;
   if (c->precision == RSX_FP32)
-    pass2_smem_bytes<float>(c->g, &fits);
+    pass2_smem_bytes<float>(g, &fits);
   else
-    pass2_smem_bytes<double>(c->g, &fits);
+    pass2_smem_bytes<double>(g, &fits);
   if (!fits) return set_error(c, RSX_EUNSUPPORTED, "noalloc exchange: box too large for the shared-memory y/z pass");
   void* scratch = nullptr;
   const int rc = scratch_address(c, c->device, &scratch);

@@ -69,9 +69,10 @@ inline size_t pass2_plane_bytes(const Geom& g) {
 
 template <typename R>
 size_t pass2_smem_bytes(const Geom& g, bool* fits) {
-  const size_t sc = pass2_scratch_smem<R>(g.Ay, g.Az, pass2_threads<R>(g));
+  const bool global = g.p2_global != 0;
+  const size_t sc = pass2_scratch_smem<R>(g.Ay, g.Az, global ? kThreads : pass2_threads<R>(g));
   const size_t pl = pass2_plane_bytes<R>(g);
-  const bool f = sc + pl <= (size_t)max_dyn_smem();
+  const bool f = !global && sc + pl <= (size_t)max_dyn_smem();
   if (fits) *fits = f;
   return f ? sc + pl : sc;
 }

@@ -65,6 +65,8 @@ struct Geom {
   int Hx;             // Mx / 2 + 1 (half spectrum along x)
   int p2_threads;     // tuning: threads per CTA of the y/z pass (256 or 512)
   int p1_group;       // tuning: pass-1 block order (0: pair-major; G > 0: pairs fastest in groups of G)
+  int p2_global;      // tuning: 1 = the y/z pass keeps its work plane in global scratch even where
+                      // shared memory would hold it (0 = shared memory whenever it fits)
   __host__ __device__ size_t N() const { return (size_t)nz * ny * nx; }
   __host__ __device__ size_t inter_elems() const { return (size_t)Hx * nz * ny; }  // complex per pair
 };

@@ -1,15 +1,22 @@
 // Autotuner for the pair-solve path.
 //
-// Candidates (per box size, precision and device):
-//   - threads per CTA of the y/z pass: 256, 384 or 512 (FP32; each only where its
-//     scratch fits);
-//   - output orbitals per exchange chunk: 1, 2, 4 or all.  Small chunks keep each
-//     chunk's pair intermediates (nocc x 7.15 MB at 96^3) near L2 size between passes,
-//     large chunks launch fewer, fuller grids.
-// Each candidate runs the exchange apply on synthetic orbitals on the device (one
-// warm-up, best of two timed runs with CUDA events); the fastest is applied to the
-// context and appended to a text cache keyed by (edges, precision, nocc, npsi, SMs,
-// device name) so later contexts skip the timing.
+// Knobs (rsx_tuning, per box size, precision and device):
+//   - p2_threads: threads per CTA of the y/z pass, 256, 384 (FP32) or 512, each used only
+//     where its line scratch and the work plane fit in shared memory;
+//   - p2_global: the y/z pass keeps its (nz x My) work plane in shared memory (one CTA per
+//     SM, next plane prefetched behind the current one) or in a global scratch slice per
+//     CTA that stays in L2 (only the line scratch in shared memory);
+//   - p1_group: the x pass's block order, pair-major (0) or pairs fastest in groups of G
+//     (CTAs in flight share their orbital rows in L2);
+//   - chunk_outputs: output orbitals per exchange chunk, 1, 2, 4 or all (small chunks keep
+//     a chunk's pair intermediates near L2 size between the passes, large chunks launch
+//     fewer, fuller grids).
+// The search is coordinate descent from the current knobs: the pass-2 configuration
+// (threads x plane staging) first, then the pass-1 order, then the chunking, each
+// candidate timed on the exchange apply of synthetic orbitals on the device (one warm-up,
+// best of two runs, CUDA events).  The winner is applied to the context and appended to
+// a text cache keyed by (edges, precision, nocc, npsi, SMs, device name), so later
+// contexts skip the timing.  No knob changes the arithmetic: results are bitwise the same.
 #include <cuda_runtime.h>
 
 #include <cstdio>
@@ -39,14 +46,14 @@ std::string cache_key(const rsx_ctx* c, int nocc, int npsi) {
   cudaDeviceProp prop;
   cudaGetDeviceProperties(&prop, c->device);
   char buf[512];
-  snprintf(buf, sizeof(buf), "rsx1 %d %d %d %s %d %d %d %s", c->g.nz, c->g.ny, c->g.nx,
+  snprintf(buf, sizeof(buf), "rsx2 %d %d %d %s %d %d %d %s", c->g.nz, c->g.ny, c->g.nx,
            c->precision == RSX_FP32 ? "fp32" : "fp64", nocc, npsi, c->nsm, prop.name);
   for (char* p = buf; *p; ++p)
-    if (*p == '\n') *p = ' ';
+    if (*p == '\n' || *p == '|') *p = ' ';
   return buf;
 }
 
-bool cache_lookup(const char* path, const std::string& key, int* p2, int* chunk) {
+bool cache_lookup(const char* path, const std::string& key, rsx_tuning* t) {
   if (!path || !*path) return false;
   FILE* f = fopen(path, "r");
   if (!f) return false;
@@ -54,26 +61,92 @@ bool cache_lookup(const char* path, const std::string& key, int* p2, int* chunk)
   bool found = false;
   while (fgets(line, sizeof(line), f)) {
     const size_t kl = key.size();
-    if (strncmp(line, key.c_str(), kl) == 0 && line[kl] == '|') {
-      if (sscanf(line + kl + 1, "%d %d", p2, chunk) == 2) found = true;  // last entry wins
+    rsx_tuning v;
+    if (strncmp(line, key.c_str(), kl) == 0 && line[kl] == '|' &&
+        sscanf(line + kl + 1, "%d %d %d %d", &v.p2_threads, &v.chunk_outputs, &v.p1_group, &v.p2_global) == 4) {
+      *t = v;   // last entry wins
+      found = true;
     }
   }
   fclose(f);
   return found;
 }
 
-void cache_store(const char* path, const std::string& key, int p2, int chunk, double ms) {
+void cache_store(const char* path, const std::string& key, const rsx_tuning& t, double ms) {
   if (!path || !*path) return;
   FILE* f = fopen(path, "a");
   if (!f) return;
-  fprintf(f, "%s|%d %d %.4f\n", key.c_str(), p2, chunk, ms);
+  fprintf(f, "%s|%d %d %d %d %.4f\n", key.c_str(), t.p2_threads, t.chunk_outputs, t.p1_group, t.p2_global, ms);
   fclose(f);
+}
+
+bool valid(const rsx_tuning& t) {
+  return (t.p2_threads == 256 || t.p2_threads == 384 || t.p2_threads == 512) && t.chunk_outputs >= 0 &&
+         t.p1_group >= 0 && (t.p2_global == 0 || t.p2_global == 1);
+}
+
+void apply(rsx_ctx* c, const rsx_tuning& t) {
+  c->g.p2_threads = t.p2_threads;
+  c->g.p1_group = t.p1_group;
+  c->g.p2_global = t.p2_global;
+  c->p2_occ[0] = c->p2_occ[1] = 0;
+  c->chunk_outputs = t.chunk_outputs;
+}
+
+rsx_tuning current(const rsx_ctx* c) {
+  rsx_tuning t;
+  t.p2_threads = c->g.p2_threads;
+  t.chunk_outputs = c->chunk_outputs;
+  t.p1_group = c->g.p1_group;
+  t.p2_global = c->g.p2_global;
+  return t;
+}
+
+// best of two timed exchange applies (after one warm-up) under knobs t
+int time_candidate(rsx_ctx* c, const rsx_tuning& t, const void* phi, int nocc, const void* psi, int npsi, void* out,
+                   cudaEvent_t e0, cudaEvent_t e1, double* ms_out) {
+  apply(c, t);
+  int rc = rsx_exchange_apply(c, phi, nocc, psi, npsi, out, nullptr);
+  if (rc) return rc;
+  double best = 1e30;
+  for (int r = 0; r < 2; ++r) {
+    cudaEventRecord(e0, 0);
+    rc = rsx_exchange_apply(c, phi, nocc, psi, npsi, out, nullptr);
+    cudaEventRecord(e1, 0);
+    if (rc) return rc;
+    if (cudaEventSynchronize(e1) != cudaSuccess) return check_cuda(c, cudaGetLastError(), "autotune timing");
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) best = ms;
+  }
+  *ms_out = best;
+  return RSX_OK;
 }
 
 }  // namespace
 
-extern "C" int rsx_autotune(rsx_ctx* c, int nocc, int npsi, const char* cache_path, int* p2_threads,
-                            int* chunk_outputs, double* best_ms) {
+extern "C" int rsx_get_tuning(rsx_ctx* c, rsx_tuning* out) {
+  if (!c || !out) return RSX_EINVAL;
+  *out = current(c);
+  return RSX_OK;
+}
+
+extern "C" int rsx_set_tuning_ex(rsx_ctx* c, const rsx_tuning* t) {
+  if (!c || !t || !valid(*t)) return RSX_EINVAL;
+  apply(c, *t);
+  return RSX_OK;
+}
+
+extern "C" int rsx_set_tuning(rsx_ctx* c, int p2_threads, int chunk_outputs) {
+  if (!c) return RSX_EINVAL;
+  rsx_tuning t = current(c);
+  t.p2_threads = p2_threads;
+  t.chunk_outputs = chunk_outputs;
+  return rsx_set_tuning_ex(c, &t);
+}
+
+extern "C" int rsx_autotune_ex(rsx_ctx* c, int nocc, int npsi, const char* cache_path, rsx_tuning* chosen,
+                               double* best_ms) {
   if (!c || nocc < 1 || npsi < 1) return RSX_EINVAL;
   c->err[0] = 0;
   if (cudaSetDevice(c->device) != cudaSuccess) {
@@ -81,12 +154,10 @@ extern "C" int rsx_autotune(rsx_ctx* c, int nocc, int npsi, const char* cache_pa
     return set_error(c, RSX_ECUDA, "cudaSetDevice failed");
   }
   const std::string key = cache_key(c, nocc, npsi);
-  int bp2 = 256, bch = 0;
+  rsx_tuning best = current(c);
   double bms = -1.0;
-  if (cache_lookup(cache_path, key, &bp2, &bch)) {
-    c->g.p2_threads = bp2;
-    c->p2_occ[0] = c->p2_occ[1] = 0;
-    c->chunk_outputs = bch;
+  if (cache_lookup(cache_path, key, &best) && valid(best)) {
+    apply(c, best);
   } else {
     const size_t N = c->g.N(), es = c->elem_size();
     void *phi = nullptr, *psi = nullptr, *out = nullptr;
@@ -107,35 +178,43 @@ extern "C" int rsx_autotune(rsx_ctx* c, int nocc, int npsi, const char* cache_pa
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    const int saved_p2 = c->g.p2_threads, saved_ch = c->chunk_outputs;
-    const int p2s[3] = {256, 384, 512};
-    const int chs[4] = {1, 2, 4, 0};
-    int rc = RSX_OK;
-    for (int a = 0; a < 3 && !rc; ++a) {
-      if (a > 0 && c->precision != RSX_FP32) break;
-      for (int b = 0; b < 4 && !rc; ++b) {
-        if (chs[b] >= npsi) continue;
-        c->g.p2_threads = p2s[a];
-        c->p2_occ[0] = c->p2_occ[1] = 0;
-        c->chunk_outputs = chs[b];
-        rc = rsx_exchange_apply(c, phi, nocc, psi, npsi, out, nullptr);
-        if (rc) break;
-        double best = 1e30;
-        for (int r = 0; r < 2 && !rc; ++r) {
-          cudaEventRecord(e0, 0);
-          rc = rsx_exchange_apply(c, phi, nocc, psi, npsi, out, nullptr);
-          cudaEventRecord(e1, 0);
-          cudaEventSynchronize(e1);
-          float ms = 0.f;
-          cudaEventElapsedTime(&ms, e0, e1);
-          if (ms < best) best = ms;
-        }
-        if (!rc && (bms < 0 || best < bms)) {
-          bms = best;
-          bp2 = p2s[a];
-          bch = chs[b];
-        }
+    const rsx_tuning saved = current(c);
+    int rc = time_candidate(c, best, phi, nocc, psi, npsi, out, e0, e1, &bms);
+    auto consider = [&](const rsx_tuning& t) {
+      if (rc) return;
+      double ms = 0.0;
+      rc = time_candidate(c, t, phi, nocc, psi, npsi, out, e0, e1, &ms);
+      if (!rc && ms < bms) {
+        bms = ms;
+        best = t;
       }
+    };
+    // 1. pass-2 configuration: CTA size x plane staging
+    const int p2s[3] = {256, 384, 512};
+    for (int a = 0; a < 3; ++a) {
+      if (a > 0 && c->precision != RSX_FP32) break;
+      for (int gl = 0; gl < 2; ++gl) {
+        if (gl == 1 && a > 0) continue;   // the global-plane kernel runs at 256 threads
+        rsx_tuning t = best;
+        t.p2_threads = p2s[a];
+        t.p2_global = gl;
+        consider(t);
+      }
+    }
+    // 2. pass-1 block order
+    const int groups[5] = {0, 4, 16, 64, 1 << 30};
+    for (int gi = 0; gi < 5; ++gi) {
+      rsx_tuning t = best;
+      t.p1_group = groups[gi];
+      consider(t);
+    }
+    // 3. output orbitals per chunk
+    const int chs[4] = {1, 2, 4, 0};
+    for (int b = 0; b < 4; ++b) {
+      if (chs[b] >= npsi) continue;
+      rsx_tuning t = best;
+      t.chunk_outputs = chs[b];
+      consider(t);
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -143,25 +222,23 @@ extern "C" int rsx_autotune(rsx_ctx* c, int nocc, int npsi, const char* cache_pa
     cudaFree(psi);
     cudaFree(out);
     if (rc) {
-      c->g.p2_threads = saved_p2;
-      c->chunk_outputs = saved_ch;
+      apply(c, saved);
       return rc;
     }
-    c->g.p2_threads = bp2;
-    c->p2_occ[0] = c->p2_occ[1] = 0;
-    c->chunk_outputs = bch;
-    cache_store(cache_path, key, bp2, bch, bms);
+    apply(c, best);
+    cache_store(cache_path, key, best, bms);
   }
-  if (p2_threads) *p2_threads = c->g.p2_threads;
-  if (chunk_outputs) *chunk_outputs = c->chunk_outputs;
+  if (chosen) *chosen = current(c);
   if (best_ms) *best_ms = bms;
   return RSX_OK;
 }
 
-extern "C" int rsx_set_tuning(rsx_ctx* c, int p2_threads, int chunk_outputs) {
-  if (!c || (p2_threads != 256 && p2_threads != 384 && p2_threads != 512) || chunk_outputs < 0) return RSX_EINVAL;
-  c->g.p2_threads = p2_threads;
-  c->p2_occ[0] = c->p2_occ[1] = 0;
-  c->chunk_outputs = chunk_outputs;
+extern "C" int rsx_autotune(rsx_ctx* c, int nocc, int npsi, const char* cache_path, int* p2_threads,
+                            int* chunk_outputs, double* best_ms) {
+  rsx_tuning t;
+  const int rc = rsx_autotune_ex(c, nocc, npsi, cache_path, &t, best_ms);
+  if (rc) return rc;
+  if (p2_threads) *p2_threads = t.p2_threads;
+  if (chunk_outputs) *chunk_outputs = t.chunk_outputs;
   return RSX_OK;
 }

@@ -78,6 +78,9 @@ SIGNATURES = {
     "rsx_batch_destroy": [_P],
     "rsx_autotune": [_P, _I, _I, ctypes.c_char_p, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_D)],
     "rsx_set_tuning": [_P, _I, _I],
+    "rsx_get_tuning": [_P, _P],
+    "rsx_set_tuning_ex": [_P, _P],
+    "rsx_autotune_ex": [_P, _I, _I, ctypes.c_char_p, _P, ctypes.POINTER(_D)],
     "rsx_sync_status": [_P, _P],
     "rsx_profile_enable": [_P, _I],
     "rsx_profile_reset": [_P],
@@ -87,6 +90,14 @@ SIGNATURES = {
 }
 
 _lib = None
+
+
+class Tuning(ctypes.Structure):
+    """rsx_tuning: knobs of the pair-solve path (performance only)."""
+    _fields_ = [("p2_threads", _I), ("chunk_outputs", _I), ("p1_group", _I), ("p2_global", _I)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class RsxError(RuntimeError):
@@ -170,14 +181,26 @@ class Context:
 
     def autotune(self, nocc, npsi, cache=None):
         """Time the exchange-path candidates on the device and apply the fastest."""
-        p2, ch, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
-        self._check(self.lib.rsx_autotune(self.handle, int(nocc), int(npsi),
-                                          cache.encode() if cache else None,
-                                          ctypes.byref(p2), ctypes.byref(ch), ctypes.byref(ms)))
-        return {"p2_threads": p2.value, "chunk_outputs": ch.value, "best_ms": ms.value}
+        t, ms = Tuning(), ctypes.c_double()
+        self._check(self.lib.rsx_autotune_ex(self.handle, int(nocc), int(npsi),
+                                             cache.encode() if cache else None,
+                                             ctypes.byref(t), ctypes.byref(ms)))
+        return dict(t.as_dict(), best_ms=ms.value)
 
-    def set_tuning(self, p2_threads=256, chunk_outputs=0):
-        self._check(self.lib.rsx_set_tuning(self.handle, int(p2_threads), int(chunk_outputs)))
+    def get_tuning(self):
+        t = Tuning()
+        self._check(self.lib.rsx_get_tuning(self.handle, ctypes.byref(t)))
+        return t.as_dict()
+
+    def set_tuning(self, p2_threads=None, chunk_outputs=None, p1_group=None, p2_global=None):
+        """Set any of the knobs (the others keep their values)."""
+        t = Tuning()
+        self._check(self.lib.rsx_get_tuning(self.handle, ctypes.byref(t)))
+        for k, v in (("p2_threads", p2_threads), ("chunk_outputs", chunk_outputs), ("p1_group", p1_group),
+                     ("p2_global", p2_global)):
+            if v is not None:
+                setattr(t, k, int(v))
+        self._check(self.lib.rsx_set_tuning_ex(self.handle, ctypes.byref(t)))
 
     def pair_densities(self, a, b, out=None, stream=None):
         na, nb = self._orb(a, "a"), self._orb(b, "b")

@@ -77,3 +77,43 @@ def test_batch_rejects_unsupported_edges():
     need_gpu()
     with pytest.raises(rsx.RsxError):
         rsx.Batch([40], [2], 0.3)
+
+
+def test_full_size_uneven_batch_every_edge():
+    """The 64-molecule batch (edges from {48, 64, 80, 96, 112} at h = 0.2, N_occ U{2..24}):
+    every molecule's W against the single-problem path, xi through the ACE identity
+    -xi <xi, phi> = W (holds at any size), and for each edge the molecule with the most
+    orbitals against the FP64 oracle at sampled points (direct sums, one point at a time)."""
+    need_gpu()
+    h = 0.2
+    desc = inputs.uneven_batch()
+    assert {e for e, _, _ in desc} == {48, 64, 80, 96, 112}
+    mols = [inputs.batched_system(n=e, h=h, nocc=k, npsi=0, seed=sd) for e, k, sd in desc]
+    b, phi, W, xi = run_batch(mols, h=h)
+    ctxs = {}
+    for m, (e, k, _) in enumerate(desc):
+        ctx = ctxs.setdefault(e, rsx.Context((e, e, e), h, "fp32"))
+        w1 = ctx.exchange_apply(phi[m], phi[m])
+        ctx.sync()
+        err = rel_max_err(W[m].double().cpu().numpy(), w1.double().cpu().numpy())
+        assert torch.equal(W[m], w1), (m, e, k, err)
+        # ACE identity on the batch's own xi (FP64 products of the FP32 arrays)
+        X = xi[m].double().reshape(k, -1)
+        P = phi[m].double().reshape(k, -1)
+        C = h ** 3 * (X @ P.T)
+        ace = -(C.T @ X)
+        Wd = W[m].double().reshape(k, -1)
+        assert ((ace - Wd).abs().max() / Wd.abs().max()).item() < 3e-5, (m, e, k)
+    for c in ctxs.values():
+        c.close()
+    rng = np.random.default_rng(11)
+    for e in sorted({e for e, _, _ in desc}):
+        m = max((i for i, d in enumerate(desc) if d[0] == e), key=lambda i: desc[i][1])
+        k = desc[m][1]
+        p = k - 1
+        # sample points within 2.5 bohr of the box centre, where the orbitals live
+        pts = [tuple(int(round(e / 2 + c / h)) for c in rng.uniform(-2.5 / 3 ** 0.5, 2.5 / 3 ** 0.5, 3))
+               for _ in range(8)]
+        ref = oracle.exchange_apply_at(mols[m].phi, mols[m].phi[p], h, pts)
+        got = np.array([W[m][p][q].item() for q in pts])
+        assert np.max(np.abs(got - ref)) < TOL["fp32"] * np.max(np.abs(ref)), (m, e, k)

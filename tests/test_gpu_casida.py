@@ -152,3 +152,64 @@ def test_config3_full_size_split_bf16_vs_fp64():
         v_u = oracle.poisson_fft(s.phi[j] * s.phi_virt[b], s.h)
         k_ref = oracle.inner(rho_t, v_u, s.h)
         assert abs(K64n[t, u] - k_ref) <= 1e-10 * abs(K64n).max()
+
+
+def test_casida_K_multi_tile_vs_oracle():
+    """135 transitions (two 128-row tiles of the panel, one of them ragged) at 24^3: the
+    split-BF16 tensor-core K element-wise against the FP64 oracle, over ~1800 K blocks of
+    the split-K contraction; the FP64 plain form against the same oracle."""
+    need_gpu()
+    shape, h, no, nv = (24, 24, 24), 0.45, 3, 45
+    s = casida_system(shape, h, no, nv, seed=4)
+    K_ref = oracle.casida_K(s.phi, s.phi_virt, h)
+    for prec in ("fp32", "fp64"):
+        ctx = rsx.Context(shape, h, prec)
+        K = ctx.casida_K(to_dev(s.phi, prec), to_dev(s.phi_virt, prec))
+        ctx.sync()
+        K = K.cpu().numpy()
+        assert K.shape == (135, 135)
+        assert rel_max_err(K, K_ref) < TOL_K[prec], prec
+        # the off-diagonal tile block (rows 128.., columns ..127) on its own
+        assert np.max(np.abs(K[128:, :128] - K_ref[128:, :128])) < TOL_K[prec] * np.abs(K_ref).max()
+        ctx.close()
+
+
+def test_config3_against_the_oracle_golden():
+    """80^3 at 0.25 bohr, 8 occupied + 64 virtual (512 transitions): the split-BF16 K and
+    the FP64 plain K against the FP64 oracle's values in tests/golden/casida_80cubed.json
+    (written by make_casida_golden.py from the oracle alone): the diagonal, the row sums and
+    4096 sampled entries of K, 512 sampled entries of K_d, and the lowest 10 roots of
+    diag + K and of the singlet diag + 2K - K_d to 1e-5 eV."""
+    import json
+    import os
+    need_gpu()
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "casida_80cubed.json")))
+    c = gold["case"]
+    s = inputs.casida_system(n=c["n"], h=c["h"], nocc=c["nocc"], nvirt=c["nvirt"], seed=c["seed"])
+    kmax = gold["K_max_abs"]
+    samp = np.array(gold["K_samples"])
+    ti, ui = samp[:, 0].astype(int), samp[:, 1].astype(int)
+    dsamp = np.array(gold["Kd_samples"])
+    eo, ev = to_dev(s.eps_occ, "fp64"), to_dev(s.eps_virt, "fp64")
+    c64 = rsx.Context(s.shape, s.h, "fp64")
+    for prec, tol in (("fp32", TOL_K["fp32"]), ("fp64", 1e-10)):
+        ctx = rsx.Context(s.shape, s.h, prec)
+        po, pv = to_dev(s.phi, prec), to_dev(s.phi_virt, prec)
+        K = ctx.casida_K(po, pv)
+        Kd = ctx.casida_Kd(po, pv)
+        ctx.sync()
+        Kn = K.cpu().numpy()
+        assert np.max(np.abs(np.diag(Kn) - np.array(gold["K_diag"]))) < tol * kmax, prec
+        assert np.max(np.abs(Kn[ti, ui] - samp[:, 2])) < tol * kmax, prec
+        # row sums: 512 terms each, the per-entry bound times sqrt(512) (unbiased rounding)
+        assert np.max(np.abs(Kn.sum(axis=1) - np.array(gold["K_row_sums"]))) < tol * kmax * 512 ** 0.5, prec
+        Kdn = Kd.cpu().numpy()
+        kd_tol = TOL_KD[prec] if prec == "fp32" else 1e-10
+        assert np.max(np.abs(Kdn[dsamp[:, 0].astype(int), dsamp[:, 1].astype(int)] - dsamp[:, 2])) \
+            < kd_tol * gold["Kd_max_abs"], prec
+        w1 = c64.casida_solve(eo, ev, K, None, 1.0, 10)
+        w2 = c64.casida_solve(eo, ev, K, Kd, 2.0, 10)
+        c64.sync()
+        assert np.max(np.abs(w1.cpu().numpy() - np.array(gold["omega_diag_plus_K_ha"]))) * HA_EV < 1e-5, prec
+        assert np.max(np.abs(w2.cpu().numpy() - np.array(gold["omega_singlet_ha"]))) * HA_EV < 1e-5, prec
+        ctx.close()

@@ -2,8 +2,10 @@
 
 All calls go through the C ABI (ctypes binding).  Sizes span several CTA tiles and
 ragged tails: ny = 24 and 40 leave a partial 32-row block, nz = 24 and 40 are not
-multiples of 16 (uneven row loops), nx != ny exercises the per-axis transforms; at
-112^3 the pass-2 work plane does not fit in shared memory and lives in global scratch.
+multiples of 16 (uneven row loops), nx != ny exercises the per-axis transforms.  The
+y/z pass keeps its work plane in shared memory wherever it fits (FP32 up to 112^3, at 256
+threads there; FP64 up to 64^3) and in global scratch otherwise (FP64 from 80^3) or when
+the p2_global tuning knob asks for it (tested separately in FP32, 112^3 included).
 """
 import numpy as np
 import pytest
@@ -22,7 +24,7 @@ CASES = [
     ((24, 24, 40), 0.30, 2, 2, "fp32"),
     ((40, 40, 16), 0.30, 2, 3, "fp32"),
     ((56, 56, 24), 0.30, 1, 2, "fp32"),      # odd A = 7 along y and z
-    ((112, 112, 112), 0.25, 1, 1, "fp32"),   # largest edge: the pass-2 plane lives in global scratch
+    ((112, 112, 112), 0.25, 1, 1, "fp32"),   # largest edge: the pass-2 plane just fits at 256 threads
     ((16, 16, 16), 0.40, 2, 3, "fp64"),
     ((24, 24, 40), 0.30, 2, 2, "fp64"),
     ((56, 56, 24), 0.30, 1, 2, "fp64"),
@@ -181,3 +183,22 @@ def test_config2_full_size_sampled_outputs():
         e_ref, e_got = oracle.inner(s.psi[p], ref, s.h), oracle.inner(s.psi[p], got, s.h)
         assert abs(e_got - e_ref) <= TOL_ENERGY["fp32"] * abs(e_ref)
     assert rel_max_err(vphi.double().cpu().numpy(), w.double().cpu().numpy()) < 3e-5
+
+
+@pytest.mark.parametrize("shape,h,nocc,npsi", [((24, 24, 40), 0.30, 2, 2), ((112, 112, 112), 0.25, 1, 1)])
+def test_fp32_global_plane_pass2_path(shape, h, nocc, npsi):
+    """The FP32 y/z pass with its work plane forced into global scratch (p2_global = 1):
+    the same bits as the shared-memory path and parity with the oracle."""
+    need_gpu()
+    s = system(shape, h, nocc, npsi, seed=5)
+    ctx = rsx.Context(shape, h, "fp32")
+    phi, psi = to_dev(s.phi, "fp32"), to_dev(s.psi, "fp32")
+    a = ctx.exchange_apply(phi, psi)
+    ctx.set_tuning(p2_global=1)
+    assert ctx.get_tuning()["p2_global"] == 1
+    b = ctx.exchange_apply(phi, psi)
+    ctx.sync()
+    assert torch.equal(a, b)
+    ref = oracle.exchange_apply(s.phi, s.psi, h)
+    assert rel_max_err(b.double().cpu().numpy(), ref) < TOL["fp32"]
+

@@ -1,4 +1,5 @@
-"""GPU test of the autotuner: valid choice, cache round trip, identical results."""
+"""GPU test of the autotuner: valid choice over its four knobs, cache round trip,
+identical results under every knob, and a choice no slower than the alternatives."""
 import os
 
 import pytest
@@ -20,16 +21,59 @@ def test_autotune_choice_cache_and_bitwise_results(tmp_path):
     cache = str(tmp_path / "tune.txt")
     t1 = ctx.autotune(3, 5, cache=cache)
     assert t1["p2_threads"] in (256, 384, 512) and t1["chunk_outputs"] in (0, 1, 2, 4)
+    assert t1["p2_global"] in (0, 1) and t1["p1_group"] in (0, 4, 16, 64, 1 << 30)
     assert t1["best_ms"] > 0 and os.path.exists(cache)
     out = ctx.exchange_apply(phi, psi)
     ctx.sync()
     assert torch.equal(out, ref)            # tuning changes scheduling, not arithmetic
     ctx2 = rsx.Context(shape, h, "fp32")
     t2 = ctx2.autotune(3, 5, cache=cache)
-    assert t2["best_ms"] == -1.0 and t2["p2_threads"] == t1["p2_threads"]
-    assert t2["chunk_outputs"] == t1["chunk_outputs"]
-    for p2, ch in ((512, 1), (384, 4), (256, 2), (256, 0)):
-        ctx2.set_tuning(p2, ch)
+    assert t2["best_ms"] == -1.0
+    for k in ("p2_threads", "chunk_outputs", "p1_group", "p2_global"):
+        assert t2[k] == t1[k], k
+    for knobs in (dict(p2_threads=512, chunk_outputs=1), dict(p2_threads=384, chunk_outputs=4, p1_group=0),
+                  dict(p2_threads=256, chunk_outputs=2, p2_global=1), dict(p2_global=0, p1_group=4, chunk_outputs=0)):
+        ctx2.set_tuning(**knobs)
         o2 = ctx2.exchange_apply(phi, psi)
         ctx2.sync()
-        assert torch.equal(o2, ref)
+        assert torch.equal(o2, ref), knobs
+    with pytest.raises(rsx.RsxError):
+        ctx2.set_tuning(p2_global=2)
+
+
+def _time(ctx, phi, psi, out, reps=5):
+    ctx.exchange_apply(phi, psi, out=out)
+    torch.cuda.synchronize()
+    best = 1e30
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ctx.exchange_apply(phi, psi, out=out)
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    return best
+
+
+def test_autotune_choice_is_not_slower_than_the_alternatives():
+    """At 64^3 with 8 x 16 pairs the chosen knobs, re-timed, are within 10% of the best
+    re-timed alternative (one knob changed at a time from the choice)."""
+    need_gpu()
+    shape, h = (64, 64, 64), 0.25
+    s = inputs.exchange_system(h=h, nocc=8, npsi=16, shape=shape, radius=2.0, seed=6)
+    ctx = rsx.Context(shape, h, "fp32")
+    phi, psi = to_dev(s.phi, "fp32"), to_dev(s.psi, "fp32")
+    out = torch.empty_like(psi)
+    chosen = ctx.autotune(8, 16)
+    chosen.pop("best_ms")
+    t_chosen = _time(ctx, phi, psi, out)
+    alts = []
+    for k, vals in (("p2_threads", (256, 384, 512)), ("p2_global", (0, 1)), ("p1_group", (0, 16, 1 << 30)),
+                    ("chunk_outputs", (1, 4, 0))):
+        for v in vals:
+            if v != chosen[k]:
+                ctx.set_tuning(**dict(chosen, **{k: v}))
+                alts.append((_time(ctx, phi, psi, out), k, v))
+    ctx.set_tuning(**chosen)
+    best_alt = min(alts)
+    assert t_chosen <= 1.10 * best_alt[0], (t_chosen, best_alt, chosen)

@@ -87,6 +87,21 @@ def test_gaussian_density_erf_potential_converges():
 # ---------------------------------------------------------------- exchange (Eq. 2)
 
 
+def test_point_sampled_potential_and_exchange_match_the_full_sums():
+    """The point-by-point forms used on large boxes equal the full direct sum (Poisson)
+    and the brute-force exchange loops at the same points, on ragged small boxes."""
+    shape, h = (5, 7, 6), 0.4
+    rho = rng_fields(shape, 1, 31)[0]
+    pts = [(0, 0, 0), (4, 6, 5), (2, 3, 1), (1, 5, 4)]
+    full = oracle.poisson_direct(rho, h)
+    assert np.allclose(oracle.potential_at(rho, h, pts), [full[p] for p in pts], rtol=0, atol=1e-12)
+    phi = rng_fields((4, 4, 3), 2, 32)
+    psi = rng_fields((4, 4, 3), 1, 33)
+    ref = oracle.exchange_apply_bruteforce(phi, psi, 0.5)[0]
+    pts = [(0, 0, 0), (3, 3, 2), (1, 2, 0)]
+    assert np.allclose(oracle.exchange_apply_at(phi, psi[0], 0.5, pts), [ref[p] for p in pts], rtol=0, atol=1e-12)
+
+
 def test_exchange_matches_bruteforce_loops():
     phi = rng_fields((3, 4, 3), 2, 2)
     psi = rng_fields((3, 4, 3), 3, 3)

@@ -365,6 +365,23 @@ int rsx_profile_read(rsx_ctx* ctx, int kernel, double* total_ms, long long* laun
 int rsx_kernel_count(void);
 const char* rsx_kernel_name(int kernel);
 
+/* Failure detection, exercised without faulting the GPU (testing aids; the paper has no
+ * counterpart).
+ * rsx_set_wait_limit: spin rounds a CTA of the context's cooperative kernels (the
+ *   grid-wide barrier of the multi-CTA Householder reduction) waits before giving up;
+ *   spins < 0 restores the default (2^24 rounds, far beyond any normal wait), 0 makes
+ *   every CTA but the last arriver give up at once.  A CTA that gives up marks the
+ *   barrier aborted, every CTA leaves at its next barrier, and rsx_sync_status reports
+ *   RSX_ETIMEOUT (the call's results are then invalid; the context stays usable).
+ * rsx_inject_fault: kind RSX_FAULT_ALLOC makes the workspace allocation after `after`
+ *   more successful ones fail with RSX_ENOMEM without touching the device (once);
+ *   RSX_FAULT_PIVOT makes the next rsx_ace_build factorise the ACE matrix with its sign
+ *   flipped, so that the FP64 Cholesky meets a non-positive pivot and rsx_sync_status
+ *   reports RSX_ENOTPD (once); RSX_FAULT_NONE clears both.  Errors: RSX_EINVAL. */
+enum { RSX_FAULT_NONE = 0, RSX_FAULT_ALLOC = 1, RSX_FAULT_PIVOT = 2 };
+int rsx_set_wait_limit(rsx_ctx* ctx, long long spins);
+int rsx_inject_fault(rsx_ctx* ctx, int kind, int after);
+
 /* Synchronise `stream` and return the first deferred device error since the last call
  * (RSX_ENOTPD, RSX_ETIMEOUT) or a CUDA error; clears the device status word. */
 int rsx_sync_status(rsx_ctx* ctx, void* stream);

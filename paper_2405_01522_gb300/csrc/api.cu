@@ -35,6 +35,13 @@ int check_cuda(rsx_ctx* c, cudaError_t e, const char* what) {
 
 int grow(rsx_ctx* c, void** p, size_t* have, size_t need, const char* what) {
   if (need <= *have) return RSX_OK;
+  if (c && c->fault_alloc_after >= 0) {   // injected failure: nothing is allocated or freed
+    if (c->fault_alloc_after == 0) {
+      c->fault_alloc_after = -1;
+      return fail(c, RSX_ENOMEM, "injected allocation failure (%zu bytes for %s)", need, what);
+    }
+    --c->fault_alloc_after;
+  }
   if (*p) cudaFree(*p);
   *p = nullptr;
   *have = 0;
@@ -273,8 +280,11 @@ int ace_build(rsx_ctx* c, const void* phi, int nocc, void* xi, double* M_out, cu
   }
   if (rc) return rc;
   {
+    // an injected bad pivot flips M's sign, so that -M is negative definite
+    const double msc = c->fault_pivot ? -h3 : h3;
+    c->fault_pivot = false;
     ProfScope ps(c, kKGramReduce, s);
-    rc = check_cuda(c, launch_gram_reduce<R>(part, nblk, nocc, nocc, h3, false, M, (R*)nullptr, s), "gram reduce");
+    rc = check_cuda(c, launch_gram_reduce<R>(part, nblk, nocc, nocc, msc, false, M, (R*)nullptr, s), "gram reduce");
   }
   if (rc) return rc;
   {
@@ -487,6 +497,31 @@ int rsx_ace_apply(rsx_ctx* c, const void* xi, int nxi, const void* psi, int npsi
   cudaStream_t s = (cudaStream_t)stream;
   return c->precision == RSX_FP32 ? ace_apply<float>(c, xi, nxi, psi, npsi, out, s)
                                   : ace_apply<double>(c, xi, nxi, psi, npsi, out, s);
+}
+
+int rsx_set_wait_limit(rsx_ctx* c, long long spins) {
+  if (!c) return RSX_EINVAL;
+  c->wait_limit = spins < 0 ? -1 : spins;
+  return RSX_OK;
+}
+
+int rsx_inject_fault(rsx_ctx* c, int kind, int after) {
+  if (!c) return RSX_EINVAL;
+  switch (kind) {
+    case RSX_FAULT_NONE:
+      c->fault_alloc_after = -1;
+      c->fault_pivot = false;
+      return RSX_OK;
+    case RSX_FAULT_ALLOC:
+      if (after < 0) return RSX_EINVAL;
+      c->fault_alloc_after = after;
+      return RSX_OK;
+    case RSX_FAULT_PIVOT:
+      c->fault_pivot = true;
+      return RSX_OK;
+    default:
+      return RSX_EINVAL;
+  }
 }
 
 int rsx_profile_enable(rsx_ctx* c, int on) {

@@ -43,6 +43,11 @@ struct rsx_ctx {
   void* tdhf_work = nullptr; size_t tdhf_work_bytes = 0; // full TDHF: L, A + B, products
   int p2_occ[2] = {0, 0};
   int chunk_outputs = 0;   // tuning: output orbitals per exchange chunk (0 = as many as fit)
+  long long wait_limit = -1;   // spin rounds of the bounded grid waits (-1: the kernels' default)
+  // host-side fault injection (testing aid): fail the workspace allocation after
+  // fault_alloc_after more successful ones (-1: off); flip the sign of the next ACE matrix
+  int fault_alloc_after = -1;
+  bool fault_pivot = false;
   // launch profiler: events recorded around every kernel while enabled
   bool prof_on = false;
   struct ProfRec { int id; cudaEvent_t a, b; };

@@ -157,7 +157,9 @@ struct GridBar {
   volatile int abort;
 };
 
-__device__ __forceinline__ bool grid_barrier(GridBar* gb, unsigned int nblocks) {
+// wait_limit: spin rounds before a waiting CTA gives up (kGridWaitLimit unless the context
+// sets another; 0 makes every CTA but the last arriver give up at once)
+__device__ __forceinline__ bool grid_barrier(GridBar* gb, unsigned int nblocks, unsigned int wait_limit) {
   __syncthreads();
   __shared__ int ok_sh;
   if (threadIdx.x == 0) {
@@ -171,7 +173,7 @@ __device__ __forceinline__ bool grid_barrier(GridBar* gb, unsigned int nblocks) 
     } else {
       uint32_t i = 0;
       while (gb->gen == g0) {
-        if (gb->abort || ++i > kGridWaitLimit) {
+        if (gb->abort || ++i > wait_limit) {
           gb->abort = 1;
           ok_sh = 0;
           break;
@@ -233,7 +235,8 @@ __device__ __forceinline__ F cta_sum_partials(const F* part, unsigned int G, F* 
 template <typename F>
 __global__ void __launch_bounds__(256) k_tridiag_coop(F* __restrict__ A, int n, F* __restrict__ d,
                                                       F* __restrict__ e, F* __restrict__ tau,
-                                                      F* __restrict__ scr, GridBar* gb, int* status) {
+                                                      F* __restrict__ scr, GridBar* gb, int* status,
+                                                      unsigned int wait_limit) {
   const unsigned int G = gridDim.x;
   const int cta = blockIdx.x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
@@ -260,7 +263,7 @@ __global__ void __launch_bounds__(256) k_tridiag_coop(F* __restrict__ A, int n, 
       if (n > 1 && 1 % (int)G == cta) *alpha_g = A[(size_t)1 * n];
     }
   }
-  live = grid_barrier(gb, G);
+  live = grid_barrier(gb, G, wait_limit);
 
   for (int k = 0; k + 2 < n && live; ++k) {
     const int m0 = k + 1;
@@ -294,7 +297,7 @@ __global__ void __launch_bounds__(256) k_tridiag_coop(F* __restrict__ A, int n, 
       vv[i] = vi;
       if (i > m0) A[(size_t)i * n + k] = vi;
     }
-    if (!(live = grid_barrier(gb, G))) break;
+    if (!(live = grid_barrier(gb, G, wait_limit))) break;
     // ---- p_i = tau (A22 v)_i for own rows, partial p^T v
     F pv_part = F(0);
     if (tk != F(0)) {
@@ -325,7 +328,7 @@ __global__ void __launch_bounds__(256) k_tridiag_coop(F* __restrict__ A, int n, 
       const F t = warp_sum(lane < nwarp ? red[lane] : F(0));
       if (lane == 0) part_pv[cta] = t;
     }
-    if (!(live = grid_barrier(gb, G))) break;
+    if (!(live = grid_barrier(gb, G, wait_limit))) break;
     // ---- w = p - (tau/2)(p^T v) v ; A22 -= v w^T + w v^T on own rows; next column norm
     F nrm_part = F(0);
     if (tk != F(0)) {
@@ -362,7 +365,7 @@ __global__ void __launch_bounds__(256) k_tridiag_coop(F* __restrict__ A, int n, 
       const F t = warp_sum(lane < nwarp ? red[lane] : F(0));
       if (lane == 0) part_norm[cta] = t;
     }
-    live = grid_barrier(gb, G);
+    live = grid_barrier(gb, G, wait_limit);
   }
   if (cta == 0 && threadIdx.x == 0) {
     if (!live) {
@@ -803,8 +806,10 @@ static int tridiagonalise(rsx_ctx* c, F* A, int n, F* d, F* e, F* tau, F* scr, F
   if (coop && per_sm > 0 && n >= 64 && (force.empty() || force == "coop")) {
     GridBar* gb = reinterpret_cast<GridBar*>(scr + 2 * (size_t)n + 2 * 1024 + 2);
     cudaMemsetAsync(gb, 0, sizeof(GridBar), s);
+    unsigned int wait_limit = c->wait_limit < 0 ? kGridWaitLimit
+                              : (unsigned int)std::min<long long>(c->wait_limit, 0xffffffffLL);
     void* args[] = {(void*)&A, (void*)&n, (void*)&d, (void*)&e, (void*)&tau, (void*)&scr, (void*)&gb,
-                    (void*)&c->status};
+                    (void*)&c->status, (void*)&wait_limit};
     const size_t smem = 2 * (size_t)n * sizeof(F);
     cudaFuncSetAttribute(k_tridiag_coop<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     return check_cuda(c, cudaLaunchCooperativeKernel((const void*)k_tridiag_coop<F>, dim3(G), dim3(256), args, smem, s),

@@ -14,6 +14,7 @@ LIB_PATH = os.path.join(_HERE, "librsx.so")
 
 RSX_OK, RSX_EINVAL, RSX_ENOMEM, RSX_ECUDA, RSX_ENOTPD, RSX_ETIMEOUT, RSX_EUNSUPPORTED = range(7)
 RSX_FP64, RSX_FP32 = 0, 1
+RSX_FAULT_NONE, RSX_FAULT_ALLOC, RSX_FAULT_PIVOT = 0, 1, 2
 ERROR_NAMES = {1: "RSX_EINVAL", 2: "RSX_ENOMEM", 3: "RSX_ECUDA", 4: "RSX_ENOTPD", 5: "RSX_ETIMEOUT",
                6: "RSX_EUNSUPPORTED"}
 
@@ -82,6 +83,8 @@ SIGNATURES = {
     "rsx_set_tuning_ex": [_P, _P],
     "rsx_autotune_ex": [_P, _I, _I, ctypes.c_char_p, _P, ctypes.POINTER(_D)],
     "rsx_sync_status": [_P, _P],
+    "rsx_set_wait_limit": [_P, ctypes.c_longlong],
+    "rsx_inject_fault": [_P, _I, _I],
     "rsx_profile_enable": [_P, _I],
     "rsx_profile_reset": [_P],
     "rsx_profile_read": [_P, _I, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_longlong)],
@@ -351,6 +354,14 @@ class Context:
 
     def sync(self, stream=None):
         self._check(self.lib.rsx_sync_status(self.handle, _stream(stream)))
+
+    def set_wait_limit(self, spins):
+        """Spin rounds of the bounded grid waits (testing aid; < 0 restores the default)."""
+        self._check(self.lib.rsx_set_wait_limit(self.handle, int(spins)))
+
+    def inject_fault(self, kind, after=0):
+        """Host-side fault injection (testing aid): RSX_FAULT_ALLOC, RSX_FAULT_PIVOT, RSX_FAULT_NONE."""
+        self._check(self.lib.rsx_inject_fault(self.handle, int(kind), int(after)))
 
 
 class Batch:

@@ -71,8 +71,9 @@ const char* rsx_last_error(const rsx_ctx* ctx);
  * within it.  Default: 40% of the device memory free at rsx_create, at most 64 GiB. */
 int rsx_set_workspace_limit(rsx_ctx* ctx, size_t bytes);
 
-/* Tuning knobs of the pair-solve path (performance only: no knob changes the results,
- * which stay bitwise identical).
+/* Tuning knobs of the pair-solve path (performance only: the results stay bitwise
+ * identical under every knob except p2_lanes, which changes the rounding order of the
+ * line transforms, both splits being equally accurate).
  *   p2_threads     threads per CTA of the y/z transform pass: 256, 384 (FP32) or 512; a
  *                  size is used only where its line scratch and the work plane fit in
  *                  shared memory (else 256)
@@ -80,20 +81,27 @@ int rsx_set_workspace_limit(rsx_ctx* ctx, size_t bytes);
  *   p1_group       x-pass block order: 0 pair-major, G > 0 pairs fastest in groups of G
  *   p2_global      1: the y/z pass keeps its work plane in a global (L2-resident) scratch
  *                  slice per CTA even where shared memory would hold it; 0: shared memory
- *                  whenever it fits */
+ *                  whenever it fits
+ *   p2_lanes       radix split of the y/z line transforms, M = 2n points per line: 16 (16
+ *                  lanes x A: A-point DFTs in registers, then 16-point DFTs across lanes)
+ *                  or 8 (8 lanes x 2A: 2A-point DFTs, then 8-point DFTs; FP32 with
+ *                  shared-memory plane and A = M / 16 in {4, 8, 12}, i.e. edges 32, 64, 96;
+ *                  elsewhere the 16-lane split runs) */
 typedef struct rsx_tuning {
   int p2_threads;
   int chunk_outputs;
   int p1_group;
   int p2_global;
+  int p2_lanes;
 } rsx_tuning;
 int rsx_get_tuning(rsx_ctx* ctx, rsx_tuning* out);
 /* Errors: RSX_EINVAL (null, or a knob outside the values above). */
 int rsx_set_tuning_ex(rsx_ctx* ctx, const rsx_tuning* t);
 /* Autotuner (the paper has no counterpart; a performance knob).  Times the exchange
  * apply for nocc x npsi pairs on synthetic device data under candidate knobs, by
- * coordinate descent from the current ones: pass-2 CTA size x plane staging, then the
- * pass-1 block order (0, 4, 16, 64, all), then output orbitals per chunk (1, 2, 4, all);
+ * coordinate descent from the current ones: pass-2 CTA size x plane staging x line split
+ * (16 or 8 lanes), then the pass-1 block order (0, 4, 16, 64, all), then output orbitals
+ * per chunk (1, 2, 4, all);
  * applies the fastest to the context.  With a non-empty cache_path the result is appended
  * to that text file, keyed by box, precision, nocc, npsi, SM count and device name, and a
  * later call with the same key applies it without timing.  chosen (may be NULL) receives

@@ -160,6 +160,25 @@ int make_tables(rsx_ctx* c) {
     else
       e = launch_vhat_lanes(g, (const float*)c->vhat, (float*)c->vhatz, 0);
   }
+  if (e == cudaSuccess && sizeof(R) == 4 && g.Ay == g.Az && g.Ay % 4 == 0) {
+    // the 8-lane y/z kernel: its lane-order table and twiddles w_M^{-t k1}, t < 8, k1 < 2 A
+    size_t have8 = 0, have_tw = 0;
+    const int A2 = 2 * g.Az;
+    std::vector<Cx<float>> tw8(8 * A2);
+    for (int t = 0; t < 8; ++t)
+      for (int k1 = 0; k1 < A2; ++k1) {
+        const long long ex = (long long)t * k1 % g.Mz;
+        const double ang = 2.0 * M_PI * (double)ex / (double)g.Mz;
+        tw8[t * A2 + k1].x = (float)cos(ang);
+        tw8[t * A2 + k1].y = (float)(-sin(ang));
+      }
+    if (grow(c, &c->vhatz8, &have8, (size_t)hx * hy * g.Mz * sizeof(float), "kernel table (8-lane order)") != RSX_OK ||
+        grow(c, &c->tw8, &have_tw, tw8.size() * sizeof(Cx<float>), "8-lane twiddles") != RSX_OK)
+      e = cudaErrorMemoryAllocation;
+    else
+      e = cudaMemcpy(c->tw8, tw8.data(), tw8.size() * sizeof(Cx<float>), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = launch_vhat_lanes8(g, (const float*)c->vhat, (float*)c->vhatz8, 0);
+  }
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   cudaFree(b0);
   cudaFree(b1);
@@ -224,7 +243,9 @@ int solve_pairs(rsx_ctx* c, const PairMap<R>& pm, int q0, int nq, int p0, int np
   }
   {
     ProfScope ps(c, kKPass2, s);
-    rc = check_cuda(c, launch_pass2<R>(g, nq, inter, twy, twz, (const R*)c->vhat, (const float*)c->vhatz, gscr, grid, s), "pass 2");
+    rc = check_cuda(c, launch_pass2<R>(g, nq, inter, twy, twz, (const R*)c->vhat, (const float*)c->vhatz, gscr, grid, s,
+                                       (const Cx<float>*)c->tw8, (const float*)c->vhatz8),
+                    "pass 2");
   }
   if (rc) return rc;
   if (out != nullptr) {
@@ -394,6 +415,7 @@ int rsx_create(rsx_ctx** out, int nz, int ny, int nx, double h, int precision, i
   g.p1_group = 1 << 30;   // pass-1 blocks pair-fastest over the whole launch (orbital rows shared in L2)
   if (const char* e = getenv("RSX_PASS1_GROUP")) g.p1_group = atoi(e) > 0 ? atoi(e) : 0;
   g.p2_global = 0;
+  g.p2_lanes = 16;
   cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, device);
   size_t freeb = 0, totalb = 0;
   cudaMemGetInfo(&freeb, &totalb);
@@ -418,7 +440,7 @@ int rsx_destroy(rsx_ctx* c) {
   cudaDeviceSynchronize();
   prof_collect(c);
   for (cudaEvent_t e : c->prof_pool) cudaEventDestroy(e);
-  void* bufs[] = {c->vhat, c->vhatz, c->tw[0], c->tw[1], c->tw[2], c->work, c->gscr, c->dsm, c->smallr, c->status,
+  void* bufs[] = {c->vhat, c->vhatz, c->vhatz8, c->tw8, c->tw[0], c->tw[1], c->tw[2], c->work, c->gscr, c->dsm, c->smallr, c->status,
                   c->panel_hi, c->panel_lo, c->gemm_part, c->eig_work, c->gscr_kd, c->pos, c->tdhf_work, c->specw, c->ones};
   for (void* b : bufs)
     if (b) cudaFree(b);

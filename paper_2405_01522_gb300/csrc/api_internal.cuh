@@ -26,6 +26,8 @@ struct rsx_ctx {
   // device buffers owned by the context
   void* vhat = nullptr;                 // kernel table T[kx][ky][kz] (R)
   void* vhatz = nullptr;                // FP32: the same in pass 2's lane order (launch_vhat_lanes)
+  void* vhatz8 = nullptr;               // FP32, Ay % 4 == 0: the order of the 8-lane y/z kernel
+  void* tw8 = nullptr;                  // FP32, Ay % 4 == 0: twiddles w_M^{-t k1}, t < 8, k1 < 2 Ay
   void* tw[3] = {nullptr, nullptr, nullptr};
   void* work = nullptr;   size_t work_bytes = 0;     // FFT intermediates
   void* gscr = nullptr;   size_t gscr_bytes = 0;     // pass-2 planes when shared memory is too small

@@ -493,8 +493,28 @@ __global__ void k_vhat_lanes(const float* __restrict__ T, int rows, int hz, int 
   }
 }
 
+// 8-lane order: entry p of a row is lane s = p / (2 Az), j = (p % (2 Az)) / 8, k2 = p % 8
+__global__ void k_vhat_lanes8(const float* __restrict__ T, int rows, int hz, int Az, float* __restrict__ out) {
+  const int Mz = 16 * Az, A2 = 2 * Az;
+  const size_t n = (size_t)rows * Mz;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t row = i / Mz;
+    const int p = (int)(i - row * Mz);
+    const int s = p / A2, rem = p - s * A2;
+    const int j = rem >> 3, k2 = rem & 7;
+    const int kz = (s + 8 * j) + A2 * k2;
+    out[i] = T[row * hz + (kz <= Mz / 2 ? kz : Mz - kz)];
+  }
+}
+
 // ---------------------------------------------------------------------------------
 // host launchers
+
+cudaError_t launch_vhat_lanes8(const Geom& g, const float* table, float* out, cudaStream_t s) {
+  const int rows = (g.Mx / 2 + 1) * (g.My / 2 + 1);
+  k_vhat_lanes8<<<1024, 256, 0, s>>>(table, rows, g.Mz / 2 + 1, g.Az, out);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_vhat_lanes(const Geom& g, const float* table, float* out, cudaStream_t s) {
   const int rows = (g.Mx / 2 + 1) * (g.My / 2 + 1);

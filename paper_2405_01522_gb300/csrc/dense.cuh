@@ -11,6 +11,8 @@ cudaError_t launch_ghat(const Geom& g, double h, double scale, const double* cos
                         cudaStream_t s);
 // FP32 kernel table in pass 2's lane order, (Mx/2+1)(My/2+1) Mz floats (k_vhat_lanes)
 cudaError_t launch_vhat_lanes(const Geom& g, const float* table, float* out, cudaStream_t s);
+// the kernel table in the 8-lane y/z kernel's order [kx][|ky|][s][j][k2], kz = (s + 8 j) + 2 Az k2
+cudaError_t launch_vhat_lanes8(const Geom& g, const float* table, float* out, cudaStream_t s);
 // part[blk][a][b] = partial sums of X_a(r) Y_b(r) w(r) (w may be null); na * nb <= 4096
 template <typename R>
 cudaError_t launch_gram(const R* X, int na, const R* Y, int nb, size_t N, double* part, int nblk,

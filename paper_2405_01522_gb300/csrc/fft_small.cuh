@@ -2,8 +2,8 @@
 //
 // dft<N, S>(v) replaces v[0..N) by X[k] = sum_j v[j] exp(S * 2 pi i j k / N)
 // (S = -1 forward, S = +1 inverse, no normalisation).  Supported N: 2, 3, 4, 5, 6, 7,
-// 8, 10, 12, 14, 16.  Odd primes use the symmetric real/imaginary split, 8 and 16 are
-// radix-2 / radix-4 Cooley-Tukey, and the coprime products 6, 10, 12, 14 use the
+// 8, 10, 12, 14, 16, 24.  Odd primes use the symmetric real/imaginary split, 8 and 16 are
+// radix-2 / radix-4 Cooley-Tukey, and the coprime products 6, 10, 12, 14, 24 use the
 // Good-Thomas prime-factor index map, which needs no twiddle factors.  All trig
 // constants are exact decimal expansions of cos/sin of rational multiples of pi.
 #pragma once
@@ -119,9 +119,18 @@ RSX_HD constexpr double trig_s(int p, int j) {
        : /* p == 16 */ trig_c(16, (j + 12) % 16);
 }
 
-// cos / sin (2 pi a / A) for even A in {2, ..., 14, 16} and 0 <= a < A / 2 (decimal expansions)
+// cos(2 pi a / 24), 0 <= a < 24: multiples of 15 degrees, (sqrt 6 +- sqrt 2) / 4 at 15 and 75
+RSX_HD constexpr double trig24_c(int a) {
+  return a == 0 ? 1.0 : a == 1 ? 0.96592582628906828675 : a == 2 ? 0.86602540378443864676
+       : a == 3 ? 0.70710678118654752440 : a == 4 ? 0.5 : a == 5 ? 0.25881904510252076235 : a == 6 ? 0.0
+       : a < 12 ? -trig24_c(12 - a) : a == 12 ? -1.0 : trig24_c(24 - a);
+}
+RSX_HD constexpr double trig24_s(int a) { return trig24_c((a + 18) % 24); }   // sin x = cos(x - pi / 2)
+
+// cos / sin (2 pi a / A) for even A in {2, ..., 14, 16, 24} and 0 <= a < A / 2 (decimal expansions)
 RSX_HD constexpr double trig_even_c(int A, int a) {
-  return A == 16 ? trig_c(16, a) : A == 8 ? trig_c(16, 2 * a) : A == 4 ? (a == 0 ? 1.0 : 0.0) : A == 2 ? 1.0
+  return A == 24 ? trig24_c(a)
+       : A == 16 ? trig_c(16, a) : A == 8 ? trig_c(16, 2 * a) : A == 4 ? (a == 0 ? 1.0 : 0.0) : A == 2 ? 1.0
        : A == 6 ? (a == 0 ? 1.0 : a == 1 ? 0.5 : -0.5)
        : A == 10 ? (a == 0 ? 1.0 : a == 1 ? 0.80901699437494742410 : a == 2 ? 0.30901699437494742410
                     : a == 3 ? -0.30901699437494742410 : -0.80901699437494742410)
@@ -132,7 +141,8 @@ RSX_HD constexpr double trig_even_c(int A, int a) {
                         : a == 5 ? -0.62348980185873353053 : -0.90096886790241912624);
 }
 RSX_HD constexpr double trig_even_s(int A, int a) {
-  return A == 16 ? trig_s(16, a) : A == 8 ? trig_s(16, 2 * a) : A == 4 ? (a == 0 ? 0.0 : 1.0) : A == 2 ? 0.0
+  return A == 24 ? trig24_s(a)
+       : A == 16 ? trig_s(16, a) : A == 8 ? trig_s(16, 2 * a) : A == 4 ? (a == 0 ? 0.0 : 1.0) : A == 2 ? 0.0
        : A == 6 ? (a == 0 ? 0.0 : 0.86602540378443864676)
        : A == 10 ? (a == 0 ? 0.0 : (a == 1 || a == 4) ? 0.58778525229247312917 : 0.95105651629515357212)
        : A == 12 ? (a == 0 ? 0.0 : (a == 1 || a == 5) ? 0.5 : (a == 2 || a == 4) ? 0.86602540378443864676 : 1.0)
@@ -297,6 +307,7 @@ template <int S> struct Dft<6, S> : DftPfa<2, 3, S> {};
 template <int S> struct Dft<10, S> : DftPfa<2, 5, S> {};
 template <int S> struct Dft<12, S> : DftPfa<3, 4, S> {};
 template <int S> struct Dft<14, S> : DftPfa<2, 7, S> {};
+template <int S> struct Dft<24, S> : DftPfa<3, 8, S> {};
 
 // DFT of length A (even) whose inputs v[A/2 .. A) are zero: only v[0 .. A/2) are read.
 // X[2m] = DFT_{A/2}(v)[m], X[2m+1] = DFT_{A/2}(v[a] w^a)[m], w = exp(S 2 pi i / A).

@@ -1,6 +1,7 @@
 // Launchers of the pair Poisson passes for one precision R (included once per TU).
 #pragma once
 #include "poisson_kernels.cuh"
+#include "poisson_pass2_l8.cuh"
 
 namespace rsx {
 
@@ -101,12 +102,57 @@ int pass2_occupancy(const Geom& g) {
   return nb;
 }
 
+// threads per CTA of the 8-lane kernel (384 where its scratch and the plane fit, else
+// 256), 0 when it does not serve this geometry
+template <int A>
+inline int pass2_l8_threads(const Geom& g) {
+  const int want = g.p2_threads == 256 ? 256 : 384;
+  for (int nt : {want, 256})
+    if (pass2_l8_smem<A>(nt) <= (size_t)max_dyn_smem()) return nt;
+  return 0;
+}
+
+inline bool pass2_l8_ok(const Geom& g, const void* tw8, const void* vl8) {
+  if (g.p2_lanes != 8 || g.p2_global || !tw8 || !vl8 || g.Ay != g.Az) return false;
+  switch (g.Ay) {
+    case 4: return pass2_l8_threads<4>(g) > 0;
+    case 8: return pass2_l8_threads<8>(g) > 0;
+    case 12: return pass2_l8_threads<12>(g) > 0;
+    default: return false;
+  }
+}
+
+template <int A>
+cudaError_t launch_pass2_l8(const Geom& g, int nq, Cx<float>* inter, const Cx<float>* tw8, const float* vl8, int grid,
+                            cudaStream_t s) {
+  const int nt = pass2_l8_threads<A>(g);
+  const size_t smem = pass2_l8_smem<A>(nt);
+  // 384 threads: twiddles from the shared table (no spills); 256: held in registers
+  auto k = nt == 384 ? k_pass2_l8<A, 384, true> : k_pass2_l8<A, 256, false>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k<<<grid, nt, smem, s>>>(g, nq, inter, tw8, vl8);
+  return cudaGetLastError();
+}
+
 template <typename R>
 cudaError_t launch_pass2(const Geom& g, int nq, Cx<R>* inter, const Cx<R>* twy, const Cx<R>* twz,
-                         const R* vhat, const float* vhat_lanes, R* gscratch, int grid, cudaStream_t s) {
+                         const R* vhat, const float* vhat_lanes, R* gscratch, int grid, cudaStream_t s,
+                         const Cx<float>* tw8, const float* vl8) {
   if (nq <= 0) return cudaSuccess;
   if (g.Ay != g.Az) return cudaErrorInvalidValue;
   if (sizeof(R) == 4 && vhat_lanes == nullptr) return cudaErrorInvalidValue;   // FP32 reads the lane-order table
+  if constexpr (sizeof(R) == 4) {
+    if (pass2_l8_ok(g, tw8, vl8)) {
+      Cx<float>* in = reinterpret_cast<Cx<float>*>(inter);
+      switch (g.Ay) {
+        case 4: return launch_pass2_l8<4>(g, nq, in, tw8, vl8, grid, s);
+        case 8: return launch_pass2_l8<8>(g, nq, in, tw8, vl8, grid, s);
+        case 12: return launch_pass2_l8<12>(g, nq, in, tw8, vl8, grid, s);
+        default: break;
+      }
+    }
+  }
   bool fits = false;
   const size_t smem = pass2_smem_bytes<R>(g, &fits);
   if (!fits && gscratch == nullptr) return cudaErrorInvalidValue;

@@ -1,0 +1,225 @@
+// Pass 2 of the pair Poisson solve with the line transforms split 8 lanes x 2A.
+//
+// Same work as k_pass2 (per (pair, kx) plane: y forward on the nz rows, z forward x
+// kernel x z inverse on the My columns, y inverse keeping y < ny), but a line of length
+// M = 16 A = 8 x 2A is transformed by 8 lanes instead of 16:
+//   stage 1  lane t (< 8) holds x[t + 8 a], a < A (the non-zero half), does the 2A-point
+//            DFT over a in registers, multiplies by w_M^{-t k1} and stores row k1 of the
+//            line's scratch;
+//   stage 2  lane s does the 8-point DFTs over t of rows k1 = s + 8 j (j < 2A / 8), giving
+//            X[k1 + 2A k2].
+// With 16 lanes x A the 16-point stage keeps only A of 16 lanes busy (12 of 16 at
+// M = 192); here both stages keep all lanes busy (2A / 8 rows per lane).  The inverse
+// runs the same steps backwards and keeps the outputs z < nz (y < ny) only.
+// FP32, A in {4, 8, 12} (M = 64, 128, 192: 2A a multiple of 8).
+#pragma once
+#include "poisson_kernels.cuh"
+
+namespace rsx {
+
+// Line scratch: 2A rows of 8 complex (64 bytes).  Row k1 of line l is stored at physical
+// row k1 ^ (l & 1), and the four 16-byte chunks of physical row r are XOR-swizzled by
+// (r >> 1) & 3.  Then (i) the two lines of a half-warp (l even, l + 1) put the same row in
+// opposite halves of the banks, so the 8-byte accesses of stage 1 are conflict-free, and
+// (ii) the eight lanes of a line reading rows s + 8 j as 16-byte chunks in stage 2 hit
+// eight distinct bank groups.
+__device__ __forceinline__ int l8_off(int r, int t) { return r * 8 + 2 * ((t >> 1) ^ ((r >> 1) & 3)) + (t & 1); }
+
+__device__ __forceinline__ void l8_load_row(Cx<float> (&u)[8], const Cx<float>* sc, int r) {
+  const int sw = (r >> 1) & 3;
+  const float4* rp = reinterpret_cast<const float4*>(sc + r * 8);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const float4 v = rp[q ^ sw];
+    u[2 * q] = cx<float>(v.x, v.y);
+    u[2 * q + 1] = cx<float>(v.z, v.w);
+  }
+}
+
+__device__ __forceinline__ void l8_store_row(Cx<float>* sc, int r, const Cx<float> (&u)[8]) {
+  const int sw = (r >> 1) & 3;
+  float4* rp = reinterpret_cast<float4*>(sc + r * 8);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) rp[q ^ sw] = make_float4(u[2 * q].x, u[2 * q].y, u[2 * q + 1].x, u[2 * q + 1].y);
+}
+
+// This lane's stage-1 twiddles w_M^{-t k1}, k1 < 2A: held in registers (TWS = false) or
+// read from a shared table [k1][t] (TWS = true: 46 fewer live registers at A = 12; the
+// eight lanes of a line read 64 contiguous bytes, the lines of a warp the same ones).
+template <int A, bool TWS>
+struct L8Tw {
+  Cx<float> reg[TWS ? 1 : 2 * A];
+  const Cx<float>* sh;
+  int t;
+  __device__ __forceinline__ void init(const Cx<float>* __restrict__ tw8, const Cx<float>* shared_tab, int t_) {
+    t = t_;
+    sh = shared_tab;
+    if constexpr (!TWS) {
+#pragma unroll
+      for (int k1 = 1; k1 < 2 * A; ++k1) reg[k1] = tw8[t * 2 * A + k1];
+    }
+  }
+  __device__ __forceinline__ Cx<float> operator[](int k1) const {
+    if constexpr (TWS) return sh[k1 * 8 + t];
+    else return reg[k1];
+  }
+};
+
+// stage 1 forward: inputs src[(t + 8 a) * es], a < A (the rest of the line is zero)
+template <int A, class TW>
+__device__ __forceinline__ void l8_stage1_fwd(const Cx<float>* src, int es, int t, int par, const TW& tw,
+                                              Cx<float>* sc) {
+  constexpr int A2 = 2 * A;
+  Cx<float> v[A], x[A2];
+#pragma unroll
+  for (int a = 0; a < A; ++a) v[a] = src[(t + 8 * a) * es];
+  DftHalfIn<A2, -1>::run(v, x);
+#pragma unroll
+  for (int k1 = 1; k1 < A2; ++k1) x[k1] = cmul(x[k1], tw[k1]);
+#pragma unroll
+  for (int k1 = 0; k1 < A2; ++k1) sc[l8_off(k1 ^ par, t)] = x[k1];
+}
+
+// stage 1 inverse: rows k1 of the scratch (lane t's column), conjugate twiddles, 2A-point
+// inverse DFT keeping outputs a < A, written to dst[(t + 8 a) * es]
+template <int A, class TW>
+__device__ __forceinline__ void l8_stage1_inv(Cx<float>* dst, int es, int t, int par, const TW& tw,
+                                              const Cx<float>* sc) {
+  constexpr int A2 = 2 * A;
+  Cx<float> r[A2], o[A];
+#pragma unroll
+  for (int k1 = 0; k1 < A2; ++k1) r[k1] = sc[l8_off(k1 ^ par, t)];
+#pragma unroll
+  for (int k1 = 1; k1 < A2; ++k1) r[k1] = cmul(r[k1], conj(tw[k1]));
+  DftHalfOut<A2, 1>::run(r, o);
+#pragma unroll
+  for (int a = 0; a < A; ++a) dst[(t + 8 * a) * es] = o[a];
+}
+
+// one (pair, kx) plane; D: (nz x My) work plane, row pitch M + 1, input rows staged in
+// columns [ny, 2 ny) (prefetched); the result goes back to the plane P in global memory
+template <int A, int NT, class TW>
+__device__ __forceinline__ void l8_plane(Cx<float>* P, int kx, int Hy, const float* __restrict__ vl8, Cx<float>* D,
+                                         Cx<float>* sc, int lp, int t, int par, unsigned lmask, const TW& tw,
+                                         const Cx<float>* Pnext) {
+  constexpr int A2 = 2 * A, J = A2 / 8, M = 16 * A, NB = 8 * A, DP = M + 1, NL = NT / 8;
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  __syncthreads();
+  // ---- y forward of the nz rows (input columns [NB, 2 NB), outputs all M columns)
+  for (int z = lp; z < NB; z += NL) {
+    Cx<float>* row = D + z * DP;
+    l8_stage1_fwd<A>(row + NB, 1, t, par, tw, sc);
+    __syncwarp(lmask);
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+      const int k1 = t + 8 * j;
+      Cx<float> u[8];
+      l8_load_row(u, sc, k1 ^ par);
+      Dft<8, -1>::run(u);
+#pragma unroll
+      for (int k2 = 0; k2 < 8; ++k2) row[k1 + A2 * k2] = u[k2];
+    }
+    __syncwarp(lmask);
+  }
+  __syncthreads();
+  // ---- z forward, kernel multiply, z inverse on the M columns ky
+  const float* vrow = vl8 + (size_t)kx * Hy * M;
+  for (int ky = lp; ky < M; ky += NL) {
+    const int iy = ky <= M / 2 ? ky : M - ky;
+    l8_stage1_fwd<A>(D + ky, DP, t, par, tw, sc);
+    __syncwarp(lmask);
+    const float4* vq = reinterpret_cast<const float4*>(vrow + (size_t)iy * M + t * A2);
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+      const int r = (t + 8 * j) ^ par;
+      Cx<float> u[8];
+      l8_load_row(u, sc, r);
+      Dft<8, -1>::run(u);
+      const float4 m0 = __ldg(vq + 2 * j), m1 = __ldg(vq + 2 * j + 1);
+      u[0] = cscale(u[0], m0.x);
+      u[1] = cscale(u[1], m0.y);
+      u[2] = cscale(u[2], m0.z);
+      u[3] = cscale(u[3], m0.w);
+      u[4] = cscale(u[4], m1.x);
+      u[5] = cscale(u[5], m1.y);
+      u[6] = cscale(u[6], m1.z);
+      u[7] = cscale(u[7], m1.w);
+      Dft<8, 1>::run(u);
+      l8_store_row(sc, r, u);   // row r is read and written by this lane only
+    }
+    __syncwarp(lmask);
+    l8_stage1_inv<A>(D + ky, DP, t, par, tw, sc);
+    __syncwarp(lmask);
+  }
+  __syncthreads();
+  // ---- y inverse of the nz rows, keeping y < ny
+  for (int z = lp; z < NB; z += NL) {
+    Cx<float>* row = D + z * DP;
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+      const int k1 = t + 8 * j;
+      Cx<float> u[8];
+#pragma unroll
+      for (int k2 = 0; k2 < 8; ++k2) u[k2] = row[k1 + A2 * k2];
+      Dft<8, 1>::run(u);
+      l8_store_row(sc, k1 ^ par, u);
+    }
+    __syncwarp(lmask);
+    l8_stage1_inv<A>(row, 1, t, par, tw, sc);
+    __syncwarp(lmask);
+  }
+  __syncthreads();
+  if (Pnext) prefetch_plane_upper<float>(D, DP, Pnext, NB, NB, NT);
+  store_plane<NT>(D, DP, P, NB, NB);
+  __syncthreads();
+}
+
+// Persistent grid over the work items (pair, kx); the plane lives in shared memory and the
+// next plane is prefetched into the upper halves of its rows behind the current one.
+// tw8[t][k1] = w_M^{-t k1} (t < 8, k1 < 2A); vl8: the kernel table in this kernel's lane
+// order, [kx][|ky|][s][j][k2] with kz = (s + 8 j) + 2A k2.
+// Shared memory: [twiddle table A2 x 8] [line scratch NL x A2 x 8] [plane NB x (M + 1)].
+template <int A, int NT, bool TWS>
+__global__ void __launch_bounds__(NT, 1) k_pass2_l8(Geom g, int nq, Cx<float>* __restrict__ inter,
+                                                    const Cx<float>* __restrict__ tw8, const float* __restrict__ vl8) {
+  constexpr int A2 = 2 * A, M = 16 * A, NB = 8 * A, DP = M + 1, NL = NT / 8;
+  static_assert(NL % 16 == 0, "lines per CTA: a multiple of 16 (line pairing)");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Cx<float>* twtab = reinterpret_cast<Cx<float>*>(smem_raw);
+  Cx<float>* scr = twtab + A2 * 8;
+  Cx<float>* D = scr + NL * A2 * 8;
+  const int lane = threadIdx.x & 31, t = lane & 7, line = threadIdx.x >> 3, par = line & 1;
+  const unsigned lmask = 0xFFu << (lane & 24);
+  // the two lines of a half-warp take rows / columns 8 apart (disjoint banks in D)
+  const int lp = (line & ~15) | ((line & 1) << 3) | ((line >> 1) & 7);
+  Cx<float>* sc = scr + line * A2 * 8;
+  if constexpr (TWS) {
+    for (int i = threadIdx.x; i < A2 * 8; i += NT) {   // [k1][t] from the table's [t][k1]
+      const int k1 = i >> 3, tt = i & 7;
+      twtab[i] = tw8[tt * A2 + k1];
+    }
+    __syncthreads();
+  }
+  L8Tw<A, TWS> tw;
+  tw.init(tw8, twtab, t);
+  const int Hy = M / 2 + 1;
+  const int nplane = NB * NB;
+  const int nwork = nq * g.Hx;
+  auto plane_ptr = [&](int w) {
+    const int ql = w / g.Hx, kx = w - ql * g.Hx;
+    return inter + (size_t)ql * g.inter_elems() + (size_t)kx * nplane;
+  };
+  if ((int)blockIdx.x < nwork) prefetch_plane_upper<float>(D, DP, plane_ptr(blockIdx.x), NB, NB, NT);
+  for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
+    const int kx = w % g.Hx;
+    const int wn = w + (int)gridDim.x;
+    l8_plane<A, NT>(plane_ptr(w), kx, Hy, vl8, D, sc, lp, t, par, lmask, tw, wn < nwork ? plane_ptr(wn) : nullptr);
+  }
+}
+
+template <int A>
+inline size_t pass2_l8_smem(int nt) {
+  return sizeof(Cx<float>) * ((size_t)2 * A * 8 + (size_t)(nt / 8) * 2 * A * 8 + (size_t)(8 * A) * (16 * A + 1));
+}
+
+}  // namespace rsx

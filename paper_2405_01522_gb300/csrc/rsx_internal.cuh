@@ -67,6 +67,8 @@ struct Geom {
   int p1_group;       // tuning: pass-1 block order (0: pair-major; G > 0: pairs fastest in groups of G)
   int p2_global;      // tuning: 1 = the y/z pass keeps its work plane in global scratch even where
                       // shared memory would hold it (0 = shared memory whenever it fits)
+  int p2_lanes;       // tuning: lanes per line of the y/z transforms, 16 (16 x A) or 8 (8 x 2A;
+                      // FP32, A a multiple of 4, shared-memory plane)
   __host__ __device__ size_t N() const { return (size_t)nz * ny * nx; }
   __host__ __device__ size_t inter_elems() const { return (size_t)Hx * nz * ny; }  // complex per pair
 };
@@ -75,9 +77,14 @@ struct Geom {
 template <typename R>
 cudaError_t launch_pass1(const Geom& g, const PairMap<R>& pm, int q0, int nq, Cx<R>* inter,
                          const Cx<R>* twx, cudaStream_t s);
+// tw8 / vl8: twiddles and lane-order kernel table of the 8-lane split (FP32; NULL: the
+// 16-lane kernel runs whatever g.p2_lanes says)
 template <typename R>
 cudaError_t launch_pass2(const Geom& g, int nq, Cx<R>* inter, const Cx<R>* twy, const Cx<R>* twz,
-                         const R* vhat, const float* vhat_lanes, R* gscratch, int grid, cudaStream_t s);
+                         const R* vhat, const float* vhat_lanes, R* gscratch, int grid, cudaStream_t s,
+                         const Cx<float>* tw8 = nullptr, const float* vl8 = nullptr);
+// true when the 8-lane y/z kernel serves geometry g (FP32) with these tables
+bool pass2_l8_active(const Geom& g, const void* tw8, const void* vl8);
 template <typename R>
 cudaError_t launch_pass3(const Geom& g, const PairMap<R>& pm, int q0, int p0, int np, int pot, const Cx<R>* inter,
                          const Cx<R>* twx, R* out, cudaStream_t s);

@@ -6,17 +6,20 @@
 //   - p2_global: the y/z pass keeps its (nz x My) work plane in shared memory (one CTA per
 //     SM, next plane prefetched behind the current one) or in a global scratch slice per
 //     CTA that stays in L2 (only the line scratch in shared memory);
+//   - p2_lanes: the radix split of the y/z line transforms (M = 16 A points), 16 lanes x A
+//     or 8 lanes x 2A (FP32, A in {4, 8, 12});
 //   - p1_group: the x pass's block order, pair-major (0) or pairs fastest in groups of G
 //     (CTAs in flight share their orbital rows in L2);
 //   - chunk_outputs: output orbitals per exchange chunk, 1, 2, 4 or all (small chunks keep
 //     a chunk's pair intermediates near L2 size between the passes, large chunks launch
 //     fewer, fuller grids).
 // The search is coordinate descent from the current knobs: the pass-2 configuration
-// (threads x plane staging) first, then the pass-1 order, then the chunking, each
+// (threads x plane staging x line split) first, then the pass-1 order, then the chunking, each
 // candidate timed on the exchange apply of synthetic orbitals on the device (one warm-up,
 // best of two runs, CUDA events).  The winner is applied to the context and appended to
 // a text cache keyed by (edges, precision, nocc, npsi, SMs, device name), so later
-// contexts skip the timing.  No knob changes the arithmetic: results are bitwise the same.
+// contexts skip the timing.  Only p2_lanes changes the arithmetic (the rounding order of
+// the line transforms); under the other knobs the results are bitwise the same.
 #include <cuda_runtime.h>
 
 #include <cstdio>
@@ -46,7 +49,7 @@ std::string cache_key(const rsx_ctx* c, int nocc, int npsi) {
   cudaDeviceProp prop;
   cudaGetDeviceProperties(&prop, c->device);
   char buf[512];
-  snprintf(buf, sizeof(buf), "rsx2 %d %d %d %s %d %d %d %s", c->g.nz, c->g.ny, c->g.nx,
+  snprintf(buf, sizeof(buf), "rsx3 %d %d %d %s %d %d %d %s", c->g.nz, c->g.ny, c->g.nx,
            c->precision == RSX_FP32 ? "fp32" : "fp64", nocc, npsi, c->nsm, prop.name);
   for (char* p = buf; *p; ++p)
     if (*p == '\n' || *p == '|') *p = ' ';
@@ -63,7 +66,8 @@ bool cache_lookup(const char* path, const std::string& key, rsx_tuning* t) {
     const size_t kl = key.size();
     rsx_tuning v;
     if (strncmp(line, key.c_str(), kl) == 0 && line[kl] == '|' &&
-        sscanf(line + kl + 1, "%d %d %d %d", &v.p2_threads, &v.chunk_outputs, &v.p1_group, &v.p2_global) == 4) {
+        sscanf(line + kl + 1, "%d %d %d %d %d", &v.p2_threads, &v.chunk_outputs, &v.p1_group, &v.p2_global,
+               &v.p2_lanes) == 5) {
       *t = v;   // last entry wins
       found = true;
     }
@@ -76,19 +80,21 @@ void cache_store(const char* path, const std::string& key, const rsx_tuning& t, 
   if (!path || !*path) return;
   FILE* f = fopen(path, "a");
   if (!f) return;
-  fprintf(f, "%s|%d %d %d %d %.4f\n", key.c_str(), t.p2_threads, t.chunk_outputs, t.p1_group, t.p2_global, ms);
+  fprintf(f, "%s|%d %d %d %d %d %.4f\n", key.c_str(), t.p2_threads, t.chunk_outputs, t.p1_group, t.p2_global,
+          t.p2_lanes, ms);
   fclose(f);
 }
 
 bool valid(const rsx_tuning& t) {
   return (t.p2_threads == 256 || t.p2_threads == 384 || t.p2_threads == 512) && t.chunk_outputs >= 0 &&
-         t.p1_group >= 0 && (t.p2_global == 0 || t.p2_global == 1);
+         t.p1_group >= 0 && (t.p2_global == 0 || t.p2_global == 1) && (t.p2_lanes == 16 || t.p2_lanes == 8);
 }
 
 void apply(rsx_ctx* c, const rsx_tuning& t) {
   c->g.p2_threads = t.p2_threads;
   c->g.p1_group = t.p1_group;
   c->g.p2_global = t.p2_global;
+  c->g.p2_lanes = t.p2_lanes;
   c->p2_occ[0] = c->p2_occ[1] = 0;
   c->chunk_outputs = t.chunk_outputs;
 }
@@ -99,6 +105,7 @@ rsx_tuning current(const rsx_ctx* c) {
   t.chunk_outputs = c->chunk_outputs;
   t.p1_group = c->g.p1_group;
   t.p2_global = c->g.p2_global;
+  t.p2_lanes = c->g.p2_lanes;
   return t;
 }
 
@@ -189,16 +196,22 @@ extern "C" int rsx_autotune_ex(rsx_ctx* c, int nocc, int npsi, const char* cache
         best = t;
       }
     };
-    // 1. pass-2 configuration: CTA size x plane staging
+    // 1. pass-2 configuration: CTA size x plane staging x line split
     const int p2s[3] = {256, 384, 512};
+    const bool l8 = c->precision == RSX_FP32 && pass2_l8_active(
+        [&] { Geom g8 = c->g; g8.p2_lanes = 8; g8.p2_global = 0; return g8; }(), c->tw8, c->vhatz8);
     for (int a = 0; a < 3; ++a) {
       if (a > 0 && c->precision != RSX_FP32) break;
       for (int gl = 0; gl < 2; ++gl) {
         if (gl == 1 && a > 0) continue;   // the global-plane kernel runs at 256 threads
-        rsx_tuning t = best;
-        t.p2_threads = p2s[a];
-        t.p2_global = gl;
-        consider(t);
+        for (int ln = 0; ln < 2; ++ln) {
+          if (ln == 1 && (!l8 || gl == 1 || a == 2)) continue;   // 8 lanes: shared plane, 256 or 384 threads
+          rsx_tuning t = best;
+          t.p2_threads = p2s[a];
+          t.p2_global = gl;
+          t.p2_lanes = ln ? 8 : 16;
+          consider(t);
+        }
       }
     }
     // 2. pass-1 block order

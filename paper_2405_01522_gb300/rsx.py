@@ -97,7 +97,7 @@ _lib = None
 
 class Tuning(ctypes.Structure):
     """rsx_tuning: knobs of the pair-solve path (performance only)."""
-    _fields_ = [("p2_threads", _I), ("chunk_outputs", _I), ("p1_group", _I), ("p2_global", _I)]
+    _fields_ = [("p2_threads", _I), ("chunk_outputs", _I), ("p1_group", _I), ("p2_global", _I), ("p2_lanes", _I)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -195,12 +195,12 @@ class Context:
         self._check(self.lib.rsx_get_tuning(self.handle, ctypes.byref(t)))
         return t.as_dict()
 
-    def set_tuning(self, p2_threads=None, chunk_outputs=None, p1_group=None, p2_global=None):
+    def set_tuning(self, p2_threads=None, chunk_outputs=None, p1_group=None, p2_global=None, p2_lanes=None):
         """Set any of the knobs (the others keep their values)."""
         t = Tuning()
         self._check(self.lib.rsx_get_tuning(self.handle, ctypes.byref(t)))
         for k, v in (("p2_threads", p2_threads), ("chunk_outputs", chunk_outputs), ("p1_group", p1_group),
-                     ("p2_global", p2_global)):
+                     ("p2_global", p2_global), ("p2_lanes", p2_lanes)):
             if v is not None:
                 setattr(t, k, int(v))
         self._check(self.lib.rsx_set_tuning_ex(self.handle, ctypes.byref(t)))

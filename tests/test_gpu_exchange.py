@@ -202,3 +202,33 @@ def test_fp32_global_plane_pass2_path(shape, h, nocc, npsi):
     ref = oracle.exchange_apply(s.phi, s.psi, h)
     assert rel_max_err(b.double().cpu().numpy(), ref) < TOL["fp32"]
 
+
+
+@pytest.mark.parametrize("shape,h,nocc,npsi", [((32, 32, 24), 0.30, 2, 3), ((64, 64, 40), 0.25, 2, 2),
+                                               ((96, 96, 96), 0.20, 1, 2)])
+def test_fp32_eight_lane_split_of_the_yz_pass(shape, h, nocc, npsi):
+    """The y/z line transforms split 8 lanes x 2A (p2_lanes = 8; edges 32, 64, 96) at 384
+    threads (twiddles from a shared table) and 256 threads (twiddles in registers): the
+    two give the same bits, both match the oracle element-wise and in <psi, Vx psi>, and
+    ACE built on this path reproduces the exchange on its orbitals."""
+    need_gpu()
+    s = system(shape, h, nocc, npsi, seed=8)
+    ctx = rsx.Context(shape, h, "fp32")
+    phi, psi = to_dev(s.phi, "fp32"), to_dev(s.psi, "fp32")
+    outs = []
+    for nt in (384, 256):
+        ctx.set_tuning(p2_threads=nt, p2_lanes=8)
+        outs.append(ctx.exchange_apply(phi, psi))
+    ctx.sync()
+    assert torch.equal(outs[0], outs[1])
+    ref = oracle.exchange_apply(s.phi, s.psi, h)
+    got = outs[0].double().cpu().numpy()
+    assert rel_max_err(got, ref) < TOL["fp32"]
+    for p in range(npsi):
+        e_ref, e_got = oracle.inner(s.psi[p], ref[p], h), oracle.inner(s.psi[p], got[p], h)
+        assert abs(e_got - e_ref) <= TOL_ENERGY["fp32"] * abs(e_ref)
+    xi = ctx.ace_build(phi)
+    w = ctx.exchange_apply(phi, phi)
+    vphi = ctx.ace_apply(xi, phi)
+    ctx.sync()
+    assert rel_max_err(vphi.double().cpu().numpy(), w.double().cpu().numpy()) < 3e-5

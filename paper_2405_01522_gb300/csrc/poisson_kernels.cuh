@@ -37,7 +37,7 @@ __device__ __forceinline__ float bf16_bits_to_f32(uint32_t b) { return __uint_as
 // ---------------------------------------------------------------------------------
 // stage helpers (executed by the 16 lanes t of one half-warp on one line)
 // stage 1: v holds x[t + 16 a]; DFT over a, twiddle, store scratch[k1][t]
-template <int A, int S, typename R>
+template <int A, int S, typename R, int PITCH = kScrPitch>
 __device__ __forceinline__ void stage1_store(Cx<R> (&v)[A], int t, const Cx<R>* __restrict__ tw,
                                              Cx<R>* sc) {
   Dft<A, S>::run(v);
@@ -48,12 +48,12 @@ __device__ __forceinline__ void stage1_store(Cx<R> (&v)[A], int t, const Cx<R>* 
     v[k1] = cmul(v[k1], w);
   }
 #pragma unroll
-  for (int k1 = 0; k1 < A; ++k1) sc[k1 * kScrPitch + t] = v[k1];
+  for (int k1 = 0; k1 < A; ++k1) sc[k1 * PITCH + t] = v[k1];
 }
 
 // stage 1 for a forward transform whose inputs t + 16 a >= 8 A are zero (even A, the
 // padded half of a line of length 16 A): only v[0 .. A/2) are used
-template <int A, int S, typename R>
+template <int A, int S, typename R, int PITCH = kScrPitch>
 __device__ __forceinline__ void stage1_store_halfin(const Cx<R>* v, int t, const Cx<R>* __restrict__ tw, Cx<R>* sc) {
   Cx<R> x[A];
   DftHalfIn<A, S>::run(v, x);
@@ -64,26 +64,54 @@ __device__ __forceinline__ void stage1_store_halfin(const Cx<R>* v, int t, const
     x[k1] = cmul(x[k1], w);
   }
 #pragma unroll
-  for (int k1 = 0; k1 < A; ++k1) sc[k1 * kScrPitch + t] = x[k1];
+  for (int k1 = 0; k1 < A; ++k1) sc[k1 * PITCH + t] = x[k1];
 }
 
 // the same with this lane's twiddles already in registers (w[k1] = w_M^{-t k1}, k1 >= 1)
-template <int A, typename R>
+template <int A, typename R, int PITCH = kScrPitch>
 __device__ __forceinline__ void stage1_store_halfin_reg(const Cx<R>* v, int t, const Cx<R> (&w)[A], Cx<R>* sc) {
   Cx<R> x[A];
   DftHalfIn<A, -1>::run(v, x);
 #pragma unroll
   for (int k1 = 1; k1 < A; ++k1) x[k1] = cmul(x[k1], w[k1]);
 #pragma unroll
-  for (int k1 = 0; k1 < A; ++k1) sc[k1 * kScrPitch + t] = x[k1];
+  for (int k1 = 0; k1 < A; ++k1) sc[k1 * PITCH + t] = x[k1];
 }
 
-// stage 2 load: lane s (< A) gathers its 16 values scratch[s][t]
-template <typename R>
+// stage 2 load: lane s (< A) gathers its 16 values scratch[s][t]; with an even pitch (FP32
+// rows on 16-byte boundaries) as eight 16-byte loads
+template <typename R, int PITCH = kScrPitch>
 __device__ __forceinline__ void stage2_load(Cx<R> (&u)[16], int s, const Cx<R>* sc) {
+  if constexpr (sizeof(R) == 4 && PITCH % 2 == 0) {
+    const float4* rp = reinterpret_cast<const float4*>(sc + s * PITCH);
 #pragma unroll
-  for (int j = 0; j < 16; ++j) u[j] = sc[s * kScrPitch + j];
+    for (int j = 0; j < 8; ++j) {
+      const float4 v = rp[j];
+      u[2 * j] = cx<R>(v.x, v.y);
+      u[2 * j + 1] = cx<R>(v.z, v.w);
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) u[j] = sc[s * PITCH + j];
+  }
 }
+// the transposed store: lane s writes its 16 values to scratch row s
+template <typename R, int PITCH = kScrPitch>
+__device__ __forceinline__ void stage2_store(const Cx<R> (&u)[16], int s, Cx<R>* sc) {
+  if constexpr (sizeof(R) == 4 && PITCH % 2 == 0) {
+    float4* rp = reinterpret_cast<float4*>(sc + s * PITCH);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) rp[j] = make_float4(u[2 * j].x, u[2 * j].y, u[2 * j + 1].x, u[2 * j + 1].y);
+  } else {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) sc[s * PITCH + j] = u[j];
+  }
+}
+
+// line-scratch pitch (complex) of pass 2: 18 for FP32 where the extra bytes fit (rows on
+// 16-byte boundaries for the vector loads above, still conflict-free), else 17
+template <typename R>
+__host__ __device__ constexpr int p2_pitch(int A) { return (sizeof(R) == 4 && A <= 12) ? 18 : kScrPitch; }
 
 // Row-block staging of the x passes, xs[kx][r] (kRowsPerCta = 32 rows per kx): the rows
 // are paired into 16 granules (r, r + 1 with r even) and granule g of row kx sits at
@@ -252,7 +280,7 @@ __device__ __forceinline__ void store_plane(const Cx<R>* D, int DP, Cx<R>* P, in
 }
 
 // forward y transform of rows z < nz (input y < ny, output all My)
-template <typename R, int AY, int NT>
+template <typename R, int AY, int NT, int PITCH = kScrPitch>
 __device__ __forceinline__ void y_forward(Cx<R>* D, int DP, int nz, int ny, const Cx<R>* __restrict__ twy,
                                           Cx<R>* sc, int in_off = 0) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, t = lane & 15;
@@ -267,14 +295,14 @@ __device__ __forceinline__ void y_forward(Cx<R>* D, int DP, int nz, int ny, cons
       v[a] = (ok && y < ny) ? D[z * DP + in_off + y] : cx<R>(R(0), R(0));
     }
     if constexpr (AY % 2 == 0) {
-      stage1_store_halfin<AY, -1>(v, t, twy, sc);
+      stage1_store_halfin<AY, -1, R, PITCH>(v, t, twy, sc);
     } else {
-      stage1_store<AY, -1>(v, t, twy, sc);
+      stage1_store<AY, -1, R, PITCH>(v, t, twy, sc);
     }
     __syncwarp();
     Cx<R> u[16];
     if (t < AY) {
-      stage2_load(u, t, sc);
+      stage2_load<R, PITCH>(u, t, sc);
       Dft<16, -1>::run(u);
     }
     __syncwarp();
@@ -287,7 +315,7 @@ __device__ __forceinline__ void y_forward(Cx<R>* D, int DP, int nz, int ny, cons
 }
 
 // inverse y transform of rows z < nz (input all My, output y < ny)
-template <typename R, int AY, int NT>
+template <typename R, int AY, int NT, int PITCH = kScrPitch>
 __device__ __forceinline__ void y_inverse(Cx<R>* D, int DP, int nz, int ny, const Cx<R>* __restrict__ twy,
                                           Cx<R>* sc) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, t = lane & 15;
@@ -308,14 +336,14 @@ __device__ __forceinline__ void y_inverse(Cx<R>* D, int DP, int nz, int ny, cons
 #pragma unroll
       for (int k1 = 1; k1 < AY; ++k1) v[k1] = cmul(v[k1], conj(tw[k1]));
 #pragma unroll
-      for (int k1 = 0; k1 < AY; ++k1) sc[k1 * kScrPitch + t] = v[k1];
+      for (int k1 = 0; k1 < AY; ++k1) sc[k1 * PITCH + t] = v[k1];
     } else {
-      stage1_store<AY, 1>(v, t, twy, sc);
+      stage1_store<AY, 1, R, PITCH>(v, t, twy, sc);
     }
     __syncwarp();
     Cx<R> u[16];
     if (t < AY) {
-      stage2_load(u, t, sc);
+      stage2_load<R, PITCH>(u, t, sc);
       if constexpr (AY % 2 == 0) {
         Cx<R> o[8];
         DftHalfOut<16, 1>::run(u, o);   // only y = t + AY k2 < ny = 8 AY, i.e. k2 < 8
@@ -369,8 +397,10 @@ __device__ __forceinline__ void pass2_plane(const Geom& g, Cx<R>* P, int kx, con
   constexpr int LY = 16 * AY;
   constexpr int LZ = 16 * AZ;
   constexpr int AMAX = AY > AZ ? AY : AZ;
-  constexpr int SP = AMAX * kScrPitch;
+  constexpr int PITCH = p2_pitch<R>(AMAX);
+  constexpr int SP = AMAX * PITCH;
   constexpr int DP = LY + 1;
+  constexpr int NZ = 8 * AZ, NY = 8 * AY;   // the box edges (the padded edge M = 16 A is 2n)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int t = lane & 15, line = warp * 2 + (lane >> 4);
   Cx<R>* sc = scr + line * SP;
@@ -378,10 +408,10 @@ __device__ __forceinline__ void pass2_plane(const Geom& g, Cx<R>* P, int kx, con
   if (prefetched) {
     asm volatile("cp.async.wait_group 0;" ::: "memory");
   } else {
-    load_plane<NT>(D, DP, P, g.nz, g.ny);
+    load_plane<NT>(D, DP, P, NZ, NY);
   }
   __syncthreads();
-  y_forward<R, AY, NT>(D, DP, g.nz, g.ny, twy, sc, prefetched ? g.ny : 0);
+  y_forward<R, AY, NT, PITCH>(D, DP, NZ, NY, twy, sc, prefetched ? NY : 0);
   __syncthreads();
   // z forward, multiply, z inverse on columns ky (LY is a multiple of 16: uniform trips)
   const R* vrow = vhat + (size_t)kx * Hy * Hz;
@@ -399,16 +429,16 @@ __device__ __forceinline__ void pass2_plane(const Geom& g, Cx<R>* P, int kx, con
 #pragma unroll
     for (int a = 0; a < AIN; ++a) {
       const int z = t + 16 * a;
-      v[a] = (z < g.nz) ? D[z * DP + ky] : cx<R>(R(0), R(0));
+      v[a] = (z < NZ) ? D[z * DP + ky] : cx<R>(R(0), R(0));
     }
     if constexpr (AZ % 2 == 0) {
-      stage1_store_halfin_reg<AZ>(v, t, twf, sc);
+      stage1_store_halfin_reg<AZ, R, PITCH>(v, t, twf, sc);
     } else {
-      stage1_store<AZ, -1>(v, t, twz, sc);
+      stage1_store<AZ, -1, R, PITCH>(v, t, twz, sc);
     }
     __syncwarp();
     Cx<R> u[16];
-    if (t < AZ) stage2_load(u, t, sc);
+    if (t < AZ) stage2_load<R, PITCH>(u, t, sc);
     __syncwarp();
     if (t < AZ) {
       Dft<16, -1>::run(u);
@@ -434,21 +464,20 @@ __device__ __forceinline__ void pass2_plane(const Geom& g, Cx<R>* P, int kx, con
       }
       Dft<16, 1>::run(u);
       if constexpr (AZ % 2 == 0) {
-#pragma unroll
-        for (int j = 0; j < 16; ++j) sc[t * kScrPitch + j] = u[j];
+        stage2_store<R, PITCH>(u, t, sc);
       } else {
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
           Cx<R> w = twz[j * AZ + t];
           w.y = -w.y;
-          sc[t * kScrPitch + j] = cmul(u[j], w);
+          sc[t * PITCH + j] = cmul(u[j], w);
         }
       }
     }
     __syncwarp();
     Cx<R> r[AZ];
 #pragma unroll
-    for (int k1 = 0; k1 < AZ; ++k1) r[k1] = sc[k1 * kScrPitch + t];
+    for (int k1 = 0; k1 < AZ; ++k1) r[k1] = sc[k1 * PITCH + t];
     if constexpr (AZ % 2 == 0) {
       // the inverse twiddle w_M^{-j k1} (j the 16-point output index) taken after the
       // transpose, where lane t = j holds k1 = 0 .. AZ-1: the conjugates of the forward
@@ -464,16 +493,16 @@ __device__ __forceinline__ void pass2_plane(const Geom& g, Cx<R>* P, int kx, con
 #pragma unroll
       for (int a = 0; a < AZ; ++a) {
         const int z = t + 16 * a;
-        if (z < g.nz) D[z * DP + ky] = r[a];
+        if (z < NZ) D[z * DP + ky] = r[a];
       }
     }
     __syncwarp();
   }
   __syncthreads();
-  y_inverse<R, AY, NT>(D, DP, g.nz, g.ny, twy, sc);
+  y_inverse<R, AY, NT, PITCH>(D, DP, NZ, NY, twy, sc);
   __syncthreads();
-  if (Pnext) prefetch_plane_upper<R>(D, DP, Pnext, g.nz, g.ny, NT);
-  store_plane<NT>(D, DP, P, g.nz, g.ny);
+  if (Pnext) prefetch_plane_upper<R>(D, DP, Pnext, NZ, NY, NT);
+  store_plane<NT>(D, DP, P, NZ, NY);
   __syncthreads();
 }
 
@@ -485,7 +514,7 @@ __global__ void __launch_bounds__(NT, 1) k_pass2(Geom g, int nq, Cx<R>* __restri
                                                  const R* __restrict__ vhat, const float* __restrict__ vlanes,
                                                  R* gscratch) {
   constexpr int AMAX = AY > AZ ? AY : AZ;
-  constexpr int SP = AMAX * kScrPitch;
+  constexpr int SP = AMAX * p2_pitch<R>(AMAX);
   constexpr int DP = 16 * AY + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Cx<R>* scr = reinterpret_cast<Cx<R>*>(smem_raw);
@@ -499,7 +528,7 @@ __global__ void __launch_bounds__(NT, 1) k_pass2(Geom g, int nq, Cx<R>* __restri
   };
   // in shared memory the next plane is prefetched behind the current one (2 ny <= My + 1)
   const bool pipe = DSMEM;
-  if (pipe && (int)blockIdx.x < nwork) prefetch_plane_upper<R>(D, DP, plane_ptr(blockIdx.x), g.nz, g.ny, NT);
+  if (pipe && (int)blockIdx.x < nwork) prefetch_plane_upper<R>(D, DP, plane_ptr(blockIdx.x), 8 * AZ, 8 * AY, NT);
   for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
     const int kx = w % g.Hx;
     const int wn = w + (int)gridDim.x;

@@ -43,7 +43,7 @@ inline int pass2_threads(const Geom& g) {
   if (nt != 384 && nt != 512) return 256;
   if (nt == 384 && sizeof(R) != 4) return 256;
   const int A = g.Ay > g.Az ? g.Ay : g.Az;
-  const size_t sc = sizeof(Cx<R>) * (size_t)(nt / 16) * A * kScrPitch;
+  const size_t sc = sizeof(Cx<R>) * (size_t)(nt / 16) * A * p2_pitch<R>(A);
   const size_t pl = sizeof(Cx<R>) * (size_t)g.nz * (g.My + 1);
   return (sc + pl <= (size_t)max_dyn_smem()) ? nt : 256;
 }
@@ -59,7 +59,7 @@ inline auto pass2_kernel(int nt) {
 template <typename R>
 inline size_t pass2_scratch_smem(int AY, int AZ, int nt = kThreads) {
   const int A = AY > AZ ? AY : AZ;
-  return sizeof(Cx<R>) * (size_t)(nt / 16) * A * kScrPitch;
+  return sizeof(Cx<R>) * (size_t)(nt / 16) * A * p2_pitch<R>(A);
 }
 template <typename R>
 inline size_t pass2_plane_bytes(const Geom& g) {

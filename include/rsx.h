@@ -281,6 +281,15 @@ int rsx_eig_init(rsx_eig* eig, const float* psi0, void* stream);
 int rsx_eig_step(rsx_eig* eig, rsx_net* net, int jacobi_sweeps, double* theta_host, void* stream);
 int rsx_eig_orbitals(rsx_eig* eig, float* psi_out, void* stream);
 int rsx_eig_residual(rsx_eig* eig, float* r_out, void* stream);
+/* Energy of the current orbitals evaluated in FP64: the orbitals (FP32) are widened to
+ * double, H = -1/2 Lap_FD4 + V (times the mask) is applied in double, S = <Psi, Psi> and
+ * Hs = <Psi, H Psi> are summed in double and energy = trace(S^-1 Hs) (the Rayleigh-Ritz sum
+ * of the block, a variational upper bound on the sum of the lowest nband eigenvalues),
+ * written to energy_host.  Resolves energy differences far below the FP32 Ritz values'
+ * noise (used to measure convergence to 1e-6 Ha).  Synchronises the stream.
+ * Errors: RSX_EINVAL (before rsx_eig_init), RSX_EUNSUPPORTED (an exchange term is set),
+ * RSX_ENOMEM (2 nband n^3 doubles of workspace, allocated on the first call). */
+int rsx_eig_energy64(rsx_eig* eig, double* energy_host, void* stream);
 const char* rsx_eig_last_error(const rsx_eig* eig);
 int rsx_eig_destroy(rsx_eig* eig);
 /* Non-local exchange term added to H (Sec. 3.1): mode 0 none; 1 the ACE operator

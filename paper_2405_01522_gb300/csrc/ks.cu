@@ -849,6 +849,81 @@ size_t row_blocks(size_t N, int rows) { return std::max<size_t>(1, std::min<size
 
 }  // namespace
 
+namespace {
+
+// ---- FP64 energy of the current block (rsx_eig_energy64)
+__global__ void k_cast64(const float* __restrict__ x, size_t n, double* __restrict__ y) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    y[i] = (double)x[i];
+}
+
+// out = (-1/2 Lap_FD4 + V) f in FP64 (times the domain mask), f: [nb][n^3], zero values
+// outside the box; the stencil of k_ham_apply in double precision
+__global__ void k_ham_apply64(const double* __restrict__ f, int nb, int n, double inv12h2, const float* __restrict__ V,
+                              const float* __restrict__ mask, double* __restrict__ out) {
+  const int nn = n * n;
+  const size_t N = (size_t)nn * n, tot = N * nb;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < tot; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t b = i / N;
+    const int v = (int)(i - b * N);
+    const int z = v / nn, y = (v - z * nn) / n, x = v - z * nn - y * n;
+    const double* p = f + i;
+    const double c = *p;
+    auto g = [&](bool ok, int off) { return (ok ? p[off] : 0.0) - c; };
+    const double a1 = g(x > 0, -1) + g(x < n - 1, 1), a2 = g(x > 1, -2) + g(x < n - 2, 2);
+    const double b1 = g(y > 0, -n) + g(y < n - 1, n), b2 = g(y > 1, -2 * n) + g(y < n - 2, 2 * n);
+    const double c1 = g(z > 0, -nn) + g(z < n - 1, nn), c2 = g(z > 1, -2 * nn) + g(z < n - 2, 2 * nn);
+    const double lap = (16.0 * a1 - a2) + (16.0 * b1 - b2) + (16.0 * c1 - c2);
+    double r = -0.5 * lap * inv12h2 + (double)V[v] * c;
+    if (mask) r *= (double)mask[v];
+    out[i] = r;
+  }
+}
+
+// energy = trace(S^-1 Hs) = trace(L^-1 Hs L^-T), S = L L^T (k x k, FP64, one warp)
+__global__ void k_rr_trace(const double* __restrict__ S, const double* __restrict__ Hs, int k,
+                           double* __restrict__ out) {
+  __shared__ double L[32 * 32], W[32 * 32], T[32 * 32];
+  const int lane = threadIdx.x;
+  for (int i = lane; i < k * k; i += 32) {
+    L[i] = 0.0;
+    const int r = i / k, c = i - r * k;
+    W[i] = 0.5 * (Hs[r * k + c] + Hs[c * k + r]);
+  }
+  __syncwarp();
+  for (int j = 0; j < k; ++j) {
+    if (lane == 0) {
+      double d = S[j * k + j];
+      for (int p = 0; p < j; ++p) d -= L[j * k + p] * L[j * k + p];
+      L[j * k + j] = sqrt(d > 0.0 ? d : 1e-300);
+    }
+    __syncwarp();
+    for (int i = j + 1 + lane; i < k; i += 32) {
+      double a = 0.5 * (S[i * k + j] + S[j * k + i]);
+      for (int p = 0; p < j; ++p) a -= L[i * k + p] * L[j * k + p];
+      L[i * k + j] = a / L[j * k + j];
+    }
+    __syncwarp();
+  }
+  // T = L^-1 W (columns over lanes), then W = L^-1 T^T, trace of the result
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int c = lane; c < k; c += 32)
+      for (int i = 0; i < k; ++i) {
+        double a = pass == 0 ? W[i * k + c] : T[c * k + i];
+        for (int p = 0; p < i; ++p) a -= L[i * k + p] * (pass == 0 ? T[p * k + c] : W[p * k + c]);
+        (pass == 0 ? T : W)[i * k + c] = a / L[i * k + i];
+      }
+    __syncwarp();
+  }
+  if (lane == 0) {
+    double tr = 0.0;
+    for (int i = 0; i < k; ++i) tr += W[i * k + i];
+    *out = tr;
+  }
+}
+
+}  // namespace
+
 struct rsx_eig {
   rsx_ctx* ctx = nullptr;        // owns the Gram / combine workspace
   int n = 0, k = 0;
@@ -873,6 +948,7 @@ struct rsx_eig {
   rsx_ctx* xctx = nullptr;
   float* xbuf = nullptr;         // [4k][N] exact-exchange output
   const float* mask = nullptr;   // spherical domain (rsx_eig_set_mask), caller's [N] 0/1
+  double* e64 = nullptr;         // rsx_eig_energy64: Psi and H Psi in FP64 [2k][N] + small matrices
   char err[256] = {0};
 };
 
@@ -1164,11 +1240,48 @@ int rsx_eig_residual(rsx_eig* e, float* r_out, void* stream) {
                "residual");
 }
 
+// FP64 energy of the current orbitals (see rsx.h)
+int rsx_eig_energy64(rsx_eig* e, double* energy_host, void* stream) {
+  if (!e || !energy_host) return RSX_EINVAL;
+  if (!e->started) return efail(e, RSX_EINVAL, "energy64: call rsx_eig_init first");
+  if (e->xmode != 0) return efail(e, RSX_EUNSUPPORTED, "energy64: H with an exchange term is not covered");
+  cudaStream_t s = (cudaStream_t)stream;
+  rsx_ctx* c = e->ctx;
+  const int k = e->k;
+  const size_t N = (size_t)e->n * e->n * e->n;
+  if (!e->e64 && cudaMalloc(&e->e64, (2 * (size_t)k * N + 2 * 4096 + 8) * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    e->e64 = nullptr;
+    return efail(e, RSX_ENOMEM, "energy64: cannot allocate the FP64 workspace");
+  }
+  double* P = e->e64;
+  double* HP = P + (size_t)k * N;
+  double* Sm = HP + (size_t)k * N;
+  double* Hm = Sm + 4096;
+  double* res = Hm + 4096;
+  const int nblk = 2 * c->nsm;
+  int rc = grow(c, (void**)&c->dsm, &c->dsm_bytes, sizeof(double) * ((size_t)nblk * 4096 + 3 * 4096), "small FP64");
+  if (rc) return efail(e, rc, rsx_last_error(c));
+  k_cast64<<<4 * c->nsm, 256, 0, s>>>(e->B, (size_t)k * N, P);
+  k_ham_apply64<<<8 * c->nsm, 256, 0, s>>>(P, k, e->n, 1.0 / (12.0 * e->h * e->h), e->V, e->mask, HP);
+  rc = ecuda(e, cudaGetLastError(), "energy64 H");
+  const double h3 = e->h * e->h * e->h;
+  if (!rc) rc = ecuda(e, launch_gram<double>(P, k, P, k, N, c->dsm, nblk, s), "energy64 S");
+  if (!rc) rc = ecuda(e, launch_gram_reduce<double>(c->dsm, nblk, k, k, h3, false, Sm, (double*)nullptr, s), "energy64 S");
+  if (!rc) rc = ecuda(e, launch_gram<double>(P, k, HP, k, N, c->dsm, nblk, s), "energy64 H");
+  if (!rc) rc = ecuda(e, launch_gram_reduce<double>(c->dsm, nblk, k, k, h3, false, Hm, (double*)nullptr, s), "energy64 H");
+  if (rc) return rc;
+  k_rr_trace<<<1, 32, 0, s>>>(Sm, Hm, k, res);
+  rc = ecuda(e, cudaMemcpyAsync(energy_host, res, sizeof(double), cudaMemcpyDeviceToHost, s), "energy64 copy");
+  if (!rc) rc = ecuda(e, cudaStreamSynchronize(s), "energy64 sync");
+  return rc;
+}
+
 const char* rsx_eig_last_error(const rsx_eig* e) { return e ? e->err : "null eigensolver"; }
 
 int rsx_eig_destroy(rsx_eig* e) {
   if (!e) return RSX_OK;
-  void* bufs[] = {e->B, e->HB, e->R, e->tmp, e->xnet, e->sm, e->qt, e->qp, e->xbuf};
+  void* bufs[] = {e->B, e->HB, e->R, e->tmp, e->xnet, e->sm, e->qt, e->qp, e->xbuf, e->e64};
   for (void* p : bufs)
     if (p) cudaFree(p);
   rsx_destroy(e->ctx);

@@ -49,6 +49,7 @@ SIGNATURES = {
     "rsx_eig_orbitals": [_P, _P, _P],
     "rsx_eig_residual": [_P, _P, _P],
     "rsx_eig_last_error": [_P],
+    "rsx_eig_energy64": [_P, ctypes.POINTER(_D), _P],
     "rsx_eig_destroy": [_P],
     "rsx_eig_set_exchange": [_P, _P, _P, _I, _I],
     "rsx_eig_set_mask": [_P, _P],
@@ -512,6 +513,12 @@ class Eigensolver:
         self._check(self.lib.rsx_eig_step(self.handle, net.handle if net is not None else None, int(sweeps), th,
                                           _stream(stream)))
         return list(th)
+
+    def energy64(self, stream=None):
+        """FP64 Rayleigh-Ritz energy trace(S^-1 <Psi, H Psi>) of the current orbitals."""
+        e = ctypes.c_double()
+        self._check(self.lib.rsx_eig_energy64(self.handle, ctypes.byref(e), _stream(stream)))
+        return e.value
 
     def set_exchange(self, src=None, mode=0, ctx=None):
         """Exchange term of H: mode 0 none, 1 ACE with projectors src, 2 exact Vx[src] via ctx."""

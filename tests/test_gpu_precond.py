@@ -88,3 +88,69 @@ def test_learned_preconditioner_pipeline_small():
     assert np.isfinite(losses).all() and losses[-1] < losses[0]
     learned = precond.solve(V, h, psi0, nb, net=net, tol=1e-7, vscale=vscale)
     assert abs(learned["energy"] - plain["energy"]) < 1e-5
+
+
+def test_energy64_is_the_rayleigh_ritz_trace_of_the_dense_hamiltonian():
+    """rsx_eig_energy64 against the oracle: trace(S^-1 Psi^T H Psi) with the dense FD4
+    Hamiltonian and the same FP32 orbitals in FP64 (before convergence, where the block is
+    not orthonormal in any precision), and above the sum of the lowest dense eigenvalues by
+    less than 1e-9 of it once converged (variational)."""
+    need_gpu()
+    n, h, nb = 12, 0.5, 4
+    V = inputs.model_potential(n=n, h=h, natoms=2, Z=2.0, rc=0.8, radius=1.0, seed=1)
+    Hd = oe.hamiltonian_dense(V, h)
+    psi0 = inputs.starting_orbitals(n=n, h=h, nband=nb, radius=1.0, seed=2)
+    es = rsx.Eigensolver(torch.from_numpy(V).float().cuda(), h, nb)
+    es.init(torch.from_numpy(psi0).float().cuda())
+    es.step()
+    P = es.orbitals().double().cpu().numpy().reshape(nb, -1)
+    S, Hs = h ** 3 * (P @ P.T), h ** 3 * (P @ Hd @ P.T)
+    e_ref = np.trace(np.linalg.solve(S, Hs))
+    assert abs(es.energy64() - e_ref) <= 1e-12 * abs(e_ref)
+    for _ in range(300):
+        es.step()
+    w = np.linalg.eigvalsh(Hd)[:nb]
+    e = es.energy64()
+    assert -1e-12 * abs(w.sum()) <= e - w.sum() <= 1e-9 * abs(w.sum())
+    es.close()
+
+
+def test_learned_vs_plain_on_an_unseen_system(record_property):
+    """The learned preconditioner's gain, measured: train on pairs from plain runs on two
+    systems (48^3, 8 bands), then on a third system run the plain and the learned solver
+    with FP64 energies after every step against an independent plain reference converged
+    to |dE| < 1e-10 Ha.  Both must come (and stay) within 1e-6 Ha of it and end within
+    1e-6 Ha of each other; the iterations and solver times to 1e-6 Ha are recorded, and
+    the learned run must need no more iterations than the plain one."""
+    need_gpu()
+    n, h, nb = 48, 0.25, 8
+    pots = [torch.from_numpy(inputs.model_potential(n=n, h=h, natoms=3, Z=4.0, rc=0.6, radius=2.0, seed=s)).float().cuda()
+            for s in (51, 52, 53)]
+    vscale = float(1.0 / max(float(v.abs().max()) for v in pots))
+    psi0 = [torch.from_numpy(inputs.starting_orbitals(n=n, h=h, nband=nb, radius=2.0, seed=60 + s)).float().cuda()
+            for s in range(3)]
+    Xs, Ys = [], []
+    for i in range(2):
+        res = precond.solve(pots[i], h, psi0[i], nb, tol=1e-7, vscale=vscale, record_every=2, max_iter=400)
+        X, Y = precond.make_pairs(pots[i], h, res, vscale, crop=24, crops_per_sample=6, seed=i)
+        Xs.append(X)
+        Ys.append(Y)
+    X, Y = torch.cat(Xs).contiguous(), torch.cat(Ys).contiguous()
+    net = rsx.Net(precond.init_params(seed=0))
+    losses = precond.train(net, X, Y, epochs=4, batch=32, lr=1e-3, border=3)
+    assert losses[-1] < losses[0]
+    ref = precond.solve(pots[2], h, psi0[2], nb, tol=1e-10, vscale=vscale, max_iter=3000, energy64=True)
+    plain = precond.solve(pots[2], h, psi0[2], nb, tol=1e-9, vscale=vscale, max_iter=1500, energy64=True)
+    learned = precond.solve(pots[2], h, psi0[2], nb, net=net, tol=1e-9, vscale=vscale, max_iter=1500,
+                            energy64=True)
+    net.close()
+    ip, tp = precond.time_to_target(plain, ref["energy"])
+    il, tl = precond.time_to_target(learned, ref["energy"])
+    record_property("plain_iters_to_1e-6", ip)
+    record_property("learned_iters_to_1e-6", il)
+    record_property("plain_s_to_1e-6", tp)
+    record_property("learned_s_to_1e-6", tl)
+    print(f"learned vs plain to 1e-6 Ha: iterations {il} vs {ip}, solver time {tl} vs {tp} s", flush=True)
+    assert ip is not None and il is not None, (ip, il)
+    assert abs(learned["energy"] - plain["energy"]) < 1e-6
+    assert il <= ip, (il, ip, tl, tp)

@@ -542,10 +542,146 @@ cudaError_t launch_ghat(const Geom& g, double h, double scale, const double* cos
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------------
+// Streaming FP32 Gram partials (N % 4 == 0, 16-byte aligned rows; used for at most two
+// 16 x 16 output groups): the output is cut into 16 x 16 groups (grid.y); a CTA streams 256-point chunks of its 16 X rows, 16 Y rows (and
+// the weight row) through a 3-stage cp.async ring, so that two chunks are in flight while
+// one is multiplied.  Thread (ti = warp & 3, tj = lane >> 3, split = lane & 7 + 8 (warp >> 2))
+// owns the 4 x 4 outputs (4 ti + p, 4 tj + q) and the 4-point quads split, split + 16, ...
+// of each chunk; the eight lanes of a quarter-warp read eight consecutive quads of the
+// same rows (16-byte loads, no bank conflicts).  Per chunk the products are summed in FP32
+// (16 points per output and thread), the chunk sums are carried across chunks as
+// double-float pairs (TwoSum), and the 16 splits are added in FP64 at the end.
+constexpr int kGsChunk = 256, kGsStages = 3, kGsThreads = 256, kGsSlots = 33;
+
+__device__ __forceinline__ void gs_cp16(float* dst, const float* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+
+__global__ void __launch_bounds__(kGsThreads) k_gram_stream(const float* __restrict__ X, int na,
+                                                            const float* __restrict__ Y, int nb,
+                                                            const float* __restrict__ w, size_t N, int ngb,
+                                                            double* __restrict__ part) {
+  extern __shared__ __align__(16) float gs[];   // [stage][slot][kGsChunk]: X 0..15, Y 16..31, w 32
+  const int gx = blockIdx.y / ngb, gy = blockIdx.y - gx * ngb;
+  const int a_lo = 16 * gx, b_lo = 16 * gy;
+  const int nra = min(16, na - a_lo), nrb = min(16, nb - b_lo);
+  const bool shared_rows = X == Y && a_lo == b_lo && w == nullptr;   // the Y rows are the X rows
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ti = warp & 3, tj = lane >> 3, split = (lane & 7) + 8 * (warp >> 2);
+  const int a0 = 4 * ti, b0 = 4 * tj;
+  const size_t nchunk = (N + kGsChunk - 1) / kGsChunk;
+  const long long mine = blockIdx.x < nchunk ? (long long)((nchunk - 1 - blockIdx.x) / gridDim.x) + 1 : 0;
+  auto issue = [&](long long i) {
+    const size_t r0 = (blockIdx.x + (size_t)i * gridDim.x) * kGsChunk;
+    const int q4 = (int)min((size_t)kGsChunk, N - r0) >> 2;
+    float* base = gs + (size_t)(i % kGsStages) * kGsSlots * kGsChunk;
+    for (int e = threadIdx.x; e < kGsSlots * (kGsChunk / 4); e += kGsThreads) {
+      const int slot = e / (kGsChunk / 4), q = e - slot * (kGsChunk / 4);
+      if (q >= q4) continue;
+      const float* src = nullptr;
+      if (slot < 16) {
+        if (slot < nra) src = X + (size_t)(a_lo + slot) * N;
+      } else if (slot < 32) {
+        if (!shared_rows && slot - 16 < nrb) src = Y + (size_t)(b_lo + slot - 16) * N;
+      } else if (w) {
+        src = w;
+      }
+      if (src) gs_cp16(base + (size_t)slot * kGsChunk + 4 * q, src + r0 + 4 * q);
+    }
+  };
+  float ah[16], al[16];
+#pragma unroll
+  for (int o = 0; o < 16; ++o) ah[o] = al[o] = 0.f;
+#pragma unroll
+  for (int i = 0; i < kGsStages - 1; ++i) {
+    if (i < mine) issue(i);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  }
+  for (long long i = 0; i < mine; ++i) {
+    if (i + kGsStages - 1 < mine) issue(i + kGsStages - 1);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    asm volatile("cp.async.wait_group %0;" ::"n"(kGsStages - 1) : "memory");
+    __syncthreads();
+    const size_t r0 = (blockIdx.x + (size_t)i * gridDim.x) * kGsChunk;
+    const int q4 = (int)min((size_t)kGsChunk, N - r0) >> 2;
+    const float* xs = gs + (size_t)(i % kGsStages) * kGsSlots * kGsChunk;
+    const float* ys = shared_rows ? xs : xs + 16 * kGsChunk;
+    const float* ws = xs + 32 * kGsChunk;
+    float sacc[16];
+#pragma unroll
+    for (int o = 0; o < 16; ++o) sacc[o] = 0.f;
+    for (int q = split; q < q4; q += 16) {
+      float4 xv[4], yv[4];
+#pragma unroll
+      for (int p = 0; p < 4; ++p) xv[p] = *reinterpret_cast<const float4*>(xs + (a0 + p) * kGsChunk + 4 * q);
+#pragma unroll
+      for (int p = 0; p < 4; ++p) yv[p] = *reinterpret_cast<const float4*>(ys + (b0 + p) * kGsChunk + 4 * q);
+      if (w) {
+        const float4 wv = *reinterpret_cast<const float4*>(ws + 4 * q);
+#pragma unroll
+        for (int p = 0; p < 4; ++p) yv[p] = make_float4(yv[p].x * wv.x, yv[p].y * wv.y, yv[p].z * wv.z, yv[p].w * wv.w);
+      }
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          float acc = sacc[p * 4 + r];
+          acc = fmaf(xv[p].x, yv[r].x, acc);
+          acc = fmaf(xv[p].y, yv[r].y, acc);
+          acc = fmaf(xv[p].z, yv[r].z, acc);
+          acc = fmaf(xv[p].w, yv[r].w, acc);
+          sacc[p * 4 + r] = acc;
+        }
+    }
+#pragma unroll
+    for (int o = 0; o < 16; ++o) {   // TwoSum: (ah, al) += sacc
+      const float a = ah[o], b = sacc[o];
+      const float sm = a + b, bp = sm - a;
+      al[o] += (a - (sm - bp)) + (b - bp);
+      ah[o] = sm;
+    }
+    __syncthreads();   // this stage is refilled by the next issue
+  }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  double acc[16];
+#pragma unroll
+  for (int o = 0; o < 16; ++o) {
+    acc[o] = (double)ah[o] + (double)al[o];
+    for (int m = 1; m < 8; m <<= 1) acc[o] += __shfl_xor_sync(0xffffffffu, acc[o], m);
+  }
+  __syncthreads();
+  double* red = reinterpret_cast<double*>(gs);   // [2][16][16]
+  if ((lane & 7) == 0) {
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) red[((warp >> 2) * 16 + a0 + p) * 16 + b0 + r] = acc[p * 4 + r];
+  }
+  __syncthreads();
+  const int a = threadIdx.x >> 4, b = threadIdx.x & 15;
+  if (a < nra && b < nrb)
+    part[(size_t)blockIdx.x * na * nb + (size_t)(a_lo + a) * nb + (b_lo + b)] = red[a * 16 + b] + red[256 + a * 16 + b];
+}
+
 template <typename R>
 cudaError_t launch_gram(const R* X, int na, const R* Y, int nb, size_t N, double* part, int nblk,
                         cudaStream_t s, const R* w) {
   if (na * nb > 16 * kGramThreads) return cudaErrorInvalidValue;
+  if constexpr (sizeof(R) == 4) {
+    auto al16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
+    const int nga = (na + 15) / 16, ngb = (nb + 15) / 16;
+    // each 16 x 16 group streams its own rows: worth it for one or two groups (the ACE
+    // shapes 16 x 16, 16 x 32); wider bases keep the staged kernel, which reads every row once
+    if (N % 4 == 0 && al16(X) && al16(Y) && (w == nullptr || al16(w)) && nga * ngb <= 2) {
+      const size_t smem = sizeof(float) * (size_t)kGsStages * kGsSlots * kGsChunk;
+      cudaError_t e = cudaFuncSetAttribute(k_gram_stream, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      k_gram_stream<<<dim3(nblk, nga * ngb), kGsThreads, smem, s>>>(X, na, Y, nb, w, N, ngb, part);
+      return cudaGetLastError();
+    }
+  }
   const bool sym = X == Y && na == nb && w == nullptr;
   const int ta = (na + 3) / 4, tb = (nb + 3) / 4;
   const int tiles = sym ? ta * (ta + 1) / 2 : ta * tb;

@@ -163,6 +163,16 @@ int rsx_exchange_apply_noalloc(rsx_ctx* ctx, const void* phi, int nocc, const vo
  * Errors: RSX_EINVAL, RSX_ENOMEM; RSX_ENOTPD deferred to rsx_sync_status. */
 int rsx_ace_build(rsx_ctx* ctx, const void* phi, int nocc, void* xi, double* M_out, void* stream);
 
+/* The two steps of the ACE build after W (Eqs. 11-12), for callers that assemble W and M
+ * themselves (e.g. ranks that each hold a block of W's rows, see the sharded driver):
+ * rsx_gram: C[i][j] = h^3 <a_i, b_j> (device double [na][nb], na * nb <= 4096; FP64
+ *   accumulation of FP32 or FP64 products).
+ * rsx_ace_factor: M (device double [nocc][nocc]) is symmetrised in place, -M = L L^T by
+ *   the FP64 Cholesky, xi = L^-1 W ([nocc][N]; xi may equal W).  RSX_ENOTPD deferred to
+ *   rsx_sync_status.  Errors: RSX_EINVAL. */
+int rsx_gram(rsx_ctx* ctx, const void* a, int na, const void* b, int nb, double* C, void* stream);
+int rsx_ace_factor(rsx_ctx* ctx, double* M, const void* W, int nocc, void* xi, void* stream);
+
 /* ACE action of Eq. 13: out_p = -sum_k xi_k <xi_k, psi_p>.  nxi * npsi <= 4096.
  * xi: [nxi][N], psi: [npsi][N], out: [npsi][N]; out may equal psi (in place), must not alias xi.
  * Errors: RSX_EINVAL. */

@@ -390,6 +390,31 @@ int poisson(rsx_ctx* c, const void* rho, void* V, cudaStream_t s) {
 }  // namespace
 }  // namespace rsx
 
+namespace rsx {
+namespace {
+template <typename R>
+int ace_factor(rsx_ctx* c, double* M, const void* W, int nocc, void* xi, cudaStream_t s) {
+  const size_t N = c->g.N();
+  int rc = grow(c, (void**)&c->dsm, &c->dsm_bytes, sizeof(double) * ((size_t)2 * c->nsm * 4096 + 3 * 4096), "small FP64");
+  if (rc) return rc;
+  rc = grow(c, &c->smallr, &c->smallr_bytes, sizeof(R) * 4096 * 2, "small coefficients");
+  if (rc) return rc;
+  double* Linv = c->dsm + (size_t)2 * c->nsm * 4096 + 4096;
+  R* linv_r = (R*)c->smallr;
+  {
+    ProfScope ps(c, kKChol, s);
+    rc = check_cuda(c,
+                    launch_chol_linv(M, nocc, Linv, sizeof(R) == 4 ? (float*)linv_r : nullptr,
+                                     sizeof(R) == 8 ? (double*)linv_r : nullptr, c->status, s),
+                    "cholesky");
+  }
+  if (rc) return rc;
+  ProfScope ps(c, kKCombine, s);
+  return check_cuda(c, launch_combine<R>(linv_r, nocc, nocc, (const R*)W, N, (R*)xi, 4 * c->nsm, s), "xi = L^-1 W");
+}
+}  // namespace
+}  // namespace rsx
+
 extern "C" {
 
 int rsx_create(rsx_ctx** out, int nz, int ny, int nx, double h, int precision, int device) {
@@ -519,6 +544,40 @@ int rsx_ace_apply(rsx_ctx* c, const void* xi, int nxi, const void* psi, int npsi
   cudaStream_t s = (cudaStream_t)stream;
   return c->precision == RSX_FP32 ? ace_apply<float>(c, xi, nxi, psi, npsi, out, s)
                                   : ace_apply<double>(c, xi, nxi, psi, npsi, out, s);
+}
+
+int rsx_gram(rsx_ctx* c, const void* a, int na, const void* b, int nb, double* C, void* stream) {
+  RSX_PREP(c);
+  if (!a || !b || !C || na < 1 || nb < 1 || na * nb > 4096) return set_error(c, RSX_EINVAL, "bad Gram arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t N = c->g.N();
+  const int nblk = 2 * c->nsm;
+  int rc = grow(c, (void**)&c->dsm, &c->dsm_bytes, sizeof(double) * ((size_t)nblk * 4096 + 3 * 4096), "small FP64");
+  if (rc) return rc;
+  const double h3 = c->h * c->h * c->h;
+  {
+    ProfScope ps(c, kKGram, s);
+    rc = check_cuda(c, c->precision == RSX_FP32
+                           ? launch_gram<float>((const float*)a, na, (const float*)b, nb, N, c->dsm, nblk, s)
+                           : launch_gram<double>((const double*)a, na, (const double*)b, nb, N, c->dsm, nblk, s),
+                    "gram");
+  }
+  if (rc) return rc;
+  ProfScope ps(c, kKGramReduce, s);
+  return check_cuda(c, c->precision == RSX_FP32
+                           ? launch_gram_reduce<float>(c->dsm, nblk, na, nb, h3, false, C, (float*)nullptr, s)
+                           : launch_gram_reduce<double>(c->dsm, nblk, na, nb, h3, false, C, (double*)nullptr, s),
+                    "gram reduce");
+}
+
+
+int rsx_ace_factor(rsx_ctx* c, double* M, const void* W, int nocc, void* xi, void* stream) {
+  RSX_PREP(c);
+  if (!M || !W || !xi || nocc < 1 || nocc > 64) return set_error(c, RSX_EINVAL, "bad ACE factor arguments");
+  const size_t bytes = (size_t)nocc * c->g.N() * c->elem_size();
+  if (xi != W && overlaps(xi, bytes, W, bytes)) return set_error(c, RSX_EINVAL, "xi partially aliases W");
+  cudaStream_t s = (cudaStream_t)stream;
+  return c->precision == RSX_FP32 ? ace_factor<float>(c, M, W, nocc, xi, s) : ace_factor<double>(c, M, W, nocc, xi, s);
 }
 
 int rsx_set_wait_limit(rsx_ctx* c, long long spins) {

@@ -33,6 +33,8 @@ SIGNATURES = {
     "rsx_poisson": [_P, _P, _P, _P],
     "rsx_ace_build": [_P, _P, _I, _P, _P, _P],
     "rsx_ace_apply": [_P, _P, _I, _P, _I, _P, _P],
+    "rsx_gram": [_P, _P, _I, _P, _I, _P, _P],
+    "rsx_ace_factor": [_P, _P, _P, _I, _P, _P],
     "rsx_casida_K": [_P, _P, _I, _P, _I, _P, _P],
     "rsx_casida_Kd": [_P, _P, _I, _P, _I, _P, _P],
     "rsx_casida_K_uhf": [_P, _P, _I, _P, _I, _P, _I, _P, _I, _P, _P],
@@ -239,6 +241,20 @@ class Context:
         nocc = self._orb(phi, "phi")
         xi = self._new(nocc) if xi is None else xi
         self._check(self.lib.rsx_ace_build(self.handle, _ptr(phi), nocc, _ptr(xi), _ptr(M), _stream(stream)))
+        return xi
+
+    def gram(self, a, b, C=None, stream=None):
+        """C[i][j] = h^3 <a_i, b_j> (FP64)."""
+        na, nb = self._orb(a, "a"), self._orb(b, "b")
+        C = torch.empty((na, nb), dtype=torch.float64, device=self.device) if C is None else C
+        self._check(self.lib.rsx_gram(self.handle, _ptr(a), na, _ptr(b), nb, _ptr(C), _stream(stream)))
+        return C
+
+    def ace_factor(self, M, W, xi=None, stream=None):
+        """Symmetrise M in place, -M = L L^T (FP64), xi = L^-1 W (Eqs. 11-12 after W)."""
+        nocc = self._orb(W, "W")
+        xi = self._new(nocc) if xi is None else xi
+        self._check(self.lib.rsx_ace_factor(self.handle, _ptr(M), _ptr(W), nocc, _ptr(xi), _stream(stream)))
         return xi
 
     def ace_apply(self, xi, psi, out=None, stream=None):

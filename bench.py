@@ -946,6 +946,7 @@ def main():
     ap.add_argument("--precond-epochs", type=int, default=4)
     ap.add_argument("--batch-mols", type=int, default=64)
     ap.add_argument("--casida-only", action="store_true", help="only the Casida section (profiling captures)")
+    ap.add_argument("--batch-only", action="store_true", help="only the uneven-batch section (profiling captures)")
     ap.add_argument("--casida-edge", type=int, default=80, help="box edge of the Casida case")
     ap.add_argument("--nocc", type=int, default=16, help="smaller cases for profiling captures only")
     ap.add_argument("--npsi", type=int, default=32, help="smaller cases for profiling captures only")
@@ -972,6 +973,15 @@ def main():
         dev = torch.device("cuda", local_rank)
         torch.cuda.set_device(dev)
         print(json.dumps({"scf": scf_bench(args, dev)}), flush=True)
+    elif args.batch_only:
+        dev = torch.device("cuda", local_rank)
+        torch.cuda.set_device(dev)
+        peaks = {}
+        try:
+            peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        except Exception:
+            pass
+        print(json.dumps({"batch": batch_bench(args, dev, local_rank, peaks)}), flush=True)
     elif args.casida_only:
         dev = torch.device("cuda", local_rank)
         torch.cuda.set_device(dev)

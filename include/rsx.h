@@ -252,16 +252,19 @@ int rsx_casida_oscillator(rsx_ctx* ctx, const double* omega, const double* X, in
 int rsx_strength_function(rsx_ctx* ctx, const double* omega, const double* f, int nroots, double gamma,
                           const double* grid, int ngrid, double* S, void* stream);
 
-/* ---- Uneven batch of independent molecules (one persistent launch per FFT pass under a
- * captured CUDA graph).  For every molecule m (cubic box of edge edges[m] in
- * {48, 64, 80, 96, 112}, spacing h, nocc[m] <= 32 orbitals, FP32):
+/* ---- Uneven batch of independent molecules (under one captured CUDA graph).  For every
+ * molecule m (cubic box of edge edges[m] in {48, 64, 80, 96, 112}, spacing h,
+ * nocc[m] <= 32 orbitals, FP32):
  *   W_m  = Vx[phi_m] phi_m   (Eq. 2 with psi = phi; nocc(nocc+1)/2 pair solves)
  *   xi_m = ACE projectors of Eqs. 11-12 (M_m, -M_m = L L^T in FP64, xi_m = L^-1 W_m).
- * rsx_batch_create plans the work queues (largest molecules first), builds the kernel
- * tables of every distinct edge and allocates all pair intermediates.  rsx_batch_bind
- * takes host arrays of nmol device pointers (phi[m]: [nocc][edge^3], W[m], xi[m] same
- * shape, not aliasing) and may be called again with new arrays.  rsx_batch_run records
- * the launches into a CUDA graph on its first call and replays the graph afterwards.
+ * The molecules are grouped by edge; each FFT pass runs as one launch per edge over all
+ * pairs of that edge's molecules (device lists of each pair's orbitals and each output's
+ * orbital set), then the ACE Gram and L^-1 W per molecule and one FP64 Cholesky kernel for
+ * all.  rsx_batch_create builds the kernel tables of every distinct edge and allocates
+ * all pair intermediates.  rsx_batch_bind takes host arrays of nmol device pointers
+ * (phi[m]: [nocc][edge^3], W[m], xi[m] same shape, not aliasing) and may be called again
+ * with new arrays.  rsx_batch_run records the launches into a CUDA graph on its first
+ * call after a bind and replays the graph afterwards.
  * rsx_batch_sync_status synchronises and reports deferred errors (RSX_ENOTPD).
  * Errors: RSX_EINVAL, RSX_EUNSUPPORTED (edge), RSX_ENOMEM, RSX_ECUDA. */
 typedef struct rsx_batch rsx_batch;

@@ -852,7 +852,7 @@ __global__ void __launch_bounds__(kThreads) k_pass3(Geom g, PairMap<R> pm, int q
   b /= nyb;
   const int z = b % g.nz;
   const int pl = b / g.nz;
-  pass3_item<R, AX>(g, pm, q0, p0 + pl, z, yblk, pot, inter, twx, out + (size_t)pl * g.N(), smem_raw);
+  pass3_item<R, AX>(g, pm, q0, p0 + pl, z, yblk, pot, inter, twx, pm.out_row(p0 + pl, out, pl), smem_raw);
 }
 
 }  // namespace rsx

@@ -22,7 +22,18 @@ constexpr int kRowsPerCta = 32;       // rows (y) per CTA in the x passes
 //         output p (an element of B) accumulates pairs q = p * na + a, partner A[a].
 //   SYM:  unique pairs a <= b of one set A (upper triangle, row-major);
 //         output p accumulates every pair containing p, partner the other orbital.
-enum PairMode { kProd = 0, kSym = 1 };
+//   LIST: pairs and outputs of several independent orbital sets (the uneven batch):
+//         pair q has density plist[2q] * plist[2q + 1]; output p is orbital i of a set of
+//         nocc orbitals phi whose symmetric pairs start at q0 (SYM order within the set),
+//         accumulates -sum_e phi_e V[phi_i phi_e] and is written to olist[p].out.
+enum PairMode { kProd = 0, kSym = 1, kList = 2 };
+
+template <typename R>
+struct OutRef {
+  const R* phi;   // the output's orbital set [nocc][N]
+  R* out;         // the output array [N]
+  int nocc, i, q0, pad;
+};
 
 template <typename R>
 struct PairMap {
@@ -31,30 +42,44 @@ struct PairMap {
   const R* B;
   int na, nb;
   size_t N;  // points per orbital
+  const R* const* plist = nullptr;   // LIST: two orbital pointers per pair
+  const OutRef<R>* olist = nullptr;  // LIST: one entry per output
 
-  __device__ __forceinline__ int npairs() const { return mode == kProd ? na * nb : na * (na + 1) / 2; }
   __device__ __forceinline__ void pair(int q, const R*& f1, const R*& f2) const {
     if (mode == kProd) {
       const int b = q / na, a = q - b * na;
       f1 = A + (size_t)a * N;
       f2 = B + (size_t)b * N;
-    } else {
+    } else if (mode == kSym) {
       int i = 0, rem = q;
       while (rem >= na - i) { rem -= na - i; ++i; }
       f1 = A + (size_t)i * N;
       f2 = A + (size_t)(i + rem) * N;
+    } else {
+      f1 = plist[2 * q];
+      f2 = plist[2 * q + 1];
     }
   }
-  __device__ __forceinline__ int nentries(int /*p*/) const { return na; }
+  __device__ __forceinline__ int nentries(int p) const { return mode == kList ? olist[p].nocc : na; }
   // entry e of output p: pair index and the orbital multiplied into the accumulator
   __device__ __forceinline__ void entry(int p, int e, int& q, const R*& partner) const {
     if (mode == kProd) {
       q = p * na + e;
-    } else {
+      partner = A + (size_t)e * N;
+    } else if (mode == kSym) {
       const int i = p < e ? p : e, j = p < e ? e : p;
       q = i * na - i * (i - 1) / 2 + (j - i);
+      partner = A + (size_t)e * N;
+    } else {
+      const OutRef<R> o = olist[p];
+      const int i = o.i < e ? o.i : e, j = o.i < e ? e : o.i;
+      q = o.q0 + i * o.nocc - i * (i - 1) / 2 + (j - i);
+      partner = o.phi + (size_t)e * N;
     }
-    partner = A + (size_t)e * N;
+  }
+  // the array output p (local index pl of a launch starting at out) is written to
+  __device__ __forceinline__ R* out_row(int p, R* out, int pl) const {
+    return mode == kList ? olist[p].out : out + (size_t)pl * N;
   }
 };
 

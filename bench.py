@@ -129,9 +129,10 @@ def aggregate_rate(world, units_per_step, steps, ms_max):
 DFT_FLOPS = {1: 0, 2: 4, 3: 16, 4: 16, 5: 52, 6: 44, 7: 102, 8: 60, 10: 124, 12: 112, 14: 232, 16: 182}
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12     # SMs x FP32 lanes x FMA x max SM clock
 
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) from ncu captures of small cases
-# of the same kernels, scaled to a full launch by the units it processes:
-PASS2_DRAM_BYTES_PER_PAIR_96 = 404.98e6 / 32    # 32-pair launch at 96^3 (12.66 MB/pair)
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) from ncu captures of the same
+# kernels: pass 2 on the full 512-pair launch at 96^3 (3.67 + 3.60 GB = 14.2 MB per pair, a
+# one-pass metric set), the SYRK on a small case scaled by the panel bytes it reads
+PASS2_DRAM_BYTES_PER_PAIR_96 = 7.27e9 / 512
 SYRK_DRAM_PER_PANEL_BYTE = 1.938e9 / 1.850e9    # DRAM bytes per byte of the two bf16 panels
 
 
@@ -283,7 +284,8 @@ def run_rsx(args, rank, local_rank, world):
             traffic = PASS2_DRAM_BYTES_PER_PAIR_96 * sum(per_launch_pairs[top]) / len(per_launch_pairs[top])
         roof = {"kernel": top, "bound": "alu", "achieved": round(ach_f, 2), "peak": round(FP32_PEAK_TFLOPS, 2),
                 "unit": "TFLOP/s", "frac": round(ach_f / FP32_PEAK_TFLOPS, 4), "traffic": traffic,
-                "traffic_source": "ncu DRAM bytes of a 32-pair launch scaled by pairs per launch" if traffic else None,
+                "traffic_source": "ncu DRAM bytes of the 512-pair launch (14.2 MB per pair) times the average pairs "
+                                  "per launch" if traffic else None,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 (FMA) x 2.07 GHz",
                 "algorithmic_flops_per_launch": avg_flops,
                 "hbm_view": {"achieved_gbs": round(ach_b, 1), "peak_gbs": hbm_peak, "frac": round(ach_b / hbm_peak, 4),
@@ -589,7 +591,8 @@ def batch_bench(args, dev, local_rank, peaks):
     ach = byts / (ms / 1e3) / 1e9
     b.close()
     return {"workload": f"{len(desc)} molecules, edges from {{48,64,80,96,112}}, N_occ U{{2..24}}, h=0.2: "
-                        "exchange apply (psi = phi) + ACE build each, persistent launches in one CUDA graph",
+                        "exchange apply (psi = phi) + ACE build each; per box edge one launch of each FFT pass over "
+                        "all that edge's pairs, ACE per molecule, one CUDA graph",
             "solves_per_batch": solves, "ms_per_batch": round(ms, 3), "solves_per_s": round(solves / (ms / 1e3), 1),
             "hbm_model_gbs": round(ach, 1), "hbm_frac": round(ach / hbm, 4), "input_generation_s": round(gen_s, 1)}
 

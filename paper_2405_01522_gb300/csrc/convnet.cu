@@ -5,8 +5,9 @@
 //
 // Kernels: k_conv_tc (the convolution as an implicit GEMM on the tcgen05 tensor cores,
 // see below), the data gradient as the same convolution with flipped, transposed weights
-// (k_flip_weights), k_conv_wgrad (per-block partial sums, reduced in fixed order by
-// k_wgrad_reduce), masked MSE loss, ReLU backward and Adam.
+// (k_flip_weights), k_wgrad_tc (the weight gradient as an implicit GEMM on the tensor
+// cores, per-block partial sums reduced in fixed order by k_wgrad_reduce), masked MSE
+// loss, ReLU backward and Adam.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -268,74 +269,248 @@ __global__ void k_relu_back(float* __restrict__ da, const float* __restrict__ z,
     if (!(z[i] > 0.f)) da[i] = 0.f;
 }
 
-// partial weight and bias gradients of one layer over one 8^3 block of one sample:
-// part[blk][co][ci][t] = sum_v dout[co][v] act(in[ci][v + t - 1]), part[blk][CO*CI*27 + co] = sum_v dout[co][v]
+// Weight and bias gradients of one layer on the tensor cores, per CTA partial sums:
+//   part[blk][co][ci][t] = sum_v dout[co][v] act(in[ci][v + t - 1]),  part[blk][CO*CI*27 + co] = sum_v dout[co][v]
+// over the CTA's 16 (x) x 8 (y) x 8 (z) block of output voxels of one sample.  The
+// contraction is an implicit GEMM with rows (t, ci) -- four groups of 8 taps x 16 input
+// channels, M = 128 rows per MMA (the last group holds taps 24..26 and zero rows) -- columns
+// co (N = 16, zero rows for co >= CO) and K = the voxels, 16 consecutive x positions of one
+// (z, y) row per K step.  Per output plane z the input rows the plane's 8 K steps need (3
+// planes x 10 rows x 16 channels x 18 x, ReLU applied) and its dout rows are staged once in
+// shared memory.  For each K step thread (ci, 8-voxel chunk, dz) writes the 9 taps
+// (dy, dx) of its channel from those rows into the A operand (the shifted input windows:
+// one copy per tap, the operand layout having no room for a shifted view), 32 threads
+// write the B operand (dout), both in the no-swizzle K-major core-matrix layout (element
+// (row, k) at (row / 8) 256 + (k / 8) 128 + (row % 8) 16 + (k % 8) 2 bytes) and split into
+// bf16 hi + lo; one thread issues hi.hi + hi.lo + lo.hi per group into four 16-column FP32
+// accumulators in TMEM.  The tiles are double-buffered: building step s overlaps the MMAs
+// of step s - 1 (an mbarrier per buffer).  Every wait is bounded; a
+// timeout sets RSX_ETIMEOUT, the CTA waits (bounded) for its issued MMAs, frees its TMEM and
+// returns without writing.
+constexpr int kWgX = 16, kWgY = 8, kWgZ = 8;
+constexpr int kWgThreads = 128;
+constexpr int kWgATile = 4096;                          // 128 rows x 16 K bf16
+constexpr int kWgBTile = 512;                           // 16 rows x 16 K bf16
+constexpr int kWgBuf = 4 * 2 * kWgATile + 2 * kWgBTile; // (4 groups x hi, lo) + (hi, lo) of B
+constexpr int kWgRow = kWgX + 2;                        // 18 x values per staged input row
+constexpr int kWgSlabRows = 3 * (kWgY + 2) * 16;        // (dz, y, ci) rows of one plane's K steps
+constexpr int kWgSlab = kWgSlabRows * kWgRow * 4;       // 34560 bytes
+constexpr int kWgDslab = kWgY * 16 * kWgX * 4;          // dout rows of one plane: [y][co][x], 8192 bytes
+constexpr int kWgSmem = 2 * kWgBuf + kWgSlab + kWgDslab;
+
 template <int CI, int CO>
-__global__ void __launch_bounds__(kConvThreads) k_conv_wgrad(const float* __restrict__ in, const float* __restrict__ dout,
-                                                             float* __restrict__ part, int D, int H, int W, int relu_in) {
-  __shared__ float tile[kHalo][kHalo][kHalo];
-  __shared__ float dsh[CO][kT * kT * kT];
-  const int nbx = (W + kT - 1) / kT, nby = (H + kT - 1) / kT, nbz = (D + kT - 1) / kT;
+__global__ void __launch_bounds__(kWgThreads, 1) k_wgrad_tc(const float* __restrict__ in, const float* __restrict__ dout,
+                                                         float* __restrict__ part, int D, int H, int W, int relu_in,
+                                                         int* status) {
+  static_assert(CI <= 16 && CO <= 16, "channels per layer <= 16");
+  static_assert(kWgThreads == 128, "96 A-builder threads (ci, chunk, dz) + 32 B-builder threads (co, chunk)");
+  using namespace rsx::tc;
+  extern __shared__ __align__(128) unsigned char sm[];
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ uint32_t tmem_sh;
+  __shared__ int abort_sh;
+  __shared__ float bsum[16];
+  const int nbx = (W + kWgX - 1) / kWgX, nby = (H + kWgY - 1) / kWgY;
   int blk = blockIdx.x;
   const int bx = blk % nbx;
   blk /= nbx;
   const int by = blk % nby;
   const int bz = blk / nby;
   const int b = blockIdx.y;
-  const int x0 = bx * kT, y0 = by * kT, z0 = bz * kT;
+  const int x0 = bx * kWgX, y0 = by * kWgY, z0 = bz * kWgZ;
   const size_t vol = (size_t)D * H * W;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   constexpr int NOUT = CO * CI * 27 + CO;
-  float* dst = part + ((size_t)b * nbx * nby * nbz + blockIdx.x) * NOUT;
-  // stage dout block (zero outside)
-  for (int i = threadIdx.x; i < CO * kT * kT * kT; i += kConvThreads) {
-    const int o = i / (kT * kT * kT), v = i - o * kT * kT * kT;
-    const int tz = v / (kT * kT), ty = (v / kT) % kT, tx = v % kT;
-    const int z = z0 + tz, y = y0 + ty, x = x0 + tx;
-    dsh[o][v] = (z < D && y < H && x < W) ? dout[((size_t)b * CO + o) * vol + ((size_t)z * H + y) * W + x] : 0.f;
+  float* dst = part + ((size_t)b * gridDim.x + blockIdx.x) * NOUT;
+
+  for (int i = tid; i < 2 * kWgBuf / 16; i += kWgThreads) reinterpret_cast<uint4*>(sm)[i] = make_uint4(0, 0, 0, 0);
+  float* slab = reinterpret_cast<float*>(sm + 2 * kWgBuf);   // [dz][y - y0 + 1][ci][x - x0 + 1]
+  float* dslab = slab + kWgSlab / 4;                          // [y - y0][co][x - x0]
+  if (tid < 16) bsum[tid] = 0.f;
+  if (tid == 0) {
+    abort_sh = 0;
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  for (int ci = 0; ci < CI; ++ci) {
-    __syncthreads();
-    for (int i = threadIdx.x; i < kHalo * kHalo * kHalo; i += kConvThreads) {
-      const int hz = i / (kHalo * kHalo), hy = (i / kHalo) % kHalo, hx = i % kHalo;
-      const int z = z0 + hz - 1, y = y0 + hy - 1, x = x0 + hx - 1;
-      float v = 0.f;
-      if (z >= 0 && z < D && y >= 0 && y < H && x >= 0 && x < W) {
-        v = in[((size_t)b * CI + ci) * vol + ((size_t)z * H + y) * W + x];
-        if (relu_in) v = fmaxf(v, 0.f);
-      }
-      tile[hz][hy][hx] = v;
-    }
-    __syncthreads();
-    // outputs (co, t) for this ci: CO * 27 <= 432 -> threads loop
-    for (int o = threadIdx.x; o < CO * 27; o += kConvThreads) {
-      const int co = o / 27, t = o - co * 27;
-      const int dz = t / 9, dy = (t / 3) % 3, dx = t % 3;
-      float s = 0.f;
-      for (int v = 0; v < kT * kT * kT; ++v) {
-        const int tz = v / (kT * kT), ty = (v / kT) % kT, tx = v % kT;
-        s = fmaf(dsh[co][v], tile[tz + dz][ty + dy][tx + dx], s);
-      }
-      dst[((size_t)co * CI + ci) * 27 + t] = s;
-    }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_sh)), "r"(64)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  for (int co = threadIdx.x; co < CO; co += kConvThreads) {
-    float s = 0.f;
-    for (int v = 0; v < kT * kT * kT; ++v) s += dsh[co][v];
-    dst[CO * CI * 27 + co] = s;
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_sh;
+  const uint32_t sm_s = smem_u32(sm);
+  volatile int* abort_flag = &abort_sh;
+  float bacc = 0.f;
+  int issued = 0;
+  constexpr int nsteps = kWgY * kWgZ;
+  // operand descriptors of both buffers, made once (the issuing thread only)
+  uint64_t dah[2][4], dal[2][4], dbh[2], dbl[2];
+  if (tid == 0) {
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const uint32_t a_s = sm_s + (uint32_t)q * kWgBuf, b_s = a_s + 8 * kWgATile;
+      dbh[q] = kmajor_desc(b_s, 128, 256);
+      dbl[q] = kmajor_desc(b_s + kWgBTile, 128, 256);
+#pragma unroll
+      for (int g = 0; g < 4; ++g) {
+        dah[q][g] = kmajor_desc(a_s + (uint32_t)g * 2 * kWgATile, 128, 256);
+        dal[q][g] = kmajor_desc(a_s + (uint32_t)g * 2 * kWgATile + kWgATile, 128, 256);
+      }
+    }
   }
+  for (int s = 0; s < nsteps; ++s) {
+    const int buf = s & 1;
+    if (s >= 2) {   // buffer buf was read by the MMAs of step s - 2
+      if (tid == 0 && !mbar_wait(&bar[buf], (uint32_t)(((s - 2) >> 1) & 1), abort_flag)) *abort_flag = 1;
+      __syncthreads();
+      if (*abort_flag) break;
+    }
+    const int zl = s / kWgY, yl = s % kWgY;
+    const int z = z0 + zl, y = y0 + yl;
+    if (yl == 0) {   // stage the input rows of plane z's K steps (every reader of the last slab is done)
+      __syncthreads();
+      for (int e = tid; e < kWgSlabRows * kWgRow; e += kWgThreads) {
+        const int row = e / kWgRow, xo = e - row * kWgRow;
+        const int ci = row & 15, yy = (row >> 4) % (kWgY + 2), dz = (row >> 4) / (kWgY + 2);
+        const int zz = z + dz - 1, yg = y0 - 1 + yy, xg = x0 - 1 + xo;
+        float a = 0.f;
+        if (ci < CI && zz >= 0 && zz < D && yg >= 0 && yg < H && xg >= 0 && xg < W)
+          a = __ldg(in + ((size_t)b * CI + ci) * vol + ((size_t)zz * H + yg) * W + xg);
+        slab[e] = relu_in ? fmaxf(a, 0.f) : a;
+      }
+      for (int e = tid; e < kWgY * 16 * kWgX; e += kWgThreads) {
+        const int yy = e / (16 * kWgX), co = (e / kWgX) & 15, xo = e % kWgX;
+        const int yg = y0 + yy, xg = x0 + xo;
+        dslab[e] = (co < CO && z < D && yg < H && xg < W)
+                       ? __ldg(dout + ((size_t)b * CO + co) * vol + ((size_t)z * H + yg) * W + xg) : 0.f;
+      }
+      __syncthreads();
+    }
+    unsigned char* At = sm + (size_t)buf * kWgBuf;
+    unsigned char* Bt = At + 8 * kWgATile;
+    auto put = [&](unsigned char* dstp, int lo_off, const float* v) {
+      uint32_t hv[4], lv[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
+        const float2 hf = __bfloat1622float2(h2);
+        hv[q] = *reinterpret_cast<const uint32_t*>(&h2);
+        lv[q] = pack_bf16x2(v[2 * q] - hf.x, v[2 * q + 1] - hf.y);
+      }
+      *reinterpret_cast<uint4*>(dstp) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
+      *reinterpret_cast<uint4*>(dstp + lo_off) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
+    };
+    if (tid < 96) {   // A: channel ci, chunk c, plane offset dz -> taps (dz, dy, dx)
+      const int ci = tid & 15, c = (tid >> 4) & 1, dz = tid >> 5;
+      if (ci < CI) {
+#pragma unroll
+        for (int dy = 0; dy < 3; ++dy) {
+          const float2* rp = reinterpret_cast<const float2*>(
+              slab + ((dz * (kWgY + 2) + yl + dy) * 16 + ci) * kWgRow + 8 * c);
+          float r[10];
+#pragma unroll
+          for (int q = 0; q < 5; ++q) {
+            const float2 u = rp[q];
+            r[2 * q] = u.x;
+            r[2 * q + 1] = u.y;
+          }
+#pragma unroll
+          for (int dx = 0; dx < 3; ++dx) {
+            const int t = 9 * dz + 3 * dy + dx;
+            const int g = t >> 3, m = ((t & 7) << 4) | ci;
+            put(At + (size_t)g * 2 * kWgATile + (m >> 3) * 256 + c * 128 + (m & 7) * 16, kWgATile, r + dx);
+          }
+        }
+      }
+    } else {          // B: dout of channel co, chunk c (and the bias gradient)
+      const int j = tid - 96, co = j >> 1, c = j & 1;
+      const float4* dp = reinterpret_cast<const float4*>(dslab + (yl * 16 + co) * kWgX + 8 * c);
+      const float4 d0 = dp[0], d1 = dp[1];
+      const float v[8] = {d0.x, d0.y, d0.z, d0.w, d1.x, d1.y, d1.z, d1.w};
+#pragma unroll
+      for (int k = 0; k < 8; ++k) bacc += v[k];
+      put(Bt + (co >> 3) * 256 + c * 128 + (co & 7) * 16, kWgBTile, v);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (tid == 0) {
+      const uint32_t first = s > 0 ? 1u : 0u;
+#pragma unroll
+      for (int g = 0; g < 4; ++g) {
+        const uint32_t d = tmem + (uint32_t)(16 * g);
+        const uint64_t ah = buf ? dah[1][g] : dah[0][g], al = buf ? dal[1][g] : dal[0][g];
+        const uint64_t bh = buf ? dbh[1] : dbh[0], bl = buf ? dbl[1] : dbl[0];
+        mma_f16(d, ah, bh, kConvIdesc, first);
+        mma_f16(d, ah, bl, kConvIdesc, 1u);
+        mma_f16(d, al, bh, kConvIdesc, 1u);
+      }
+      mma_commit(&bar[buf]);
+      issued = s + 1;
+    }
+  }
+  // wait for the last commit of each barrier (no arrival may land after the CTA exits; the
+  // last commit also covers every MMA issued before it); bounded in every case
+  if (tid == 0 && issued > 0) {
+    for (int st = issued - 1; st >= 0 && st >= issued - 2; --st) {
+      const uint32_t par = (uint32_t)((st >> 1) & 1);
+      if (!*abort_flag) {
+        if (!mbar_wait(&bar[st & 1], par, abort_flag)) *abort_flag = 1;
+      } else {
+        for (uint32_t k = 0; k < kWaitLimit && !mbar_try_wait(&bar[st & 1], par); ++k) {
+        }
+      }
+    }
+    if (*abort_flag && status) atomicMax(status, RSX_ETIMEOUT);
+  }
+  if (tid >= 96) atomicAdd(&bsum[(tid - 96) >> 1], bacc);
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (!*abort_flag) {
+    const int m = warp * 32 + lane;
+#pragma unroll 1
+    for (int g = 0; g < 4; ++g) {
+      float acc[16];
+      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(16 * g), acc);
+      const int t = 8 * g + (m >> 4), ci = m & 15;
+      if (t < 27 && ci < CI) {
+#pragma unroll
+        for (int co = 0; co < CO; ++co) dst[((size_t)co * CI + ci) * 27 + t] = acc[co];
+      }
+    }
+    if (tid < CO) dst[CO * CI * 27 + tid] = bsum[tid];
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(64) : "memory");
 }
 
-// grad[o] (+)= sum over nparts of part[p][o], FP64 accumulation in fixed order
-__global__ void k_wgrad_reduce(const float* __restrict__ part, int nparts, int nout, float* __restrict__ gw,
-                               float* __restrict__ gb, int nw) {
-  for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < nout; o += gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int p = 0; p < nparts; ++p) s += part[(size_t)p * nout + o];
+// grad[o] = sum over nparts of part[p][o], FP64 accumulation in a fixed order: a block owns
+// 32 consecutive outputs (lane = output, coalesced reads), warp w sums the partials
+// p = w, w + 8, ..., and the 8 warp sums are added in warp order
+__global__ void __launch_bounds__(256) k_wgrad_reduce(const float* __restrict__ part, int nparts, int nout,
+                                                      float* __restrict__ gw, float* __restrict__ gb, int nw) {
+  __shared__ double red[8][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int o = blockIdx.x * 32 + lane;
+  double sum = 0.0;
+  if (o < nout)
+    for (int p = warp; p < nparts; p += 8) sum += (double)part[(size_t)p * nout + o];
+  red[warp][lane] = sum;
+  __syncthreads();
+  if (warp == 0 && o < nout) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += red[w][lane];
     if (o < nw)
-      gw[o] = (float)s;
+      gw[o] = (float)t;
     else
-      gb[o - nw] = (float)s;
+      gb[o - nw] = (float)t;
   }
 }
 
@@ -449,7 +624,7 @@ int backward(rsx_net* n, const float* x, const float* target, int B, int D, int 
   const size_t vol = (size_t)D * H * W;
   int rc = ngrow(n, &n->gout, &n->gout_elems, 2 * (size_t)B * kC2 * vol + (size_t)B * vol * 2);
   if (rc) return rc;
-  const int nblk = ((W + kT - 1) / kT) * ((H + kT - 1) / kT) * ((D + kT - 1) / kT);
+  const int nblk = ((W + kWgX - 1) / kWgX) * ((H + kWgY - 1) / kWgY) * ((D + kWgZ - 1) / kWgZ);
   rc = ngrow(n, &n->part, &n->part_elems, (size_t)B * nblk * (kW2 + kC3));
   if (rc) return rc;
   float* g2 = n->gout;                                  // d z2  [B][16][vol]
@@ -461,23 +636,26 @@ int backward(rsx_net* n, const float* x, const float* target, int B, int D, int 
   float* z1 = n->act;                                   // pre-activations of layers 1 and 2
   float* z2 = n->act + (size_t)B * kC2 * vol;
   k_mse<<<512, 256, 0, s>>>(y, target, gy, B, D, H, W, border, n->loss);
-  const dim3 g = conv_grid(B, D, H, W);
+  const dim3 g((unsigned)nblk, (unsigned)B);
   const float* P = n->params;
+  for (auto k : {k_wgrad_tc<kC3, kC4>, k_wgrad_tc<kC2, kC3>, k_wgrad_tc<kC1, kC2>})
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kWgSmem) != cudaSuccess)
+      return ncuda(n, cudaGetLastError(), "wgrad attributes");
   // layer 3: w3 grads from relu(z2) and gy; d relu(z2) = conv(gy, flip(w3)); dz2 = * (z2 > 0)
-  k_conv_wgrad<kC3, kC4><<<g, kConvThreads, 0, s>>>(z2, gy, n->part, D, H, W, 1);
-  k_wgrad_reduce<<<64, 256, 0, s>>>(n->part, B * nblk, kW3 + kC4, n->grads + kOffW3, n->grads + kOffB3, kW3);
+  k_wgrad_tc<kC3, kC4><<<g, kWgThreads, kWgSmem, s>>>(z2, gy, n->part, D, H, W, 1, n->status);
+  k_wgrad_reduce<<<(kW3 + kC4 + 31) / 32, 256, 0, s>>>(n->part, B * nblk, kW3 + kC4, n->grads + kOffW3, n->grads + kOffB3, kW3);
   k_flip_weights<<<16, 256, 0, s>>>(P + kOffW3, n->wflip, kC3, kC4);
   conv<kC4, kC3>(n, gy, n->wflip, nullptr, g2, B, D, H, W, 0, s);
   k_relu_back<<<512, 256, 0, s>>>(g2, z2, (size_t)B * kC2 * vol);
   // layer 2
-  k_conv_wgrad<kC2, kC3><<<g, kConvThreads, 0, s>>>(z1, g2, n->part, D, H, W, 1);
-  k_wgrad_reduce<<<64, 256, 0, s>>>(n->part, B * nblk, kW2 + kC3, n->grads + kOffW2, n->grads + kOffB2, kW2);
+  k_wgrad_tc<kC2, kC3><<<g, kWgThreads, kWgSmem, s>>>(z1, g2, n->part, D, H, W, 1, n->status);
+  k_wgrad_reduce<<<(kW2 + kC3 + 31) / 32, 256, 0, s>>>(n->part, B * nblk, kW2 + kC3, n->grads + kOffW2, n->grads + kOffB2, kW2);
   k_flip_weights<<<32, 256, 0, s>>>(P + kOffW2, n->wflip, kC2, kC3);
   conv<kC3, kC2>(n, g2, n->wflip, nullptr, g1, B, D, H, W, 0, s);
   k_relu_back<<<512, 256, 0, s>>>(g1, z1, (size_t)B * kC2 * vol);
   // layer 1
-  k_conv_wgrad<kC1, kC2><<<g, kConvThreads, 0, s>>>(x, g1, n->part, D, H, W, 0);
-  k_wgrad_reduce<<<64, 256, 0, s>>>(n->part, B * nblk, kW1 + kC2, n->grads + kOffW1, n->grads + kOffB1, kW1);
+  k_wgrad_tc<kC1, kC2><<<g, kWgThreads, kWgSmem, s>>>(x, g1, n->part, D, H, W, 0, n->status);
+  k_wgrad_reduce<<<(kW1 + kC2 + 31) / 32, 256, 0, s>>>(n->part, B * nblk, kW1 + kC2, n->grads + kOffW1, n->grads + kOffB1, kW1);
   return ncuda(n, cudaGetLastError(), "network backward");
 }
 

@@ -462,6 +462,7 @@ def casida_bench(args, dev, local_rank, peaks):
     k_ms = e[0].elapsed_time(e[1]) / reps
     gemm_ms = prof["k_gemm_tcgen05"][0] / prof["k_gemm_tcgen05"][1]
     useful = 2.0 * nt * nt * ng                      # one product, full nt x nt
+    method = 3 * nt * (nt + 1) * ng                  # three split products of the SYRK half (upper triangle)
     nbk = (nt + 127) // 128
     executed = 3 * (nbk * (nbk + 1) // 2) * 2.0 * 128 * 128 * ng   # three products, upper-triangle tiles
     peak = peaks.get("bf16_tflops", 1900.0)
@@ -527,6 +528,9 @@ def casida_bench(args, dev, local_rank, peaks):
                          "what": "A and B (Eqs. 3-5), half-size form by FP64 Cholesky, lowest 10 roots"},
            "uhf": uhf,
            "useful_tflops": round(useful / (gemm_ms / 1e3) / 1e12, 1),
+           "method_work": {"what": "3 split products of the SYRK half, 3 nt (nt + 1) N_G flops",
+                           "tflops": round(method / (gemm_ms / 1e3) / 1e12, 1),
+                           "frac_of_peak": round(method / (gemm_ms / 1e3) / 1e12 / peaks.get("bf16_tflops", 1900.0), 4)},
            "kernels": {k: {"ms_per_launch": round(v[0] / v[1], 4), "launches": v[1]} for k, v in prof.items()},
            "roofline": {"kernel": "k_syrk_bf16x3 (tcgen05)", "bound": "tensor",
                         "achieved": round(executed / (gemm_ms / 1e3) / 1e12, 1), "peak": peak, "unit": "TFLOP/s",

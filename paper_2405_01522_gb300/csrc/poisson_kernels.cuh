@@ -314,10 +314,15 @@ __device__ __forceinline__ void y_forward(Cx<R>* D, int DP, int nz, int ny, cons
   }
 }
 
-// inverse y transform of rows z < nz (input all My, output y < ny)
+// inverse y transform of rows z < nz (input all My of D's rows, output y < ny written to
+// out[z * opitch + y]: back into D, or straight to the plane in global memory)
 template <typename R, int AY, int NT, int PITCH = kScrPitch>
 __device__ __forceinline__ void y_inverse(Cx<R>* D, int DP, int nz, int ny, const Cx<R>* __restrict__ twy,
-                                          Cx<R>* sc) {
+                                          Cx<R>* sc, Cx<R>* out = nullptr, int opitch = 0) {
+  if (out == nullptr) {
+    out = D;
+    opitch = DP;
+  }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, t = lane & 15;
   // this lane's stage-1 twiddles (conjugated below), the same for every row
   Cx<R> tw[AY];
@@ -358,7 +363,7 @@ __device__ __forceinline__ void y_inverse(Cx<R>* D, int DP, int nz, int ny, cons
 #pragma unroll
       for (int k2 = 0; k2 < ((AY % 2 == 0) ? 8 : 16); ++k2) {
         const int y = t + AY * k2;
-        if (y < ny) D[z * DP + y] = u[k2];
+        if (y < ny) out[z * opitch + y] = u[k2];
       }
     }
     __syncwarp();
@@ -499,11 +504,10 @@ __device__ __forceinline__ void pass2_plane(const Geom& g, Cx<R>* P, int kx, con
     __syncwarp();
   }
   __syncthreads();
-  y_inverse<R, AY, NT, PITCH>(D, DP, NZ, NY, twy, sc);
-  __syncthreads();
+  // the inverse rows go straight to the plane in global memory (no copy through D)
+  y_inverse<R, AY, NT, PITCH>(D, DP, NZ, NY, twy, sc, P, NY);
+  __syncthreads();   // every read of D's upper halves is done
   if (Pnext) prefetch_plane_upper<R>(D, DP, Pnext, NZ, NY, NT);
-  store_plane<NT>(D, DP, P, NZ, NY);
-  __syncthreads();
 }
 
 // D lives in shared memory (DSMEM) or, when it does not fit, in a per-CTA slice of

@@ -490,6 +490,7 @@ int rsx_set_workspace_limit(rsx_ctx* c, size_t bytes) {
   }
 
 int rsx_build_pair_densities(rsx_ctx* c, const void* a, int na, const void* b, int nb, void* rho, void* stream) {
+  rsx::NvtxRange nvtx_range("rsx_build_pair_densities");
   RSX_PREP(c);
   if (!a || !b || !rho || na < 1 || nb < 1) return set_error(c, RSX_EINVAL, "bad pair-density arguments");
   const size_t N = c->g.N(), es = c->elem_size();
@@ -504,6 +505,7 @@ int rsx_build_pair_densities(rsx_ctx* c, const void* a, int na, const void* b, i
 }
 
 int rsx_exchange_apply(rsx_ctx* c, const void* phi, int nocc, const void* psi, int npsi, void* out, void* stream) {
+  rsx::NvtxRange nvtx_range("rsx_exchange_apply");
   RSX_PREP(c);
   if (!phi || !psi || !out || nocc < 1 || npsi < 1) return set_error(c, RSX_EINVAL, "bad exchange arguments");
   const size_t N = c->g.N(), es = c->elem_size();
@@ -515,6 +517,7 @@ int rsx_exchange_apply(rsx_ctx* c, const void* phi, int nocc, const void* psi, i
 }
 
 int rsx_poisson(rsx_ctx* c, const void* rho, void* V, void* stream) {
+  rsx::NvtxRange nvtx_range("rsx_poisson");
   RSX_PREP(c);
   if (!rho || !V) return set_error(c, RSX_EINVAL, "bad Poisson arguments");
   const size_t bytes = c->g.N() * c->elem_size();
@@ -524,6 +527,7 @@ int rsx_poisson(rsx_ctx* c, const void* rho, void* V, void* stream) {
 }
 
 int rsx_ace_build(rsx_ctx* c, const void* phi, int nocc, void* xi, double* M_out, void* stream) {
+  rsx::NvtxRange nvtx_range("rsx_ace_build");
   RSX_PREP(c);
   if (!phi || !xi || nocc < 1 || nocc > 64) return set_error(c, RSX_EINVAL, "bad ACE build arguments");
   const size_t N = c->g.N(), es = c->elem_size();
@@ -534,6 +538,7 @@ int rsx_ace_build(rsx_ctx* c, const void* phi, int nocc, void* xi, double* M_out
 }
 
 int rsx_ace_apply(rsx_ctx* c, const void* xi, int nxi, const void* psi, int npsi, void* out, void* stream) {
+  rsx::NvtxRange nvtx_range("rsx_ace_apply");
   RSX_PREP(c);
   if (!xi || !psi || !out || nxi < 1 || npsi < 1 || nxi * npsi > 4096 || nxi > 64)
     return set_error(c, RSX_EINVAL, "bad ACE apply arguments");
@@ -547,6 +552,7 @@ int rsx_ace_apply(rsx_ctx* c, const void* xi, int nxi, const void* psi, int npsi
 }
 
 int rsx_gram(rsx_ctx* c, const void* a, int na, const void* b, int nb, double* C, void* stream) {
+  rsx::NvtxRange nvtx_range("rsx_gram");
   RSX_PREP(c);
   if (!a || !b || !C || na < 1 || nb < 1 || na * nb > 4096) return set_error(c, RSX_EINVAL, "bad Gram arguments");
   cudaStream_t s = (cudaStream_t)stream;
@@ -572,6 +578,7 @@ int rsx_gram(rsx_ctx* c, const void* a, int na, const void* b, int nb, double* C
 
 
 int rsx_ace_factor(rsx_ctx* c, double* M, const void* W, int nocc, void* xi, void* stream) {
+  rsx::NvtxRange nvtx_range("rsx_ace_factor");
   RSX_PREP(c);
   if (!M || !W || !xi || nocc < 1 || nocc > 64) return set_error(c, RSX_EINVAL, "bad ACE factor arguments");
   const size_t bytes = (size_t)nocc * c->g.N() * c->elem_size();

@@ -3,6 +3,8 @@
 #include <algorithm>
 #include <cstddef>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <vector>
 
 #include "rsx_internal.cuh"
@@ -69,6 +71,14 @@ struct rsx_ctx {
 };
 
 namespace rsx {
+// NVTX range around a C-ABI call (tracing with Nsight Systems; a few nanoseconds when no
+// tool is attached)
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 int check_cuda(rsx_ctx* c, cudaError_t e, const char* what);
 int grow(rsx_ctx* c, void** p, size_t* have, size_t need, const char* what);
 int set_error(rsx_ctx* c, int code, const char* msg);

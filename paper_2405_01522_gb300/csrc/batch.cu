@@ -308,6 +308,7 @@ int rsx_batch_bind(rsx_batch* b, const void* const* phi, void* const* W, void* c
 }
 
 int rsx_batch_run(rsx_batch* b, void* stream) {
+  rsx::NvtxRange nvtx_range("rsx_batch_run");
   if (!b) return RSX_EINVAL;
   if (!b->bound) return bfail(b, RSX_EINVAL, "batch run: bind the molecule arrays first");
   if (cudaSetDevice(b->device) != cudaSuccess) return bcuda(b, cudaGetLastError(), "cudaSetDevice");

@@ -276,6 +276,7 @@ extern "C" {
 
 int rsx_casida_K(rsx_ctx* c, const void* phi_occ, int nocc, const void* phi_virt, int nvirt, double* K,
                  void* stream) {
+  rsx::NvtxRange nvtx_range("rsx_casida_K");
   RSX_PREP_C(c);
   int rc = check_casida_args(c, phi_occ, nocc, phi_virt, nvirt, K);
   if (rc) return rc;
@@ -290,6 +291,7 @@ int rsx_casida_K(rsx_ctx* c, const void* phi_occ, int nocc, const void* phi_virt
 
 int rsx_casida_K_uhf(rsx_ctx* c, const void* occ_a, int nocc_a, const void* virt_a, int nvirt_a, const void* occ_b,
                      int nocc_b, const void* virt_b, int nvirt_b, double* K, void* stream) {
+  rsx::NvtxRange nvtx_range("rsx_casida_K_uhf");
   RSX_PREP_C(c);
   int rc = check_casida_args(c, occ_a, nocc_a, virt_a, nvirt_a, K);
   if (rc) return rc;
@@ -314,6 +316,7 @@ int rsx_casida_K_uhf(rsx_ctx* c, const void* occ_a, int nocc_a, const void* virt
 int rsx_casida_solve_uhf(rsx_ctx* c, const double* eo_a, int nocc_a, const double* ev_a, int nvirt_a,
                          const double* eo_b, int nocc_b, const double* ev_b, int nvirt_b, const double* K,
                          const double* Kd_a, const double* Kd_b, int nroots, double* omega, double* X, void* stream) {
+  rsx::NvtxRange nvtx_range("rsx_casida_solve_uhf");
   RSX_PREP_C(c);
   const bool has_b = nocc_b > 0 && nvirt_b > 0;
   const int nt = nocc_a * nvirt_a + (has_b ? nocc_b * nvirt_b : 0);
@@ -328,6 +331,7 @@ int rsx_casida_solve_uhf(rsx_ctx* c, const double* eo_a, int nocc_a, const doubl
 
 int rsx_casida_Kd(rsx_ctx* c, const void* phi_occ, int nocc, const void* phi_virt, int nvirt, double* Kd,
                   void* stream) {
+  rsx::NvtxRange nvtx_range("rsx_casida_Kd");
   RSX_PREP_C(c);
   int rc = check_casida_args(c, phi_occ, nocc, phi_virt, nvirt, Kd);
   if (rc) return rc;
@@ -338,6 +342,7 @@ int rsx_casida_Kd(rsx_ctx* c, const void* phi_occ, int nocc, const void* phi_vir
 
 int rsx_casida_solve(rsx_ctx* c, const double* eps_occ, int nocc, const double* eps_virt, int nvirt, const double* K,
                      const double* Kd, double delta_M, int nroots, double* omega, double* X, void* stream) {
+  rsx::NvtxRange nvtx_range("rsx_casida_solve");
   RSX_PREP_C(c);
   const int nt = nocc * nvirt;
   if (!eps_occ || !eps_virt || !K || !omega || nocc < 1 || nvirt < 1 || nt > 4096 || nroots < 1 || nroots > nt)
@@ -350,6 +355,7 @@ int rsx_casida_solve(rsx_ctx* c, const double* eps_occ, int nocc, const double* 
 
 // C = H H^T + H L^T + L H^T for bf16 panels H, L: [n][ld] (n % 128 == 0, ld % 64 == 0)
 int rsx_syrk_bf16x3(rsx_ctx* c, const void* hi, const void* lo, int n, long long ld, double* C, void* stream) {
+  rsx::NvtxRange nvtx_range("rsx_syrk_bf16x3");
   RSX_PREP_C(c);
   if (!hi || !lo || !C || n < 128 || n % 128 || ld < 64 || ld % 64)
     return set_error(c, RSX_EINVAL, "syrk: need n % 128 == 0 and ld % 64 == 0");

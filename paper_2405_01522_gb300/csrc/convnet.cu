@@ -708,6 +708,7 @@ int rsx_net_get_params(rsx_net* n, float* host, int count) {
 }
 
 int rsx_net_forward(rsx_net* n, const float* x, int B, int D, int H, int W, float* out, void* stream) {
+  rsx::NvtxRange nvtx_range("rsx_net_forward");
   if (!n || !x || !out || B < 1 || D < 1 || H < 1 || W < 1) return RSX_EINVAL;
   cudaSetDevice(n->device);
   return forward(n, x, B, D, H, W, out, (cudaStream_t)stream);
@@ -715,6 +716,7 @@ int rsx_net_forward(rsx_net* n, const float* x, int B, int D, int H, int W, floa
 
 int rsx_net_loss_grad(rsx_net* n, const float* x, const float* target, int B, int D, int H, int W, int border,
                       double* loss_host, float* grad_host, void* stream) {
+  rsx::NvtxRange nvtx_range("rsx_net_loss_grad");
   if (!n || !x || !target || B < 1 || D <= 2 * border || H <= 2 * border || W <= 2 * border) return RSX_EINVAL;
   cudaSetDevice(n->device);
   cudaStream_t s = (cudaStream_t)stream;
@@ -730,6 +732,7 @@ int rsx_net_loss_grad(rsx_net* n, const float* x, const float* target, int B, in
 
 int rsx_net_train_step(rsx_net* n, const float* x, const float* target, int B, int D, int H, int W, int border,
                        float lr, double* loss_host, void* stream) {
+  rsx::NvtxRange nvtx_range("rsx_net_train_step");
   if (!n || !x || !target || B < 1 || D <= 2 * border || H <= 2 * border || W <= 2 * border || !(lr > 0.f))
     return RSX_EINVAL;
   cudaSetDevice(n->device);

@@ -1104,6 +1104,7 @@ int rsx_eig_init(rsx_eig* e, const float* psi0, void* stream) {
 // One step; net may be NULL (plain).  theta_host[k] receives the new Ritz values; the
 // residual used in this step is kept (rsx_eig_residual).  Synchronises the stream.
 int rsx_eig_step(rsx_eig* e, rsx_net* net, int jacobi_sweeps, double* theta_host, void* stream) {
+  rsx::NvtxRange nvtx_range("rsx_eig_step");
   if (!e || !e->started || jacobi_sweeps < 0) return RSX_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   const int k = e->k;
@@ -1215,6 +1216,7 @@ int rsx_eig_set_mask(rsx_eig* e, const float* mask) {
 // H has changed (the potential's contents or the exchange term): H Psi and Rayleigh-Ritz
 // on the current orbitals, the LOBPCG direction dropped.
 int rsx_eig_refresh(rsx_eig* e, double* theta_host, void* stream) {
+  rsx::NvtxRange nvtx_range("rsx_eig_refresh");
   if (!e || !e->started) return RSX_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   int rc = ham(e, e->B, e->k, e->HB, nullptr, e->V, s);
@@ -1242,6 +1244,7 @@ int rsx_eig_residual(rsx_eig* e, float* r_out, void* stream) {
 
 // FP64 energy of the current orbitals (see rsx.h)
 int rsx_eig_energy64(rsx_eig* e, double* energy_host, void* stream) {
+  rsx::NvtxRange nvtx_range("rsx_eig_energy64");
   if (!e || !energy_host) return RSX_EINVAL;
   if (!e->started) return efail(e, RSX_EINVAL, "energy64: call rsx_eig_init first");
   if (e->xmode != 0) return efail(e, RSX_EUNSUPPORTED, "energy64: H with an exchange term is not covered");
@@ -1407,6 +1410,7 @@ int rsx_scf_init(rsx_scf* c, const float* psi0, void* stream) {
 // exchange), the relative density error of the previous iteration (Eq. 15; 0 on the
 // first), and the sum of the new Ritz values.  Synchronises the stream.
 int rsx_scf_step(rsx_scf* c, int inner, double* out_host, void* stream) {
+  rsx::NvtxRange nvtx_range("rsx_scf_step");
   if (!c || inner < 1 || !out_host) return RSX_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   const int k = c->nocc;

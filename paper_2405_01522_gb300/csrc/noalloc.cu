@@ -112,6 +112,7 @@ int noalloc_on_device(rsx_ctx* c, const void* phi, int nocc, const void* psi, in
 
 extern "C" int rsx_exchange_apply_noalloc(rsx_ctx* c, const void* phi, int nocc, const void* psi, int npsi,
                                           void* out, void* stream) {
+  rsx::NvtxRange nvtx_range("rsx_exchange_apply_noalloc");
   if (!c) return RSX_EINVAL;
   c->err[0] = 0;
   if (!phi || !psi || !out || nocc < 1 || npsi < 1) return set_error(c, RSX_EINVAL, "bad exchange arguments");

@@ -264,6 +264,7 @@ extern "C" {
 
 int rsx_casida_dipoles(rsx_ctx* c, const void* phi_occ, int nocc, const void* phi_virt, int nvirt, double* dip,
                        void* stream) {
+  rsx::NvtxRange nvtx_range("rsx_casida_dipoles");
   if (!c) return RSX_EINVAL;
   if (!phi_occ || !phi_virt || !dip || nocc < 1 || nvirt < 1 || nocc * nvirt > 4096)
     return set_error(c, RSX_EINVAL, "casida_dipoles: bad arguments (nocc * nvirt <= 4096)");
@@ -275,6 +276,7 @@ int rsx_casida_dipoles(rsx_ctx* c, const void* phi_occ, int nocc, const void* ph
 
 int rsx_casida_oscillator(rsx_ctx* c, const double* omega, const double* X, int nroots, int nt, const double* dip,
                           double* f, void* stream) {
+  rsx::NvtxRange nvtx_range("rsx_casida_oscillator");
   if (!c) return RSX_EINVAL;
   if (!omega || !X || !dip || !f || nroots < 1 || nt < 1) return set_error(c, RSX_EINVAL, "oscillator: bad arguments");
   if (cudaSetDevice(c->device) != cudaSuccess) return check_cuda(c, cudaGetLastError(), "cudaSetDevice");
@@ -284,6 +286,7 @@ int rsx_casida_oscillator(rsx_ctx* c, const double* omega, const double* X, int 
 
 int rsx_strength_function(rsx_ctx* c, const double* omega, const double* f, int nroots, double gamma,
                           const double* grid, int ngrid, double* S, void* stream) {
+  rsx::NvtxRange nvtx_range("rsx_strength_function");
   if (!c) return RSX_EINVAL;
   if (!omega || !f || !grid || !S || nroots < 1 || ngrid < 1 || !(gamma > 0.0))
     return set_error(c, RSX_EINVAL, "strength_function: bad arguments");
@@ -295,6 +298,7 @@ int rsx_strength_function(rsx_ctx* c, const double* omega, const double* f, int 
 int rsx_casida_solve_full(rsx_ctx* c, const double* eps_occ, int nocc, const double* eps_virt, int nvirt,
                           const double* K, const double* Kd, double delta_M, int nroots, double* omega, double* XpY,
                           void* stream) {
+  rsx::NvtxRange nvtx_range("rsx_casida_solve_full");
   if (!c) return RSX_EINVAL;
   const int n = nocc * nvirt;
   if (!eps_occ || !eps_virt || !K || !omega || nocc < 1 || nvirt < 1 || n > 4096 || nroots < 1 || nroots > n)

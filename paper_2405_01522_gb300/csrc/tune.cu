@@ -154,6 +154,7 @@ extern "C" int rsx_set_tuning(rsx_ctx* c, int p2_threads, int chunk_outputs) {
 
 extern "C" int rsx_autotune_ex(rsx_ctx* c, int nocc, int npsi, const char* cache_path, rsx_tuning* chosen,
                                double* best_ms) {
+  rsx::NvtxRange nvtx_range("rsx_autotune_ex");
   if (!c || nocc < 1 || npsi < 1) return RSX_EINVAL;
   c->err[0] = 0;
   if (cudaSetDevice(c->device) != cudaSuccess) {

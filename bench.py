@@ -356,12 +356,25 @@ def run_rsx(args, rank, local_rank, world):
     torch.cuda.synchronize()
     ace_ms = ea[0].elapsed_time(ea[1]) / 5
 
+    # ---- the Gram kernel alone per ACE shape (launch profiler: kernel time only)
+    gram_us = {}
+    for label, (ga, gb) in (("16x16 <phi, W>", (phi, xi)), ("16x32 <xi, psi>", (xi, psi))):
+        ctx.sync()
+        ctx.profile_reset()
+        ctx.profile(True)
+        for _ in range(10):
+            ctx.gram(ga, gb)
+        ctx.profile(False)
+        ctx.sync()
+        g = ctx.profile_read().get("gram")
+        gram_us[label] = round(g[0] / g[1] * 1e3, 1) if g else None
+
     out = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": bench_config(shape, world),
            "tuning": tuning, "roofline": roof, "kernels": kernels, "gpu_launches": launches, "clocks": clk, "e2e": e2e,
-           "ace_build_ms": round(ace_ms, 4)}
+           "ace_build_ms": round(ace_ms, 4), "gram_kernel_us": gram_us}
 
     # ---- FP64 plain form of the same step, and FP32 accuracy against it
     if not args.skip_fp64 and rank == 0:

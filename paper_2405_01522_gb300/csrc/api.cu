@@ -297,7 +297,7 @@ int ace_build(rsx_ctx* c, const void* phi, int nocc, void* xi, double* M_out, cu
   const double h3 = c->h * c->h * c->h;
   {
     ProfScope ps(c, kKGram, s);
-    rc = check_cuda(c, launch_gram<R>((const R*)phi, nocc, (const R*)xi, nocc, N, part, nblk, s), "gram");
+    rc = check_cuda(c, launch_gram<R>((const R*)phi, nocc, (const R*)xi, nocc, N, part, nblk, s, nullptr, c->status), "gram");
   }
   if (rc) return rc;
   {
@@ -342,7 +342,7 @@ int ace_apply(rsx_ctx* c, const void* xi, int nxi, const void* psi, int npsi, vo
   // C_kp = h^3 <xi_k, psi_p>; Cm[p][k] = -C_kp
   {
     ProfScope ps(c, kKGram, s);
-    rc = check_cuda(c, launch_gram<R>((const R*)xi, nxi, (const R*)psi, npsi, N, part, nblk, s), "gram");
+    rc = check_cuda(c, launch_gram<R>((const R*)xi, nxi, (const R*)psi, npsi, N, part, nblk, s, nullptr, c->status), "gram");
   }
   if (rc) return rc;
   {
@@ -564,7 +564,7 @@ int rsx_gram(rsx_ctx* c, const void* a, int na, const void* b, int nb, double* C
   {
     ProfScope ps(c, kKGram, s);
     rc = check_cuda(c, c->precision == RSX_FP32
-                           ? launch_gram<float>((const float*)a, na, (const float*)b, nb, N, c->dsm, nblk, s)
+                           ? launch_gram<float>((const float*)a, na, (const float*)b, nb, N, c->dsm, nblk, s, nullptr, c->status)
                            : launch_gram<double>((const double*)a, na, (const double*)b, nb, N, c->dsm, nblk, s),
                     "gram");
   }

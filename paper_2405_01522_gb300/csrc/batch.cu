@@ -138,7 +138,7 @@ int record(rsx_batch* b, cudaStream_t s) {
   const int nblk = 2 * b->nsm;
   for (int qi = 0; qi < b->nmol; ++qi) {
     const MolDesc& d = b->desc[qi];
-    rc = bcuda(b, launch_gram<float>(d.phi, d.nocc, d.W, d.nocc, d.g.N(), b->part, nblk, s), "batch gram");
+    rc = bcuda(b, launch_gram<float>(d.phi, d.nocc, d.W, d.nocc, d.g.N(), b->part, nblk, s, nullptr, b->status), "batch gram");
     if (!rc)
       rc = bcuda(b, launch_gram_reduce<float>(b->part, nblk, d.nocc, d.nocc, 1.0, false, b->Mm + (size_t)qi * 1024,
                                               (float*)nullptr, s),

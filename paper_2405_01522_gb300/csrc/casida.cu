@@ -77,7 +77,7 @@ int gram_blocks(rsx_ctx* c, const R* X, const R* Y, int n, size_t N, double scal
       const int nb = std::min(64, n - b1);
       {
         ProfScope ps(c, kKGram, s);
-        rc = check_cuda(c, launch_gram<R>(X + (size_t)b0 * N, na, Y + (size_t)b1 * N, nb, N, c->dsm, nblk, s, w),
+        rc = check_cuda(c, launch_gram<R>(X + (size_t)b0 * N, na, Y + (size_t)b1 * N, nb, N, c->dsm, nblk, s, w, c->status),
                         "gram block");
       }
       if (rc) return rc;

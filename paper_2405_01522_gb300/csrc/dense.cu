@@ -5,6 +5,9 @@
 #include <cstdint>
 
 #include "dense.cuh"
+#include "tcgen05_util.cuh"
+#include "gemm_tcgen05.cuh"
+#include "../../include/rsx.h"
 
 namespace rsx {
 
@@ -288,21 +291,32 @@ __global__ void __launch_bounds__(kGramThreads) k_gram_tiled(const R* __restrict
 // out[a][b] (or out[b][a] when transpose) = scale * sum_blk part[blk][a][b]; optional
 // R copy with the same layout.  32 outputs per block, 8 warps splitting the partials.
 // (ldo: row stride of out / out_r; 0 means na or nb as implied by transpose)
+constexpr int kRedGroups = 16;   // warps of k_gram_reduce, each over every 16th partial block
+
 template <typename R>
 __global__ void k_gram_reduce(const double* __restrict__ part, int nblk, int na, int nb, double scale,
                               int transpose, double* __restrict__ out, R* __restrict__ out_r, int ldo) {
-  __shared__ double red[8][33];
+  __shared__ double red[kRedGroups][33];
   const int nout = na * nb;
   const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
   const int o = blockIdx.x * 32 + lane;
-  double s = 0.0;
-  if (o < nout)
-    for (int k = g; k < nblk; k += 8) s += part[(size_t)k * nout + o];
-  red[g][lane] = s;
+  // four independent partial sums per thread, so that four loads are in flight at a time
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  if (o < nout) {
+    int k = g;
+    for (; k + 3 * kRedGroups < nblk; k += 4 * kRedGroups) {
+      s0 += part[(size_t)k * nout + o];
+      s1 += part[(size_t)(k + kRedGroups) * nout + o];
+      s2 += part[(size_t)(k + 2 * kRedGroups) * nout + o];
+      s3 += part[(size_t)(k + 3 * kRedGroups) * nout + o];
+    }
+    for (; k < nblk; k += kRedGroups) s0 += part[(size_t)k * nout + o];
+  }
+  red[g][lane] = (s0 + s1) + (s2 + s3);
   __syncthreads();
   if (g == 0 && o < nout) {
     double t = 0.0;
-    for (int q = 0; q < 8; ++q) t += red[q][lane];
+    for (int q = 0; q < kRedGroups; ++q) t += red[q][lane];
     t *= scale;
     const int a = o / nb, b = o - a * nb;
     const size_t d = transpose ? (size_t)b * (ldo ? ldo : na) + a : (size_t)a * (ldo ? ldo : nb) + b;
@@ -544,130 +558,214 @@ cudaError_t launch_ghat(const Geom& g, double h, double scale, const double* cos
 
 // ---------------------------------------------------------------------------------
 // Streaming FP32 Gram partials (N % 4 == 0, 16-byte aligned rows; used for at most two
-// 16 x 16 output groups): the output is cut into 16 x 16 groups (grid.y); a CTA streams 256-point chunks of its 16 X rows, 16 Y rows (and
-// the weight row) through a 3-stage cp.async ring, so that two chunks are in flight while
-// one is multiplied.  Thread (ti = warp & 3, tj = lane >> 3, split = lane & 7 + 8 (warp >> 2))
-// owns the 4 x 4 outputs (4 ti + p, 4 tj + q) and the 4-point quads split, split + 16, ...
-// of each chunk; the eight lanes of a quarter-warp read eight consecutive quads of the
-// same rows (16-byte loads, no bank conflicts).  Per chunk the products are summed in FP32
-// (16 points per output and thread), the chunk sums are carried across chunks as
-// double-float pairs (TwoSum), and the 16 splits are added in FP64 at the end.
-constexpr int kGsChunk = 256, kGsStages = 3, kGsThreads = 256, kGsSlots = 33;
+// 16 x 16 output groups, the ACE shapes 16 x 16 and 16 x 32).  The output is cut into
+// 16 x 16 groups (grid.y); a CTA streams chunks of 256 points of its 16 X rows, 16 Y rows
+// (and the weight row) into a 3-stage ring, each chunk as one 2-D TMA box per operand
+// (16 rows x 256 points; rows past na / nb and points past N arrive as zeros) completing
+// on the stage's mbarrier.  Thread (ti = warp & 3, tj = lane >> 3, split = lane & 7 +
+// 8 (warp >> 2)) owns the 4 x 4 outputs (4 ti + p, 4 tj + q) and the 4-point quads split,
+// split + 16, ... of each chunk; the eight lanes of a quarter-warp read eight consecutive
+// quads of the same rows (16-byte loads, no bank conflicts).  The products of a quad are
+// packed FP32x2 fused multiply-adds (even and odd points in the two halves); every two
+// chunks the FP32 sums are carried into double-float pairs (Knuth's TwoSum), and the 16
+// split lanes are combined as pairs too -- FP64 arithmetic is slow on this part.
+//
+// There is no CTA-wide barrier per chunk: every warp waits only for its chunk's mbarrier,
+// multiplies, and counts itself out of the stage on a shared counter; the warp that counts
+// out last (all eight have read the stage) re-arms the mbarrier and issues the chunk three
+// ahead into it, so warps drift apart by up to two chunks.  The stage of chunk j is
+// refilled only after every warp has finished chunk j, so no warp waits on a phase that has
+// been overtaken.  Every wait is bounded: on a timeout the CTA stops, waits (bounded) for
+// the copies it issued, writes NaN partials and raises RSX_ETIMEOUT in `status`.
+constexpr int kGsChunk = 256, kGsStages = 3, kGsFold = 2, kGsThreads = 256, kGsSlots = 33;
 
-__device__ __forceinline__ void gs_cp16(float* dst, const float* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
-               : "memory");
-}
-
-__global__ void __launch_bounds__(kGsThreads) k_gram_stream(const float* __restrict__ X, int na,
-                                                            const float* __restrict__ Y, int nb,
-                                                            const float* __restrict__ w, size_t N, int ngb,
-                                                            double* __restrict__ part) {
-  extern __shared__ __align__(16) float gs[];   // [stage][slot][kGsChunk]: X 0..15, Y 16..31, w 32
+template <int CHUNK, int STAGES, int FOLD>
+__global__ void __launch_bounds__(kGsThreads, 2) k_gram_stream(const float* __restrict__ X, int na,
+                                                              const float* __restrict__ Y, int nb,
+                                                              const float* __restrict__ w, size_t N, int ngb,
+                                                              double* __restrict__ part, int* status,
+                                                              const __grid_constant__ CUtensorMap map_x,
+                                                              const __grid_constant__ CUtensorMap map_y,
+                                                              const __grid_constant__ CUtensorMap map_w) {
+  extern __shared__ __align__(1024) float gstream[];   // [stage][slot][CHUNK], then STAGES mbarriers
+  float* gs = gstream;
+  uint64_t* full = reinterpret_cast<uint64_t*>(gs + (size_t)STAGES * kGsSlots * CHUNK);
+  __shared__ int abort_flag;
+  __shared__ unsigned out_count[STAGES];          // warps done with the stage, all uses so far
+  __shared__ unsigned long long issued;           // chunks whose copies have been issued
   const int gx = blockIdx.y / ngb, gy = blockIdx.y - gx * ngb;
   const int a_lo = 16 * gx, b_lo = 16 * gy;
   const int nra = min(16, na - a_lo), nrb = min(16, nb - b_lo);
-  const bool shared_rows = X == Y && a_lo == b_lo && w == nullptr;   // the Y rows are the X rows
+  const bool shared_rows = X == Y && a_lo == b_lo && w == nullptr;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ti = warp & 3, tj = lane >> 3, split = (lane & 7) + 8 * (warp >> 2);
   const int a0 = 4 * ti, b0 = 4 * tj;
-  const size_t nchunk = (N + kGsChunk - 1) / kGsChunk;
+  constexpr int kWarps = kGsThreads / 32;
+  const size_t nchunk = (N + CHUNK - 1) / CHUNK;
   const long long mine = blockIdx.x < nchunk ? (long long)((nchunk - 1 - blockIdx.x) / gridDim.x) + 1 : 0;
-  auto issue = [&](long long i) {
-    const size_t r0 = (blockIdx.x + (size_t)i * gridDim.x) * kGsChunk;
-    const int q4 = (int)min((size_t)kGsChunk, N - r0) >> 2;
-    float* base = gs + (size_t)(i % kGsStages) * kGsSlots * kGsChunk;
-    for (int e = threadIdx.x; e < kGsSlots * (kGsChunk / 4); e += kGsThreads) {
-      const int slot = e / (kGsChunk / 4), q = e - slot * (kGsChunk / 4);
-      if (q >= q4) continue;
-      const float* src = nullptr;
-      if (slot < 16) {
-        if (slot < nra) src = X + (size_t)(a_lo + slot) * N;
-      } else if (slot < 32) {
-        if (!shared_rows && slot - 16 < nrb) src = Y + (size_t)(b_lo + slot - 16) * N;
-      } else if (w) {
-        src = w;
-      }
-      if (src) gs_cp16(base + (size_t)slot * kGsChunk + 4 * q, src + r0 + 4 * q);
+  if (threadIdx.x == 0) {
+    abort_flag = 0;
+    issued = 0;
+    for (int st = 0; st < STAGES; ++st) {
+      tc::mbar_init(&full[st], 1);
+      out_count[st] = 0;
     }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+  auto issue = [&](long long i) {   // one whole warp
+    const size_t r0 = (blockIdx.x + (size_t)i * gridDim.x) * CHUNK;
+    float* base = gs + (size_t)(i % STAGES) * kGsSlots * CHUNK;
+    uint64_t* bar = &full[i % STAGES];
+    // whole boxes of 16 rows x CHUNK points (rows past the end and points past N read as 0)
+    if (lane == 0) {
+      const uint32_t box = 16u * CHUNK * 4u;
+      tc::mbar_arrive_expect_tx(bar, box * (shared_rows ? 1u : 2u) + (w ? CHUNK * 4u : 0u));
+      tc::tma_load_2d(base, &map_x, bar, (int)r0, a_lo);
+      if (!shared_rows) tc::tma_load_2d(base + 16 * CHUNK, &map_y, bar, (int)r0, b_lo);
+      if (w) tc::tma_load_2d(base + 32 * CHUNK, &map_w, bar, (int)r0, 0);
+      atomicMax(&issued, (unsigned long long)(i + 1));
+    }
+    __syncwarp();
   };
+  if (warp == 0)
+    for (int i = 0; i < STAGES && i < mine; ++i) issue(i);
   float ah[16], al[16];
+  float2 s2[16];
 #pragma unroll
   for (int o = 0; o < 16; ++o) ah[o] = al[o] = 0.f;
-#pragma unroll
-  for (int i = 0; i < kGsStages - 1; ++i) {
-    if (i < mine) issue(i);
-    asm volatile("cp.async.commit_group;" ::: "memory");
-  }
+  bool ok = true;
   for (long long i = 0; i < mine; ++i) {
-    if (i + kGsStages - 1 < mine) issue(i + kGsStages - 1);
-    asm volatile("cp.async.commit_group;" ::: "memory");
-    asm volatile("cp.async.wait_group %0;" ::"n"(kGsStages - 1) : "memory");
-    __syncthreads();
-    const size_t r0 = (blockIdx.x + (size_t)i * gridDim.x) * kGsChunk;
-    const int q4 = (int)min((size_t)kGsChunk, N - r0) >> 2;
-    const float* xs = gs + (size_t)(i % kGsStages) * kGsSlots * kGsChunk;
-    const float* ys = shared_rows ? xs : xs + 16 * kGsChunk;
-    const float* ws = xs + 32 * kGsChunk;
-    float sacc[16];
+    ok = tc::mbar_wait(&full[i % STAGES], (uint32_t)((i / STAGES) & 1), &abort_flag);
+    if (!ok) break;
+    const size_t r0 = (blockIdx.x + (size_t)i * gridDim.x) * CHUNK;
+    const int q4 = (int)min((size_t)CHUNK, N - r0) >> 2;
+    const float* xs = gs + (size_t)(i % STAGES) * kGsSlots * CHUNK;
+    const float* ys = shared_rows ? xs : xs + 16 * CHUNK;
+    const float* ws = xs + 32 * CHUNK;
+    if (i % FOLD == 0) {
 #pragma unroll
-    for (int o = 0; o < 16; ++o) sacc[o] = 0.f;
+      for (int o = 0; o < 16; ++o) s2[o] = make_float2(0.f, 0.f);
+    }
     for (int q = split; q < q4; q += 16) {
       float4 xv[4], yv[4];
 #pragma unroll
-      for (int p = 0; p < 4; ++p) xv[p] = *reinterpret_cast<const float4*>(xs + (a0 + p) * kGsChunk + 4 * q);
+      for (int p = 0; p < 4; ++p) xv[p] = *reinterpret_cast<const float4*>(xs + (a0 + p) * CHUNK + 4 * q);
 #pragma unroll
-      for (int p = 0; p < 4; ++p) yv[p] = *reinterpret_cast<const float4*>(ys + (b0 + p) * kGsChunk + 4 * q);
+      for (int p = 0; p < 4; ++p) yv[p] = *reinterpret_cast<const float4*>(ys + (b0 + p) * CHUNK + 4 * q);
       if (w) {
         const float4 wv = *reinterpret_cast<const float4*>(ws + 4 * q);
 #pragma unroll
-        for (int p = 0; p < 4; ++p) yv[p] = make_float4(yv[p].x * wv.x, yv[p].y * wv.y, yv[p].z * wv.z, yv[p].w * wv.w);
+        for (int p = 0; p < 4; ++p) {
+          const float2 lo = __fmul2_rn(make_float2(yv[p].x, yv[p].y), make_float2(wv.x, wv.y));
+          const float2 hi = __fmul2_rn(make_float2(yv[p].z, yv[p].w), make_float2(wv.z, wv.w));
+          yv[p] = make_float4(lo.x, lo.y, hi.x, hi.y);
+        }
       }
 #pragma unroll
       for (int p = 0; p < 4; ++p)
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
-          float acc = sacc[p * 4 + r];
-          acc = fmaf(xv[p].x, yv[r].x, acc);
-          acc = fmaf(xv[p].y, yv[r].y, acc);
-          acc = fmaf(xv[p].z, yv[r].z, acc);
-          acc = fmaf(xv[p].w, yv[r].w, acc);
-          sacc[p * 4 + r] = acc;
+          float2 acc = s2[p * 4 + r];
+          acc = __ffma2_rn(make_float2(xv[p].x, xv[p].y), make_float2(yv[r].x, yv[r].y), acc);
+          acc = __ffma2_rn(make_float2(xv[p].z, xv[p].w), make_float2(yv[r].z, yv[r].w), acc);
+          s2[p * 4 + r] = acc;
         }
     }
+    if (i % FOLD == FOLD - 1 || i == mine - 1) {
 #pragma unroll
-    for (int o = 0; o < 16; ++o) {   // TwoSum: (ah, al) += sacc
-      const float a = ah[o], b = sacc[o];
-      const float sm = a + b, bp = sm - a;
-      al[o] += (a - (sm - bp)) + (b - bp);
+      for (int o = 0; o < 16; ++o) {   // TwoSum: (ah, al) += the FP32 sum of FOLD chunks
+        const float a = ah[o], b = s2[o].x + s2[o].y;
+        const float sm = a + b, bp = sm - a;
+        al[o] += (a - (sm - bp)) + (b - bp);
+        ah[o] = sm;
+      }
+    }
+    // count this warp out of the stage; the last one refills it with chunk i + STAGES
+    __syncwarp();
+    unsigned before = 0;
+    if (lane == 0) {
+      __threadfence_block();
+      before = atomicAdd(&out_count[i % STAGES], 1u);
+    }
+    before = __shfl_sync(0xffffffffu, before, 0);
+    if (before % kWarps == kWarps - 1 && i + STAGES < mine) issue(i + STAGES);
+  }
+  const bool failed = __syncthreads_or(!ok);
+  if (failed) {
+    if (threadIdx.x == 0) {
+      // the last chunk issued into each stage may still be landing
+      const long long last = (long long)issued;
+      for (long long j = max(0ll, last - STAGES); j < last; ++j)
+        for (uint32_t it = 0; it < tc::kWaitLimit; ++it)
+          if (tc::mbar_try_wait(&full[j % STAGES], (uint32_t)((j / STAGES) & 1))) break;
+      if (status) atomicMax(status, RSX_ETIMEOUT);
+    }
+    __syncthreads();
+    const int a = threadIdx.x >> 4, b = threadIdx.x & 15;
+    if (a < nra && b < nrb)
+      part[(size_t)blockIdx.x * na * nb + (size_t)(a_lo + a) * nb + (b_lo + b)] = __longlong_as_double(0x7ff8000000000000ll);
+    return;
+  }
+#pragma unroll
+  for (int o = 0; o < 16; ++o)
+#pragma unroll
+    for (int m = 1; m < 8; m <<= 1) {
+      const float bh = __shfl_xor_sync(0xffffffffu, ah[o], m), bl = __shfl_xor_sync(0xffffffffu, al[o], m);
+      const float sm = ah[o] + bh, bp = sm - ah[o];
+      al[o] += bl + ((ah[o] - (sm - bp)) + (bh - bp));
       ah[o] = sm;
     }
-    __syncthreads();   // this stage is refilled by the next issue
-  }
-  asm volatile("cp.async.wait_group 0;" ::: "memory");
-  double acc[16];
-#pragma unroll
-  for (int o = 0; o < 16; ++o) {
-    acc[o] = (double)ah[o] + (double)al[o];
-    for (int m = 1; m < 8; m <<= 1) acc[o] += __shfl_xor_sync(0xffffffffu, acc[o], m);
-  }
-  __syncthreads();
-  double* red = reinterpret_cast<double*>(gs);   // [2][16][16]
+  float2* red = reinterpret_cast<float2*>(gs);   // [2][16][16] (h, l); every copy has landed
   if ((lane & 7) == 0) {
 #pragma unroll
     for (int p = 0; p < 4; ++p)
 #pragma unroll
-      for (int r = 0; r < 4; ++r) red[((warp >> 2) * 16 + a0 + p) * 16 + b0 + r] = acc[p * 4 + r];
+      for (int r = 0; r < 4; ++r)
+        red[((warp >> 2) * 16 + a0 + p) * 16 + b0 + r] = make_float2(ah[p * 4 + r], al[p * 4 + r]);
   }
   __syncthreads();
   const int a = threadIdx.x >> 4, b = threadIdx.x & 15;
-  if (a < nra && b < nrb)
-    part[(size_t)blockIdx.x * na * nb + (size_t)(a_lo + a) * nb + (b_lo + b)] = red[a * 16 + b] + red[256 + a * 16 + b];
+  if (a < nra && b < nrb) {
+    const float2 u = red[a * 16 + b], v = red[256 + a * 16 + b];
+    part[(size_t)blockIdx.x * na * nb + (size_t)(a_lo + a) * nb + (b_lo + b)] =
+        ((double)u.x + (double)v.x) + ((double)u.y + (double)v.y);
+  }
+}
+
+// 2-D tensor map of `rows` rows of N floats, boxes of box_rows x chunk
+static bool gram_map(CUtensorMap* m, const float* base, int rows, size_t N, int box_rows, int chunk) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)N, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)N * 4};
+  cuuint32_t box[2] = {(cuuint32_t)chunk, (cuuint32_t)box_rows};
+  cuuint32_t es[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// cudaErrorNotSupported when the tensor maps cannot be encoded (the caller takes the staged kernel)
+static cudaError_t launch_gram_stream(const float* X, int na, const float* Y, int nb, size_t N, double* part,
+                                      int nblk, cudaStream_t s, const float* w, int* status) {
+  const int ngb = (nb + 15) / 16, ngrp = ((na + 15) / 16) * ngb;
+  CUtensorMap mx{}, my{}, mw{};
+  if (!gram_map(&mx, X, na, N, 16, kGsChunk) || !gram_map(&my, Y, nb, N, 16, kGsChunk) ||
+      (w && !gram_map(&mw, w, 1, N, 1, kGsChunk)))
+    return cudaErrorNotSupported;
+  const size_t smem = sizeof(float) * (size_t)kGsStages * kGsSlots * kGsChunk + 8 * kGsStages;
+  auto kern = k_gram_stream<kGsChunk, kGsStages, kGsFold>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<dim3(nblk, ngrp), kGsThreads, smem, s>>>(X, na, Y, nb, w, N, ngb, part, status, mx, my, mw);
+  return cudaGetLastError();
 }
 
 template <typename R>
 cudaError_t launch_gram(const R* X, int na, const R* Y, int nb, size_t N, double* part, int nblk,
-                        cudaStream_t s, const R* w) {
+                        cudaStream_t s, const R* w, int* status) {
   if (na * nb > 16 * kGramThreads) return cudaErrorInvalidValue;
   if constexpr (sizeof(R) == 4) {
     auto al16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
@@ -675,11 +773,8 @@ cudaError_t launch_gram(const R* X, int na, const R* Y, int nb, size_t N, double
     // each 16 x 16 group streams its own rows: worth it for one or two groups (the ACE
     // shapes 16 x 16, 16 x 32); wider bases keep the staged kernel, which reads every row once
     if (N % 4 == 0 && al16(X) && al16(Y) && (w == nullptr || al16(w)) && nga * ngb <= 2) {
-      const size_t smem = sizeof(float) * (size_t)kGsStages * kGsSlots * kGsChunk;
-      cudaError_t e = cudaFuncSetAttribute(k_gram_stream, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-      k_gram_stream<<<dim3(nblk, nga * ngb), kGsThreads, smem, s>>>(X, na, Y, nb, w, N, ngb, part);
-      return cudaGetLastError();
+      const cudaError_t e = launch_gram_stream(X, na, Y, nb, N, part, nblk, s, w, status);
+      if (e != cudaErrorNotSupported) return e;
     }
   }
   const bool sym = X == Y && na == nb && w == nullptr;
@@ -706,7 +801,7 @@ cudaError_t launch_gram(const R* X, int na, const R* Y, int nb, size_t N, double
 template <typename R>
 cudaError_t launch_gram_reduce(const double* part, int nblk, int na, int nb, double scale, bool transpose,
                                double* out, R* out_r, cudaStream_t s, int ldo) {
-  k_gram_reduce<R><<<(na * nb + 31) / 32, 256, 0, s>>>(part, nblk, na, nb, scale, transpose ? 1 : 0, out,
+  k_gram_reduce<R><<<(na * nb + 31) / 32, 32 * kRedGroups, 0, s>>>(part, nblk, na, nb, scale, transpose ? 1 : 0, out,
                                                         out_r, ldo);
   return cudaGetLastError();
 }
@@ -755,7 +850,7 @@ cudaError_t launch_pair_products(const R* A, int na, const R* B, int nb, size_t 
 
 #define RSX_INST(R)                                                                                        \
   template cudaError_t launch_gram<R>(const R*, int, const R*, int, size_t, double*, int, cudaStream_t,   \
-                                      const R*);                                                          \
+                                      const R*, int*);                                                          \
   template cudaError_t launch_gram_reduce<R>(const double*, int, int, int, double, bool, double*, R*,      \
                                              cudaStream_t, int);                                          \
   template cudaError_t launch_combine<R>(const R*, int, int, const R*, size_t, R*, int, cudaStream_t);     \

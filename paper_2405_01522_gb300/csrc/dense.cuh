@@ -13,10 +13,11 @@ cudaError_t launch_ghat(const Geom& g, double h, double scale, const double* cos
 cudaError_t launch_vhat_lanes(const Geom& g, const float* table, float* out, cudaStream_t s);
 // the kernel table in the 8-lane y/z kernel's order [kx][|ky|][s][j][k2], kz = (s + 8 j) + 2 Az k2
 cudaError_t launch_vhat_lanes8(const Geom& g, const float* table, float* out, cudaStream_t s);
-// part[blk][a][b] = partial sums of X_a(r) Y_b(r) w(r) (w may be null); na * nb <= 4096
+// part[blk][a][b] = partial sums of X_a(r) Y_b(r) w(r) (w may be null); na * nb <= 4096.
+// A kernel that gives up a bounded wait writes NaN partials and raises RSX_ETIMEOUT in *status.
 template <typename R>
 cudaError_t launch_gram(const R* X, int na, const R* Y, int nb, size_t N, double* part, int nblk,
-                        cudaStream_t s, const R* w = nullptr);
+                        cudaStream_t s, const R* w = nullptr, int* status = nullptr);
 // out[a * ldo + b] (or out[b * ldo + a] when transpose) = scale * sum of the partials
 template <typename R>
 cudaError_t launch_gram_reduce(const double* part, int nblk, int na, int nb, double scale, bool transpose,

@@ -269,9 +269,7 @@ __global__ void k_syrk_reduce(const double* __restrict__ part, int n, int nb, in
   }
 }
 
-typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+}  // namespace
 
 EncodeTiledFn encode_fn() {
   static EncodeTiledFn fn = nullptr;
@@ -287,6 +285,8 @@ EncodeTiledFn encode_fn() {
   }
   return fn;
 }
+
+namespace {
 
 // 2-D view of a panel: row-major [rows][ld], or tile-major as [rows * ld / 64][64]
 bool make_map(CUtensorMap* m, const void* base, int rows, long long ld, bool blocked) {

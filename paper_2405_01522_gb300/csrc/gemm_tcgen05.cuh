@@ -1,5 +1,6 @@
 // Split-BF16 symmetric contraction on tcgen05 tensor cores (gemm_tcgen05.cu).
 #pragma once
+#include <cuda.h>
 #include <cstdint>
 
 #include "rsx_internal.cuh"
@@ -7,6 +8,11 @@
 struct rsx_ctx;
 
 namespace rsx {
+// cuTensorMapEncodeTiled from the driver (null if the driver does not provide it)
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_fn();
 // number of K splits for an n x n output on nsm SMs (about one CTA per SM)
 int syrk_splits(int nsm, int n);
 // bytes of the FP32 split partials

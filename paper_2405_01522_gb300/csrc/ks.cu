@@ -972,7 +972,7 @@ int gram(rsx_eig* e, const float* X, int na, const float* Y, int nb, const float
   const size_t N = (size_t)e->n * e->n * e->n;
   int rc = grow(c, (void**)&c->dsm, &c->dsm_bytes, sizeof(double) * ((size_t)nblk * 4096 + 3 * 4096), "small FP64");
   if (rc) return rc;
-  rc = check_cuda(c, launch_gram<float>(X, na, Y, nb, N, c->dsm, nblk, s, w), "gram");
+  rc = check_cuda(c, launch_gram<float>(X, na, Y, nb, N, c->dsm, nblk, s, w, c->status), "gram");
   if (rc) return rc;
   return check_cuda(c, launch_gram_reduce<float>(c->dsm, nblk, na, nb, e->h * e->h * e->h, false, out, (float*)nullptr, s),
                     "gram reduce");

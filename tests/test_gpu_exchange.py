@@ -232,3 +232,37 @@ def test_fp32_eight_lane_split_of_the_yz_pass(shape, h, nocc, npsi):
     vphi = ctx.ace_apply(xi, phi)
     ctx.sync()
     assert rel_max_err(vphi.double().cpu().numpy(), w.double().cpu().numpy()) < 3e-5
+
+
+GRAM_CASES = [
+    ((96, 96, 96), 16, 16, False),   # the ACE shape: one 16 x 16 group, TMA-streamed
+    ((96, 96, 96), 16, 16, True),    # <phi, phi>: the Y rows are the X rows
+    ((96, 96, 96), 16, 32, False),   # two groups
+    ((48, 48, 48), 13, 7, False),    # rows past na / nb read as zeros by the tensor map
+    ((16, 16, 24), 5, 6, False),     # a single partial group
+    ((24, 24, 24), 48, 40, False),   # more than two groups: the staged kernel
+]
+# (Context edges are multiples of 8, so N is a multiple of the 256-point chunk here; the
+# ragged last chunk is exercised by the eigensolver's Grams at n = 12.)
+
+
+@pytest.mark.parametrize("shape,na,nb,same", GRAM_CASES)
+def test_gram_vs_fp64_products(shape, na, nb, same):
+    """rsx_gram C_ij = h^3 <a_i, b_j> of FP32 rows against the FP64 sum of the same FP32
+    values.  The bound is the accumulation error of FP32 products summed in FP32 over 32
+    points before double-float accumulation: 4e-6 of h^3 sum_r |a_i(r) b_j(r)|."""
+    need_gpu()
+    h = 0.3
+    rng = np.random.default_rng(na * 100 + nb)
+    a = rng.standard_normal((na,) + shape).astype(np.float32)
+    b = a if same else rng.standard_normal((nb,) + shape).astype(np.float32)
+    ctx = rsx.Context(shape, h, "fp32")
+    ad = torch.from_numpy(a).cuda()
+    bd = ad if same else torch.from_numpy(b).cuda()
+    C = ctx.gram(ad, bd).cpu().numpy()
+    ctx.sync()
+    A, B = a.reshape(na, -1).astype(np.float64), b.reshape(b.shape[0], -1).astype(np.float64)
+    ref = h ** 3 * (A @ B.T)
+    scale = h ** 3 * (np.abs(A) @ np.abs(B).T)
+    assert np.all(np.abs(C - ref) <= 4e-6 * scale), np.max(np.abs(C - ref) / scale)
+    ctx.close()

@@ -850,12 +850,15 @@ __global__ void __launch_bounds__(kThreads) k_pass3(Geom g, PairMap<R> pm, int q
                                                     const Cx<R>* __restrict__ inter,
                                                     const Cx<R>* __restrict__ twx, R* __restrict__ out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  // outputs are the fastest index: the CTAs in flight share (z, row block), so the partner
+  // rows they multiply come from HBM once and then from L2 for the other outputs
   const int nyb = (g.ny + kRowsPerCta - 1) / kRowsPerCta;
+  const int np = (int)(gridDim.x / ((unsigned)g.nz * nyb));
   int b = blockIdx.x;
+  const int pl = b % np;
+  b /= np;
   const int yblk = b % nyb;
-  b /= nyb;
-  const int z = b % g.nz;
-  const int pl = b / g.nz;
+  const int z = b / nyb;
   pass3_item<R, AX>(g, pm, q0, p0 + pl, z, yblk, pot, inter, twx, pm.out_row(p0 + pl, out, pl), smem_raw);
 }
 

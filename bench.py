@@ -369,12 +369,25 @@ def run_rsx(args, rank, local_rank, world):
         g = ctx.profile_read().get("gram")
         gram_us[label] = round(g[0] / g[1] * 1e3, 1) if g else None
 
+    # step-level HBM view against the per-solve byte model of a plane-pass design (orbital
+    # rows read in the first and last pass, the 2x-padded-in-y intermediate written and read
+    # twice: 3.54 + 4 x 14.30 + 3.54 MB at 96^3); this design moves fewer bytes per solve
+    nz_, ny_, nx_ = shape
+    model_bytes = 2 * nz_ * ny_ * nx_ * 4 + 4 * (nx_ + 1) * nz_ * (2 * ny_) * 8
+    model_gbs = value * model_bytes / 1e9
+    step_model = {"bytes_per_solve": model_bytes, "effective_gbs": round(model_gbs, 1),
+                  "frac_of_measured_hbm": round(model_gbs / hbm_peak, 4),
+                  "what": "solves/s x the per-solve HBM bytes of a plane-pass design (orbital rows read twice, "
+                          "four passes over a (Mx/2 + 1) x nz x 2 ny complex intermediate)"}
+    logical = SOLVES_EXCHANGE + NOCC * NOCC   # the ACE build's rho_ij and rho_ji counted separately
     out = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": bench_config(shape, world),
            "tuning": tuning, "roofline": roof, "kernels": kernels, "gpu_launches": launches, "clocks": clk, "e2e": e2e,
-           "ace_build_ms": round(ace_ms, 4), "gram_kernel_us": gram_us}
+           "ace_build_ms": round(ace_ms, 4), "gram_kernel_us": gram_us, "step_model_hbm": step_model,
+           "solves_logical": {"per_step": logical, "per_s": round(value * logical / SOLVES_PER_STEP, 1),
+                              "what": "the ACE build's 16 x 16 pair potentials counted as 256 (136 unique)"}}
 
     # ---- FP64 plain form of the same step, and FP32 accuracy against it
     if not args.skip_fp64 and rank == 0:

@@ -707,7 +707,8 @@ def precond_bench(args, dev, local_rank):
             "learned": {"iters_to_target": il, "time_to_target_s": None if tl is None else round(tl, 3),
                         "iters_to_1e-5": il5, "time_to_1e-5_s": None if tl5 is None else round(tl5, 3),
                         "final_energy_ha": learned["energy"], "min_energy_ha": min(learned["trace"]),
-                        "iters": learned["iters"], "s_per_iter": round(learned["time_s"] / learned["iters"], 5)},
+                        "iters": learned["iters"], "s_per_iter": round(learned["time_s"] / learned["iters"], 5),
+                        "fell_back_at": learned["fell_back_at"]},
             "final_energy_diff_ha": abs(learned["energy"] - plain["energy"]),
             "conv_forward_tflops": round(fwd_tflops, 2), "conv_train_step_tflops": round(train_tflops, 2),
             "total_s": round(time.perf_counter() - t_all, 1)}

@@ -11,8 +11,10 @@ kernels on (residual -> correction) pairs the plain solver generates:
   psi_i into the converged subspace).
 
 In the solver the network adds directions |R_i| net(R_i/|R_i|, vscale V) next to the plain
-ones, so the Rayleigh-Ritz step can only gain from them; the plain preconditioner stays
-as the fallback and as the reference for convergence (same energy to 1e-6 Ha).
+ones (taking the place of the LOBPCG P block where the basis would not hold both); the
+plain preconditioner stays as the reference for convergence (same energy to 1e-6 Ha) and
+as the fallback: a learned run whose energy stops falling (no new minimum by more than the
+tolerance within `fallback_patience` steps) drops the network and continues plain.
 """
 import time
 
@@ -34,8 +36,16 @@ def init_params(seed=0):
     return np.concatenate(out)
 
 
+def should_fall_back(trace, patience, tol):
+    """True when none of the last `patience` energies is below the best energy before them
+    by more than tol (the learned directions have stopped paying for themselves)."""
+    if patience <= 0 or len(trace) <= patience:
+        return False
+    return min(trace[-patience:]) > min(trace[:-patience]) - tol
+
+
 def solve(V, h, psi0, nband, net=None, tol=1e-6, max_iter=400, sweeps=3, vscale=1.0, record_every=0,
-          energy64=False):
+          energy64=False, fallback_patience=8):
     """Run the block eigensolver until |E_k - E_{k-1}| < tol.
 
     E is the sum of the step's Ritz values, or with energy64 the block's energy evaluated
@@ -43,13 +53,15 @@ def solve(V, h, psi0, nband, net=None, tol=1e-6, max_iter=400, sweeps=3, vscale=
     values; its cost is left out of the times).  Returns a dict with iterations, energy,
     Ritz values, solver wall time (s), the energy trace with the elapsed solver time at
     each entry and, with record_every > 0, a list of (psi_it, R_it) device tensors every
-    that many iterations (psi before the step, R the residual the step used)."""
+    that many iterations (psi before the step, R the residual the step used).  With a
+    network, `fell_back_at` is the iteration after which it was dropped (None: never)."""
     es = rsx.Eigensolver(V, h, nband, vscale=vscale, device=V.device.index or 0)
     es.init(psi0)
     torch.cuda.synchronize()
     trace, rec, times, trace32 = [], [], [], []
     elapsed = 0.0
     E_prev, th, it = None, None, 0
+    fell_back_at = None
     for it in range(1, max_iter + 1):
         psi_before = es.orbitals() if record_every and it % record_every == 1 else None
         t0 = time.perf_counter()
@@ -64,12 +76,14 @@ def solve(V, h, psi0, nband, net=None, tol=1e-6, max_iter=400, sweeps=3, vscale=
         if E_prev is not None and abs(E - E_prev) < tol:
             break
         E_prev = E
+        if net is not None and should_fall_back(trace, fallback_patience, tol):
+            net, fell_back_at = None, it
     torch.cuda.synchronize()
     dt = elapsed
     psi = es.orbitals()
     es.close()
     return {"iters": it, "energy": trace[-1], "theta": th, "time_s": dt, "trace": trace, "times": times,
-            "trace32": trace32, "records": rec, "psi": psi}
+            "trace32": trace32, "records": rec, "psi": psi, "fell_back_at": fell_back_at}
 
 
 def time_to_target(res, e_ref, tol=1e-6):

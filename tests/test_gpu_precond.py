@@ -88,6 +88,13 @@ def test_learned_preconditioner_pipeline_small():
     assert np.isfinite(losses).all() and losses[-1] < losses[0]
     learned = precond.solve(V, h, psi0, nb, net=net, tol=1e-7, vscale=vscale)
     assert abs(learned["energy"] - plain["energy"]) < 1e-5
+    # the fallback rule ran alongside: either it never fired, or the run went on plain
+    fb = learned["fell_back_at"]
+    assert fb is None or 1 <= fb <= learned["iters"]
+    # with no patience at all the network is dropped after the first step without a new
+    # minimum; the run still ends at the plain energy
+    quick = precond.solve(V, h, psi0, nb, net=net, tol=1e-7, vscale=vscale, fallback_patience=1)
+    assert abs(quick["energy"] - plain["energy"]) < 1e-5
 
 
 def test_energy64_is_the_rayleigh_ritz_trace_of_the_dense_hamiltonian():

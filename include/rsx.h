@@ -407,7 +407,10 @@ const char* rsx_kernel_name(int kernel);
  *   more successful ones fail with RSX_ENOMEM without touching the device (once);
  *   RSX_FAULT_PIVOT makes the next rsx_ace_build factorise the ACE matrix with its sign
  *   flipped, so that the FP64 Cholesky meets a non-positive pivot and rsx_sync_status
- *   reports RSX_ENOTPD (once); RSX_FAULT_NONE clears both.  Errors: RSX_EINVAL. */
+ *   reports RSX_ENOTPD (once); RSX_FAULT_NONE clears both.  Errors: RSX_EINVAL.
+ *   The same faults can be armed for every context a process creates through the
+ *   environment: RSX_INJECT_FAULT=alloc:N or RSX_INJECT_FAULT=pivot, read at the end of
+ *   rsx_create (the count starts after the context's own set-up allocations). */
 enum { RSX_FAULT_NONE = 0, RSX_FAULT_ALLOC = 1, RSX_FAULT_PIVOT = 2 };
 int rsx_set_wait_limit(rsx_ctx* ctx, long long spins);
 int rsx_inject_fault(rsx_ctx* ctx, int kind, int after);

@@ -455,6 +455,13 @@ int rsx_create(rsx_ctx** out, int nz, int ny, int nx, double h, int precision, i
     rsx_destroy(c);
     return rc;
   }
+  // host-side fault injection from the environment, armed once the context exists (the
+  // same faults as rsx_inject_fault): RSX_INJECT_FAULT=alloc:N (the workspace allocation
+  // after N successful ones fails) or pivot
+  if (const char* e = getenv("RSX_INJECT_FAULT")) {
+    if (strncmp(e, "alloc:", 6) == 0 && atoi(e + 6) >= 0) c->fault_alloc_after = atoi(e + 6);
+    if (strcmp(e, "pivot") == 0) c->fault_pivot = true;
+  }
   *out = c;
   return RSX_OK;
 }

@@ -79,3 +79,28 @@ def test_injected_bad_pivot_is_reported_as_not_positive_definite():
     xi = ctx.ace_build(phi)                      # once only: the next build is correct
     ctx.sync()
     assert rel_max_err(xi.cpu().numpy(), oracle.ace_build(s.phi, h)) < 1e-10
+
+
+def test_faults_armed_from_the_environment(monkeypatch):
+    """RSX_INJECT_FAULT, read by rsx_create: alloc:0 fails the first workspace allocation,
+    pivot makes the first ACE build report RSX_ENOTPD; both fire once."""
+    need_gpu()
+    shape, h = (24, 24, 24), 0.35
+    s = inputs.exchange_system(h=h, nocc=3, npsi=2, shape=shape, radius=1.5, seed=4)
+    monkeypatch.setenv("RSX_INJECT_FAULT", "alloc:0")
+    ctx = rsx.Context(shape, h, "fp32")
+    phi, psi = to_dev(s.phi, "fp32"), to_dev(s.psi, "fp32")
+    with pytest.raises(rsx.RsxError) as err:
+        ctx.exchange_apply(phi, psi)
+    assert err.value.code == rsx.RSX_ENOMEM
+    out = ctx.exchange_apply(phi, psi)
+    ctx.sync()
+    assert rel_max_err(out.double().cpu().numpy(), oracle.exchange_apply(s.phi, s.psi, h)) < TOL["fp32"]
+    monkeypatch.setenv("RSX_INJECT_FAULT", "pivot")
+    ctx2 = rsx.Context(shape, h, "fp32")
+    ctx2.ace_build(phi)
+    with pytest.raises(rsx.RsxError) as err:
+        ctx2.sync()
+    assert err.value.code == rsx.RSX_ENOTPD
+    ctx2.ace_build(phi)
+    ctx2.sync()

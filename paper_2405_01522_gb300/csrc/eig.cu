@@ -384,18 +384,26 @@ __global__ void __launch_bounds__(256) k_tridiag_coop(F* __restrict__ A, int n, 
 // ---------------------------------------------------------------------------------
 // Householder tridiagonalisation on one thread-block cluster (same reflectors and outputs
 // as k_tridiagonalise).  The matrix lives in the CTAs' shared memory: rows dealt
-// cyclically (row i in CTA i % CS, local row i / CS); v, p/w and the per-CTA partial sums
-// are replicated in every CTA, which writes its own entries into all the others through
-// distributed shared memory.  Per step three hardware cluster barriers separate
-// (norm partials -> v) -> (p = tau A22 v, p^T v partials) -> (rank-2 update of own rows,
-// next column's norm partials).  The rows are copied back to global memory at the end
-// (the reflectors below the subdiagonal, for the back-transformation).
+// cyclically (row i in CTA i % CS, local row i / CS).  Every CTA holds a replica of the
+// current column (below the diagonal), from which it forms the norm, tau and v itself; p
+// and the p^T v partials go to every CTA through distributed shared memory.  Per step two
+// hardware cluster barriers separate (v from the replicated column; p = tau A22 v on own
+// rows, sent to all) -> (w = p - (tau/2)(p^T v) v, rank-2 update of own rows, their new
+// next-column entries sent to all).  The rows are copied back to global memory at the
+// end (the reflectors below the subdiagonal, for the back-transformation).
 constexpr int kClThreads = 512;
 namespace cg = cooperative_groups;
 
+// shared-memory values of k_tridiag_cluster (rows unless GROWS, v, p, two column replicas,
+// the p^T v partials)
+template <typename F>
+inline size_t tridiag_cluster_smem(int n, int CS, bool grows) {
+  return ((grows ? 0 : ((size_t)(n + CS - 1) / CS) * n) + 4 * (size_t)n + CS) * sizeof(F);
+}
+
 // GROWS: the owned rows stay in global memory (rows of A, L2-resident) instead of
-// distributed shared memory, for n too large for the latter; only v, p and the partials
-// go through DSMEM.  A CTA only ever touches the rows it owns.
+// distributed shared memory, for n too large for the latter; only p, the columns and the
+// partials go through DSMEM.  A CTA only ever touches the rows it owns.
 template <typename F, bool GROWS>
 __global__ void __launch_bounds__(kClThreads) k_tridiag_cluster(F* __restrict__ A, int n, F* __restrict__ d,
                                                                 F* __restrict__ e, F* __restrict__ tau) {
@@ -409,11 +417,10 @@ __global__ void __launch_bounds__(kClThreads) k_tridiag_cluster(F* __restrict__ 
   F* R = cl_smem;                               // [nloc][n] (shared-memory rows)
   F* v = GROWS ? cl_smem : R + (size_t)((n + CS - 1) / CS) * n;   // [n]
   F* p = v + n;                                 // [n] (p, then w)
-  F* part = p + n;                              // [CS] norm partials, [CS] p^T v partials, alpha
-  F* part2 = part + CS;
-  F* alpha_sl = part2 + CS;
+  F* colb = p + n;                              // [2][n]: column k (and k + 1) replicas
+  F* part2 = p + 3 * n;                         // [CS] p^T v partials
   __shared__ F red[kClThreads / 32];
-  __shared__ F sh_tau, sh_beta, sh_scale;
+  __shared__ F sh_tau, sh_scale;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = kClThreads / 32;
   auto grow = [&](int li) { return me + li * CS; };
   auto rowp = [&](int li) -> F* { return GROWS ? A + (size_t)grow(li) * lda : R + (size_t)li * n; };
@@ -438,61 +445,49 @@ __global__ void __launch_bounds__(kClThreads) k_tridiag_cluster(F* __restrict__ 
     __syncthreads();
     return t;
   };
-  // publish this CTA's partial (and alpha when it owns row m0 + 1) for column c
-  auto publish_norm = [&](int c) {
-    F s = F(0);
-    for (int li = tid; li < nloc; li += kClThreads) {
+  // own rows' entries i >= r0 of column c, sent to every CTA's replica
+  auto send_column = [&](int c, int r0, F* dst) {
+    for (int q = tid; q < nloc * CS; q += kClThreads) {
+      const int li = q / CS, to = q - li * CS;
       const int i = grow(li);
-      if (i >= c + 2) s += rowp(li)[c] * rowp(li)[c];
+      if (i >= r0) *cl.map_shared_rank(dst + i, to) = rowp(li)[c];
     }
-    const F t = block_sum0(s);
-    if (tid == 0) red[0] = t;
-    __syncthreads();
-    const F tot = red[0];
-    if (tid < CS) *cl.map_shared_rank(part + me, tid) = tot;
-    if ((c + 1) % CS == me && tid >= 32 && tid < 32 + CS)
-      *cl.map_shared_rank(alpha_sl, tid - 32) = rowp((c + 1) / CS)[c];
   };
-  if (n > 2) publish_norm(0);
+  if (n > 2) send_column(0, 1, colb);
   cl.sync();
   for (int k = 0; k + 2 < n; ++k) {
     const int m0 = k + 1;
-    if (warp == 0) {
-      F xn2 = lane < CS ? part[lane] : F(0);
-      for (int o = 16; o > 0; o >>= 1) xn2 += __shfl_xor_sync(0xffffffffu, xn2, o);
-      if (lane == 0) {
-        const F alpha = *alpha_sl;
-        if (xn2 == F(0)) {
-          sh_tau = F(0);
-          sh_beta = alpha;
-          sh_scale = F(0);
-        } else {
-          // beta = -sign(alpha) |x|, tau = (beta - alpha) / beta = 1 + |alpha| / |x|:
-          // one reciprocal square root and one division
-          const F s2 = alpha * alpha + xn2, rs = rsq(s2);
-          const F beta = -copysign(s2 * rs, alpha);
-          sh_tau = F(1) + fabs(alpha) * rs;
-          sh_scale = F(1) / (alpha - beta);
-          sh_beta = beta;
-        }
-        if (me == 0) {
-          e[k] = sh_beta;
-          tau[k] = sh_tau;
-        }
-        if (k % CS == me) d[k] = rowp(k / CS)[k];
+    const F* col = colb + (size_t)(k & 1) * n;
+    // norm of the column below the subdiagonal and alpha = A[m0][k], from the replica
+    F s2 = F(0);
+    for (int j = m0 + 1 + tid; j < n; j += kClThreads) s2 += col[j] * col[j];
+    const F xn2 = block_sum0(s2);
+    if (tid == 0) {
+      const F alpha = col[m0];
+      F beta;
+      if (xn2 == F(0)) {
+        sh_tau = F(0);
+        beta = alpha;
+        sh_scale = F(0);
+      } else {
+        // beta = -sign(alpha) |x|, tau = (beta - alpha) / beta = 1 + |alpha| / |x|:
+        // one reciprocal square root and one division
+        const F s = alpha * alpha + xn2, rs = rsq(s);
+        beta = -copysign(s * rs, alpha);
+        sh_tau = F(1) + fabs(alpha) * rs;
+        sh_scale = F(1) / (alpha - beta);
       }
+      if (me == 0) {
+        e[k] = beta;
+        tau[k] = sh_tau;
+      }
+      if (k % CS == me) d[k] = rowp(k / CS)[k];
     }
     __syncthreads();
     const F tk = sh_tau, sc = sh_scale;
-    // v on own rows (stored in the column), sent to every CTA
-    for (int q = tid; q < nloc * CS; q += kClThreads) {
-      const int li = q / CS, dst = q - li * CS;
-      const int i = grow(li);
-      if (i < m0) continue;
-      const F vi = (i == m0) ? F(1) : rowp(li)[k] * sc;
-      *cl.map_shared_rank(v + i, dst) = vi;
-    }
-    cl.sync();
+    // v (every entry, from the replica); own rows keep theirs as the reflector
+    for (int j = m0 + tid; j < n; j += kClThreads) v[j] = (j == m0) ? F(1) : col[j] * sc;
+    __syncthreads();
     for (int li = tid; li < nloc; li += kClThreads) {
       const int i = grow(li);
       if (i > m0) rowp(li)[k] = v[i];
@@ -537,9 +532,10 @@ __global__ void __launch_bounds__(kClThreads) k_tridiag_cluster(F* __restrict__ 
       }
       __syncthreads();
     } else {
-      cl.sync();   // matches the p-broadcast barrier of the other branch (tau is the same everywhere)
+      cl.sync();   // matches the p barrier of the other branch (tau is the same everywhere)
     }
-    if (m0 + 2 < n) publish_norm(m0);
+    // the next column's entries below its diagonal, to every replica
+    if (m0 + 2 < n) send_column(m0, m0 + 1, colb + (size_t)((k + 1) & 1) * n);
     cl.sync();
   }
   // last 2 x 2 block, rows back to global memory
@@ -771,7 +767,7 @@ static int tridiagonalise(rsx_ctx* c, F* A, int n, F* d, F* e, F* tau, F* scr, F
   const std::string force = fp ? fp : "";
   auto try_cluster = [&](int CS, bool grows) -> int {   // -1: not possible here
     if (n < 64) return -1;
-    const size_t smem = ((grows ? 0 : ((size_t)(n + CS - 1) / CS) * n) + 2 * (size_t)n + 2 * CS + 1) * sizeof(F);
+    const size_t smem = tridiag_cluster_smem<F>(n, CS, grows);
     if (smem > (size_t)227 * 1024) return -1;
     auto kern = grows ? k_tridiag_cluster<F, true> : k_tridiag_cluster<F, false>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||

@@ -145,10 +145,11 @@ __global__ void __launch_bounds__(kEigThreads) k_tridiagonalise(double* __restri
 
 // ---------------------------------------------------------------------------------
 // Multi-CTA Householder tridiagonalisation (same reflectors and outputs as
-// k_tridiagonalise).  Rows are dealt cyclically to the CTAs; per step three grid-wide
-// barriers separate (v) -> (p = tau A22 v, p^T v partials) -> (rank-2 update of own rows
-// and the next column's norm partials).  The kernel is launched cooperatively so that
-// all CTAs are resident; the barrier itself is bounded and raises RSX_ETIMEOUT.
+// k_tridiagonalise).  Rows are dealt cyclically to the CTAs; per step two grid-wide
+// barriers separate (v from the whole current column, p = tau A22 v on own rows, p^T v
+// partials) -> (rank-2 update of own rows and their entries of the next column).  The
+// kernel is launched cooperatively so that all CTAs are resident; the barrier itself is
+// bounded and raises RSX_ETIMEOUT.
 constexpr uint32_t kGridWaitLimit = 1u << 24;
 
 struct GridBar {
@@ -231,7 +232,10 @@ __device__ __forceinline__ F cta_sum_partials(const F* part, unsigned int G, F* 
   return *out_sh;
 }
 
-// scratch layout (Fs): v[n], p[n], part_norm[G], part_pv[G], alpha
+// scratch layout (Fs): p[n], the current and the next column [2][n], part_pv[G].  Every
+// CTA reads the whole current column (below the diagonal) from L2 and forms the norm, tau
+// and v itself, so a step needs two grid barriers: (v; p = tau A22 v on own rows, p^T v
+// partials) -> (w, rank-2 update of own rows, their entries of the next column).
 template <typename F>
 __global__ void __launch_bounds__(256) k_tridiag_coop(F* __restrict__ A, int n, F* __restrict__ d,
                                                       F* __restrict__ e, F* __restrict__ tau,
@@ -240,69 +244,70 @@ __global__ void __launch_bounds__(256) k_tridiag_coop(F* __restrict__ A, int n, 
   const unsigned int G = gridDim.x;
   const int cta = blockIdx.x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
-  F* vv = scr;
-  F* pp = scr + n;
-  F* part_norm = scr + 2 * n;
-  F* part_pv = part_norm + G;
-  F* alpha_g = part_pv + G;
+  F* pp = scr;
+  F* colg = scr + n;            // [2][n]
+  F* part_pv = scr + 3 * n;
   extern __shared__ __align__(16) unsigned char tri_smem_raw[];   // local copies of v and p (2 n values)
   F* tri_smem = reinterpret_cast<F*>(tri_smem_raw);
   F* vs = tri_smem;
   F* ps = tri_smem + n;
   __shared__ F red[8];
-  __shared__ F sh_tau, sh_beta, sh_scale, sh_sum;
+  __shared__ F sh_tau, sh_scale, sh_sum;
   bool live = true;
 
-  // norm partials of column 0 below the subdiagonal, alpha of column 0
-  {
-    F s = F(0);
-    for (int i = first_owned(2, cta, G); i < n; i += G)
-      if (threadIdx.x == 0) s += A[(size_t)i * n] * A[(size_t)i * n];
-    if (threadIdx.x == 0) {
-      part_norm[cta] = s;
-      if (n > 1 && 1 % (int)G == cta) *alpha_g = A[(size_t)1 * n];
-    }
-  }
+  // own rows' entries of column 0 below the diagonal
+  for (int i = first_owned(1, cta, G) + (int)G * threadIdx.x; i < n; i += (int)G * blockDim.x)
+    colg[i] = A[(size_t)i * n];
   live = grid_barrier(gb, G, wait_limit);
 
   for (int k = 0; k + 2 < n && live; ++k) {
     const int m0 = k + 1;
-    // ---- reflector (every CTA computes the same scalars)
-    const F xn2 = cta_sum_partials(part_norm, G, red, &sh_sum);
+    const F* col = colg + (size_t)(k & 1) * n;
+    // ---- reflector from the whole column (every CTA computes the same scalars, in the
+    // same order, from the same values)
+    F s2 = F(0);
+    for (int j = m0 + 1 + threadIdx.x; j < n; j += blockDim.x) {
+      const F x = __ldcg(col + j);
+      s2 += x * x;
+    }
+    s2 = warp_sum(s2);
+    if (lane == 0) red[warp] = s2;
+    __syncthreads();
+    if (warp == 0) {
+      const F t = warp_sum(lane < nwarp ? red[lane] : F(0));
+      if (lane == 0) sh_sum = t;
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
-      const F alpha = __ldcg(alpha_g);
+      const F xn2 = sh_sum, alpha = __ldcg(col + m0);
+      F beta;
       if (xn2 == F(0)) {
         sh_tau = F(0);
-        sh_beta = alpha;
+        beta = alpha;
         sh_scale = F(0);
       } else {
         // beta = -sign(alpha) |x|, tau = 1 + |alpha| / |x|: one rsqrt, one division
-        const F s2 = alpha * alpha + xn2, rs = rsq(s2);
-        const F beta = -copysign(s2 * rs, alpha);
+        const F s = alpha * alpha + xn2, rs = rsq(s);
+        beta = -copysign(s * rs, alpha);
         sh_tau = F(1) + fabs(alpha) * rs;
         sh_scale = F(1) / (alpha - beta);
-        sh_beta = beta;
       }
       if (cta == 0) {
-        e[k] = sh_beta;
+        e[k] = beta;
         tau[k] = sh_tau;
       }
       if (k % (int)G == cta) d[k] = A[(size_t)k * n + k];
     }
     __syncthreads();
     const F tk = sh_tau, sc = sh_scale;
-    // own rows: v_i, stored in the column for the back-transformation
-    for (int i = first_owned(m0, cta, G) + (int)G * threadIdx.x; i < n; i += (int)G * blockDim.x) {
-      const F vi = (i == m0) ? F(1) : A[(size_t)i * n + k] * sc;
-      vv[i] = vi;
-      if (i > m0) A[(size_t)i * n + k] = vi;
-    }
-    if (!(live = grid_barrier(gb, G, wait_limit))) break;
+    // v (every entry), own rows keep theirs in the column for the back-transformation
+    for (int j = m0 + threadIdx.x; j < n; j += blockDim.x) vs[j] = (j == m0) ? F(1) : __ldcg(col + j) * sc;
+    __syncthreads();
+    for (int i = first_owned(m0 + 1, cta, G) + (int)G * threadIdx.x; i < n; i += (int)G * blockDim.x)
+      A[(size_t)i * n + k] = vs[i];
     // ---- p_i = tau (A22 v)_i for own rows, partial p^T v
     F pv_part = F(0);
     if (tk != F(0)) {
-      for (int j = m0 + threadIdx.x; j < n; j += blockDim.x) vs[j] = __ldcg(vv + j);
-      __syncthreads();
       int r = 0;
       for (int i = first_owned(m0, cta, G); i < n; i += G, ++r) {
         if (r % nwarp != warp) continue;
@@ -329,8 +334,9 @@ __global__ void __launch_bounds__(256) k_tridiag_coop(F* __restrict__ A, int n, 
       if (lane == 0) part_pv[cta] = t;
     }
     if (!(live = grid_barrier(gb, G, wait_limit))) break;
-    // ---- w = p - (tau/2)(p^T v) v ; A22 -= v w^T + w v^T on own rows; next column norm
-    F nrm_part = F(0);
+    // ---- w = p - (tau/2)(p^T v) v ; A22 -= v w^T + w v^T on own rows; their entries of
+    // the next column (k + 1, rows below its diagonal) to the other column buffer
+    F* nxt = colg + (size_t)((k + 1) & 1) * n;
     if (tk != F(0)) {
       const F pvs = cta_sum_partials(part_pv, G, red, &sh_sum);
       const F cc = F(0.5) * tk * pvs;
@@ -344,26 +350,11 @@ __global__ void __launch_bounds__(256) k_tridiag_coop(F* __restrict__ A, int n, 
         F* row = A + (size_t)i * n;
         for (int j = m0 + lane; j < n; j += 32) row[j] -= vi * ps[j] + wi * vs[j];
         __syncwarp();
-        if (lane == 0) {
-          const F x = row[m0];   // column k + 1 of row i
-          if (i >= m0 + 2) nrm_part += x * x;
-          if (i == m0 + 1) *alpha_g = x;
-        }
+        if (lane == 0 && i >= m0 + 1) nxt[i] = row[m0];
       }
     } else {
-      int r = 0;
-      for (int i = first_owned(m0, cta, G); i < n; i += G, ++r) {
-        if (r % nwarp != warp || lane != 0) continue;
-        const F x = A[(size_t)i * n + m0];
-        if (i >= m0 + 2) nrm_part += x * x;
-        if (i == m0 + 1) *alpha_g = x;
-      }
-    }
-    if (lane == 0) red[warp] = nrm_part;
-    __syncthreads();
-    if (warp == 0) {
-      const F t = warp_sum(lane < nwarp ? red[lane] : F(0));
-      if (lane == 0) part_norm[cta] = t;
+      for (int i = first_owned(m0 + 1, cta, G) + (int)G * threadIdx.x; i < n; i += (int)G * blockDim.x)
+        nxt[i] = A[(size_t)i * n + m0];
     }
     live = grid_barrier(gb, G, wait_limit);
   }
@@ -723,7 +714,7 @@ template <typename F>
 static F* y_end(F* tw, int n, int nroots) { return tw + 2 * n + (size_t)nroots * n + 5 * (size_t)nroots * n; }
 // coop scratch (v, p, partials, alpha) + the grid barrier, in units of F
 template <typename F>
-static size_t coop_scratch(int n) { return 2 * (size_t)n + 2 * 1024 + 2 + (sizeof(GridBar) + sizeof(F) - 1) / sizeof(F) + 2; }
+static size_t coop_scratch(int n) { return 3 * (size_t)n + 1024 + 2 + (sizeof(GridBar) + sizeof(F) - 1) / sizeof(F) + 2; }
 
 static size_t tda_work_doubles_fp64(int n, int nroots) {
   return (size_t)n * n + 14 * (size_t)n + 6 * (size_t)nroots * n + 4096;
@@ -758,7 +749,7 @@ static int tridiagonalise(rsx_ctx* c, F* A, int n, F* d, F* e, F* tau, F* scr, F
   // small); FP32: one per SM (measured at n = 960: 64 -> 24.0 ms, 152 -> 19.8 ms)
   int gcap = sizeof(F) == 4 ? c->nsm : 64;
   if (const char* ev = getenv("RSX_TRIDIAG_CTAS")) gcap = std::max(1, atoi(ev));
-  const int G = std::min(std::min(c->nsm * std::max(per_sm, 0), gcap), std::max(1, n / 2));
+  const int G = std::min(std::min(std::min(c->nsm * std::max(per_sm, 0), gcap), std::max(1, n / 2)), 1024);
   // rows in distributed shared memory (16 CTAs, else 8), else the cooperative grid, else
   // one 16-CTA cluster with the rows in global memory (slower than the grid at n ~ 1000,
   // measured), else one CTA.  RSX_TRIDIAG_PATH = cluster, coop, global or cta forces one
@@ -800,7 +791,7 @@ static int tridiagonalise(rsx_ctx* c, F* A, int n, F* d, F* e, F* tau, F* scr, F
       if (r >= 0) return r;
     }
   if (coop && per_sm > 0 && n >= 64 && (force.empty() || force == "coop")) {
-    GridBar* gb = reinterpret_cast<GridBar*>(scr + 2 * (size_t)n + 2 * 1024 + 2);
+    GridBar* gb = reinterpret_cast<GridBar*>(scr + 3 * (size_t)n + 1024 + 2);
     cudaMemsetAsync(gb, 0, sizeof(GridBar), s);
     unsigned int wait_limit = c->wait_limit < 0 ? kGridWaitLimit
                               : (unsigned int)std::min<long long>(c->wait_limit, 0xffffffffLL);

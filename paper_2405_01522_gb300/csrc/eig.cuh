@@ -49,69 +49,85 @@ __device__ inline int sturm_count_f32(const float* d, const float* e2, int n, fl
 
 // LU with partial pivoting of T - lam I (serial, one thread): sc holds 4 n values
 // (reciprocal pivots, first and second superdiagonal of U, multipliers), piv n ints.
-// R = double, or float for a first approximation.
+// R = double, or float for a first approximation.  The recurrence carries the current
+// pivot row's diagonal and superdiagonal in registers; the factors are only stored, so
+// the dependent chain is one reciprocal and one fused multiply-add per row.
 template <typename R>
-__device__ inline void tri_factor_shifted(const R* d, const R* e, int n, R lam, R* sc, int* piv) {
+__device__ inline void tri_factor_shifted(const R* __restrict__ d, const R* __restrict__ e, int n, R lam,
+                                          R* __restrict__ sc, int* __restrict__ piv) {
   R* dg = sc;
   R* u1 = sc + n;
   R* u2 = sc + 2 * n;
   R* lw = sc + 3 * n;
   const R eps_shift = R(sizeof(R) == 8 ? 1e-14 : 1e-6) * fmax(R(1), fabs(lam));
-  for (int i = 0; i < n; ++i) {
-    dg[i] = d[i] - lam;
-    u1[i] = i < n - 1 ? e[i] : R(0);
-    u2[i] = R(0);
-  }
-  // one division per step: the pivot's reciprocal, which the solves use as well
+  R cur = d[0] - lam;                    // row i's diagonal, as updated by the previous step
+  R cu1 = n > 1 ? e[0] : R(0);           // row i's first superdiagonal, likewise
+#pragma unroll 4
   for (int i = 0; i < n - 1; ++i) {
     const R sub = e[i];
-    if (fabs(dg[i]) >= fabs(sub)) {
+    const R dn = d[i + 1] - lam;                   // row i + 1 before this step
+    const R en = (i + 1 < n - 1) ? e[i + 1] : R(0);
+    if (fabs(cur) >= fabs(sub)) {
       piv[i] = 0;
-      if (dg[i] == R(0)) dg[i] = eps_shift;
-      const R r = R(1) / dg[i];
+      if (cur == R(0)) cur = eps_shift;
+      const R r = R(1) / cur;
       const R l = sub * r;
       lw[i] = l;
-      dg[i + 1] -= l * u1[i];
       dg[i] = r;
+      u1[i] = cu1;
+      u2[i] = R(0);
+      cur = dn - l * cu1;
+      cu1 = en;
     } else {
+      // rows i and i + 1 swapped: U's row i is the old row i + 1
       piv[i] = 1;
       const R r = R(1) / sub;
-      const R l = dg[i] * r;
+      const R l = cur * r;
       lw[i] = l;
-      const R t0 = dg[i + 1], t1 = (i + 1 < n - 1) ? u1[i + 1] : R(0);
       dg[i] = r;
-      const R old_u1 = u1[i];
-      u1[i] = t0;
-      u2[i] = t1;
-      dg[i + 1] = old_u1 - l * t0;
-      if (i + 1 < n - 1) u1[i + 1] = -l * t1;
+      u1[i] = dn;
+      u2[i] = en;
+      cur = cu1 - l * dn;
+      cu1 = -l * en;
     }
   }
-  if (dg[n - 1] == R(0)) dg[n - 1] = eps_shift;
-  dg[n - 1] = R(1) / dg[n - 1];   // dg now holds the reciprocal pivots the solves multiply by
+  if (cur == R(0)) cur = eps_shift;
+  dg[n - 1] = R(1) / cur;   // dg now holds the reciprocal pivots the solves multiply by
 }
 
-// z <- (T - lam I)^{-1} z with the factors of tri_factor_shifted (serial, one thread)
+// z <- (T - lam I)^{-1} z with the factors of tri_factor_shifted (serial, one thread; the
+// running entries of z in registers, the factors read ahead)
 template <typename R>
-__device__ inline void tri_solve_factored(int n, R* z, const R* sc, const int* piv) {
+__device__ inline void tri_solve_factored(int n, R* __restrict__ z, const R* __restrict__ sc,
+                                          const int* __restrict__ piv) {
   const R* rdg = sc;
   const R* u1 = sc + n;
   const R* u2 = sc + 2 * n;
   const R* lw = sc + 3 * n;
+  R c = z[0];   // entry i of the forward sweep, as updated by the previous step
+#pragma unroll 4
   for (int i = 0; i < n - 1; ++i) {
+    const R zn = z[i + 1];
+    const R l = lw[i];
     if (piv[i]) {
-      const R t = z[i];
-      z[i] = z[i + 1];
-      z[i + 1] = t - lw[i] * z[i];
+      z[i] = zn;
+      c = c - l * zn;
     } else {
-      z[i + 1] -= lw[i] * z[i];
+      z[i] = c;
+      c = zn - l * c;
     }
   }
+  z[n - 1] = c;
+  R z1 = R(0), z2 = R(0);   // the solution's entries i + 1 and i + 2
+#pragma unroll 4
   for (int i = n - 1; i >= 0; --i) {
     R s = z[i];
-    if (i + 1 < n) s -= u1[i] * z[i + 1];
-    if (i + 2 < n) s -= u2[i] * z[i + 2];
-    z[i] = s * rdg[i];
+    if (i + 1 < n) s -= u1[i] * z1;
+    if (i + 2 < n) s -= u2[i] * z2;
+    const R zi = s * rdg[i];
+    z[i] = zi;
+    z2 = z1;
+    z1 = zi;
   }
 }
 

@@ -813,6 +813,110 @@ static int tridiagonalise(rsx_ctx* c, F* A, int n, F* d, F* e, F* tau, F* scr, F
   return set_error(c, RSX_EUNSUPPORTED, "no FP32 tridiagonalisation path for this size");
 }
 
+// Blocked back-transformation (compact WY form, as in LAPACK's xLARFT / xLARFB): the
+// reflectors are taken 32 at a time, H_j0 ... H_j0+m-1 = I - V T V^T with V the block's
+// reflector vectors (n x m) and T upper triangular, T[i][i] = tau_i,
+// T[0:i][i] = -tau_i T[0:i][0:i] (V[:, 0:i]^T v_i).  k_wy_t builds T of every block (one
+// CTA per block, into Tg[block][32][32]); k_backtransform_wy applies the blocks, last
+// first, to each root's vector (a warp per root): s = V^T x (a lane per reflector),
+// u = T s, x -= V u (lanes over the rows).  The dependent steps per root drop from one
+// per reflector to three per block.
+constexpr int kWy = 32;
+
+template <typename F>
+__global__ void __launch_bounds__(256) k_wy_t(const F* __restrict__ A, const F* __restrict__ tau, int n, int nref,
+                                              F* __restrict__ Tg) {
+  __shared__ F G[kWy][kWy + 1];
+  __shared__ F T[kWy][kWy + 1];
+  const int b = blockIdx.x, j0 = b * kWy, m = min(kWy, nref - j0);
+  // G[a][c] = v_a^T v_c for a < c (v_a[r] = 0 for r <= ja, 1 at ja + 1, A[ja][r] beyond)
+  for (int q = threadIdx.x; q < kWy * kWy; q += blockDim.x) {
+    const int a = q / kWy, c = q - a * kWy;
+    F g = F(0);
+    if (a < c && c < m) {
+      const int ja = j0 + a, jc = j0 + c;   // ja < jc: v_c vanishes at and above jc
+      const F* va = A + (size_t)ja * n;
+      const F* vc = A + (size_t)jc * n;
+      g = va[jc + 1];                        // v_c[jc + 1] = 1
+      for (int r = jc + 2; r < n; ++r) g += va[r] * vc[r];
+    }
+    G[a][c] = g;
+    T[a][c] = F(0);
+  }
+  __syncthreads();
+  for (int i = 0; i < m; ++i) {
+    const F ti = tau[j0 + i];
+    // T[a][i] = -tau_i sum_{c < i} T[a][c] G[c][i], a < i (T[0:i][0:i] is final)
+    F t = F(0);
+    const int a = threadIdx.x;
+    if (a < i) {
+      for (int c = a; c < i; ++c) t += T[a][c] * G[c][i];
+    }
+    __syncthreads();
+    if (a < i) T[a][i] = -ti * t;
+    if (a == i) T[i][i] = ti;
+    __syncthreads();
+  }
+  for (int q = threadIdx.x; q < kWy * kWy; q += blockDim.x) {
+    const int a = q / kWy, c = q - a * kWy;
+    Tg[(size_t)b * kWy * kWy + q] = T[a][c];
+  }
+}
+
+template <typename F>
+__global__ void __launch_bounds__(32) k_backtransform_wy(const F* __restrict__ A, const F* __restrict__ Tg, int n,
+                                                         int nref, const F* __restrict__ y, int nroots,
+                                                         F* __restrict__ X) {
+  extern __shared__ __align__(16) unsigned char xs_wy_raw[];
+  F* x = reinterpret_cast<F*>(xs_wy_raw);
+  __shared__ F us[kWy];
+  const int lane = threadIdx.x & 31;
+  const int k = blockIdx.x;
+  if (k >= nroots) return;
+  for (int i = lane; i < n; i += 32) x[i] = y[(size_t)k * n + i];
+  __syncwarp();
+  const int nb = (nref + kWy - 1) / kWy;
+  for (int b = nb - 1; b >= 0; --b) {
+    const int j0 = b * kWy, m = min(kWy, nref - j0);
+    // s_j = v_j^T x, lane j
+    F sj = F(0);
+    if (lane < m) {
+      const int ja = j0 + lane;
+      const F* va = A + (size_t)ja * n;
+      F s0 = x[ja + 1], s1 = F(0);   // two chains
+      int r = ja + 2;
+      for (; r + 1 < n; r += 2) {
+        s0 += va[r] * x[r];
+        s1 += va[r + 1] * x[r + 1];
+      }
+      if (r < n) s0 += va[r] * x[r];
+      sj = s0 + s1;
+    }
+    // u_i = sum_{j >= i} T[i][j] s_j, lane i
+    F ui = F(0);
+    const F* Trow = Tg + (size_t)b * kWy * kWy + (size_t)lane * kWy;
+    for (int j = 0; j < kWy; ++j) {
+      const F sjj = __shfl_sync(0xffffffffu, sj, j);
+      if (j >= lane && j < m) ui += Trow[j] * sjj;
+    }
+    us[lane] = ui;
+    __syncwarp();
+    // x_r -= sum_j v_j[r] u_j for r > j0 (rows of the block's reflectors)
+    for (int r = j0 + 1 + lane; r < n; r += 32) {
+      F acc = F(0);
+      const int jmax = min(m, r - j0);   // v_j[r] = 0 for r <= j0 + j
+      for (int j = 0; j < jmax; ++j) {
+        const int ja = j0 + j;
+        const F vj = (r == ja + 1) ? F(1) : A[(size_t)ja * n + r];
+        acc += vj * us[j];
+      }
+      x[r] -= acc;
+    }
+    __syncwarp();
+  }
+  for (int i = lane; i < n; i += 32) X[(size_t)k * n + i] = x[i];
+}
+
 // lowest q eigenpairs of the tridiagonal (d, e) and x = Q y through the reflectors of A
 template <typename F>
 static void tridiag_eigs(F* A, const F* tau, const F* d, const F* e, int n, int q, F* w, F* yv, F* sc, F* X,
@@ -824,6 +928,14 @@ static void tridiag_eigs(F* A, const F* tau, const F* d, const F* e, int n, int 
   k_invit_clusters<F><<<1, 32, 0, s>>>(d, e, n, w, q, yv, sc);
   k_reflectors_to_rows<F><<<dim3((n + 31) / 32, (n + 31) / 32), 256, 0, s>>>(A, n);
   const size_t smem = (size_t)n * sizeof(F);
+  const int nref = n - 2, nb = (nref + kWy - 1) / kWy;
+  if (nref >= kWy && (size_t)nb * kWy * kWy <= 5 * (size_t)n * q) {
+    // T of every block in the inverse-iteration scratch (free again here)
+    k_wy_t<F><<<nb, 256, 0, s>>>(A, tau, n, nref, sc);
+    cudaFuncSetAttribute(k_backtransform_wy<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_backtransform_wy<F><<<q, 32, smem, s>>>(A, sc, n, nref, yv, q, X);
+    return;
+  }
   cudaFuncSetAttribute(k_backtransform<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k_backtransform<F><<<q, 32, smem, s>>>(A, tau, n, yv, q, X);
 }

@@ -333,6 +333,8 @@ __global__ void k_chol_linv(double* __restrict__ M, int k, double* __restrict__ 
   extern __shared__ double sm[];
   double* B = sm;            // k*k
   double* L = sm + k * k;    // k*k
+  __shared__ double rinv[64];   // 1 / L_jj (FP64 division and square root are long sequences
+                                // on this part: one rsqrt per column, multiplications after)
   __shared__ int bad;
   if (threadIdx.x == 0) bad = 0;
   for (int i = threadIdx.x; i < k * k; i += blockDim.x) {
@@ -351,13 +353,15 @@ __global__ void k_chol_linv(double* __restrict__ M, int k, double* __restrict__ 
         bad = 1;
         d = 1.0;
       }
-      L[j * k + j] = sqrt(d);
+      const double rs = rsqrt(d);
+      L[j * k + j] = d * rs;
+      rinv[j] = rs;
     }
     __syncthreads();
     for (int i = j + 1 + threadIdx.x; i < k; i += blockDim.x) {
       double s = B[i * k + j];
       for (int p = 0; p < j; ++p) s -= L[i * k + p] * L[j * k + p];
-      L[i * k + j] = s / L[j * k + j];
+      L[i * k + j] = s * rinv[j];
     }
     __syncthreads();
   }
@@ -370,7 +374,7 @@ __global__ void k_chol_linv(double* __restrict__ M, int k, double* __restrict__ 
         continue;
       }
       for (int p = c; p < i; ++p) s -= L[i * k + p] * B[p * k + c];
-      B[i * k + c] = s / L[i * k + i];
+      B[i * k + c] = s * rinv[i];
     }
   }
   __syncthreads();

@@ -337,7 +337,7 @@ def run_rsx(args, rank, local_rank, world):
     e2e_run(2)
     barrier()
     e2 = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-    ne2e = max(3, args.steps // 2)   # pipeline fill and drain amortised over more steps
+    ne2e = max(3, args.steps)   # as many steps as the device-resident timing
     e2e_run(ne2e, e2[0], e2[1])
     barrier()
     ms_e2e = max_over_ranks(e2[0].elapsed_time(e2[1]), dist, dev)

@@ -49,7 +49,9 @@ enum {
   RSX_ECUDA = 3,          /* a CUDA runtime call failed (message in rsx_last_error) */
   RSX_ENOTPD = 4,         /* -M not positive definite in the ACE Cholesky (deferred) */
   RSX_ETIMEOUT = 5,       /* a bounded device wait gave up (deferred) */
-  RSX_EUNSUPPORTED = 6    /* box edge or mode not supported */
+  RSX_EUNSUPPORTED = 6,   /* box edge or mode not supported */
+  RSX_EBOUNDS = 7         /* bounds-checked build only: an FFT-pass index left its array
+                             (the access was skipped; deferred to rsx_sync_status) */
 };
 
 enum { RSX_FP64 = 0, RSX_FP32 = 1 };

@@ -2,7 +2,10 @@
 
 Each translation unit is compiled by nvcc in parallel, then linked into
 ``paper_2405_01522_gb300/librsx.so``.  Objects go to ``paper_2405_01522_gb300/_build``
-and are rebuilt only when a source or header is newer.
+and are rebuilt only when a source or header is newer.  ``build(checked=True)`` makes the
+bounds-checked variant ``librsx_checked.so`` (``-DRSX_CHECKED``, objects in
+``_build_checked``): the FFT passes test their computed indices and report a violation as
+RSX_EBOUNDS instead of making the access; the binding loads it when RSX_CHECKED=1.
 """
 import glob
 import os
@@ -14,6 +17,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librsx.so")
+BUILD_CHECKED = os.path.join(HERE, "_build_checked")
+LIB_CHECKED = os.path.join(HERE, "librsx_checked.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc" if os.path.exists("/usr/local/cuda/bin/nvcc") else "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "--expt-relaxed-constexpr", "-O3", "-lineinfo", "-Xcompiler", "-fPIC",
@@ -25,11 +30,11 @@ def _newest_header():
     return max((os.path.getmtime(h) for h in hs), default=0.0)
 
 
-def _compile(src, hdr_time, verbose):
-    obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+def _compile(src, hdr_time, verbose, build_dir=BUILD, extra=()):
+    obj = os.path.join(build_dir, os.path.basename(src)[:-3] + ".o")
     if os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(src), hdr_time):
         return obj, None
-    cmd = [NVCC] + ARCH + FLAGS + ["-c", src, "-o", obj]
+    cmd = [NVCC] + ARCH + FLAGS + list(extra) + ["-c", src, "-o", obj]
     if verbose:
         print(" ".join(cmd), flush=True)
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -38,27 +43,30 @@ def _compile(src, hdr_time, verbose):
     return obj, None
 
 
-def build(verbose=False, jobs=None):
-    """Compile every csrc/*.cu and link librsx.so; returns the library path."""
-    os.makedirs(BUILD, exist_ok=True)
+def build(verbose=False, jobs=None, checked=False):
+    """Compile every csrc/*.cu and link librsx.so (librsx_checked.so with checked=True);
+    returns the library path."""
+    build_dir, lib = (BUILD_CHECKED, LIB_CHECKED) if checked else (BUILD, LIB)
+    extra = ("-DRSX_CHECKED",) if checked else ()
+    os.makedirs(build_dir, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     hdr_time = _newest_header()
     jobs = jobs or max(1, min(len(srcs), os.cpu_count() or 4))
     with ThreadPoolExecutor(jobs) as ex:
-        res = list(ex.map(lambda s: _compile(s, hdr_time, verbose), srcs))
+        res = list(ex.map(lambda s: _compile(s, hdr_time, verbose, build_dir, extra), srcs))
     errs = [e for _, e in res if e]
     if errs:
         raise RuntimeError("nvcc failed:\n" + "\n".join(errs))
     objs = [o for o, _ in res]
-    if not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
-        cmd = [NVCC] + ARCH + ["-shared", "-o", LIB] + objs
+    if not os.path.exists(lib) or os.path.getmtime(lib) < max(os.path.getmtime(o) for o in objs):
+        cmd = [NVCC] + ARCH + ["-shared", "-o", lib] + objs
         if verbose:
             print(" ".join(cmd), flush=True)
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("link failed:\n" + r.stdout + r.stderr)
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(verbose="-v" in sys.argv))
+    print(build(verbose="-v" in sys.argv, checked="--checked" in sys.argv))

@@ -213,7 +213,8 @@ namespace rsx {
 template <typename R>
 int solve_pairs(rsx_ctx* c, const PairMap<R>& pm, int q0, int nq, int p0, int np, R* out, cudaStream_t s,
                 int pot) {
-  const Geom& g = c->g;
+  Geom g = c->g;
+  g.dbg_nq = nq;   // pairs of this launch's intermediate (read by bounds-checked builds)
   const size_t need = (size_t)nq * g.inter_elems() * sizeof(Cx<R>);
   int rc = grow(c, &c->work, &c->work_bytes, need, "FFT intermediates");
   if (rc) return rc;
@@ -450,6 +451,9 @@ int rsx_create(rsx_ctx** out, int nz, int ny, int nx, double h, int precision, i
     return RSX_ENOMEM;
   }
   cudaMemset(c->status, 0, sizeof(int));
+#ifdef RSX_CHECKED
+  g.dbg = c->status;   // out-of-range indices of the FFT passes are reported here
+#endif
   const int rc = precision == RSX_FP32 ? make_tables<float>(c) : make_tables<double>(c);
   if (rc) {
     rsx_destroy(c);
@@ -658,6 +662,7 @@ int rsx_sync_status(rsx_ctx* c, void* stream) {
   cudaMemset(c->status, 0, sizeof(int));
   if (st == RSX_ENOTPD) return set_error(c, RSX_ENOTPD, "ACE: -M is not positive definite");
   if (st == RSX_ETIMEOUT) return set_error(c, RSX_ETIMEOUT, "a bounded device wait timed out");
+  if (st == RSX_EBOUNDS) return set_error(c, RSX_EBOUNDS, "bounds-checked build: an FFT-pass index left its array");
   if (st) return set_error(c, st, "deferred device error");
   return RSX_OK;
 }

@@ -172,8 +172,10 @@ __device__ __forceinline__ void pass1_item(const Geom& g, const R* f1, const R* 
     const int x = t + 16 * a;
     R re = R(0), im = R(0);
     if (x < g.nx) {
-      if (ya < g.ny) re = __ldg(f1 + (size_t)ya * g.nx + x) * __ldg(f2 + (size_t)ya * g.nx + x);
-      if (yb < g.ny) im = __ldg(f1 + (size_t)yb * g.nx + x) * __ldg(f2 + (size_t)yb * g.nx + x);
+      if (ya < g.ny && RSX_IN_RANGE(g, plane + (size_t)ya * g.nx + x, g.N()))
+        re = __ldg(f1 + (size_t)ya * g.nx + x) * __ldg(f2 + (size_t)ya * g.nx + x);
+      if (yb < g.ny && RSX_IN_RANGE(g, plane + (size_t)yb * g.nx + x, g.N()))
+        im = __ldg(f1 + (size_t)yb * g.nx + x) * __ldg(f2 + (size_t)yb * g.nx + x);
     }
     v[a] = cx<R>(re, im);
   }
@@ -220,7 +222,7 @@ __device__ __forceinline__ void pass1_item(const Geom& g, const R* f1, const R* 
   const size_t kstride = (size_t)g.nz * g.ny;
   for (int e = threadIdx.x; e < H * (kRowsPerCta / 2); e += kThreads) {
     const int kx = e / (kRowsPerCta / 2), r = 2 * (e - kx * (kRowsPerCta / 2));
-    if (r < nrow) {
+    if (r < nrow && RSX_IN_RANGE(g, (size_t)z * g.ny + y0 + (size_t)kx * kstride + r + 1, g.inter_elems())) {
       Cx<R> a, b;
       ld_granule(xs + xs_idx(kx, r), a, b);
       st_granule(dst + (size_t)kx * kstride + r, a, b);
@@ -254,6 +256,7 @@ __global__ void __launch_bounds__(kThreads) k_pass1(Geom g, PairMap<R> pm, int q
     ql = (b / g.nz) * g.p1_group + lo;
     if (ql >= nq) return;   // whole CTA: the last group is partial
   }
+  if (!RSX_IN_RANGE(g, ql, nq)) return;   // whole CTA
   const R* f1;
   const R* f2;
   pm.pair(q0 + ql, f1, f2);
@@ -534,6 +537,9 @@ __global__ void __launch_bounds__(NT, 1) k_pass2(Geom g, int nq, Cx<R>* __restri
   const bool pipe = DSMEM;
   if (pipe && (int)blockIdx.x < nwork) prefetch_plane_upper<R>(D, DP, plane_ptr(blockIdx.x), 8 * AZ, 8 * AY, NT);
   for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
+    if (!RSX_IN_RANGE(g, (long long)(w / g.Hx) * g.inter_elems() + (long long)(w % g.Hx + 1) * nplane - 1,
+                      (long long)nq * g.inter_elems()))
+      break;   // whole CTA: its work index decides
     const int kx = w % g.Hx;
     const int wn = w + (int)gridDim.x;
     pass2_plane<R, AY, AZ, NT>(g, plane_ptr(w), kx, twy, twz, vhat, vlanes, D, scr, pipe,
@@ -698,12 +704,14 @@ __device__ __forceinline__ void pass3_prefetch(const Geom& g, const PairMap<R>& 
   if (!pot) pm.entry(p, e, q, partner);
   const Cx<R>* src = inter + (size_t)(q - q0) * g.inter_elems() + (size_t)z * g.ny + y0;
   const size_t kstride = (size_t)g.nz * g.ny;
+  const bool slot_ok = RSX_IN_RANGE(g, q - q0, g.dbg_nq > 0 ? g.dbg_nq : 0x7fffffff);
   // one granule (rows r, r + 1) per copy; the intermediate is library-owned and 16-byte
   // aligned, nrow is a multiple of 8
   for (int i = threadIdx.x; i < H * (kRowsPerCta / 2); i += kThreads) {
     const int kx = i / (kRowsPerCta / 2), r = 2 * (i - kx * (kRowsPerCta / 2));
     Cx<R>* dp = xs + xs_idx(kx, r);
-    if (r < nrow) {
+    if (r < nrow && slot_ok &&
+        RSX_IN_RANGE(g, (size_t)z * g.ny + y0 + (size_t)kx * kstride + r + 1, g.inter_elems())) {
       const Cx<R>* sp = src + (size_t)kx * kstride + r;
       cp_async16(dp, sp);
       if (sizeof(R) == 8) cp_async16(dp + 1, sp + 1);
@@ -713,7 +721,7 @@ __device__ __forceinline__ void pass3_prefetch(const Geom& g, const PairMap<R>& 
   }
   if (!pot) {
     const R* prow = partner + (size_t)z * g.ny * g.nx + (size_t)y0 * g.nx;
-    const int cnt = nrow * g.nx;
+    const int cnt = RSX_IN_RANGE(g, (size_t)z * g.ny * g.nx + (size_t)(y0 + nrow) * g.nx - 1, g.N()) ? nrow * g.nx : 0;
     if (((reinterpret_cast<uintptr_t>(prow) | (uintptr_t)(cnt * sizeof(R))) & 15u) == 0) {
       constexpr int V = 16 / (int)sizeof(R);
       for (int i = threadIdx.x * V; i < cnt; i += kThreads * V) cp_async16(tile + i, prow + i);
@@ -841,7 +849,8 @@ __device__ __forceinline__ void pass3_item(const Geom& g, const PairMap<R>& pm, 
   }
   __syncthreads();
   R* orow = out_p + plane + (size_t)y0 * g.nx;
-  for (int i = threadIdx.x; i < nrow * g.nx; i += kThreads) orow[i] = tile[i];
+  if (RSX_IN_RANGE(g, plane + (size_t)(y0 + nrow) * g.nx - 1, g.N()))
+    for (int i = threadIdx.x; i < nrow * g.nx; i += kThreads) orow[i] = tile[i];
   __syncthreads();
 }
 

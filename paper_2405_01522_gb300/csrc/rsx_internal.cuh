@@ -94,9 +94,26 @@ struct Geom {
                       // shared memory would hold it (0 = shared memory whenever it fits)
   int p2_lanes;       // tuning: lanes per line of the y/z transforms, 16 (16 x A) or 8 (8 x 2A;
                       // FP32, A a multiple of 4, shared-memory plane)
+  int* dbg = nullptr; // bounds-checked builds: the status word an out-of-range index is reported in
+  int dbg_nq = 0;     // bounds-checked builds: pairs the launch's intermediate holds (0: unknown)
   __host__ __device__ size_t N() const { return (size_t)nz * ny * nx; }
   __host__ __device__ size_t inter_elems() const { return (size_t)Hx * nz * ny; }  // complex per pair
 };
+
+// Bounds-checked builds (-DRSX_CHECKED, `librsx_checked.so`): the FFT passes test the
+// indices they compute against the arrays they address, report the first violation as
+// RSX_EBOUNDS in the context's status word and skip the access.  In the normal build the
+// test is the constant true and compiles away.
+#ifdef RSX_CHECKED
+__device__ inline bool in_range_checked(int* dbg, long long i, long long n) {
+  if (i >= 0 && i < n) return true;
+  if (dbg) atomicMax(dbg, 7);   // RSX_EBOUNDS
+  return false;
+}
+#define RSX_IN_RANGE(g, i, n) ::rsx::in_range_checked((g).dbg, (long long)(i), (long long)(n))
+#else
+#define RSX_IN_RANGE(g, i, n) true
+#endif
 
 // ---- launchers (defined per precision in poisson_f32.cu / poisson_f64.cu)
 template <typename R>

@@ -10,13 +10,15 @@ import os
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "librsx.so")
+# RSX_CHECKED=1 selects the bounds-checked build (librsx_checked.so, built by
+# build(checked=True)): same ABI, the FFT passes report out-of-range indices as RSX_EBOUNDS
+LIB_PATH = os.path.join(_HERE, "librsx_checked.so" if os.environ.get("RSX_CHECKED") == "1" else "librsx.so")
 
-RSX_OK, RSX_EINVAL, RSX_ENOMEM, RSX_ECUDA, RSX_ENOTPD, RSX_ETIMEOUT, RSX_EUNSUPPORTED = range(7)
+RSX_OK, RSX_EINVAL, RSX_ENOMEM, RSX_ECUDA, RSX_ENOTPD, RSX_ETIMEOUT, RSX_EUNSUPPORTED, RSX_EBOUNDS = range(8)
 RSX_FP64, RSX_FP32 = 0, 1
 RSX_FAULT_NONE, RSX_FAULT_ALLOC, RSX_FAULT_PIVOT = 0, 1, 2
 ERROR_NAMES = {1: "RSX_EINVAL", 2: "RSX_ENOMEM", 3: "RSX_ECUDA", 4: "RSX_ENOTPD", 5: "RSX_ETIMEOUT",
-               6: "RSX_EUNSUPPORTED"}
+               6: "RSX_EUNSUPPORTED", 7: "RSX_EBOUNDS"}
 
 # exported symbol -> ctypes argument types (mirrors include/rsx.h)
 _P = ctypes.c_void_p

@@ -386,17 +386,18 @@ constexpr int kClThreads = 512;
 namespace cg = cooperative_groups;
 
 // shared-memory values of k_tridiag_cluster (rows unless GROWS, v, p, two column replicas,
-// the p^T v partials)
+// the p^T v partials of every warp of every CTA)
 template <typename F>
 inline size_t tridiag_cluster_smem(int n, int CS, bool grows) {
-  return ((grows ? 0 : ((size_t)(n + CS - 1) / CS) * n) + 4 * (size_t)n + CS) * sizeof(F);
+  return ((grows ? 0 : ((size_t)(n + CS - 1) / CS) * n) + 4 * (size_t)n + (size_t)CS * (kClThreads / 32)) *
+         sizeof(F);
 }
 
 // GROWS: the owned rows stay in global memory (rows of A, L2-resident) instead of
 // distributed shared memory, for n too large for the latter; only p, the columns and the
 // partials go through DSMEM.  A CTA only ever touches the rows it owns.
 template <typename F, bool GROWS>
-__global__ void __launch_bounds__(kClThreads) k_tridiag_cluster(F* __restrict__ A, int n, F* __restrict__ d,
+__global__ void __launch_bounds__(kClThreads, 1) k_tridiag_cluster(F* __restrict__ A, int n, F* __restrict__ d,
                                                                 F* __restrict__ e, F* __restrict__ tau) {
   cg::cluster_group cl = cg::this_cluster();
   const int CS = (int)cl.num_blocks();
@@ -409,7 +410,7 @@ __global__ void __launch_bounds__(kClThreads) k_tridiag_cluster(F* __restrict__ 
   F* v = GROWS ? cl_smem : R + (size_t)((n + CS - 1) / CS) * n;   // [n]
   F* p = v + n;                                 // [n] (p, then w)
   F* colb = p + n;                              // [2][n]: column k (and k + 1) replicas
-  F* part2 = p + 3 * n;                         // [CS] p^T v partials
+  F* part2 = p + 3 * n;                         // [CS][warps] p^T v partials
   __shared__ F red[kClThreads / 32];
   __shared__ F sh_tau, sh_scale;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = kClThreads / 32;
@@ -450,41 +451,47 @@ __global__ void __launch_bounds__(kClThreads) k_tridiag_cluster(F* __restrict__ 
     const int m0 = k + 1;
     const F* col = colb + (size_t)(k & 1) * n;
     // norm of the column below the subdiagonal and alpha = A[m0][k], from the replica
-    F s2 = F(0);
-    for (int j = m0 + 1 + tid; j < n; j += kClThreads) s2 += col[j] * col[j];
-    const F xn2 = block_sum0(s2);
-    if (tid == 0) {
-      const F alpha = col[m0];
-      F beta;
-      if (xn2 == F(0)) {
-        sh_tau = F(0);
-        beta = alpha;
-        sh_scale = F(0);
-      } else {
-        // beta = -sign(alpha) |x|, tau = (beta - alpha) / beta = 1 + |alpha| / |x|:
-        // one reciprocal square root and one division
-        const F s = alpha * alpha + xn2, rs = rsq(s);
-        beta = -copysign(s * rs, alpha);
-        sh_tau = F(1) + fabs(alpha) * rs;
-        sh_scale = F(1) / (alpha - beta);
+    // (one warp: the other warps wait at the barrier below anyway)
+    if (warp == 0) {
+      F s2 = F(0);
+      for (int j = m0 + 1 + lane; j < n; j += 32) s2 += col[j] * col[j];
+      for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+      if (lane == 0) {
+        const F alpha = col[m0];
+        F beta;
+        if (s2 == F(0)) {
+          sh_tau = F(0);
+          beta = alpha;
+          sh_scale = F(0);
+        } else {
+          // beta = -sign(alpha) |x|, tau = (beta - alpha) / beta = 1 + |alpha| / |x|:
+          // one reciprocal square root and one division
+          const F s = alpha * alpha + s2, rs = rsq(s);
+          beta = -copysign(s * rs, alpha);
+          sh_tau = F(1) + fabs(alpha) * rs;
+          sh_scale = F(1) / (alpha - beta);
+        }
+        if (me == 0) {
+          e[k] = beta;
+          tau[k] = sh_tau;
+        }
+        if (k % CS == me) d[k] = rowp(k / CS)[k];
       }
-      if (me == 0) {
-        e[k] = beta;
-        tau[k] = sh_tau;
-      }
-      if (k % CS == me) d[k] = rowp(k / CS)[k];
     }
     __syncthreads();
     const F tk = sh_tau, sc = sh_scale;
     // v (every entry, from the replica); own rows keep theirs as the reflector
     for (int j = m0 + tid; j < n; j += kClThreads) v[j] = (j == m0) ? F(1) : col[j] * sc;
-    __syncthreads();
     for (int li = tid; li < nloc; li += kClThreads) {
       const int i = grow(li);
-      if (i > m0) rowp(li)[k] = v[i];
+      if (i > m0) rowp(li)[k] = col[i] * sc;
     }
+    __syncthreads();
+    F* nxt = colb + (size_t)((k + 1) & 1) * n;
+    const bool send = m0 + 2 < n;   // a next step needs the next column
     if (tk != F(0)) {
-      // p_i = tau (A22 v)_i on own rows, a warp per row; p^T v partial
+      // p_i = tau (A22 v)_i on own rows, a warp per row, sent to every CTA; each warp's
+      // p^T v partial to every CTA's partial array (no CTA-wide reduction)
       F pv = F(0);
       for (int li = warp; li < nloc; li += nw) {
         const int i = grow(li);
@@ -501,32 +508,32 @@ __global__ void __launch_bounds__(kClThreads) k_tridiag_cluster(F* __restrict__ 
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         const F pi = tk * acc;
         if (lane < CS) *cl.map_shared_rank(p + i, lane) = pi;
-        if (lane == 0) pv += pi * v[i];
+        pv += pi * v[i];   // the same in every lane
       }
-      const F t = block_sum0(pv);
-      if (tid == 0) red[0] = t;
-      __syncthreads();
-      if (tid < CS) *cl.map_shared_rank(part2 + me, tid) = red[0];
+      if (lane < CS) *cl.map_shared_rank(part2 + me * nw + warp, lane) = pv;
       cl.sync();
-      // w = p - (tau/2)(p^T v) v, rank-2 update of own rows
-      F pvs = lane < CS ? part2[lane] : F(0);   // every warp reduces the CS partials
+      // w = p - (tau/2)(p^T v) v formed on the fly; rank-2 update of own rows, then the
+      // row's next-column entry to every replica by the warp that updated it
+      F pvs = F(0);
+      for (int q = lane; q < CS * nw; q += 32) pvs += part2[q];
       for (int o = 16; o > 0; o >>= 1) pvs += __shfl_xor_sync(0xffffffffu, pvs, o);
       const F cc = F(0.5) * tk * pvs;
-      for (int j = m0 + tid; j < n; j += kClThreads) p[j] -= cc * v[j];
-      __syncthreads();
       for (int li = warp; li < nloc; li += nw) {
         const int i = grow(li);
         if (i < m0) continue;
-        const F vi = v[i], wi = p[i];
+        const F vi = v[i], wi = p[i] - cc * vi;
         F* row = rowp(li);
-        for (int j = m0 + lane; j < n; j += 32) row[j] -= vi * p[j] + wi * v[j];
+        for (int j = m0 + lane; j < n; j += 32) row[j] -= vi * (p[j] - cc * v[j]) + wi * v[j];
+        __syncwarp();
+        if (send && i >= m0 + 1 && lane < CS) *cl.map_shared_rank(nxt + i, lane) = row[m0];
       }
-      __syncthreads();
     } else {
       cl.sync();   // matches the p barrier of the other branch (tau is the same everywhere)
+      for (int li = warp; li < nloc; li += nw) {
+        const int i = grow(li);
+        if (send && i >= m0 + 1 && lane < CS) *cl.map_shared_rank(nxt + i, lane) = rowp(li)[m0];
+      }
     }
-    // the next column's entries below its diagonal, to every replica
-    if (m0 + 2 < n) send_column(m0, m0 + 1, colb + (size_t)((k + 1) & 1) * n);
     cl.sync();
   }
   // last 2 x 2 block, rows back to global memory

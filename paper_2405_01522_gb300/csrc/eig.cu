@@ -376,20 +376,23 @@ __global__ void __launch_bounds__(256) k_tridiag_coop(F* __restrict__ A, int n, 
 // Householder tridiagonalisation on one thread-block cluster (same reflectors and outputs
 // as k_tridiagonalise).  The matrix lives in the CTAs' shared memory: rows dealt
 // cyclically (row i in CTA i % CS, local row i / CS).  Every CTA holds a replica of the
-// current column (below the diagonal), from which it forms the norm, tau and v itself; p
-// and the p^T v partials go to every CTA through distributed shared memory.  Per step two
-// hardware cluster barriers separate (v from the replicated column; p = tau A22 v on own
-// rows, sent to all) -> (w = p - (tau/2)(p^T v) v, rank-2 update of own rows, their new
-// next-column entries sent to all).  The rows are copied back to global memory at the
+// current column (below the diagonal), from which it forms the norm, tau and v itself, and
+// of the next column as it stood before this step's update.  Per step one hardware
+// cluster barrier: before it, p = tau A22 v on own rows and each warp's p^T v partial go to
+// every CTA; after it, every CTA knows w = p - (tau/2)(p^T v) v, updates its own rows,
+// sends their entries of the column after next (before the next step's update), and forms
+// the next column itself from its replica minus the rank-2 terms.  p, the partials and
+// the pre-update column replicas are double-buffered, so that a CTA one step ahead never
+// writes what a slower one still reads.  The rows are copied back to global memory at the
 // end (the reflectors below the subdiagonal, for the back-transformation).
 constexpr int kClThreads = 512;
 namespace cg = cooperative_groups;
 
-// shared-memory values of k_tridiag_cluster (rows unless GROWS, v, p, two column replicas,
-// the p^T v partials of every warp of every CTA)
+// shared-memory values of k_tridiag_cluster (rows unless GROWS, v, p x 2, the current
+// column, the pre-update next columns x 2, the p^T v partials of every warp of every CTA x 2)
 template <typename F>
 inline size_t tridiag_cluster_smem(int n, int CS, bool grows) {
-  return ((grows ? 0 : ((size_t)(n + CS - 1) / CS) * n) + 4 * (size_t)n + (size_t)CS * (kClThreads / 32)) *
+  return ((grows ? 0 : ((size_t)(n + CS - 1) / CS) * n) + 6 * (size_t)n + 2 * (size_t)CS * (kClThreads / 32)) *
          sizeof(F);
 }
 
@@ -408,9 +411,10 @@ __global__ void __launch_bounds__(kClThreads, 1) k_tridiag_cluster(F* __restrict
   F* cl_smem = reinterpret_cast<F*>(cl_smem_raw);
   F* R = cl_smem;                               // [nloc][n] (shared-memory rows)
   F* v = GROWS ? cl_smem : R + (size_t)((n + CS - 1) / CS) * n;   // [n]
-  F* p = v + n;                                 // [n] (p, then w)
-  F* colb = p + n;                              // [2][n]: column k (and k + 1) replicas
-  F* part2 = p + 3 * n;                         // [CS][warps] p^T v partials
+  F* pb = v + n;                                // [2][n] p of even / odd steps
+  F* col = pb + 2 * n;                          // [n] current column (below the diagonal)
+  F* pre = col + n;                             // [2][n] next columns before the step's update
+  F* part2 = pre + 2 * n;                       // [2][CS][warps] p^T v partials
   __shared__ F red[kClThreads / 32];
   __shared__ F sh_tau, sh_scale;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = kClThreads / 32;
@@ -445,11 +449,14 @@ __global__ void __launch_bounds__(kClThreads, 1) k_tridiag_cluster(F* __restrict
       if (i >= r0) *cl.map_shared_rank(dst + i, to) = rowp(li)[c];
     }
   };
-  if (n > 2) send_column(0, 1, colb);
+  // replicas of column 0 (rows >= 1) and of column 1 before any update (rows >= 2)
+  if (n > 2) send_column(0, 1, col);
+  if (n > 3) send_column(1, 2, pre + n);
   cl.sync();
   for (int k = 0; k + 2 < n; ++k) {
     const int m0 = k + 1;
-    const F* col = colb + (size_t)(k & 1) * n;
+    F* p = pb + (size_t)(k & 1) * n;
+    F* part = part2 + (size_t)(k & 1) * CS * nw;
     // norm of the column below the subdiagonal and alpha = A[m0][k], from the replica
     // (one warp: the other warps wait at the barrier below anyway)
     if (warp == 0) {
@@ -487,12 +494,10 @@ __global__ void __launch_bounds__(kClThreads, 1) k_tridiag_cluster(F* __restrict
       if (i > m0) rowp(li)[k] = col[i] * sc;
     }
     __syncthreads();
-    F* nxt = colb + (size_t)((k + 1) & 1) * n;
-    const bool send = m0 + 2 < n;   // a next step needs the next column
+    // p_i = tau (A22 v)_i on own rows, a warp per row, sent to every CTA; each warp's
+    // p^T v partial to every CTA's partial array
+    F pv = F(0);
     if (tk != F(0)) {
-      // p_i = tau (A22 v)_i on own rows, a warp per row, sent to every CTA; each warp's
-      // p^T v partial to every CTA's partial array (no CTA-wide reduction)
-      F pv = F(0);
       for (int li = warp; li < nloc; li += nw) {
         const int i = grow(li);
         if (i < m0) continue;
@@ -510,14 +515,19 @@ __global__ void __launch_bounds__(kClThreads, 1) k_tridiag_cluster(F* __restrict
         if (lane < CS) *cl.map_shared_rank(p + i, lane) = pi;
         pv += pi * v[i];   // the same in every lane
       }
-      if (lane < CS) *cl.map_shared_rank(part2 + me * nw + warp, lane) = pv;
-      cl.sync();
-      // w = p - (tau/2)(p^T v) v formed on the fly; rank-2 update of own rows, then the
-      // row's next-column entry to every replica by the warp that updated it
-      F pvs = F(0);
-      for (int q = lane; q < CS * nw; q += 32) pvs += part2[q];
-      for (int o = 16; o > 0; o >>= 1) pvs += __shfl_xor_sync(0xffffffffu, pvs, o);
-      const F cc = F(0.5) * tk * pvs;
+    }
+    if (lane < CS) *cl.map_shared_rank(part + me * nw + warp, lane) = pv;
+    cl.sync();
+    // w = p - (tau/2)(p^T v) v formed on the fly
+    F pvs = F(0);
+    for (int q = lane; q < CS * nw; q += 32) pvs += part[q];
+    for (int o = 16; o > 0; o >>= 1) pvs += __shfl_xor_sync(0xffffffffu, pvs, o);
+    const F cc = F(0.5) * tk * pvs;
+    const F* prek = pre + (size_t)((k + 1) & 1) * n;   // column k + 1 before this update
+    F* pren = pre + (size_t)(k & 1) * n;               // column k + 2 after it (next step's pre)
+    const bool need_next = k + 3 < n, need_after = k + 4 < n;
+    // rank-2 update of own rows, then their entries of column k + 2 to every replica
+    if (tk != F(0)) {
       for (int li = warp; li < nloc; li += nw) {
         const int i = grow(li);
         if (i < m0) continue;
@@ -525,16 +535,24 @@ __global__ void __launch_bounds__(kClThreads, 1) k_tridiag_cluster(F* __restrict
         F* row = rowp(li);
         for (int j = m0 + lane; j < n; j += 32) row[j] -= vi * (p[j] - cc * v[j]) + wi * v[j];
         __syncwarp();
-        if (send && i >= m0 + 1 && lane < CS) *cl.map_shared_rank(nxt + i, lane) = row[m0];
+        if (need_after && i >= k + 3 && lane < CS) *cl.map_shared_rank(pren + i, lane) = row[k + 2];
       }
     } else {
-      cl.sync();   // matches the p barrier of the other branch (tau is the same everywhere)
       for (int li = warp; li < nloc; li += nw) {
         const int i = grow(li);
-        if (send && i >= m0 + 1 && lane < CS) *cl.map_shared_rank(nxt + i, lane) = rowp(li)[m0];
+        if (need_after && i >= k + 3 && lane < CS) *cl.map_shared_rank(pren + i, lane) = rowp(li)[k + 2];
       }
     }
-    cl.sync();
+    // the next column (column m0, rows >= m0 + 1), here: its pre-update replica minus the
+    // rank-2 terms v_j w_m0 + w_j v_m0
+    if (need_next) {
+      const F vm = v[m0], wm = p[m0] - cc * vm;   // column m0's own v and w entries (v_m0 = 1)
+      for (int j = m0 + 1 + tid; j < n; j += kClThreads) {
+        const F vj = v[j];
+        col[j] = tk != F(0) ? prek[j] - (vj * wm + (p[j] - cc * vj) * vm) : prek[j];
+      }
+    }
+    __syncthreads();
   }
   // last 2 x 2 block, rows back to global memory
   if (tid == 0) {

@@ -145,11 +145,11 @@ __global__ void __launch_bounds__(kEigThreads) k_tridiagonalise(double* __restri
 
 // ---------------------------------------------------------------------------------
 // Multi-CTA Householder tridiagonalisation (same reflectors and outputs as
-// k_tridiagonalise).  Rows are dealt cyclically to the CTAs; per step two grid-wide
-// barriers separate (v from the whole current column, p = tau A22 v on own rows, p^T v
-// partials) -> (rank-2 update of own rows and their entries of the next column).  The
-// kernel is launched cooperatively so that all CTAs are resident; the barrier itself is
-// bounded and raises RSX_ETIMEOUT.
+// k_tridiagonalise).  Rows are dealt cyclically to the CTAs; per step one grid-wide
+// barrier separates (v from the CTA's copy of the current column, p = tau A22 v on own
+// rows, p^T v partials) -> (rank-2 update of own rows, their entries of the column after
+// next, the next column formed locally).  The kernel is launched cooperatively so that
+// all CTAs are resident; the barrier itself is bounded and raises RSX_ETIMEOUT.
 constexpr uint32_t kGridWaitLimit = 1u << 24;
 
 struct GridBar {
@@ -232,10 +232,13 @@ __device__ __forceinline__ F cta_sum_partials(const F* part, unsigned int G, F* 
   return *out_sh;
 }
 
-// scratch layout (Fs): p[n], the current and the next column [2][n], part_pv[G].  Every
-// CTA reads the whole current column (below the diagonal) from L2 and forms the norm, tau
-// and v itself, so a step needs two grid barriers: (v; p = tau A22 v on own rows, p^T v
-// partials) -> (w, rank-2 update of own rows, their entries of the next column).
+// scratch layout (Fs): p of even / odd steps [2][n], the next columns as they stood before
+// the step's update [2][n], part_pv of even / odd steps [2][1024].  Every CTA keeps the
+// current column (below the diagonal) in shared memory and forms the norm, tau and v from
+// it; after the step's one grid barrier it knows p, hence w, updates its own rows, writes
+// their entries of the column after next (after the update) and forms the next column from
+// the replica written one step earlier minus the rank-2 terms.  Double buffers keep a CTA
+// one step ahead from overwriting what a slower one still reads.
 template <typename F>
 __global__ void __launch_bounds__(256) k_tridiag_coop(F* __restrict__ A, int n, F* __restrict__ d,
                                                       F* __restrict__ e, F* __restrict__ tau,
@@ -244,32 +247,32 @@ __global__ void __launch_bounds__(256) k_tridiag_coop(F* __restrict__ A, int n, 
   const unsigned int G = gridDim.x;
   const int cta = blockIdx.x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
-  F* pp = scr;
-  F* colg = scr + n;            // [2][n]
-  F* part_pv = scr + 3 * n;
-  extern __shared__ __align__(16) unsigned char tri_smem_raw[];   // local copies of v and p (2 n values)
+  F* ppb = scr;                 // [2][n]
+  F* preg = scr + 2 * n;        // [2][n]
+  F* part_pvb = scr + 4 * n;    // [2][1024]
+  extern __shared__ __align__(16) unsigned char tri_smem_raw[];   // v, w, current column (3 n values)
   F* tri_smem = reinterpret_cast<F*>(tri_smem_raw);
   F* vs = tri_smem;
   F* ps = tri_smem + n;
+  F* col = tri_smem + 2 * n;
   __shared__ F red[8];
   __shared__ F sh_tau, sh_scale, sh_sum;
   bool live = true;
 
-  // own rows' entries of column 0 below the diagonal
-  for (int i = first_owned(1, cta, G) + (int)G * threadIdx.x; i < n; i += (int)G * blockDim.x)
-    colg[i] = A[(size_t)i * n];
+  // column 0 (rows >= 1) straight from A; owners put column 1 (rows >= 2) in preg[1]
+  for (int i = 1 + threadIdx.x; i < n; i += blockDim.x) col[i] = A[(size_t)i * n];
+  for (int i = first_owned(2, cta, G) + (int)G * threadIdx.x; i < n; i += (int)G * blockDim.x)
+    preg[n + i] = A[(size_t)i * n + 1];
   live = grid_barrier(gb, G, wait_limit);
 
   for (int k = 0; k + 2 < n && live; ++k) {
     const int m0 = k + 1;
-    const F* col = colg + (size_t)(k & 1) * n;
-    // ---- reflector from the whole column (every CTA computes the same scalars, in the
-    // same order, from the same values)
+    F* pp = ppb + (size_t)(k & 1) * n;
+    F* part_pv = part_pvb + (size_t)(k & 1) * 1024;
+    // ---- reflector from the column (every CTA computes the same scalars, in the same
+    // order, from the same values)
     F s2 = F(0);
-    for (int j = m0 + 1 + threadIdx.x; j < n; j += blockDim.x) {
-      const F x = __ldcg(col + j);
-      s2 += x * x;
-    }
+    for (int j = m0 + 1 + threadIdx.x; j < n; j += blockDim.x) s2 += col[j] * col[j];
     s2 = warp_sum(s2);
     if (lane == 0) red[warp] = s2;
     __syncthreads();
@@ -279,7 +282,7 @@ __global__ void __launch_bounds__(256) k_tridiag_coop(F* __restrict__ A, int n, 
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-      const F xn2 = sh_sum, alpha = __ldcg(col + m0);
+      const F xn2 = sh_sum, alpha = col[m0];
       F beta;
       if (xn2 == F(0)) {
         sh_tau = F(0);
@@ -301,10 +304,10 @@ __global__ void __launch_bounds__(256) k_tridiag_coop(F* __restrict__ A, int n, 
     __syncthreads();
     const F tk = sh_tau, sc = sh_scale;
     // v (every entry), own rows keep theirs in the column for the back-transformation
-    for (int j = m0 + threadIdx.x; j < n; j += blockDim.x) vs[j] = (j == m0) ? F(1) : __ldcg(col + j) * sc;
-    __syncthreads();
+    for (int j = m0 + threadIdx.x; j < n; j += blockDim.x) vs[j] = (j == m0) ? F(1) : col[j] * sc;
     for (int i = first_owned(m0 + 1, cta, G) + (int)G * threadIdx.x; i < n; i += (int)G * blockDim.x)
-      A[(size_t)i * n + k] = vs[i];
+      A[(size_t)i * n + k] = col[i] * sc;
+    __syncthreads();
     // ---- p_i = tau (A22 v)_i for own rows, partial p^T v
     F pv_part = F(0);
     if (tk != F(0)) {
@@ -335,11 +338,14 @@ __global__ void __launch_bounds__(256) k_tridiag_coop(F* __restrict__ A, int n, 
     }
     if (!(live = grid_barrier(gb, G, wait_limit))) break;
     // ---- w = p - (tau/2)(p^T v) v ; A22 -= v w^T + w v^T on own rows; their entries of
-    // the next column (k + 1, rows below its diagonal) to the other column buffer
-    F* nxt = colg + (size_t)((k + 1) & 1) * n;
+    // column k + 2 after the update; the next column from its replica
+    const F* prek = preg + (size_t)((k + 1) & 1) * n;   // column k + 1 before this update
+    F* pren = preg + (size_t)(k & 1) * n;               // column k + 2 after it
+    const bool need_next = k + 3 < n, need_after = k + 4 < n;
+    F cc = F(0);
     if (tk != F(0)) {
       const F pvs = cta_sum_partials(part_pv, G, red, &sh_sum);
-      const F cc = F(0.5) * tk * pvs;
+      cc = F(0.5) * tk * pvs;
       for (int j = m0 + threadIdx.x; j < n; j += blockDim.x) ps[j] = __ldcg(pp + j) - cc * vs[j];   // w
       __syncthreads();
       int r = 0;
@@ -350,13 +356,21 @@ __global__ void __launch_bounds__(256) k_tridiag_coop(F* __restrict__ A, int n, 
         F* row = A + (size_t)i * n;
         for (int j = m0 + lane; j < n; j += 32) row[j] -= vi * ps[j] + wi * vs[j];
         __syncwarp();
-        if (lane == 0 && i >= m0 + 1) nxt[i] = row[m0];
+        if (lane == 0 && need_after && i >= k + 3) pren[i] = row[k + 2];
+      }
+      if (need_next) {
+        const F vm = vs[m0], wm = ps[m0];   // column m0's own v and w entries (v_m0 = 1)
+        for (int j = m0 + 1 + threadIdx.x; j < n; j += blockDim.x)
+          col[j] = __ldcg(prek + j) - (vs[j] * wm + ps[j] * vm);
       }
     } else {
-      for (int i = first_owned(m0 + 1, cta, G) + (int)G * threadIdx.x; i < n; i += (int)G * blockDim.x)
-        nxt[i] = A[(size_t)i * n + m0];
+      for (int i = first_owned(k + 3, cta, G) + (int)G * threadIdx.x; need_after && i < n;
+           i += (int)G * blockDim.x)
+        pren[i] = A[(size_t)i * n + k + 2];
+      if (need_next)
+        for (int j = m0 + 1 + threadIdx.x; j < n; j += blockDim.x) col[j] = __ldcg(prek + j);
     }
-    live = grid_barrier(gb, G, wait_limit);
+    __syncthreads();
   }
   if (cta == 0 && threadIdx.x == 0) {
     if (!live) {
@@ -739,7 +753,7 @@ template <typename F>
 static F* y_end(F* tw, int n, int nroots) { return tw + 2 * n + (size_t)nroots * n + 5 * (size_t)nroots * n; }
 // coop scratch (v, p, partials, alpha) + the grid barrier, in units of F
 template <typename F>
-static size_t coop_scratch(int n) { return 3 * (size_t)n + 1024 + 2 + (sizeof(GridBar) + sizeof(F) - 1) / sizeof(F) + 2; }
+static size_t coop_scratch(int n) { return 4 * (size_t)n + 2048 + 2 + (sizeof(GridBar) + sizeof(F) - 1) / sizeof(F) + 2; }
 
 static size_t tda_work_doubles_fp64(int n, int nroots) {
   return (size_t)n * n + 14 * (size_t)n + 6 * (size_t)nroots * n + 4096;
@@ -768,8 +782,8 @@ template <typename F>
 static int tridiagonalise(rsx_ctx* c, F* A, int n, F* d, F* e, F* tau, F* scr, F* tw, cudaStream_t s) {
   int coop = 0, per_sm = 0;
   cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, c->device);
-  cudaFuncSetAttribute(k_tridiag_coop<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(2 * (size_t)n * sizeof(F)));
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tridiag_coop<F>, 256, 2 * (size_t)n * sizeof(F));
+  cudaFuncSetAttribute(k_tridiag_coop<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(3 * (size_t)n * sizeof(F)));
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tridiag_coop<F>, 256, 3 * (size_t)n * sizeof(F));
   // FP64: 64 CTAs (fewer make each grid barrier cheaper, the FP64 work per step is
   // small); FP32: one per SM (measured at n = 960: 64 -> 24.0 ms, 152 -> 19.8 ms)
   int gcap = sizeof(F) == 4 ? c->nsm : 64;
@@ -816,13 +830,13 @@ static int tridiagonalise(rsx_ctx* c, F* A, int n, F* d, F* e, F* tau, F* scr, F
       if (r >= 0) return r;
     }
   if (coop && per_sm > 0 && n >= 64 && (force.empty() || force == "coop")) {
-    GridBar* gb = reinterpret_cast<GridBar*>(scr + 3 * (size_t)n + 1024 + 2);
+    GridBar* gb = reinterpret_cast<GridBar*>(scr + 4 * (size_t)n + 2048 + 2);
     cudaMemsetAsync(gb, 0, sizeof(GridBar), s);
     unsigned int wait_limit = c->wait_limit < 0 ? kGridWaitLimit
                               : (unsigned int)std::min<long long>(c->wait_limit, 0xffffffffLL);
     void* args[] = {(void*)&A, (void*)&n, (void*)&d, (void*)&e, (void*)&tau, (void*)&scr, (void*)&gb,
                     (void*)&c->status, (void*)&wait_limit};
-    const size_t smem = 2 * (size_t)n * sizeof(F);
+    const size_t smem = 3 * (size_t)n * sizeof(F);
     cudaFuncSetAttribute(k_tridiag_coop<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     return check_cuda(c, cudaLaunchCooperativeKernel((const void*)k_tridiag_coop<F>, dim3(G), dim3(256), args, smem, s),
                       "cooperative tridiagonalisation");

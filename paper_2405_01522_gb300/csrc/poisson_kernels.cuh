@@ -574,15 +574,17 @@ __global__ void __launch_bounds__(NT) k_spectrum(Geom g, int nq, const Cx<float>
   constexpr int Hy = LY / 2 + 1, Hz = LZ / 2 + 1;
   const int nplane = g.nz * g.ny;
   const int nwork = nq * g.Hx;
+  // transitions are the fastest index of the work items: the CTAs in flight fill the same
+  // 128 x 64 panel tiles (rows = transitions) instead of scattering 128-byte rows
   auto plane_ptr = [&](int w) {
-    const int ql = w / g.Hx, kx = w - ql * g.Hx;
+    const int kx = w / nq, ql = w - kx * nq;
     return inter + (size_t)ql * g.inter_elems() + (size_t)kx * nplane;
   };
   // the plane is staged in the upper halves [ny, 2 ny) of the D rows; the next plane is
   // prefetched there once the z transforms of the upper ky columns are done
   if ((int)blockIdx.x < nwork) prefetch_plane_upper<float>(D, DP, plane_ptr(blockIdx.x), g.nz, g.ny, NT);
   for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
-    const int ql = w / g.Hx, kx = w - ql * g.Hx;
+    const int kx = w / nq, ql = w - kx * nq;
     asm volatile("cp.async.wait_group 0;" ::: "memory");
     __syncthreads();
     y_forward<float, AY, NT>(D, DP, g.nz, g.ny, twy, sc, g.ny);

@@ -601,14 +601,17 @@ __global__ void __launch_bounds__(NT) k_spectrum(Geom g, int nq, const Cx<float>
 #pragma unroll
       for (int k1 = 1; k1 < AZ; ++k1) twf[k1] = twz[t * AZ + k1];
     }
-    // columns ky: upper half first, then the prefetch of the next plane, then the lower half
-    for (int half = 1; half >= 0; --half) {
-      if (half == 0) {
-        __syncthreads();   // every read of the upper halves is done
-        if (wn < nwork) prefetch_plane_upper<float>(D, DP, plane_ptr(wn), g.nz, g.ny, NT);
-      }
-      for (int kyl = line; kyl < LY / 2; kyl += LPC) {
-        const int ky = half * (LY / 2) + kyl;
+    // columns ky: the upper half [LY/2, LY) first, then the lower half; slot s of line l
+    // takes flat position f = s LPC + l (f < LY/2: upper column LY/2 + f, else lower
+    // column f - LY/2), so every line runs the same number of columns, and after slot
+    // kPre - 1 (when every upper column is done; possibly the last slot) the next plane is
+    // prefetched into the upper halves of the D rows
+    constexpr int kSlots = (LY + LPC - 1) / LPC;
+    constexpr int kPre = (LY / 2 + LPC - 1) / LPC;
+    for (int slot = 0; slot < kSlots; ++slot) {
+      const int f = slot * LPC + line;
+      if (f < LY) {   // uniform in a warp: LPC is even, a warp's two lines are f, f + 1 with LY even
+        const int ky = f < LY / 2 ? LY / 2 + f : f - LY / 2;
         const int iy = ky <= LY / 2 ? ky : LY - ky;
         const float* vcol = vrow + (size_t)iy * Hz;
         constexpr int AIN = (AZ % 2 == 0) ? AZ / 2 : AZ;
@@ -660,6 +663,10 @@ __global__ void __launch_bounds__(NT) k_spectrum(Geom g, int nq, const Cx<float>
           *reinterpret_cast<uint4*>(lo + off) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
         }
         __syncwarp();
+      }
+      if (slot == kPre - 1) {
+        __syncthreads();   // every read of the upper halves is done
+        if (wn < nwork) prefetch_plane_upper<float>(D, DP, plane_ptr(wn), g.nz, g.ny, NT);
       }
     }
   }

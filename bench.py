@@ -125,8 +125,10 @@ def aggregate_rate(world, units_per_step, steps, ms_max):
 
 
 # Real flops of the register DFTs as implemented (adds + multiplies; odd primes by the
-# symmetric split, 6/10/12/14 by Good-Thomas, 8/16 by radix 2/4).
-DFT_FLOPS = {1: 0, 2: 4, 3: 16, 4: 16, 5: 52, 6: 44, 7: 102, 8: 60, 10: 124, 12: 112, 14: 232, 16: 182}
+# symmetric split, 6/10/12/14/24 by Good-Thomas, 8/16 by radix 2/4; a rotation by +-i is a
+# swap, no flops).
+DFT_FLOPS = {1: 0, 2: 4, 3: 16, 4: 16, 5: 52, 6: 44, 7: 102, 8: 60, 10: 124, 12: 112, 14: 232, 16: 176,
+             24: 3 * 60 + 8 * 16}
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12     # SMs x FP32 lanes x FMA x max SM clock
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) from ncu captures of the same
@@ -136,12 +138,57 @@ PASS2_DRAM_BYTES_PER_PAIR_96 = 7.27e9 / 512
 SYRK_DRAM_PER_PANEL_BYTE = 1.938e9 / 1.850e9    # DRAM bytes per byte of the two bf16 panels
 
 
+def _modinv(a, m):
+    return next(i for i in range(1, m + 1) if (a * i) % m == 1 % m)
+
+
+_PFA = {6: (2, 3), 10: (2, 5), 12: (3, 4), 14: (2, 7), 24: (3, 8)}
+
+
+def _pfa_maps(A):
+    P, Q = _PFA[A]
+    qinv, pinv = _modinv(Q % P, P), _modinv(P % Q, Q)
+    return P, Q, (lambda n1, n2: (Q * n1 + P * n2) % A), (lambda k1, k2: (Q * qinv * k1 + P * pinv * k2) % A)
+
+
+def _small_in(m):
+    """P-point DFT (P = 2, 3) with the inputs flagged False zero (all outputs formed)."""
+    n = sum(m)
+    if len(m) == 2:
+        return 4 if n == 2 else 0
+    return DFT_FLOPS[3] if n == 3 else 12 if n == 2 else (0 if m[0] else 8)
+
+
+def _small_out(w):
+    """P-point DFT (P = 2, 3) forming only the outputs flagged True."""
+    n = sum(w)
+    if len(w) == 2:
+        return 4 if n == 2 else 2 * n
+    if n == 0:
+        return 0
+    return 4 if (w[0] and n == 1) else 10 + 2 * n
+
+
 def _half_in(A):
-    return 2 * DFT_FLOPS[A // 2] + (A // 2 - 1) * 6 if A % 2 == 0 else DFT_FLOPS[A]
+    """A-point DFT whose inputs A/2 .. A are zero."""
+    if A % 2:
+        return DFT_FLOPS[A]
+    if A in _PFA:   # zero-skipping P-point DFTs, then P complete Q-point DFTs
+        P, Q, fin, _ = _pfa_maps(A)
+        return sum(_small_in([fin(n1, n2) < A // 2 for n1 in range(P)]) for n2 in range(Q)) + P * DFT_FLOPS[Q]
+    return 2 * DFT_FLOPS[A // 2] + max(A // 2 - 2, 0) * 6   # radix 2, the rotation by i free
 
 
 def _half_out(A):
-    return 2 * DFT_FLOPS[A // 2] + (A // 2 - 1) * 6 + A if A % 2 == 0 else DFT_FLOPS[A]
+    """A-point DFT of which outputs 0 .. A/2 are formed."""
+    if A % 2:
+        return DFT_FLOPS[A]
+    if A in _PFA:   # P complete Q-point DFTs, then P-point DFTs forming the kept outputs
+        P, Q, _, fout = _pfa_maps(A)
+        return P * DFT_FLOPS[Q] + sum(_small_out([fout(k1, k2) < A // 2 for k1 in range(P)]) for k2 in range(Q))
+    if A == 16:     # radix 4, second 4-point DFTs forming two outputs each
+        return 4 * 16 + 8 * 6 + 4 * 12
+    return 2 * DFT_FLOPS[A // 2] + max(A // 2 - 2, 0) * 6 + A
 
 
 def line_flops(A, kind):

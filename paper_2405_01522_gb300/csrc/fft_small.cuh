@@ -120,10 +120,12 @@ RSX_HD constexpr double trig_s(int p, int j) {
 }
 
 // cos(2 pi a / 24), 0 <= a < 24: multiples of 15 degrees, (sqrt 6 +- sqrt 2) / 4 at 15 and 75
-RSX_HD constexpr double trig24_c(int a) {
+RSX_HD constexpr double trig24_c_q(int a) {   // first quadrant, 0 <= a <= 6
   return a == 0 ? 1.0 : a == 1 ? 0.96592582628906828675 : a == 2 ? 0.86602540378443864676
-       : a == 3 ? 0.70710678118654752440 : a == 4 ? 0.5 : a == 5 ? 0.25881904510252076235 : a == 6 ? 0.0
-       : a < 12 ? -trig24_c(12 - a) : a == 12 ? -1.0 : trig24_c(24 - a);
+       : a == 3 ? 0.70710678118654752440 : a == 4 ? 0.5 : a == 5 ? 0.25881904510252076235 : 0.0;
+}
+RSX_HD constexpr double trig24_c(int a) {
+  return a <= 6 ? trig24_c_q(a) : a <= 12 ? -trig24_c_q(12 - a) : a <= 18 ? -trig24_c_q(a - 12) : trig24_c_q(24 - a);
 }
 RSX_HD constexpr double trig24_s(int a) { return trig24_c((a + 18) % 24); }   // sin x = cos(x - pi / 2)
 
@@ -250,8 +252,8 @@ struct Dft<16, S> {
       Dft<4, S>::run(c);
 #pragma unroll
       for (int k1 = 0; k1 < 4; ++k1) {
-        const int e = j2 * k1;
-        y[j2][k1] = (e == 0) ? c[k1] : rot<S>(c[k1], R(trig_c(16, e)), R(trig_s(16, e)));
+        const int e = j2 * k1;   // e = 4 is the rotation by S i: a swap, no multiplies
+        y[j2][k1] = (e == 0) ? c[k1] : (e == 4) ? mul_si<S>(c[k1]) : rot<S>(c[k1], R(trig_c(16, e)), R(trig_s(16, e)));
       }
     }
 #pragma unroll
@@ -321,7 +323,7 @@ struct DftHalfIn {
 #pragma unroll
     for (int a = 0; a < H; ++a) {
       e[a] = v[a];
-      o[a] = (a == 0) ? v[a] : rot<S>(v[a], R(trig_even_c(A, a)), R(trig_even_s(A, a)));
+      o[a] = (a == 0) ? v[a] : (4 * a == A) ? mul_si<S>(v[a]) : rot<S>(v[a], R(trig_even_c(A, a)), R(trig_even_s(A, a)));
     }
     Dft<H, S>::run(e);
     Dft<H, S>::run(o);
@@ -350,7 +352,235 @@ struct DftHalfOut {
     Dft<H, S>::run(o);
 #pragma unroll
     for (int a = 0; a < H; ++a)
-      out[a] = e[a] + ((a == 0) ? o[a] : rot<S>(o[a], R(trig_even_c(A, a)), R(trig_even_s(A, a))));
+      out[a] = e[a] + ((a == 0) ? o[a] : (4 * a == A) ? mul_si<S>(o[a]) : rot<S>(o[a], R(trig_even_c(A, a)), R(trig_even_s(A, a))));
+  }
+};
+
+
+// Pruned 3-point DFTs for the prime-factor codelets below (w = exp(S 2 pi i / 3)):
+//   X0 = x0 + a,  X1,2 = x0 - a / 2 +- S i (sqrt 3 / 2) b,   a = x1 + x2,  b = x1 - x2.
+// dft3_in<S, N0, N1, N2>: inputs flagged false are zero and never read (all three outputs).
+template <int S, bool N0, bool N1, bool N2, typename R>
+RSX_HD void dft3_in(Cx<R>& x0, Cx<R>& x1, Cx<R>& x2) {
+  const R h = R(-0.5), s3 = R(0.86602540378443864676);
+  static_assert(N0 || N1 || N2, "at least one input");
+  if constexpr (!N1 && !N2) {   // X_k = x0
+    x1 = x0;
+    x2 = x0;
+  } else if constexpr (!N0 && !N2) {   // only x1: X_k = x1 w^k
+    const Cx<R> re = cscale(x1, h), u = mul_si<S>(cscale(x1, s3));
+    x0 = x1;
+    x2 = re - u;
+    x1 = re + u;
+  } else if constexpr (!N0 && !N1) {   // only x2: X_k = x2 w^2k
+    const Cx<R> re = cscale(x2, h), u = mul_si<S>(cscale(x2, s3));
+    x0 = x2;
+    x1 = re - u;
+    x2 = re + u;
+  } else if constexpr (!N2) {   // a = b = x1
+    const Cx<R> re = cfma(x1, h, x0), u = mul_si<S>(cscale(x1, s3));
+    x0 = x0 + x1;
+    x1 = re + u;
+    x2 = re - u;
+  } else if constexpr (!N1) {   // a = x2, b = -x2
+    const Cx<R> re = cfma(x2, h, x0), u = mul_si<S>(cscale(x2, s3));
+    x0 = x0 + x2;
+    x1 = re - u;
+    x2 = re + u;
+  } else if constexpr (!N0) {
+    const Cx<R> a = x1 + x2, b = x1 - x2;
+    const Cx<R> re = cscale(a, h), u = mul_si<S>(cscale(b, s3));
+    x0 = a;
+    x1 = re + u;
+    x2 = re - u;
+  } else {
+    Cx<R> v[3] = {x0, x1, x2};
+    Dft<3, S>::run(v);
+    x0 = v[0];
+    x1 = v[1];
+    x2 = v[2];
+  }
+}
+
+// dft3_out<S, W0, W1, W2>: all inputs, only the outputs flagged true are formed (in place).
+template <int S, bool W0, bool W1, bool W2, typename R>
+RSX_HD void dft3_out(Cx<R>& x0, Cx<R>& x1, Cx<R>& x2) {
+  const R h = R(-0.5), s3 = R(0.86602540378443864676);
+  const Cx<R> a = x1 + x2;
+  if constexpr (W0 && !W1 && !W2) {
+    x0 = x0 + a;
+  } else {
+    const Cx<R> b = x1 - x2;
+    const Cx<R> re = cfma(a, h, x0), u = mul_si<S>(cscale(b, s3));
+    if constexpr (W0) x0 = x0 + a;
+    if constexpr (W1) x1 = re + u;
+    if constexpr (W2) x2 = re - u;
+  }
+}
+
+// 4-point DFT forming only outputs 0 and K (K = 1, 3) or 1 and 2 (in place)
+template <int S, int W, typename R>
+RSX_HD void dft4_two_out(Cx<R>* v) {   // W: 1 -> {0, 1}, 3 -> {0, 3}, 12 -> {1, 2}
+  const Cx<R> a = v[0] + v[2], b = v[0] - v[2], c = v[1] + v[3], d = mul_si<S>(v[1] - v[3]);
+  if constexpr (W == 1) {
+    v[0] = a + c;
+    v[1] = b + d;
+  } else if constexpr (W == 3) {
+    v[0] = a + c;
+    v[3] = b - d;
+  } else {
+    v[1] = b + d;
+    v[2] = a - c;
+  }
+}
+
+// 2-point DFTs with zero inputs skipped / unwanted outputs not formed (in place)
+template <bool N0, bool N1, typename R>
+RSX_HD void dft2_in(Cx<R>& x0, Cx<R>& x1) {
+  static_assert(N0 || N1, "at least one input");
+  if constexpr (N0 && N1) {
+    const Cx<R> a = x0;
+    x0 = a + x1;
+    x1 = a - x1;
+  } else if constexpr (N0) {
+    x1 = x0;
+  } else {
+    x0 = x1;
+    x1 = cx<R>(-x1.x, -x1.y);
+  }
+}
+template <bool W0, bool W1, typename R>
+RSX_HD void dft2_out(Cx<R>& x0, Cx<R>& x1) {
+  if constexpr (W0 && W1) {
+    const Cx<R> a = x0;
+    x0 = a + x1;
+    x1 = a - x1;
+  } else if constexpr (W0) {
+    x0 = x0 + x1;
+  } else if constexpr (W1) {
+    x1 = x0 - x1;
+  }
+}
+
+// Pruned Good-Thomas DFTs of length N = P Q (P = 2 or 3, gcd(P, Q) = 1), the index maps
+// of DftPfa: input (Q n1 + P n2) mod N, output (Q qinv k1 + P pinv k2) mod N.
+//   half in  (inputs N/2 .. N zero): per column n2 the P-point DFT over n1 skips the zero
+//            inputs, then the Q-point DFTs over n2 are complete;
+//   half out (outputs 0 .. N/2 kept): the Q-point DFTs over n2 first, complete, then per
+//            column k2 the P-point DFT over n1 forms only the kept outputs.
+template <int P, int Q>
+struct PfaMap {
+  static constexpr int N = P * Q;
+  RSX_HD static constexpr int in(int n1, int n2) { return (Q * n1 + P * n2) % N; }
+  RSX_HD static constexpr int out(int k1, int k2) { return (Q * modinv(Q % P, P) * k1 + P * modinv(P % Q, Q) * k2) % N; }
+  RSX_HD static constexpr bool in_nz(int n1, int n2) { return n1 < P && in(n1, n2) < N / 2; }
+  RSX_HD static constexpr bool out_kept(int k1, int k2) { return k1 < P && out(k1, k2) < N / 2; }
+};
+
+template <int P, int Q, int S, int C>
+struct PfaHalfInCols {   // columns n2 = C .. Q-1
+  template <typename R>
+  RSX_HD static void run(const Cx<R>* v, Cx<R> (&y)[P][Q]) {
+    if constexpr (C < Q) {
+      using M = PfaMap<P, Q>;
+      constexpr bool m0 = M::in_nz(0, C), m1 = M::in_nz(1, C), m2 = M::in_nz(2, C);
+      if constexpr (m0) y[0][C] = v[M::in(0, C)];
+      if constexpr (m1) y[1][C] = v[M::in(1, C)];
+      if constexpr (P == 2) {
+        dft2_in<m0, m1>(y[0][C], y[1][C]);
+      } else {
+        if constexpr (m2) y[2][C] = v[M::in(2, C)];
+        dft3_in<S, m0, m1, m2>(y[0][C], y[1][C], y[2][C]);
+      }
+      PfaHalfInCols<P, Q, S, C + 1>::run(v, y);
+    }
+  }
+};
+
+template <int P, int Q, int S, int C>
+struct PfaHalfOutCols {   // columns k2 = C .. Q-1
+  template <typename R>
+  RSX_HD static void run(Cx<R> (&y)[P][Q], Cx<R>* out) {
+    if constexpr (C < Q) {
+      using M = PfaMap<P, Q>;
+      constexpr bool w0 = M::out_kept(0, C), w1 = M::out_kept(1, C), w2 = M::out_kept(2, C);
+      if constexpr (P == 2) {
+        dft2_out<w0, w1>(y[0][C], y[1][C]);
+      } else {
+        if constexpr (w0 || w1 || w2) dft3_out<S, w0, w1, w2>(y[0][C], y[1][C], y[2][C]);
+      }
+      if constexpr (w0) out[M::out(0, C)] = y[0][C];
+      if constexpr (w1) out[M::out(1, C)] = y[1][C];
+      if constexpr (w2) out[M::out(2, C)] = y[2][C];
+      PfaHalfOutCols<P, Q, S, C + 1>::run(y, out);
+    }
+  }
+};
+
+template <int P, int Q, int S>
+struct DftPfaHalfIn {
+  template <typename R>
+  RSX_HD static void run(const Cx<R>* v, Cx<R>* out) {
+    Cx<R> y[P][Q];
+    PfaHalfInCols<P, Q, S, 0>::run(v, y);
+#pragma unroll
+    for (int k1 = 0; k1 < P; ++k1) {
+      Dft<Q, S>::run(y[k1]);
+#pragma unroll
+      for (int k2 = 0; k2 < Q; ++k2) out[PfaMap<P, Q>::out(k1, k2)] = y[k1][k2];
+    }
+  }
+};
+
+template <int P, int Q, int S>
+struct DftPfaHalfOut {
+  template <typename R>
+  RSX_HD static void run(const Cx<R>* v, Cx<R>* out) {
+    Cx<R> y[P][Q];
+#pragma unroll
+    for (int n1 = 0; n1 < P; ++n1) {
+#pragma unroll
+      for (int n2 = 0; n2 < Q; ++n2) y[n1][n2] = v[PfaMap<P, Q>::in(n1, n2)];
+      Dft<Q, S>::run(y[n1]);
+    }
+    PfaHalfOutCols<P, Q, S, 0>::run(y, out);
+  }
+};
+
+template <int S> struct DftHalfIn<6, S> : DftPfaHalfIn<2, 3, S> {};
+template <int S> struct DftHalfIn<10, S> : DftPfaHalfIn<2, 5, S> {};
+template <int S> struct DftHalfIn<12, S> : DftPfaHalfIn<3, 4, S> {};
+template <int S> struct DftHalfIn<14, S> : DftPfaHalfIn<2, 7, S> {};
+template <int S> struct DftHalfIn<24, S> : DftPfaHalfIn<3, 8, S> {};
+template <int S> struct DftHalfOut<6, S> : DftPfaHalfOut<2, 3, S> {};
+template <int S> struct DftHalfOut<10, S> : DftPfaHalfOut<2, 5, S> {};
+template <int S> struct DftHalfOut<12, S> : DftPfaHalfOut<3, 4, S> {};
+template <int S> struct DftHalfOut<14, S> : DftPfaHalfOut<2, 7, S> {};
+template <int S> struct DftHalfOut<24, S> : DftPfaHalfOut<3, 8, S> {};
+
+// The 16-point DFT of which only outputs 0 .. 7 are wanted: Dft<16>'s radix-4 steps with
+// the second 4-point DFTs forming outputs k2 = 0, 1 only (k = k1 + 4 k2 < 8).
+template <int S>
+struct DftHalfOut<16, S> {
+  template <typename R>
+  RSX_HD static void run(const Cx<R>* v, Cx<R>* out) {
+    Cx<R> y[4][4];
+#pragma unroll
+    for (int j2 = 0; j2 < 4; ++j2) {
+      Cx<R> c[4] = {v[j2], v[j2 + 4], v[j2 + 8], v[j2 + 12]};
+      Dft<4, S>::run(c);
+#pragma unroll
+      for (int k1 = 0; k1 < 4; ++k1) {
+        const int e = j2 * k1;
+        y[k1][j2] = (e == 0) ? c[k1] : (e == 4) ? mul_si<S>(c[k1]) : rot<S>(c[k1], R(trig_c(16, e)), R(trig_s(16, e)));
+      }
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+      dft4_two_out<S, 1>(y[k1]);
+      out[k1] = y[k1][0];
+      out[k1 + 4] = y[k1][1];
+    }
   }
 };
 

@@ -132,9 +132,9 @@ DFT_FLOPS = {1: 0, 2: 4, 3: 16, 4: 16, 5: 52, 6: 44, 7: 102, 8: 60, 10: 124, 12:
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12     # SMs x FP32 lanes x FMA x max SM clock
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) from ncu captures of the same
-# kernels: pass 2 on the full 512-pair launch at 96^3 (3.67 + 3.60 GB = 14.2 MB per pair, a
-# one-pass metric set), the SYRK on a small case scaled by the panel bytes it reads
-PASS2_DRAM_BYTES_PER_PAIR_96 = 7.27e9 / 512
+# kernels: pass 2 on the full 512-pair launch at 96^3 (a one-pass metric set), per line
+# split and CTA size; the SYRK on a small case scaled by the panel bytes it reads
+PASS2_DRAM_BYTES_PER_PAIR_96 = {}
 SYRK_DRAM_PER_PANEL_BYTE = 1.938e9 / 1.850e9    # DRAM bytes per byte of the two bf16 panels
 
 
@@ -205,16 +205,29 @@ def line_flops(A, kind):
     raise ValueError(kind)
 
 
-def algorithmic_flops(kernel, shape, nq, npsi_out):
-    """Implemented FP32 flops of one launch over nq pairs (npsi_out outputs for pass 3)."""
+def line_flops_l8(A, kind):
+    """Flops of one line of length 16 A split 8 lanes x 2A: 2A-point DFTs (pruned halves)
+    on 8 lanes, 8 x (2A - 1) twiddles, 2A 8-point DFTs."""
+    tw = 8 * (2 * A - 1) * 6
+    if kind == "fwd_pruned":
+        return 8 * _half_in(2 * A) + tw + 2 * A * DFT_FLOPS[8]
+    if kind in ("inv_keep_half", "z_inverse"):
+        return 2 * A * DFT_FLOPS[8] + tw + 8 * _half_out(2 * A)
+    raise ValueError(kind)
+
+
+def algorithmic_flops(kernel, shape, nq, npsi_out, lanes=16):
+    """Implemented FP32 flops of one launch over nq pairs (npsi_out outputs for pass 3);
+    lanes: the line split of pass 2 (16 x A or 8 x 2A)."""
     nz, ny, nx = shape
     Ax, Ay, Az = nx // 8, ny // 8, nz // 8
     Hx = nx + 1
     if kernel == "pass2_yz_kernel":
         Ly = 16 * Ay
-        plane = (nz * line_flops(Ay, "fwd_pruned")
-                 + Ly * (line_flops(Az, "fwd_pruned") + 2 * 16 * Az + line_flops(Az, "z_inverse"))
-                 + nz * line_flops(Ay, "inv_keep_half"))
+        lf = line_flops_l8 if lanes == 8 else line_flops
+        plane = (nz * lf(Ay, "fwd_pruned")
+                 + Ly * (lf(Az, "fwd_pruned") + 2 * 16 * Az + lf(Az, "z_inverse"))
+                 + nz * lf(Ay, "inv_keep_half"))
         return nq * Hx * plane
     if kernel == "pass1_x_forward":
         return nq * nz * (ny // 2) * (line_flops(Ax, "fwd_pruned") + 8 * Hx)
@@ -320,19 +333,25 @@ def run_rsx(args, rank, local_rank, world):
         # report the ALU roofline, with the HBM view alongside
         byts = [algorithmic_bytes(top, shape, nq, NOCC, NPSI if nq == SOLVES_EXCHANGE else 0)
                 for nq in per_launch_pairs[top]]
-        flops = [algorithmic_flops(top, shape, nq, 0) for nq in per_launch_pairs[top]]
+        lanes = (tuning or {}).get("p2_lanes", 16)
+        p2_threads = (tuning or {}).get("p2_threads", int(os.environ.get("RSX_PASS2_THREADS", "256")))
+        flops = [algorithmic_flops(top, shape, nq, 0, lanes) for nq in per_launch_pairs[top]]
         avg_bytes = sum(byts) / len(byts)
         avg_flops = sum(flops) / len(flops)
         avg_ms = kernels[top]["ms_per_launch"]
         ach_f = avg_flops / (avg_ms / 1e3) / 1e12
         ach_b = avg_bytes / (avg_ms / 1e3) / 1e9
         traffic = None
-        if top == "pass2_yz_kernel" and tuple(shape) == (96, 96, 96):
-            traffic = PASS2_DRAM_BYTES_PER_PAIR_96 * sum(per_launch_pairs[top]) / len(per_launch_pairs[top])
-        roof = {"kernel": top, "bound": "alu", "achieved": round(ach_f, 2), "peak": round(FP32_PEAK_TFLOPS, 2),
+        per_pair = PASS2_DRAM_BYTES_PER_PAIR_96.get((lanes, p2_threads))
+        if top == "pass2_yz_kernel" and tuple(shape) == (96, 96, 96) and per_pair:
+            traffic = per_pair * sum(per_launch_pairs[top]) / len(per_launch_pairs[top])
+        split = "8 lanes x 2A" if lanes == 8 else "16 lanes x A"
+        roof = {"kernel": f"{top} ({split}, {p2_threads} threads)", "bound": "alu", "achieved": round(ach_f, 2),
+                "peak": round(FP32_PEAK_TFLOPS, 2),
                 "unit": "TFLOP/s", "frac": round(ach_f / FP32_PEAK_TFLOPS, 4), "traffic": traffic,
-                "traffic_source": "ncu DRAM bytes of the 512-pair launch (14.2 MB per pair) times the average pairs "
-                                  "per launch" if traffic else None,
+                "traffic_source": (f"ncu DRAM bytes of the 512-pair launch ({per_pair / 1e6:.1f} MB per pair) times "
+                                   "the average pairs per launch") if traffic else
+                                  "none: no capture of this kernel build yet",
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 (FMA) x 2.07 GHz",
                 "algorithmic_flops_per_launch": avg_flops,
                 "hbm_view": {"achieved_gbs": round(ach_b, 1), "peak_gbs": hbm_peak, "frac": round(ach_b / hbm_peak, 4),

@@ -127,8 +127,8 @@ cudaError_t launch_pass2_l8(const Geom& g, int nq, Cx<float>* inter, const Cx<fl
                             cudaStream_t s) {
   const int nt = pass2_l8_threads<A>(g);
   const size_t smem = pass2_l8_smem<A>(nt);
-  // 384 threads: twiddles from the shared table (no spills); 256: held in registers
-  auto k = nt == 384 ? k_pass2_l8<A, 384, true> : k_pass2_l8<A, 256, false>;
+  // twiddles held in registers (153 registers at A = 12: 384 threads fit without spills)
+  auto k = nt == 384 ? k_pass2_l8<A, 384, false> : k_pass2_l8<A, 256, false>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k<<<grid, nt, smem, s>>>(g, nq, inter, tw8, vl8);

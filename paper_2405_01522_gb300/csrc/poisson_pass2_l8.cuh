@@ -97,7 +97,8 @@ __device__ __forceinline__ void l8_stage1_inv(Cx<float>* dst, int es, int t, int
 }
 
 // one (pair, kx) plane; D: (nz x My) work plane, row pitch M + 1, input rows staged in
-// columns [ny, 2 ny) (prefetched); the result goes back to the plane P in global memory
+// columns [ny, 2 ny) (prefetched); the y inverse writes the result to the plane P in
+// global memory
 template <int A, int NT, class TW>
 __device__ __forceinline__ void l8_plane(Cx<float>* P, int kx, int Hy, const float* __restrict__ vl8, Cx<float>* D,
                                          Cx<float>* sc, int lp, int t, int par, unsigned lmask, const TW& tw,
@@ -152,7 +153,8 @@ __device__ __forceinline__ void l8_plane(Cx<float>* P, int kx, int Hy, const flo
     __syncwarp(lmask);
   }
   __syncthreads();
-  // ---- y inverse of the nz rows, keeping y < ny
+  // ---- y inverse of the nz rows, keeping y < ny: the rows go from registers straight to
+  // the plane in global memory
   for (int z = lp; z < NB; z += NL) {
     Cx<float>* row = D + z * DP;
 #pragma unroll
@@ -165,13 +167,11 @@ __device__ __forceinline__ void l8_plane(Cx<float>* P, int kx, int Hy, const flo
       l8_store_row(sc, k1 ^ par, u);
     }
     __syncwarp(lmask);
-    l8_stage1_inv<A>(row, 1, t, par, tw, sc);
+    l8_stage1_inv<A>(P + z * NB, 1, t, par, tw, sc);
     __syncwarp(lmask);
   }
-  __syncthreads();
+  __syncthreads();   // every read of D's upper halves is done
   if (Pnext) prefetch_plane_upper<float>(D, DP, Pnext, NB, NB, NT);
-  store_plane<NT>(D, DP, P, NB, NB);
-  __syncthreads();
 }
 
 // Persistent grid over the work items (pair, kx); the plane lives in shared memory and the

@@ -333,7 +333,7 @@ def run_rsx(args, rank, local_rank, world):
         # report the ALU roofline, with the HBM view alongside
         byts = [algorithmic_bytes(top, shape, nq, NOCC, NPSI if nq == SOLVES_EXCHANGE else 0)
                 for nq in per_launch_pairs[top]]
-        lanes = (tuning or {}).get("p2_lanes", 16)
+        lanes = (tuning or {}).get("p2_lanes", 8 if os.environ.get("RSX_PASS2_LANES") == "8" else 16)
         p2_threads = (tuning or {}).get("p2_threads", int(os.environ.get("RSX_PASS2_THREADS", "256")))
         flops = [algorithmic_flops(top, shape, nq, 0, lanes) for nq in per_launch_pairs[top]]
         avg_bytes = sum(byts) / len(byts)

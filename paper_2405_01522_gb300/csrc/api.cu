@@ -442,6 +442,7 @@ int rsx_create(rsx_ctx** out, int nz, int ny, int nx, double h, int precision, i
   if (const char* e = getenv("RSX_PASS1_GROUP")) g.p1_group = atoi(e) > 0 ? atoi(e) : 0;
   g.p2_global = 0;
   g.p2_lanes = 16;
+  if (const char* e = getenv("RSX_PASS2_LANES")) g.p2_lanes = atoi(e) == 8 ? 8 : 16;
   cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, device);
   size_t freeb = 0, totalb = 0;
   cudaMemGetInfo(&freeb, &totalb);

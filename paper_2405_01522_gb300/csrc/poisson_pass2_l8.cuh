@@ -96,6 +96,45 @@ __device__ __forceinline__ void l8_stage1_inv(Cx<float>* dst, int es, int t, int
   for (int a = 0; a < A; ++a) dst[(t + 8 * a) * es] = o[a];
 }
 
+// this lane's kernel factors of one folded column |ky| (lane order: kz = (t + 8 j) + 2A k2,
+// j < 2A / 8, k2 < 8), 2 x 2A / 8 16-byte loads
+template <int J>
+__device__ __forceinline__ void l8_load_factors(float4 (&fac)[2 * J], const float* __restrict__ src) {
+  const float4* vq = reinterpret_cast<const float4*>(src);
+#pragma unroll
+  for (int i = 0; i < 2 * J; ++i) fac[i] = __ldg(vq + i);
+}
+
+// z forward, kernel multiply, z inverse of one column (col = D + ky, row pitch M + 1)
+template <int A, class TW>
+__device__ __forceinline__ void l8_z_column(Cx<float>* col, int t, int par, unsigned lmask, const TW& tw,
+                                            Cx<float>* sc, const float4 (&fac)[2 * (2 * A / 8)]) {
+  constexpr int A2 = 2 * A, J = A2 / 8, DP = 16 * A + 1;
+  l8_stage1_fwd<A>(col, DP, t, par, tw, sc);
+  __syncwarp(lmask);
+#pragma unroll
+  for (int j = 0; j < J; ++j) {
+    const int r = (t + 8 * j) ^ par;
+    Cx<float> u[8];
+    l8_load_row(u, sc, r);
+    Dft<8, -1>::run(u);
+    const float4 m0 = fac[2 * j], m1 = fac[2 * j + 1];
+    u[0] = cscale(u[0], m0.x);
+    u[1] = cscale(u[1], m0.y);
+    u[2] = cscale(u[2], m0.z);
+    u[3] = cscale(u[3], m0.w);
+    u[4] = cscale(u[4], m1.x);
+    u[5] = cscale(u[5], m1.y);
+    u[6] = cscale(u[6], m1.z);
+    u[7] = cscale(u[7], m1.w);
+    Dft<8, 1>::run(u);
+    l8_store_row(sc, r, u);   // row r is read and written by this lane only
+  }
+  __syncwarp(lmask);
+  l8_stage1_inv<A>(col, DP, t, par, tw, sc);
+  __syncwarp(lmask);
+}
+
 // one (pair, kx) plane; D: (nz x My) work plane, row pitch M + 1, input rows staged in
 // columns [ny, 2 ny) (prefetched); the y inverse writes the result to the plane P in
 // global memory
@@ -123,34 +162,17 @@ __device__ __forceinline__ void l8_plane(Cx<float>* P, int kx, int Hy, const flo
     __syncwarp(lmask);
   }
   __syncthreads();
-  // ---- z forward, kernel multiply, z inverse on the M columns ky
+  // ---- z forward, kernel multiply, z inverse on the M columns ky.  Columns ky and M - ky
+  // use the same kernel factors (the table is folded in |ky|): a line takes them as one
+  // item (item 0: the two unpaired columns 0 and M / 2), loading the factors once, before
+  // the first column's stage 1, which covers the loads' latency.
   const float* vrow = vl8 + (size_t)kx * Hy * M;
-  for (int ky = lp; ky < M; ky += NL) {
-    const int iy = ky <= M / 2 ? ky : M - ky;
-    l8_stage1_fwd<A>(D + ky, DP, t, par, tw, sc);
-    __syncwarp(lmask);
-    const float4* vq = reinterpret_cast<const float4*>(vrow + (size_t)iy * M + t * A2);
-#pragma unroll
-    for (int j = 0; j < J; ++j) {
-      const int r = (t + 8 * j) ^ par;
-      Cx<float> u[8];
-      l8_load_row(u, sc, r);
-      Dft<8, -1>::run(u);
-      const float4 m0 = __ldg(vq + 2 * j), m1 = __ldg(vq + 2 * j + 1);
-      u[0] = cscale(u[0], m0.x);
-      u[1] = cscale(u[1], m0.y);
-      u[2] = cscale(u[2], m0.z);
-      u[3] = cscale(u[3], m0.w);
-      u[4] = cscale(u[4], m1.x);
-      u[5] = cscale(u[5], m1.y);
-      u[6] = cscale(u[6], m1.z);
-      u[7] = cscale(u[7], m1.w);
-      Dft<8, 1>::run(u);
-      l8_store_row(sc, r, u);   // row r is read and written by this lane only
-    }
-    __syncwarp(lmask);
-    l8_stage1_inv<A>(D + ky, DP, t, par, tw, sc);
-    __syncwarp(lmask);
+  for (int it = lp; it < M / 2; it += NL) {
+    float4 fac[2 * J];
+    l8_load_factors<J>(fac, vrow + (size_t)it * M + t * A2);
+    l8_z_column<A>(D + it, t, par, lmask, tw, sc, fac);
+    if (it == 0) l8_load_factors<J>(fac, vrow + (size_t)(M / 2) * M + t * A2);
+    l8_z_column<A>(D + (it == 0 ? M / 2 : M - it), t, par, lmask, tw, sc, fac);
   }
   __syncthreads();
   // ---- y inverse of the nz rows, keeping y < ny: the rows go from registers straight to

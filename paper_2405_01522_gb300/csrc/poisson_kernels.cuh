@@ -848,7 +848,7 @@ __device__ __forceinline__ void pass3_item(const Geom& g, const PairMap<R>& pm, 
   if (t < AX) {
     const int ra = 2 * line, rb = ra + 1;
 #pragma unroll
-    for (int k2 = 0; k2 < 16; ++k2) {
+    for (int k2 = 0; k2 < ((AX % 2 == 0) ? 8 : 16); ++k2) {   // x = t + AX k2 < nx = 8 AX
       const int x = t + AX * k2;
       if (x < g.nx) {
         if (ra < nrow) tile[ra * g.nx + x] = acc0[k2];

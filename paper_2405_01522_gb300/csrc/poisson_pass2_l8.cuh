@@ -43,6 +43,29 @@ __device__ __forceinline__ void l8_store_row(Cx<float>* sc, int r, const Cx<floa
   for (int q = 0; q < 4; ++q) rp[q ^ sw] = make_float4(u[2 * q].x, u[2 * q].y, u[2 * q + 1].x, u[2 * q + 1].y);
 }
 
+// Row pitch of the work plane, M + 2 complex: every row starts on a 16-byte boundary (the
+// next plane is prefetched with 16-byte copies).  Bank pairs (8-byte units) of an access
+// are then 2 row + column mod 16: the two lines of a half-warp take rows 4 apart (the
+// 8 consecutive columns of a row access land 8 bank pairs apart) and z columns 1 apart
+// (the 8 rows t + 8 a of a column access fall on even bank pairs for one line, odd ones
+// for the other).
+template <int A>
+__host__ __device__ constexpr int l8_pitch() { return 16 * A + 2; }
+
+// the next plane P (NB x NB complex, contiguous) into the upper halves of D's rows,
+// columns [NB, 2 NB), as 16-byte cp.async copies
+template <int A, int NT>
+__device__ __forceinline__ void l8_prefetch_plane(Cx<float>* D, const Cx<float>* P) {
+  constexpr int NB = 8 * A, DP = l8_pitch<A>(), G = NB / 2;   // granules (2 complex) per row
+  for (int i = threadIdx.x; i < NB * G; i += NT) {
+    const int z = i / G, y = 2 * (i - z * G);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(D + z * DP + NB + y)),
+                 "l"(P + z * NB + y)
+                 : "memory");
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
 // This lane's stage-1 twiddles w_M^{-t k1}, k1 < 2A: held in registers (TWS = false) or
 // read from a shared table [k1][t] (TWS = true: 46 fewer live registers at A = 12; the
 // eight lanes of a line read 64 contiguous bytes, the lines of a warp the same ones).
@@ -105,11 +128,11 @@ __device__ __forceinline__ void l8_load_factors(float4 (&fac)[2 * J], const floa
   for (int i = 0; i < 2 * J; ++i) fac[i] = __ldg(vq + i);
 }
 
-// z forward, kernel multiply, z inverse of one column (col = D + ky, row pitch M + 1)
+// z forward, kernel multiply, z inverse of one column (col = D + ky, row pitch l8_pitch)
 template <int A, class TW>
 __device__ __forceinline__ void l8_z_column(Cx<float>* col, int t, int par, unsigned lmask, const TW& tw,
                                             Cx<float>* sc, const float4 (&fac)[2 * (2 * A / 8)]) {
-  constexpr int A2 = 2 * A, J = A2 / 8, DP = 16 * A + 1;
+  constexpr int A2 = 2 * A, J = A2 / 8, DP = l8_pitch<A>();
   l8_stage1_fwd<A>(col, DP, t, par, tw, sc);
   __syncwarp(lmask);
 #pragma unroll
@@ -135,18 +158,18 @@ __device__ __forceinline__ void l8_z_column(Cx<float>* col, int t, int par, unsi
   __syncwarp(lmask);
 }
 
-// one (pair, kx) plane; D: (nz x My) work plane, row pitch M + 1, input rows staged in
+// one (pair, kx) plane; D: (nz x My) work plane, row pitch l8_pitch, input rows staged in
 // columns [ny, 2 ny) (prefetched); the y inverse writes the result to the plane P in
 // global memory
 template <int A, int NT, class TW>
 __device__ __forceinline__ void l8_plane(Cx<float>* P, int kx, int Hy, const float* __restrict__ vl8, Cx<float>* D,
-                                         Cx<float>* sc, int lp, int t, int par, unsigned lmask, const TW& tw,
+                                         Cx<float>* sc, int lrow, int litem, int t, int par, unsigned lmask, const TW& tw,
                                          const Cx<float>* Pnext) {
-  constexpr int A2 = 2 * A, J = A2 / 8, M = 16 * A, NB = 8 * A, DP = M + 1, NL = NT / 8;
+  constexpr int A2 = 2 * A, J = A2 / 8, M = 16 * A, NB = 8 * A, DP = l8_pitch<A>(), NL = NT / 8;
   asm volatile("cp.async.wait_group 0;" ::: "memory");
   __syncthreads();
   // ---- y forward of the nz rows (input columns [NB, 2 NB), outputs all M columns)
-  for (int z = lp; z < NB; z += NL) {
+  for (int z = lrow; z < NB; z += NL) {
     Cx<float>* row = D + z * DP;
     l8_stage1_fwd<A>(row + NB, 1, t, par, tw, sc);
     __syncwarp(lmask);
@@ -167,7 +190,7 @@ __device__ __forceinline__ void l8_plane(Cx<float>* P, int kx, int Hy, const flo
   // item (item 0: the two unpaired columns 0 and M / 2), loading the factors once, before
   // the first column's stage 1, which covers the loads' latency.
   const float* vrow = vl8 + (size_t)kx * Hy * M;
-  for (int it = lp; it < M / 2; it += NL) {
+  for (int it = litem; it < M / 2; it += NL) {
     float4 fac[2 * J];
     l8_load_factors<J>(fac, vrow + (size_t)it * M + t * A2);
     l8_z_column<A>(D + it, t, par, lmask, tw, sc, fac);
@@ -177,7 +200,7 @@ __device__ __forceinline__ void l8_plane(Cx<float>* P, int kx, int Hy, const flo
   __syncthreads();
   // ---- y inverse of the nz rows, keeping y < ny: the rows go from registers straight to
   // the plane in global memory
-  for (int z = lp; z < NB; z += NL) {
+  for (int z = lrow; z < NB; z += NL) {
     Cx<float>* row = D + z * DP;
 #pragma unroll
     for (int j = 0; j < J; ++j) {
@@ -193,18 +216,18 @@ __device__ __forceinline__ void l8_plane(Cx<float>* P, int kx, int Hy, const flo
     __syncwarp(lmask);
   }
   __syncthreads();   // every read of D's upper halves is done
-  if (Pnext) prefetch_plane_upper<float>(D, DP, Pnext, NB, NB, NT);
+  if (Pnext) l8_prefetch_plane<A, NT>(D, Pnext);
 }
 
 // Persistent grid over the work items (pair, kx); the plane lives in shared memory and the
 // next plane is prefetched into the upper halves of its rows behind the current one.
 // tw8[t][k1] = w_M^{-t k1} (t < 8, k1 < 2A); vl8: the kernel table in this kernel's lane
 // order, [kx][|ky|][s][j][k2] with kz = (s + 8 j) + 2A k2.
-// Shared memory: [twiddle table A2 x 8] [line scratch NL x A2 x 8] [plane NB x (M + 1)].
+// Shared memory: [twiddle table A2 x 8] [line scratch NL x A2 x 8] [plane NB x l8_pitch].
 template <int A, int NT, bool TWS>
 __global__ void __launch_bounds__(NT, 1) k_pass2_l8(Geom g, int nq, Cx<float>* __restrict__ inter,
                                                     const Cx<float>* __restrict__ tw8, const float* __restrict__ vl8) {
-  constexpr int A2 = 2 * A, M = 16 * A, NB = 8 * A, DP = M + 1, NL = NT / 8;
+  constexpr int A2 = 2 * A, M = 16 * A, NB = 8 * A, NL = NT / 8;
   static_assert(NL % 16 == 0, "lines per CTA: a multiple of 16 (line pairing)");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Cx<float>* twtab = reinterpret_cast<Cx<float>*>(smem_raw);
@@ -212,8 +235,11 @@ __global__ void __launch_bounds__(NT, 1) k_pass2_l8(Geom g, int nq, Cx<float>* _
   Cx<float>* D = scr + NL * A2 * 8;
   const int lane = threadIdx.x & 31, t = lane & 7, line = threadIdx.x >> 3, par = line & 1;
   const unsigned lmask = 0xFFu << (lane & 24);
-  // the two lines of a half-warp take rows / columns 8 apart (disjoint banks in D)
-  const int lp = (line & ~15) | ((line & 1) << 3) | ((line >> 1) & 7);
+  // the two lines of a half-warp (line 2k, 2k + 1) take rows 4 apart and z items (columns)
+  // 1 apart, see l8_pitch
+  const int k = (line >> 1) & 7;
+  const int lrow = (line & ~15) | (k & 3) | ((k & 4) << 1) | ((line & 1) << 2);
+  const int litem = line;
   Cx<float>* sc = scr + line * A2 * 8;
   if constexpr (TWS) {
     for (int i = threadIdx.x; i < A2 * 8; i += NT) {   // [k1][t] from the table's [t][k1]
@@ -231,17 +257,18 @@ __global__ void __launch_bounds__(NT, 1) k_pass2_l8(Geom g, int nq, Cx<float>* _
     const int ql = w / g.Hx, kx = w - ql * g.Hx;
     return inter + (size_t)ql * g.inter_elems() + (size_t)kx * nplane;
   };
-  if ((int)blockIdx.x < nwork) prefetch_plane_upper<float>(D, DP, plane_ptr(blockIdx.x), NB, NB, NT);
+  if ((int)blockIdx.x < nwork) l8_prefetch_plane<A, NT>(D, plane_ptr(blockIdx.x));
   for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
     const int kx = w % g.Hx;
     const int wn = w + (int)gridDim.x;
-    l8_plane<A, NT>(plane_ptr(w), kx, Hy, vl8, D, sc, lp, t, par, lmask, tw, wn < nwork ? plane_ptr(wn) : nullptr);
+    l8_plane<A, NT>(plane_ptr(w), kx, Hy, vl8, D, sc, lrow, litem, t, par, lmask, tw,
+                    wn < nwork ? plane_ptr(wn) : nullptr);
   }
 }
 
 template <int A>
 inline size_t pass2_l8_smem(int nt) {
-  return sizeof(Cx<float>) * ((size_t)2 * A * 8 + (size_t)(nt / 8) * 2 * A * 8 + (size_t)(8 * A) * (16 * A + 1));
+  return sizeof(Cx<float>) * ((size_t)2 * A * 8 + (size_t)(nt / 8) * 2 * A * 8 + (size_t)(8 * A) * l8_pitch<A>());
 }
 
 }  // namespace rsx

@@ -187,15 +187,26 @@ __device__ __forceinline__ void l8_plane(Cx<float>* P, int kx, int Hy, const flo
   __syncthreads();
   // ---- z forward, kernel multiply, z inverse on the M columns ky.  Columns ky and M - ky
   // use the same kernel factors (the table is folded in |ky|): a line takes them as one
-  // item (item 0: the two unpaired columns 0 and M / 2), loading the factors once, before
-  // the first column's stage 1, which covers the loads' latency.
-  const float* vrow = vl8 + (size_t)kx * Hy * M;
-  for (int it = litem; it < M / 2; it += NL) {
-    float4 fac[2 * J];
-    l8_load_factors<J>(fac, vrow + (size_t)it * M + t * A2);
-    l8_z_column<A>(D + it, t, par, lmask, tw, sc, fac);
-    if (it == 0) l8_load_factors<J>(fac, vrow + (size_t)(M / 2) * M + t * A2);
-    l8_z_column<A>(D + (it == 0 ? M / 2 : M - it), t, par, lmask, tw, sc, fac);
+  // item (item 0: the two unpaired columns 0 and M / 2), 2 columns per item.  The factors
+  // of a column's row |ky| are loaded one column ahead (the DFTs of the column before cover
+  // the loads' latency): fa holds the current row, fb the next one.
+  const float* vrow = vl8 + (size_t)kx * Hy * M + t * A2;
+  const int ncol = 2 * ((M / 2 - litem + NL - 1) / NL);
+  float4 fa[2 * J], fb[2 * J];
+  if (ncol > 0) l8_load_factors<J>(fa, vrow + (size_t)litem * M);   // lines without an item load nothing
+  for (int c = 0; c < ncol; ++c) {
+    const int it = litem + NL * (c >> 1);
+    const int col = (c & 1) ? (it == 0 ? M / 2 : M - it) : it;
+    // the next column's row differs at the start of every item and inside item 0
+    const int itn = litem + NL * ((c + 1) >> 1);
+    const int rown = ((c + 1) & 1) ? (itn == 0 ? M / 2 : itn) : itn;
+    const bool next = c + 1 < ncol && (((c + 1) & 1) == 0 || itn == 0);
+    if (next) l8_load_factors<J>(fb, vrow + (size_t)rown * M);
+    l8_z_column<A>(D + col, t, par, lmask, tw, sc, fa);
+    if (next) {
+#pragma unroll
+      for (int i = 0; i < 2 * J; ++i) fa[i] = fb[i];
+    }
   }
   __syncthreads();
   // ---- y inverse of the nz rows, keeping y < ny: the rows go from registers straight to

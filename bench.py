@@ -133,9 +133,9 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12     # SMs x FP32 lanes x FMA x 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) from ncu captures of the same
 # kernels: pass 2 on the full 512-pair launch at 96^3 (a one-pass metric set), per line
-# split and CTA size (8 lanes x 2A at 256 threads: 3.680 + 3.602 GB); the SYRK on a small
+# split and CTA size (8 lanes x 2A at 256 threads: 3.669 + 3.602 GB); the SYRK on a small
 # case scaled by the panel bytes it reads
-PASS2_DRAM_BYTES_PER_PAIR_96 = {(8, 256): 7.282e9 / 512}
+PASS2_DRAM_BYTES_PER_PAIR_96 = {(8, 256): 7.271e9 / 512}
 SYRK_DRAM_PER_PANEL_BYTE = 1.938e9 / 1.850e9    # DRAM bytes per byte of the two bf16 panels
 
 

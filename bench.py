@@ -124,11 +124,12 @@ def aggregate_rate(world, units_per_step, steps, ms_max):
     return world * units_per_step * steps / (ms_max / 1e3)
 
 
-# Real flops of the register DFTs as implemented (adds + multiplies; odd primes by the
-# symmetric split, 6/10/12/14/24 by Good-Thomas, 8/16 by radix 2/4; a rotation by +-i is a
-# swap, no flops).
-DFT_FLOPS = {1: 0, 2: 4, 3: 16, 4: 16, 5: 52, 6: 44, 7: 102, 8: 60, 10: 124, 12: 112, 14: 232, 16: 176,
-             24: 3 * 60 + 8 * 16}
+# Real flops of the register DFTs as implemented (adds + multiplies, a fused multiply-add
+# counting 2; odd primes by the symmetric split, 6/10/12/14/24 by Good-Thomas, 8/16 by
+# radix 2/4; a rotation by +-i is a swap, no flops).  tests/test_flop_model.py counts the
+# codelets' operations on the host and checks these figures and the pruned forms below.
+DFT_FLOPS = {1: 0, 2: 4, 3: 18, 4: 16, 5: 52, 6: 48, 7: 102, 8: 60, 10: 124, 12: 120, 14: 232, 16: 176,
+             24: 3 * 60 + 8 * 18}
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12     # SMs x FP32 lanes x FMA x max SM clock
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) from ncu captures of the same

@@ -128,7 +128,8 @@ int record(rsx_batch* b, cudaStream_t s) {
     const long long nwork = (long long)grp.npairs * c->g.Hx;
     const int grid = (int)std::min<long long>(nwork, (long long)c->pass2_ctas_per_sm<float>() * c->nsm);
     rc = bcuda(b, launch_pass2<float>(c->g, grp.npairs, inter, (const Cx<float>*)c->tw[1], (const Cx<float>*)c->tw[0],
-                                      (const float*)c->vhat, (const float*)c->vhatz, nullptr, grid, s),
+                                      (const float*)c->vhat, (const float*)c->vhatz, nullptr, grid, s,
+                                      (const Cx<float>*)c->tw8, (const float*)c->vhatz8),
                "batch pass 2");
     if (rc) return rc;
     rc = bcuda(b, launch_pass3<float>(c->g, pm, 0, 0, grp.nout, 0, inter, twx, nullptr, s), "batch pass 3");
@@ -189,7 +190,15 @@ int rsx_batch_create(rsx_batch** out, int nmol, const int* edges, const int* noc
       rsx_batch_destroy(b);
       return rc;
     }
-    c->g.p2_threads = 384;   // 12 warps where the plane fits (else 256)
+    // y/z transforms: the 8-lane x 2A split where its tables exist (edges a multiple of 32:
+    // every lane busy in both DFT stages, the autotuner's choice at 96^3), else 16 lanes x A
+    // at 12 warps where the plane fits (else 256 threads)
+    if (c->tw8 != nullptr && c->vhatz8 != nullptr) {
+      c->g.p2_lanes = 8;
+      c->g.p2_threads = 256;
+    } else {
+      c->g.p2_threads = 384;
+    }
     b->size_ctx.push_back(c);
   }
   b->size_of_mol.resize(nmol);
